@@ -1,0 +1,581 @@
+/*
+ * oracle.c -- plain FP64 CPU oracle for the PERF Gauss-Newton path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product library links, loads or
+ * calls this file; only the tests, the smoke check and the CPU-baseline leg
+ * of the benchmark do.  It shares no code with the CUDA path.
+ *
+ * What it computes (PERF, Rasmuson, Sintorn, Assarsson):
+ *   - the discrete ray march of Eq. 3-4 through the RGBA voxel grid, followed
+ *     by the environment-map shells intersected in order from the grid exit
+ *     outwards (Section "Volume Rendering", Section "Rendering");
+ *   - residuals r = H^ - C and the objective of Eq. 5-6;
+ *   - the analytic partial derivatives of Eq. 3 by Algorithm 1 (backward
+ *     traversal with the two auxiliaries V and G), chained through the
+ *     trilinear / bilinear interpolation weights;
+ *   - J p, J^T v and the exact diag(J^T J) of Section "Preconditioner"
+ *     together with the gradient J^T r.
+ *
+ * Readings of the paper taken here (each is listed with its reason in the
+ * design notes of the repository):
+ *   - V in Algorithm 1 is the optical depth sum sigma_i delta_i (the paper
+ *     initialises it with an exponential but subtracts sigma_i delta_i and
+ *     exponentiates it afterwards); e^{-V} is then the transmittance T_i.
+ *   - delta is measured in voxel sides (delta_bar = delta / h), so sigma is an
+ *     opacity per voxel side; a shell hit counts as one sample with
+ *     delta_bar = 1.
+ *   - The step is the voxel side shortened to split the chord evenly:
+ *     K = ceil(L / h) samples at t_in + (k + 1/2 + j_k) delta, delta = L / K.
+ *   - Interpolation is exact trilinear (grid) / bilinear (shells), clamped to
+ *     the edge, in place of texture hardware.
+ *   - The ray itself (pixel -> origin and unit direction, the box entry and
+ *     exit, K, delta, and which shells are hit) is defined in IEEE binary32
+ *     without contraction, the precision in which the kernels take these
+ *     integer decisions; every later quantity is FP64.
+ *   - Jitter uses SplitMix64 (Steele, Lea, Flood 2014) of (seed, epoch, ray,
+ *     stream); it is fixed within one Gauss-Newton step.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -fPIC -shared (see build.py).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OC_MAX_SHELLS 8
+
+typedef struct {
+    int G;              /* grid resolution per axis */
+    int S;              /* number of shells */
+    int env_h, env_w;   /* shell texels (rows = theta, cols = phi) */
+    float radii[OC_MAX_SHELLS];
+    int n_cams, width, height;
+    const float* c2w;   /* n_cams x 3 x 4, row-major */
+    const float* focal; /* n_cams, pixels */
+    int max_samples;
+    int jitter;
+    uint64_t seed;
+    uint32_t epoch;
+    int n_threads;      /* <= 0: OpenMP default */
+} oc_problem;
+
+/* ---------------------------------------------------------------- jitter */
+static uint64_t splitmix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+/* U[0,1) with 24 random bits, exactly representable in binary32. */
+static float oc_uniform(const oc_problem* P, int64_t ray, uint32_t stream) {
+    uint64_t h = splitmix64(P->seed + (uint64_t)P->epoch);
+    h = splitmix64(h + (uint64_t)ray);
+    h = splitmix64(h + (uint64_t)stream);
+    return (float)(h >> 40) * (1.0f / 16777216.0f);
+}
+
+/* --------------------------------------------------- binary32 ray set-up */
+typedef struct {
+    float o[3], d[3];
+    float t_in, t_out, delta;
+    int K;              /* 0: the ray misses the grid */
+    unsigned shell_hit; /* bit s: shell s is hit */
+} oc_ray;
+
+static void oc_ray_setup(const oc_problem* P, int64_t ray, oc_ray* R) {
+    const int64_t hw = (int64_t)P->width * P->height;
+    const int cam = (int)(ray / hw);
+    const int64_t rem = ray % hw;
+    const int row = (int)(rem / P->width);
+    const int col = (int)(rem % P->width);
+    const float* M = P->c2w + 12 * cam;
+    const float f = P->focal[cam];
+    float jx = 0.5f, jy = 0.5f;
+    if (P->jitter) {
+        jx = oc_uniform(P, ray, 0u);
+        jy = oc_uniform(P, ray, 1u);
+    }
+    const float px = (float)col + jx;
+    const float py = (float)row + jy;
+    const float xc = (px - 0.5f * (float)P->width) / f;
+    const float yc = -((py - 0.5f * (float)P->height) / f);
+    float d[3];
+    for (int a = 0; a < 3; ++a) {
+        const float u = M[4 * a + 0] * xc;
+        const float v = M[4 * a + 1] * yc;
+        d[a] = (u + v) - M[4 * a + 2];
+    }
+    const float s0 = d[0] * d[0];
+    const float s1 = d[1] * d[1];
+    const float s2 = d[2] * d[2];
+    const float nn = sqrtf((s0 + s1) + s2);
+    for (int a = 0; a < 3; ++a) {
+        R->d[a] = d[a] / nn;
+        R->o[a] = M[4 * a + 3];
+    }
+    float lo[3], hi[3];
+    int miss = 0;
+    for (int a = 0; a < 3; ++a) {
+        if (R->d[a] != 0.0f) {
+            const float t0 = (-1.0f - R->o[a]) / R->d[a];
+            const float t1 = (1.0f - R->o[a]) / R->d[a];
+            lo[a] = fminf(t0, t1);
+            hi[a] = fmaxf(t0, t1);
+        } else {
+            if (R->o[a] < -1.0f || R->o[a] > 1.0f) miss = 1;
+            lo[a] = -INFINITY;
+            hi[a] = INFINITY;
+        }
+    }
+    R->t_in = fmaxf(fmaxf(fmaxf(lo[0], lo[1]), lo[2]), 0.0f);
+    R->t_out = fminf(fminf(hi[0], hi[1]), hi[2]);
+    R->K = 0;
+    R->delta = 0.0f;
+    if (!miss && R->t_out > R->t_in) {
+        const float h = 2.0f / (float)P->G;
+        const float L = R->t_out - R->t_in;
+        int K = (int)ceilf(L / h);
+        if (K > P->max_samples) K = P->max_samples;
+        if (K < 1) K = 1;
+        R->K = K;
+        R->delta = L / (float)K;
+    }
+    /* far-root shell hits: the ray leaves sphere s at t > 0 */
+    const float b = (R->o[0] * R->d[0] + R->o[1] * R->d[1]) + R->o[2] * R->d[2];
+    const float oo = (R->o[0] * R->o[0] + R->o[1] * R->o[1]) + R->o[2] * R->o[2];
+    R->shell_hit = 0u;
+    for (int s = 0; s < P->S; ++s) {
+        const float rr = P->radii[s] * P->radii[s];
+        const float c = oo - rr;
+        const float bb = b * b;
+        const float disc = bb - c;
+        if (disc > 0.0f && (b < 0.0f || c < 0.0f)) R->shell_hit |= 1u << s;
+    }
+}
+
+/* ------------------------------------------------------- sample records */
+typedef struct {
+    int64_t idx[8];     /* voxel / texel index (parameter block of 4) */
+    double w[8];        /* interpolation weights */
+    int nc;             /* 8 (grid) or 4 (shell) */
+    int is_grid;
+    double sigma, c[3], dbar;
+} oc_sample;
+
+static void oc_trilinear(const oc_problem* P, const double p[3], oc_sample* s) {
+    const int G = P->G;
+    int64_t b[3];
+    double f[3];
+    for (int a = 0; a < 3; ++a) {
+        double u = (p[a] + 1.0) * (0.5 * G) - 0.5;
+        if (u < 0.0) u = 0.0;
+        if (u > (double)(G - 1)) u = (double)(G - 1);
+        double fl = floor(u);
+        if (fl > (double)(G - 2)) fl = (double)(G - 2);
+        b[a] = (int64_t)fl;
+        f[a] = u - fl;
+    }
+    s->nc = 8;
+    s->is_grid = 1;
+    for (int c = 0; c < 8; ++c) {
+        const int cx = c & 1, cy = (c >> 1) & 1, cz = (c >> 2) & 1;
+        const int64_t ix = b[0] + cx, iy = b[1] + cy, iz = b[2] + cz;
+        s->idx[c] = (iz * G + iy) * G + ix;
+        s->w[c] = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) *
+                  (cz ? f[2] : 1.0 - f[2]);
+    }
+}
+
+static void oc_bilinear(const oc_problem* P, int shell, const double q[3],
+                        oc_sample* s) {
+    const int He = P->env_h, We = P->env_w;
+    const double r = sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2]);
+    const double wx = q[0] / r, wy = q[1] / r, wz = q[2] / r;
+    const double phi = atan2(wy, wx);
+    const double theta = atan2(sqrt(wx * wx + wy * wy), wz);
+    const double u = (phi / (2.0 * M_PI) + 0.5) * We - 0.5;
+    double v = theta / M_PI * He - 0.5;
+    const double j0 = floor(u);
+    const double fu = u - j0;
+    int64_t c0 = ((int64_t)j0 % We + We) % We;
+    int64_t c1 = (c0 + 1) % We;
+    if (v < 0.0) v = 0.0;
+    if (v > (double)(He - 1)) v = (double)(He - 1);
+    double i0 = floor(v);
+    if (i0 > (double)(He - 2)) i0 = (double)(He - 2);
+    const double fv = v - i0;
+    const int64_t r0 = (int64_t)i0, r1 = r0 + 1;
+    const int64_t base = (int64_t)P->G * P->G * P->G + (int64_t)shell * He * We;
+    s->nc = 4;
+    s->is_grid = 0;
+    s->idx[0] = base + r0 * We + c0; s->w[0] = (1.0 - fu) * (1.0 - fv);
+    s->idx[1] = base + r0 * We + c1; s->w[1] = fu * (1.0 - fv);
+    s->idx[2] = base + r1 * We + c0; s->w[2] = (1.0 - fu) * fv;
+    s->idx[3] = base + r1 * We + c1; s->w[3] = fu * fv;
+    for (int c = 4; c < 8; ++c) { s->idx[c] = 0; s->w[c] = 0.0; }
+}
+
+static void oc_interp(const double* x, oc_sample* s) {
+    double acc[4] = {0, 0, 0, 0};
+    for (int c = 0; c < s->nc; ++c)
+        for (int ch = 0; ch < 4; ++ch) acc[ch] += s->w[c] * x[4 * s->idx[c] + ch];
+    s->c[0] = acc[0]; s->c[1] = acc[1]; s->c[2] = acc[2];
+    s->sigma = acc[3];
+}
+
+/* Build the ordered sample list of one ray: K grid samples, then the shells
+ * that the ray hits, innermost first.  Returns the count; *n_grid gets K. */
+static int oc_collect(const oc_problem* P, const double* x, int64_t ray,
+                      oc_sample* out, int* n_grid) {
+    oc_ray R;
+    oc_ray_setup(P, ray, &R);
+    const double o[3] = {R.o[0], R.o[1], R.o[2]};
+    const double d[3] = {R.d[0], R.d[1], R.d[2]};
+    const double delta = (double)R.delta;
+    const double dbar = delta * (0.5 * P->G); /* delta / h */
+    int n = 0;
+    for (int k = 0; k < R.K; ++k) {
+        double jk = 0.0;
+        if (P->jitter) jk = (double)oc_uniform(P, ray, 2u + (uint32_t)k) - 0.5;
+        const double t = (double)R.t_in + ((double)k + 0.5 + jk) * delta;
+        const double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+        oc_trilinear(P, p, &out[n]);
+        oc_interp(x, &out[n]);
+        out[n].dbar = dbar;
+        ++n;
+    }
+    *n_grid = n;
+    const double b = o[0] * d[0] + o[1] * d[1] + o[2] * d[2];
+    const double oo = o[0] * o[0] + o[1] * o[1] + o[2] * o[2];
+    for (int s = 0; s < P->S; ++s) {
+        if (!(R.shell_hit & (1u << s))) continue;
+        const double rad = (double)P->radii[s];
+        const double c = oo - rad * rad;
+        double disc = b * b - c;
+        if (disc < 0.0) disc = 0.0;
+        const double sq = sqrt(disc);
+        const double t = (b < 0.0) ? (-b + sq) : (c / (-b - sq));
+        const double q[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+        oc_bilinear(P, s, q, &out[n]);
+        oc_interp(x, &out[n]);
+        out[n].dbar = 1.0;
+        ++n;
+    }
+    return n;
+}
+
+/* Eq. 3-4: H^ = sum_i T_i (1 - e^{-sigma_i dbar_i}) c_i. */
+static void oc_composite(const oc_sample* s, int n, int n_grid, double H[3],
+                         double* T_exit, double* T_final) {
+    double T = 1.0;
+    H[0] = H[1] = H[2] = 0.0;
+    *T_exit = 1.0;
+    for (int i = 0; i < n; ++i) {
+        const double alpha = -expm1(-s[i].sigma * s[i].dbar);
+        for (int k = 0; k < 3; ++k) H[k] += T * alpha * s[i].c[k];
+        T *= exp(-s[i].sigma * s[i].dbar);
+        if (i + 1 == n_grid) *T_exit = T;
+    }
+    if (n_grid == 0) *T_exit = 1.0;
+    *T_final = T;
+}
+
+/* Algorithm 1: backward traversal with the optical depth V and the colour
+ * accumulator G.  dHdc[i] is dH/dc_i (same for the three channels),
+ * dHds[3*i + k] is dH_k/dsigma_i. */
+static void oc_partials(const oc_sample* s, int n, double* dHdc, double* dHds) {
+    double V = 0.0;
+    for (int i = 0; i < n; ++i) V += s[i].sigma * s[i].dbar;
+    double G[3] = {0.0, 0.0, 0.0};
+    for (int i = n - 1; i >= 0; --i) {
+        const double sd = s[i].sigma * s[i].dbar;
+        V = V - sd;
+        const double eV = exp(-V);
+        const double e = exp(-sd);
+        dHdc[i] = eV * (1.0 - e);
+        for (int k = 0; k < 3; ++k)
+            dHds[3 * i + k] = eV * s[i].dbar * e * s[i].c[k] - s[i].dbar * G[k];
+        for (int k = 0; k < 3; ++k) G[k] += eV * (1.0 - e) * s[i].c[k];
+    }
+}
+
+static int oc_nthreads(const oc_problem* P) {
+#ifdef _OPENMP
+    return P->n_threads > 0 ? P->n_threads : omp_get_max_threads();
+#else
+    (void)P;
+    return 1;
+#endif
+}
+
+static int64_t oc_n_rays(const oc_problem* P) {
+    return (int64_t)P->n_cams * P->width * P->height;
+}
+
+static int64_t oc_n_params(const oc_problem* P) {
+    return 4 * ((int64_t)P->G * P->G * P->G + (int64_t)P->S * P->env_h * P->env_w);
+}
+
+static int oc_cap(const oc_problem* P) { return P->max_samples + P->S + 1; }
+
+/* ---------------------------------------------------------- public API */
+
+int oc_param_count(const oc_problem* P, int64_t* n) { *n = oc_n_params(P); return 0; }
+
+/* Render: rgb[3 * j], T_exit[j] (transmittance at the grid exit) and
+ * T_final[j] for ray ids[j] (ids == NULL: all rays in order). */
+int oc_render(const oc_problem* P, const double* x, const int64_t* ids, int64_t n_ids,
+              double* rgb, double* T_exit, double* T_final) {
+    const int64_t N = ids ? n_ids : oc_n_rays(P);
+    const int cap = oc_cap(P);
+#pragma omp parallel num_threads(oc_nthreads(P))
+    {
+        oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t j = 0; j < N; ++j) {
+            const int64_t ray = ids ? ids[j] : j;
+            int ng;
+            const int n = oc_collect(P, x, ray, buf, &ng);
+            double H[3], Te, Tf;
+            oc_composite(buf, n, ng, H, &Te, &Tf);
+            if (rgb) { rgb[3 * j] = H[0]; rgb[3 * j + 1] = H[1]; rgb[3 * j + 2] = H[2]; }
+            if (T_exit) T_exit[j] = Te;
+            if (T_final) T_final[j] = Tf;
+        }
+        free(buf);
+    }
+    return 0;
+}
+
+/* Residuals r = H^ - C (Eq. 5, C8 sign) and F = 1/2 sum r^2 (Eq. 6). */
+int oc_residual(const oc_problem* P, const double* x, const double* target,
+                const int64_t* ids, int64_t n_ids, double* r, double* F) {
+    const int64_t N = ids ? n_ids : oc_n_rays(P);
+    const int cap = oc_cap(P);
+    double acc = 0.0;
+#pragma omp parallel num_threads(oc_nthreads(P)) reduction(+:acc)
+    {
+        oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t j = 0; j < N; ++j) {
+            const int64_t ray = ids ? ids[j] : j;
+            int ng;
+            const int n = oc_collect(P, x, ray, buf, &ng);
+            double H[3], Te, Tf;
+            oc_composite(buf, n, ng, H, &Te, &Tf);
+            for (int k = 0; k < 3; ++k) {
+                const double rk = H[k] - target[3 * j + k];
+                if (r) r[3 * j + k] = rk;
+                acc += 0.5 * rk * rk;
+            }
+        }
+        free(buf);
+    }
+    if (F) *F = acc;
+    return 0;
+}
+
+/* (J p) for the listed rays: sum over samples and interpolation corners of
+ * dH/dx_j p_j, with the partials of Algorithm 1. */
+int oc_jvp(const oc_problem* P, const double* x, const double* p, const int64_t* ids,
+           int64_t n_ids, double* out) {
+    const int64_t N = ids ? n_ids : oc_n_rays(P);
+    const int cap = oc_cap(P);
+#pragma omp parallel num_threads(oc_nthreads(P))
+    {
+        oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
+        double* dc = (double*)malloc(sizeof(double) * cap);
+        double* ds = (double*)malloc(sizeof(double) * 3 * cap);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t j = 0; j < N; ++j) {
+            const int64_t ray = ids ? ids[j] : j;
+            int ng;
+            const int n = oc_collect(P, x, ray, buf, &ng);
+            oc_partials(buf, n, dc, ds);
+            double acc[3] = {0, 0, 0};
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < buf[i].nc; ++c) {
+                    const int64_t q = 4 * buf[i].idx[c];
+                    const double w = buf[i].w[c];
+                    for (int k = 0; k < 3; ++k)
+                        acc[k] += w * (dc[i] * p[q + k] + ds[3 * i + k] * p[q + 3]);
+                }
+            out[3 * j] = acc[0]; out[3 * j + 1] = acc[1]; out[3 * j + 2] = acc[2];
+        }
+        free(buf); free(dc); free(ds);
+    }
+    return 0;
+}
+
+/* Reduce per-thread n-vectors into out (fixed thread order). */
+static void oc_reduce(double** parts, int nt, int64_t n, double* out, int accumulate) {
+    for (int64_t q = 0; q < n; ++q) {
+        double s = accumulate ? out[q] : 0.0;
+        for (int t = 0; t < nt; ++t) s += parts[t][q];
+        out[q] = s;
+    }
+}
+
+/* out = J^T v (all rays): out_j = sum_rays sum_k v_k dr_k/dx_j. */
+int oc_vjp(const oc_problem* P, const double* x, const double* v, double* out,
+           int accumulate) {
+    const int64_t N = oc_n_rays(P);
+    const int64_t np = oc_n_params(P);
+    const int cap = oc_cap(P);
+    const int nt = oc_nthreads(P);
+    double** parts = (double**)calloc(nt, sizeof(double*));
+#pragma omp parallel num_threads(nt)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* acc = (double*)calloc(np, sizeof(double));
+        parts[tid] = acc;
+        oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
+        double* dc = (double*)malloc(sizeof(double) * cap);
+        double* ds = (double*)malloc(sizeof(double) * 3 * cap);
+#pragma omp for schedule(dynamic, 256)
+        for (int64_t ray = 0; ray < N; ++ray) {
+            const double* vr = v + 3 * ray;
+            if (vr[0] == 0.0 && vr[1] == 0.0 && vr[2] == 0.0) continue;
+            int ng;
+            const int n = oc_collect(P, x, ray, buf, &ng);
+            oc_partials(buf, n, dc, ds);
+            for (int i = 0; i < n; ++i) {
+                const double gs = vr[0] * ds[3 * i] + vr[1] * ds[3 * i + 1] +
+                                  vr[2] * ds[3 * i + 2];
+                for (int c = 0; c < buf[i].nc; ++c) {
+                    const int64_t q = 4 * buf[i].idx[c];
+                    const double w = buf[i].w[c];
+                    for (int k = 0; k < 3; ++k) acc[q + k] += w * dc[i] * vr[k];
+                    acc[q + 3] += w * gs;
+                }
+            }
+        }
+        free(buf); free(dc); free(ds);
+    }
+    int used = 0;
+    for (int t = 0; t < nt; ++t) if (parts[t]) used = t + 1;
+    oc_reduce(parts, used, np, out, accumulate);
+    for (int t = 0; t < nt; ++t) free(parts[t]);
+    free(parts);
+    return 0;
+}
+
+typedef struct { int64_t q; int k; double val; } oc_entry;
+
+static int oc_entry_cmp(const void* a, const void* b) {
+    const oc_entry* x = (const oc_entry*)a;
+    const oc_entry* y = (const oc_entry*)b;
+    if (x->q != y->q) return x->q < y->q ? -1 : 1;
+    return x->k - y->k;
+}
+
+/* Exact Jacobi diagonal diag(J^T J)_q = sum_rows (dr/dx_q)^2 and (when r is
+ * given) the gradient J^T r.  Each row's entry for parameter q is first
+ * summed over all samples of the ray that touch q, then squared. */
+int oc_diag_grad(const oc_problem* P, const double* x, const double* r,
+                 double* diag, double* grad) {
+    const int64_t N = oc_n_rays(P);
+    const int64_t np = oc_n_params(P);
+    const int cap = oc_cap(P);
+    const int nt = oc_nthreads(P);
+    double** pd = (double**)calloc(nt, sizeof(double*));
+    double** pg = (double**)calloc(nt, sizeof(double*));
+#pragma omp parallel num_threads(nt)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double* ad = (double*)calloc(np, sizeof(double));
+        double* ag = (double*)calloc(np, sizeof(double));
+        pd[tid] = ad;
+        pg[tid] = ag;
+        oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
+        double* dc = (double*)malloc(sizeof(double) * cap);
+        double* ds = (double*)malloc(sizeof(double) * 3 * cap);
+        oc_entry* ent = (oc_entry*)malloc(sizeof(oc_entry) * (size_t)cap * 8 * 6);
+#pragma omp for schedule(dynamic, 64)
+        for (int64_t ray = 0; ray < N; ++ray) {
+            int ng;
+            const int n = oc_collect(P, x, ray, buf, &ng);
+            oc_partials(buf, n, dc, ds);
+            int64_t ne = 0;
+            for (int i = 0; i < n; ++i)
+                for (int c = 0; c < buf[i].nc; ++c) {
+                    const int64_t q = 4 * buf[i].idx[c];
+                    const double w = buf[i].w[c];
+                    for (int k = 0; k < 3; ++k) {
+                        ent[ne].q = q + k; ent[ne].k = k; ent[ne].val = w * dc[i]; ++ne;
+                        ent[ne].q = q + 3; ent[ne].k = k; ent[ne].val = w * ds[3 * i + k]; ++ne;
+                    }
+                }
+            qsort(ent, (size_t)ne, sizeof(oc_entry), oc_entry_cmp);
+            int64_t a = 0;
+            while (a < ne) {
+                int64_t b = a;
+                double g[3] = {0, 0, 0};
+                while (b < ne && ent[b].q == ent[a].q) { g[ent[b].k] += ent[b].val; ++b; }
+                const int64_t q = ent[a].q;
+                ad[q] += g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
+                if (r) ag[q] += g[0] * r[3 * ray] + g[1] * r[3 * ray + 1] + g[2] * r[3 * ray + 2];
+                a = b;
+            }
+        }
+        free(buf); free(dc); free(ds); free(ent);
+    }
+    int used = 0;
+    for (int t = 0; t < nt; ++t) if (pd[t]) used = t + 1;
+    if (diag) oc_reduce(pd, used, np, diag, 0);
+    if (grad && r) oc_reduce(pg, used, np, grad, 0);
+    for (int t = 0; t < nt; ++t) { free(pd[t]); free(pg[t]); }
+    free(pd); free(pg);
+    return 0;
+}
+
+/* Per-sample record of one ray, for invariant checks: returns the number of
+ * samples n (grid first, then shells) and fills, for i < min(n, cap):
+ * T_before[i], alpha[i], sigma[i], c[3i..3i+2], dbar[i]; *n_grid = K. */
+int oc_ray_samples(const oc_problem* P, const double* x, int64_t ray, int cap,
+                   double* T_before, double* alpha, double* sigma, double* c,
+                   double* dbar, int* n_grid) {
+    const int cc = oc_cap(P);
+    oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cc);
+    int ng;
+    const int n = oc_collect(P, x, ray, buf, &ng);
+    double T = 1.0;
+    for (int i = 0; i < n && i < cap; ++i) {
+        const double a = -expm1(-buf[i].sigma * buf[i].dbar);
+        T_before[i] = T;
+        alpha[i] = a;
+        sigma[i] = buf[i].sigma;
+        for (int k = 0; k < 3; ++k) c[3 * i + k] = buf[i].c[k];
+        dbar[i] = buf[i].dbar;
+        T *= exp(-buf[i].sigma * buf[i].dbar);
+    }
+    *n_grid = ng;
+    free(buf);
+    return n;
+}
+
+/* The binary32 ray definition, exposed for checks of the host-side logic. */
+int oc_ray_info(const oc_problem* P, int64_t ray, float* o, float* d, float* t_in,
+                float* t_out, float* delta, int* K, unsigned* shell_hit) {
+    oc_ray R;
+    oc_ray_setup(P, ray, &R);
+    for (int a = 0; a < 3; ++a) { o[a] = R.o[a]; d[a] = R.d[a]; }
+    *t_in = R.t_in; *t_out = R.t_out; *delta = R.delta; *K = R.K;
+    *shell_hit = R.shell_hit;
+    return 0;
+}
+
+/* SplitMix64 uniform draw, exposed for cross-checks. */
+float oc_jitter_uniform(const oc_problem* P, int64_t ray, uint32_t stream) {
+    return oc_uniform(P, ray, stream);
+}

@@ -1,0 +1,309 @@
+"""Seeded synthetic scenes for the PERF Gauss-Newton path.
+
+This module only *describes* inputs: voxel grids, environment-map shells,
+pinhole cameras and starting guesses.  It holds none of the method's
+arithmetic (no ray marching, no compositing, no derivatives); both the
+FP64 CPU oracle and the CUDA library consume the arrays it returns.
+
+Conventions (PERF, Section "Method" and Section "Implementation"):
+
+* The RGBA voxel grid has G^3 cells spanning [-1, 1]^3, voxel side h = 2/G,
+  cell (ix, iy, iz) centred at -1 + (i + 1/2) h.  Parameters are stored
+  ``[iz][iy][ix][4]`` (x fastest) with channels (r, g, b, sigma).
+* S environment-map shells (equirectangular, H_e x W_e texels, RGBA) follow
+  the grid in the parameter vector, innermost first, each ``[row][col][4]``;
+  row 0 is the +z pole.
+* A camera is a 3x4 camera-to-world matrix (columns: right, up, back,
+  position; the camera looks down its -z axis) plus a focal length in
+  pixels.  Pixel (col, row) has its centre at (col + 1/2, row + 1/2), rows
+  going down the image.
+* sigma is the differential opacity per voxel side (sigma = 0.9 absorbs
+  1 - e^-0.9 of the light over one voxel side).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional
+
+import numpy as np
+
+__all__ = [
+    "SceneConfig", "Scene", "CONFIGS", "make_scene", "param_count",
+    "look_at_c2w", "focal_from_fov", "constant_params", "random_params",
+    "ray_count",
+]
+
+
+@dataclasses.dataclass(frozen=True)
+class SceneConfig:
+    name: str
+    G: int
+    radii: tuple            # shell radii, innermost first
+    env_h: int
+    env_w: int
+    n_prims: int
+    prim_kinds: tuple        # ("ellipsoid",) or ("ellipsoid", "box")
+    prim_size: tuple         # (lo, hi) semi-axis / half-extent range
+    n_cams: int
+    width: int
+    height: int
+    cam_radius: float
+    cam_layout: str          # "sphere" | "hemisphere" | "ring"
+    fov_deg: float = 40.0
+    max_samples: int = 64
+    gn_steps: int = 5
+    pcg_iters: int = 20
+    start_rgb: float = 0.5
+    start_sigma: float = 0.05
+    ring_elev_deg: float = 15.0
+    background_sigma: Optional[float] = None   # opaque textured outer shell
+    n_heldout: int = 10
+    seed: int = 1234
+
+
+# The five workloads.  Sizes follow the configurations the method is
+# measured on; shell radii and ring elevation that the workload text leaves
+# open are fixed here (2, 4, 8, 16 and 15 degrees).
+CONFIGS = {
+    "small32": SceneConfig(
+        name="small32", G=32, radii=(2.0, 4.0), env_h=32, env_w=64,
+        n_prims=3, prim_kinds=("ellipsoid",), prim_size=(0.15, 0.45),
+        n_cams=8, width=64, height=64, cam_radius=3.0, cam_layout="sphere",
+        max_samples=64, gn_steps=5, pcg_iters=20, seed=1234),
+    "scale128": SceneConfig(
+        name="scale128", G=128, radii=(2.0, 4.0, 8.0), env_h=256, env_w=512,
+        n_prims=20, prim_kinds=("ellipsoid", "box"), prim_size=(0.1, 0.4),
+        n_cams=100, width=800, height=800, cam_radius=4.0,
+        cam_layout="hemisphere", max_samples=256, gn_steps=10, pcg_iters=50,
+        seed=1235),
+    "bf16_256": SceneConfig(
+        name="bf16_256", G=256, radii=(2.0, 4.0, 8.0, 16.0), env_h=512,
+        env_w=1024, n_prims=60, prim_kinds=("ellipsoid", "box"),
+        prim_size=(0.08, 0.3), n_cams=100, width=800, height=800,
+        cam_radius=4.0, cam_layout="hemisphere", max_samples=512,
+        gn_steps=10, pcg_iters=50, seed=1236),
+    "ring256": SceneConfig(
+        name="ring256", G=256, radii=(2.0, 4.0, 8.0, 16.0), env_h=512,
+        env_w=1024, n_prims=60, prim_kinds=("ellipsoid", "box"),
+        prim_size=(0.08, 0.3), n_cams=150, width=960, height=540,
+        cam_radius=4.0, cam_layout="ring", max_samples=512, gn_steps=10,
+        pcg_iters=50, background_sigma=10.0, seed=1238),
+}
+
+
+def param_count(G: int, n_shells: int, env_h: int, env_w: int) -> int:
+    """n = 4 (G^3 + S H_e W_e): four unknowns per voxel and per texel."""
+    return 4 * (G ** 3 + n_shells * env_h * env_w)
+
+
+def ray_count(n_cams: int, width: int, height: int) -> int:
+    return n_cams * width * height
+
+
+def focal_from_fov(width: int, fov_deg: float) -> float:
+    """Focal length in pixels for a horizontal field of view."""
+    return 0.5 * width / math.tan(0.5 * math.radians(fov_deg))
+
+
+def look_at_c2w(pos) -> np.ndarray:
+    """3x4 camera-to-world matrix of a camera at ``pos`` looking at the
+    origin, up = +z (falling back to +y when looking almost along z)."""
+    pos = np.asarray(pos, dtype=np.float64)
+    fwd = -pos / np.linalg.norm(pos)
+    up = np.array([0.0, 0.0, 1.0])
+    if abs(float(fwd @ up)) > 0.999:
+        up = np.array([0.0, 1.0, 0.0])
+    right = np.cross(fwd, up)
+    right /= np.linalg.norm(right)
+    cam_up = np.cross(right, fwd)
+    m = np.zeros((3, 4))
+    m[:, 0] = right
+    m[:, 1] = cam_up
+    m[:, 2] = -fwd
+    m[:, 3] = pos
+    return m
+
+
+def _camera_positions(rng, n, radius, layout, elev_deg):
+    if layout == "ring":
+        el = math.radians(elev_deg)
+        az = 2.0 * np.pi * np.arange(n) / n
+        return np.stack([radius * np.cos(el) * np.cos(az),
+                         radius * np.cos(el) * np.sin(az),
+                         np.full(n, radius * np.sin(el))], axis=1)
+    v = rng.normal(size=(n, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    if layout == "hemisphere":
+        v[:, 2] = np.abs(v[:, 2])
+    return radius * v
+
+
+def _rotation(rng):
+    q = rng.normal(size=4)
+    q /= np.linalg.norm(q)
+    a, b, c, d = q
+    return np.array([
+        [a*a + b*b - c*c - d*d, 2*(b*c - a*d), 2*(b*d + a*c)],
+        [2*(b*c + a*d), a*a - b*b + c*c - d*d, 2*(c*d - a*b)],
+        [2*(b*d - a*c), 2*(c*d + a*b), a*a - b*b - c*c + d*d]])
+
+
+def _voxelise(rng, G, n_prims, kinds, size, sigma_inside=0.9):
+    """Primitives evaluated at voxel centres: sigma = 0.9 inside, 0 outside;
+    one uniform RGB colour per primitive (later primitives overwrite)."""
+    grid = np.zeros((G, G, G, 4), dtype=np.float32)
+    h = 2.0 / G
+    centres = -1.0 + (np.arange(G) + 0.5) * h
+    for q in range(n_prims):
+        kind = kinds[q % len(kinds)]
+        c = rng.uniform(-0.6, 0.6, size=3)
+        ax = rng.uniform(size[0], size[1], size=3)
+        R = _rotation(rng)
+        rgb = rng.uniform(0.0, 1.0, size=3)
+        r = float(np.linalg.norm(ax)) + h
+        lo = np.searchsorted(centres, c - r)
+        hi = np.searchsorted(centres, c + r)
+        sl = [slice(int(lo[a]), int(hi[a])) for a in range(3)]
+        zz, yy, xx = np.meshgrid(centres[sl[2]], centres[sl[1]],
+                                 centres[sl[0]], indexing="ij")
+        p = np.stack([xx - c[0], yy - c[1], zz - c[2]], axis=-1) @ R
+        if kind == "ellipsoid":
+            inside = np.sum((p / ax) ** 2, axis=-1) <= 1.0
+        else:
+            inside = np.all(np.abs(p) <= ax, axis=-1)
+        blk = grid[sl[2], sl[1], sl[0]]
+        blk[inside, 0:3] = rgb
+        blk[inside, 3] = sigma_inside
+    return grid
+
+
+def _env_noise(rng, H, W, sigma_max):
+    """Smooth seeded noise: per channel a sum of 8 low-frequency sinusoids
+    in (theta, phi), periodic in phi, mapped to [0, 1] (RGB) and
+    [0, sigma_max] (sigma)."""
+    theta = (np.arange(H) + 0.5) / H * np.pi
+    phi = (np.arange(W) + 0.5) / W * 2.0 * np.pi - np.pi
+    T, P = np.meshgrid(theta, phi, indexing="ij")
+    out = np.zeros((H, W, 4), dtype=np.float64)
+    for ch in range(4):
+        acc = np.zeros((H, W))
+        for _ in range(8):
+            k = rng.uniform(0.5, 4.0)
+            l = float(rng.integers(0, 5))
+            ph = rng.uniform(0, 2 * np.pi)
+            acc += rng.uniform(0.3, 1.0) * np.sin(k * T + l * P + ph)
+        acc = (acc - acc.min()) / max(acc.max() - acc.min(), 1e-12)
+        out[..., ch] = acc if ch < 3 else sigma_max * acc
+    return out.astype(np.float32)
+
+
+@dataclasses.dataclass
+class Scene:
+    cfg: SceneConfig
+    G: int
+    radii: np.ndarray        # float32 [S]
+    env_h: int
+    env_w: int
+    c2w: np.ndarray          # float32 [n_cams, 3, 4]
+    focal: np.ndarray        # float32 [n_cams]
+    width: int
+    height: int
+    x_gt: np.ndarray         # float32 [n] ground-truth parameters
+    x0: np.ndarray           # float32 [n] starting guess
+    heldout_c2w: np.ndarray  # float32 [n_heldout, 3, 4]
+    heldout_focal: np.ndarray
+
+    @property
+    def n_shells(self) -> int:
+        return int(self.radii.shape[0])
+
+    @property
+    def n_params(self) -> int:
+        return param_count(self.G, self.n_shells, self.env_h, self.env_w)
+
+    @property
+    def n_cams(self) -> int:
+        return int(self.c2w.shape[0])
+
+    @property
+    def n_rays(self) -> int:
+        return ray_count(self.n_cams, self.width, self.height)
+
+
+def constant_params(G, n_shells, env_h, env_w, rgb=0.5, sigma=0.05):
+    n = param_count(G, n_shells, env_h, env_w)
+    x = np.empty((n // 4, 4), dtype=np.float32)
+    x[:, 0:3] = rgb
+    x[:, 3] = sigma
+    return x.reshape(-1)
+
+
+def random_params(rng, G, n_shells, env_h, env_w, sigma_lo=0.0, sigma_hi=1.0,
+                  shell_sigma_hi=None):
+    """Uniform random colours in [0,1] and opacities in [sigma_lo, sigma_hi]."""
+    n = param_count(G, n_shells, env_h, env_w)
+    x = rng.uniform(0.0, 1.0, size=(n // 4, 4))
+    x[:, 3] = rng.uniform(sigma_lo, sigma_hi, size=n // 4)
+    if shell_sigma_hi is not None:
+        g = G ** 3
+        x[g:, 3] = rng.uniform(sigma_lo, shell_sigma_hi, size=n // 4 - g)
+    return x.astype(np.float32).reshape(-1)
+
+
+def make_cameras(rng, n, width, radius, layout, fov_deg, elev_deg=15.0):
+    pos = _camera_positions(rng, n, radius, layout, elev_deg)
+    c2w = np.stack([look_at_c2w(p) for p in pos]).astype(np.float32)
+    focal = np.full(n, focal_from_fov(width, fov_deg), dtype=np.float32)
+    return c2w, focal
+
+
+def make_scene(cfg, seed: Optional[int] = None, n_cams: Optional[int] = None,
+               G: Optional[int] = None) -> Scene:
+    """Build the seeded scene of a workload.  ``n_cams`` / ``G`` override the
+    camera count or grid size (for reduced test cases)."""
+    if isinstance(cfg, str):
+        cfg = CONFIGS[cfg]
+    if G is not None or n_cams is not None:
+        cfg = dataclasses.replace(cfg, G=G or cfg.G, n_cams=n_cams or cfg.n_cams)
+    rng = np.random.default_rng(cfg.seed if seed is None else seed)
+    grid = _voxelise(rng, cfg.G, cfg.n_prims, cfg.prim_kinds, cfg.prim_size)
+    shells = []
+    S = len(cfg.radii)
+    for s in range(S):
+        env = _env_noise(rng, cfg.env_h, cfg.env_w, 3.0)
+        if cfg.background_sigma is not None and s == S - 1:
+            env[..., 3] = cfg.background_sigma
+        shells.append(env.reshape(-1))
+    x_gt = np.concatenate([grid.reshape(-1)] + shells).astype(np.float32)
+    c2w, focal = make_cameras(rng, cfg.n_cams, cfg.width, cfg.cam_radius,
+                              cfg.cam_layout, cfg.fov_deg, cfg.ring_elev_deg)
+    hc2w, hfocal = make_cameras(rng, cfg.n_heldout, cfg.width, cfg.cam_radius,
+                                "hemisphere" if cfg.cam_layout != "sphere"
+                                else "sphere", cfg.fov_deg)
+    x0 = constant_params(cfg.G, S, cfg.env_h, cfg.env_w,
+                         cfg.start_rgb, cfg.start_sigma)
+    return Scene(cfg=cfg, G=cfg.G, radii=np.asarray(cfg.radii, np.float32),
+                 env_h=cfg.env_h, env_w=cfg.env_w, c2w=c2w, focal=focal,
+                 width=cfg.width, height=cfg.height, x_gt=x_gt, x0=x0,
+                 heldout_c2w=hc2w, heldout_focal=hfocal)
+
+
+def sample_ray_ids(rng, n_rays: int, k: int) -> np.ndarray:
+    """k distinct ray indices (sorted) for sampled parity checks."""
+    k = min(k, n_rays)
+    return np.sort(rng.choice(n_rays, size=k, replace=False)).astype(np.int64)
+
+
+def batch_scene_configs(rng, n_scenes=64, G_lo=32, G_hi=96, cams_lo=8,
+                        cams_hi=40, res=128, shells_lo=1, shells_hi=3) -> List[dict]:
+    """Uneven scene descriptions for the many-scenes workload: grid sizes
+    uniform in [32, 96], 8-40 cameras at 128x128, 1-3 shells of G x 2G."""
+    out = []
+    for i in range(n_scenes):
+        G = int(rng.integers(G_lo, G_hi + 1))
+        S = int(rng.integers(shells_lo, shells_hi + 1))
+        out.append(dict(G=G, n_cams=int(rng.integers(cams_lo, cams_hi + 1)),
+                        res=res, radii=tuple(2.0 * 2 ** s for s in range(S)),
+                        env_h=G, env_w=2 * G, seed=int(rng.integers(1 << 30))))
+    return out
