@@ -1,0 +1,326 @@
+#!/usr/bin/env python
+"""Benchmark of the PERF Gauss-Newton step on GB300.
+
+One step = one Gauss-Newton step of the 128^3 workload (3 shells 256x512,
+100 cameras 800x800, up to 256 samples per ray): residuals and F, gradient
+and exact Jacobi diagonal, 50 fixed PCG iterations (each one A p ray march
+plus the fused vector kernels), and the Algorithm 3 line search.  The metric
+is PCG iterations per second over whole Gauss-Newton steps (line search and
+set-up included).  Inputs are synthetic (seeded scene, targets rendered from
+the voxelised ground truth); the targets (768 MB) and residuals (768 MB) are
+larger than L2, so every step streams them from HBM.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+With N > 1 (torchrun) every rank runs an independent replica of the
+workload (the single-scene step has no exchange to shard without a
+collective); value = all ranks' PCG iterations / max-over-ranks time.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np
+
+WORKLOAD = "scale128"
+METRIC = "PCG iters/s"
+
+# Algorithmic work of one A p launch (fused J p and J^T (J p)), per ray-march
+# sample: tangent sweep = two 4-channel trilinear interpolations (x and p,
+# 7 lerps x 4 channels x 2 FLOP each = 112) + 28 FLOP of the transmittance /
+# tangent recurrence; adjoint sweep = one interpolation of x (56) + 12 FLOP of
+# corner weights + 27 FLOP of Algorithm 1 partials + 32 FLOP accumulating the
+# (w_i, v.dH/dsigma_i) pair into the 8 corners + 4 FLOP scaling the flushed
+# colour entries by v.  Total 271 FLOP per sample (two exp per sample are
+# counted as special-function work, not FLOP).
+FLOP_PER_SAMPLE_APPLY = 271
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--e2e-steps", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-cams", type=int, default=1)
+    return ap.parse_args()
+
+
+def dist_setup(n_gpus):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(v, world):
+    if world == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = max(mx, float(f[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_baseline(scene, n_cams, pcg_per_gn):
+    """The FP64 oracle on a bounded sample: A p (Algorithm 1 twice per ray) on
+    the first n_cams cameras, scaled to all cameras -> PCG iterations/s."""
+    from oracle import Oracle
+    orc = Oracle(scene.G, scene.radii, scene.env_h, scene.env_w, scene.c2w[:n_cams],
+                 scene.focal[:n_cams], scene.width, scene.height,
+                 max_samples=scene.cfg.max_samples)
+    x = scene.x0.astype(np.float64)
+    p = np.random.default_rng(0).normal(size=scene.n_params)
+    t0 = time.perf_counter()
+    orc.apply_A(x, p)
+    dt = time.perf_counter() - t0
+    full = dt * scene.n_cams / n_cams
+    return {"value": 1.0 / full, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"one A p (J p then J^T v, FP64, OpenMP over rays) on {n_cams} of "
+                      f"{scene.n_cams} cameras ({orc.n_rays} rays, {dt:.1f} s), scaled by the "
+                      f"ray count; PCG vector work (O(n)) not included"}
+
+
+def run_reference(args, rank, world):
+    from scenegen import make_scene
+    if rank != 0:
+        return
+    sc = make_scene(args.workload)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        vals.append(cpu_baseline(sc, args.cpu_cams, sc.cfg.pcg_iters))
+    timed = vals[args.warmup:]
+    v = statistics.median([b["value"] for b in timed])
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": METRIC,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * sc.cfg.pcg_iters / v, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": _workload_desc(sc)},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": timed[0]["sample"]},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _workload_desc(sc):
+    c = sc.cfg
+    return (f"{c.name}: {c.G}^3 RGBA grid + {len(c.radii)} shells {c.env_h}x{c.env_w} "
+            f"(radii {','.join(str(r) for r in c.radii)}), {c.n_cams} cameras {c.width}x{c.height}, "
+            f"<= {c.max_samples} samples/ray, {c.pcg_iters} fixed Jacobi-PCG iterations per GN step")
+
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2112_05598_gb300 import Context
+    from paper_2112_05598_gb300._binding import launch_count
+    from scenegen import make_scene
+
+    sc = make_scene(args.workload)
+    cfg = sc.cfg
+    dev = torch.device("cuda", local)
+    ctx = Context.from_scene(sc, pcg_iters=cfg.pcg_iters, pcg_fixed=1)
+    stream = torch.cuda.current_stream()
+    x_gt = torch.from_numpy(sc.x_gt).to(dev)
+    target = torch.empty(3 * ctx.n_rays, device=dev)
+    ctx.render(x_gt, target)
+    del x_gt
+    samples = ctx.sample_count()
+    x = torch.from_numpy(sc.x0.copy()).to(dev)
+
+    for _ in range(args.warmup):
+        ctx.gn_solve(x, target, 1)
+    torch.cuda.synchronize()
+    ctx.enable_timing(True)
+    ctx.timing(reset=True)
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.extend(ctx.gn_solve(x, target, 1))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    launches = launch_count() - l0
+    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(ms, world)
+    pcg_total = sum_over_ranks(float(sum(s["pcg_iters"] for s in stats)), world)
+    value = pcg_total / (ms / 1000.0)
+    tm = ctx.timing(reset=True)
+    ctx.enable_timing(False)
+
+    # end to end through the public API with host buffers
+    e2e_steps = args.e2e_steps or args.steps
+    x_host = torch.from_numpy(sc.x0.copy()).pin_memory()
+    t_host = target.cpu().pin_memory()
+    x_dev = torch.empty_like(x)
+    t_dev = torch.empty_like(target)
+    barrier(world)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    e2e_pcg = 0
+    for _ in range(e2e_steps):
+        x_dev.copy_(x_host, non_blocking=True)
+        t_dev.copy_(t_host, non_blocking=True)
+        st = ctx.gn_solve(x_dev, t_dev, 1)
+        x_host.copy_(x_dev, non_blocking=True)
+        e2e_pcg += sum(s["pcg_iters"] for s in st)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = sum_over_ranks(float(e2e_pcg), world) / (ms_e2e / 1000.0)
+
+    peaks, peak_src = measured_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    apply_ms = tm["apply"]["ms"] / max(tm["apply"]["launches"], 1)
+    achieved = FLOP_PER_SAMPLE_APPLY * samples / (apply_ms / 1000.0) / 1e12
+    per_step = {k: v["ms"] / args.steps for k, v in tm.items()}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded voxelised primitives, targets rendered from ground truth)",
+        "config": {"workload": _workload_desc(sc), "n_params": sc.n_params, "n_rays": sc.n_rays,
+                   "samples_per_march": samples,
+                   "l2": "inputs larger than L2: targets and residuals 768 MB each per step"},
+        "gpu_launches": int(launches),
+        "rays_per_s": 2.0 * sc.n_rays * pcg_total / (ms / 1000.0),
+        "gn_steps": [{k: s[k] for k in ("F_before", "F_after", "gamma", "ls_evals", "pcg_iters")}
+                     for s in stats],
+        "kernel_ms_per_step": per_step,
+        "apply_ms_per_launch": apply_ms,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": None,
+                     "kernel": "k_scatter<float,float,1> (A p)",
+                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
+                                    f"(max SM clock, {peak_src})"},
+        "e2e": {"value": e2e_value, "unit": METRIC,
+                "h2d_bytes_per_step": int(4 * (sc.n_params + 3 * sc.n_rays)),
+                "d2h_bytes_per_step": int(4 * sc.n_params)},
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(sc, args.cpu_cams, cfg.pcg_iters)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_setup(args.gpus)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

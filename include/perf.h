@@ -1,0 +1,213 @@
+/*
+ * perf.h -- C ABI of libperf: the matrix-free Gauss-Newton step of PERF
+ * (Performant, Explicit Radiance Fields; Rasmuson, Sintorn, Assarsson) on one
+ * GB300 GPU.
+ *
+ * Problem (Section "Method"): the unknowns x are an RGBA voxel grid of G^3
+ * cells on [-1, 1]^3 followed by S equirectangular RGBA environment-map
+ * shells; every training pixel is one ray with three residuals
+ * r = H^ - C (Eq. 5-6); J is the m x n Jacobian of r, A = J^T J and
+ * b = -J^T r (Section "Update step"); the Gauss-Newton step solves A Delta = b
+ * by Jacobi-preconditioned CG (Algorithm 2) and scales it by the
+ * backtracking line search of Algorithm 3 (Eq. 7).
+ *
+ * Layouts (all little-endian, C order):
+ *   x       n = 4 (G^3 + S H_e W_e) values: grid [z][y][x][4], then shell 0,
+ *           1, ... each [row][col][4]; channels (r, g, b, sigma).  Row 0 of a
+ *           shell is its +z pole; columns run in azimuth from -pi.  sigma is
+ *           an opacity per voxel side.  Storage is float32, or bfloat16 when
+ *           the scene's dtype is PERF_BF16 (per-call entry points only).
+ *   rays    N_r = n_cams * height * width, ray = (cam * height + row) * width
+ *           + col; a residual / image / J p vector has 3 N_r floats indexed
+ *           ray * 3 + channel.
+ * Pointers are DEVICE pointers unless a comment says HOST.  The caller owns
+ * every buffer it passes in; the context owns only its workspace (PCG
+ * vectors, residual buffer, FP64 scalars) and frees it in perf_destroy.
+ * Every call is asynchronous on the given stream (a cudaStream_t; NULL = the
+ * legacy default stream) unless it writes a HOST output, in which case it
+ * synchronises that stream before returning.
+ *
+ * Errors: every call returns a perf_status; nothing throws.  Arguments are
+ * validated before any launch (PERF_ERR_INVALID_ARG); CUDA failures return
+ * PERF_ERR_CUDA; perf_last_error() gives a message for the context's last
+ * failure.  A context is not thread-safe: one host thread at a time.
+ */
+#ifndef PERF_H
+#define PERF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PERF_OK = 0,
+    PERF_ERR_INVALID_ARG = 1,
+    PERF_ERR_CUDA = 2,
+    PERF_ERR_NONFINITE = 3,   /* a PCG scalar or the objective is NaN / Inf */
+    PERF_ERR_TIMEOUT = 4,     /* a bounded device-side wait gave up */
+    PERF_ERR_NOT_SPD = 5,     /* p^T A p <= 0 in PCG */
+    PERF_ERR_UNSUPPORTED = 6
+} perf_status;
+
+enum { PERF_F32 = 0, PERF_BF16 = 1 };
+enum { PERF_PRECOND_JACOBI = 0, PERF_PRECOND_BLOCK4 = 1 };
+enum { PERF_EXIT_FIXED = 0, PERF_EXIT_EPS = 1, PERF_EXIT_STALL = 2,
+       PERF_EXIT_BREAKDOWN = 3, PERF_EXIT_NONFINITE = 4 };
+
+#define PERF_MAX_SHELLS 8
+
+typedef struct perf_ctx perf_ctx;
+
+/* Scene geometry (Section "Method"; Fig. "scene"). */
+typedef struct {
+    int32_t grid_res;                      /* G >= 2 */
+    int32_t n_shells;                      /* S in [0, 8] */
+    float shell_radii[PERF_MAX_SHELLS];    /* increasing, each > sqrt(3) */
+    int32_t env_h, env_w;                  /* texels per shell, >= 2 if S > 0 */
+    int32_t dtype;                         /* PERF_F32 or PERF_BF16 */
+} perf_scene;
+
+/* Pinhole cameras: pixel (col, row) has its centre at (col+1/2, row+1/2);
+ * camera-space ray ((col+1/2 - W/2)/f, -(row+1/2 - H/2)/f, -1). */
+typedef struct {
+    int32_t n_cams, width, height;
+    const float* c2w;     /* HOST, n_cams x 3 x 4 row-major camera-to-world; copied */
+    const float* focal;   /* HOST, n_cams focal lengths in pixels; copied */
+} perf_cameras;
+
+typedef struct {
+    int32_t max_samples;  /* cap on grid samples per ray (Section "Rendering") */
+    int32_t jitter;       /* 1: jitter pixel and sample positions (Section "Jittering") */
+    uint64_t seed;        /* jitter seed (SplitMix64 counter stream) */
+    uint32_t epoch;       /* jitter epoch; perf_gn_solve uses epoch + step index */
+    int32_t pcg_iters;    /* PCG iteration limit per GN step */
+    int32_t pcg_fixed;    /* 1: run exactly pcg_iters iterations (no exit test) */
+    double pcg_eps_rel;   /* paper mode: exit when R < eps^2 R_0 (Algorithm 2 EPS) */
+    double pcg_stall;     /* paper mode: exit when R / R_prev > stall (0.85) */
+    double ls_alpha;      /* Algorithm 3 decimation factor (0.7) */
+    int32_t ls_max;       /* at most ls_max decimations (the printed loop has no cap) */
+    int32_t project;      /* 1: trial points are projected to sigma >= 0, 0 <= c <= 1 */
+    int32_t precond;      /* PERF_PRECOND_JACOBI, or PERF_PRECOND_BLOCK4 with
+                             blocks supplied by perf_pcg_set_blocks */
+} perf_options;
+
+typedef struct {
+    int32_t iters;        /* PCG iterations taken */
+    int32_t exit_reason;  /* PERF_EXIT_* */
+    double R0;            /* r_0^T r_0 */
+    double R;             /* r_k^T r_k after the last iteration */
+    double rz;            /* r_k^T z_k */
+} perf_pcg_info;
+
+typedef struct {
+    double F_before;      /* F(x) at the start of the step (Eq. 5) */
+    double F_after;       /* F at the accepted point (F_before if rejected) */
+    double gamma;         /* step length from Algorithm 3 */
+    int32_t accepted;     /* 1 if F fell and x was updated */
+    int32_t ls_evals;     /* Error(gamma) evaluations */
+    perf_pcg_info pcg;
+    float ms;             /* device time of the step */
+} perf_gn_stats;
+
+/* Device time per kernel family, from CUDA events recorded on the launching
+ * stream around each launch while timing is enabled. */
+enum { PERF_T_APPLY = 0,    /* A p: the fused J p / J^T (J p) ray march */
+       PERF_T_FORWARD = 1,  /* residual and line-search objective marches */
+       PERF_T_DIAG = 2,     /* diag(J^T J) with J^T r */
+       PERF_T_VECTOR = 3,   /* PCG vector kernels (update, exit test, direction) */
+       PERF_T_COUNT = 4 };
+typedef struct {
+    double ms[PERF_T_COUNT];
+    int64_t launches[PERF_T_COUNT];
+} perf_timing;
+
+/* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
+ * eps 1e-3, stall 0.85, ls_alpha 0.7, ls_max 20, projection on, Jacobi. */
+perf_status perf_default_options(perf_options* out);
+
+/* Creates a context for one scene and camera set.  Validates everything
+ * (G >= 2, 0 <= S <= 8, radii increasing and > sqrt(3), env size >= 2,
+ * cameras >= 0, max_samples >= 1), copies the cameras to the device and
+ * allocates the workspace.  On failure *out is NULL. */
+perf_status perf_create(perf_ctx** out, const perf_scene* scene,
+                        const perf_cameras* cams, const perf_options* opts);
+perf_status perf_destroy(perf_ctx* ctx);
+perf_status perf_set_options(perf_ctx* ctx, const perf_options* opts);
+int64_t perf_param_count(const perf_ctx* ctx);   /* n, or -1 */
+int64_t perf_ray_count(const perf_ctx* ctx);     /* N_r, or -1 */
+const char* perf_last_error(const perf_ctx* ctx);
+
+/* Eq. 3-4: rgb_out[3 N_r] = H^ per ray (grid march, then the shells in order
+ * from the grid exit outwards, Section "Rendering"); T_out[N_r] (may be NULL)
+ * = transmittance at the grid exit. */
+perf_status perf_render(perf_ctx* ctx, const void* x, float* rgb_out,
+                        float* T_out, void* stream);
+
+/* Eq. 5-6: r_out[3 N_r] = H^ - C (may be NULL), *F_out (device double,
+ * overwritten) = 1/2 sum r^2 accumulated in FP64. */
+perf_status perf_residual(perf_ctx* ctx, const void* x, const float* target,
+                          float* r_out, double* F_out, void* stream);
+
+/* jp_out[3 N_r] = J p: the directional derivative of every ray along p, the
+ * per-sample partials of Algorithm 1 chained through the interpolation. */
+perf_status perf_jvp(perf_ctx* ctx, const void* x, const float* p,
+                     float* jp_out, void* stream);
+
+/* out[n] (+)= J^T v for v[3 N_r] (Section "Update step", the scatter of
+ * grad r_i (grad r_i^T p)); accumulate = 0 overwrites out. */
+perf_status perf_vjp(perf_ctx* ctx, const void* x, const float* v, float* out,
+                     int32_t accumulate, void* stream);
+
+/* Section "Preconditioner": diag_out[n] = diag(J^T J) (each row's entry for a
+ * parameter is summed over all samples of that ray before squaring);
+ * grad_out[n] = J^T r when r[3 N_r] and grad_out are given (both or neither). */
+perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const float* r,
+                          float* diag_out, float* grad_out, void* stream);
+
+/* A p = J^T (J p) = sum_i grad r_i (grad r_i^T p) without forming J
+ * (Section "Update step"); ap_out[n] is overwritten; *pap_out (device double,
+ * may be NULL) = p^T A p = |J p|^2 in FP64. */
+perf_status perf_apply_normal(perf_ctx* ctx, const void* x, const float* p,
+                              float* ap_out, double* pap_out, void* stream);
+
+/* Algorithm 2 on the context's workspace.  perf_pcg_begin starts from
+ * Delta_0 = 0 with b = -grad (grad[n] = J^T r) and M = diag(diag[n]);
+ * perf_pcg_step runs one iteration at x (A p, the fused vector updates with
+ * FP64 inner products, the exit test on the device); *done_out (HOST, may be
+ * NULL; synchronises) = 1 once PCG has exited.  perf_pcg_result copies
+ * Delta to delta_out[n] (may be NULL) and fills *info (HOST, may be NULL;
+ * synchronises). */
+perf_status perf_pcg_begin(perf_ctx* ctx, const float* grad, const float* diag,
+                           void* stream);
+perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out,
+                          void* stream);
+perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out,
+                            perf_pcg_info* info, void* stream);
+
+/* n_steps Gauss-Newton steps (Eq. 7) on x_inout[n] (float32 master copy, in
+ * place; the scene dtype decides the storage the ray marches read): residual
+ * and F, gradient and Jacobi diagonal, PCG, Algorithm 3 line search on
+ * F(P(x + gamma Delta)), accept only if F falls.  stats (HOST, may be NULL)
+ * receives n_steps records.  Synchronises (the line search reads one FP64
+ * scalar per trial step). */
+perf_status perf_gn_solve(perf_ctx* ctx, float* x_inout, const float* target,
+                          int32_t n_steps, perf_gn_stats* stats, void* stream);
+
+/* Kernel timing (instrumentation, off by default).  perf_get_timing
+ * synchronises the context's pending events and copies the totals to *out
+ * (HOST); reset = 1 clears them afterwards. */
+perf_status perf_enable_timing(perf_ctx* ctx, int32_t on);
+/* Number of kernels this library has launched in the process so far. */
+uint64_t perf_launch_count(void);
+/* *out (HOST; synchronises) = grid samples + shell hits of one march over all
+ * rays of the context (the units of work of every ray-march kernel). */
+perf_status perf_sample_count(perf_ctx* ctx, uint64_t* out, void* stream);
+perf_status perf_get_timing(perf_ctx* ctx, perf_timing* out, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PERF_H */

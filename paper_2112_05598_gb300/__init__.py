@@ -1,0 +1,11 @@
+"""GB300-native matrix-free Gauss-Newton step of PERF (Performant, Explicit
+Radiance Fields): a C-ABI CUDA library (``libperf.so``, include/perf.h) and a
+thin ctypes binding.  Importing the package loads the library; it raises if
+the library has not been built (``python -m paper_2112_05598_gb300.build``)."""
+from ._binding import (Context, Options, PerfError, default_options, load_library,
+                       PERF_F32, PERF_BF16, PERF_PRECOND_JACOBI, PERF_PRECOND_BLOCK4)
+
+__all__ = ["Context", "Options", "PerfError", "default_options", "load_library",
+           "PERF_F32", "PERF_BF16", "PERF_PRECOND_JACOBI", "PERF_PRECOND_BLOCK4"]
+
+load_library()

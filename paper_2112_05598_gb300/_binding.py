@@ -1,0 +1,292 @@
+"""ctypes binding of libperf (include/perf.h): argument marshalling only.
+
+Every step of the Gauss-Newton path runs in the CUDA library; this module
+turns torch tensors into device pointers and the current torch stream into a
+cudaStream_t.  It raises if the library is missing -- there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libperf.so")
+
+PERF_F32, PERF_BF16 = 0, 1
+PERF_PRECOND_JACOBI, PERF_PRECOND_BLOCK4 = 0, 1
+STATUS = {0: "PERF_OK", 1: "PERF_ERR_INVALID_ARG", 2: "PERF_ERR_CUDA",
+          3: "PERF_ERR_NONFINITE", 4: "PERF_ERR_TIMEOUT", 5: "PERF_ERR_NOT_SPD",
+          6: "PERF_ERR_UNSUPPORTED"}
+EXIT = {0: "fixed", 1: "eps", 2: "stall", 3: "breakdown", 4: "nonfinite"}
+
+
+class PerfError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Scene(ctypes.Structure):
+    _fields_ = [("grid_res", ctypes.c_int32), ("n_shells", ctypes.c_int32),
+                ("shell_radii", ctypes.c_float * 8),
+                ("env_h", ctypes.c_int32), ("env_w", ctypes.c_int32),
+                ("dtype", ctypes.c_int32)]
+
+
+class Cameras(ctypes.Structure):
+    _fields_ = [("n_cams", ctypes.c_int32), ("width", ctypes.c_int32),
+                ("height", ctypes.c_int32), ("c2w", ctypes.c_void_p),
+                ("focal", ctypes.c_void_p)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("max_samples", ctypes.c_int32), ("jitter", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32),
+                ("pcg_iters", ctypes.c_int32), ("pcg_fixed", ctypes.c_int32),
+                ("pcg_eps_rel", ctypes.c_double), ("pcg_stall", ctypes.c_double),
+                ("ls_alpha", ctypes.c_double), ("ls_max", ctypes.c_int32),
+                ("project", ctypes.c_int32), ("precond", ctypes.c_int32)]
+
+
+class PcgInfo(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int32), ("exit_reason", ctypes.c_int32),
+                ("R0", ctypes.c_double), ("R", ctypes.c_double), ("rz", ctypes.c_double)]
+
+
+class Timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4)]
+
+
+TIMING_KINDS = ("apply", "forward", "diag", "vector")
+
+
+class GNStats(ctypes.Structure):
+    _fields_ = [("F_before", ctypes.c_double), ("F_after", ctypes.c_double),
+                ("gamma", ctypes.c_double), ("accepted", ctypes.c_int32),
+                ("ls_evals", ctypes.c_int32), ("pcg", PcgInfo), ("ms", ctypes.c_float)]
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "perf_default_options": [ctypes.POINTER(Options)],
+    "perf_create": [ctypes.POINTER(_VP), ctypes.POINTER(Scene), ctypes.POINTER(Cameras),
+                    ctypes.POINTER(Options)],
+    "perf_destroy": [_VP],
+    "perf_set_options": [_VP, ctypes.POINTER(Options)],
+    "perf_render": [_VP, _VP, _VP, _VP, _VP],
+    "perf_residual": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "perf_jvp": [_VP, _VP, _VP, _VP, _VP],
+    "perf_vjp": [_VP, _VP, _VP, _VP, ctypes.c_int32, _VP],
+    "perf_diag_jtj": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "perf_apply_normal": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "perf_pcg_begin": [_VP, _VP, _VP, _VP],
+    "perf_pcg_step": [_VP, _VP, ctypes.POINTER(ctypes.c_int32), _VP],
+    "perf_pcg_result": [_VP, _VP, ctypes.POINTER(PcgInfo), _VP],
+    "perf_gn_solve": [_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(GNStats), _VP],
+    "perf_enable_timing": [_VP, ctypes.c_int32],
+    "perf_get_timing": [_VP, ctypes.POINTER(Timing), ctypes.c_int32],
+    "perf_sample_count": [_VP, ctypes.POINTER(ctypes.c_uint64), _VP],
+}
+_OPTIONAL_SIGS = {
+    "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
+}
+
+_lib = None
+
+
+def load_library(path: Optional[str] = None):
+    """Load libperf.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise ImportError(f"libperf.so not built at {p}: run paper_2112_05598_gb300/build.py")
+    lib = ctypes.CDLL(p)
+    for name, args in _SIGS.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    for name, args in _OPTIONAL_SIGS.items():
+        if hasattr(lib, name):
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_int
+    lib.perf_param_count.argtypes = [_VP]
+    lib.perf_param_count.restype = ctypes.c_int64
+    lib.perf_ray_count.argtypes = [_VP]
+    lib.perf_ray_count.restype = ctypes.c_int64
+    lib.perf_launch_count.argtypes = []
+    lib.perf_launch_count.restype = ctypes.c_uint64
+    lib.perf_last_error.argtypes = [_VP]
+    lib.perf_last_error.restype = ctypes.c_char_p
+    if path is None:
+        _lib = lib
+    return lib
+
+
+def launch_count() -> int:
+    """Kernels launched by libperf in this process so far."""
+    return int(load_library().perf_launch_count())
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load_library().perf_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """One scene + camera set (``perf_create``).  Methods take torch CUDA
+    tensors and run on the current torch stream unless one is given."""
+
+    def __init__(self, G, radii, env_h, env_w, c2w, focal, width, height,
+                 dtype=PERF_F32, options: Optional[Options] = None, **opt_kw):
+        self.lib = load_library()
+        sc = Scene()
+        sc.grid_res = int(G)
+        radii = [float(r) for r in radii]
+        sc.n_shells = len(radii)
+        for i, r in enumerate(radii):
+            sc.shell_radii[i] = r
+        sc.env_h, sc.env_w = int(env_h), int(env_w)
+        sc.dtype = int(dtype)
+        self._c2w = np.ascontiguousarray(c2w, dtype=np.float32).reshape(-1, 12)
+        self._focal = np.ascontiguousarray(focal, dtype=np.float32).reshape(-1)
+        cams = Cameras()
+        cams.n_cams = int(self._c2w.shape[0])
+        cams.width, cams.height = int(width), int(height)
+        cams.c2w = self._c2w.ctypes.data_as(ctypes.c_void_p)
+        cams.focal = self._focal.ctypes.data_as(ctypes.c_void_p)
+        self.options = options if options is not None else default_options()
+        for k, v in opt_kw.items():
+            setattr(self.options, k, v)
+        h = ctypes.c_void_p()
+        st = self.lib.perf_create(ctypes.byref(h), ctypes.byref(sc), ctypes.byref(cams),
+                                  ctypes.byref(self.options))
+        if st != 0:
+            raise PerfError(st, "perf_create rejected the scene, cameras or options")
+        self.h = h
+        self.dtype = dtype
+        self.G, self.n_shells, self.env_h, self.env_w = int(G), len(radii), int(env_h), int(env_w)
+        self.width, self.height, self.n_cams = int(width), int(height), cams.n_cams
+        self.n_params = int(self.lib.perf_param_count(h))
+        self.n_rays = int(self.lib.perf_ray_count(h))
+
+    @classmethod
+    def from_scene(cls, scene, dtype=PERF_F32, c2w=None, focal=None, **opt_kw):
+        opt_kw.setdefault("max_samples", scene.cfg.max_samples)
+        return cls(scene.G, scene.radii, scene.env_h, scene.env_w,
+                   scene.c2w if c2w is None else c2w,
+                   scene.focal if focal is None else focal,
+                   scene.width, scene.height, dtype=dtype, **opt_kw)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.perf_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.perf_last_error(self.h)
+            raise PerfError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            setattr(self.options, k, v)
+        self._check(self.lib.perf_set_options(self.h, ctypes.byref(self.options)), "set_options")
+
+    # --- per-call entry points (device tensors)
+    def render(self, x, rgb_out, T_out=None, stream=None):
+        self._check(self.lib.perf_render(self.h, _ptr(x), _ptr(rgb_out), _ptr(T_out),
+                                         _stream(stream)), "render")
+
+    def residual(self, x, target, r_out, F_out, stream=None):
+        self._check(self.lib.perf_residual(self.h, _ptr(x), _ptr(target), _ptr(r_out),
+                                           _ptr(F_out), _stream(stream)), "residual")
+
+    def jvp(self, x, p, out, stream=None):
+        self._check(self.lib.perf_jvp(self.h, _ptr(x), _ptr(p), _ptr(out), _stream(stream)), "jvp")
+
+    def vjp(self, x, v, out, accumulate=False, stream=None):
+        self._check(self.lib.perf_vjp(self.h, _ptr(x), _ptr(v), _ptr(out), int(accumulate),
+                                      _stream(stream)), "vjp")
+
+    def diag_jtj(self, x, diag_out, r=None, grad_out=None, stream=None):
+        self._check(self.lib.perf_diag_jtj(self.h, _ptr(x), _ptr(r), _ptr(diag_out),
+                                           _ptr(grad_out), _stream(stream)), "diag_jtj")
+
+    def apply_normal(self, x, p, ap_out, pap_out=None, stream=None):
+        self._check(self.lib.perf_apply_normal(self.h, _ptr(x), _ptr(p), _ptr(ap_out),
+                                               _ptr(pap_out), _stream(stream)), "apply_normal")
+
+    def pcg_begin(self, grad, diag, stream=None):
+        self._check(self.lib.perf_pcg_begin(self.h, _ptr(grad), _ptr(diag), _stream(stream)),
+                    "pcg_begin")
+
+    def pcg_step(self, x, want_done=False, stream=None):
+        done = ctypes.c_int32(0)
+        self._check(self.lib.perf_pcg_step(self.h, _ptr(x), ctypes.byref(done) if want_done else None,
+                                           _stream(stream)), "pcg_step")
+        return bool(done.value) if want_done else None
+
+    def pcg_result(self, delta_out=None, stream=None):
+        info = PcgInfo()
+        self._check(self.lib.perf_pcg_result(self.h, _ptr(delta_out), ctypes.byref(info),
+                                             _stream(stream)), "pcg_result")
+        return dict(iters=info.iters, exit=EXIT.get(info.exit_reason, info.exit_reason),
+                    R0=info.R0, R=info.R, rz=info.rz)
+
+    def set_blocks(self, blocks, n_block):
+        self._check(self.lib.perf_pcg_set_blocks(self.h, _ptr(blocks), int(n_block)), "set_blocks")
+
+    def sample_count(self, stream=None):
+        n = ctypes.c_uint64(0)
+        self._check(self.lib.perf_sample_count(self.h, ctypes.byref(n), _stream(stream)), "sample_count")
+        return int(n.value)
+
+    def enable_timing(self, on=True):
+        self._check(self.lib.perf_enable_timing(self.h, int(bool(on))), "enable_timing")
+
+    def timing(self, reset=False):
+        t = Timing()
+        self._check(self.lib.perf_get_timing(self.h, ctypes.byref(t), int(bool(reset))), "timing")
+        return {k: dict(ms=t.ms[i], launches=int(t.launches[i])) for i, k in enumerate(TIMING_KINDS)}
+
+    def gn_solve(self, x, target, n_steps, stream=None):
+        stats = (GNStats * max(int(n_steps), 1))()
+        self._check(self.lib.perf_gn_solve(self.h, _ptr(x), _ptr(target), int(n_steps), stats,
+                                           _stream(stream)), "gn_solve")
+        out = []
+        for i in range(int(n_steps)):
+            s = stats[i]
+            out.append(dict(F_before=s.F_before, F_after=s.F_after, gamma=s.gamma,
+                            accepted=bool(s.accepted), ls_evals=s.ls_evals,
+                            pcg_iters=s.pcg.iters, pcg_exit=EXIT.get(s.pcg.exit_reason),
+                            R0=s.pcg.R0, R=s.pcg.R, ms=s.ms))
+        return out

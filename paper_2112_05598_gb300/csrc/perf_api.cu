@@ -1,0 +1,584 @@
+// perf_api.cu -- the C ABI of libperf (declared in include/perf.h).
+//
+// Host orchestration of the Gauss-Newton step (PERF Eq. 7): residual and F,
+// gradient with the Jacobi diagonal, Algorithm 2 on the context's workspace,
+// and Algorithm 3 evaluating F(P(x + gamma Delta)) on the device with one
+// FP64 scalar read back per trial step length.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <utility>
+#include <vector>
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include "../../include/perf.h"
+#include "perf_kernels.h"
+
+using perf::DevScene;
+using perf::PcgScalars;
+
+struct perf_ctx {
+    perf_scene scene;
+    perf_options opts;
+    DevScene ds;
+    long long n = 0, n_rays = 0;
+    int device = 0;
+    float* cams = nullptr;
+    // workspace (allocated on first use)
+    float* r = nullptr;
+    float* diag = nullptr;
+    float* grad = nullptr;
+    float* delta = nullptr;
+    float* rho = nullptr;
+    float* p = nullptr;
+    float* Ap = nullptr;
+    float* x_trial = nullptr;
+    __nv_bfloat16* x16 = nullptr;
+    __nv_bfloat16* p16 = nullptr;
+    __nv_bfloat16* t16 = nullptr;
+    PcgScalars* s = nullptr;
+    double* dF = nullptr;
+    const float* blocks = nullptr;   // caller-owned 4x4 blocks per voxel (or null)
+    long long n_block = 0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    std::string err;
+    // kernel timing
+    bool timing = false;
+    struct KTimer {
+        std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev;
+        size_t used = 0;
+        double ms = 0.0;
+        long long launches = 0;
+    } kt[PERF_T_COUNT];
+};
+
+namespace {
+
+perf_status fail(perf_ctx* c, perf_status st, const std::string& msg) {
+    if (c) c->err = msg;
+    return st;
+}
+
+perf_status cuda_fail(perf_ctx* c, cudaError_t e, const char* where) {
+    std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(c, PERF_ERR_CUDA, m);
+}
+
+#define CK(call)                                                     \
+    do {                                                             \
+        cudaError_t e_ = (call);                                     \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call);     \
+    } while (0)
+
+inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+perf_status check_options(const perf_options* o, std::string& why) {
+    if (!o) { why = "options is NULL"; return PERF_ERR_INVALID_ARG; }
+    if (o->max_samples < 1 || o->max_samples > (1 << 20)) { why = "max_samples out of range"; return PERF_ERR_INVALID_ARG; }
+    if (o->pcg_iters < 0) { why = "pcg_iters < 0"; return PERF_ERR_INVALID_ARG; }
+    if (!(o->ls_alpha > 0.0 && o->ls_alpha < 1.0)) { why = "ls_alpha must be in (0,1)"; return PERF_ERR_INVALID_ARG; }
+    if (o->ls_max < 0 || o->ls_max > 200) { why = "ls_max out of range"; return PERF_ERR_INVALID_ARG; }
+    if (o->precond != PERF_PRECOND_JACOBI && o->precond != PERF_PRECOND_BLOCK4) { why = "unknown preconditioner"; return PERF_ERR_INVALID_ARG; }
+    if (!(o->pcg_eps_rel >= 0.0) || !(o->pcg_stall > 0.0)) { why = "pcg_eps_rel / pcg_stall invalid"; return PERF_ERR_INVALID_ARG; }
+    return PERF_OK;
+}
+
+template <typename T>
+cudaError_t alloc(T** p, long long count) {
+    if (*p) return cudaSuccess;
+    return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+perf_status ensure_pcg(perf_ctx* ctx) {
+    CK(alloc(&ctx->diag, ctx->n));
+    CK(alloc(&ctx->grad, ctx->n));
+    CK(alloc(&ctx->delta, ctx->n));
+    CK(alloc(&ctx->rho, ctx->n));
+    CK(alloc(&ctx->p, ctx->n));
+    CK(alloc(&ctx->Ap, ctx->n));
+    if (ctx->scene.dtype == PERF_BF16) CK(alloc(&ctx->p16, ctx->n));
+    return PERF_OK;
+}
+
+bool bad_ptr(const void* p) { return p == nullptr; }
+
+void t_begin(perf_ctx* c, int k, cudaStream_t st) {
+    if (!c->timing) return;
+    auto& t = c->kt[k];
+    if (t.used == t.ev.size()) {
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        t.ev.emplace_back(a, b);
+    }
+    cudaEventRecord(t.ev[t.used].first, st);
+}
+
+void t_end(perf_ctx* c, int k, cudaStream_t st) {
+    if (!c->timing) return;
+    auto& t = c->kt[k];
+    cudaEventRecord(t.ev[t.used].second, st);
+    ++t.used;
+}
+
+void t_harvest(perf_ctx* c) {
+    for (auto& t : c->kt) {
+        for (size_t i = 0; i < t.used; ++i) {
+            cudaEventSynchronize(t.ev[i].second);
+            float ms = 0.f;
+            if (cudaEventElapsedTime(&ms, t.ev[i].first, t.ev[i].second) == cudaSuccess) t.ms += ms;
+        }
+        t.launches += (long long)t.used;
+        t.used = 0;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+perf_status perf_default_options(perf_options* o) {
+    if (!o) return PERF_ERR_INVALID_ARG;
+    std::memset(o, 0, sizeof(*o));
+    o->max_samples = 512;
+    o->jitter = 0;
+    o->seed = 0;
+    o->epoch = 0;
+    o->pcg_iters = 20;
+    o->pcg_fixed = 1;
+    o->pcg_eps_rel = 1e-3;
+    o->pcg_stall = 0.85;
+    o->ls_alpha = 0.7;
+    o->ls_max = 20;
+    o->project = 1;
+    o->precond = PERF_PRECOND_JACOBI;
+    return PERF_OK;
+}
+
+perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras* cams,
+                        const perf_options* opts) {
+    if (!out) return PERF_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!sc || !cams || !opts) return PERF_ERR_INVALID_ARG;
+    std::string why;
+    if (check_options(opts, why) != PERF_OK) return PERF_ERR_INVALID_ARG;
+    if (sc->grid_res < 2 || sc->grid_res > 2048) return PERF_ERR_INVALID_ARG;
+    if (sc->n_shells < 0 || sc->n_shells > PERF_MAX_SHELLS) return PERF_ERR_INVALID_ARG;
+    if (sc->dtype != PERF_F32 && sc->dtype != PERF_BF16) return PERF_ERR_INVALID_ARG;
+    if (sc->n_shells > 0 && (sc->env_h < 2 || sc->env_w < 2)) return PERF_ERR_INVALID_ARG;
+    for (int s = 0; s < sc->n_shells; ++s) {
+        if (!(sc->shell_radii[s] > 1.7320508f)) return PERF_ERR_INVALID_ARG;
+        if (s > 0 && !(sc->shell_radii[s] > sc->shell_radii[s - 1])) return PERF_ERR_INVALID_ARG;
+    }
+    if (cams->n_cams < 0 || cams->width < 0 || cams->height < 0) return PERF_ERR_INVALID_ARG;
+    if (cams->n_cams > 0 && (cams->width > 0 && cams->height > 0) && (!cams->c2w || !cams->focal))
+        return PERF_ERR_INVALID_ARG;
+    for (int c = 0; c < cams->n_cams && cams->focal; ++c)
+        if (!(cams->focal[c] > 0.0f) || !std::isfinite(cams->focal[c])) return PERF_ERR_INVALID_ARG;
+
+    perf_ctx* ctx = new (std::nothrow) perf_ctx();
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    ctx->scene = *sc;
+    ctx->opts = *opts;
+    if (sc->n_shells == 0) { ctx->scene.env_h = 0; ctx->scene.env_w = 0; }
+    const long long G = sc->grid_res;
+    const long long texels = (long long)ctx->scene.env_h * ctx->scene.env_w;
+    ctx->n = 4 * (G * G * G + (long long)sc->n_shells * texels);
+    ctx->n_rays = (long long)cams->n_cams * cams->width * cams->height;
+    cudaGetDevice(&ctx->device);
+
+    DevScene& d = ctx->ds;
+    std::memset(&d, 0, sizeof(d));
+    d.G = (int)G;
+    d.halfG = 0.5f * (float)G;
+    d.h = 2.0f / (float)G;
+    d.S = sc->n_shells;
+    for (int s = 0; s < sc->n_shells; ++s) d.R[s] = sc->shell_radii[s];
+    d.He = ctx->scene.env_h;
+    d.We = ctx->scene.env_w;
+    d.n_vox = G * G * G;
+    d.shell_texels = texels;
+    d.W = cams->width;
+    d.H = cams->height;
+    d.n_cams = cams->n_cams;
+    d.n_rays = ctx->n_rays;
+    d.tiles_x = (cams->width + 7) / 8;
+    d.tiles_y = (cams->height + 3) / 4;
+    d.n_tiles = (long long)d.tiles_x * d.tiles_y * cams->n_cams;
+    if (ctx->n_rays == 0) d.n_tiles = 0;
+    d.max_samples = opts->max_samples;
+    d.jitter = opts->jitter;
+    d.seed = opts->seed;
+    d.epoch = opts->epoch;
+
+    if (cams->n_cams > 0) {
+        float* host = new (std::nothrow) float[16 * (size_t)cams->n_cams];
+        if (!host) { delete ctx; return PERF_ERR_INVALID_ARG; }
+        std::memset(host, 0, sizeof(float) * 16 * (size_t)cams->n_cams);
+        for (int c = 0; c < cams->n_cams; ++c) {
+            if (cams->c2w) std::memcpy(host + 16 * c, cams->c2w + 12 * c, 12 * sizeof(float));
+            host[16 * c + 12] = cams->focal ? cams->focal[c] : 1.0f;
+        }
+        cudaError_t e = cudaMalloc(&ctx->cams, sizeof(float) * 16 * (size_t)cams->n_cams);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(ctx->cams, host, sizeof(float) * 16 * (size_t)cams->n_cams,
+                           cudaMemcpyHostToDevice);
+        delete[] host;
+        if (e != cudaSuccess) { perf_destroy(ctx); return PERF_ERR_CUDA; }
+    }
+    d.cams = ctx->cams;
+    cudaError_t e = cudaMalloc(&ctx->s, sizeof(PcgScalars));
+    if (e == cudaSuccess) e = cudaMemset(ctx->s, 0, sizeof(PcgScalars));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->dF, sizeof(double) * 2);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev0);
+    if (e == cudaSuccess) e = cudaEventCreate(&ctx->ev1);
+    if (e != cudaSuccess) { perf_destroy(ctx); return PERF_ERR_CUDA; }
+    *out = ctx;
+    return PERF_OK;
+}
+
+perf_status perf_destroy(perf_ctx* ctx) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
+                    ctx->Ap, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    for (auto& t : ctx->kt)
+        for (auto& pr : t.ev) {
+            cudaEventDestroy(pr.first);
+            cudaEventDestroy(pr.second);
+        }
+    delete ctx;
+    return PERF_OK;
+}
+
+perf_status perf_set_options(perf_ctx* ctx, const perf_options* opts) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    std::string why;
+    if (check_options(opts, why) != PERF_OK) return fail(ctx, PERF_ERR_INVALID_ARG, why);
+    ctx->opts = *opts;
+    ctx->ds.max_samples = opts->max_samples;
+    ctx->ds.jitter = opts->jitter;
+    ctx->ds.seed = opts->seed;
+    ctx->ds.epoch = opts->epoch;
+    return PERF_OK;
+}
+
+int64_t perf_param_count(const perf_ctx* ctx) { return ctx ? (int64_t)ctx->n : -1; }
+int64_t perf_ray_count(const perf_ctx* ctx) { return ctx ? (int64_t)ctx->n_rays : -1; }
+const char* perf_last_error(const perf_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+perf_status perf_render(perf_ctx* ctx, const void* x, float* rgb_out, float* T_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x) || bad_ptr(rgb_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "render: NULL x or rgb_out");
+    CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, x, nullptr, rgb_out, T_out, nullptr, 0, S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_residual(perf_ctx* ctx, const void* x, const float* target, float* r_out,
+                          double* F_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(F_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "residual: NULL F_out");
+    CK(cudaMemsetAsync(F_out, 0, sizeof(double), S(stream)));
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x) || bad_ptr(target)) return fail(ctx, PERF_ERR_INVALID_ARG, "residual: NULL x or target");
+    CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, x, target, r_out, nullptr, F_out,
+                            r_out ? 1 : 2, S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_jvp(perf_ctx* ctx, const void* x, const float* p, float* jp_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x) || bad_ptr(p) || bad_ptr(jp_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "jvp: NULL pointer");
+    CK(perf::launch_jvp(ctx->ds, ctx->scene.dtype, x, p, PERF_F32, jp_out, S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_vjp(perf_ctx* ctx, const void* x, const float* v, float* out, int32_t accumulate,
+                     void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(out)) return fail(ctx, PERF_ERR_INVALID_ARG, "vjp: NULL out");
+    if (!accumulate) CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)ctx->n, S(stream)));
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x) || bad_ptr(v)) return fail(ctx, PERF_ERR_INVALID_ARG, "vjp: NULL x or v");
+    CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 0, x, nullptr, PERF_F32, v, out, nullptr,
+                            nullptr, S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const float* r, float* diag_out,
+                          float* grad_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(diag_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "diag_jtj: NULL diag_out");
+    if ((r == nullptr) != (grad_out == nullptr))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "diag_jtj: give both r and grad_out or neither");
+    CK(cudaMemsetAsync(diag_out, 0, sizeof(float) * (size_t)ctx->n, S(stream)));
+    if (grad_out) CK(cudaMemsetAsync(grad_out, 0, sizeof(float) * (size_t)ctx->n, S(stream)));
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "diag_jtj: NULL x");
+    CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, r, diag_out,
+                            grad_out, nullptr, S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_apply_normal(perf_ctx* ctx, const void* x, const float* p, float* ap_out,
+                              double* pap_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(ap_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "apply_normal: NULL ap_out");
+    CK(cudaMemsetAsync(ap_out, 0, sizeof(float) * (size_t)ctx->n, S(stream)));
+    if (pap_out) CK(cudaMemsetAsync(pap_out, 0, sizeof(double), S(stream)));
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x) || bad_ptr(p)) return fail(ctx, PERF_ERR_INVALID_ARG, "apply_normal: NULL x or p");
+    CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, p, PERF_F32, nullptr, ap_out, nullptr,
+                            pap_out, S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_pcg_begin(perf_ctx* ctx, const float* grad, const float* diag, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(grad) || bad_ptr(diag)) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_begin: NULL grad or diag");
+    perf_status st = ensure_pcg(ctx);
+    if (st != PERF_OK) return st;
+    // the iterations precondition with the context's copy of the diagonal
+    if (diag != ctx->diag)
+        CK(cudaMemcpyAsync(ctx->diag, diag, sizeof(float) * (size_t)ctx->n,
+                           cudaMemcpyDeviceToDevice, S(stream)));
+    const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
+    CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p, ctx->p16,
+                              ctx->Ap, ctx->s, ctx->opts.pcg_iters, ctx->opts.pcg_fixed,
+                              ctx->opts.pcg_eps_rel, ctx->opts.pcg_stall, B, ctx->n_block,
+                              S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void* stream);
+
+}  // extern "C"
+
+namespace {
+
+// One Algorithm 2 iteration on the context workspace with diagonal `diag`.
+perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, cudaStream_t st) {
+    const bool bf = ctx->scene.dtype == PERF_BF16;
+    const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
+    const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p);
+    t_begin(ctx, PERF_T_APPLY, st);
+    CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32, nullptr,
+                            ctx->Ap, nullptr, &ctx->s->pAp, st));
+    t_end(ctx, PERF_T_APPLY, st);
+    t_begin(ctx, PERF_T_VECTOR, st);
+    CK(perf::launch_pcg_update(ctx->n, ctx->delta, ctx->rho, ctx->p, ctx->Ap, diag, B, ctx->n_block,
+                               ctx->s, st));
+    CK(perf::launch_pcg_finish(ctx->s, st));
+    CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p16, ctx->Ap,
+                            ctx->s, st));
+    t_end(ctx, PERF_T_VECTOR, st);
+    return PERF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_step: NULL x");
+    if (!ctx->delta || !ctx->s) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_step before pcg_begin");
+    perf_status st = pcg_iter(ctx, x, ctx->diag, S(stream));
+    if (st != PERF_OK) return st;
+    if (done_out) {
+        int done = 0;
+        CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, S(stream)));
+        CK(cudaStreamSynchronize(S(stream)));
+        *done_out = done;
+    }
+    return PERF_OK;
+}
+
+perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out, perf_pcg_info* info, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (!ctx->delta || !ctx->s) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_result before pcg_begin");
+    if (delta_out)
+        CK(cudaMemcpyAsync(delta_out, ctx->delta, sizeof(float) * (size_t)ctx->n,
+                           cudaMemcpyDeviceToDevice, S(stream)));
+    if (info) {
+        PcgScalars h;
+        CK(cudaMemcpyAsync(&h, ctx->s, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
+        CK(cudaStreamSynchronize(S(stream)));
+        info->iters = h.iter;
+        info->exit_reason = h.exit_reason;
+        info->R0 = h.R0;
+        info->R = h.R;
+        info->rz = h.rz;
+    }
+    return PERF_OK;
+}
+
+perf_status perf_gn_solve(perf_ctx* ctx, float* x, const float* target, int32_t n_steps,
+                          perf_gn_stats* stats, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (n_steps < 0) return fail(ctx, PERF_ERR_INVALID_ARG, "gn_solve: n_steps < 0");
+    if (bad_ptr(x) || (ctx->n_rays > 0 && bad_ptr(target)))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "gn_solve: NULL x or target");
+    cudaStream_t st = S(stream);
+    const bool bf = ctx->scene.dtype == PERF_BF16;
+    perf_status ps = ensure_pcg(ctx);
+    if (ps != PERF_OK) return ps;
+    CK(alloc(&ctx->r, 3 * ctx->n_rays));
+    CK(alloc(&ctx->x_trial, ctx->n));
+    if (bf) {
+        CK(alloc(&ctx->x16, ctx->n));
+        CK(alloc(&ctx->t16, ctx->n));
+    }
+    const perf_options& o = ctx->opts;
+    const uint32_t epoch0 = o.epoch;
+    perf_status result = PERF_OK;
+    for (int step = 0; step < n_steps; ++step) {
+        ctx->ds.epoch = epoch0 + (uint32_t)step;
+        CK(cudaEventRecord(ctx->ev0, st));
+        const void* xm = x;
+        if (bf) {
+            CK(perf::launch_to_bf16(ctx->n, x, ctx->x16, st));
+            xm = ctx->x16;
+        }
+        // residuals and F(x)
+        CK(cudaMemsetAsync(ctx->dF, 0, sizeof(double), st));
+        t_begin(ctx, PERF_T_FORWARD, st);
+        if (ctx->n_rays > 0)
+            CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, xm, target, ctx->r, nullptr, ctx->dF, 1, st));
+        t_end(ctx, PERF_T_FORWARD, st);
+        // b = -J^T r and M = diag(J^T J)
+        CK(cudaMemsetAsync(ctx->diag, 0, sizeof(float) * (size_t)ctx->n, st));
+        CK(cudaMemsetAsync(ctx->grad, 0, sizeof(float) * (size_t)ctx->n, st));
+        t_begin(ctx, PERF_T_DIAG, st);
+        if (ctx->n_rays > 0)
+            CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, xm, nullptr, PERF_F32, ctx->r,
+                                    ctx->diag, ctx->grad, nullptr, st));
+        t_end(ctx, PERF_T_DIAG, st);
+        const float* B = o.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
+        CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
+                                  ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
+                                  o.pcg_eps_rel, o.pcg_stall, B, ctx->n_block, st));
+        for (int k = 0; k < o.pcg_iters; ++k) {
+            ps = pcg_iter(ctx, xm, ctx->diag, st);
+            if (ps != PERF_OK) return ps;
+            if (!o.pcg_fixed) {
+                int done = 0;
+                CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                if (done) break;
+            }
+        }
+        double F0 = 0.0;
+        CK(cudaMemcpyAsync(&F0, ctx->dF, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        // Algorithm 3 on F(P(x + gamma Delta))
+        double gamma = 1.0, mu_prev = 3.4028234663852886e38, g_star = 1.0, mu_star = mu_prev;
+        int evals = 0;
+        bool found = false;
+        for (int it = 0; it <= o.ls_max; ++it) {
+            CK(perf::launch_trial(ctx->n, x, ctx->delta, (float)gamma, o.project, ctx->x_trial,
+                                  bf ? ctx->t16 : nullptr, st));
+            CK(cudaMemsetAsync(ctx->dF, 0, sizeof(double), st));
+            t_begin(ctx, PERF_T_FORWARD, st);
+            if (ctx->n_rays > 0)
+                CK(perf::launch_forward(ctx->ds, ctx->scene.dtype,
+                                        bf ? static_cast<const void*>(ctx->t16)
+                                           : static_cast<const void*>(ctx->x_trial),
+                                        target, nullptr, nullptr, ctx->dF, 2, st));
+            t_end(ctx, PERF_T_FORWARD, st);
+            double mu = 0.0;
+            CK(cudaMemcpyAsync(&mu, ctx->dF, sizeof(double), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            ++evals;
+            if (std::isnan(mu)) mu = INFINITY;
+            if (mu > mu_prev) {
+                g_star = gamma / o.ls_alpha;
+                mu_star = mu_prev;
+                found = true;
+                break;
+            }
+            gamma *= o.ls_alpha;
+            mu_prev = mu;
+        }
+        if (!found) { g_star = gamma / o.ls_alpha; mu_star = mu_prev; }
+        const bool accept = std::isfinite(mu_star) && mu_star < F0;
+        if (accept) {
+            CK(perf::launch_trial(ctx->n, x, ctx->delta, (float)g_star, o.project, ctx->x_trial,
+                                  nullptr, st));
+            CK(cudaMemcpyAsync(x, ctx->x_trial, sizeof(float) * (size_t)ctx->n,
+                               cudaMemcpyDeviceToDevice, st));
+        }
+        CK(cudaEventRecord(ctx->ev1, st));
+        PcgScalars h;
+        CK(cudaMemcpyAsync(&h, ctx->s, sizeof(h), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        t_harvest(ctx);
+        if (!std::isfinite(F0)) result = PERF_ERR_NONFINITE;
+        if (stats) {
+            perf_gn_stats& g = stats[step];
+            g.F_before = F0;
+            g.F_after = accept ? mu_star : F0;
+            g.gamma = g_star;
+            g.accepted = accept ? 1 : 0;
+            g.ls_evals = evals;
+            g.pcg.iters = h.iter;
+            g.pcg.exit_reason = h.exit_reason;
+            g.pcg.R0 = h.R0;
+            g.pcg.R = h.R;
+            g.pcg.rz = h.rz;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
+            g.ms = ms;
+        }
+        if (result != PERF_OK) break;
+    }
+    ctx->ds.epoch = epoch0;
+    if (result == PERF_ERR_NONFINITE) return fail(ctx, result, "gn_solve: non-finite objective");
+    return result;
+}
+
+perf_status perf_enable_timing(perf_ctx* ctx, int32_t on) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    ctx->timing = on != 0;
+    return PERF_OK;
+}
+
+uint64_t perf_launch_count(void) { return (uint64_t)__atomic_load_n(&perf::g_launches, __ATOMIC_RELAXED); }
+
+perf_status perf_sample_count(perf_ctx* ctx, uint64_t* out, void* stream) {
+    if (!ctx || !out) return PERF_ERR_INVALID_ARG;
+    *out = 0;
+    if (ctx->n_rays == 0) return PERF_OK;
+    unsigned long long* d = reinterpret_cast<unsigned long long*>(ctx->dF + 1);
+    CK(perf::launch_count_samples(ctx->ds, d, S(stream)));
+    unsigned long long h = 0;
+    CK(cudaMemcpyAsync(&h, d, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
+    CK(cudaStreamSynchronize(S(stream)));
+    *out = (uint64_t)h;
+    return PERF_OK;
+}
+
+perf_status perf_get_timing(perf_ctx* ctx, perf_timing* out, int32_t reset) {
+    if (!ctx || !out) return PERF_ERR_INVALID_ARG;
+    t_harvest(ctx);
+    for (int k = 0; k < PERF_T_COUNT; ++k) {
+        out->ms[k] = ctx->kt[k].ms;
+        out->launches[k] = ctx->kt[k].launches;
+        if (reset) {
+            ctx->kt[k].ms = 0.0;
+            ctx->kt[k].launches = 0;
+        }
+    }
+    return PERF_OK;
+}
+
+}  // extern "C"

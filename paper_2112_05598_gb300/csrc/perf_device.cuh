@@ -1,0 +1,297 @@
+// perf_device.cuh -- device-side geometry of the PERF ray march (sm_103a).
+//
+// One ray per thread.  The ray itself (pixel -> origin / unit direction, box
+// entry and exit, the sample count K and step delta, which shells are hit) is
+// computed in IEEE binary32 with every operation rounded separately
+// (__fadd_rn & co. block FMA contraction), so that these integer decisions are
+// a fixed function of the inputs.  Everything after that is ordinary FP32.
+//
+// Conventions (PERF Section "Method", Section "Rendering", Section
+// "Jittering"):
+//   - grid [-1,1]^3, G^3 voxels, voxel side h = 2/G, centres at -1+(i+1/2)h;
+//   - K = ceil(L/h) samples (capped at max_samples) at t_in + (k+1/2+j_k) delta,
+//     delta = L/K, optical thickness sigma * delta/h (sigma per voxel side);
+//   - exact trilinear interpolation clamped to the edge;
+//   - shells: far root of |o + t d| = R, composited after the grid in order,
+//     with optical thickness sigma (one voxel side); equirectangular bilinear
+//     lookup wrapped in azimuth, clamped in polar angle.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+
+namespace perf {
+
+constexpr int kMaxShells = 8;
+
+struct DevScene {
+    int G;
+    float halfG;             // G/2
+    float h;                 // 2/G in binary32
+    int S;
+    float R[kMaxShells];
+    int He, We;
+    long long n_vox;         // G^3
+    long long shell_texels;  // He*We
+    int W, H, n_cams;
+    long long n_rays;
+    long long n_tiles;       // 8x4 pixel tiles over all cameras
+    int tiles_x, tiles_y;
+    const float* cams;       // n_cams x 16: c2w (12), focal, pad
+    int max_samples;
+    int jitter;
+    unsigned long long seed;
+    unsigned epoch;
+};
+
+struct Ray {
+    float o[3], d[3];
+    float t_in, delta;
+    int K;                   // 0: misses the grid
+    unsigned shell_hit;
+};
+
+__device__ __forceinline__ unsigned long long splitmix64(unsigned long long z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// U[0,1) with 24 bits: SplitMix64 (Steele, Lea, Flood 2014) of (seed+epoch,
+// ray, stream); stream 0/1 = pixel jitter, 2+k = sample k.
+__device__ __forceinline__ float jitter_u(const DevScene& sc, long long ray, unsigned stream) {
+    unsigned long long h = splitmix64(sc.seed + (unsigned long long)sc.epoch);
+    h = splitmix64(h + (unsigned long long)ray);
+    h = splitmix64(h + (unsigned long long)stream);
+    return (float)(h >> 40) * (1.0f / 16777216.0f);
+}
+
+// Pixel of lane `lane` in tile `tile`: tiles are 8 wide x 4 high.
+__device__ __forceinline__ bool tile_pixel(const DevScene& sc, long long tile, int lane,
+                                           long long& ray) {
+    const long long per_cam = (long long)sc.tiles_x * sc.tiles_y;
+    const int cam = (int)(tile / per_cam);
+    const int t = (int)(tile - (long long)cam * per_cam);
+    const int ty = t / sc.tiles_x, tx = t - ty * sc.tiles_x;
+    const int col = tx * 8 + (lane & 7);
+    const int row = ty * 4 + (lane >> 3);
+    if (col >= sc.W || row >= sc.H) return false;
+    ray = ((long long)cam * sc.H + row) * sc.W + col;
+    return true;
+}
+
+__device__ __forceinline__ void ray_setup(const DevScene& sc, long long ray, Ray& R) {
+    const long long hw = (long long)sc.W * sc.H;
+    const int cam = (int)(ray / hw);
+    const long long rem = ray - (long long)cam * hw;
+    const int row = (int)(rem / sc.W);
+    const int col = (int)(rem - (long long)row * sc.W);
+    const float* M = sc.cams + 16 * cam;
+    const float f = M[12];
+    float jx = 0.5f, jy = 0.5f;
+    if (sc.jitter) { jx = jitter_u(sc, ray, 0u); jy = jitter_u(sc, ray, 1u); }
+    const float px = __fadd_rn((float)col, jx);
+    const float py = __fadd_rn((float)row, jy);
+    const float xc = __fdiv_rn(__fsub_rn(px, __fmul_rn(0.5f, (float)sc.W)), f);
+    const float yc = -__fdiv_rn(__fsub_rn(py, __fmul_rn(0.5f, (float)sc.H)), f);
+    float d[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const float u = __fmul_rn(M[4 * a + 0], xc);
+        const float v = __fmul_rn(M[4 * a + 1], yc);
+        d[a] = __fsub_rn(__fadd_rn(u, v), M[4 * a + 2]);
+    }
+    const float nn = __fsqrt_rn(__fadd_rn(__fadd_rn(__fmul_rn(d[0], d[0]), __fmul_rn(d[1], d[1])),
+                                          __fmul_rn(d[2], d[2])));
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        R.d[a] = __fdiv_rn(d[a], nn);
+        R.o[a] = M[4 * a + 3];
+    }
+    float lo[3], hi[3];
+    bool miss = false;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (R.d[a] != 0.0f) {
+            const float t0 = __fdiv_rn(__fsub_rn(-1.0f, R.o[a]), R.d[a]);
+            const float t1 = __fdiv_rn(__fsub_rn(1.0f, R.o[a]), R.d[a]);
+            lo[a] = fminf(t0, t1);
+            hi[a] = fmaxf(t0, t1);
+        } else {
+            if (R.o[a] < -1.0f || R.o[a] > 1.0f) miss = true;
+            lo[a] = -INFINITY;
+            hi[a] = INFINITY;
+        }
+    }
+    const float t_in = fmaxf(fmaxf(fmaxf(lo[0], lo[1]), lo[2]), 0.0f);
+    const float t_out = fminf(fminf(hi[0], hi[1]), hi[2]);
+    R.t_in = t_in;
+    R.K = 0;
+    R.delta = 0.0f;
+    if (!miss && t_out > t_in) {
+        const float L = __fsub_rn(t_out, t_in);
+        int K = (int)ceilf(__fdiv_rn(L, sc.h));
+        K = min(K, sc.max_samples);
+        K = max(K, 1);
+        R.K = K;
+        R.delta = __fdiv_rn(L, (float)K);
+    }
+    const float b = __fadd_rn(__fadd_rn(__fmul_rn(R.o[0], R.d[0]), __fmul_rn(R.o[1], R.d[1])),
+                              __fmul_rn(R.o[2], R.d[2]));
+    const float oo = __fadd_rn(__fadd_rn(__fmul_rn(R.o[0], R.o[0]), __fmul_rn(R.o[1], R.o[1])),
+                               __fmul_rn(R.o[2], R.o[2]));
+    unsigned hit = 0u;
+    for (int s = 0; s < sc.S; ++s) {
+        const float c = __fsub_rn(oo, __fmul_rn(sc.R[s], sc.R[s]));
+        const float disc = __fsub_rn(__fmul_rn(b, b), c);
+        if (disc > 0.0f && (b < 0.0f || c < 0.0f)) hit |= 1u << s;
+    }
+    R.shell_hit = hit;
+}
+
+// Trilinear cell of a sample: base voxel (linear index) and fractions.
+struct Cell {
+    int bx, by, bz;
+    float fx, fy, fz;
+};
+
+__device__ __forceinline__ void axis_cell(float p, const DevScene& sc, int& b, float& f) {
+    float u = fmaf(p, sc.halfG, sc.halfG - 0.5f);
+    u = fminf(fmaxf(u, 0.0f), (float)(sc.G - 1));
+    float fl = floorf(u);
+    fl = fminf(fl, (float)(sc.G - 2));
+    b = (int)fl;
+    f = u - fl;
+}
+
+__device__ __forceinline__ Cell sample_cell(const DevScene& sc, const Ray& R, long long ray, int k) {
+    float jk = 0.0f;
+    if (sc.jitter) jk = jitter_u(sc, ray, 2u + (unsigned)k) - 0.5f;
+    const float t = fmaf((float)k + 0.5f + jk, R.delta, R.t_in);
+    Cell c;
+    axis_cell(fmaf(t, R.d[0], R.o[0]), sc, c.bx, c.fx);
+    axis_cell(fmaf(t, R.d[1], R.o[1]), sc, c.by, c.fy);
+    axis_cell(fmaf(t, R.d[2], R.o[2]), sc, c.bz, c.fz);
+    return c;
+}
+
+// --- storage access: float4 (FP32) or 4 x bf16 (BF16) per voxel / texel
+template <typename T> struct Store;
+template <> struct Store<float> {
+    static __device__ __forceinline__ float4 ld(const float* x, long long v) {
+        return __ldg(reinterpret_cast<const float4*>(x) + v);
+    }
+};
+template <> struct Store<__nv_bfloat16> {
+    static __device__ __forceinline__ float4 ld(const __nv_bfloat16* x, long long v) {
+        const uint2 u = __ldg(reinterpret_cast<const uint2*>(x) + v);
+        float4 r;
+        r.x = __uint_as_float(u.x << 16);
+        r.y = __uint_as_float(u.x & 0xffff0000u);
+        r.z = __uint_as_float(u.y << 16);
+        r.w = __uint_as_float(u.y & 0xffff0000u);
+        return r;
+    }
+};
+
+__device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
+    return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y),
+                       fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
+}
+
+template <typename T>
+__device__ __forceinline__ float4 interp_grid(const T* x, const DevScene& sc, const Cell& c) {
+    const long long G = sc.G;
+    const long long i0 = ((long long)c.bz * G + c.by) * G + c.bx;
+    const long long sy = G, sz = G * G;
+    const float4 a000 = Store<T>::ld(x, i0);
+    const float4 a100 = Store<T>::ld(x, i0 + 1);
+    const float4 a010 = Store<T>::ld(x, i0 + sy);
+    const float4 a110 = Store<T>::ld(x, i0 + sy + 1);
+    const float4 a001 = Store<T>::ld(x, i0 + sz);
+    const float4 a101 = Store<T>::ld(x, i0 + sz + 1);
+    const float4 a011 = Store<T>::ld(x, i0 + sz + sy);
+    const float4 a111 = Store<T>::ld(x, i0 + sz + sy + 1);
+    const float4 b00 = lerp4(a000, a100, c.fx), b10 = lerp4(a010, a110, c.fx);
+    const float4 b01 = lerp4(a001, a101, c.fx), b11 = lerp4(a011, a111, c.fx);
+    const float4 c0 = lerp4(b00, b10, c.fy), c1 = lerp4(b01, b11, c.fy);
+    return lerp4(c0, c1, c.fz);
+}
+
+// Bilinear texels of one shell hit: 4 parameter-block indices and weights.
+struct ShellHit {
+    long long idx[4];
+    float w[4];
+};
+
+__device__ __forceinline__ bool shell_lookup(const DevScene& sc, const Ray& R, int s, ShellHit& hs) {
+    if (!(R.shell_hit & (1u << s))) return false;
+    const float b = R.o[0] * R.d[0] + R.o[1] * R.d[1] + R.o[2] * R.d[2];
+    const float c = R.o[0] * R.o[0] + R.o[1] * R.o[1] + R.o[2] * R.o[2] - sc.R[s] * sc.R[s];
+    const float disc = fmaxf(b * b - c, 0.0f);
+    const float sq = sqrtf(disc);
+    const float t = (b < 0.0f) ? (sq - b) : (c / (-b - sq));
+    const float qx = fmaf(t, R.d[0], R.o[0]);
+    const float qy = fmaf(t, R.d[1], R.o[1]);
+    const float qz = fmaf(t, R.d[2], R.o[2]);
+    const float phi = atan2f(qy, qx);
+    const float theta = atan2f(sqrtf(qx * qx + qy * qy), qz);
+    const float u = (phi * 0.15915494309189535f + 0.5f) * (float)sc.We - 0.5f;
+    float v = theta * 0.31830988618379067f * (float)sc.He - 0.5f;
+    const float j0 = floorf(u);
+    const float fu = u - j0;
+    int c0 = (int)j0 % sc.We;
+    if (c0 < 0) c0 += sc.We;
+    int c1 = c0 + 1;
+    if (c1 >= sc.We) c1 -= sc.We;
+    v = fminf(fmaxf(v, 0.0f), (float)(sc.He - 1));
+    float i0 = floorf(v);
+    i0 = fminf(i0, (float)(sc.He - 2));
+    const float fv = v - i0;
+    const int r0 = (int)i0;
+    const long long base = sc.n_vox + (long long)s * sc.shell_texels;
+    hs.idx[0] = base + (long long)r0 * sc.We + c0;
+    hs.idx[1] = base + (long long)r0 * sc.We + c1;
+    hs.idx[2] = base + (long long)(r0 + 1) * sc.We + c0;
+    hs.idx[3] = base + (long long)(r0 + 1) * sc.We + c1;
+    hs.w[0] = (1.0f - fu) * (1.0f - fv);
+    hs.w[1] = fu * (1.0f - fv);
+    hs.w[2] = (1.0f - fu) * fv;
+    hs.w[3] = fu * fv;
+    return true;
+}
+
+template <typename T>
+__device__ __forceinline__ float4 interp_shell(const T* x, const ShellHit& hs) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float4 a = Store<T>::ld(x, hs.idx[q]);
+        acc.x = fmaf(hs.w[q], a.x, acc.x);
+        acc.y = fmaf(hs.w[q], a.y, acc.y);
+        acc.z = fmaf(hs.w[q], a.z, acc.z);
+        acc.w = fmaf(hs.w[q], a.w, acc.w);
+    }
+    return acc;
+}
+
+// FP64 block reduction into one device double (one atomic per block).
+template <int NWARPS>
+__device__ __forceinline__ void block_add_f64(double v, double* dst) {
+    __shared__ double red[NWARPS];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) red[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        v = lane < NWARPS ? red[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0 && v != 0.0) atomicAdd(dst, v);
+    }
+    __syncthreads();   // red[] may be reused by a following call
+}
+
+}  // namespace perf

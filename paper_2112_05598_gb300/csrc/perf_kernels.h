@@ -1,0 +1,65 @@
+// perf_kernels.h -- host launchers of the libperf kernels (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include "perf_device.cuh"
+
+namespace perf {
+
+// Device scalars of Algorithm 2 and the line search (FP64).
+struct PcgScalars {
+    double rz;        // r_k^T z_k
+    double R0;        // r_0^T r_0
+    double R_prev;    // r_{k}^T r_{k} of the previous iteration
+    double R;         // latest r^T r
+    double pAp;       // accumulator: p^T A p
+    double acc_R;     // accumulator: r_{k+1}^T r_{k+1}
+    double acc_rz;    // accumulator: r_{k+1}^T z_{k+1}
+    double beta;
+    double F;         // accumulator: objective
+    int iter;
+    int done;
+    int exit_reason;
+    int max_iter;
+    int fixed;
+    int pad;
+    double eps_rel;
+    double stall;
+};
+
+// Kernels launched by this library since load (instrumentation).
+extern unsigned long long g_launches;
+inline void count_launch(unsigned long long k = 1) { __atomic_fetch_add(&g_launches, k, __ATOMIC_RELAXED); }
+
+// Total grid samples and shell hits over all rays (one march of the scene).
+cudaError_t launch_count_samples(const DevScene& sc, unsigned long long* out, cudaStream_t st);
+
+// mode: 0 render (out = rgb, T_out), 1 residual (out = r, F), 2 F only.
+cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const float* target,
+                           float* out, float* T_out, double* F, int mode, cudaStream_t st);
+cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void* p, int p_dtype,
+                       float* out, cudaStream_t st);
+// mode: 0 J^T v, 1 A p (+p^T A p), 2 diag(J^T J) (+ J^T r when v = r and out2 given).
+cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* x, const void* p,
+                           int p_dtype, const float* v, float* out, float* out2, double* pap,
+                           cudaStream_t st);
+
+// Algorithm 2 vector work (k_pcg.cu).
+cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, float* delta,
+                             float* rho, float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
+                             int max_iter, int fixed, double eps_rel, double stall,
+                             const float* blocks, long long n_block, cudaStream_t st);
+cudaError_t launch_pcg_update(long long n, float* delta, float* rho, const float* p,
+                              const float* Ap, const float* diag, const float* blocks,
+                              long long n_block, PcgScalars* s, cudaStream_t st);
+cudaError_t launch_pcg_dir(long long n, const float* rho, const float* diag, const float* blocks,
+                           long long n_block, float* p, __nv_bfloat16* p16, float* Ap,
+                           PcgScalars* s, cudaStream_t st);
+// One thread: the exit test of Algorithm 2 and beta (after launch_pcg_update).
+cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st);
+// x_out = P(x + gamma delta) (project: sigma >= 0, 0 <= c <= 1); optional
+// float32 and bf16 outputs.
+cudaError_t launch_trial(long long n, const float* x, const float* delta, float gamma, int project,
+                         float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
+cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaStream_t st);
+
+}  // namespace perf

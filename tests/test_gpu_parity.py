@@ -1,0 +1,248 @@
+"""CUDA path vs the FP64 oracle, element by element, through the C ABI.
+
+Small cases cover several 8x4 ray tiles with ragged image edges and every
+derivative term; the 32^3 workload (8 cameras 64x64, 2 shells) is compared
+in full, Gauss-Newton steps included.  Tolerances: relative L2 1e-5 for
+FP32 r, J p, J^T v (and the image and Jacobi diagonal), 1e-4 for the
+parameters after each Gauss-Newton step."""
+import numpy as np
+import pytest
+
+from conftest import rel_l2, tiny_problem
+from gpu_common import (TOL_FP32, TOL_GN, cuda_tensor, empty, host, make_pair,
+                        mid_state, pair_from_scene)
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def small():
+    from scenegen import make_scene
+    sc = make_scene("small32")
+    ctx, orc = pair_from_scene(sc)
+    rng = np.random.default_rng(100)
+    target = orc.render(sc.x_gt)[0].astype(np.float32).ravel()
+    x = mid_state(rng, sc)
+    return dict(sc=sc, ctx=ctx, orc=orc, target=target, x=x, rng=rng)
+
+
+def _render(ctx, x):
+    import torch
+    rgb = empty(3 * ctx.n_rays)
+    T = empty(ctx.n_rays)
+    ctx.render(cuda_tensor(x), rgb, T)
+    return host(rgb), host(T)
+
+
+def test_render_parity(small):
+    ctx, orc, x = small["ctx"], small["orc"], small["x"]
+    rgb, T = _render(ctx, x)
+    ref, Tref, _ = orc.render(x.astype(np.float64))
+    assert rel_l2(rgb, ref) < TOL_FP32
+    assert rel_l2(T, Tref) < TOL_FP32
+    assert np.abs(rgb - ref.ravel()).max() < 1e-4
+
+
+def test_residual_and_objective_parity(small):
+    import torch
+    ctx, orc, x, target = small["ctx"], small["orc"], small["x"], small["target"]
+    r = empty(3 * ctx.n_rays)
+    F = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.residual(cuda_tensor(x), cuda_tensor(target), r, F)
+    rref, Fref = orc.residual(x.astype(np.float64), target)
+    assert rel_l2(host(r), rref) < TOL_FP32
+    assert abs(host(F)[0] - Fref) <= 1e-5 * Fref
+    # F only (no residual buffer)
+    ctx.residual(cuda_tensor(x), cuda_tensor(target), None, F)
+    assert abs(host(F)[0] - Fref) <= 1e-5 * Fref
+
+
+def test_jvp_parity(small):
+    ctx, orc, x, rng = small["ctx"], small["orc"], small["x"], small["rng"]
+    p = rng.normal(size=x.shape[0]).astype(np.float32)
+    out = empty(3 * ctx.n_rays)
+    ctx.jvp(cuda_tensor(x), cuda_tensor(p), out)
+    ref = orc.jvp(x.astype(np.float64), p.astype(np.float64))
+    assert rel_l2(host(out), ref) < TOL_FP32
+
+
+def test_vjp_parity(small):
+    ctx, orc, x, rng = small["ctx"], small["orc"], small["x"], small["rng"]
+    v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
+    out = empty(ctx.n_params)
+    ctx.vjp(cuda_tensor(x), cuda_tensor(v), out)
+    ref = orc.vjp(x.astype(np.float64), v.astype(np.float64))
+    assert rel_l2(host(out), ref) < TOL_FP32
+    # accumulate = 1 adds onto the output
+    ctx.vjp(cuda_tensor(x), cuda_tensor(v), out, accumulate=True)
+    assert rel_l2(host(out), 2 * ref) < TOL_FP32
+
+
+def test_diag_and_gradient_parity(small):
+    ctx, orc, x, target = small["ctx"], small["orc"], small["x"], small["target"]
+    rref, _ = orc.residual(x.astype(np.float64), target)
+    r = cuda_tensor(rref.astype(np.float32))
+    d = empty(ctx.n_params)
+    g = empty(ctx.n_params)
+    ctx.diag_jtj(cuda_tensor(x), d, r, g)
+    dref, gref = orc.diag_grad(x.astype(np.float64), rref.astype(np.float32).astype(np.float64))
+    assert rel_l2(host(d), dref) < TOL_FP32
+    assert rel_l2(host(g), gref) < TOL_FP32
+    # diagonal alone
+    d2 = empty(ctx.n_params)
+    ctx.diag_jtj(cuda_tensor(x), d2)
+    assert rel_l2(host(d2), dref) < TOL_FP32
+
+
+def test_apply_normal_parity(small):
+    import torch
+    ctx, orc, x, rng = small["ctx"], small["orc"], small["x"], small["rng"]
+    p = rng.normal(size=x.shape[0]).astype(np.float32)
+    ap = empty(ctx.n_params)
+    pap = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.apply_normal(cuda_tensor(x), cuda_tensor(p), ap, pap)
+    ref = orc.apply_A(x.astype(np.float64), p.astype(np.float64))
+    assert rel_l2(host(ap), ref) < TOL_FP32
+    jp = orc.jvp(x.astype(np.float64), p.astype(np.float64))
+    assert abs(host(pap)[0] - float(jp @ jp)) <= 1e-5 * float(jp @ jp)
+
+
+def test_adjoint_identity_on_gpu(small):
+    ctx, x, rng = small["ctx"], small["x"], small["rng"]
+    p = rng.normal(size=x.shape[0]).astype(np.float32)
+    v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
+    jp = empty(3 * ctx.n_rays)
+    jtv = empty(ctx.n_params)
+    ctx.jvp(cuda_tensor(x), cuda_tensor(p), jp)
+    ctx.vjp(cuda_tensor(x), cuda_tensor(v), jtv)
+    lhs = float(host(jp) @ v.astype(np.float64))
+    rhs = float(p.astype(np.float64) @ host(jtv))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+def test_pcg_iterations_parity(small):
+    from oracle import jacobi_apply, pcg
+    ctx, orc, x, target = small["ctx"], small["orc"], small["x"], small["target"]
+    x64 = x.astype(np.float64)
+    rref, _ = orc.residual(x64, target)
+    dref, gref = orc.diag_grad(x64, rref)
+    k = 5
+    res = pcg(lambda p: orc.apply_A(x64, p), -gref, lambda v: jacobi_apply(dref, v), k, fixed=True)
+    ctx.set_options(pcg_iters=k, pcg_fixed=1)
+    xd = cuda_tensor(x)
+    ctx.pcg_begin(cuda_tensor(gref.astype(np.float32)), cuda_tensor(dref.astype(np.float32)))
+    for _ in range(k):
+        ctx.pcg_step(xd)
+    delta = empty(ctx.n_params)
+    info = ctx.pcg_result(delta)
+    assert info["iters"] == k
+    assert rel_l2(host(delta), res.x) < 1e-4
+    assert abs(info["R"] - res.R[-1]) <= 1e-3 * res.R[-1]
+
+
+def test_gn_steps_parity(small):
+    """Each GPU Gauss-Newton step (20 PCG iterations, line search, projection)
+    against one oracle step from the same starting point."""
+    from oracle import gn_step
+    sc, ctx, orc, target = small["sc"], small["ctx"], small["orc"], small["target"]
+    ctx.set_options(pcg_iters=sc.cfg.pcg_iters, pcg_fixed=1)
+    x = sc.x0.copy()
+    xd = cuda_tensor(x)
+    td = cuda_tensor(target)
+    checked = 0
+    for step in range(sc.cfg.gn_steps):
+        x_before = host(xd)
+        st = ctx.gn_solve(xd, td, 1)[0]
+        ref = gn_step(orc, x_before, target, sc.cfg.pcg_iters)
+        assert st["accepted"] == ref.accepted
+        assert abs(st["F_before"] - ref.F_before) <= 1e-5 * ref.F_before
+        mus = [m for _, m in ref.trace]
+        tie = any(abs(a - b) <= 1e-6 * abs(a) for a, b in zip(mus, mus[1:]))
+        if abs(st["gamma"] - ref.gamma) > 1e-9:
+            assert tie, (step, st["gamma"], ref.gamma)
+            xd = cuda_tensor(ref.x.astype(np.float32))
+            continue
+        assert rel_l2(host(xd), ref.x) < TOL_GN, step
+        checked += 1
+    assert checked >= 3
+
+
+def test_jitter_parity():
+    rng = np.random.default_rng(101)
+    prob = tiny_problem(rng, G=10, n_cams=3, res=13, radii=(2.5, 5.0))
+    ctx, orc = make_pair(prob["G"], prob["radii"], prob["env_h"], prob["env_w"], prob["c2w"],
+                         prob["focal"], 13, 13, jitter=True, seed=77, epoch=4)
+    x = prob["x"]
+    rgb, _ = _render(ctx, x)
+    ref = orc.render(x.astype(np.float64))[0]
+    assert rel_l2(rgb, ref) < TOL_FP32
+    v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
+    out = empty(ctx.n_params)
+    ctx.vjp(cuda_tensor(x), cuda_tensor(v), out)
+    assert rel_l2(host(out), orc.vjp(x.astype(np.float64), v.astype(np.float64))) < TOL_FP32
+    d = empty(ctx.n_params)
+    ctx.diag_jtj(cuda_tensor(x), d)
+    assert rel_l2(host(d), orc.diag_grad(x.astype(np.float64))[0]) < TOL_FP32
+
+
+@pytest.mark.parametrize("G,res,max_samples,radii", [
+    (2, 7, 64, (2.0,)),          # smallest grid, ragged 7x7 image (one partial tile)
+    (9, 13, 4, (2.0, 3.0, 6.0)),  # max_samples cap binds (K > 4)
+    (16, 9, 64, ()),              # no shells
+])
+def test_edge_cases_parity(G, res, max_samples, radii):
+    rng = np.random.default_rng(G * 31 + res)
+    prob = tiny_problem(rng, G=G, res=res, n_cams=2, radii=radii, max_samples=max_samples)
+    ctx, orc = make_pair(G, radii, prob["env_h"], prob["env_w"], prob["c2w"], prob["focal"],
+                         res, res, max_samples=max_samples)
+    x = prob["x"]
+    rgb, _ = _render(ctx, x)
+    assert rel_l2(rgb, orc.render(x.astype(np.float64))[0]) < TOL_FP32
+    v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
+    out = empty(ctx.n_params)
+    ctx.vjp(cuda_tensor(x), cuda_tensor(v), out)
+    assert rel_l2(host(out), orc.vjp(x.astype(np.float64), v.astype(np.float64))) < TOL_FP32
+    d = empty(ctx.n_params)
+    ctx.diag_jtj(cuda_tensor(x), d)
+    assert rel_l2(host(d), orc.diag_grad(x.astype(np.float64))[0]) < TOL_FP32
+
+
+def test_rays_missing_the_grid():
+    """Cameras looking away from the grid: every ray misses it and sees only
+    the shells; the grid gets no gradient and a zero Jacobi diagonal."""
+    from scenegen import look_at_c2w
+    rng = np.random.default_rng(102)
+    c2w = []
+    for pos in ([0.0, 0.0, 1.8], [1.9, 0.0, 0.0]):
+        m = look_at_c2w(np.array(pos))
+        m[:, 0:3] = -m[:, 0:3]           # turn around: look away from the origin
+        m[:, 1] = -m[:, 1]
+        c2w.append(m)
+    c2w = np.array(c2w, np.float32)
+    focal = np.full(2, 20.0, np.float32)
+    ctx, orc = make_pair(5, (2.5, 4.0), 6, 12, c2w, focal, 16, 16)
+    from scenegen import random_params
+    x = random_params(rng, 5, 2, 6, 12, 0.1, 1.0)
+    rgb, T = _render(ctx, x)
+    ref, Tref, _ = orc.render(x.astype(np.float64))
+    assert np.all(Tref == 1.0) and np.all(T == 1.0)
+    assert rel_l2(rgb, ref) < TOL_FP32
+    d = empty(ctx.n_params)
+    ctx.diag_jtj(cuda_tensor(x), d)
+    dd = host(d)
+    assert np.all(dd[: 4 * 125] == 0)
+    assert rel_l2(dd, orc.diag_grad(x.astype(np.float64))[0]) < TOL_FP32
+
+
+def test_empty_camera_set():
+    import torch
+    from paper_2112_05598_gb300 import Context
+    ctx = Context(4, (2.0,), 4, 8, np.zeros((0, 3, 4), np.float32), np.zeros(0, np.float32), 8, 8)
+    assert ctx.n_rays == 0
+    x = cuda_tensor(np.full(ctx.n_params, 0.5, np.float32))
+    F = torch.ones(1, dtype=torch.float64, device="cuda")
+    ctx.residual(x, x, None, F)
+    assert host(F)[0] == 0.0
+    out = empty(ctx.n_params) + 3.0
+    ctx.vjp(x, x, out)
+    assert np.all(host(out) == 0.0)
