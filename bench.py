@@ -205,6 +205,8 @@ def _workload_desc(sc):
 
 def run_ours(args, rank, world, local):
     import torch
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_2112_05598_gb300 import Context
     from paper_2112_05598_gb300._binding import launch_count
     from scenegen import make_scene

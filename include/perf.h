@@ -63,7 +63,7 @@ typedef struct perf_ctx perf_ctx;
 
 /* Scene geometry (Section "Method"; Fig. "scene"). */
 typedef struct {
-    int32_t grid_res;                      /* G >= 2 */
+    int32_t grid_res;                      /* 2 <= G <= 1024 */
     int32_t n_shells;                      /* S in [0, 8] */
     float shell_radii[PERF_MAX_SHELLS];    /* increasing, each > sqrt(3) */
     int32_t env_h, env_w;                  /* texels per shell, >= 2 if S > 0 */
@@ -129,7 +129,8 @@ typedef struct {
 perf_status perf_default_options(perf_options* out);
 
 /* Creates a context for one scene and camera set.  Validates everything
- * (G >= 2, 0 <= S <= 8, radii increasing and > sqrt(3), env size >= 2,
+ * (2 <= G <= 1024, 0 <= S <= 8, radii increasing and > sqrt(3), env size >= 2,
+ * fewer than 2^31 parameter blocks,
  * cameras >= 0, max_samples >= 1), copies the cameras to the device and
  * allocates the workspace.  On failure *out is NULL. */
 perf_status perf_create(perf_ctx** out, const perf_scene* scene,

@@ -216,11 +216,20 @@ class PCGResult:
     exit: str               # "fixed" | "eps" | "stall" | "breakdown"
 
 
+# Jacobi diagonal entries at or below this count as unobserved (z_j = 0).
+# The paper's implementation keeps the diagonal in binary32, where the square
+# of a row entry below ~1e-19 is not a normal number; parameters that deep
+# behind opaque matter are indistinguishable from ones no ray sees (Section
+# "Preconditioner").  1e-30 leaves binary32 full relative precision above it.
+JACOBI_FLOOR = 1e-30
+
+
 def jacobi_apply(diag: np.ndarray, r: np.ndarray) -> np.ndarray:
     """z = M^{-1} r with M = diag(J^T J); parameters that no residual depends
-    on (d_j = 0) get z_j = 0."""
+    on (d_j = 0), or only through entries squaring to at most JACOBI_FLOOR,
+    get z_j = 0."""
     z = np.zeros_like(r)
-    nz = diag > 0
+    nz = diag > JACOBI_FLOOR
     z[nz] = r[nz] / diag[nz]
     return z
 

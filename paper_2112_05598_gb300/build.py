@@ -6,6 +6,7 @@ shares device state with PyTorch in the same process.
 """
 import concurrent.futures
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -13,8 +14,9 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(os.path.dirname(HERE), "include")
-BUILD = os.path.join(HERE, "_build")
+BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libperf.so")
+STAMP = LIB + ".arch"
 
 SOURCES = ["k_march.cu", "k_pcg.cu", "k_lpc.cu", "perf_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -34,6 +36,14 @@ def _cuda_lib_dir(nvcc):
         if os.path.exists(os.path.join(p, "libcudart.so")):
             return p
     return os.path.join(root, "lib64")
+
+
+def _lib_arch_ok():
+    try:
+        with open(STAMP) as f:
+            return f.read().strip() == platform.machine()
+    except OSError:
+        return False
 
 
 def _stale(srcs, out):
@@ -67,7 +77,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
 
     with concurrent.futures.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    if force or _stale(objs, LIB):
+    if force or _stale(objs, LIB) or not _lib_arch_ok():
         libdir = _cuda_lib_dir(nvcc)
         cmd = [nvcc, "-shared", "-o", LIB + ".tmp"] + objs + ARCH + [
             "-cudart", "shared", "-L" + libdir, "-Xlinker", "-rpath," + libdir]
@@ -75,6 +85,8 @@ def build(force: bool = False, verbose: bool = False, extra_flags=None) -> str:
         if r.returncode != 0:
             raise RuntimeError(f"link failed:\n{r.stderr}")
         os.replace(LIB + ".tmp", LIB)
+        with open(STAMP, "w") as f:
+            f.write(platform.machine())
     return LIB
 
 

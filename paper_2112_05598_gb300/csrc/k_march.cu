@@ -5,23 +5,32 @@
 //   k_scatter   J^T v, the fused A p = J^T (J p), and diag(J^T J) with J^T r
 //
 // Derivatives (Algorithm 1, Section "Computation of partial derivatives"):
-// for sample i with transmittance T_i, e_i = exp(-sigma_i dbar_i),
-// alpha_i = 1 - e_i and weight w_i = T_i alpha_i,
+// for sample i with optical thickness s_i = sigma_i dbar_i, transmittance
+// T_i = e^{-V_i} (V_i = sum_{j<i} s_j), alpha_i = 1 - e^{-s_i} and weight
+// w_i = T_i alpha_i,
 //   dH/dc_i       = w_i
-//   dH_k/dsigma_i = dbar_i (T_i e_i c_ik - G_ik),   G_i = sum_{j>i} w_j c_j.
-// Algorithm 1 obtains G_i by a backward sweep; here G_i = H^ - P_i with the
-// forward prefix P_i = sum_{j<=i} w_j c_j and H^ from a first sweep, so each
-// ray is marched front to back twice (the paper also invokes Algorithm 1
-// twice per ray for A p) and no per-sample state is stored.
+//   dH_k/dsigma_i = dbar_i (T_i e^{-s_i} c_ik - G_ik),  G_i = sum_{j>i} w_j c_j.
+// The scatter kernels run Algorithm 1 as printed: a first front-to-back sweep
+// gives the total optical depth V (grid samples and shell hits), then a
+// back-to-front sweep subtracts s_i from V (so e^{-V} = T_i) and accumulates
+// G after each use.  G is a sum of non-negative terms, so every partial has
+// full relative accuracy even where T_i is tiny -- which matters because the
+// Jacobi preconditioner rescales every parameter to unit diagonal.  V is kept
+// as an unevaluated FP32 sum (hi + lo, TwoSum) so that T_i stays accurate in
+// front of optically deep media.
 //
 // Scatter: consecutive samples of one ray share most of their 8 trilinear
 // voxels.  A register window of the 2x2x2 voxels of the current sample keeps
-// one running sum per voxel; a voxel is flushed (one 16-byte vector atomic)
-// when the window slides past it.  Because a voxel's trilinear support is a
-// box, the samples of one ray that touch it are consecutive, so each voxel is
-// flushed exactly once per ray -- which also makes the window compute the
-// EXACT diag(J^T J): a row's entry for a voxel is complete before it is
-// squared (Section "Preconditioner").
+// one running sum per voxel; a voxel is flushed when the window slides past
+// it.  A voxel's trilinear support is a box, so the samples of one ray that
+// touch it are consecutive and each voxel is flushed exactly once per ray --
+// which also makes the window compute the EXACT diag(J^T J): a row's entry for
+// a voxel is complete before it is squared (Section "Preconditioner").
+// Neighbouring rays cross the same voxels at the same time.  Window slots are
+// indexed by the parity of the voxel's coordinates, and the sample loop is
+// warp-uniform, so the lanes of a warp (an 8x4 pixel tile) that evict the
+// same voxel do it in the same 16-byte vector atomic, which the load/store
+// unit merges before it reaches L2.
 #include "perf_device.cuh"
 #include "perf_kernels.h"
 
@@ -29,16 +38,46 @@ namespace perf {
 
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
+constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ helpers
+
+// 1 - e^{-x} with full relative accuracy: for |x| < 1/4 the Taylor series
+// x (1 - x/2 (1 - x/3 (1 - x/4 (1 - x/5 (1 - x/6 (1 - x/7)))))) (truncation
+// below 2e-9 relative), elsewhere 1 - e (no cancellation there).
+__device__ __forceinline__ float one_minus_exp_neg(float x, float e) {
+    if (fabsf(x) < 0.25f) {
+        float p = fmaf(-x, 1.0f / 7.0f, 1.0f);
+        p = fmaf(-x * (1.0f / 6.0f), p, 1.0f);
+        p = fmaf(-x * (1.0f / 5.0f), p, 1.0f);
+        p = fmaf(-x * (1.0f / 4.0f), p, 1.0f);
+        p = fmaf(-x * (1.0f / 3.0f), p, 1.0f);
+        p = fmaf(-x * 0.5f, p, 1.0f);
+        return x * p;
+    }
+    return 1.0f - e;
+}
+
+// Compensated running sum (Knuth's TwoSum): value = hi + lo.
+struct CSum {
+    float hi, lo;
+};
+__device__ __forceinline__ void csum_add(CSum& s, float a) {
+    const float t = __fadd_rn(s.hi, a);
+    const float bp = __fsub_rn(t, s.hi);
+    const float err = __fadd_rn(__fsub_rn(s.hi, __fsub_rn(t, bp)), __fsub_rn(a, bp));
+    s.hi = t;
+    s.lo = __fadd_rn(s.lo, err);
+}
 
 struct Comp {   // running composite of one ray
     float T, H[3];
 };
 
 __device__ __forceinline__ void comp_step(Comp& s, const float4 a, float dbar) {
-    const float e = expf(-__fmul_rn(a.w, dbar));
-    const float w = __fmul_rn(s.T, __fsub_rn(1.0f, e));
+    const float sd = __fmul_rn(a.w, dbar);
+    const float e = expf(-sd);
+    const float w = __fmul_rn(s.T, one_minus_exp_neg(sd, e));
     s.H[0] = fmaf(w, a.x, s.H[0]);
     s.H[1] = fmaf(w, a.y, s.H[1]);
     s.H[2] = fmaf(w, a.z, s.H[2]);
@@ -63,14 +102,33 @@ __device__ __forceinline__ void composite(const DevScene& sc, const T* __restric
     }
 }
 
-// Tangent sweep: H^ and (J p) of one ray.
+// Total optical depth of a ray (grid samples, then shell hits), compensated.
+template <typename T>
+__device__ __forceinline__ CSum optical_depth(const DevScene& sc, const T* __restrict__ x,
+                                              const Ray& R, long long ray) {
+    CSum V = {0.0f, 0.0f};
+    const float dbar = R.delta * sc.halfG;
+    for (int k = 0; k < R.K; ++k) {
+        const Cell cl = sample_cell(sc, R, ray, k);
+        csum_add(V, __fmul_rn(interp_grid(x, sc, cl).w, dbar));
+    }
+    for (int q = 0; q < sc.S; ++q) {
+        ShellHit hs;
+        if (shell_lookup(sc, R, q, hs)) csum_add(V, interp_shell(x, hs).w);
+    }
+    return V;
+}
+
+// Tangent sweep: H^, (J p) and the optical depth V of one ray.
 struct Tang {
     float T, Td, H[3], J[3];
+    CSum V;
 };
 
 __device__ __forceinline__ void tang_step(Tang& s, const float4 a, const float4 q, float dbar) {
-    const float e = expf(-__fmul_rn(a.w, dbar));
-    const float alpha = __fsub_rn(1.0f, e);
+    const float sd = __fmul_rn(a.w, dbar);
+    const float e = expf(-sd);
+    const float alpha = one_minus_exp_neg(sd, e);
     const float w = __fmul_rn(s.T, alpha);
     const float tsd = s.T * dbar * q.w;               // T dbar sigma_dot
     const float coef = fmaf(s.Td, alpha, tsd * e);     // T_dot alpha + T e dbar sigma_dot
@@ -82,6 +140,7 @@ __device__ __forceinline__ void tang_step(Tang& s, const float4 a, const float4 
     s.H[2] = fmaf(w, a.z, s.H[2]);
     s.Td = e * (s.Td - tsd);
     s.T = __fmul_rn(s.T, e);
+    csum_add(s.V, sd);
 }
 
 template <typename T, typename TP>
@@ -91,6 +150,7 @@ __device__ __forceinline__ void tangent(const DevScene& sc, const T* __restrict_
     s.T = 1.0f; s.Td = 0.0f;
     s.H[0] = s.H[1] = s.H[2] = 0.0f;
     s.J[0] = s.J[1] = s.J[2] = 0.0f;
+    s.V.hi = 0.0f; s.V.lo = 0.0f;
     const float dbar = R.delta * sc.halfG;
     for (int k = 0; k < R.K; ++k) {
         const Cell cl = sample_cell(sc, R, ray, k);
@@ -104,140 +164,46 @@ __device__ __forceinline__ void tangent(const DevScene& sc, const T* __restrict_
 
 // ------------------------------------------------------- voxel window
 
+__device__ __forceinline__ void red_add4(float* base, long long blk, float4 v) {
+    atomicAdd(reinterpret_cast<float4*>(base) + blk, v);
+}
+
+// The 2x2x2 window of the current sample holds exactly one voxel of each
+// coordinate-parity class, so slot p (bit a = parity along axis a) always
+// holds the window's voxel of parity p.  A voxel therefore sits in the same
+// slot on every lane of the warp, and lanes that evict it in the same
+// iteration do so in the same vector atomic, which the hardware merges.
 template <int NV>
 struct Window {
     float v[8][NV];
     int b[3];
 };
 
-template <int NV>
-__device__ __forceinline__ void win_zero(Window<NV>& w, int c) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) w.v[c][q] = 0.0f;
-}
+// Coordinate along one axis of the window voxel with parity bit `pa`.
+__device__ __forceinline__ int par_coord(int base, int pa) { return base + ((pa ^ base) & 1); }
 
-template <int NV>
-__device__ __forceinline__ void win_move(Window<NV>& w, int dst, int src) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) w.v[dst][q] = w.v[src][q];
-}
+__device__ __forceinline__ int vox_key(int x, int y, int z, int G) { return (z * G + y) * G + x; }
 
-template <int NV, class F>
-__device__ __forceinline__ void win_flush(Window<NV>& w, int c, int G, F& fl) {
-    const long long key = ((long long)(w.b[2] + (c >> 2)) * G + (w.b[1] + ((c >> 1) & 1))) * G +
-                          (w.b[0] + (c & 1));
-    fl(key, w.v[c]);
-}
-
-// Slide the window along axis A to base nb, flushing the voxels it leaves.
-template <int A, int NV, class F>
-__device__ __forceinline__ void win_shift(Window<NV>& w, int nb, int G, F& fl) {
-    const int d = nb - w.b[A];
-    if (d == 0) return;
-    constexpr int B = 1 << A;
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        if (c & B) continue;
-        const int lo = c, hi = c | B;
-        if (d == 1) {
-            win_flush(w, lo, G, fl);
-            win_move(w, lo, hi);
-            win_zero(w, hi);
-        } else if (d == -1) {
-            win_flush(w, hi, G, fl);
-            win_move(w, hi, lo);
-            win_zero(w, lo);
-        } else {
-            win_flush(w, lo, G, fl);
-            win_flush(w, hi, G, fl);
-            win_zero(w, lo);
-            win_zero(w, hi);
-        }
-    }
-    w.b[A] = nb;
-}
-
-template <int NV, class F>
-__device__ __forceinline__ void win_goto(Window<NV>& w, const Cell& cl, int G, F& fl) {
-    win_shift<0>(w, cl.bx, G, fl);
-    win_shift<1>(w, cl.by, G, fl);
-    win_shift<2>(w, cl.bz, G, fl);
-}
-
-template <int NV>
-__device__ __forceinline__ void win_add(Window<NV>& w, const Cell& cl, const float (&val)[NV]) {
-    const float wx[2] = {1.0f - cl.fx, cl.fx};
-    const float wy[2] = {1.0f - cl.fy, cl.fy};
-    const float wz[2] = {1.0f - cl.fz, cl.fz};
-#pragma unroll
-    for (int c = 0; c < 8; ++c) {
-        const float W = wx[c & 1] * wy[(c >> 1) & 1] * wz[c >> 2];
-#pragma unroll
-        for (int q = 0; q < NV; ++q) w.v[c][q] = fmaf(W, val[q], w.v[c][q]);
-    }
-}
-
-// ------------------------------------------------------------- sinks
-
-__device__ __forceinline__ void red_add4(float* base, long long blk, float4 v) {
-    atomicAdd(reinterpret_cast<float4*>(base) + blk, v);
-}
-
-// J^T v: per voxel the colour part is v_k sum W w_i, the opacity part
-// sum W (v . dH/dsigma_i); the window keeps (sum W w_i, sum W v.dH/dsigma_i).
-struct VjpFlush {
+// VJP sink: slot = (a, s) with a = sum W w_i and s = sum W v.dH/dsigma_i;
+// the parameter block receives (a v_0, a v_1, a v_2, s).
+struct VjpSink {
     float* out;
     float v0, v1, v2;
-    __device__ __forceinline__ void operator()(long long key, const float (&a)[2]) {
-        if (a[0] != 0.0f || a[1] != 0.0f)
+    __device__ __forceinline__ void put(bool ev, int key, const float (&a)[2]) {
+        if (ev && (a[0] != 0.0f || a[1] != 0.0f))
             red_add4(out, key, make_float4(a[0] * v0, a[0] * v1, a[0] * v2, a[1]));
     }
 };
 
-struct VjpSink {
-    Window<2> w;
-    VjpFlush fl;
-    int G;
-    bool started;
-    __device__ __forceinline__ void grid(const Cell& cl, float wi, const float (&ds)[3]) {
-        if (!started) {
-            w.b[0] = cl.bx; w.b[1] = cl.by; w.b[2] = cl.bz;
-#pragma unroll
-            for (int c = 0; c < 8; ++c) win_zero(w, c);
-            started = true;
-        } else {
-            win_goto(w, cl, G, fl);
-        }
-        const float val[2] = {wi, fl.v0 * ds[0] + fl.v1 * ds[1] + fl.v2 * ds[2]};
-        win_add(w, cl, val);
-    }
-    __device__ __forceinline__ void end_grid() {
-        if (!started) return;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) win_flush(w, c, G, fl);
-    }
-    __device__ __forceinline__ void shell(const ShellHit& hs, float wi, const float (&ds)[3]) {
-        const float s = fl.v0 * ds[0] + fl.v1 * ds[1] + fl.v2 * ds[2];
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float W = hs.w[q];
-            if (W != 0.0f)
-                red_add4(fl.out, hs.idx[q],
-                         make_float4(W * wi * fl.v0, W * wi * fl.v1, W * wi * fl.v2, W * s));
-        }
-    }
-};
-
-// diag(J^T J) and J^T r: the window keeps, per voxel, the row entries
-// a = sum W w_i (colour, same for the three residuals) and
-// s_k = sum W dH_k/dsigma_i; at the flush they are squared (diag) and
-// multiplied by r (gradient).
-struct DiagFlush {
+// Diagonal sink: slot = (a, s_0, s_1, s_2), the ray's row entries for the
+// voxel (colour: a for each channel's residual; opacity: s_k for residual k),
+// squared into diag and multiplied by r into the gradient.
+struct DiagSink {
     float* diag;
     float* grad;
     float r0, r1, r2;
-    __device__ __forceinline__ void operator()(long long key, const float (&a)[4]) {
-        if (a[0] == 0.0f && a[1] == 0.0f && a[2] == 0.0f && a[3] == 0.0f) return;
+    __device__ __forceinline__ void put(bool ev, int key, const float (&a)[4]) {
+        if (!(ev && (a[0] != 0.0f || a[1] != 0.0f || a[2] != 0.0f || a[3] != 0.0f))) return;
         const float aa = a[0] * a[0];
         red_add4(diag, key, make_float4(aa, aa, aa, a[1] * a[1] + a[2] * a[2] + a[3] * a[3]));
         if (grad)
@@ -246,78 +212,142 @@ struct DiagFlush {
     }
 };
 
-struct DiagSink {
-    Window<4> w;
-    DiagFlush fl;
-    int G;
-    bool started;
-    __device__ __forceinline__ void grid(const Cell& cl, float wi, const float (&ds)[3]) {
-        if (!started) {
-            w.b[0] = cl.bx; w.b[1] = cl.by; w.b[2] = cl.bz;
+// Move the window (all lanes; `on` = this lane moves) to base nb, handing the
+// voxels that leave it to the sink.  A voxel never re-enters a ray's window:
+// its trilinear support meets the ray in one run of samples.
+template <int NV, class Sink>
+__device__ __forceinline__ void win_move(Window<NV>& w, const int (&nb)[3], bool on, int G, Sink& sk) {
 #pragma unroll
-            for (int c = 0; c < 8; ++c) win_zero(w, c);
-            started = true;
-        } else {
-            win_goto(w, cl, G, fl);
-        }
-        const float val[4] = {wi, ds[0], ds[1], ds[2]};
-        win_add(w, cl, val);
-    }
-    __device__ __forceinline__ void end_grid() {
-        if (!started) return;
+    for (int p = 0; p < 8; ++p) {
+        const int ox = par_coord(w.b[0], p & 1), oy = par_coord(w.b[1], (p >> 1) & 1),
+                  oz = par_coord(w.b[2], p >> 2);
+        const int nx = par_coord(nb[0], p & 1), ny = par_coord(nb[1], (p >> 1) & 1),
+                  nz = par_coord(nb[2], p >> 2);
+        const bool ev = on && (ox != nx || oy != ny || oz != nz);
+        sk.put(ev, vox_key(ox, oy, oz, G), w.v[p]);
+        if (ev) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) win_flush(w, c, G, fl);
-    }
-    __device__ __forceinline__ void shell(const ShellHit& hs, float wi, const float (&ds)[3]) {
-#pragma unroll
-        for (int q = 0; q < 4; ++q) {
-            const float W = hs.w[q];
-            if (W == 0.0f) continue;
-            const float a[4] = {W * wi, W * ds[0], W * ds[1], W * ds[2]};
-            fl(hs.idx[q], a);
+            for (int q = 0; q < NV; ++q) w.v[p][q] = 0.0f;
         }
     }
-};
+    if (on) { w.b[0] = nb[0]; w.b[1] = nb[1]; w.b[2] = nb[2]; }
+}
 
-// Second sweep: per-sample partials (Algorithm 1 quantities) into a sink.
-template <typename T, class Sink>
-__device__ __forceinline__ void scatter_sweep(const DevScene& sc, const T* __restrict__ x,
-                                              const Ray& R, long long ray, const float (&Hh)[3],
-                                              Sink& sink) {
-    float Tr = 1.0f;
-    float P[3] = {0.0f, 0.0f, 0.0f};
-    const float dbar = R.delta * sc.halfG;
-    for (int k = 0; k < R.K; ++k) {
-        const Cell cl = sample_cell(sc, R, ray, k);
-        const float4 a = interp_grid(x, sc, cl);
-        const float e = expf(-__fmul_rn(a.w, dbar));
-        const float w = __fmul_rn(Tr, __fsub_rn(1.0f, e));
-        P[0] = fmaf(w, a.x, P[0]);
-        P[1] = fmaf(w, a.y, P[1]);
-        P[2] = fmaf(w, a.z, P[2]);
-        const float te = Tr * e;
-        const float ds[3] = {dbar * (te * a.x - (Hh[0] - P[0])),
-                             dbar * (te * a.y - (Hh[1] - P[1])),
-                             dbar * (te * a.z - (Hh[2] - P[2]))};
-        sink.grid(cl, w, ds);
-        Tr = __fmul_rn(Tr, e);
+// Add a sample's contribution val (per unit weight) to the 8 window voxels.
+template <int NV>
+__device__ __forceinline__ void win_add(Window<NV>& w, const Cell& cl, const float (&val)[NV]) {
+    // weight of the corner whose parity is p: corner offset = p ^ (base parity)
+    const bool sx = cl.bx & 1, sy = cl.by & 1, sz = cl.bz & 1;
+    const float wx[2] = {sx ? cl.fx : 1.0f - cl.fx, sx ? 1.0f - cl.fx : cl.fx};
+    const float wy[2] = {sy ? cl.fy : 1.0f - cl.fy, sy ? 1.0f - cl.fy : cl.fy};
+    const float wz[2] = {sz ? cl.fz : 1.0f - cl.fz, sz ? 1.0f - cl.fz : cl.fz};
+#pragma unroll
+    for (int p = 0; p < 8; ++p) {
+        const float W = wx[p & 1] * wy[(p >> 1) & 1] * wz[p >> 2];
+#pragma unroll
+        for (int q = 0; q < NV; ++q) w.v[p][q] = fmaf(W, val[q], w.v[p][q]);
     }
-    sink.end_grid();
-    for (int q = 0; q < sc.S; ++q) {
+}
+
+// Back-to-front sweep of Algorithm 1 for the 32 rays of a warp (all lanes
+// call it; `act` marks lanes with a ray to scatter).  V = total optical depth
+// from the first sweep; vv = the ray's weights on its three residuals (VJP:
+// v; diagonal: r).  NV = 2 (VJP) or 4 (diagonal).  The loop over samples is
+// warp-uniform (sample k of every lane in the same iteration), so coherent
+// rays evict a shared voxel in the same instruction.
+template <int NV, typename T, class Sink>
+__device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __restrict__ x,
+                                               const Ray& R, long long ray, bool act, CSum V,
+                                               const float (&vv)[3], Sink& sk) {
+    float G[3] = {0.0f, 0.0f, 0.0f};
+    // shells, outermost first
+    for (int q = sc.S - 1; q >= 0; --q) {
         ShellHit hs;
-        if (!shell_lookup(sc, R, q, hs)) continue;
-        const float4 a = interp_shell(x, hs);
-        const float e = expf(-a.w);
-        const float w = __fmul_rn(Tr, __fsub_rn(1.0f, e));
-        P[0] = fmaf(w, a.x, P[0]);
-        P[1] = fmaf(w, a.y, P[1]);
-        P[2] = fmaf(w, a.z, P[2]);
-        const float te = Tr * e;
-        const float ds[3] = {te * a.x - (Hh[0] - P[0]), te * a.y - (Hh[1] - P[1]),
-                             te * a.z - (Hh[2] - P[2])};
-        sink.shell(hs, w, ds);
-        Tr = __fmul_rn(Tr, e);
+        const bool hit = act && shell_lookup(sc, R, q, hs);
+        float wi = 0.0f, ds[3] = {0.0f, 0.0f, 0.0f};
+        if (hit) {
+            const float4 a = interp_shell(x, hs);
+            const float sd = a.w;
+            csum_add(V, -sd);
+            const float Ti = expf(-fmaxf(V.hi + V.lo, 0.0f));
+            const float e = expf(-sd);
+            wi = Ti * one_minus_exp_neg(sd, e);
+            const float te = Ti * e;
+            ds[0] = te * a.x - G[0];
+            ds[1] = te * a.y - G[1];
+            ds[2] = te * a.z - G[2];
+            G[0] = fmaf(wi, a.x, G[0]);
+            G[1] = fmaf(wi, a.y, G[1]);
+            G[2] = fmaf(wi, a.z, G[2]);
+        }
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float W = hit ? hs.w[c] : 0.0f;
+            float val[NV];
+            val[0] = W * wi;
+            if (NV == 2) {
+                val[1 % NV] = W * (vv[0] * ds[0] + vv[1] * ds[1] + vv[2] * ds[2]);
+            } else {
+                val[1 % NV] = W * ds[0];
+                val[2 % NV] = W * ds[1];
+                val[3 % NV] = W * ds[2];
+            }
+            sk.put(hit, hit ? (int)hs.idx[c] : 0, val);
+        }
     }
+    // grid samples, last to first (warp-uniform loop; lane active while k < K)
+    const int Kl = act ? R.K : 0;
+    const int Kmax = __reduce_max_sync(kFull, Kl);
+    const float dbar = R.delta * sc.halfG;
+    Window<NV> w;
+#pragma unroll
+    for (int c = 0; c < 8; ++c)
+#pragma unroll
+        for (int q = 0; q < NV; ++q) w.v[c][q] = 0.0f;
+    w.b[0] = w.b[1] = w.b[2] = 0;
+    for (int k = Kmax - 1; k >= 0; --k) {
+        const bool on = k < Kl;
+        Cell cl;
+        cl.bx = w.b[0]; cl.by = w.b[1]; cl.bz = w.b[2];
+        cl.fx = cl.fy = cl.fz = 0.0f;
+        if (on) {
+            cl = sample_cell(sc, R, ray, k);
+            if (k == Kl - 1) { w.b[0] = cl.bx; w.b[1] = cl.by; w.b[2] = cl.bz; }
+        }
+        const int nb[3] = {cl.bx, cl.by, cl.bz};
+        win_move(w, nb, on, sc.G, sk);
+        if (on) {
+            const float4 a = interp_grid(x, sc, cl);
+            const float sd = __fmul_rn(a.w, dbar);
+            csum_add(V, -sd);
+            const float Ti = expf(-fmaxf(V.hi + V.lo, 0.0f));
+            const float e = expf(-sd);
+            const float wi = Ti * one_minus_exp_neg(sd, e);
+            const float te = Ti * e;
+            const float ds0 = dbar * (te * a.x - G[0]);
+            const float ds1 = dbar * (te * a.y - G[1]);
+            const float ds2 = dbar * (te * a.z - G[2]);
+            G[0] = fmaf(wi, a.x, G[0]);
+            G[1] = fmaf(wi, a.y, G[1]);
+            G[2] = fmaf(wi, a.z, G[2]);
+            float val[NV];
+            val[0] = wi;
+            if (NV == 2) {
+                val[1 % NV] = vv[0] * ds0 + vv[1] * ds1 + vv[2] * ds2;
+            } else {
+                val[1 % NV] = ds0;
+                val[2 % NV] = ds1;
+                val[3 % NV] = ds2;
+            }
+            win_add(w, cl, val);
+        }
+    }
+    // the remaining window
+#pragma unroll
+    for (int p = 0; p < 8; ++p)
+        sk.put(Kl > 0, vox_key(par_coord(w.b[0], p & 1), par_coord(w.b[1], (p >> 1) & 1),
+                               par_coord(w.b[2], p >> 2), sc.G),
+               w.v[p]);
 }
 
 // ------------------------------------------------------------- kernels
@@ -383,44 +413,37 @@ __global__ void __launch_bounds__(kThreads) k_scatter(DevScene sc, const T* __re
                                                       float* __restrict__ out2, double* pap) {
     double acc = 0.0;
     PERF_TILE_LOOP {
-        long long ray;
-        if (!tile_pixel(sc, tile, lane, ray)) continue;
+        long long ray = 0;
+        bool act = tile_pixel(sc, tile, lane, ray);
         Ray R;
-        ray_setup(sc, ray, R);
-        float Hh[3], vr[3];
-        if (MODE == 1) {
-            Tang s;
-            tangent(sc, x, p, R, ray, s);
-            Hh[0] = s.H[0]; Hh[1] = s.H[1]; Hh[2] = s.H[2];
-            vr[0] = s.J[0]; vr[1] = s.J[1]; vr[2] = s.J[2];
-            acc += (double)vr[0] * vr[0] + (double)vr[1] * vr[1] + (double)vr[2] * vr[2];
-        } else {
-            if (MODE == 0) {
-                vr[0] = v[3 * ray]; vr[1] = v[3 * ray + 1]; vr[2] = v[3 * ray + 2];
-                if (vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f) continue;
+        R.K = 0;
+        R.shell_hit = 0u;
+        R.delta = 0.0f;
+        float vr[3] = {0.0f, 0.0f, 0.0f};
+        CSum V = {0.0f, 0.0f};
+        if (act) {
+            ray_setup(sc, ray, R);
+            if (MODE == 1) {
+                Tang s;
+                tangent(sc, x, p, R, ray, s);
+                vr[0] = s.J[0]; vr[1] = s.J[1]; vr[2] = s.J[2];
+                acc += (double)vr[0] * vr[0] + (double)vr[1] * vr[1] + (double)vr[2] * vr[2];
+                V = s.V;
             } else {
-                vr[0] = v ? v[3 * ray] : 0.0f;
-                vr[1] = v ? v[3 * ray + 1] : 0.0f;
-                vr[2] = v ? v[3 * ray + 2] : 0.0f;
+                if (MODE == 0 || v != nullptr) {
+                    vr[0] = v[3 * ray]; vr[1] = v[3 * ray + 1]; vr[2] = v[3 * ray + 2];
+                }
+                if (MODE == 2 || vr[0] != 0.0f || vr[1] != 0.0f || vr[2] != 0.0f)
+                    V = optical_depth(sc, x, R, ray);
             }
-            Comp s;
-            float Te;
-            composite(sc, x, R, ray, s, Te);
-            Hh[0] = s.H[0]; Hh[1] = s.H[1]; Hh[2] = s.H[2];
+            if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f) act = false;
         }
         if (MODE == 2) {
-            DiagSink sink;
-            sink.fl.diag = out; sink.fl.grad = out2;
-            sink.fl.r0 = vr[0]; sink.fl.r1 = vr[1]; sink.fl.r2 = vr[2];
-            sink.G = sc.G; sink.started = false;
-            scatter_sweep(sc, x, R, ray, Hh, sink);
+            DiagSink sk{out, out2, vr[0], vr[1], vr[2]};
+            backward_sweep<4>(sc, x, R, ray, act, V, vr, sk);
         } else {
-            if (vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f) continue;
-            VjpSink sink;
-            sink.fl.out = out;
-            sink.fl.v0 = vr[0]; sink.fl.v1 = vr[1]; sink.fl.v2 = vr[2];
-            sink.G = sc.G; sink.started = false;
-            scatter_sweep(sc, x, R, ray, Hh, sink);
+            VjpSink sk{out, vr[0], vr[1], vr[2]};
+            backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
         }
     }
     if (MODE == 1 && pap) block_add_f64<kWarps>(acc, pap);

@@ -3,14 +3,19 @@
 // and written as few times as the recurrence allows (Section "Update step":
 // the vector additions and inner products run in parallel on the GPU).
 //
-// Vectors are float32, handled one parameter block (4 values = one voxel or
-// texel) per thread as float4; inner products accumulate in FP64.
+// The CG recurrence vectors Delta, rho and p are FP64 (the vector kernels are
+// a few hundred MB of traffic per iteration against a ray march of tens of
+// ms, and FP32 recurrences lose conjugacy within 20 iterations on these
+// ill-conditioned normal equations); A p arrives in FP32 from the ray-march
+// scatter, and p is also written as FP32 (and BF16) for the next march's
+// gathers.  One thread handles one parameter block (4 values = one voxel or
+// texel); inner products accumulate in FP64.
 //   begin : rho = b = -grad, z = M^-1 rho, p = z, Delta = 0, R0, rho^T z
 //   update: Delta += alpha p, rho -= alpha A p, z = M^-1 rho, R, rho^T z
 //   finish: exit test (R < eps^2 R0 or R / R_prev > stall, or a fixed count),
 //           beta = rho'^T z' / rho^T z                               [1 thread]
 //   dir   : p = z + beta p, A p = 0 for the next scatter
-// M^-1 is Jacobi (z_j = rho_j / d_j, 0 where d_j = 0) or, where 4x4 blocks
+// M^-1 is Jacobi (z_j = rho_j / d_j, 0 where d_j <= 1e-30) or, where 4x4 blocks
 // are given for the grid voxels, z_v = P_v rho_v per voxel.
 #include <cuda_bf16.h>
 #include "perf_kernels.h"
@@ -35,22 +40,43 @@ static int vec_blocks(long long nblk) {
     return (int)(b > 0 ? b : 1);
 }
 
-__device__ __forceinline__ float4 precond(float4 r, long long v, const float4* __restrict__ d4,
-                                          const float4* __restrict__ B, long long n_block) {
-    if (B != nullptr && v < n_block) {
-        const float4 b0 = B[4 * v], b1 = B[4 * v + 1], b2 = B[4 * v + 2], b3 = B[4 * v + 3];
-        return make_float4(b0.x * r.x + b0.y * r.y + b0.z * r.z + b0.w * r.w,
-                           b1.x * r.x + b1.y * r.y + b1.z * r.z + b1.w * r.w,
-                           b2.x * r.x + b2.y * r.y + b2.z * r.z + b2.w * r.w,
-                           b3.x * r.x + b3.y * r.y + b3.z * r.z + b3.w * r.w);
-    }
-    const float4 d = d4[v];
-    return make_float4(d.x > 0.0f ? r.x / d.x : 0.0f, d.y > 0.0f ? r.y / d.y : 0.0f,
-                       d.z > 0.0f ? r.z / d.z : 0.0f, d.w > 0.0f ? r.w / d.w : 0.0f);
+// Jacobi entries at or below this are treated as unobserved (z = 0): the
+// square of a row entry below ~1e-19 is not a normal binary32 number, so such
+// parameters (deep behind opaque matter) cannot be told apart from ones no ray
+// sees; 1e-30 keeps full binary32 precision above the cut.
+constexpr float kJacobiFloor = 1e-30f;
+
+struct D4 {
+    double x, y, z, w;
+};
+
+__device__ __forceinline__ D4 ld4(const double* a, long long v) {
+    const double2 lo = reinterpret_cast<const double2*>(a)[2 * v];
+    const double2 hi = reinterpret_cast<const double2*>(a)[2 * v + 1];
+    return D4{lo.x, lo.y, hi.x, hi.y};
 }
 
-__device__ __forceinline__ double dot4(float4 a, float4 b) {
-    return (double)a.x * b.x + (double)a.y * b.y + (double)a.z * b.z + (double)a.w * b.w;
+__device__ __forceinline__ void st4(double* a, long long v, const D4& d) {
+    reinterpret_cast<double2*>(a)[2 * v] = make_double2(d.x, d.y);
+    reinterpret_cast<double2*>(a)[2 * v + 1] = make_double2(d.z, d.w);
+}
+
+__device__ __forceinline__ D4 precond(const D4& r, long long v, const float4* __restrict__ d4,
+                                      const float4* __restrict__ B, long long n_block) {
+    if (B != nullptr && v < n_block) {
+        const float4 b0 = B[4 * v], b1 = B[4 * v + 1], b2 = B[4 * v + 2], b3 = B[4 * v + 3];
+        return D4{b0.x * r.x + b0.y * r.y + b0.z * r.z + b0.w * r.w,
+                  b1.x * r.x + b1.y * r.y + b1.z * r.z + b1.w * r.w,
+                  b2.x * r.x + b2.y * r.y + b2.z * r.z + b2.w * r.w,
+                  b3.x * r.x + b3.y * r.y + b3.z * r.z + b3.w * r.w};
+    }
+    const float4 d = d4[v];
+    return D4{d.x > kJacobiFloor ? r.x / d.x : 0.0, d.y > kJacobiFloor ? r.y / d.y : 0.0,
+              d.z > kJacobiFloor ? r.z / d.z : 0.0, d.w > kJacobiFloor ? r.w / d.w : 0.0};
+}
+
+__device__ __forceinline__ double dot4(const D4& a, const D4& b) {
+    return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
 }
 
 __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* y, long long v, float4 a) {
@@ -62,23 +88,29 @@ __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* y, long long v, floa
     reinterpret_cast<uint2*>(y)[v] = u;
 }
 
+__device__ __forceinline__ void store_p(float4* p32, __nv_bfloat16* p16, long long v, const D4& p) {
+    const float4 f = make_float4((float)p.x, (float)p.y, (float)p.z, (float)p.w);
+    p32[v] = f;
+    if (p16) store_bf16x4(p16, v, f);
+}
+
 __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const float4* __restrict__ g,
                                                         const float4* __restrict__ d4,
                                                         const float4* __restrict__ B, long long n_block,
-                                                        float4* delta, float4* rho, float4* p,
-                                                        __nv_bfloat16* p16, float4* Ap,
+                                                        double* delta, double* rho, double* p,
+                                                        float4* p32, __nv_bfloat16* p16, float4* Ap,
                                                         PcgScalars* s) {
     double aR = 0.0, aRz = 0.0;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
          v += (long long)gridDim.x * blockDim.x) {
         const float4 gg = g[v];
-        const float4 r = make_float4(-gg.x, -gg.y, -gg.z, -gg.w);
-        const float4 z = precond(r, v, d4, B, n_block);
-        rho[v] = r;
-        p[v] = z;
-        if (p16) store_bf16x4(p16, v, z);
-        delta[v] = zero;
+        const D4 r{-(double)gg.x, -(double)gg.y, -(double)gg.z, -(double)gg.w};
+        const D4 z = precond(r, v, d4, B, n_block);
+        st4(rho, v, r);
+        st4(p, v, z);
+        store_p(p32, p16, v, z);
+        st4(delta, v, D4{0.0, 0.0, 0.0, 0.0});
         Ap[v] = zero;
         aR += dot4(r, r);
         aRz += dot4(r, z);
@@ -111,8 +143,8 @@ __global__ void k_pcg_begin_fin(PcgScalars* s, int max_iter, int fixed, double e
     }
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, float4* delta, float4* rho,
-                                                         const float4* __restrict__ p,
+__global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, double* delta, double* rho,
+                                                         const double* __restrict__ p,
                                                          const float4* __restrict__ Ap,
                                                          const float4* __restrict__ d4,
                                                          const float4* __restrict__ B,
@@ -120,19 +152,20 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, float4* 
     if (s->done) return;
     const double pAp = s->pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) return;
-    const float alpha = (float)(s->rz / pAp);
+    const double alpha = s->rz / pAp;
     double aR = 0.0, aRz = 0.0;
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
          v += (long long)gridDim.x * blockDim.x) {
-        const float4 pv = p[v], av = Ap[v];
-        float4 dv = delta[v], r = rho[v];
-        dv.x = fmaf(alpha, pv.x, dv.x); dv.y = fmaf(alpha, pv.y, dv.y);
-        dv.z = fmaf(alpha, pv.z, dv.z); dv.w = fmaf(alpha, pv.w, dv.w);
-        r.x = fmaf(-alpha, av.x, r.x); r.y = fmaf(-alpha, av.y, r.y);
-        r.z = fmaf(-alpha, av.z, r.z); r.w = fmaf(-alpha, av.w, r.w);
-        delta[v] = dv;
-        rho[v] = r;
-        const float4 z = precond(r, v, d4, B, n_block);
+        const D4 pv = ld4(p, v);
+        const float4 av = Ap[v];
+        D4 dv = ld4(delta, v), r = ld4(rho, v);
+        dv.x = fma(alpha, pv.x, dv.x); dv.y = fma(alpha, pv.y, dv.y);
+        dv.z = fma(alpha, pv.z, dv.z); dv.w = fma(alpha, pv.w, dv.w);
+        r.x = fma(-alpha, (double)av.x, r.x); r.y = fma(-alpha, (double)av.y, r.y);
+        r.z = fma(-alpha, (double)av.z, r.z); r.w = fma(-alpha, (double)av.w, r.w);
+        st4(delta, v, dv);
+        st4(rho, v, r);
+        const D4 z = precond(r, v, d4, B, n_block);
         aR += dot4(r, r);
         aRz += dot4(r, z);
     }
@@ -171,35 +204,38 @@ __global__ void k_pcg_finish(PcgScalars* s) {
     s->pAp = 0.0;
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const float4* __restrict__ rho,
+__global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const double* __restrict__ rho,
                                                       const float4* __restrict__ d4,
                                                       const float4* __restrict__ B, long long n_block,
-                                                      float4* p, __nv_bfloat16* p16, float4* Ap,
-                                                      const PcgScalars* s) {
+                                                      double* p, float4* p32, __nv_bfloat16* p16,
+                                                      float4* Ap, const PcgScalars* s) {
     if (s->done) return;
-    const float beta = (float)s->beta;
+    const double beta = s->beta;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
          v += (long long)gridDim.x * blockDim.x) {
-        const float4 z = precond(rho[v], v, d4, B, n_block);
-        float4 pv = p[v];
-        pv.x = fmaf(beta, pv.x, z.x); pv.y = fmaf(beta, pv.y, z.y);
-        pv.z = fmaf(beta, pv.z, z.z); pv.w = fmaf(beta, pv.w, z.w);
-        p[v] = pv;
-        if (p16) store_bf16x4(p16, v, pv);
+        const D4 z = precond(ld4(rho, v), v, d4, B, n_block);
+        D4 pv = ld4(p, v);
+        pv.x = fma(beta, pv.x, z.x); pv.y = fma(beta, pv.y, z.y);
+        pv.z = fma(beta, pv.z, z.z); pv.w = fma(beta, pv.w, z.w);
+        st4(p, v, pv);
+        store_p(p32, p16, v, pv);
         Ap[v] = zero;
     }
 }
 
-__global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4* __restrict__ x,
-                                                    const float4* __restrict__ delta, float gamma,
+// x_out = P(x + gamma Delta): the trial point is formed in FP64 and rounded
+// once to the storage type(s).
+__global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4* x,
+                                                    const double* __restrict__ delta, double gamma,
                                                     int project, float4* x_out,
                                                     __nv_bfloat16* x16) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
          v += (long long)gridDim.x * blockDim.x) {
-        const float4 a = x[v], d = delta[v];
-        float4 y = make_float4(fmaf(gamma, d.x, a.x), fmaf(gamma, d.y, a.y),
-                               fmaf(gamma, d.z, a.z), fmaf(gamma, d.w, a.w));
+        const float4 a = x[v];
+        const D4 d = ld4(delta, v);
+        float4 y = make_float4((float)fma(gamma, d.x, (double)a.x), (float)fma(gamma, d.y, (double)a.y),
+                               (float)fma(gamma, d.z, (double)a.z), (float)fma(gamma, d.w, (double)a.w));
         if (project) {
             y.x = fminf(fmaxf(y.x, 0.0f), 1.0f);
             y.y = fminf(fmaxf(y.y, 0.0f), 1.0f);
@@ -218,35 +254,43 @@ __global__ void __launch_bounds__(kVThreads) k_to_bf16(long long nb, const float
         store_bf16x4(y, v, x[v]);
 }
 
+__global__ void __launch_bounds__(kVThreads) k_to_f32(long long n, const double* __restrict__ a,
+                                                     float* b) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
 // ------------------------------------------------------------- launchers
 
 #define F4(p) reinterpret_cast<float4*>(p)
 #define CF4(p) reinterpret_cast<const float4*>(p)
 
-cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, float* delta,
-                             float* rho, float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
-                             int max_iter, int fixed, double eps_rel, double stall,
+cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
+                             double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
+                             PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st) {
     const long long nb = n / 4;
     cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars), st);
     if (e != cudaSuccess) return e;
     if (nb > 0)
         k_pcg_begin<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(grad), CF4(diag), CF4(blocks),
-                                                          n_block, F4(delta), F4(rho), F4(p), p16,
+                                                          n_block, delta, rho, p, F4(p32), p16,
                                                           F4(Ap), s);
     k_pcg_begin_fin<<<1, 1, 0, st>>>(s, max_iter, fixed, eps_rel, stall);
     count_launch(nb > 0 ? 2 : 1);
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_update(long long n, float* delta, float* rho, const float* p,
+cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
                               const float* Ap, const float* diag, const float* blocks,
                               long long n_block, PcgScalars* s, cudaStream_t st) {
     const long long nb = n / 4;
-    if (nb > 0)
-        k_pcg_update<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, F4(delta), F4(rho), CF4(p), CF4(Ap),
-                                                           CF4(diag), CF4(blocks), n_block, s);
-    if (nb > 0) count_launch();
+    if (nb > 0) {
+        k_pcg_update<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, delta, rho, p, CF4(Ap), CF4(diag),
+                                                           CF4(blocks), n_block, s);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -256,24 +300,26 @@ cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_dir(long long n, const float* rho, const float* diag, const float* blocks,
-                           long long n_block, float* p, __nv_bfloat16* p16, float* Ap,
+cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
+                           long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                            PcgScalars* s, cudaStream_t st) {
     const long long nb = n / 4;
-    if (nb > 0)
-        k_pcg_dir<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(rho), CF4(diag), CF4(blocks),
-                                                        n_block, F4(p), p16, F4(Ap), s);
-    if (nb > 0) count_launch();
+    if (nb > 0) {
+        k_pcg_dir<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, rho, CF4(diag), CF4(blocks), n_block, p,
+                                                        F4(p32), p16, F4(Ap), s);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_trial(long long n, const float* x, const float* delta, float gamma, int project,
-                         float* x_out, __nv_bfloat16* x16_out, cudaStream_t st) {
+cudaError_t launch_trial(long long n, const float* x, const double* delta, double gamma,
+                         int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st) {
     const long long nb = n / 4;
-    if (nb > 0)
-        k_trial<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), CF4(delta), gamma, project,
-                                                      F4(x_out), x16_out);
-    if (nb > 0) count_launch();
+    if (nb > 0) {
+        k_trial<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), delta, gamma, project, F4(x_out),
+                                                      x16_out);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -281,6 +327,14 @@ cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaSt
     const long long nb = n / 4;
     if (nb > 0) {
         k_to_bf16<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), y);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t st) {
+    if (n > 0) {
+        k_to_f32<<<vec_blocks((n + 3) / 4), kVThreads, 0, st>>>(n, a, b);
         count_launch();
     }
     return cudaGetLastError();

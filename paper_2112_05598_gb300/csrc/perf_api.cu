@@ -32,9 +32,10 @@ struct perf_ctx {
     float* r = nullptr;
     float* diag = nullptr;
     float* grad = nullptr;
-    float* delta = nullptr;
-    float* rho = nullptr;
-    float* p = nullptr;
+    double* delta = nullptr;
+    double* rho = nullptr;
+    double* p = nullptr;
+    float* p32 = nullptr;
     float* Ap = nullptr;
     float* x_trial = nullptr;
     __nv_bfloat16* x16 = nullptr;
@@ -99,6 +100,7 @@ perf_status ensure_pcg(perf_ctx* ctx) {
     CK(alloc(&ctx->delta, ctx->n));
     CK(alloc(&ctx->rho, ctx->n));
     CK(alloc(&ctx->p, ctx->n));
+    CK(alloc(&ctx->p32, ctx->n));
     CK(alloc(&ctx->Ap, ctx->n));
     if (ctx->scene.dtype == PERF_BF16) CK(alloc(&ctx->p16, ctx->n));
     return PERF_OK;
@@ -166,7 +168,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
     if (!sc || !cams || !opts) return PERF_ERR_INVALID_ARG;
     std::string why;
     if (check_options(opts, why) != PERF_OK) return PERF_ERR_INVALID_ARG;
-    if (sc->grid_res < 2 || sc->grid_res > 2048) return PERF_ERR_INVALID_ARG;
+    if (sc->grid_res < 2 || sc->grid_res > 1024) return PERF_ERR_INVALID_ARG;
     if (sc->n_shells < 0 || sc->n_shells > PERF_MAX_SHELLS) return PERF_ERR_INVALID_ARG;
     if (sc->dtype != PERF_F32 && sc->dtype != PERF_BF16) return PERF_ERR_INVALID_ARG;
     if (sc->n_shells > 0 && (sc->env_h < 2 || sc->env_w < 2)) return PERF_ERR_INVALID_ARG;
@@ -188,6 +190,10 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
     const long long G = sc->grid_res;
     const long long texels = (long long)ctx->scene.env_h * ctx->scene.env_w;
     ctx->n = 4 * (G * G * G + (long long)sc->n_shells * texels);
+    if (ctx->n / 4 >= (1ll << 31)) {   // parameter blocks are indexed with int
+        delete ctx;
+        return PERF_ERR_INVALID_ARG;
+    }
     ctx->n_rays = (long long)cams->n_cams * cams->width * cams->height;
     cudaGetDevice(&ctx->device);
 
@@ -244,7 +250,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->Ap, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->p32, ctx->Ap, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -352,8 +358,8 @@ perf_status perf_pcg_begin(perf_ctx* ctx, const float* grad, const float* diag, 
         CK(cudaMemcpyAsync(ctx->diag, diag, sizeof(float) * (size_t)ctx->n,
                            cudaMemcpyDeviceToDevice, S(stream)));
     const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
-    CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p, ctx->p16,
-                              ctx->Ap, ctx->s, ctx->opts.pcg_iters, ctx->opts.pcg_fixed,
+    CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p, ctx->p32,
+                              ctx->p16, ctx->Ap, ctx->s, ctx->opts.pcg_iters, ctx->opts.pcg_fixed,
                               ctx->opts.pcg_eps_rel, ctx->opts.pcg_stall, B, ctx->n_block,
                               S(stream)));
     return PERF_OK;
@@ -369,7 +375,7 @@ namespace {
 perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, cudaStream_t st) {
     const bool bf = ctx->scene.dtype == PERF_BF16;
     const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
-    const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p);
+    const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p32);
     t_begin(ctx, PERF_T_APPLY, st);
     CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32, nullptr,
                             ctx->Ap, nullptr, &ctx->s->pAp, st));
@@ -378,8 +384,8 @@ perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, cudaStream
     CK(perf::launch_pcg_update(ctx->n, ctx->delta, ctx->rho, ctx->p, ctx->Ap, diag, B, ctx->n_block,
                                ctx->s, st));
     CK(perf::launch_pcg_finish(ctx->s, st));
-    CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p16, ctx->Ap,
-                            ctx->s, st));
+    CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p32, ctx->p16,
+                            ctx->Ap, ctx->s, st));
     t_end(ctx, PERF_T_VECTOR, st);
     return PERF_OK;
 }
@@ -406,9 +412,7 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
 perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out, perf_pcg_info* info, void* stream) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (!ctx->delta || !ctx->s) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_result before pcg_begin");
-    if (delta_out)
-        CK(cudaMemcpyAsync(delta_out, ctx->delta, sizeof(float) * (size_t)ctx->n,
-                           cudaMemcpyDeviceToDevice, S(stream)));
+    if (delta_out) CK(perf::launch_to_f32(ctx->n, ctx->delta, delta_out, S(stream)));
     if (info) {
         PcgScalars h;
         CK(cudaMemcpyAsync(&h, ctx->s, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
@@ -465,7 +469,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const float* target, int32_t 
         t_end(ctx, PERF_T_DIAG, st);
         const float* B = o.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
         CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
-                                  ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
+                                  ctx->p32, ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
                                   o.pcg_eps_rel, o.pcg_stall, B, ctx->n_block, st));
         for (int k = 0; k < o.pcg_iters; ++k) {
             ps = pcg_iter(ctx, xm, ctx->diag, st);
@@ -485,7 +489,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const float* target, int32_t 
         int evals = 0;
         bool found = false;
         for (int it = 0; it <= o.ls_max; ++it) {
-            CK(perf::launch_trial(ctx->n, x, ctx->delta, (float)gamma, o.project, ctx->x_trial,
+            CK(perf::launch_trial(ctx->n, x, ctx->delta, gamma, o.project, ctx->x_trial,
                                   bf ? ctx->t16 : nullptr, st));
             CK(cudaMemsetAsync(ctx->dF, 0, sizeof(double), st));
             t_begin(ctx, PERF_T_FORWARD, st);
@@ -512,7 +516,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const float* target, int32_t 
         if (!found) { g_star = gamma / o.ls_alpha; mu_star = mu_prev; }
         const bool accept = std::isfinite(mu_star) && mu_star < F0;
         if (accept) {
-            CK(perf::launch_trial(ctx->n, x, ctx->delta, (float)g_star, o.project, ctx->x_trial,
+            CK(perf::launch_trial(ctx->n, x, ctx->delta, g_star, o.project, ctx->x_trial,
                                   nullptr, st));
             CK(cudaMemcpyAsync(x, ctx->x_trial, sizeof(float) * (size_t)ctx->n,
                                cudaMemcpyDeviceToDevice, st));

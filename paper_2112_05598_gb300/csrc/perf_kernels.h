@@ -43,23 +43,25 @@ cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* 
                            int p_dtype, const float* v, float* out, float* out2, double* pap,
                            cudaStream_t st);
 
-// Algorithm 2 vector work (k_pcg.cu).
-cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, float* delta,
-                             float* rho, float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
-                             int max_iter, int fixed, double eps_rel, double stall,
+// Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP64; p32 / p16: the
+// FP32 / BF16 copies of p that the ray march gathers; Ap: FP32 scatter target.
+cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
+                             double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
+                             PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st);
-cudaError_t launch_pcg_update(long long n, float* delta, float* rho, const float* p,
+cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
                               const float* Ap, const float* diag, const float* blocks,
                               long long n_block, PcgScalars* s, cudaStream_t st);
-cudaError_t launch_pcg_dir(long long n, const float* rho, const float* diag, const float* blocks,
-                           long long n_block, float* p, __nv_bfloat16* p16, float* Ap,
-                           PcgScalars* s, cudaStream_t st);
 // One thread: the exit test of Algorithm 2 and beta (after launch_pcg_update).
 cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st);
-// x_out = P(x + gamma delta) (project: sigma >= 0, 0 <= c <= 1); optional
-// float32 and bf16 outputs.
-cudaError_t launch_trial(long long n, const float* x, const float* delta, float gamma, int project,
-                         float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
+cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
+                           long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
+                           PcgScalars* s, cudaStream_t st);
+// x_out = P(x + gamma delta) (project: sigma >= 0, 0 <= c <= 1), formed in FP64;
+// optional float32 and bf16 outputs.
+cudaError_t launch_trial(long long n, const float* x, const double* delta, double gamma,
+                         int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
 cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaStream_t st);
+cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t st);
 
 }  // namespace perf

@@ -25,8 +25,8 @@ def _declared():
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_2112_05598_gb300 import build as b
-    b.build()
+    import __graft_entry__
+    __graft_entry__.build()
     from paper_2112_05598_gb300 import _binding
     return _binding.load_library()
 
