@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-cams", type=int, default=1)
+    ap.add_argument("--cpu-cams", type=int, default=16)
     return ap.parse_args()
 
 
