@@ -208,6 +208,29 @@ uint64_t perf_launch_count(void);
 perf_status perf_sample_count(perf_ctx* ctx, uint64_t* out, void* stream);
 perf_status perf_get_timing(perf_ctx* ctx, perf_timing* out, int32_t reset);
 
+/* Residual and objective without a context and without any device
+ * allocation -- the paper has no counterpart; this serves callers that cannot
+ * allocate device memory when they need a residual (a device-memory budget
+ * fixed at start-up, a host engine whose own pool allocator owns all device
+ * memory, a latency-critical loop that must avoid cudaMalloc / cudaFree).
+ * Same result as perf_create + perf_residual with the same arguments:
+ * r_out[3 N_r] (may be NULL) = H^ - C and *F_out (device double, overwritten)
+ * = 1/2 sum r^2.  scene, cams (HOST arrays) and opts are validated as in
+ * perf_create; at most PERF_NOALLOC_MAX_CAMS cameras (more returns
+ * PERF_ERR_INVALID_ARG).  The camera table is staged in one file-scope device
+ * array of PERF_NOALLOC_MAX_CAMS x 64 bytes (256 KiB), held by every GPU that
+ * loads the library until the process exits, and shared by every call:
+ * calls that overlap on the GPU race on it, so serialise them (one stream,
+ * or events).  The first call on a device looks up that array's device
+ * address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture.  Not thread-safe: one host thread at a time.
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+#define PERF_NOALLOC_MAX_CAMS 4096
+perf_status perf_residual_noalloc(const perf_scene* scene, const perf_cameras* cams,
+                                  const perf_options* opts, const void* x,
+                                  const float* target, float* r_out, double* F_out,
+                                  void* stream);
+
 #ifdef __cplusplus
 }
 #endif

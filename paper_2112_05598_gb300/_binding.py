@@ -92,6 +92,8 @@ _SIGS = {
 }
 _OPTIONAL_SIGS = {
     "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
+    "perf_residual_noalloc": [ctypes.POINTER(Scene), ctypes.POINTER(Cameras),
+                              ctypes.POINTER(Options), _VP, _VP, _VP, _VP, _VP],
 }
 
 _lib = None
@@ -126,6 +128,34 @@ def load_library(path: Optional[str] = None):
     if path is None:
         _lib = lib
     return lib
+
+
+def residual_noalloc(G, radii, env_h, env_w, c2w, focal, width, height, x, target, r_out,
+                     F_out, dtype=PERF_F32, options: Optional[Options] = None, stream=None):
+    """perf_residual_noalloc: the residual / objective march with no context and
+    no device allocation (for callers that cannot allocate device memory)."""
+    lib = load_library()
+    sc = Scene()
+    sc.grid_res = int(G)
+    radii = [float(r) for r in radii]
+    sc.n_shells = len(radii)
+    for i, r in enumerate(radii):
+        sc.shell_radii[i] = r
+    sc.env_h, sc.env_w = int(env_h), int(env_w)
+    sc.dtype = int(dtype)
+    c2w = np.ascontiguousarray(c2w, dtype=np.float32).reshape(-1, 12)
+    focal = np.ascontiguousarray(focal, dtype=np.float32).reshape(-1)
+    cams = Cameras()
+    cams.n_cams = int(c2w.shape[0])
+    cams.width, cams.height = int(width), int(height)
+    cams.c2w = c2w.ctypes.data_as(ctypes.c_void_p)
+    cams.focal = focal.ctypes.data_as(ctypes.c_void_p)
+    o = options if options is not None else default_options()
+    st = lib.perf_residual_noalloc(ctypes.byref(sc), ctypes.byref(cams), ctypes.byref(o),
+                                   _ptr(x), _ptr(target), _ptr(r_out), _ptr(F_out),
+                                   _stream(stream))
+    if st != 0:
+        raise PerfError(st, "perf_residual_noalloc rejected its arguments or failed")
 
 
 def launch_count() -> int:
