@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
+    ap.add_argument("--cams", type=int, default=None, help="first N cameras only (profiling)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cams", type=int, default=16)
@@ -211,14 +213,19 @@ def run_ours(args, rank, world, local):
     from paper_2112_05598_gb300._binding import launch_count
     from scenegen import make_scene
 
-    sc = make_scene(args.workload)
+    from paper_2112_05598_gb300 import PERF_BF16, PERF_F32
+    sc = make_scene(args.workload, n_cams=args.cams)
     cfg = sc.cfg
     dev = torch.device("cuda", local)
-    ctx = Context.from_scene(sc, pcg_iters=cfg.pcg_iters, pcg_fixed=1)
+    bf = args.dtype == "bf16"
+    sdt = torch.bfloat16 if bf else torch.float32
+    ctx = Context.from_scene(sc, dtype=PERF_BF16 if bf else PERF_F32, pcg_iters=cfg.pcg_iters,
+                             pcg_fixed=1)
     stream = torch.cuda.current_stream()
-    x_gt = torch.from_numpy(sc.x_gt).to(dev)
+    x_gt = torch.from_numpy(sc.x_gt).to(dev).to(sdt)
     target = torch.empty(3 * ctx.n_rays, device=dev)
     ctx.render(x_gt, target)
+    target = target.to(sdt)
     del x_gt
     samples = ctx.sample_count()
     x = torch.from_numpy(sc.x0.copy()).to(dev)
@@ -286,9 +293,11 @@ def run_ours(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "bf16" if bf else "f32",
         "data": "synthetic (seeded voxelised primitives, targets rendered from ground truth)",
-        "config": {"workload": _workload_desc(sc), "n_params": sc.n_params, "n_rays": sc.n_rays,
+        "config": {"workload": _workload_desc(sc) + (" (BF16 storage form)" if bf else ""),
+                   "n_params": sc.n_params, "n_rays": sc.n_rays,
                    "samples_per_march": samples,
                    "l2": "inputs larger than L2: targets and residuals 768 MB each per step"},
         "gpu_launches": int(launches),
@@ -299,15 +308,16 @@ def run_ours(args, rank, world, local):
         "apply_ms_per_launch": apply_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": "k_scatter<float,float,1> (A p)",
+                     "kernel": ("k_scatter<bf16,bf16,1> (A p)" if bf else
+                                "k_scatter<float,float,1> (A p)"),
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
                                     f"(max SM clock, {peak_src})"},
         "e2e": {"value": e2e_value, "unit": METRIC,
-                "h2d_bytes_per_step": int(4 * (sc.n_params + 3 * sc.n_rays)),
+                "h2d_bytes_per_step": int(4 * sc.n_params + (2 if bf else 4) * 3 * sc.n_rays),
                 "d2h_bytes_per_step": int(4 * sc.n_params)},
         "clocks": clk,
     }
-    if not args.no_cpu_baseline and world == 1:
+    if not args.no_cpu_baseline and world == 1 and args.cams is None:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_cams, cfg.pcg_iters)
     print(json.dumps(line), flush=True)
 

@@ -18,8 +18,10 @@
  *           an opacity per voxel side.  Storage is float32, or bfloat16 when
  *           the scene's dtype is PERF_BF16 (per-call entry points only).
  *   rays    N_r = n_cams * height * width, ray = (cam * height + row) * width
- *           + col; a residual / image / J p vector has 3 N_r floats indexed
- *           ray * 3 + channel.
+ *           + col; a residual / image / J p vector has 3 N_r values indexed
+ *           ray * 3 + channel.  Images and J p are float32; targets and
+ *           residuals (the per-ray intermediates of a step) are float32, or
+ *           bfloat16 when the scene's dtype is PERF_BF16.
  * Pointers are DEVICE pointers unless a comment says HOST.  The caller owns
  * every buffer it passes in; the context owns only its workspace (PCG
  * vectors, residual buffer, FP64 scalars) and frees it in perf_destroy.
@@ -149,8 +151,8 @@ perf_status perf_render(perf_ctx* ctx, const void* x, float* rgb_out,
 
 /* Eq. 5-6: r_out[3 N_r] = H^ - C (may be NULL), *F_out (device double,
  * overwritten) = 1/2 sum r^2 accumulated in FP64. */
-perf_status perf_residual(perf_ctx* ctx, const void* x, const float* target,
-                          float* r_out, double* F_out, void* stream);
+perf_status perf_residual(perf_ctx* ctx, const void* x, const void* target,
+                          void* r_out, double* F_out, void* stream);
 
 /* jp_out[3 N_r] = J p: the directional derivative of every ray along p, the
  * per-sample partials of Algorithm 1 chained through the interpolation. */
@@ -165,7 +167,7 @@ perf_status perf_vjp(perf_ctx* ctx, const void* x, const float* v, float* out,
 /* Section "Preconditioner": diag_out[n] = diag(J^T J) (each row's entry for a
  * parameter is summed over all samples of that ray before squaring);
  * grad_out[n] = J^T r when r[3 N_r] and grad_out are given (both or neither). */
-perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const float* r,
+perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const void* r,
                           float* diag_out, float* grad_out, void* stream);
 
 /* A p = J^T (J p) = sum_i grad r_i (grad r_i^T p) without forming J
@@ -194,7 +196,7 @@ perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out,
  * F(P(x + gamma Delta)), accept only if F falls.  stats (HOST, may be NULL)
  * receives n_steps records.  Synchronises (the line search reads one FP64
  * scalar per trial step). */
-perf_status perf_gn_solve(perf_ctx* ctx, float* x_inout, const float* target,
+perf_status perf_gn_solve(perf_ctx* ctx, float* x_inout, const void* target,
                           int32_t n_steps, perf_gn_stats* stats, void* stream);
 
 /* Kernel timing (instrumentation, off by default).  perf_get_timing
@@ -228,7 +230,7 @@ perf_status perf_get_timing(perf_ctx* ctx, perf_timing* out, int32_t reset);
 #define PERF_NOALLOC_MAX_CAMS 4096
 perf_status perf_residual_noalloc(const perf_scene* scene, const perf_cameras* cams,
                                   const perf_options* opts, const void* x,
-                                  const float* target, float* r_out, double* F_out,
+                                  const void* target, void* r_out, double* F_out,
                                   void* stream);
 
 #ifdef __cplusplus

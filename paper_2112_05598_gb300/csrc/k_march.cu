@@ -42,6 +42,12 @@ constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ helpers
 
+// Per-ray intermediates (targets, residuals) are stored in the scene's type.
+__device__ __forceinline__ float ldv(const float* p, long long i) { return p[i]; }
+__device__ __forceinline__ float ldv(const __nv_bfloat16* p, long long i) { return __bfloat162float(p[i]); }
+__device__ __forceinline__ void stv(float* p, long long i, float v) { p[i] = v; }
+__device__ __forceinline__ void stv(__nv_bfloat16* p, long long i, float v) { p[i] = __float2bfloat16_rn(v); }
+
 // 1 - e^{-x} with full relative accuracy: for |x| < 1/4 the Taylor series
 // x (1 - x/2 (1 - x/3 (1 - x/4 (1 - x/5 (1 - x/6 (1 - x/7)))))) (truncation
 // below 2e-9 relative), elsewhere 1 - e (no cancellation there).
@@ -360,8 +366,9 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
 
 template <typename T, int MODE>   // 0 render, 1 residual (+F), 2 F only
 __global__ void __launch_bounds__(kThreads) k_forward(DevScene sc, const T* __restrict__ x,
-                                                      const float* __restrict__ target,
-                                                      float* __restrict__ out,
+                                                      const T* __restrict__ target,
+                                                      float* __restrict__ img,
+                                                      T* __restrict__ res,
                                                       float* __restrict__ T_out, double* F) {
     double facc = 0.0;
     PERF_TILE_LOOP {
@@ -373,15 +380,15 @@ __global__ void __launch_bounds__(kThreads) k_forward(DevScene sc, const T* __re
         float Te;
         composite(sc, x, R, ray, s, Te);
         if (MODE == 0) {
-            out[3 * ray + 0] = s.H[0];
-            out[3 * ray + 1] = s.H[1];
-            out[3 * ray + 2] = s.H[2];
+            img[3 * ray + 0] = s.H[0];
+            img[3 * ray + 1] = s.H[1];
+            img[3 * ray + 2] = s.H[2];
             if (T_out) T_out[ray] = Te;
         } else {
 #pragma unroll
             for (int k = 0; k < 3; ++k) {
-                const float r = s.H[k] - target[3 * ray + k];
-                if (MODE == 1 && out) out[3 * ray + k] = r;
+                const float r = s.H[k] - ldv(target, 3 * ray + k);
+                if (MODE == 1 && res) stv(res, 3 * ray + k, r);
                 facc += 0.5 * (double)r * (double)r;
             }
         }
@@ -405,10 +412,10 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
     }
 }
 
-template <typename T, typename TP, int MODE>   // 0 vjp, 1 apply A, 2 diag (+grad)
+template <typename T, typename TP, int MODE, typename TV>   // 0 vjp, 1 apply A, 2 diag (+grad)
 __global__ void __launch_bounds__(kThreads) k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
-                                                      const float* __restrict__ v,
+                                                      const TV* __restrict__ v,
                                                       float* __restrict__ out,
                                                       float* __restrict__ out2, double* pap) {
     double acc = 0.0;
@@ -431,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(DevScene sc, const T* __re
                 V = s.V;
             } else {
                 if (MODE == 0 || v != nullptr) {
-                    vr[0] = v[3 * ray]; vr[1] = v[3 * ray + 1]; vr[2] = v[3 * ray + 2];
+                    vr[0] = ldv(v, 3 * ray); vr[1] = ldv(v, 3 * ray + 1); vr[2] = ldv(v, 3 * ray + 2);
                 }
                 if (MODE == 2 || vr[0] != 0.0f || vr[1] != 0.0f || vr[2] != 0.0f)
                     V = optical_depth(sc, x, R, ray);
@@ -482,25 +489,6 @@ static int grid_blocks(const void* fn, long long n_tiles) {
     return (int)(b > 0 ? b : 1);
 }
 
-template <typename T>
-cudaError_t launch_forward_t(const DevScene& sc, const void* x, const float* target, float* out,
-                             float* T_out, double* F, int mode, cudaStream_t st) {
-    const T* xx = static_cast<const T*>(x);
-    if (sc.n_tiles == 0) return cudaSuccess;
-    if (mode == 0) {
-        auto fn = k_forward<T, 0>;
-        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(sc, xx, target, out, T_out, F);
-    } else if (mode == 1) {
-        auto fn = k_forward<T, 1>;
-        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(sc, xx, target, out, T_out, F);
-    } else {
-        auto fn = k_forward<T, 2>;
-        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(sc, xx, target, out, T_out, F);
-    }
-    count_launch();
-    return cudaGetLastError();
-}
-
 cudaError_t launch_count_samples(const DevScene& sc, unsigned long long* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess || sc.n_tiles == 0) return e;
@@ -509,8 +497,31 @@ cudaError_t launch_count_samples(const DevScene& sc, unsigned long long* out, cu
     return cudaGetLastError();
 }
 
-cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const float* target,
-                           float* out, float* T_out, double* F, int mode, cudaStream_t st) {
+template <typename T>
+cudaError_t launch_forward_t(const DevScene& sc, const void* x, const void* target, void* out,
+                             float* T_out, double* F, int mode, cudaStream_t st) {
+    const T* xx = static_cast<const T*>(x);
+    const T* tt = static_cast<const T*>(target);
+    if (sc.n_tiles == 0) return cudaSuccess;
+    if (mode == 0) {
+        auto fn = k_forward<T, 0>;
+        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
+            sc, xx, tt, static_cast<float*>(out), nullptr, T_out, F);
+    } else if (mode == 1) {
+        auto fn = k_forward<T, 1>;
+        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
+            sc, xx, tt, nullptr, static_cast<T*>(out), T_out, F);
+    } else {
+        auto fn = k_forward<T, 2>;
+        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(sc, xx, tt, nullptr,
+                                                                           nullptr, T_out, F);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const void* target,
+                           void* out, float* T_out, double* F, int mode, cudaStream_t st) {
     return dtype == 1 ? launch_forward_t<__nv_bfloat16>(sc, x, target, out, T_out, F, mode, st)
                       : launch_forward_t<float>(sc, x, target, out, T_out, F, mode, st);
 }
@@ -534,31 +545,34 @@ cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void*
     return launch_jvp_t<float, float>(sc, x, p, out, st);
 }
 
-template <typename T, typename TP, int MODE>
-cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, const float* v,
+template <typename T, typename TP, int MODE, typename TV>
+cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, const void* v,
                              float* out, float* out2, double* pap, cudaStream_t st) {
     if (sc.n_tiles == 0) return cudaSuccess;
-    auto fn = k_scatter<T, TP, MODE>;
+    auto fn = k_scatter<T, TP, MODE, TV>;
     fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
-        sc, static_cast<const T*>(x), static_cast<const TP*>(p), v, out, out2, pap);
+        sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
+        out2, pap);
     count_launch();
     return cudaGetLastError();
 }
 
+// v: float32 for the VJP (mode 0); the scene's storage type for the residual
+// of the diagonal / gradient (mode 2).
 cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* x, const void* p,
-                           int p_dtype, const float* v, float* out, float* out2, double* pap,
+                           int p_dtype, const void* v, float* out, float* out2, double* pap,
                            cudaStream_t st) {
+    typedef __nv_bfloat16 B;
     if (dtype == 1) {
         if (mode == 1)
-            return p_dtype == 1
-                       ? launch_scatter_t<__nv_bfloat16, __nv_bfloat16, 1>(sc, x, p, v, out, out2, pap, st)
-                       : launch_scatter_t<__nv_bfloat16, float, 1>(sc, x, p, v, out, out2, pap, st);
-        if (mode == 0) return launch_scatter_t<__nv_bfloat16, float, 0>(sc, x, p, v, out, out2, pap, st);
-        return launch_scatter_t<__nv_bfloat16, float, 2>(sc, x, p, v, out, out2, pap, st);
+            return p_dtype == 1 ? launch_scatter_t<B, B, 1, float>(sc, x, p, v, out, out2, pap, st)
+                                : launch_scatter_t<B, float, 1, float>(sc, x, p, v, out, out2, pap, st);
+        if (mode == 0) return launch_scatter_t<B, float, 0, float>(sc, x, p, v, out, out2, pap, st);
+        return launch_scatter_t<B, float, 2, B>(sc, x, p, v, out, out2, pap, st);
     }
-    if (mode == 1) return launch_scatter_t<float, float, 1>(sc, x, p, v, out, out2, pap, st);
-    if (mode == 0) return launch_scatter_t<float, float, 0>(sc, x, p, v, out, out2, pap, st);
-    return launch_scatter_t<float, float, 2>(sc, x, p, v, out, out2, pap, st);
+    if (mode == 1) return launch_scatter_t<float, float, 1, float>(sc, x, p, v, out, out2, pap, st);
+    if (mode == 0) return launch_scatter_t<float, float, 0, float>(sc, x, p, v, out, out2, pap, st);
+    return launch_scatter_t<float, float, 2, float>(sc, x, p, v, out, out2, pap, st);
 }
 
 }  // namespace perf

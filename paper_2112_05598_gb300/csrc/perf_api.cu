@@ -29,7 +29,7 @@ struct perf_ctx {
     int device = 0;
     float* cams = nullptr;
     // workspace (allocated on first use)
-    float* r = nullptr;
+    void* r = nullptr;          // residuals, scene storage type
     float* diag = nullptr;
     float* grad = nullptr;
     double* delta = nullptr;
@@ -288,7 +288,7 @@ perf_status perf_render(perf_ctx* ctx, const void* x, float* rgb_out, float* T_o
     return PERF_OK;
 }
 
-perf_status perf_residual(perf_ctx* ctx, const void* x, const float* target, float* r_out,
+perf_status perf_residual(perf_ctx* ctx, const void* x, const void* target, void* r_out,
                           double* F_out, void* stream) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (bad_ptr(F_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "residual: NULL F_out");
@@ -320,7 +320,7 @@ perf_status perf_vjp(perf_ctx* ctx, const void* x, const float* v, float* out, i
     return PERF_OK;
 }
 
-perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const float* r, float* diag_out,
+perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const void* r, float* diag_out,
                           float* grad_out, void* stream) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (bad_ptr(diag_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "diag_jtj: NULL diag_out");
@@ -426,7 +426,7 @@ perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out, perf_pcg_info* info
     return PERF_OK;
 }
 
-perf_status perf_gn_solve(perf_ctx* ctx, float* x, const float* target, int32_t n_steps,
+perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n_steps,
                           perf_gn_stats* stats, void* stream) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (n_steps < 0) return fail(ctx, PERF_ERR_INVALID_ARG, "gn_solve: n_steps < 0");
@@ -436,7 +436,8 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const float* target, int32_t 
     const bool bf = ctx->scene.dtype == PERF_BF16;
     perf_status ps = ensure_pcg(ctx);
     if (ps != PERF_OK) return ps;
-    CK(alloc(&ctx->r, 3 * ctx->n_rays));
+    if (!ctx->r)
+        CK(cudaMalloc(&ctx->r, (bf ? 2 : 4) * (size_t)(3 * ctx->n_rays > 0 ? 3 * ctx->n_rays : 1)));
     CK(alloc(&ctx->x_trial, ctx->n));
     if (bf) {
         CK(alloc(&ctx->x16, ctx->n));

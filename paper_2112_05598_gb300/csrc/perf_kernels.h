@@ -33,14 +33,16 @@ inline void count_launch(unsigned long long k = 1) { __atomic_fetch_add(&g_launc
 // Total grid samples and shell hits over all rays (one march of the scene).
 cudaError_t launch_count_samples(const DevScene& sc, unsigned long long* out, cudaStream_t st);
 
-// mode: 0 render (out = rgb, T_out), 1 residual (out = r, F), 2 F only.
-cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const float* target,
-                           float* out, float* T_out, double* F, int mode, cudaStream_t st);
+// mode: 0 render (out = float rgb, T_out), 1 residual (out = r, F), 2 F only.
+// target and the residual are in the scene's storage type (float / bf16).
+cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const void* target,
+                           void* out, float* T_out, double* F, int mode, cudaStream_t st);
 cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void* p, int p_dtype,
                        float* out, cudaStream_t st);
-// mode: 0 J^T v, 1 A p (+p^T A p), 2 diag(J^T J) (+ J^T r when v = r and out2 given).
+// mode: 0 J^T v (v float32), 1 A p (+p^T A p), 2 diag(J^T J) (+ J^T r when v = r,
+// in the scene's storage type, and out2 given).
 cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* x, const void* p,
-                           int p_dtype, const float* v, float* out, float* out2, double* pap,
+                           int p_dtype, const void* v, float* out, float* out2, double* pap,
                            cudaStream_t st);
 
 // Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP64; p32 / p16: the

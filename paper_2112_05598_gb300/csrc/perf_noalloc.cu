@@ -46,7 +46,7 @@ perf_status setup(float** out) {
 
 extern "C" perf_status perf_residual_noalloc(const perf_scene* sc, const perf_cameras* cams,
                                              const perf_options* opts, const void* x,
-                                             const float* target, float* r_out, double* F_out,
+                                             const void* target, void* r_out, double* F_out,
                                              void* stream) {
     if (!sc || !cams || !opts || !F_out) return PERF_ERR_INVALID_ARG;
     if (sc->grid_res < 2 || sc->grid_res > 1024) return PERF_ERR_INVALID_ARG;
