@@ -205,6 +205,86 @@ def _workload_desc(sc):
             f"<= {c.max_samples} samples/ray, {c.pcg_iters} fixed Jacobi-PCG iterations per GN step")
 
 
+BATCH_PCG = 20
+
+
+def run_batch(args, rank, world, local):
+    """The many-scenes form: 64 uneven scenes (grids 32^3-96^3, 8-40 cameras at
+    128x128, 1-3 shells), every ray march one persistent launch, the PCG loop
+    a CUDA graph, tile shape from the autotuner.  One step = one GN step of
+    every scene with 20 PCG iterations; value = scene-PCG-iterations/s."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2112_05598_gb300 import Batch
+    from paper_2112_05598_gb300._binding import launch_count
+    from scenegen import make_batch
+    scenes = make_batch()
+    dev = torch.device("cuda", local)
+    b = Batch(scenes, max_samples=192, pcg_iters=BATCH_PCG, pcg_fixed=1)
+    x_gt = torch.from_numpy(np.concatenate([s["x_gt"] for s in scenes])).to(dev)
+    target = torch.empty(3 * b.n_rays, device=dev)
+    b.render(x_gt, target)
+    x = torch.from_numpy(np.concatenate([s["x0"] for s in scenes])).to(dev)
+    tuning = b.autotune(x)
+    for _ in range(args.warmup):
+        b.gn_solve(x, target, 1)
+    stream = torch.cuda.current_stream()
+    clocks = Clocks(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = launch_count()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    stats = []
+    for _ in range(args.steps):
+        stats.extend(b.gn_solve(x, target, 1))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms = max_over_ranks(e0.elapsed_time(e1), world)
+    iters = sum_over_ranks(float(sum(s["pcg_iters"] for st in stats for s in st)), world)
+    value = iters / (ms / 1000.0)
+    # end to end with host buffers
+    x_host = torch.from_numpy(np.concatenate([s["x0"] for s in scenes])).pin_memory()
+    t_host = target.cpu().pin_memory()
+    x_dev = torch.empty_like(x)
+    t_dev = torch.empty_like(target)
+    e2e_steps = args.e2e_steps or args.steps
+    torch.cuda.synchronize()
+    e0.record(stream)
+    it2 = 0
+    for _ in range(e2e_steps):
+        x_dev.copy_(x_host, non_blocking=True)
+        t_dev.copy_(t_host, non_blocking=True)
+        st = b.gn_solve(x_dev, t_dev, 1)
+        x_host.copy_(x_dev, non_blocking=True)
+        it2 += sum(s["pcg_iters"] for s in st[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms2 = max_over_ranks(e0.elapsed_time(e1), world)
+    if rank != 0:
+        return
+    Gs = [s["G"] for s in scenes]
+    line = {"metric": METRIC + " (scene-iterations, batched)", "value": value,
+            "unit": "PCG iters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic (64 seeded voxelised scenes)",
+            "config": {"workload": f"batch64: {len(scenes)} scenes, grids {min(Gs)}^3-{max(Gs)}^3, "
+                                   f"8-40 cameras 128x128, 1-3 shells Gx2G, {BATCH_PCG} PCG/GN step",
+                       "n_params": b.n_params, "n_rays": b.n_rays, "tuning": tuning},
+            "gpu_launches": int(launch_count() - l0),
+            "e2e": {"value": it2 / (ms2 / 1000.0), "unit": "PCG iters/s",
+                    "h2d_bytes_per_step": int(4 * (b.n_params + 3 * b.n_rays)),
+                    "d2h_bytes_per_step": int(4 * b.n_params)},
+            "clocks": clk,
+            "accepted_fraction": float(np.mean([s["accepted"] for st in stats for s in st]))}
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, rank, world, local):
     import torch
     import __graft_entry__
@@ -327,6 +407,8 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "batch64":
+        run_batch(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -55,13 +55,17 @@ typedef enum {
 } perf_status;
 
 enum { PERF_F32 = 0, PERF_BF16 = 1 };
-enum { PERF_PRECOND_JACOBI = 0, PERF_PRECOND_BLOCK4 = 1 };
+enum { PERF_PRECOND_JACOBI = 0,        /* diag(J^T J) (Section "Preconditioner") */
+       PERF_PRECOND_BLOCK4 = 1,        /* 4x4 block per voxel: learned (perf_set_lpc) or
+                                          caller-supplied (perf_pcg_set_blocks) */
+       PERF_PRECOND_BLOCK_JACOBI = 2   /* exact inverse of each voxel's 4x4 block of J^T J */ };
 enum { PERF_EXIT_FIXED = 0, PERF_EXIT_EPS = 1, PERF_EXIT_STALL = 2,
        PERF_EXIT_BREAKDOWN = 3, PERF_EXIT_NONFINITE = 4 };
 
 #define PERF_MAX_SHELLS 8
 
 typedef struct perf_ctx perf_ctx;
+typedef struct perf_lpc perf_lpc;
 
 /* Scene geometry (Section "Method"; Fig. "scene"). */
 typedef struct {
@@ -92,8 +96,7 @@ typedef struct {
     double ls_alpha;      /* Algorithm 3 decimation factor (0.7) */
     int32_t ls_max;       /* at most ls_max decimations (the printed loop has no cap) */
     int32_t project;      /* 1: trial points are projected to sigma >= 0, 0 <= c <= 1 */
-    int32_t precond;      /* PERF_PRECOND_JACOBI, or PERF_PRECOND_BLOCK4 with
-                             blocks supplied by perf_pcg_set_blocks */
+    int32_t precond;      /* PERF_PRECOND_*; texels always use Jacobi */
 } perf_options;
 
 typedef struct {
@@ -112,6 +115,8 @@ typedef struct {
     int32_t ls_evals;     /* Error(gamma) evaluations */
     perf_pcg_info pcg;
     float ms;             /* device time of the step */
+    int32_t precond_fallback;  /* 1: the learned blocks failed the true-residual test and
+                                  the step's PCG was rerun with Jacobi */
 } perf_gn_stats;
 
 /* Device time per kernel family, from CUDA events recorded on the launching
@@ -120,7 +125,8 @@ enum { PERF_T_APPLY = 0,    /* A p: the fused J p / J^T (J p) ray march */
        PERF_T_FORWARD = 1,  /* residual and line-search objective marches */
        PERF_T_DIAG = 2,     /* diag(J^T J) with J^T r */
        PERF_T_VECTOR = 3,   /* PCG vector kernels (update, exit test, direction) */
-       PERF_T_COUNT = 4 };
+       PERF_T_PRECOND = 4,  /* block preconditioner construction (network or block inverse) */
+       PERF_T_COUNT = 5 };
 typedef struct {
     double ms[PERF_T_COUNT];
     int64_t launches[PERF_T_COUNT];
@@ -199,6 +205,20 @@ perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out,
 perf_status perf_gn_solve(perf_ctx* ctx, float* x_inout, const void* target,
                           int32_t n_steps, perf_gn_stats* stats, void* stream);
 
+/* Block preconditioners for Algorithm 2.  perf_pcg_set_blocks: caller-owned
+ * row-major 4x4 blocks (16 floats) for the first n_block grid voxels, used by
+ * perf_pcg_* and by perf_gn_solve when precond = PERF_PRECOND_BLOCK4 and no
+ * network is set.  perf_set_lpc: a learned preconditioner (not owned) whose
+ * blocks perf_gn_solve recomputes every step from that step's x, J^T r,
+ * diag(J^T J) and block couplings; PCG is rerun with Jacobi when the learned
+ * blocks leave the true residual r^T r not below r_0^T r_0 (the residual
+ * judges).  perf_diag_cross: diag(J^T J) and, per grid voxel, the cross
+ * entries (colour k, opacity) of its 4x4 block of J^T J (4 floats, the 4th 0). */
+perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_block);
+perf_status perf_set_lpc(perf_ctx* ctx, perf_lpc* lpc);
+perf_status perf_diag_cross(perf_ctx* ctx, const void* x, float* diag_out, float* cross_out,
+                            void* stream);
+
 /* Kernel timing (instrumentation, off by default).  perf_get_timing
  * synchronises the context's pending events and copies the totals to *out
  * (HOST); reset = 1 clears them afterwards. */
@@ -209,6 +229,93 @@ uint64_t perf_launch_count(void);
  * rays of the context (the units of work of every ray-march kernel). */
 perf_status perf_sample_count(perf_ctx* ctx, uint64_t* out, void* stream);
 perf_status perf_get_timing(perf_ctx* ctx, perf_timing* out, int32_t reset);
+
+/* ------------------------------------------------------------------------
+ * Learned block preconditioner (a 4-layer 3x3x3 convolutional network, 16
+ * channels, bfloat16 activations and weights copies, FP32 accumulation and
+ * master weights).  It maps per-voxel features of one Gauss-Newton system to
+ * P_v = D_v^{-1/2} (L_v L_v^T + 1e-3 I) D_v^{-1/2} (D_v: the voxel's Jacobi
+ * diagonal; L_v lower triangular with a softplus diagonal), so P is SPD by
+ * construction and the initial network (L = I) is Jacobi.  Weights: per
+ * layer W[27 taps][16 out][16 in] then bias[16]; perf_lpc_weight_count floats.
+ * Features: G^3 x 16 bfloat16.  Probe pairs for training: xi (G^3 x 4) and
+ * a_hat = D^{-1/2} A D^{-1/2} xi on the grid voxels, mask (G^3 bytes, may be
+ * NULL) selects voxels whose four parameters are observed. */
+int64_t perf_lpc_weight_count(void);
+perf_status perf_lpc_create(perf_lpc** out, uint64_t seed);
+perf_status perf_lpc_destroy(perf_lpc* lpc);
+const char* perf_lpc_last_error(const perf_lpc* lpc);
+perf_status perf_lpc_get_weights(perf_lpc* lpc, float* host_out);
+perf_status perf_lpc_set_weights(perf_lpc* lpc, const float* host_in);
+/* feat_out = features from x (G^3 grid blocks), J^T r, diag and cross. */
+perf_status perf_lpc_features(perf_lpc* lpc, int32_t G, const float* x, const float* grad,
+                              const float* diag, const float* cross, void* feat_out, void* stream);
+/* Relative loss sum_v |Q_v a_hat_v - xi_v|^2 / sum |xi|^2 (HOST *loss_out) and
+ * its gradient with respect to all weights (grad_out: device floats, may be
+ * NULL).  Synchronises. */
+perf_status perf_lpc_loss_grad(perf_lpc* lpc, int32_t G, const void* feat, const float* ahat,
+                               const float* xi, const uint8_t* mask, double* loss_out,
+                               float* grad_out, void* stream);
+/* One Adam step (lr) on that loss.  Synchronises. */
+perf_status perf_lpc_train_step(perf_lpc* lpc, int32_t G, const void* feat, const float* ahat,
+                                const float* xi, const uint8_t* mask, float lr,
+                                double* loss_out, void* stream);
+/* Raw head outputs (G^3 x 16 bfloat16; channels 0-9 used). */
+perf_status perf_lpc_head_outputs(perf_lpc* lpc, int32_t G, const void* feat, void* out,
+                                  void* stream);
+/* blocks_out (G^3 x 16 floats) = P_v for every grid voxel. */
+perf_status perf_lpc_infer(perf_lpc* lpc, int32_t G, const void* feat, const float* diag,
+                           float* blocks_out, void* stream);
+/* out_v = D_v^{-1/2} in_v on the G^3 grid voxels (4 floats each; 0 where a
+ * voxel has an unobserved parameter); mask_out (may be NULL) = 1 where all
+ * four parameters are observed.  Prepares probe pairs for training. */
+perf_status perf_lpc_dscale(int32_t G, const float* diag, const float* in, float* out,
+                            uint8_t* mask_out, void* stream);
+/* Exact block-Jacobi: blocks_out = inverse of each voxel's 4x4 block of J^T J
+ * (Jacobi where a block is unobserved or singular). */
+perf_status perf_block_jacobi(int32_t G, const float* diag, const float* cross,
+                              float* blocks_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Batched form: many independent scenes (each its own grid, shells and
+ * cameras; float32) solved together.  Parameters, rays, targets and
+ * residuals of all scenes are concatenated in scene order; use
+ * perf_batch_param_offset / perf_batch_ray_offset (scene = n_scenes gives the
+ * totals).  Every ray march is one persistent launch taking (scene, pixel
+ * tile) items from a work queue; each scene has its own PCG scalars and its
+ * own line search; the fixed-iteration PCG loop is captured once as a CUDA
+ * graph (on an internal stream) and replayed each Gauss-Newton step.
+ * scenes and cams are HOST arrays of n_scenes entries (cameras copied);
+ * validation as perf_create; dtype must be PERF_F32. */
+typedef struct perf_batch perf_batch;
+
+/* Ray-tile shape and resident-CTA cap chosen by perf_batch_autotune. */
+typedef struct {
+    int32_t tile_w, tile_h;   /* pixels per warp tile (tile_w * tile_h = 32) */
+    int32_t ctas_per_sm;      /* 0 = as many as fit */
+    float apply_ms;           /* time of the fastest A p launch */
+} perf_tuning;
+
+perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_scene* scenes,
+                              const perf_cameras* cams, const perf_options* opts);
+perf_status perf_batch_destroy(perf_batch* b);
+int64_t perf_batch_param_offset(const perf_batch* b, int32_t scene);
+int64_t perf_batch_ray_offset(const perf_batch* b, int32_t scene);
+const char* perf_batch_last_error(const perf_batch* b);
+/* rgb_out[3 N_r total] = H^ of every scene's rays (Eq. 3-4). */
+perf_status perf_batch_render(perf_batch* b, const float* x, float* rgb_out, void* stream);
+/* r_out (may be NULL) = H^ - C; F_out[n_scenes] (device doubles) = 1/2 sum r^2 per scene. */
+perf_status perf_batch_residual(perf_batch* b, const float* x, const float* target,
+                                float* r_out, double* F_out, void* stream);
+/* Times the A p launch at x over tile shapes 8x4, 4x8, 16x2, 32x1 and CTA caps
+ * {all, 3, 2}, keeps the fastest (used by every later launch) and reports it
+ * in *out (HOST, may be NULL).  Synchronises. */
+perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out, void* stream);
+/* n_steps Gauss-Newton steps for every scene (opts.pcg_iters fixed PCG
+ * iterations, Algorithm 3 per scene, accept per scene).  stats (HOST, may be
+ * NULL) receives n_steps * n_scenes records, step-major.  Synchronises. */
+perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, int32_t n_steps,
+                                perf_gn_stats* stats, void* stream);
 
 /* Residual and objective without a context and without any device
  * allocation -- the paper has no counterpart; this serves callers that cannot

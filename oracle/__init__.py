@@ -175,6 +175,15 @@ class Oracle:
                             _dptr(diag), _dptr(grad))
         return diag, (grad if r is not None else None)
 
+    def block_cross(self, x):
+        """(diag(J^T J), cross) with cross[4v + k] = sum_rows dr/dc_{v,k} dr/dsigma_v
+        for grid voxel v (the off-diagonal entries of its 4x4 block of J^T J)."""
+        x = self._x(x)
+        diag = np.zeros(self.n_params)
+        cross = np.zeros(4 * self.G ** 3)
+        _lib().oc_block_cross(ctypes.byref(self.p), _dptr(x), _dptr(diag), _dptr(cross))
+        return diag, cross
+
     def ray_samples(self, x, ray, cap=1024):
         x = self._x(x)
         T = np.zeros(cap); a = np.zeros(cap); s = np.zeros(cap)

@@ -479,14 +479,31 @@ static int oc_entry_cmp(const void* a, const void* b) {
 /* Exact Jacobi diagonal diag(J^T J)_q = sum_rows (dr/dx_q)^2 and (when r is
  * given) the gradient J^T r.  Each row's entry for parameter q is first
  * summed over all samples of the ray that touch q, then squared. */
-int oc_diag_grad(const oc_problem* P, const double* x, const double* r,
-                 double* diag, double* grad) {
+static int oc_diag_impl(const oc_problem* P, const double* x, const double* r, double* diag,
+                        double* grad, double* cross);
+
+int oc_diag_grad(const oc_problem* P, const double* x, const double* r, double* diag,
+                 double* grad) {
+    return oc_diag_impl(P, x, r, diag, grad, NULL);
+}
+
+/* Off-diagonal entries of each grid voxel's 4x4 block of J^T J: cross[4v+k] =
+ * sum_rows (dr/dc_{v,k}) (dr/dsigma_v) for k < 3 (colour-colour entries vanish
+ * since colour k only enters residual k); cross[4v+3] = 0. */
+int oc_block_cross(const oc_problem* P, const double* x, double* diag, double* cross) {
+    return oc_diag_impl(P, x, NULL, diag, NULL, cross);
+}
+
+static int oc_diag_impl(const oc_problem* P, const double* x, const double* r, double* diag,
+                        double* grad, double* cross) {
     const int64_t N = oc_n_rays(P);
     const int64_t np = oc_n_params(P);
     const int cap = oc_cap(P);
     const int nt = oc_nthreads(P);
     double** pd = (double**)calloc(nt, sizeof(double*));
     double** pg = (double**)calloc(nt, sizeof(double*));
+    double** pc = (double**)calloc(nt, sizeof(double*));
+    const int64_t nvox = (int64_t)P->G * P->G * P->G;
 #pragma omp parallel num_threads(nt)
     {
         int tid = 0;
@@ -495,8 +512,10 @@ int oc_diag_grad(const oc_problem* P, const double* x, const double* r,
 #endif
         double* ad = (double*)calloc(np, sizeof(double));
         double* ag = (double*)calloc(np, sizeof(double));
+        double* ac = cross ? (double*)calloc(4 * nvox, sizeof(double)) : NULL;
         pd[tid] = ad;
         pg[tid] = ag;
+        pc[tid] = ac;
         oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
         double* dc = (double*)malloc(sizeof(double) * cap);
         double* ds = (double*)malloc(sizeof(double) * 3 * cap);
@@ -518,6 +537,9 @@ int oc_diag_grad(const oc_problem* P, const double* x, const double* r,
                 }
             qsort(ent, (size_t)ne, sizeof(oc_entry), oc_entry_cmp);
             int64_t a = 0;
+            int64_t cur_vox = -1;
+            double gv[4][3];
+            memset(gv, 0, sizeof(gv));
             while (a < ne) {
                 int64_t b = a;
                 double g[3] = {0, 0, 0};
@@ -525,8 +547,19 @@ int oc_diag_grad(const oc_problem* P, const double* x, const double* r,
                 const int64_t q = ent[a].q;
                 ad[q] += g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
                 if (r) ag[q] += g[0] * r[3 * ray] + g[1] * r[3 * ray + 1] + g[2] * r[3 * ray + 2];
+                if (ac && q / 4 < nvox) {
+                    if (q / 4 != cur_vox) {
+                        if (cur_vox >= 0)
+                            for (int k = 0; k < 3; ++k) ac[4 * cur_vox + k] += gv[k][k] * gv[3][k];
+                        cur_vox = q / 4;
+                        memset(gv, 0, sizeof(gv));
+                    }
+                    for (int k = 0; k < 3; ++k) gv[q % 4][k] = g[k];
+                }
                 a = b;
             }
+            if (ac && cur_vox >= 0)
+                for (int k = 0; k < 3; ++k) ac[4 * cur_vox + k] += gv[k][k] * gv[3][k];
         }
         free(buf); free(dc); free(ds); free(ent);
     }
@@ -534,8 +567,9 @@ int oc_diag_grad(const oc_problem* P, const double* x, const double* r,
     for (int t = 0; t < nt; ++t) if (pd[t]) used = t + 1;
     if (diag) oc_reduce(pd, used, np, diag, 0);
     if (grad && r) oc_reduce(pg, used, np, grad, 0);
-    for (int t = 0; t < nt; ++t) { free(pd[t]); free(pg[t]); }
-    free(pd); free(pg);
+    if (cross) oc_reduce(pc, used, 4 * nvox, cross, 0);
+    for (int t = 0; t < nt; ++t) { free(pd[t]); free(pg[t]); if (pc[t]) free(pc[t]); }
+    free(pd); free(pg); free(pc);
     return 0;
 }
 

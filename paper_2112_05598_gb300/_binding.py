@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libperf.so")
 
 PERF_F32, PERF_BF16 = 0, 1
-PERF_PRECOND_JACOBI, PERF_PRECOND_BLOCK4 = 0, 1
+PERF_PRECOND_JACOBI, PERF_PRECOND_BLOCK4, PERF_PRECOND_BLOCK_JACOBI = 0, 1, 2
 STATUS = {0: "PERF_OK", 1: "PERF_ERR_INVALID_ARG", 2: "PERF_ERR_CUDA",
           3: "PERF_ERR_NONFINITE", 4: "PERF_ERR_TIMEOUT", 5: "PERF_ERR_NOT_SPD",
           6: "PERF_ERR_UNSUPPORTED"}
@@ -57,16 +57,22 @@ class PcgInfo(ctypes.Structure):
 
 
 class Timing(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4)]
+    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5)]
 
 
-TIMING_KINDS = ("apply", "forward", "diag", "vector")
+TIMING_KINDS = ("apply", "forward", "diag", "vector", "precond")
+
+
+class Tuning(ctypes.Structure):
+    _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
+                ("ctas_per_sm", ctypes.c_int32), ("apply_ms", ctypes.c_float)]
 
 
 class GNStats(ctypes.Structure):
     _fields_ = [("F_before", ctypes.c_double), ("F_after", ctypes.c_double),
                 ("gamma", ctypes.c_double), ("accepted", ctypes.c_int32),
-                ("ls_evals", ctypes.c_int32), ("pcg", PcgInfo), ("ms", ctypes.c_float)]
+                ("ls_evals", ctypes.c_int32), ("pcg", PcgInfo), ("ms", ctypes.c_float),
+                ("precond_fallback", ctypes.c_int32)]
 
 
 _VP = ctypes.c_void_p
@@ -89,9 +95,30 @@ _SIGS = {
     "perf_enable_timing": [_VP, ctypes.c_int32],
     "perf_get_timing": [_VP, ctypes.POINTER(Timing), ctypes.c_int32],
     "perf_sample_count": [_VP, ctypes.POINTER(ctypes.c_uint64), _VP],
+    "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
+    "perf_set_lpc": [_VP, _VP],
+    "perf_diag_cross": [_VP, _VP, _VP, _VP, _VP],
+    "perf_lpc_create": [ctypes.POINTER(_VP), ctypes.c_uint64],
+    "perf_lpc_destroy": [_VP],
+    "perf_lpc_get_weights": [_VP, _VP],
+    "perf_lpc_set_weights": [_VP, _VP],
+    "perf_lpc_features": [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, _VP, _VP],
+    "perf_lpc_loss_grad": [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.POINTER(ctypes.c_double),
+                           _VP, _VP],
+    "perf_lpc_train_step": [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP, ctypes.c_float,
+                            ctypes.POINTER(ctypes.c_double), _VP],
+    "perf_lpc_head_outputs": [_VP, ctypes.c_int32, _VP, _VP, _VP],
+    "perf_lpc_infer": [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP],
+    "perf_block_jacobi": [ctypes.c_int32, _VP, _VP, _VP, _VP],
+    "perf_lpc_dscale": [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP],
+    "perf_batch_create": [ctypes.POINTER(_VP), ctypes.c_int32, _VP, _VP, ctypes.POINTER(Options)],
+    "perf_batch_destroy": [_VP],
+    "perf_batch_render": [_VP, _VP, _VP, _VP],
+    "perf_batch_residual": [_VP, _VP, _VP, _VP, _VP, _VP],
+    "perf_batch_autotune": [_VP, _VP, ctypes.POINTER(Tuning), _VP],
+    "perf_batch_gn_solve": [_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(GNStats), _VP],
 }
 _OPTIONAL_SIGS = {
-    "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
     "perf_residual_noalloc": [ctypes.POINTER(Scene), ctypes.POINTER(Cameras),
                               ctypes.POINTER(Options), _VP, _VP, _VP, _VP, _VP],
 }
@@ -123,6 +150,15 @@ def load_library(path: Optional[str] = None):
     lib.perf_ray_count.restype = ctypes.c_int64
     lib.perf_launch_count.argtypes = []
     lib.perf_launch_count.restype = ctypes.c_uint64
+    for name in ("perf_batch_param_offset", "perf_batch_ray_offset"):
+        getattr(lib, name).argtypes = [_VP, ctypes.c_int32]
+        getattr(lib, name).restype = ctypes.c_int64
+    lib.perf_lpc_weight_count.argtypes = []
+    lib.perf_lpc_weight_count.restype = ctypes.c_int64
+    lib.perf_lpc_last_error.argtypes = [_VP]
+    lib.perf_lpc_last_error.restype = ctypes.c_char_p
+    lib.perf_batch_last_error.argtypes = [_VP]
+    lib.perf_batch_last_error.restype = ctypes.c_char_p
     lib.perf_last_error.argtypes = [_VP]
     lib.perf_last_error.restype = ctypes.c_char_p
     if path is None:
@@ -295,6 +331,14 @@ class Context:
     def set_blocks(self, blocks, n_block):
         self._check(self.lib.perf_pcg_set_blocks(self.h, _ptr(blocks), int(n_block)), "set_blocks")
 
+    def set_lpc(self, lpc):
+        self._lpc = lpc
+        self._check(self.lib.perf_set_lpc(self.h, lpc.h if lpc is not None else None), "set_lpc")
+
+    def diag_cross(self, x, diag_out, cross_out, stream=None):
+        self._check(self.lib.perf_diag_cross(self.h, _ptr(x), _ptr(diag_out), _ptr(cross_out),
+                                             _stream(stream)), "diag_cross")
+
     def sample_count(self, stream=None):
         n = ctypes.c_uint64(0)
         self._check(self.lib.perf_sample_count(self.h, ctypes.byref(n), _stream(stream)), "sample_count")
@@ -318,5 +362,173 @@ class Context:
             out.append(dict(F_before=s.F_before, F_after=s.F_after, gamma=s.gamma,
                             accepted=bool(s.accepted), ls_evals=s.ls_evals,
                             pcg_iters=s.pcg.iters, pcg_exit=EXIT.get(s.pcg.exit_reason),
-                            R0=s.pcg.R0, R=s.pcg.R, ms=s.ms))
+                            R0=s.pcg.R0, R=s.pcg.R, ms=s.ms,
+                            precond_fallback=bool(s.precond_fallback)))
         return out
+
+
+class Batch:
+    """Many independent scenes solved together (``perf_batch_*``).  ``scenes``
+    is a list of dicts with G, radii, env_h, env_w, c2w, focal, width, height."""
+
+    def __init__(self, scenes, options: Optional[Options] = None, **opt_kw):
+        self.lib = load_library()
+        n = len(scenes)
+        sc_arr = (Scene * n)()
+        cam_arr = (Cameras * n)()
+        self._keep = []
+        for i, d in enumerate(scenes):
+            radii = [float(r) for r in d["radii"]]
+            sc_arr[i].grid_res = int(d["G"])
+            sc_arr[i].n_shells = len(radii)
+            for j, r in enumerate(radii):
+                sc_arr[i].shell_radii[j] = r
+            sc_arr[i].env_h, sc_arr[i].env_w = int(d["env_h"]), int(d["env_w"])
+            sc_arr[i].dtype = PERF_F32
+            c2w = np.ascontiguousarray(d["c2w"], dtype=np.float32).reshape(-1, 12)
+            focal = np.ascontiguousarray(d["focal"], dtype=np.float32).reshape(-1)
+            self._keep += [c2w, focal]
+            cam_arr[i].n_cams = int(c2w.shape[0])
+            cam_arr[i].width, cam_arr[i].height = int(d["width"]), int(d["height"])
+            cam_arr[i].c2w = c2w.ctypes.data_as(ctypes.c_void_p)
+            cam_arr[i].focal = focal.ctypes.data_as(ctypes.c_void_p)
+        self.options = options if options is not None else default_options()
+        for k, v in opt_kw.items():
+            setattr(self.options, k, v)
+        h = ctypes.c_void_p()
+        st = self.lib.perf_batch_create(ctypes.byref(h), n, ctypes.cast(sc_arr, ctypes.c_void_p),
+                                        ctypes.cast(cam_arr, ctypes.c_void_p),
+                                        ctypes.byref(self.options))
+        if st != 0:
+            raise PerfError(st, "perf_batch_create rejected the scenes or options")
+        self.h = h
+        self.n = n
+        self.param_off = [int(self.lib.perf_batch_param_offset(h, i)) for i in range(n + 1)]
+        self.ray_off = [int(self.lib.perf_batch_ray_offset(h, i)) for i in range(n + 1)]
+        self.n_params = self.param_off[-1]
+        self.n_rays = self.ray_off[-1]
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.perf_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.perf_batch_last_error(self.h)
+            raise PerfError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def render(self, x, rgb_out, stream=None):
+        self._check(self.lib.perf_batch_render(self.h, _ptr(x), _ptr(rgb_out), _stream(stream)),
+                    "batch render")
+
+    def residual(self, x, target, r_out, F_out, stream=None):
+        self._check(self.lib.perf_batch_residual(self.h, _ptr(x), _ptr(target), _ptr(r_out),
+                                                 _ptr(F_out), _stream(stream)), "batch residual")
+
+    def autotune(self, x, stream=None):
+        t = Tuning()
+        self._check(self.lib.perf_batch_autotune(self.h, _ptr(x), ctypes.byref(t), _stream(stream)),
+                    "batch autotune")
+        return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms)
+
+    def gn_solve(self, x, target, n_steps, stream=None):
+        stats = (GNStats * max(int(n_steps) * self.n, 1))()
+        self._check(self.lib.perf_batch_gn_solve(self.h, _ptr(x), _ptr(target), int(n_steps), stats,
+                                                 _stream(stream)), "batch gn_solve")
+        out = []
+        for k in range(int(n_steps)):
+            out.append([dict(F_before=s.F_before, F_after=s.F_after, gamma=s.gamma,
+                             accepted=bool(s.accepted), ls_evals=s.ls_evals,
+                             pcg_iters=s.pcg.iters, ms=s.ms)
+                        for s in stats[k * self.n:(k + 1) * self.n]])
+        return out
+
+
+class LPC:
+    """Learned block preconditioner (``perf_lpc_*``): a 4-layer 3x3x3 conv net
+    trained and run by the library's own BF16 kernels."""
+
+    def __init__(self, seed=0):
+        self.lib = load_library()
+        h = ctypes.c_void_p()
+        st = self.lib.perf_lpc_create(ctypes.byref(h), ctypes.c_uint64(int(seed)))
+        if st != 0:
+            raise PerfError(st, "perf_lpc_create failed")
+        self.h = h
+        self.n_weights = int(self.lib.perf_lpc_weight_count())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.perf_lpc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.perf_lpc_last_error(self.h)
+            raise PerfError(st, f"{what}: {msg.decode() if msg else ''}")
+
+    def get_weights(self):
+        w = np.zeros(self.n_weights, np.float32)
+        self._check(self.lib.perf_lpc_get_weights(self.h, w.ctypes.data_as(ctypes.c_void_p)),
+                    "get_weights")
+        return w
+
+    def set_weights(self, w):
+        w = np.ascontiguousarray(w, dtype=np.float32)
+        assert w.shape[0] == self.n_weights
+        self._check(self.lib.perf_lpc_set_weights(self.h, w.ctypes.data_as(ctypes.c_void_p)),
+                    "set_weights")
+
+    def features(self, G, x, grad, diag, cross, feat_out, stream=None):
+        self._check(self.lib.perf_lpc_features(self.h, int(G), _ptr(x), _ptr(grad), _ptr(diag),
+                                               _ptr(cross), _ptr(feat_out), _stream(stream)),
+                    "features")
+
+    def loss_grad(self, G, feat, ahat, xi, mask=None, grad_out=None, stream=None):
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.perf_lpc_loss_grad(self.h, int(G), _ptr(feat), _ptr(ahat), _ptr(xi),
+                                                _ptr(mask), ctypes.byref(loss), _ptr(grad_out),
+                                                _stream(stream)), "loss_grad")
+        return loss.value
+
+    def train_step(self, G, feat, ahat, xi, mask=None, lr=1e-3, stream=None):
+        loss = ctypes.c_double(0.0)
+        self._check(self.lib.perf_lpc_train_step(self.h, int(G), _ptr(feat), _ptr(ahat), _ptr(xi),
+                                                 _ptr(mask), ctypes.c_float(lr), ctypes.byref(loss),
+                                                 _stream(stream)), "train_step")
+        return loss.value
+
+    def head_outputs(self, G, feat, out, stream=None):
+        self._check(self.lib.perf_lpc_head_outputs(self.h, int(G), _ptr(feat), _ptr(out),
+                                                   _stream(stream)), "head_outputs")
+
+    def infer(self, G, feat, diag, blocks_out, stream=None):
+        self._check(self.lib.perf_lpc_infer(self.h, int(G), _ptr(feat), _ptr(diag),
+                                            _ptr(blocks_out), _stream(stream)), "infer")
+
+
+def dscale(G, diag, inp, out, mask_out=None, stream=None):
+    st = load_library().perf_lpc_dscale(int(G), _ptr(diag), _ptr(inp), _ptr(out), _ptr(mask_out),
+                                        _stream(stream))
+    if st != 0:
+        raise PerfError(st, "perf_lpc_dscale failed")
+
+
+def block_jacobi(G, diag, cross, blocks_out, stream=None):
+    st = load_library().perf_block_jacobi(int(G), _ptr(diag), _ptr(cross), _ptr(blocks_out),
+                                          _stream(stream))
+    if st != 0:
+        raise PerfError(st, "perf_block_jacobi failed")

@@ -204,9 +204,12 @@ struct VjpSink {
 // Diagonal sink: slot = (a, s_0, s_1, s_2), the ray's row entries for the
 // voxel (colour: a for each channel's residual; opacity: s_k for residual k),
 // squared into diag and multiplied by r into the gradient.
+// With `cross`, also the off-diagonal entries of the voxel's 4x4 block of
+// J^T J: (colour k, opacity) = sum_rays a s_k (colour-colour entries vanish).
 struct DiagSink {
     float* diag;
     float* grad;
+    float* cross;
     float r0, r1, r2;
     __device__ __forceinline__ void put(bool ev, int key, const float (&a)[4]) {
         if (!(ev && (a[0] != 0.0f || a[1] != 0.0f || a[2] != 0.0f || a[3] != 0.0f))) return;
@@ -215,7 +218,9 @@ struct DiagSink {
         if (grad)
             red_add4(grad, key, make_float4(a[0] * r0, a[0] * r1, a[0] * r2,
                                             a[1] * r0 + a[2] * r1 + a[3] * r2));
+        if (cross && key < n_vox) red_add4(cross, key, make_float4(a[0] * a[1], a[0] * a[2], a[0] * a[3], 0.0f));
     }
+    long long n_vox;
 };
 
 // Move the window (all lanes; `on` = this lane moves) to base nb, handing the
@@ -358,41 +363,92 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
 
 // ------------------------------------------------------------- kernels
 
+// Per-tile bodies: one warp marches the 32 rays of one pixel tile.  The
+// single-scene kernels stride over tiles; the batched kernels take tiles of
+// many scenes from a work queue.
+
+template <typename T, int MODE>   // 0 render, 1 residual (+F), 2 F only
+__device__ __forceinline__ void forward_tile(const DevScene& sc, const T* __restrict__ x,
+                                             const T* __restrict__ target, float* __restrict__ img,
+                                             T* __restrict__ res, float* __restrict__ T_out,
+                                             long long tile, int lane, double& facc) {
+    long long ray;
+    if (!tile_pixel(sc, tile, lane, ray)) return;
+    Ray R;
+    ray_setup(sc, ray, R);
+    Comp s;
+    float Te;
+    composite(sc, x, R, ray, s, Te);
+    if (MODE == 0) {
+        img[3 * ray + 0] = s.H[0];
+        img[3 * ray + 1] = s.H[1];
+        img[3 * ray + 2] = s.H[2];
+        if (T_out) T_out[ray] = Te;
+    } else {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float r = s.H[k] - ldv(target, 3 * ray + k);
+            if (MODE == 1 && res) stv(res, 3 * ray + k, r);
+            facc += 0.5 * (double)r * (double)r;
+        }
+    }
+}
+
+// All 32 lanes call it (the back-to-front sweep is warp-synchronous).
+template <typename T, typename TP, int MODE, typename TV>   // 0 vjp, 1 apply A, 2 diag (+grad)
+__device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __restrict__ x,
+                                             const TP* __restrict__ p, const TV* __restrict__ v,
+                                             float* __restrict__ out, float* __restrict__ out2,
+                                             float* __restrict__ out3, long long tile, int lane,
+                                             double& acc) {
+    long long ray = 0;
+    bool act = tile_pixel(sc, tile, lane, ray);
+    Ray R;
+    R.K = 0;
+    R.shell_hit = 0u;
+    R.delta = 0.0f;
+    float vr[3] = {0.0f, 0.0f, 0.0f};
+    CSum V = {0.0f, 0.0f};
+    if (act) {
+        ray_setup(sc, ray, R);
+        if (MODE == 1) {
+            Tang s;
+            tangent(sc, x, p, R, ray, s);
+            vr[0] = s.J[0]; vr[1] = s.J[1]; vr[2] = s.J[2];
+            acc += (double)vr[0] * vr[0] + (double)vr[1] * vr[1] + (double)vr[2] * vr[2];
+            V = s.V;
+        } else {
+            if (MODE == 0 || v != nullptr) {
+                vr[0] = ldv(v, 3 * ray); vr[1] = ldv(v, 3 * ray + 1); vr[2] = ldv(v, 3 * ray + 2);
+            }
+            if (MODE == 2 || vr[0] != 0.0f || vr[1] != 0.0f || vr[2] != 0.0f)
+                V = optical_depth(sc, x, R, ray);
+        }
+        if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f) act = false;
+    }
+    if (MODE == 2) {
+        DiagSink sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox};
+        backward_sweep<4>(sc, x, R, ray, act, V, vr, sk);
+    } else {
+        VjpSink sk{out, vr[0], vr[1], vr[2]};
+        backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
+    }
+}
+
 #define PERF_TILE_LOOP                                                              \
     const int lane = threadIdx.x & 31;                                              \
     const long long nw = (long long)gridDim.x * kWarps;                             \
     for (long long tile = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);      \
          tile < sc.n_tiles; tile += nw)
 
-template <typename T, int MODE>   // 0 render, 1 residual (+F), 2 F only
+template <typename T, int MODE>
 __global__ void __launch_bounds__(kThreads) k_forward(DevScene sc, const T* __restrict__ x,
                                                       const T* __restrict__ target,
                                                       float* __restrict__ img,
                                                       T* __restrict__ res,
                                                       float* __restrict__ T_out, double* F) {
     double facc = 0.0;
-    PERF_TILE_LOOP {
-        long long ray;
-        if (!tile_pixel(sc, tile, lane, ray)) continue;
-        Ray R;
-        ray_setup(sc, ray, R);
-        Comp s;
-        float Te;
-        composite(sc, x, R, ray, s, Te);
-        if (MODE == 0) {
-            img[3 * ray + 0] = s.H[0];
-            img[3 * ray + 1] = s.H[1];
-            img[3 * ray + 2] = s.H[2];
-            if (T_out) T_out[ray] = Te;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const float r = s.H[k] - ldv(target, 3 * ray + k);
-                if (MODE == 1 && res) stv(res, 3 * ray + k, r);
-                facc += 0.5 * (double)r * (double)r;
-            }
-        }
-    }
+    PERF_TILE_LOOP { forward_tile<T, MODE>(sc, x, target, img, res, T_out, tile, lane, facc); }
     if (MODE != 0) block_add_f64<kWarps>(facc, F);
 }
 
@@ -412,48 +468,120 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
     }
 }
 
-template <typename T, typename TP, int MODE, typename TV>   // 0 vjp, 1 apply A, 2 diag (+grad)
+template <typename T, typename TP, int MODE, typename TV>
 __global__ void __launch_bounds__(kThreads) k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
                                                       const TV* __restrict__ v,
                                                       float* __restrict__ out,
-                                                      float* __restrict__ out2, double* pap) {
+                                                      float* __restrict__ out2,
+                                                      float* __restrict__ out3, double* pap) {
     double acc = 0.0;
     PERF_TILE_LOOP {
-        long long ray = 0;
-        bool act = tile_pixel(sc, tile, lane, ray);
-        Ray R;
-        R.K = 0;
-        R.shell_hit = 0u;
-        R.delta = 0.0f;
-        float vr[3] = {0.0f, 0.0f, 0.0f};
-        CSum V = {0.0f, 0.0f};
-        if (act) {
-            ray_setup(sc, ray, R);
-            if (MODE == 1) {
-                Tang s;
-                tangent(sc, x, p, R, ray, s);
-                vr[0] = s.J[0]; vr[1] = s.J[1]; vr[2] = s.J[2];
-                acc += (double)vr[0] * vr[0] + (double)vr[1] * vr[1] + (double)vr[2] * vr[2];
-                V = s.V;
-            } else {
-                if (MODE == 0 || v != nullptr) {
-                    vr[0] = ldv(v, 3 * ray); vr[1] = ldv(v, 3 * ray + 1); vr[2] = ldv(v, 3 * ray + 2);
-                }
-                if (MODE == 2 || vr[0] != 0.0f || vr[1] != 0.0f || vr[2] != 0.0f)
-                    V = optical_depth(sc, x, R, ray);
-            }
-            if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f) act = false;
-        }
-        if (MODE == 2) {
-            DiagSink sk{out, out2, vr[0], vr[1], vr[2]};
-            backward_sweep<4>(sc, x, R, ray, act, V, vr, sk);
-        } else {
-            VjpSink sk{out, vr[0], vr[1], vr[2]};
-            backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
-        }
+        scatter_tile<T, TP, MODE, TV>(sc, x, p, v, out, out2, out3, tile, lane, acc);
     }
     if (MODE == 1 && pap) block_add_f64<kWarps>(acc, pap);
+}
+
+// ------------------------------------------------------ batched (many scenes)
+
+constexpr int kBatchSmem = 48;   // scene descriptors staged in shared memory
+
+// Next tile of the work queue for this warp (-1: queue empty) and its scene.
+__device__ __forceinline__ long long batch_next(unsigned long long* counter, long long total,
+                                                const long long* __restrict__ start, int n,
+                                                int lane, int& scene) {
+    unsigned long long t = 0;
+    if (lane == 0) t = atomicAdd(counter, 1ull);
+    t = __shfl_sync(kFull, t, 0);
+    if ((long long)t >= total) return -1;
+    int lo = 0, hi = n - 1;               // last scene with start <= t
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= (long long)t) lo = mid; else hi = mid - 1;
+    }
+    scene = lo;
+    return (long long)t - start[lo];
+}
+
+__device__ __forceinline__ const BatchItem* stage_items(const BatchItem* items, int n,
+                                                        BatchItem* smem) {
+    if (n > kBatchSmem) return items;
+    const int words = (int)(n * sizeof(BatchItem) / sizeof(int));
+    const int* src = reinterpret_cast<const int*>(items);
+    int* dst = reinterpret_cast<int*>(smem);
+    for (int i = threadIdx.x; i < words; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
+    return smem;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+    return v;
+}
+
+// mode 0: image into img; 1: residual into res (+ F per scene); 2: F per scene only.
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_forward_batch(const BatchItem* __restrict__ items,
+                                                            const long long* __restrict__ start,
+                                                            int n, long long total,
+                                                            unsigned long long* counter,
+                                                            const float* __restrict__ x,
+                                                            const float* __restrict__ target,
+                                                            float* __restrict__ res, double* F,
+                                                            const int* __restrict__ active,
+                                                            float* __restrict__ img) {
+    __shared__ BatchItem s_items[kBatchSmem];
+    const BatchItem* it = stage_items(items, n, s_items);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int sidx = 0;
+        const long long tile = batch_next(counter, total, start, n, lane, sidx);
+        if (tile < 0) break;
+        if (active && !active[sidx]) continue;
+        const BatchItem& b = it[sidx];
+        double facc = 0.0;
+        forward_tile<float, MODE>(b.sc, x + b.x_off, target ? target + 3 * b.r_off : nullptr,
+                                  img ? img + 3 * b.r_off : nullptr,
+                                  res ? res + 3 * b.r_off : nullptr, nullptr, tile, lane, facc);
+        if (MODE != 0) {
+            facc = warp_sum(facc);
+            if (lane == 0 && facc != 0.0) atomicAdd(&F[sidx], facc);
+        }
+    }
+}
+
+// mode 1: A p (+ p^T A p per scene into pap[scene * pap_stride]),
+// mode 2: diag (+ grad with v = residuals).
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_scatter_batch(const BatchItem* __restrict__ items,
+                                                            const long long* __restrict__ start,
+                                                            int n, long long total,
+                                                            unsigned long long* counter,
+                                                            const float* __restrict__ x,
+                                                            const float* __restrict__ p,
+                                                            const float* __restrict__ v,
+                                                            float* __restrict__ out,
+                                                            float* __restrict__ out2, double* pap,
+                                                            int pap_stride) {
+    __shared__ BatchItem s_items[kBatchSmem];
+    const BatchItem* it = stage_items(items, n, s_items);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int sidx = 0;
+        const long long tile = batch_next(counter, total, start, n, lane, sidx);
+        if (tile < 0) break;
+        const BatchItem& b = it[sidx];
+        double acc = 0.0;
+        scatter_tile<float, float, MODE, float>(b.sc, x + b.x_off, p ? p + b.x_off : nullptr,
+                                                v ? v + 3 * b.r_off : nullptr, out + b.x_off,
+                                                out2 ? out2 + b.x_off : nullptr, nullptr, tile,
+                                                lane, acc);
+        if (MODE == 1) {
+            acc = warp_sum(acc);
+            if (lane == 0 && acc != 0.0) atomicAdd(&pap[(long long)sidx * pap_stride], acc);
+        }
+    }
 }
 
 __global__ void __launch_bounds__(kThreads) k_count(DevScene sc, unsigned long long* out) {
@@ -547,12 +675,13 @@ cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void*
 
 template <typename T, typename TP, int MODE, typename TV>
 cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, const void* v,
-                             float* out, float* out2, double* pap, cudaStream_t st) {
+                             float* out, float* out2, double* pap, cudaStream_t st,
+                             float* out3 = nullptr) {
     if (sc.n_tiles == 0) return cudaSuccess;
     auto fn = k_scatter<T, TP, MODE, TV>;
     fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
-        out2, pap);
+        out2, out3, pap);
     count_launch();
     return cudaGetLastError();
 }
@@ -561,18 +690,74 @@ cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, c
 // of the diagonal / gradient (mode 2).
 cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* x, const void* p,
                            int p_dtype, const void* v, float* out, float* out2, double* pap,
-                           cudaStream_t st) {
+                           cudaStream_t st, float* out3) {
     typedef __nv_bfloat16 B;
     if (dtype == 1) {
         if (mode == 1)
             return p_dtype == 1 ? launch_scatter_t<B, B, 1, float>(sc, x, p, v, out, out2, pap, st)
                                 : launch_scatter_t<B, float, 1, float>(sc, x, p, v, out, out2, pap, st);
         if (mode == 0) return launch_scatter_t<B, float, 0, float>(sc, x, p, v, out, out2, pap, st);
-        return launch_scatter_t<B, float, 2, B>(sc, x, p, v, out, out2, pap, st);
+        return launch_scatter_t<B, float, 2, B>(sc, x, p, v, out, out2, pap, st, out3);
     }
     if (mode == 1) return launch_scatter_t<float, float, 1, float>(sc, x, p, v, out, out2, pap, st);
     if (mode == 0) return launch_scatter_t<float, float, 0, float>(sc, x, p, v, out, out2, pap, st);
-    return launch_scatter_t<float, float, 2, float>(sc, x, p, v, out, out2, pap, st);
+    return launch_scatter_t<float, float, 2, float>(sc, x, p, v, out, out2, pap, st, out3);
+}
+
+// ------------------------------------------------------ batched launchers
+
+static int batch_blocks(const void* fn, int cap_per_sm) {
+    int sms = 0, dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int occ = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, 0);
+    if (occ <= 0) occ = 1;
+    if (cap_per_sm > 0 && cap_per_sm < occ) occ = cap_per_sm;
+    return (sms > 0 ? sms : 1) * occ;
+}
+
+cudaError_t launch_forward_batch(const BatchItem* items, const long long* start, int n,
+                                 long long total, unsigned long long* counter, const float* x,
+                                 const float* target, float* res, double* F, const int* active,
+                                 int mode, int cap_per_sm, cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || total == 0) return e;
+    if (mode == 0) {
+        auto fn = k_forward_batch<0>;
+        fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
+            items, start, n, total, counter, x, nullptr, nullptr, nullptr, active, res);
+    } else if (mode == 1) {
+        auto fn = k_forward_batch<1>;
+        fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
+            items, start, n, total, counter, x, target, res, F, active, nullptr);
+    } else {
+        auto fn = k_forward_batch<2>;
+        fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
+            items, start, n, total, counter, x, target, nullptr, F, active, nullptr);
+    }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start, int n,
+                                 long long total, unsigned long long* counter, const float* x,
+                                 const float* p, const float* v, float* out, float* out2,
+                                 double* pap, int pap_stride, int mode, int cap_per_sm,
+                                 cudaStream_t st) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || total == 0) return e;
+    if (mode == 1) {
+        auto fn = k_scatter_batch<1>;
+        fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
+            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride);
+    } else {
+        auto fn = k_scatter_batch<2>;
+        fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
+            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride);
+    }
+    count_launch();
+    return cudaGetLastError();
 }
 
 }  // namespace perf

@@ -75,6 +75,21 @@ __device__ __forceinline__ D4 precond(const D4& r, long long v, const float4* __
               d.z > kJacobiFloor ? r.z / d.z : 0.0, d.w > kJacobiFloor ? r.w / d.w : 0.0};
 }
 
+// Segments: blockIdx.y selects one independent system (a scene of a batch)
+// whose parameter blocks are [seg[y], seg[y+1]) and whose scalars are s[y];
+// seg == nullptr means a single segment [0, nb).
+__device__ __forceinline__ void seg_range(const long long* seg, long long nb, long long& lo,
+                                          long long& hi) {
+    if (seg) { lo = seg[blockIdx.y]; hi = seg[blockIdx.y + 1]; }
+    else { lo = 0; hi = nb; }
+}
+
+#define SEG_LOOP(v)                                                                      \
+    long long lo_, hi_;                                                                   \
+    seg_range(seg, nb, lo_, hi_);                                                         \
+    for (long long v = lo_ + (long long)blockIdx.x * blockDim.x + threadIdx.x; v < hi_;   \
+         v += (long long)gridDim.x * blockDim.x)
+
 __device__ __forceinline__ double dot4(const D4& a, const D4& b) {
     return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
 }
@@ -94,16 +109,17 @@ __device__ __forceinline__ void store_p(float4* p32, __nv_bfloat16* p16, long lo
     if (p16) store_bf16x4(p16, v, f);
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const float4* __restrict__ g,
+__global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const long long* seg,
+                                                        const float4* __restrict__ g,
                                                         const float4* __restrict__ d4,
                                                         const float4* __restrict__ B, long long n_block,
                                                         double* delta, double* rho, double* p,
                                                         float4* p32, __nv_bfloat16* p16, float4* Ap,
                                                         PcgScalars* s) {
+    s += blockIdx.y;
     double aR = 0.0, aRz = 0.0;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
-         v += (long long)gridDim.x * blockDim.x) {
+    SEG_LOOP(v) {
         const float4 gg = g[v];
         const D4 r{-(double)gg.x, -(double)gg.y, -(double)gg.z, -(double)gg.w};
         const D4 z = precond(r, v, d4, B, n_block);
@@ -119,7 +135,11 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const flo
     block_add_f64<kVThreads / 32>(aRz, &s->acc_rz);
 }
 
-__global__ void k_pcg_begin_fin(PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall) {
+__global__ void k_pcg_begin_fin(PcgScalars* s, int n_seg, int max_iter, int fixed, double eps_rel,
+                                double stall) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seg) return;
+    s += i;
     s->R0 = s->acc_R;
     s->R_prev = s->acc_R;
     s->R = s->acc_R;
@@ -143,19 +163,20 @@ __global__ void k_pcg_begin_fin(PcgScalars* s, int max_iter, int fixed, double e
     }
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, double* delta, double* rho,
+__global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, const long long* seg,
+                                                         double* delta, double* rho,
                                                          const double* __restrict__ p,
                                                          const float4* __restrict__ Ap,
                                                          const float4* __restrict__ d4,
                                                          const float4* __restrict__ B,
                                                          long long n_block, PcgScalars* s) {
+    s += blockIdx.y;
     if (s->done) return;
     const double pAp = s->pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) return;
     const double alpha = s->rz / pAp;
     double aR = 0.0, aRz = 0.0;
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
-         v += (long long)gridDim.x * blockDim.x) {
+    SEG_LOOP(v) {
         const D4 pv = ld4(p, v);
         const float4 av = Ap[v];
         D4 dv = ld4(delta, v), r = ld4(rho, v);
@@ -173,7 +194,10 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, double* 
     block_add_f64<kVThreads / 32>(aRz, &s->acc_rz);
 }
 
-__global__ void k_pcg_finish(PcgScalars* s) {
+__global__ void k_pcg_finish(PcgScalars* s, int n_seg) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_seg) return;
+    s += i;
     if (s->done) return;
     const double pAp = s->pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) {
@@ -204,16 +228,17 @@ __global__ void k_pcg_finish(PcgScalars* s) {
     s->pAp = 0.0;
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const double* __restrict__ rho,
+__global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const long long* seg,
+                                                      const double* __restrict__ rho,
                                                       const float4* __restrict__ d4,
                                                       const float4* __restrict__ B, long long n_block,
                                                       double* p, float4* p32, __nv_bfloat16* p16,
                                                       float4* Ap, const PcgScalars* s) {
+    s += blockIdx.y;
     if (s->done) return;
     const double beta = s->beta;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
-         v += (long long)gridDim.x * blockDim.x) {
+    SEG_LOOP(v) {
         const D4 z = precond(ld4(rho, v), v, d4, B, n_block);
         D4 pv = ld4(p, v);
         pv.x = fma(beta, pv.x, z.x); pv.y = fma(beta, pv.y, z.y);
@@ -247,6 +272,31 @@ __global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4*
     }
 }
 
+// Batched trial: segment y gets x_out = P(x + gamma[y] Delta) where mask[y]
+// is set (mask == nullptr: every segment); other segments are left alone.
+__global__ void __launch_bounds__(kVThreads) k_trial_seg(long long nb, const long long* seg,
+                                                        const float4* x,
+                                                        const double* __restrict__ delta,
+                                                        const double* __restrict__ gamma,
+                                                        const int* __restrict__ mask, int project,
+                                                        float4* x_out) {
+    if (mask && !mask[blockIdx.y]) return;
+    const double g = gamma[blockIdx.y];
+    SEG_LOOP(v) {
+        const float4 a = x[v];
+        const D4 d = ld4(delta, v);
+        float4 y = make_float4((float)fma(g, d.x, (double)a.x), (float)fma(g, d.y, (double)a.y),
+                               (float)fma(g, d.z, (double)a.z), (float)fma(g, d.w, (double)a.w));
+        if (project) {
+            y.x = fminf(fmaxf(y.x, 0.0f), 1.0f);
+            y.y = fminf(fmaxf(y.y, 0.0f), 1.0f);
+            y.z = fminf(fmaxf(y.z, 0.0f), 1.0f);
+            y.w = fmaxf(y.w, 0.0f);
+        }
+        x_out[v] = y;
+    }
+}
+
 __global__ void __launch_bounds__(kVThreads) k_to_bf16(long long nb, const float4* __restrict__ x,
                                                       __nv_bfloat16* y) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
@@ -266,47 +316,99 @@ __global__ void __launch_bounds__(kVThreads) k_to_f32(long long n, const double*
 #define F4(p) reinterpret_cast<float4*>(p)
 #define CF4(p) reinterpret_cast<const float4*>(p)
 
+static dim3 seg_grid(long long nb, int n_seg, long long max_seg) {
+    if (n_seg <= 1) return dim3(vec_blocks(nb), 1, 1);
+    int per = vec_blocks(max_seg);
+    const int cap = (vec_blocks(1ll << 40) + n_seg - 1) / n_seg;   // total ~ SMs * 8
+    if (per > cap) per = cap;
+    return dim3(per > 0 ? per : 1, n_seg, 1);
+}
+
+cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                                 const float* grad, const float* diag, double* delta, double* rho,
+                                 double* p, float* p32, __nv_bfloat16* p16, float* Ap,
+                                 PcgScalars* s, int max_iter, int fixed, double eps_rel,
+                                 double stall, const float* blocks, long long n_block,
+                                 cudaStream_t st) {
+    const long long nb = n / 4;
+    cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars) * (size_t)(n_seg > 0 ? n_seg : 1), st);
+    if (e != cudaSuccess) return e;
+    if (nb > 0) {
+        k_pcg_begin<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
+            nb, seg, CF4(grad), CF4(diag), CF4(blocks), n_block, delta, rho, p, F4(p32), p16,
+            F4(Ap), s);
+        count_launch();
+    }
+    const int ns = n_seg > 1 ? n_seg : 1;
+    k_pcg_begin_fin<<<(ns + 31) / 32, 32, 0, st>>>(s, ns, max_iter, fixed, eps_rel, stall);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
                              double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                              PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st) {
+    return launch_pcg_begin_seg(n, 1, nullptr, n / 4, grad, diag, delta, rho, p, p32, p16, Ap, s,
+                                max_iter, fixed, eps_rel, stall, blocks, n_block, st);
+}
+
+cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                                  double* delta, double* rho, const double* p, const float* Ap,
+                                  const float* diag, const float* blocks, long long n_block,
+                                  PcgScalars* s, cudaStream_t st) {
     const long long nb = n / 4;
-    cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars), st);
-    if (e != cudaSuccess) return e;
-    if (nb > 0)
-        k_pcg_begin<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(grad), CF4(diag), CF4(blocks),
-                                                          n_block, delta, rho, p, F4(p32), p16,
-                                                          F4(Ap), s);
-    k_pcg_begin_fin<<<1, 1, 0, st>>>(s, max_iter, fixed, eps_rel, stall);
-    count_launch(nb > 0 ? 2 : 1);
+    if (nb > 0) {
+        k_pcg_update<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
+            nb, seg, delta, rho, p, CF4(Ap), CF4(diag), CF4(blocks), n_block, s);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
                               const float* Ap, const float* diag, const float* blocks,
                               long long n_block, PcgScalars* s, cudaStream_t st) {
-    const long long nb = n / 4;
-    if (nb > 0) {
-        k_pcg_update<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, delta, rho, p, CF4(Ap), CF4(diag),
-                                                           CF4(blocks), n_block, s);
-        count_launch();
-    }
+    return launch_pcg_update_seg(n, 1, nullptr, n / 4, delta, rho, p, Ap, diag, blocks, n_block, s,
+                                 st);
+}
+
+cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st) {
+    const int ns = n_seg > 1 ? n_seg : 1;
+    k_pcg_finish<<<(ns + 31) / 32, 32, 0, st>>>(s, ns);
+    count_launch();
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st) {
-    k_pcg_finish<<<1, 1, 0, st>>>(s);
-    count_launch();
+cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st) { return launch_pcg_finish_seg(s, 1, st); }
+
+cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                               const double* rho, const float* diag, const float* blocks,
+                               long long n_block, double* p, float* p32, __nv_bfloat16* p16,
+                               float* Ap, PcgScalars* s, cudaStream_t st) {
+    const long long nb = n / 4;
+    if (nb > 0) {
+        k_pcg_dir<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
+            nb, seg, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
 cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
                            long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                            PcgScalars* s, cudaStream_t st) {
+    return launch_pcg_dir_seg(n, 1, nullptr, n / 4, rho, diag, blocks, n_block, p, p32, p16, Ap, s,
+                              st);
+}
+
+cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                             const float* x, const double* delta, const double* gamma,
+                             const int* mask, int project, float* x_out, cudaStream_t st) {
     const long long nb = n / 4;
     if (nb > 0) {
-        k_pcg_dir<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, rho, CF4(diag), CF4(blocks), n_block, p,
-                                                        F4(p32), p16, F4(Ap), s);
+        k_trial_seg<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
+            nb, seg, CF4(x), delta, gamma, mask, project, F4(x_out));
         count_launch();
     }
     return cudaGetLastError();

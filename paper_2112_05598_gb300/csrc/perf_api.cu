@@ -21,6 +21,13 @@
 using perf::DevScene;
 using perf::PcgScalars;
 
+namespace perf {
+cudaError_t lpc_blocks_for(perf_lpc* L, int G, const float* x, const float* grad, const float* diag,
+                           const float* cross, __nv_bfloat16* feat, float* blocks, cudaStream_t st);
+cudaError_t launch_block_jacobi(const float* diag, const float* cross, float* blocks, long long V,
+                                cudaStream_t st);
+}  // namespace perf
+
 struct perf_ctx {
     perf_scene scene;
     perf_options opts;
@@ -45,6 +52,10 @@ struct perf_ctx {
     double* dF = nullptr;
     const float* blocks = nullptr;   // caller-owned 4x4 blocks per voxel (or null)
     long long n_block = 0;
+    perf_lpc* lpc = nullptr;         // learned preconditioner (not owned)
+    float* cross = nullptr;          // per voxel (a s_0, a s_1, a s_2, 0)
+    float* blocks_ws = nullptr;      // blocks computed each GN step
+    __nv_bfloat16* feat = nullptr;   // network input features
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::string err;
     // kernel timing
@@ -83,7 +94,8 @@ perf_status check_options(const perf_options* o, std::string& why) {
     if (o->pcg_iters < 0) { why = "pcg_iters < 0"; return PERF_ERR_INVALID_ARG; }
     if (!(o->ls_alpha > 0.0 && o->ls_alpha < 1.0)) { why = "ls_alpha must be in (0,1)"; return PERF_ERR_INVALID_ARG; }
     if (o->ls_max < 0 || o->ls_max > 200) { why = "ls_max out of range"; return PERF_ERR_INVALID_ARG; }
-    if (o->precond != PERF_PRECOND_JACOBI && o->precond != PERF_PRECOND_BLOCK4) { why = "unknown preconditioner"; return PERF_ERR_INVALID_ARG; }
+    if (o->precond != PERF_PRECOND_JACOBI && o->precond != PERF_PRECOND_BLOCK4 &&
+        o->precond != PERF_PRECOND_BLOCK_JACOBI) { why = "unknown preconditioner"; return PERF_ERR_INVALID_ARG; }
     if (!(o->pcg_eps_rel >= 0.0) || !(o->pcg_stall > 0.0)) { why = "pcg_eps_rel / pcg_stall invalid"; return PERF_ERR_INVALID_ARG; }
     return PERF_OK;
 }
@@ -212,8 +224,10 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
     d.H = cams->height;
     d.n_cams = cams->n_cams;
     d.n_rays = ctx->n_rays;
-    d.tiles_x = (cams->width + 7) / 8;
-    d.tiles_y = (cams->height + 3) / 4;
+    d.tile_w = 8;
+    d.tile_h = 4;
+    d.tiles_x = (cams->width + d.tile_w - 1) / d.tile_w;
+    d.tiles_y = (cams->height + d.tile_h - 1) / d.tile_h;
     d.n_tiles = (long long)d.tiles_x * d.tiles_y * cams->n_cams;
     if (ctx->n_rays == 0) d.n_tiles = 0;
     d.max_samples = opts->max_samples;
@@ -250,7 +264,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->p32, ctx->Ap, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->p32, ctx->Ap, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -371,10 +385,10 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
 
 namespace {
 
-// One Algorithm 2 iteration on the context workspace with diagonal `diag`.
-perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, cudaStream_t st) {
+// One Algorithm 2 iteration on the context workspace with diagonal `diag`
+// and block preconditioner B (null: Jacobi).
+perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const float* B, cudaStream_t st) {
     const bool bf = ctx->scene.dtype == PERF_BF16;
-    const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
     const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p32);
     t_begin(ctx, PERF_T_APPLY, st);
     CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32, nullptr,
@@ -398,7 +412,8 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_step: NULL x");
     if (!ctx->delta || !ctx->s) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_step before pcg_begin");
-    perf_status st = pcg_iter(ctx, x, ctx->diag, S(stream));
+    const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
+    perf_status st = pcg_iter(ctx, x, ctx->diag, B, S(stream));
     if (st != PERF_OK) return st;
     if (done_out) {
         int done = 0;
@@ -463,24 +478,64 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         // b = -J^T r and M = diag(J^T J)
         CK(cudaMemsetAsync(ctx->diag, 0, sizeof(float) * (size_t)ctx->n, st));
         CK(cudaMemsetAsync(ctx->grad, 0, sizeof(float) * (size_t)ctx->n, st));
+        const long long nvox = ctx->ds.n_vox;
+        const bool blk = o.precond != PERF_PRECOND_JACOBI;
+        const bool need_cross = o.precond == PERF_PRECOND_BLOCK_JACOBI ||
+                                (o.precond == PERF_PRECOND_BLOCK4 && ctx->lpc);
+        if (need_cross) {
+            CK(alloc(&ctx->cross, 4 * nvox));
+            CK(cudaMemsetAsync(ctx->cross, 0, sizeof(float) * 4 * (size_t)nvox, st));
+        }
         t_begin(ctx, PERF_T_DIAG, st);
         if (ctx->n_rays > 0)
             CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, xm, nullptr, PERF_F32, ctx->r,
-                                    ctx->diag, ctx->grad, nullptr, st));
+                                    ctx->diag, ctx->grad, nullptr, st,
+                                    need_cross ? ctx->cross : nullptr));
         t_end(ctx, PERF_T_DIAG, st);
-        const float* B = o.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
-        CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
-                                  ctx->p32, ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
-                                  o.pcg_eps_rel, o.pcg_stall, B, ctx->n_block, st));
-        for (int k = 0; k < o.pcg_iters; ++k) {
-            ps = pcg_iter(ctx, xm, ctx->diag, st);
-            if (ps != PERF_OK) return ps;
-            if (!o.pcg_fixed) {
-                int done = 0;
-                CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-                CK(cudaStreamSynchronize(st));
-                if (done) break;
+        const float* B = nullptr;
+        long long nB = 0;
+        if (o.precond == PERF_PRECOND_BLOCK_JACOBI ||
+            (o.precond == PERF_PRECOND_BLOCK4 && ctx->lpc)) {
+            CK(alloc(&ctx->blocks_ws, 16 * nvox));
+            t_begin(ctx, PERF_T_PRECOND, st);
+            if (o.precond == PERF_PRECOND_BLOCK_JACOBI) {
+                CK(perf::launch_block_jacobi(ctx->diag, ctx->cross, ctx->blocks_ws, nvox, st));
+            } else {
+                CK(alloc(&ctx->feat, 16 * nvox));
+                CK(perf::lpc_blocks_for(ctx->lpc, ctx->ds.G, x, ctx->grad, ctx->diag, ctx->cross,
+                                        ctx->feat, ctx->blocks_ws, st));
             }
+            t_end(ctx, PERF_T_PRECOND, st);
+            B = ctx->blocks_ws;
+            nB = nvox;
+        } else if (o.precond == PERF_PRECOND_BLOCK4) {
+            B = ctx->blocks;
+            nB = ctx->n_block;
+        }
+        int fallback = 0;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
+                                      ctx->p32, ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
+                                      o.pcg_eps_rel, o.pcg_stall, B, nB, st));
+            for (int k = 0; k < o.pcg_iters; ++k) {
+                ps = pcg_iter(ctx, xm, ctx->diag, B, st);
+                if (ps != PERF_OK) return ps;
+                if (!o.pcg_fixed) {
+                    int done = 0;
+                    CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+                    CK(cudaStreamSynchronize(st));
+                    if (done) break;
+                }
+            }
+            if (!(o.precond == PERF_PRECOND_BLOCK4 && blk) || B == nullptr) break;
+            // the true residual judges the learned preconditioner; Jacobi is the fallback
+            PcgScalars hj;
+            CK(cudaMemcpyAsync(&hj, ctx->s, sizeof(hj), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+            if (std::isfinite(hj.R) && hj.R < hj.R0 && hj.exit_reason != 3 && hj.exit_reason != 4) break;
+            B = nullptr;
+            nB = 0;
+            fallback = 1;
         }
         double F0 = 0.0;
         CK(cudaMemcpyAsync(&F0, ctx->dF, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -540,6 +595,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
             g.pcg.R0 = h.R0;
             g.pcg.R = h.R;
             g.pcg.rz = h.rz;
+            g.precond_fallback = fallback;
             float ms = 0.f;
             cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1);
             g.ms = ms;
@@ -554,6 +610,35 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
 perf_status perf_enable_timing(perf_ctx* ctx, int32_t on) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     ctx->timing = on != 0;
+    return PERF_OK;
+}
+
+perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_block) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (n_block < 0 || n_block > ctx->ds.n_vox || (n_block > 0 && !blocks))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_set_blocks: 0 <= n_block <= G^3 blocks required");
+    ctx->blocks = blocks;
+    ctx->n_block = n_block;
+    return PERF_OK;
+}
+
+perf_status perf_set_lpc(perf_ctx* ctx, perf_lpc* lpc) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    ctx->lpc = lpc;
+    return PERF_OK;
+}
+
+perf_status perf_diag_cross(perf_ctx* ctx, const void* x, float* diag_out, float* cross_out,
+                            void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(diag_out) || bad_ptr(cross_out))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "diag_cross: NULL output");
+    CK(cudaMemsetAsync(diag_out, 0, sizeof(float) * (size_t)ctx->n, S(stream)));
+    CK(cudaMemsetAsync(cross_out, 0, sizeof(float) * 4 * (size_t)ctx->ds.n_vox, S(stream)));
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "diag_cross: NULL x");
+    CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr, diag_out,
+                            nullptr, nullptr, S(stream), cross_out));
     return PERF_OK;
 }
 

@@ -35,8 +35,9 @@ struct DevScene {
     long long shell_texels;  // He*We
     int W, H, n_cams;
     long long n_rays;
-    long long n_tiles;       // 8x4 pixel tiles over all cameras
+    long long n_tiles;       // tile_w x tile_h pixel tiles over all cameras
     int tiles_x, tiles_y;
+    int tile_w, tile_h;      // one warp per tile: tile_w * tile_h = 32
     const float* cams;       // n_cams x 16: c2w (12), focal, pad
     int max_samples;
     int jitter;
@@ -67,15 +68,16 @@ __device__ __forceinline__ float jitter_u(const DevScene& sc, long long ray, uns
     return (float)(h >> 40) * (1.0f / 16777216.0f);
 }
 
-// Pixel of lane `lane` in tile `tile`: tiles are 8 wide x 4 high.
+// Pixel of lane `lane` in tile `tile` (tiles are tile_w wide, tile_h high,
+// row-major over each camera's image, cameras one after the other).
 __device__ __forceinline__ bool tile_pixel(const DevScene& sc, long long tile, int lane,
                                            long long& ray) {
     const long long per_cam = (long long)sc.tiles_x * sc.tiles_y;
     const int cam = (int)(tile / per_cam);
     const int t = (int)(tile - (long long)cam * per_cam);
     const int ty = t / sc.tiles_x, tx = t - ty * sc.tiles_x;
-    const int col = tx * 8 + (lane & 7);
-    const int row = ty * 4 + (lane >> 3);
+    const int col = tx * sc.tile_w + lane % sc.tile_w;
+    const int row = ty * sc.tile_h + lane / sc.tile_w;
     if (col >= sc.W || row >= sc.H) return false;
     ray = ((long long)cam * sc.H + row) * sc.W + col;
     return true;

@@ -5,6 +5,31 @@
 
 namespace perf {
 
+// One scene of a batch: its geometry and where its parameters, rays and
+// tiles start in the batch's concatenated vectors / work queue.
+struct BatchItem {
+    DevScene sc;
+    long long x_off;      // first parameter (floats; multiple of 4)
+    long long r_off;      // first ray
+    long long tile_off;   // first tile in the work queue
+};
+
+// Batched ray marches over many scenes in one persistent launch: warps take
+// tiles from the work queue `counter` (zeroed here); `start[n]` are the
+// scenes' first tiles.  Forward: mode 0 image into res, 1 residual
+// (+F[scene]), 2 F[scene] only,
+// scenes with active[s] == 0 skipped (active may be null).  Scatter: mode 1
+// A p (+ p^T A p into pap[scene * pap_stride]), 2 diag (+ grad with v = r).
+cudaError_t launch_forward_batch(const BatchItem* items, const long long* start, int n,
+                                 long long total, unsigned long long* counter, const float* x,
+                                 const float* target, float* res, double* F, const int* active,
+                                 int mode, int cap_per_sm, cudaStream_t st);
+cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start, int n,
+                                 long long total, unsigned long long* counter, const float* x,
+                                 const float* p, const float* v, float* out, float* out2,
+                                 double* pap, int pap_stride, int mode, int cap_per_sm,
+                                 cudaStream_t st);
+
 // Device scalars of Algorithm 2 and the line search (FP64).
 struct PcgScalars {
     double rz;        // r_k^T z_k
@@ -41,9 +66,11 @@ cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void*
                        float* out, cudaStream_t st);
 // mode: 0 J^T v (v float32), 1 A p (+p^T A p), 2 diag(J^T J) (+ J^T r when v = r,
 // in the scene's storage type, and out2 given).
+// out3 (mode 2, may be null): per grid voxel the cross entries (colour k,
+// opacity) of the 4x4 diagonal block of J^T J.
 cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* x, const void* p,
                            int p_dtype, const void* v, float* out, float* out2, double* pap,
-                           cudaStream_t st);
+                           cudaStream_t st, float* out3 = nullptr);
 
 // Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP64; p32 / p16: the
 // FP32 / BF16 copies of p that the ray march gathers; Ap: FP32 scatter target.
@@ -64,6 +91,29 @@ cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, co
 cudaError_t launch_trial(long long n, const float* x, const double* delta, double gamma,
                          int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
 cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaStream_t st);
+
+// Segmented forms (a batch of independent systems): segment y owns parameter
+// blocks [seg[y], seg[y+1]) (seg: device array of n_seg + 1), scalars s[y];
+// max_seg = the largest segment (blocks) for grid sizing.
+cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                                 const float* grad, const float* diag, double* delta, double* rho,
+                                 double* p, float* p32, __nv_bfloat16* p16, float* Ap,
+                                 PcgScalars* s, int max_iter, int fixed, double eps_rel,
+                                 double stall, const float* blocks, long long n_block,
+                                 cudaStream_t st);
+cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                                  double* delta, double* rho, const double* p, const float* Ap,
+                                  const float* diag, const float* blocks, long long n_block,
+                                  PcgScalars* s, cudaStream_t st);
+cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st);
+cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                               const double* rho, const float* diag, const float* blocks,
+                               long long n_block, double* p, float* p32, __nv_bfloat16* p16,
+                               float* Ap, PcgScalars* s, cudaStream_t st);
+// Segment y: x_out = P(x + gamma[y] Delta) where mask[y] (or every segment).
+cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+                             const float* x, const double* delta, const double* gamma,
+                             const int* mask, int project, float* x_out, cudaStream_t st);
 cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t st);
 
 }  // namespace perf

@@ -101,8 +101,10 @@ extern "C" perf_status perf_residual_noalloc(const perf_scene* sc, const perf_ca
     d.H = cams->height;
     d.n_cams = cams->n_cams;
     d.n_rays = n_rays;
-    d.tiles_x = (cams->width + 7) / 8;
-    d.tiles_y = (cams->height + 3) / 4;
+    d.tile_w = 8;
+    d.tile_h = 4;
+    d.tiles_x = (cams->width + d.tile_w - 1) / d.tile_w;
+    d.tiles_y = (cams->height + d.tile_h - 1) / d.tile_h;
     d.n_tiles = (long long)d.tiles_x * d.tiles_y * cams->n_cams;
     d.cams = dcam;
     d.max_samples = opts->max_samples;

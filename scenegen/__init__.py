@@ -307,3 +307,24 @@ def batch_scene_configs(rng, n_scenes=64, G_lo=32, G_hi=96, cams_lo=8,
                         res=res, radii=tuple(2.0 * 2 ** s for s in range(S)),
                         env_h=G, env_w=2 * G, seed=int(rng.integers(1 << 30))))
     return out
+
+
+def make_batch(n_scenes=64, seed=1237, G_lo=32, G_hi=96, cams_lo=8, cams_hi=40, res=128,
+               n_prims=8) -> List[dict]:
+    """The many-scenes workload: n_scenes independent seeded scenes with grid
+    sizes uniform in [G_lo, G_hi], cams_lo..cams_hi cameras at res x res on a
+    radius-3 sphere, 1-3 shells of G x 2G texels at radii 2, 4, 8; voxelised
+    ellipsoids and boxes as ground truth; start rgb 0.5, sigma 0.05."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for c in batch_scene_configs(rng, n_scenes, G_lo, G_hi, cams_lo, cams_hi, res):
+        r2 = np.random.default_rng(c["seed"])
+        G, S = c["G"], len(c["radii"])
+        grid = _voxelise(r2, G, n_prims, ("ellipsoid", "box"), (0.1, 0.4))
+        shells = [_env_noise(r2, c["env_h"], c["env_w"], 3.0).reshape(-1) for _ in range(S)]
+        x_gt = np.concatenate([grid.reshape(-1)] + shells).astype(np.float32)
+        c2w, focal = make_cameras(r2, c["n_cams"], res, 3.0, "sphere", 40.0)
+        out.append(dict(G=G, radii=c["radii"], env_h=c["env_h"], env_w=c["env_w"], c2w=c2w,
+                        focal=focal, width=res, height=res, x_gt=x_gt,
+                        x0=constant_params(G, S, c["env_h"], c["env_w"], 0.5, 0.05)))
+    return out
