@@ -57,6 +57,12 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cams", type=int, default=16)
+    ap.add_argument("--lpc", action="store_true", help="learned vs Jacobi preconditioner study")
+    ap.add_argument("--lpc-scenes", type=int, default=100)
+    ap.add_argument("--lpc-steps", type=int, default=20)
+    ap.add_argument("--lpc-epochs", type=int, default=2)
+    ap.add_argument("--lpc-gn", type=int, default=2)
+    ap.add_argument("--lpc-max-iter", type=int, default=150)
     return ap.parse_args()
 
 
@@ -208,6 +214,103 @@ def _workload_desc(sc):
 BATCH_PCG = 20
 
 
+def _psnr_from_F(F, n_rays):
+    mse = 2.0 * F / (3.0 * n_rays)
+    return float("inf") if mse <= 0 else 10.0 * np.log10(1.0 / mse)
+
+
+def run_lpc(args, rank, world, local):
+    """Learned block preconditioner vs Jacobi (and exact block-Jacobi) on the
+    ring workload (256^3, 4 shells, 150 cameras 960x540 on a 360-degree ring,
+    opaque textured background).  The network is first trained on systems the
+    solver logs from Gauss-Newton runs of 32^3 scenes (the small workload's
+    recipe, seeds 0..N); every method then runs GN steps from the same start
+    with PCG to a relative residual of 1e-3 (at most --lpc-max-iter
+    iterations), and held-out-view PSNR is recorded after each step."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2112_05598_gb300 import (Context, LPC, PERF_PRECOND_BLOCK4,
+                                        PERF_PRECOND_BLOCK_JACOBI, PERF_PRECOND_JACOBI)
+    from paper_2112_05598_gb300 import lpc_train as T
+    from scenegen import make_scene
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    gen = torch.Generator(device=dev).manual_seed(0)
+    # 1. log systems from the solver's own runs on small scenes
+    t0 = time.perf_counter()
+    net = LPC(seed=7)
+    systems = []
+    n_train_scenes = args.lpc_scenes
+    for seed in range(n_train_scenes):
+        sc = make_scene("small32", seed=2000 + seed)
+        ctx = Context.from_scene(sc, pcg_iters=5, pcg_fixed=1)
+        target = torch.empty(3 * ctx.n_rays, device=dev)
+        ctx.render(torch.from_numpy(sc.x_gt).to(dev), target)
+        x = torch.from_numpy(sc.x0.copy()).to(dev)
+        for _ in range(args.lpc_steps):
+            systems.append(T.log_system(ctx, net, x, target, n_probes=1, generator=gen))
+            ctx.gn_solve(x, target, 1)
+        ctx.close()
+    t_log = time.perf_counter() - t0
+    held = systems[-max(1, len(systems) // 10):]
+    train = systems[:len(systems) - len(held)]
+    loss0 = T.mean_loss(net, held)
+    t0 = time.perf_counter()
+    T.train(net, train, epochs=args.lpc_epochs, lr=1e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    loss1 = T.mean_loss(net, held)
+    del systems, train, held
+    # 2. evaluate on the ring workload
+    sc = make_scene(args.workload, n_cams=args.cams)
+    ctx = Context.from_scene(sc)
+    hold = Context.from_scene(sc, c2w=sc.heldout_c2w, focal=sc.heldout_focal)
+    x_gt = torch.from_numpy(sc.x_gt).to(dev)
+    target = torch.empty(3 * ctx.n_rays, device=dev)
+    ctx.render(x_gt, target)
+    htarget = torch.empty(3 * hold.n_rays, device=dev)
+    hold.render(x_gt, htarget)
+    F = torch.zeros(1, dtype=torch.float64, device=dev)
+    results = {}
+    for name, pc in (("jacobi", PERF_PRECOND_JACOBI), ("learned", PERF_PRECOND_BLOCK4),
+                     ("block_jacobi", PERF_PRECOND_BLOCK_JACOBI)):
+        x = torch.from_numpy(sc.x0.copy()).to(dev)
+        ctx.set_options(pcg_iters=args.lpc_max_iter, pcg_fixed=0, pcg_eps_rel=1e-3,
+                        pcg_stall=1e30, precond=pc)
+        ctx.set_lpc(net if pc == PERF_PRECOND_BLOCK4 else None)
+        hold.residual(x, htarget, None, F)
+        curve = [(0.0, _psnr_from_F(float(F.item()), hold.n_rays))]
+        steps = []
+        t_acc = 0.0
+        for _ in range(args.lpc_gn):
+            st = ctx.gn_solve(x, target, 1)[0]
+            t_acc += st["ms"] / 1000.0
+            hold.residual(x, htarget, None, F)
+            curve.append((t_acc, _psnr_from_F(float(F.item()), hold.n_rays)))
+            steps.append({"pcg_iters": st["pcg_iters"], "exit": st["pcg_exit"], "ms": st["ms"],
+                          "F_after": st["F_after"], "fallback": st["precond_fallback"]})
+        results[name] = {"steps": steps, "psnr_curve": curve}
+    target_psnr = results["jacobi"]["psnr_curve"][-1][1] - 0.1
+
+    def time_to(curve):
+        for t, p in curve:
+            if p >= target_psnr:
+                return t
+        return None
+    line = {"metric": "PCG iterations to relative residual 1e-3 and time-to-PSNR, learned vs Jacobi",
+            "workload": f"{args.workload}: {sc.G}^3, {sc.n_shells} shells {sc.env_h}x{sc.env_w}, "
+                        f"{sc.n_cams} cameras {sc.width}x{sc.height} ring, background shell sigma 10",
+            "training": {"systems": n_train_scenes * args.lpc_steps, "scenes": n_train_scenes,
+                         "epochs": args.lpc_epochs, "log_s": t_log, "train_s": t_train,
+                         "held_out_probe_loss_identity": loss0, "held_out_probe_loss_trained": loss1},
+            "target_psnr_db": target_psnr,
+            "time_to_psnr_s": {k: time_to(v["psnr_curve"]) for k, v in results.items()},
+            "results": results}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, rank, world, local):
     """The many-scenes form: 64 uneven scenes (grids 32^3-96^3, 8-40 cameras at
     128x128, 1-3 shells), every ray march one persistent launch, the PCG loop
@@ -312,6 +415,11 @@ def run_ours(args, rank, world, local):
 
     for _ in range(args.warmup):
         ctx.gn_solve(x, target, 1)
+    # tile shape / CTA cap tuned at the warmed-up state along a random direction
+    gp = torch.Generator(device=dev).manual_seed(0)
+    probe = torch.randn(sc.n_params, device=dev, generator=gp).to(sdt)
+    tuning = ctx.autotune(x.to(sdt) if bf else x, probe)
+    del probe
     torch.cuda.synchronize()
     ctx.enable_timing(True)
     ctx.timing(reset=True)
@@ -378,7 +486,7 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (seeded voxelised primitives, targets rendered from ground truth)",
         "config": {"workload": _workload_desc(sc) + (" (BF16 storage form)" if bf else ""),
                    "n_params": sc.n_params, "n_rays": sc.n_rays,
-                   "samples_per_march": samples,
+                   "samples_per_march": samples, "tuning": tuning,
                    "l2": "inputs larger than L2: targets and residuals 768 MB each per step"},
         "gpu_launches": int(launches),
         "rays_per_s": 2.0 * sc.n_rays * pcg_total / (ms / 1000.0),
@@ -407,6 +515,8 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.lpc:
+        run_lpc(args, rank, world, local)
     elif args.workload == "batch64":
         run_batch(args, rank, world, local)
     else:

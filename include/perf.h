@@ -132,6 +132,13 @@ typedef struct {
     int64_t launches[PERF_T_COUNT];
 } perf_timing;
 
+/* Ray-tile shape and resident-CTA cap chosen by an autotuner. */
+typedef struct {
+    int32_t tile_w, tile_h;   /* pixels per warp tile (tile_w * tile_h = 32) */
+    int32_t ctas_per_sm;      /* 0 = as many as fit */
+    float apply_ms;           /* time of the fastest A p launch */
+} perf_tuning;
+
 /* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
  * eps 1e-3, stall 0.85, ls_alpha 0.7, ls_max 20, projection on, Jacobi. */
 perf_status perf_default_options(perf_options* out);
@@ -215,6 +222,14 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x_inout, const void* target,
  * judges).  perf_diag_cross: diag(J^T J) and, per grid voxel, the cross
  * entries (colour k, opacity) of its 4x4 block of J^T J (4 floats, the 4th 0). */
 perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_block);
+/* Times the A p launch at x along p (both in the scene storage type; p NULL:
+ * p = x) over tile shapes 8x4, 4x8, 16x2, 32x1 and resident-CTA caps
+ * {all, 3, 2} (two timed launches each), keeps the fastest for every later
+ * ray march of the context unless the default (8x4, no cap) is within 3%,
+ * and reports the choice in *out (HOST, may be NULL).  Uses the PCG
+ * workspace; synchronises. */
+perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
+                          void* stream);
 perf_status perf_set_lpc(perf_ctx* ctx, perf_lpc* lpc);
 perf_status perf_diag_cross(perf_ctx* ctx, const void* x, float* diag_out, float* cross_out,
                             void* stream);
@@ -288,13 +303,6 @@ perf_status perf_block_jacobi(int32_t G, const float* diag, const float* cross,
  * scenes and cams are HOST arrays of n_scenes entries (cameras copied);
  * validation as perf_create; dtype must be PERF_F32. */
 typedef struct perf_batch perf_batch;
-
-/* Ray-tile shape and resident-CTA cap chosen by perf_batch_autotune. */
-typedef struct {
-    int32_t tile_w, tile_h;   /* pixels per warp tile (tile_w * tile_h = 32) */
-    int32_t ctas_per_sm;      /* 0 = as many as fit */
-    float apply_ms;           /* time of the fastest A p launch */
-} perf_tuning;
 
 perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_scene* scenes,
                               const perf_cameras* cams, const perf_options* opts);

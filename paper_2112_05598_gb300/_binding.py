@@ -13,7 +13,7 @@ from typing import Optional
 import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libperf.so")
+LIB_PATH = os.environ.get("PERF_LIB_PATH") or os.path.join(HERE, "libperf.so")
 
 PERF_F32, PERF_BF16 = 0, 1
 PERF_PRECOND_JACOBI, PERF_PRECOND_BLOCK4, PERF_PRECOND_BLOCK_JACOBI = 0, 1, 2
@@ -96,6 +96,7 @@ _SIGS = {
     "perf_get_timing": [_VP, ctypes.POINTER(Timing), ctypes.c_int32],
     "perf_sample_count": [_VP, ctypes.POINTER(ctypes.c_uint64), _VP],
     "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
+    "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_set_lpc": [_VP, _VP],
     "perf_diag_cross": [_VP, _VP, _VP, _VP, _VP],
     "perf_lpc_create": [ctypes.POINTER(_VP), ctypes.c_uint64],
@@ -330,6 +331,12 @@ class Context:
 
     def set_blocks(self, blocks, n_block):
         self._check(self.lib.perf_pcg_set_blocks(self.h, _ptr(blocks), int(n_block)), "set_blocks")
+
+    def autotune(self, x, p=None, stream=None):
+        t = Tuning()
+        self._check(self.lib.perf_autotune(self.h, _ptr(x), _ptr(p), ctypes.byref(t),
+                                           _stream(stream)), "autotune")
+        return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms)
 
     def set_lpc(self, lpc):
         self._lpc = lpc

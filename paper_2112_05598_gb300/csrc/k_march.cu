@@ -38,6 +38,31 @@ namespace perf {
 
 constexpr int kThreads = 128;
 constexpr int kWarps = kThreads / 32;
+// Build-time tuning of the ray-march kernels: reuse of gathered corner values
+// of x (PERF_CACHE_X) and of p (PERF_CACHE_P) between samples, and the
+// minimum resident CTAs per SM requested from the register allocator.  Reuse
+// is off by default: on GB300 it raised the A p kernel from 128 to 238
+// registers and ran slower (37.5 ms plain vs 50.7-71.6 ms with reuse on
+// 20 cameras of the 128^3 workload).
+#ifndef PERF_CACHE_X
+#define PERF_CACHE_X 0
+#endif
+#ifndef PERF_CACHE_P
+#define PERF_CACHE_P 0
+#endif
+#ifndef PERF_MIN_CTAS
+#define PERF_MIN_CTAS 1
+#endif
+
+// Corner interpolation with (Corners) or without (plain gathers) reuse.
+template <typename T, bool CACHE>
+struct Interp {
+    Corners<T> c;
+    __device__ __forceinline__ void reset() { if (CACHE) c.reset(); }
+    __device__ __forceinline__ float4 at(const T* __restrict__ x, const DevScene& sc, const Cell& cl) {
+        return CACHE ? c.interp(x, sc, cl) : interp_grid(x, sc, cl);
+    }
+};
 constexpr unsigned kFull = 0xffffffffu;
 
 // ------------------------------------------------------------------ helpers
@@ -97,9 +122,11 @@ __device__ __forceinline__ void composite(const DevScene& sc, const T* __restric
     s.T = 1.0f;
     s.H[0] = s.H[1] = s.H[2] = 0.0f;
     const float dbar = R.delta * sc.halfG;
+    Interp<T, PERF_CACHE_X != 0> cx;
+    cx.reset();
     for (int k = 0; k < R.K; ++k) {
         const Cell cl = sample_cell(sc, R, ray, k);
-        comp_step(s, interp_grid(x, sc, cl), dbar);
+        comp_step(s, cx.at(x, sc, cl), dbar);
     }
     T_exit = s.T;
     for (int q = 0; q < sc.S; ++q) {
@@ -114,9 +141,11 @@ __device__ __forceinline__ CSum optical_depth(const DevScene& sc, const T* __res
                                               const Ray& R, long long ray) {
     CSum V = {0.0f, 0.0f};
     const float dbar = R.delta * sc.halfG;
+    Interp<T, PERF_CACHE_X != 0> cx;
+    cx.reset();
     for (int k = 0; k < R.K; ++k) {
         const Cell cl = sample_cell(sc, R, ray, k);
-        csum_add(V, __fmul_rn(interp_grid(x, sc, cl).w, dbar));
+        csum_add(V, __fmul_rn(cx.at(x, sc, cl).w, dbar));
     }
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
@@ -158,9 +187,13 @@ __device__ __forceinline__ void tangent(const DevScene& sc, const T* __restrict_
     s.J[0] = s.J[1] = s.J[2] = 0.0f;
     s.V.hi = 0.0f; s.V.lo = 0.0f;
     const float dbar = R.delta * sc.halfG;
+    Interp<T, PERF_CACHE_X != 0> cx;
+    Interp<TP, PERF_CACHE_P != 0> cp;
+    cx.reset();
+    cp.reset();
     for (int k = 0; k < R.K; ++k) {
         const Cell cl = sample_cell(sc, R, ray, k);
-        tang_step(s, interp_grid(x, sc, cl), interp_grid(p, sc, cl), dbar);
+        tang_step(s, cx.at(x, sc, cl), cp.at(p, sc, cl), dbar);
     }
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
@@ -185,8 +218,6 @@ struct Window {
     int b[3];
 };
 
-// Coordinate along one axis of the window voxel with parity bit `pa`.
-__device__ __forceinline__ int par_coord(int base, int pa) { return base + ((pa ^ base) & 1); }
 
 __device__ __forceinline__ int vox_key(int x, int y, int z, int G) { return (z * G + y) * G + x; }
 
@@ -316,6 +347,8 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
 #pragma unroll
         for (int q = 0; q < NV; ++q) w.v[c][q] = 0.0f;
     w.b[0] = w.b[1] = w.b[2] = 0;
+    Interp<T, PERF_CACHE_X != 0> cx;
+    cx.reset();
     for (int k = Kmax - 1; k >= 0; --k) {
         const bool on = k < Kl;
         Cell cl;
@@ -328,7 +361,7 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
         const int nb[3] = {cl.bx, cl.by, cl.bz};
         win_move(w, nb, on, sc.G, sk);
         if (on) {
-            const float4 a = interp_grid(x, sc, cl);
+            const float4 a = cx.at(x, sc, cl);
             const float sd = __fmul_rn(a.w, dbar);
             csum_add(V, -sd);
             const float Ti = expf(-fmaxf(V.hi + V.lo, 0.0f));
@@ -469,7 +502,7 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
 }
 
 template <typename T, typename TP, int MODE, typename TV>
-__global__ void __launch_bounds__(kThreads) k_scatter(DevScene sc, const T* __restrict__ x,
+__global__ void __launch_bounds__(kThreads, PERF_MIN_CTAS) k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
                                                       const TV* __restrict__ v,
                                                       float* __restrict__ out,
@@ -600,7 +633,7 @@ __global__ void __launch_bounds__(kThreads) k_count(DevScene sc, unsigned long l
 
 // ------------------------------------------------------------- launchers
 
-static int grid_blocks(const void* fn, long long n_tiles) {
+static int grid_blocks(const void* fn, long long n_tiles, int cap_per_sm = 0) {
     static int sms = 0;
     if (!sms) {
         int dev = 0;
@@ -611,6 +644,7 @@ static int grid_blocks(const void* fn, long long n_tiles) {
     int occ = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, fn, kThreads, 0);
     if (occ <= 0) occ = 1;
+    if (cap_per_sm > 0 && cap_per_sm < occ) occ = cap_per_sm;
     long long want = (n_tiles + kWarps - 1) / kWarps;
     long long cap = (long long)sms * occ;
     long long b = want < cap ? want : cap;
@@ -679,7 +713,7 @@ cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, c
                              float* out3 = nullptr) {
     if (sc.n_tiles == 0) return cudaSuccess;
     auto fn = k_scatter<T, TP, MODE, TV>;
-    fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
+    fn<<<grid_blocks((const void*)fn, sc.n_tiles, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
         out2, out3, pap);
     count_launch();

@@ -613,6 +613,68 @@ perf_status perf_enable_timing(perf_ctx* ctx, int32_t on) {
     return PERF_OK;
 }
 
+// Re-tile the context's rays for tile width tw (tile height 32 / tw).
+static void set_tiling(perf_ctx* ctx, int tw) {
+    DevScene& d = ctx->ds;
+    d.tile_w = tw;
+    d.tile_h = 32 / tw;
+    d.tiles_x = (d.W + d.tile_w - 1) / d.tile_w;
+    d.tiles_y = (d.H + d.tile_h - 1) / d.tile_h;
+    d.n_tiles = ctx->n_rays > 0 ? (long long)d.tiles_x * d.tiles_y * d.n_cams : 0;
+}
+
+perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
+                          void* stream) {
+    if (!ctx || !x) return PERF_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    perf_status ps = ensure_pcg(ctx);
+    if (ps != PERF_OK) return ps;
+    const bool bf = ctx->scene.dtype == PERF_BF16;
+    // the probe direction (default x: every ray then has a non-zero J p)
+    void* pbuf = bf ? static_cast<void*>(ctx->p16) : static_cast<void*>(ctx->p32);
+    CK(cudaMemcpyAsync(pbuf, p ? p : x, (bf ? 2 : 4) * (size_t)ctx->n, cudaMemcpyDeviceToDevice, st));
+    const void* pp = pbuf;
+    const int tws[4] = {8, 4, 16, 32};
+    const int caps[3] = {0, 3, 2};
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    // each candidate: one warm-up launch, then the mean of two timed launches;
+    // the default (8x4, no cap, timed first) is kept unless beaten by 3%
+    float best = 1e30f, incumbent = 1e30f;
+    int best_tw = 8, best_cap = 0;
+    for (int i = 0; i < 4; ++i) {
+        set_tiling(ctx, tws[i]);
+        for (int j = 0; j < 3; ++j) {
+            ctx->ds.cap_per_sm = caps[j];
+            for (int rep = 0; rep < 3; ++rep) {
+                if (rep == 1) CK(cudaEventRecord(e0, st));
+                CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32,
+                                        nullptr, ctx->Ap, nullptr, nullptr, st));
+            }
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms *= 0.5f;
+            if (i == 0 && j == 0) incumbent = ms;
+            if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; }
+        }
+    }
+    if (!(best < 0.97f * incumbent)) { best = incumbent; best_tw = 8; best_cap = 0; }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    set_tiling(ctx, best_tw);
+    ctx->ds.cap_per_sm = best_cap;
+    if (out) {
+        out->tile_w = best_tw;
+        out->tile_h = 32 / best_tw;
+        out->ctas_per_sm = best_cap;
+        out->apply_ms = best;
+    }
+    return PERF_OK;
+}
+
 perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_block) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (n_block < 0 || n_block > ctx->ds.n_vox || (n_block > 0 && !blocks))

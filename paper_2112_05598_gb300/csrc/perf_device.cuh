@@ -38,6 +38,7 @@ struct DevScene {
     long long n_tiles;       // tile_w x tile_h pixel tiles over all cameras
     int tiles_x, tiles_y;
     int tile_w, tile_h;      // one warp per tile: tile_w * tile_h = 32
+    int cap_per_sm;          // resident-CTA cap of the scatter kernels (0 = none)
     const float* cams;       // n_cams x 16: c2w (12), focal, pad
     int max_samples;
     int jitter;
@@ -220,6 +221,50 @@ __device__ __forceinline__ float4 interp_grid(const T* x, const DevScene& sc, co
     const float4 c0 = lerp4(b00, b10, c.fy), c1 = lerp4(b01, b11, c.fy);
     return lerp4(c0, c1, c.fz);
 }
+
+// Coordinate along one axis of the voxel with parity bit `pa` in the 2x2x2
+// window whose lower corner is at `base`.
+__device__ __forceinline__ int par_coord(int base, int pa) { return base + ((pa ^ base) & 1); }
+
+// The 8 corner values of the current sample's cell, held between samples.
+// Slot p holds the window voxel whose coordinate parities are p, so when the
+// cell moves only the voxels that enter the window are loaded (consecutive
+// samples one voxel side apart share half their corners or more).
+template <typename T>
+struct Corners {
+    float4 v[8];
+    int b[3];
+
+    __device__ __forceinline__ void reset() { b[0] = b[1] = b[2] = -(1 << 28); }
+
+    __device__ __forceinline__ float4 interp(const T* __restrict__ x, const DevScene& sc,
+                                             const Cell& cl) {
+        const long long G = sc.G;
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const int nx = par_coord(cl.bx, p & 1), ny = par_coord(cl.by, (p >> 1) & 1),
+                      nz = par_coord(cl.bz, p >> 2);
+            const bool same = nx == par_coord(b[0], p & 1) && ny == par_coord(b[1], (p >> 1) & 1) &&
+                              nz == par_coord(b[2], p >> 2);
+            if (!same) v[p] = Store<T>::ld(x, ((long long)nz * G + ny) * G + nx);
+        }
+        b[0] = cl.bx; b[1] = cl.by; b[2] = cl.bz;
+        const bool sx = cl.bx & 1, sy = cl.by & 1, sz = cl.bz & 1;
+        const float wx[2] = {sx ? cl.fx : 1.0f - cl.fx, sx ? 1.0f - cl.fx : cl.fx};
+        const float wy[2] = {sy ? cl.fy : 1.0f - cl.fy, sy ? 1.0f - cl.fy : cl.fy};
+        const float wz[2] = {sz ? cl.fz : 1.0f - cl.fz, sz ? 1.0f - cl.fz : cl.fz};
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            const float W = wx[p & 1] * wy[(p >> 1) & 1] * wz[p >> 2];
+            acc.x = fmaf(W, v[p].x, acc.x);
+            acc.y = fmaf(W, v[p].y, acc.y);
+            acc.z = fmaf(W, v[p].z, acc.z);
+            acc.w = fmaf(W, v[p].w, acc.w);
+        }
+        return acc;
+    }
+};
 
 // Bilinear texels of one shell hit: 4 parameter-block indices and weights.
 struct ShellHit {

@@ -283,3 +283,21 @@ def test_empty_camera_set():
     out = empty(ctx.n_params) + 3.0
     ctx.vjp(x, x, out)
     assert np.all(host(out) == 0.0)
+
+
+def test_autotuned_tiling_keeps_results(small):
+    """The autotuner only changes the ray-to-warp tiling and the CTA cap:
+    A p and the image still match the oracle."""
+    import torch
+    from paper_2112_05598_gb300 import Context
+    sc, orc, x, rng = small["sc"], small["orc"], small["x"], small["rng"]
+    ctx = Context.from_scene(sc)
+    info = ctx.autotune(cuda_tensor(x))
+    assert info["tile_w"] * info["tile_h"] == 32 and info["apply_ms"] > 0
+    p = rng.normal(size=x.shape[0]).astype(np.float32)
+    ap = empty(ctx.n_params)
+    ctx.apply_normal(cuda_tensor(x), cuda_tensor(p), ap)
+    assert rel_l2(host(ap), orc.apply_A(x.astype(np.float64), p.astype(np.float64))) < TOL_FP32
+    rgb = empty(3 * ctx.n_rays)
+    ctx.render(cuda_tensor(x), rgb)
+    assert rel_l2(host(rgb), orc.render(x.astype(np.float64))[0]) < TOL_FP32
