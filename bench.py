@@ -61,8 +61,9 @@ def parse():
     ap.add_argument("--lpc-scenes", type=int, default=100)
     ap.add_argument("--lpc-steps", type=int, default=20)
     ap.add_argument("--lpc-epochs", type=int, default=2)
-    ap.add_argument("--lpc-gn", type=int, default=2)
-    ap.add_argument("--lpc-max-iter", type=int, default=150)
+    ap.add_argument("--lpc-gn", type=int, default=6)
+    ap.add_argument("--lpc-pcg", type=int, default=5)
+    ap.add_argument("--lpc-traj", type=int, default=60)
     return ap.parse_args()
 
 
@@ -264,6 +265,7 @@ def run_lpc(args, rank, world, local):
     loss1 = T.mean_loss(net, held)
     del systems, train, held
     # 2. evaluate on the ring workload
+    from paper_2112_05598_gb300 import block_jacobi
     sc = make_scene(args.workload, n_cams=args.cams)
     ctx = Context.from_scene(sc)
     hold = Context.from_scene(sc, c2w=sc.heldout_c2w, focal=sc.heldout_focal)
@@ -272,13 +274,65 @@ def run_lpc(args, rank, world, local):
     ctx.render(x_gt, target)
     htarget = torch.empty(3 * hold.n_rays, device=dev)
     hold.render(x_gt, htarget)
+    del x_gt
     F = torch.zeros(1, dtype=torch.float64, device=dev)
+    G, n, V = sc.G, sc.n_params, sc.G ** 3
+    # 2a. PCG residual trajectories on the first Gauss-Newton system
+    x = torch.from_numpy(sc.x0.copy()).to(dev)
+    r = torch.empty(3 * ctx.n_rays, device=dev)
+    ctx.residual(x, target, r, F)
+    d = torch.empty(n, device=dev)
+    g = torch.empty(n, device=dev)
+    ctx.diag_jtj(x, d, r, g)
+    del r
+    d2 = torch.empty(n, device=dev)
+    cross = torch.empty(4 * V, device=dev)
+    ctx.diag_cross(x, d2, cross)
+    del d2
+    blocks = torch.empty(16 * V, device=dev)
+    traj = {}
+    t_blocks = {}
+    for name in ("jacobi", "learned", "block_jacobi"):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        if name == "learned":
+            feat = torch.empty(16 * V, dtype=torch.bfloat16, device=dev)
+            net.features(G, x, g, d, cross, feat)
+            net.infer(G, feat, d, blocks)
+            del feat
+        elif name == "block_jacobi":
+            block_jacobi(G, d, cross, blocks)
+        e1.record()
+        torch.cuda.synchronize()
+        t_blocks[name] = e0.elapsed_time(e1)
+        if name == "jacobi":
+            ctx.set_options(precond=PERF_PRECOND_JACOBI, pcg_iters=args.lpc_traj, pcg_fixed=1)
+        else:
+            ctx.set_blocks(blocks, V)
+            ctx.set_options(precond=PERF_PRECOND_BLOCK4, pcg_iters=args.lpc_traj, pcg_fixed=1)
+        ctx.pcg_begin(g, d)
+        rel = []
+        e0.record()
+        for _ in range(args.lpc_traj):
+            ctx.pcg_step(x)
+            info = ctx.pcg_result()
+            rel.append(float(np.sqrt(info["R"] / info["R0"])))
+        e1.record()
+        torch.cuda.synchronize()
+        first = {f"{t:g}": next((k + 1 for k, v in enumerate(rel) if v < t), None)
+                 for t in (1e-1, 1e-2, 1e-3)}
+        traj[name] = {"rel_residual": rel, "iters_to": first,
+                      "ms_per_iter": e0.elapsed_time(e1) / args.lpc_traj,
+                      "ms_preconditioner_setup": t_blocks[name]}
+    del blocks, cross, d, g
+    ctx.set_blocks(None, 0)
+    # 2b. Gauss-Newton with few PCG iterations per step: time to PSNR
     results = {}
     for name, pc in (("jacobi", PERF_PRECOND_JACOBI), ("learned", PERF_PRECOND_BLOCK4),
                      ("block_jacobi", PERF_PRECOND_BLOCK_JACOBI)):
         x = torch.from_numpy(sc.x0.copy()).to(dev)
-        ctx.set_options(pcg_iters=args.lpc_max_iter, pcg_fixed=0, pcg_eps_rel=1e-3,
-                        pcg_stall=1e30, precond=pc)
+        ctx.set_options(pcg_iters=args.lpc_pcg, pcg_fixed=1, precond=pc)
         ctx.set_lpc(net if pc == PERF_PRECOND_BLOCK4 else None)
         hold.residual(x, htarget, None, F)
         curve = [(0.0, _psnr_from_F(float(F.item()), hold.n_rays))]
@@ -289,25 +343,27 @@ def run_lpc(args, rank, world, local):
             t_acc += st["ms"] / 1000.0
             hold.residual(x, htarget, None, F)
             curve.append((t_acc, _psnr_from_F(float(F.item()), hold.n_rays)))
-            steps.append({"pcg_iters": st["pcg_iters"], "exit": st["pcg_exit"], "ms": st["ms"],
-                          "F_after": st["F_after"], "fallback": st["precond_fallback"]})
+            steps.append({"rel_residual": float(np.sqrt(st["R"] / st["R0"])) if st["R0"] > 0 else None,
+                          "ms": st["ms"], "F_after": st["F_after"], "gamma": st["gamma"],
+                          "fallback": st["precond_fallback"]})
         results[name] = {"steps": steps, "psnr_curve": curve}
     target_psnr = results["jacobi"]["psnr_curve"][-1][1] - 0.1
 
     def time_to(curve):
-        for t, p in curve:
-            if p >= target_psnr:
+        for t, pv in curve:
+            if pv >= target_psnr:
                 return t
         return None
-    line = {"metric": "PCG iterations to relative residual 1e-3 and time-to-PSNR, learned vs Jacobi",
+    line = {"metric": "PCG iterations to relative residual and time-to-PSNR, learned vs Jacobi",
             "workload": f"{args.workload}: {sc.G}^3, {sc.n_shells} shells {sc.env_h}x{sc.env_w}, "
                         f"{sc.n_cams} cameras {sc.width}x{sc.height} ring, background shell sigma 10",
             "training": {"systems": n_train_scenes * args.lpc_steps, "scenes": n_train_scenes,
                          "epochs": args.lpc_epochs, "log_s": t_log, "train_s": t_train,
                          "held_out_probe_loss_identity": loss0, "held_out_probe_loss_trained": loss1},
-            "target_psnr_db": target_psnr,
-            "time_to_psnr_s": {k: time_to(v["psnr_curve"]) for k, v in results.items()},
-            "results": results}
+            "first_system_pcg": traj,
+            "gn": {"pcg_iters_per_step": args.lpc_pcg, "target_psnr_db": target_psnr,
+                   "time_to_psnr_s": {k: time_to(v["psnr_curve"]) for k, v in results.items()},
+                   "runs": results}}
     print(json.dumps(line), flush=True)
 
 

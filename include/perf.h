@@ -287,7 +287,9 @@ perf_status perf_lpc_infer(perf_lpc* lpc, int32_t G, const void* feat, const flo
 perf_status perf_lpc_dscale(int32_t G, const float* diag, const float* in, float* out,
                             uint8_t* mask_out, void* stream);
 /* Exact block-Jacobi: blocks_out = inverse of each voxel's 4x4 block of J^T J
- * (Jacobi where a block is unobserved or singular). */
+ * (closed form through the Schur complement q of the opacity entry; Jacobi
+ * where the block is unobserved or numerically singular, q <= 1e-4 times the
+ * opacity diagonal). */
 perf_status perf_block_jacobi(int32_t G, const float* diag, const float* cross,
                               float* blocks_out, void* stream);
 

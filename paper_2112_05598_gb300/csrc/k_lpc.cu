@@ -384,11 +384,15 @@ __global__ void k_f32_to_bf16(const float* __restrict__ a, __nv_bfloat16* __rest
     if (i < n) b[i] = __float2bfloat16(a[i]);
 }
 
-// Exact block-Jacobi: invert each voxel's 4x4 diagonal block of J^T J,
-//   [[a2, 0, 0, c0], [0, a2, 0, c1], [0, 0, a2, c2], [c0, c1, c2, s2]]
-// (a2 = diag colour entry, s2 = diag opacity entry, c_k = cross terms), by
-// Gauss-Jordan in FP64; a voxel with an unobserved or singular block falls
-// back to Jacobi (1/d_j, 0 for d_j <= floor).
+// Exact block-Jacobi: invert each voxel's 4x4 diagonal block of J^T J.  A
+// colour parameter c_k enters only residual k, so the block is
+//   [[a I_3, c], [c^T, s]],   a = colour diagonal (equal for r, g, b),
+//   c_k = sum_rows (dr/dc_k)(dr/dsigma),  s = opacity diagonal,
+// with inverse [[I/a + c c^T / (a^2 q), -c / (a q)], [-c^T / (a q), 1 / q]],
+// q = s - c.c / a (Schur complement), evaluated in FP64.  Where the block is
+// numerically singular (q <= 1e-4 s: the rays through the voxel have nearly
+// proportional derivatives) or unobserved, the voxel falls back to Jacobi
+// (1/d_j, 0 for d_j <= floor).
 __global__ void __launch_bounds__(256) k_block_jacobi(const float4* __restrict__ diag,
                                                      const float4* __restrict__ cross,
                                                      float* __restrict__ blocks, long long V,
@@ -397,34 +401,26 @@ __global__ void __launch_bounds__(256) k_block_jacobi(const float4* __restrict__
          v += (long long)gridDim.x * blockDim.x) {
         const float4 d4 = diag[v], c4 = cross[v];
         const double d[4] = {d4.x, d4.y, d4.z, d4.w};
-        double M[4][8];
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 8; ++j) M[i][j] = (j == i + 4) ? 1.0 : 0.0;
-        for (int i = 0; i < 4; ++i) M[i][i] = d[i];
-        M[0][3] = M[3][0] = c4.x;
-        M[1][3] = M[3][1] = c4.y;
-        M[2][3] = M[3][2] = c4.z;
-        bool ok = d[0] > floor_d && d[1] > floor_d && d[2] > floor_d && d[3] > floor_d;
-        for (int c = 0; ok && c < 4; ++c) {
-            int piv = c;
-            for (int r = c + 1; r < 4; ++r)
-                if (fabs(M[r][c]) > fabs(M[piv][c])) piv = r;
-            if (!(fabs(M[piv][c]) > 1e-300)) { ok = false; break; }
-            if (piv != c)
-                for (int j = 0; j < 8; ++j) { const double t = M[c][j]; M[c][j] = M[piv][j]; M[piv][j] = t; }
-            const double inv = 1.0 / M[c][c];
-            for (int j = 0; j < 8; ++j) M[c][j] *= inv;
-            for (int r = 0; r < 4; ++r) {
-                if (r == c) continue;
-                const double f = M[r][c];
-                for (int j = 0; j < 8; ++j) M[r][j] -= f * M[c][j];
-            }
-        }
+        const double c[3] = {c4.x, c4.y, c4.z};
+        const double a = d[0], sv = d[3];
+        const double q = (a > floor_d) ? sv - (c[0] * c[0] + c[1] * c[1] + c[2] * c[2]) / a : 0.0;
+        const bool ok = d[0] > floor_d && d[1] > floor_d && d[2] > floor_d && d[3] > floor_d &&
+                        q > 1e-4 * sv;
         float* B = blocks + v * 16;
-        for (int i = 0; i < 4; ++i)
-            for (int j = 0; j < 4; ++j)
-                B[i * 4 + j] = ok ? (float)M[i][j + 4]
-                                  : ((i == j && d[i] > floor_d) ? (float)(1.0 / d[i]) : 0.0f);
+        if (ok) {
+            for (int i = 0; i < 3; ++i)
+                for (int j = 0; j < 3; ++j)
+                    B[i * 4 + j] = (float)((i == j ? 1.0 / a : 0.0) + c[i] * c[j] / (a * a * q));
+            for (int i = 0; i < 3; ++i) {
+                B[i * 4 + 3] = (float)(-c[i] / (a * q));
+                B[12 + i] = (float)(-c[i] / (a * q));
+            }
+            B[15] = (float)(1.0 / q);
+        } else {
+            for (int i = 0; i < 4; ++i)
+                for (int j = 0; j < 4; ++j)
+                    B[i * 4 + j] = (i == j && d[i] > floor_d) ? (float)(1.0 / d[i]) : 0.0f;
+        }
     }
 }
 
