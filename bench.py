@@ -44,6 +44,42 @@ METRIC = "PCG iters/s"
 # counted as special-function work, not FLOP).
 FLOP_PER_SAMPLE_APPLY = 271
 
+# DRAM traffic of one A p launch, from the ncu capture summarised in this
+# file; it applies only while the kernel sources hash to the recorded value.
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "apply_traffic_scale128.md")
+KERNEL_SOURCES = ("paper_2112_05598_gb300/csrc/k_march.cu",
+                  "paper_2112_05598_gb300/csrc/perf_device.cuh")
+
+
+def kernel_source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
+def recorded_traffic(kernel, workload):
+    """Bytes per launch recorded for `kernel` on `workload`, or None when the
+    record is missing or was taken on other kernel sources."""
+    try:
+        with open(TRAFFIC_PROFILE) as fh:
+            kv = {}
+            for line in fh:
+                if ":" in line and line.startswith("- "):
+                    k, v = line[2:].split(":", 1)
+                    kv[k.strip()] = v.strip().strip("`")
+    except OSError:
+        return None
+    if (kv.get("kernel") != kernel or kv.get("workload") != workload
+            or kv.get("source_sha256") != kernel_source_hash()):
+        return None
+    try:
+        return int(kv["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
+
 
 def parse():
     ap = argparse.ArgumentParser()
@@ -531,6 +567,9 @@ def run_ours(args, rank, world, local):
     apply_ms = tm["apply"]["ms"] / max(tm["apply"]["launches"], 1)
     achieved = FLOP_PER_SAMPLE_APPLY * samples / (apply_ms / 1000.0) / 1e12
     per_step = {k: v["ms"] / args.steps for k, v in tm.items()}
+    apply_kernel = ("k_scatter<bf16,bf16,1> (A p)" if bf else
+                    "k_scatter<PairF32,PairF32,1> (A p, paired x/p records)"
+                    if tuning.get("paired") else "k_scatter<float,float,1> (A p)")
 
     if rank != 0:
         return
@@ -551,9 +590,10 @@ def run_ours(args, rank, world, local):
         "kernel_ms_per_step": per_step,
         "apply_ms_per_launch": apply_ms,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": None,
-                     "kernel": ("k_scatter<bf16,bf16,1> (A p)" if bf else
-                                "k_scatter<float,float,1> (A p)"),
+                     "frac": achieved / fp32_peak,
+                     "traffic": (recorded_traffic(apply_kernel, args.workload)
+                                 if args.cams is None else None),
+                     "kernel": apply_kernel,
                      "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
                                     f"(max SM clock, {peak_src})"},
         "e2e": {"value": e2e_value, "unit": METRIC,

@@ -132,11 +132,14 @@ typedef struct {
     int64_t launches[PERF_T_COUNT];
 } perf_timing;
 
-/* Ray-tile shape and resident-CTA cap chosen by an autotuner. */
+/* Ray-tile shape, resident-CTA cap and parameter layout chosen by an
+ * autotuner. */
 typedef struct {
     int32_t tile_w, tile_h;   /* pixels per warp tile (tile_w * tile_h = 32) */
     int32_t ctas_per_sm;      /* 0 = as many as fit */
     float apply_ms;           /* time of the fastest A p launch */
+    int32_t paired;           /* 1: perf_gn_solve's A p reads x and p from paired
+                                 32-byte records (FP32 scenes); 0: two arrays */
 } perf_tuning;
 
 /* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
@@ -226,8 +229,10 @@ perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_bl
  * p = x) over tile shapes 8x4, 4x8, 16x2, 32x1 and resident-CTA caps
  * {all, 3, 2} (two timed launches each), keeps the fastest for every later
  * ray march of the context unless the default (8x4, no cap) is within 3%,
- * and reports the choice in *out (HOST, may be NULL).  Uses the PCG
- * workspace; synchronises. */
+ * then, for FP32 scenes, times A p from separate x and p arrays against the
+ * paired records that perf_gn_solve uses by default and keeps the separate
+ * arrays only when 3% faster.  Reports the choice in *out (HOST, may be
+ * NULL).  Uses the PCG workspace; synchronises. */
 perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
                           void* stream);
 perf_status perf_set_lpc(perf_ctx* ctx, perf_lpc* lpc);
@@ -300,8 +305,9 @@ perf_status perf_block_jacobi(int32_t G, const float* diag, const float* cross,
  * perf_batch_param_offset / perf_batch_ray_offset (scene = n_scenes gives the
  * totals).  Every ray march is one persistent launch taking (scene, pixel
  * tile) items from a work queue; each scene has its own PCG scalars and its
- * own line search; the fixed-iteration PCG loop is captured once as a CUDA
- * graph (on an internal stream) and replayed each Gauss-Newton step.
+ * own line search; the PCG loop of opts.pcg_iters iterations is captured
+ * once as a CUDA graph (on an internal stream) and replayed each
+ * Gauss-Newton step.
  * scenes and cams are HOST arrays of n_scenes entries (cameras copied);
  * validation as perf_create; dtype must be PERF_F32. */
 typedef struct perf_batch perf_batch;
@@ -321,9 +327,12 @@ perf_status perf_batch_residual(perf_batch* b, const float* x, const float* targ
  * {all, 3, 2}, keeps the fastest (used by every later launch) and reports it
  * in *out (HOST, may be NULL).  Synchronises. */
 perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out, void* stream);
-/* n_steps Gauss-Newton steps for every scene (opts.pcg_iters fixed PCG
- * iterations, Algorithm 3 per scene, accept per scene).  stats (HOST, may be
- * NULL) receives n_steps * n_scenes records, step-major.  Synchronises. */
+/* n_steps Gauss-Newton steps for every scene (Algorithm 2 per scene: with
+ * opts.pcg_fixed exactly opts.pcg_iters iterations, else at most that many
+ * with the exit tests of perf_options, a scene's device exit flag making
+ * every later A p launch of the captured loop skip its rays; Algorithm 3 per
+ * scene, accept per scene).  stats (HOST, may be NULL) receives
+ * n_steps * n_scenes records, step-major.  Synchronises. */
 perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, int32_t n_steps,
                                 perf_gn_stats* stats, void* stream);
 

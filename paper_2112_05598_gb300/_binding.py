@@ -65,7 +65,8 @@ TIMING_KINDS = ("apply", "forward", "diag", "vector", "precond")
 
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("apply_ms", ctypes.c_float)]
+                ("ctas_per_sm", ctypes.c_int32), ("apply_ms", ctypes.c_float),
+                ("paired", ctypes.c_int32)]
 
 
 class GNStats(ctypes.Structure):
@@ -336,7 +337,8 @@ class Context:
         t = Tuning()
         self._check(self.lib.perf_autotune(self.h, _ptr(x), _ptr(p), ctypes.byref(t),
                                            _stream(stream)), "autotune")
-        return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms)
+        return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms,
+                    paired=t.paired)
 
     def set_lpc(self, lpc):
         self._lpc = lpc
@@ -453,7 +455,8 @@ class Batch:
         for k in range(int(n_steps)):
             out.append([dict(F_before=s.F_before, F_after=s.F_after, gamma=s.gamma,
                              accepted=bool(s.accepted), ls_evals=s.ls_evals,
-                             pcg_iters=s.pcg.iters, ms=s.ms)
+                             pcg_iters=s.pcg.iters, pcg_exit=EXIT.get(s.pcg.exit_reason),
+                             ms=s.ms)
                         for s in stats[k * self.n:(k + 1) * self.n]])
         return out
 

@@ -53,6 +53,12 @@ constexpr int kWarps = kThreads / 32;
 #ifndef PERF_MIN_CTAS
 #define PERF_MIN_CTAS 1
 #endif
+// The A p kernels ask for 5 resident CTAs per SM (96 registers; a few spill
+// slots): on GB300 at 128^3, 100 cameras, 167 ms per launch against 175 ms
+// with the allocator unconstrained (150 registers, 3 CTAs) and 169 ms at 4.
+#ifndef PERF_APPLY_MIN_CTAS
+#define PERF_APPLY_MIN_CTAS 5
+#endif
 
 // Corner interpolation with (Corners) or without (plain gathers) reuse.
 template <typename T, bool CACHE>
@@ -198,6 +204,31 @@ __device__ __forceinline__ void tangent(const DevScene& sc, const T* __restrict_
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
         if (shell_lookup(sc, R, q, hs)) tang_step(s, interp_shell(x, hs), interp_shell(p, hs), 1.0f);
+    }
+}
+
+// The same sweep from paired x / p storage (one 256-bit load per corner).
+__device__ __forceinline__ void tangent(const DevScene& sc, const PairF32* __restrict__ xp,
+                                        const PairF32* __restrict__, const Ray& R, long long ray,
+                                        Tang& s) {
+    s.T = 1.0f; s.Td = 0.0f;
+    s.H[0] = s.H[1] = s.H[2] = 0.0f;
+    s.J[0] = s.J[1] = s.J[2] = 0.0f;
+    s.V.hi = 0.0f; s.V.lo = 0.0f;
+    const float dbar = R.delta * sc.halfG;
+    for (int k = 0; k < R.K; ++k) {
+        const Cell cl = sample_cell(sc, R, ray, k);
+        float4 a, q;
+        interp_grid_pair(xp, sc, cl, a, q);
+        tang_step(s, a, q, dbar);
+    }
+    for (int k = 0; k < sc.S; ++k) {
+        ShellHit hs;
+        if (shell_lookup(sc, R, k, hs)) {
+            float4 a, q;
+            interp_shell_pair(xp, hs, a, q);
+            tang_step(s, a, q, 1.0f);
+        }
     }
 }
 
@@ -502,7 +533,8 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
 }
 
 template <typename T, typename TP, int MODE, typename TV>
-__global__ void __launch_bounds__(kThreads, PERF_MIN_CTAS) k_scatter(DevScene sc, const T* __restrict__ x,
+__global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PERF_MIN_CTAS)
+    k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
                                                       const TV* __restrict__ v,
                                                       float* __restrict__ out,
@@ -585,9 +617,12 @@ __global__ void __launch_bounds__(kThreads) k_forward_batch(const BatchItem* __r
 }
 
 // mode 1: A p (+ p^T A p per scene into pap[scene * pap_stride]),
-// mode 2: diag (+ grad with v = residuals).
+// mode 2: diag (+ grad with v = residuals).  pcg (may be null): per-scene
+// Algorithm 2 state; tiles of scenes whose solve has exited are skipped (the
+// early exit of a graph-captured PCG loop).
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_scatter_batch(const BatchItem* __restrict__ items,
+__global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PERF_MIN_CTAS)
+    k_scatter_batch(const BatchItem* __restrict__ items,
                                                             const long long* __restrict__ start,
                                                             int n, long long total,
                                                             unsigned long long* counter,
@@ -596,7 +631,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter_batch(const BatchItem* __r
                                                             const float* __restrict__ v,
                                                             float* __restrict__ out,
                                                             float* __restrict__ out2, double* pap,
-                                                            int pap_stride) {
+                                                            int pap_stride,
+                                                            const PcgScalars* __restrict__ pcg) {
     __shared__ BatchItem s_items[kBatchSmem];
     const BatchItem* it = stage_items(items, n, s_items);
     const int lane = threadIdx.x & 31;
@@ -604,6 +640,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_batch(const BatchItem* __r
         int sidx = 0;
         const long long tile = batch_next(counter, total, start, n, lane, sidx);
         if (tile < 0) break;
+        if (pcg && pcg[sidx].done) continue;
         const BatchItem& b = it[sidx];
         double acc = 0.0;
         scatter_tile<float, float, MODE, float>(b.sc, x + b.x_off, p ? p + b.x_off : nullptr,
@@ -738,6 +775,12 @@ cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* 
     return launch_scatter_t<float, float, 2, float>(sc, x, p, v, out, out2, pap, st, out3);
 }
 
+// A p from paired x / p storage (FP32 scenes).
+cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
+                              cudaStream_t st) {
+    return launch_scatter_t<PairF32, PairF32, 1, float>(sc, xp, xp, nullptr, out, nullptr, pap, st);
+}
+
 // ------------------------------------------------------ batched launchers
 
 static int batch_blocks(const void* fn, int cap_per_sm) {
@@ -778,17 +821,17 @@ cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start,
                                  long long total, unsigned long long* counter, const float* x,
                                  const float* p, const float* v, float* out, float* out2,
                                  double* pap, int pap_stride, int mode, int cap_per_sm,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const PcgScalars* pcg) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess || total == 0) return e;
     if (mode == 1) {
         auto fn = k_scatter_batch<1>;
         fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
-            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride);
+            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg);
     } else {
         auto fn = k_scatter_batch<2>;
         fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
-            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride);
+            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg);
     }
     count_launch();
     return cudaGetLastError();

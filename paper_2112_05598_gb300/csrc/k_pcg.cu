@@ -103,10 +103,14 @@ __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* y, long long v, floa
     reinterpret_cast<uint2*>(y)[v] = u;
 }
 
-__device__ __forceinline__ void store_p(float4* p32, __nv_bfloat16* p16, long long v, const D4& p) {
+// pxp (may be null): paired x / p records (two float4 each); p goes to the
+// second half of record v.
+__device__ __forceinline__ void store_p(float4* p32, __nv_bfloat16* p16, float4* pxp, long long v,
+                                        const D4& p) {
     const float4 f = make_float4((float)p.x, (float)p.y, (float)p.z, (float)p.w);
     p32[v] = f;
     if (p16) store_bf16x4(p16, v, f);
+    if (pxp) pxp[2 * v + 1] = f;
 }
 
 __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const long long* seg,
@@ -115,7 +119,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const lon
                                                         const float4* __restrict__ B, long long n_block,
                                                         double* delta, double* rho, double* p,
                                                         float4* p32, __nv_bfloat16* p16, float4* Ap,
-                                                        PcgScalars* s) {
+                                                        PcgScalars* s, float4* pxp) {
     s += blockIdx.y;
     double aR = 0.0, aRz = 0.0;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -125,7 +129,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const lon
         const D4 z = precond(r, v, d4, B, n_block);
         st4(rho, v, r);
         st4(p, v, z);
-        store_p(p32, p16, v, z);
+        store_p(p32, p16, pxp, v, z);
         st4(delta, v, D4{0.0, 0.0, 0.0, 0.0});
         Ap[v] = zero;
         aR += dot4(r, r);
@@ -233,7 +237,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const long 
                                                       const float4* __restrict__ d4,
                                                       const float4* __restrict__ B, long long n_block,
                                                       double* p, float4* p32, __nv_bfloat16* p16,
-                                                      float4* Ap, const PcgScalars* s) {
+                                                      float4* Ap, const PcgScalars* s, float4* pxp) {
     s += blockIdx.y;
     if (s->done) return;
     const double beta = s->beta;
@@ -244,8 +248,18 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const long 
         pv.x = fma(beta, pv.x, z.x); pv.y = fma(beta, pv.y, z.y);
         pv.z = fma(beta, pv.z, z.z); pv.w = fma(beta, pv.w, z.w);
         st4(p, v, pv);
-        store_p(p32, p16, v, pv);
+        store_p(p32, p16, pxp, v, pv);
         Ap[v] = zero;
+    }
+}
+
+// Paired records: xp[v] = (x[v], p[v]) (p may be null: the p half is kept).
+__global__ void __launch_bounds__(kVThreads) k_pair_pack(long long nb, const float4* __restrict__ x,
+                                                        const float4* __restrict__ p, float4* xp) {
+    for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
+         v += (long long)gridDim.x * blockDim.x) {
+        xp[2 * v] = x[v];
+        if (p) xp[2 * v + 1] = p[v];
     }
 }
 
@@ -329,14 +343,14 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, l
                                  double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                                  PcgScalars* s, int max_iter, int fixed, double eps_rel,
                                  double stall, const float* blocks, long long n_block,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, float* pxp) {
     const long long nb = n / 4;
     cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars) * (size_t)(n_seg > 0 ? n_seg : 1), st);
     if (e != cudaSuccess) return e;
     if (nb > 0) {
         k_pcg_begin<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
             nb, seg, CF4(grad), CF4(diag), CF4(blocks), n_block, delta, rho, p, F4(p32), p16,
-            F4(Ap), s);
+            F4(Ap), s, F4(pxp));
         count_launch();
     }
     const int ns = n_seg > 1 ? n_seg : 1;
@@ -348,9 +362,9 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, l
 cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
                              double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                              PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
-                             const float* blocks, long long n_block, cudaStream_t st) {
+                             const float* blocks, long long n_block, cudaStream_t st, float* pxp) {
     return launch_pcg_begin_seg(n, 1, nullptr, n / 4, grad, diag, delta, rho, p, p32, p16, Ap, s,
-                                max_iter, fixed, eps_rel, stall, blocks, n_block, st);
+                                max_iter, fixed, eps_rel, stall, blocks, n_block, st, pxp);
 }
 
 cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
@@ -385,11 +399,11 @@ cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st) { return launch_pc
 cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                                const double* rho, const float* diag, const float* blocks,
                                long long n_block, double* p, float* p32, __nv_bfloat16* p16,
-                               float* Ap, PcgScalars* s, cudaStream_t st) {
+                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_pcg_dir<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
-            nb, seg, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s);
+            nb, seg, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s, F4(pxp));
         count_launch();
     }
     return cudaGetLastError();
@@ -397,9 +411,9 @@ cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, lon
 
 cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
                            long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                           PcgScalars* s, cudaStream_t st) {
+                           PcgScalars* s, cudaStream_t st, float* pxp) {
     return launch_pcg_dir_seg(n, 1, nullptr, n / 4, rho, diag, blocks, n_block, p, p32, p16, Ap, s,
-                              st);
+                              st, pxp);
 }
 
 cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,
@@ -429,6 +443,16 @@ cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaSt
     const long long nb = n / 4;
     if (nb > 0) {
         k_to_bf16<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), y);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pair_pack(long long n, const float* x, const float* p, float* xp,
+                             cudaStream_t st) {
+    const long long nb = n / 4;
+    if (nb > 0) {
+        k_pair_pack<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), CF4(p), F4(xp));
         count_launch();
     }
     return cudaGetLastError();

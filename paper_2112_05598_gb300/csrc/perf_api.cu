@@ -43,6 +43,8 @@ struct perf_ctx {
     double* rho = nullptr;
     double* p = nullptr;
     float* p32 = nullptr;
+    float* xp = nullptr;        // paired (x, p) records for A p (FP32 scenes)
+    bool pair = true;           // Gauss-Newton A p reads the paired records
     float* Ap = nullptr;
     float* x_trial = nullptr;
     __nv_bfloat16* x16 = nullptr;
@@ -115,6 +117,7 @@ perf_status ensure_pcg(perf_ctx* ctx) {
     CK(alloc(&ctx->p32, ctx->n));
     CK(alloc(&ctx->Ap, ctx->n));
     if (ctx->scene.dtype == PERF_BF16) CK(alloc(&ctx->p16, ctx->n));
+    else CK(alloc(&ctx->xp, 2 * ctx->n));
     return PERF_OK;
 }
 
@@ -264,7 +267,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->p32, ctx->Ap, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->p32, ctx->xp, ctx->Ap, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -386,20 +389,25 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
 namespace {
 
 // One Algorithm 2 iteration on the context workspace with diagonal `diag`
-// and block preconditioner B (null: Jacobi).
-perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const float* B, cudaStream_t st) {
+// and block preconditioner B (null: Jacobi).  paired: A p reads the paired
+// records ctx->xp, whose x half holds x (FP32 scenes).
+perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const float* B, cudaStream_t st,
+                     bool paired = false) {
     const bool bf = ctx->scene.dtype == PERF_BF16;
     const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p32);
     t_begin(ctx, PERF_T_APPLY, st);
-    CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32, nullptr,
-                            ctx->Ap, nullptr, &ctx->s->pAp, st));
+    if (paired)
+        CK(perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, &ctx->s->pAp, st));
+    else
+        CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32,
+                                nullptr, ctx->Ap, nullptr, &ctx->s->pAp, st));
     t_end(ctx, PERF_T_APPLY, st);
     t_begin(ctx, PERF_T_VECTOR, st);
     CK(perf::launch_pcg_update(ctx->n, ctx->delta, ctx->rho, ctx->p, ctx->Ap, diag, B, ctx->n_block,
                                ctx->s, st));
     CK(perf::launch_pcg_finish(ctx->s, st));
     CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p32, ctx->p16,
-                            ctx->Ap, ctx->s, st));
+                            ctx->Ap, ctx->s, st, paired ? ctx->xp : nullptr));
     t_end(ctx, PERF_T_VECTOR, st);
     return PERF_OK;
 }
@@ -513,12 +521,15 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
             nB = ctx->n_block;
         }
         int fallback = 0;
+        const bool paired = !bf && ctx->pair;
+        if (paired) CK(perf::launch_pair_pack(ctx->n, x, nullptr, ctx->xp, st));
         for (int attempt = 0; attempt < 2; ++attempt) {
             CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
                                       ctx->p32, ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
-                                      o.pcg_eps_rel, o.pcg_stall, B, nB, st));
+                                      o.pcg_eps_rel, o.pcg_stall, B, nB, st,
+                                      paired ? ctx->xp : nullptr));
             for (int k = 0; k < o.pcg_iters; ++k) {
-                ps = pcg_iter(ctx, xm, ctx->diag, B, st);
+                ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired);
                 if (ps != PERF_OK) return ps;
                 if (!o.pcg_fixed) {
                     int done = 0;
@@ -634,43 +645,66 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     void* pbuf = bf ? static_cast<void*>(ctx->p16) : static_cast<void*>(ctx->p32);
     CK(cudaMemcpyAsync(pbuf, p ? p : x, (bf ? 2 : 4) * (size_t)ctx->n, cudaMemcpyDeviceToDevice, st));
     const void* pp = pbuf;
+    if (!bf) CK(perf::launch_pair_pack(ctx->n, static_cast<const float*>(x), ctx->p32, ctx->xp, st));
+    auto apply = [&](bool paired) -> cudaError_t {
+        return paired ? perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, nullptr, st)
+                      : perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp,
+                                             bf ? PERF_BF16 : PERF_F32, nullptr, ctx->Ap, nullptr,
+                                             nullptr, st);
+    };
     const int tws[4] = {8, 4, 16, 32};
     const int caps[3] = {0, 3, 2};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    // each candidate: one warm-up launch, then the mean of two timed launches;
-    // the default (8x4, no cap, timed first) is kept unless beaten by 3%
+    // each candidate: one warm-up launch, then the mean of two timed launches
+    auto time_apply = [&](bool paired, float& ms) -> cudaError_t {
+        cudaError_t e = cudaSuccess;
+        for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+            if (rep == 1) e = cudaEventRecord(e0, st);
+            if (e == cudaSuccess) e = apply(paired);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+        if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        ms *= 0.5f;
+        return e;
+    };
+    // tile shape and CTA cap with the default layout (paired for FP32); the
+    // default (8x4, no cap, timed first) is kept unless beaten by 3%
+    const bool pair0 = !bf;
     float best = 1e30f, incumbent = 1e30f;
     int best_tw = 8, best_cap = 0;
     for (int i = 0; i < 4; ++i) {
         set_tiling(ctx, tws[i]);
         for (int j = 0; j < 3; ++j) {
             ctx->ds.cap_per_sm = caps[j];
-            for (int rep = 0; rep < 3; ++rep) {
-                if (rep == 1) CK(cudaEventRecord(e0, st));
-                CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32,
-                                        nullptr, ctx->Ap, nullptr, nullptr, st));
-            }
-            CK(cudaEventRecord(e1, st));
-            CK(cudaEventSynchronize(e1));
             float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            ms *= 0.5f;
+            CK(time_apply(pair0, ms));
             if (i == 0 && j == 0) incumbent = ms;
             if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; }
         }
     }
     if (!(best < 0.97f * incumbent)) { best = incumbent; best_tw = 8; best_cap = 0; }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     set_tiling(ctx, best_tw);
     ctx->ds.cap_per_sm = best_cap;
+    // then the layout: separate x and p arrays replace the paired records
+    // only when 3% faster
+    bool pair = pair0;
+    if (!bf) {
+        float ms = 0.f;
+        CK(time_apply(false, ms));
+        if (ms < 0.97f * best) { best = ms; pair = false; }
+    }
+    ctx->pair = pair;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
     if (out) {
         out->tile_w = best_tw;
         out->tile_h = 32 / best_tw;
         out->ctas_per_sm = best_cap;
         out->apply_ms = best;
+        out->paired = pair ? 1 : 0;
     }
     return PERF_OK;
 }

@@ -105,15 +105,20 @@ perf_status apply_tiling(perf_batch* b, int tw) {
     return PERF_OK;
 }
 
-cudaError_t apply_launch(perf_batch* b, const float* x, const float* p32, cudaStream_t st) {
+// A p for every scene; with skip_done, scenes whose PCG has exited are
+// skipped (their device flag is read by the kernel, so a captured loop of
+// max_iter iterations stops working on a scene once it converges).
+cudaError_t apply_launch(perf_batch* b, const float* x, const float* p32, cudaStream_t st,
+                         bool skip_done = false) {
     return perf::launch_scatter_batch(b->d_items, b->d_start, b->n, b->total_tiles, b->counter, x,
                                       p32, nullptr, b->Ap, nullptr, &b->s[0].pAp,
-                                      (int)(sizeof(PcgScalars) / sizeof(double)), 1, b->cap, st);
+                                      (int)(sizeof(PcgScalars) / sizeof(double)), 1, b->cap, st,
+                                      skip_done ? b->s : nullptr);
 }
 
 // One Algorithm 2 iteration for every scene.
 cudaError_t pcg_iter(perf_batch* b, cudaStream_t st) {
-    cudaError_t e = apply_launch(b, b->x_work, b->p32, st);
+    cudaError_t e = apply_launch(b, b->x_work, b->p32, st, true);
     if (e == cudaSuccess)
         e = perf::launch_pcg_update_seg(b->n_params, b->n, b->d_seg, b->max_seg, b->delta, b->rho,
                                         b->p, b->Ap, b->diag, nullptr, 0, b->s, st);
@@ -336,6 +341,7 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
         out->tile_h = 32 / best_tw;
         out->ctas_per_sm = best_cap;
         out->apply_ms = best;
+        out->paired = 0;
     }
     return PERF_OK;
 }
@@ -343,10 +349,6 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
 perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, int32_t n_steps,
                                 perf_gn_stats* stats, void* stream) {
     if (!b || !x || !target || n_steps < 0) return PERF_ERR_INVALID_ARG;
-    if (!b->opts.pcg_fixed) {
-        b->err = "batched solve runs a fixed number of PCG iterations (pcg_fixed = 1)";
-        return PERF_ERR_UNSUPPORTED;
-    }
     cudaStream_t st = S(stream);
     const perf_options& o = b->opts;
     const int n = b->n;
@@ -371,7 +373,8 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
                                       b->cap, st));
         BK(perf::launch_pcg_begin_seg(b->n_params, n, b->d_seg, b->max_seg, b->grad, b->diag,
                                       b->delta, b->rho, b->p, b->p32, nullptr, b->Ap, b->s,
-                                      o.pcg_iters, 1, o.pcg_eps_rel, o.pcg_stall, nullptr, 0, st));
+                                      o.pcg_iters, o.pcg_fixed, o.pcg_eps_rel, o.pcg_stall,
+                                      nullptr, 0, st));
         if (o.pcg_iters > 0) BK(cudaGraphLaunch(b->graph, st));
         BK(cudaMemcpyAsync(F0.data(), b->F, sizeof(double) * n, cudaMemcpyDeviceToHost, st));
         BK(cudaStreamSynchronize(st));

@@ -198,6 +198,24 @@ template <> struct Store<__nv_bfloat16> {
     }
 };
 
+// Paired FP32 storage: record v holds parameter block v of x (first 16 bytes)
+// and of the PCG direction p (last 16 bytes), so the tangent sweep of A p
+// fetches both with one 256-bit load per corner.  Read through Store it
+// yields the x half.  Records are 32-byte aligned (device allocations are).
+struct PairF32 {
+    float4 x, p;
+};
+template <> struct Store<PairF32> {
+    static __device__ __forceinline__ float4 ld(const PairF32* x, long long v) {
+        return __ldg(&x[v].x);
+    }
+};
+__device__ __forceinline__ void ld_pair(const PairF32* xp, long long v, float4& a, float4& q) {
+    asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+        : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
+        : "l"(xp + v));
+}
+
 __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
     return make_float4(fmaf(t, b.x - a.x, a.x), fmaf(t, b.y - a.y, a.y),
                        fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
@@ -220,6 +238,28 @@ __device__ __forceinline__ float4 interp_grid(const T* x, const DevScene& sc, co
     const float4 b01 = lerp4(a001, a101, c.fx), b11 = lerp4(a011, a111, c.fx);
     const float4 c0 = lerp4(b00, b10, c.fy), c1 = lerp4(b01, b11, c.fy);
     return lerp4(c0, c1, c.fz);
+}
+
+// Trilinear interpolation of x (a) and p (q) from paired storage.
+__device__ __forceinline__ void interp_grid_pair(const PairF32* xp, const DevScene& sc,
+                                                 const Cell& c, float4& a, float4& q) {
+    const long long G = sc.G;
+    const long long i0 = ((long long)c.bz * G + c.by) * G + c.bx;
+    const long long sy = G, sz = G * G;
+    float4 a000, a100, a010, a110, a001, a101, a011, a111;
+    float4 q000, q100, q010, q110, q001, q101, q011, q111;
+    ld_pair(xp, i0, a000, q000);
+    ld_pair(xp, i0 + 1, a100, q100);
+    ld_pair(xp, i0 + sy, a010, q010);
+    ld_pair(xp, i0 + sy + 1, a110, q110);
+    ld_pair(xp, i0 + sz, a001, q001);
+    ld_pair(xp, i0 + sz + 1, a101, q101);
+    ld_pair(xp, i0 + sz + sy, a011, q011);
+    ld_pair(xp, i0 + sz + sy + 1, a111, q111);
+    a = lerp4(lerp4(lerp4(a000, a100, c.fx), lerp4(a010, a110, c.fx), c.fy),
+              lerp4(lerp4(a001, a101, c.fx), lerp4(a011, a111, c.fx), c.fy), c.fz);
+    q = lerp4(lerp4(lerp4(q000, q100, c.fx), lerp4(q010, q110, c.fx), c.fy),
+              lerp4(lerp4(q001, q101, c.fx), lerp4(q011, q111, c.fx), c.fy), c.fz);
 }
 
 // Coordinate along one axis of the voxel with parity bit `pa` in the 2x2x2
@@ -321,6 +361,25 @@ __device__ __forceinline__ float4 interp_shell(const T* x, const ShellHit& hs) {
         acc.w = fmaf(hs.w[q], a.w, acc.w);
     }
     return acc;
+}
+
+__device__ __forceinline__ void interp_shell_pair(const PairF32* xp, const ShellHit& hs,
+                                                  float4& a, float4& q) {
+    a = make_float4(0.f, 0.f, 0.f, 0.f);
+    q = a;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        float4 u, w;
+        ld_pair(xp, hs.idx[k], u, w);
+        a.x = fmaf(hs.w[k], u.x, a.x);
+        a.y = fmaf(hs.w[k], u.y, a.y);
+        a.z = fmaf(hs.w[k], u.z, a.z);
+        a.w = fmaf(hs.w[k], u.w, a.w);
+        q.x = fmaf(hs.w[k], w.x, q.x);
+        q.y = fmaf(hs.w[k], w.y, q.y);
+        q.z = fmaf(hs.w[k], w.z, q.z);
+        q.w = fmaf(hs.w[k], w.w, q.w);
+    }
 }
 
 // FP64 block reduction into one device double (one atomic per block).

@@ -24,11 +24,14 @@ cudaError_t launch_forward_batch(const BatchItem* items, const long long* start,
                                  long long total, unsigned long long* counter, const float* x,
                                  const float* target, float* res, double* F, const int* active,
                                  int mode, int cap_per_sm, cudaStream_t st);
+struct PcgScalars;
+// pcg (may be null): per-scene Algorithm 2 state; scenes whose solve has
+// exited (done) are skipped.
 cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start, int n,
                                  long long total, unsigned long long* counter, const float* x,
                                  const float* p, const float* v, float* out, float* out2,
                                  double* pap, int pap_stride, int mode, int cap_per_sm,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const PcgScalars* pcg = nullptr);
 
 // Device scalars of Algorithm 2 and the line search (FP64).
 struct PcgScalars {
@@ -71,13 +74,19 @@ cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void*
 cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* x, const void* p,
                            int p_dtype, const void* v, float* out, float* out2, double* pap,
                            cudaStream_t st, float* out3 = nullptr);
+// A p (+p^T A p) of an FP32 scene from paired records xp[v] = (x[v], p[v])
+// (2 n floats, 32-byte aligned).
+cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
+                              cudaStream_t st);
 
 // Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP64; p32 / p16: the
-// FP32 / BF16 copies of p that the ray march gathers; Ap: FP32 scatter target.
+// FP32 / BF16 copies of p that the ray march gathers; Ap: FP32 scatter target;
+// pxp (may be null): paired x / p records whose p half also receives p.
 cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
                              double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                              PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
-                             const float* blocks, long long n_block, cudaStream_t st);
+                             const float* blocks, long long n_block, cudaStream_t st,
+                             float* pxp = nullptr);
 cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
                               const float* Ap, const float* diag, const float* blocks,
                               long long n_block, PcgScalars* s, cudaStream_t st);
@@ -85,7 +94,10 @@ cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const dou
 cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st);
 cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
                            long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                           PcgScalars* s, cudaStream_t st);
+                           PcgScalars* s, cudaStream_t st, float* pxp = nullptr);
+// xp[v] = (x[v], p[v]) for the n / 4 parameter blocks (p null: x half only).
+cudaError_t launch_pair_pack(long long n, const float* x, const float* p, float* xp,
+                             cudaStream_t st);
 // x_out = P(x + gamma delta) (project: sigma >= 0, 0 <= c <= 1), formed in FP64;
 // optional float32 and bf16 outputs.
 cudaError_t launch_trial(long long n, const float* x, const double* delta, double gamma,
@@ -100,7 +112,7 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, l
                                  double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                                  PcgScalars* s, int max_iter, int fixed, double eps_rel,
                                  double stall, const float* blocks, long long n_block,
-                                 cudaStream_t st);
+                                 cudaStream_t st, float* pxp = nullptr);
 cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                                   double* delta, double* rho, const double* p, const float* Ap,
                                   const float* diag, const float* blocks, long long n_block,
@@ -109,7 +121,7 @@ cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st);
 cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                                const double* rho, const float* diag, const float* blocks,
                                long long n_block, double* p, float* p32, __nv_bfloat16* p16,
-                               float* Ap, PcgScalars* s, cudaStream_t st);
+                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp = nullptr);
 // Segment y: x_out = P(x + gamma[y] Delta) where mask[y] (or every segment).
 cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                              const float* x, const double* delta, const double* gamma,
