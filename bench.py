@@ -44,6 +44,18 @@ METRIC = "PCG iters/s"
 # counted as special-function work, not FLOP).
 FLOP_PER_SAMPLE_APPLY = 271
 
+# The coefficient-cached A p streams the per-sample coefficients (16 bytes,
+# stored by the step's diagonal march) twice per launch -- the J p sweep and
+# the J^T (J p) sweep -- and otherwise touches p (gathers) and A p (vector
+# atomics), both L2-resident: its algorithmic HBM bytes per launch are
+# 32 per sample or shell hit plus p read once and A p written once (8 bytes
+# per parameter).  Its arithmetic is 207 FLOP per sample (interpolation of p
+# with corner weights 116, J p update 12, corner weights and accumulation of
+# the scatter window 44, v.dH/dsigma 6, flushed colour entries scaled by v
+# 14 on average, shells and per-ray work not counted).
+COEF_BYTES_PER_SAMPLE = 32
+FLOP_PER_SAMPLE_COEF = 207
+
 # DRAM traffic of one A p launch, from the ncu capture summarised in this
 # file; it applies only while the kernel sources hash to the recorded value.
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "apply_traffic_scale128.md")
@@ -565,11 +577,32 @@ def run_ours(args, rank, world, local):
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     apply_ms = tm["apply"]["ms"] / max(tm["apply"]["launches"], 1)
-    achieved = FLOP_PER_SAMPLE_APPLY * samples / (apply_ms / 1000.0) / 1e12
     per_step = {k: v["ms"] / args.steps for k, v in tm.items()}
-    apply_kernel = ("k_scatter<bf16,bf16,1> (A p)" if bf else
-                    "k_scatter<PairF32,PairF32,1> (A p, paired x/p records)"
-                    if tuning.get("paired") else "k_scatter<float,float,1> (A p)")
+    coef = bool(tuning.get("coef"))
+    if coef:
+        apply_kernel = ("k_apply_coef<bf16> (A p from stored coefficients)" if bf else
+                        "k_apply_coef<float> (A p from stored coefficients)")
+        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+        algo_bytes = COEF_BYTES_PER_SAMPLE * samples + (4 if not bf else 2) * sc.n_params + 4 * sc.n_params
+        achieved = algo_bytes / (apply_ms / 1000.0) / 1e9
+        alu = FLOP_PER_SAMPLE_COEF * samples / (apply_ms / 1000.0) / 1e12
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                "frac": achieved / hbm_peak,
+                "algorithmic_bytes_per_launch": algo_bytes,
+                "alu_frac": alu / fp32_peak,
+                "peak_source": f"hbm_gbs ({peak_src}); alu_frac against {sm_count} SMs x 128 "
+                               f"FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz"}
+    else:
+        apply_kernel = ("k_scatter<bf16,bf16,1> (A p)" if bf else
+                        "k_scatter<PairF32,PairF32,1> (A p, paired x/p records)"
+                        if tuning.get("paired") else "k_scatter<float,float,1> (A p)")
+        achieved = FLOP_PER_SAMPLE_APPLY * samples / (apply_ms / 1000.0) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp32_peak,
+                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
+                               f"(max SM clock, {peak_src})"}
+    roof["traffic"] = recorded_traffic(apply_kernel, args.workload) if args.cams is None else None
+    roof["kernel"] = apply_kernel
 
     if rank != 0:
         return
@@ -589,13 +622,7 @@ def run_ours(args, rank, world, local):
                      for s in stats],
         "kernel_ms_per_step": per_step,
         "apply_ms_per_launch": apply_ms,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak,
-                     "traffic": (recorded_traffic(apply_kernel, args.workload)
-                                 if args.cams is None else None),
-                     "kernel": apply_kernel,
-                     "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
-                                    f"(max SM clock, {peak_src})"},
+        "roofline": roof,
         "e2e": {"value": e2e_value, "unit": METRIC,
                 "h2d_bytes_per_step": int(4 * sc.n_params + (2 if bf else 4) * 3 * sc.n_rays),
                 "d2h_bytes_per_step": int(4 * sc.n_params)},

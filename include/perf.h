@@ -140,6 +140,8 @@ typedef struct {
     float apply_ms;           /* time of the fastest A p launch */
     int32_t paired;           /* 1: perf_gn_solve's A p reads x and p from paired
                                  32-byte records (FP32 scenes); 0: two arrays */
+    int32_t coef;             /* 1: the coefficient-cached A p was timed (it is
+                                 what perf_gn_solve runs while the store fits) */
 } perf_tuning;
 
 /* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
@@ -225,13 +227,30 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x_inout, const void* target,
  * judges).  perf_diag_cross: diag(J^T J) and, per grid voxel, the cross
  * entries (colour k, opacity) of its 4x4 block of J^T J (4 floats, the 4th 0). */
 perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_block);
+/* Coefficient-cached A p (no counterpart in the paper: a memory-for-compute
+ * trade of this implementation).  Within one Gauss-Newton step x is fixed,
+ * so the derivatives of every ray-march sample are too; perf_gn_solve's
+ * diagonal march stores them (w_i and dH/dsigma_i, 16 bytes per sample and
+ * shell hit, one row of 32 per pixel tile up to the tile's largest sample
+ * count) and every PCG iteration's A p then gathers only p and reads the
+ * stored values -- the same A p up to rounding.  The store is used when it
+ * fits the budget: bytes = -1 (default) the free device memory minus 6 GiB
+ * at the time of the step, 0 never (marches recompute everything; frees the
+ * store), > 0 at most that many bytes.  The per-call entry points
+ * (perf_apply_normal, perf_pcg_step) always recompute.
+ * perf_coef_info: bytes held by the store, and whether the last
+ * Gauss-Newton step (or perf_autotune) used it (HOST pointers, may be NULL). */
+perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes);
+perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used);
 /* Times the A p launch at x along p (both in the scene storage type; p NULL:
  * p = x) over tile shapes 8x4, 4x8, 16x2, 32x1 and resident-CTA caps
  * {all, 3, 2} (two timed launches each), keeps the fastest for every later
  * ray march of the context unless the default (8x4, no cap) is within 3%,
  * then, for FP32 scenes, times A p from separate x and p arrays against the
  * paired records that perf_gn_solve uses by default and keeps the separate
- * arrays only when 3% faster.  Reports the choice in *out (HOST, may be
+ * arrays only when 3% faster.  When the coefficient store fits its budget it
+ * instead stores the coefficients at x and times the coefficient-cached A p
+ * over the CTA caps with 8x4 tiles.  Reports the choice in *out (HOST, may be
  * NULL).  Uses the PCG workspace; synchronises. */
 perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
                           void* stream);

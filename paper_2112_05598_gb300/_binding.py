@@ -66,7 +66,7 @@ TIMING_KINDS = ("apply", "forward", "diag", "vector", "precond")
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("apply_ms", ctypes.c_float),
-                ("paired", ctypes.c_int32)]
+                ("paired", ctypes.c_int32), ("coef", ctypes.c_int32)]
 
 
 class GNStats(ctypes.Structure):
@@ -98,6 +98,8 @@ _SIGS = {
     "perf_sample_count": [_VP, ctypes.POINTER(ctypes.c_uint64), _VP],
     "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
     "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
+    "perf_set_coef_budget": [_VP, ctypes.c_int64],
+    "perf_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
     "perf_set_lpc": [_VP, _VP],
     "perf_diag_cross": [_VP, _VP, _VP, _VP, _VP],
     "perf_lpc_create": [ctypes.POINTER(_VP), ctypes.c_uint64],
@@ -338,7 +340,17 @@ class Context:
         self._check(self.lib.perf_autotune(self.h, _ptr(x), _ptr(p), ctypes.byref(t),
                                            _stream(stream)), "autotune")
         return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms,
-                    paired=t.paired)
+                    paired=t.paired, coef=t.coef)
+
+    def set_coef_budget(self, nbytes):
+        """Budget of the coefficient store: -1 automatic, 0 off, > 0 bytes."""
+        self._check(self.lib.perf_set_coef_budget(self.h, int(nbytes)), "set_coef_budget")
+
+    def coef_info(self):
+        b = ctypes.c_int64(0)
+        u = ctypes.c_int32(0)
+        self._check(self.lib.perf_coef_info(self.h, ctypes.byref(b), ctypes.byref(u)), "coef_info")
+        return dict(bytes=int(b.value), used=bool(u.value))
 
     def set_lpc(self, lpc):
         self._lpc = lpc

@@ -31,6 +31,7 @@
 // warp-uniform, so the lanes of a warp (an 8x4 pixel tile) that evict the
 // same voxel do it in the same 16-byte vector atomic, which the load/store
 // unit merges before it reaches L2.
+#include <type_traits>
 #include "perf_device.cuh"
 #include "perf_kernels.h"
 
@@ -234,7 +235,7 @@ __device__ __forceinline__ void tangent(const DevScene& sc, const PairF32* __res
 
 // ------------------------------------------------------- voxel window
 
-__device__ __forceinline__ void red_add4(float* base, long long blk, float4 v) {
+__device__ __forceinline__ void red_add4(float* base, int blk, float4 v) {
     atomicAdd(reinterpret_cast<float4*>(base) + blk, v);
 }
 
@@ -250,13 +251,39 @@ struct Window {
 };
 
 
-__device__ __forceinline__ int vox_key(int x, int y, int z, int G) { return (z * G + y) * G + x; }
+// Index of a voxel / texel block in a scatter target: canonical order, or
+// the brick order of the A p accumulation buffer (see ApMap).
+// A key is the sum of one term per axis (axis(a, c)).
+struct CanonKey {
+    int G;
+    __device__ __forceinline__ int axis(int a, int c) const {
+        return a == 0 ? c : a == 1 ? c * G : c * G * G;
+    }
+    __device__ __forceinline__ int key(int x, int y, int z) const { return (z * G + y) * G + x; }
+    __device__ __forceinline__ int shell(int idx) const { return idx; }
+};
+struct BrickKey {
+    int my, mz, shell_off;
+    __device__ __forceinline__ int axis(int a, int c) const {
+        return brick_part(c, a, a == 0 ? 64 : a == 1 ? my : mz);
+    }
+    __device__ __forceinline__ int key(int x, int y, int z) const {
+        return brick_part(x, 0, 64) + brick_part(y, 1, my) + brick_part(z, 2, mz);
+    }
+    __device__ __forceinline__ int shell(int idx) const { return idx + shell_off; }
+};
+__device__ __forceinline__ BrickKey brick_key(const DevScene& sc) {
+    const int Gq = (sc.G + 3) >> 2;
+    return BrickKey{64 * Gq, 64 * Gq * Gq, (int)(64ll * Gq * Gq * Gq - sc.n_vox)};
+}
 
 // VJP sink: slot = (a, s) with a = sum W w_i and s = sum W v.dH/dsigma_i;
 // the parameter block receives (a v_0, a v_1, a v_2, s).
+template <class Key>
 struct VjpSink {
     float* out;
     float v0, v1, v2;
+    Key km;
     __device__ __forceinline__ void put(bool ev, int key, const float (&a)[2]) {
         if (ev && (a[0] != 0.0f || a[1] != 0.0f))
             red_add4(out, key, make_float4(a[0] * v0, a[0] * v1, a[0] * v2, a[1]));
@@ -283,13 +310,49 @@ struct DiagSink {
         if (cross && key < n_vox) red_add4(cross, key, make_float4(a[0] * a[1], a[0] * a[2], a[0] * a[3], 0.0f));
     }
     long long n_vox;
+    CanonKey km;
 };
 
 // Move the window (all lanes; `on` = this lane moves) to base nb, handing the
 // voxels that leave it to the sink.  A voxel never re-enters a ray's window:
 // its trilinear support meets the ray in one run of samples.
+#ifndef PERF_WIN_SKIP
+#define PERF_WIN_SKIP 1
+#endif
 template <int NV, class Sink>
 __device__ __forceinline__ void win_move(Window<NV>& w, const int (&nb)[3], bool on, int G, Sink& sk) {
+#if PERF_WIN_SKIP
+    // Along axis a the window's voxel of parity q moves iff par_coord changes;
+    // slot p leaves iff one of its three axis voxels moves.  Slots that no
+    // lane of the warp leaves are skipped as a whole (warp-uniform branch).
+    unsigned ev = 0;
+    if (on) {
+        const unsigned axis_slots[3][2] = {{0x55u, 0xAAu}, {0x33u, 0xCCu}, {0x0Fu, 0xF0u}};
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int q = 0; q < 2; ++q)
+                if (par_coord(w.b[a], q) != par_coord(nb[a], q)) ev |= axis_slots[a][q];
+    }
+    const unsigned wev = __reduce_or_sync(kFull, ev);
+    if (wev) {
+        int k[3][2];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int q = 0; q < 2; ++q) k[a][q] = sk.km.axis(a, par_coord(w.b[a], q));
+#pragma unroll
+        for (int p = 0; p < 8; ++p) {
+            if (!(wev & (1u << p))) continue;
+            const bool e = (ev >> p) & 1u;
+            sk.put(e, k[0][p & 1] + k[1][(p >> 1) & 1] + k[2][p >> 2], w.v[p]);
+            if (e) {
+#pragma unroll
+                for (int q = 0; q < NV; ++q) w.v[p][q] = 0.0f;
+            }
+        }
+    }
+#else
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int ox = par_coord(w.b[0], p & 1), oy = par_coord(w.b[1], (p >> 1) & 1),
@@ -297,12 +360,13 @@ __device__ __forceinline__ void win_move(Window<NV>& w, const int (&nb)[3], bool
         const int nx = par_coord(nb[0], p & 1), ny = par_coord(nb[1], (p >> 1) & 1),
                   nz = par_coord(nb[2], p >> 2);
         const bool ev = on && (ox != nx || oy != ny || oz != nz);
-        sk.put(ev, vox_key(ox, oy, oz, G), w.v[p]);
+        sk.put(ev, sk.km.key(ox, oy, oz), w.v[p]);
         if (ev) {
 #pragma unroll
             for (int q = 0; q < NV; ++q) w.v[p][q] = 0.0f;
         }
     }
+#endif
     if (on) { w.b[0] = nb[0]; w.b[1] = nb[1]; w.b[2] = nb[2]; }
 }
 
@@ -331,8 +395,11 @@ __device__ __forceinline__ void win_add(Window<NV>& w, const Cell& cl, const flo
 template <int NV, typename T, class Sink>
 __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __restrict__ x,
                                                const Ray& R, long long ray, bool act, CSum V,
-                                               const float (&vv)[3], Sink& sk) {
+                                               const float (&vv)[3], Sink& sk,
+                                               float4* __restrict__ crow = nullptr) {
     float G[3] = {0.0f, 0.0f, 0.0f};
+    const int Kl = act ? R.K : 0;
+    const int Kmax = __reduce_max_sync(kFull, Kl);
     // shells, outermost first
     for (int q = sc.S - 1; q >= 0; --q) {
         ShellHit hs;
@@ -352,6 +419,7 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
             G[0] = fmaf(wi, a.x, G[0]);
             G[1] = fmaf(wi, a.y, G[1]);
             G[2] = fmaf(wi, a.z, G[2]);
+            if (crow) __stcs(crow + (long long)(Kmax + q) * 32, make_float4(wi, ds[0], ds[1], ds[2]));
         }
 #pragma unroll
         for (int c = 0; c < 4; ++c) {
@@ -365,12 +433,10 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
                 val[2 % NV] = W * ds[1];
                 val[3 % NV] = W * ds[2];
             }
-            sk.put(hit, hit ? (int)hs.idx[c] : 0, val);
+            sk.put(hit, hit ? sk.km.shell(hs.idx[c]) : 0, val);
         }
     }
     // grid samples, last to first (warp-uniform loop; lane active while k < K)
-    const int Kl = act ? R.K : 0;
-    const int Kmax = __reduce_max_sync(kFull, Kl);
     const float dbar = R.delta * sc.halfG;
     Window<NV> w;
 #pragma unroll
@@ -405,6 +471,7 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
             G[0] = fmaf(wi, a.x, G[0]);
             G[1] = fmaf(wi, a.y, G[1]);
             G[2] = fmaf(wi, a.z, G[2]);
+            if (crow) __stcs(crow + (long long)k * 32, make_float4(wi, ds0, ds1, ds2));
             float val[NV];
             val[0] = wi;
             if (NV == 2) {
@@ -420,8 +487,8 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
     // the remaining window
 #pragma unroll
     for (int p = 0; p < 8; ++p)
-        sk.put(Kl > 0, vox_key(par_coord(w.b[0], p & 1), par_coord(w.b[1], (p >> 1) & 1),
-                               par_coord(w.b[2], p >> 2), sc.G),
+        sk.put(Kl > 0, sk.km.key(par_coord(w.b[0], p & 1), par_coord(w.b[1], (p >> 1) & 1),
+                                 par_coord(w.b[2], p >> 2)),
                w.v[p]);
 }
 
@@ -459,12 +526,14 @@ __device__ __forceinline__ void forward_tile(const DevScene& sc, const T* __rest
 }
 
 // All 32 lanes call it (the back-to-front sweep is warp-synchronous).
-template <typename T, typename TP, int MODE, typename TV>   // 0 vjp, 1 apply A, 2 diag (+grad)
+// BRICK: the J^T v / A p target is in brick order (see ApMap).
+template <typename T, typename TP, int MODE, typename TV, bool BRICK = false>   // 0 vjp, 1 apply A, 2 diag (+grad)
 __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __restrict__ x,
                                              const TP* __restrict__ p, const TV* __restrict__ v,
                                              float* __restrict__ out, float* __restrict__ out2,
                                              float* __restrict__ out3, long long tile, int lane,
-                                             double& acc) {
+                                             double& acc, float4* __restrict__ coef = nullptr,
+                                             const long long* __restrict__ tile_off = nullptr) {
     long long ray = 0;
     bool act = tile_pixel(sc, tile, lane, ray);
     Ray R;
@@ -491,10 +560,14 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
         if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f) act = false;
     }
     if (MODE == 2) {
-        DiagSink sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox};
-        backward_sweep<4>(sc, x, R, ray, act, V, vr, sk);
+        DiagSink sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}};
+        backward_sweep<4>(sc, x, R, ray, act, V, vr, sk,
+                          coef ? coef + tile_off[tile] * 32 + lane : nullptr);
+    } else if (BRICK) {
+        VjpSink<BrickKey> sk{out, vr[0], vr[1], vr[2], brick_key(sc)};
+        backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
     } else {
-        VjpSink sk{out, vr[0], vr[1], vr[2]};
+        VjpSink<CanonKey> sk{out, vr[0], vr[1], vr[2], CanonKey{sc.G}};
         backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
     }
 }
@@ -532,19 +605,150 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
     }
 }
 
-template <typename T, typename TP, int MODE, typename TV>
+template <typename T, typename TP, int MODE, typename TV, bool BRICK = false>
 __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PERF_MIN_CTAS)
     k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
                                                       const TV* __restrict__ v,
                                                       float* __restrict__ out,
                                                       float* __restrict__ out2,
-                                                      float* __restrict__ out3, double* pap) {
+                                                      float* __restrict__ out3, double* pap,
+                                                      float4* __restrict__ coef,
+                                                      const long long* __restrict__ tile_off) {
     double acc = 0.0;
     PERF_TILE_LOOP {
-        scatter_tile<T, TP, MODE, TV>(sc, x, p, v, out, out2, out3, tile, lane, acc);
+        scatter_tile<T, TP, MODE, TV, BRICK>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
+                                             tile_off);
     }
     if (MODE == 1 && pap) block_add_f64<kWarps>(acc, pap);
+}
+
+// ------------------------------------------- coefficient-cached A p
+//
+// Within one Gauss-Newton step x is fixed, so every sample's derivatives are
+// fixed too: J_ray p = sum_i [w_i p~c_i + dH/dsigma_i p~sigma_i] (p~ = p
+// interpolated at sample i) and the scatter of J^T v uses the same
+// (w_i, dH/dsigma_i).  The diagonal march of the step (Algorithm 1, run once)
+// stores these four numbers per sample; each PCG iteration's A p then
+// gathers only p and streams the coefficients -- no interpolation of x,
+// no exponentials, no transmittance recurrence.
+//
+// Store layout: per pixel tile, rows of 32 float4 (one per lane): rows
+// 0..Kmax-1 the grid samples (Kmax = the tile's largest sample count), then
+// one row per shell.  tile_off[t] = first row of tile t (exclusive prefix sum
+// of Kmax + S over tiles).  Entries of samples a lane does not have (k >= K,
+// a shell it misses) are never read.
+
+// rows[t] = Kmax of tile t + S.
+__global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) {
+    PERF_TILE_LOOP {
+        long long ray;
+        int K = 0;
+        if (tile_pixel(sc, tile, lane, ray)) {
+            Ray R;
+            ray_setup(sc, ray, R);
+            K = R.K;
+        }
+        K = __reduce_max_sync(kFull, K);
+        if (lane == 0) rows[tile] = K + sc.S;
+    }
+}
+
+template <typename TP, bool BRICK>
+__device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __restrict__ p,
+                                                const float4* __restrict__ coef,
+                                                const long long* __restrict__ tile_off,
+                                                float* __restrict__ out, long long tile, int lane,
+                                                double& acc) {
+    long long ray = 0;
+    bool act = tile_pixel(sc, tile, lane, ray);
+    Ray R;
+    R.K = 0;
+    R.shell_hit = 0u;
+    R.delta = 0.0f;
+    if (act) ray_setup(sc, ray, R);
+    const long long r0 = tile_off[tile];
+    const int kmax_rows = (int)(tile_off[tile + 1] - r0) - sc.S;
+    const float4* crow = coef + r0 * 32 + lane;
+    // J p
+    float J[3] = {0.0f, 0.0f, 0.0f};
+    if (act) {
+        for (int k = 0; k < R.K; ++k) {
+            const Cell cl = sample_cell(sc, R, ray, k);
+            const float4 q = interp_grid(p, sc, cl);
+            const float4 c = __ldcs(crow + (long long)k * 32);
+            J[0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[0]));
+            J[1] = fmaf(c.x, q.y, fmaf(c.z, q.w, J[1]));
+            J[2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[2]));
+        }
+        for (int s = 0; s < sc.S; ++s) {
+            ShellHit hs;
+            if (shell_lookup(sc, R, s, hs)) {
+                const float4 q = interp_shell(p, hs);
+                const float4 c = __ldcs(crow + (long long)(kmax_rows + s) * 32);
+                J[0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[0]));
+                J[1] = fmaf(c.x, q.y, fmaf(c.z, q.w, J[1]));
+                J[2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[2]));
+            }
+        }
+        acc += (double)J[0] * J[0] + (double)J[1] * J[1] + (double)J[2] * J[2];
+        if (J[0] == 0.0f && J[1] == 0.0f && J[2] == 0.0f) act = false;
+    }
+    // J^T (J p): the scatter of Algorithm 1 with v = J p
+    typedef typename std::conditional<BRICK, BrickKey, CanonKey>::type Key;
+    Key km;
+    if constexpr (BRICK) km = brick_key(sc); else km = CanonKey{sc.G};
+    VjpSink<Key> sk{out, J[0], J[1], J[2], km};
+    for (int s = sc.S - 1; s >= 0; --s) {
+        ShellHit hs;
+        const bool hit = act && shell_lookup(sc, R, s, hs);
+        float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (hit) c = __ldcs(crow + (long long)(kmax_rows + s) * 32);
+        const float sv = J[0] * c.y + J[1] * c.z + J[2] * c.w;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const float W = hit ? hs.w[k] : 0.0f;
+            const float val[2] = {W * c.x, W * sv};
+            sk.put(hit, hit ? sk.km.shell(hs.idx[k]) : 0, val);
+        }
+    }
+    const int Kl = act ? R.K : 0;
+    const int Kmax = __reduce_max_sync(kFull, Kl);
+    Window<2> w;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) w.v[c][0] = w.v[c][1] = 0.0f;
+    w.b[0] = w.b[1] = w.b[2] = 0;
+    for (int k = Kmax - 1; k >= 0; --k) {
+        const bool on = k < Kl;
+        Cell cl;
+        cl.bx = w.b[0]; cl.by = w.b[1]; cl.bz = w.b[2];
+        cl.fx = cl.fy = cl.fz = 0.0f;
+        if (on) {
+            cl = sample_cell(sc, R, ray, k);
+            if (k == Kl - 1) { w.b[0] = cl.bx; w.b[1] = cl.by; w.b[2] = cl.bz; }
+        }
+        const int nb[3] = {cl.bx, cl.by, cl.bz};
+        win_move(w, nb, on, sc.G, sk);
+        if (on) {
+            const float4 c = __ldcs(crow + (long long)k * 32);
+            const float val[2] = {c.x, J[0] * c.y + J[1] * c.z + J[2] * c.w};
+            win_add(w, cl, val);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        sk.put(Kl > 0, sk.km.key(par_coord(w.b[0], q & 1), par_coord(w.b[1], (q >> 1) & 1),
+                                 par_coord(w.b[2], q >> 2)),
+               w.v[q]);
+}
+
+template <typename TP, bool BRICK>
+__global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
+    k_apply_coef(DevScene sc, const TP* __restrict__ p, const float4* __restrict__ coef,
+                 const long long* __restrict__ tile_off, float* __restrict__ out, double* pap) {
+    double acc = 0.0;
+    PERF_TILE_LOOP { coef_apply_tile<TP, BRICK>(sc, p, coef, tile_off, out, tile, lane, acc); }
+    if (pap) block_add_f64<kWarps>(acc, pap);
 }
 
 // ------------------------------------------------------ batched (many scenes)
@@ -744,15 +948,16 @@ cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void*
     return launch_jvp_t<float, float>(sc, x, p, out, st);
 }
 
-template <typename T, typename TP, int MODE, typename TV>
+template <typename T, typename TP, int MODE, typename TV, bool BRICK = false>
 cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, const void* v,
                              float* out, float* out2, double* pap, cudaStream_t st,
-                             float* out3 = nullptr) {
+                             float* out3 = nullptr, float* coef = nullptr,
+                             const long long* tile_off = nullptr) {
     if (sc.n_tiles == 0) return cudaSuccess;
-    auto fn = k_scatter<T, TP, MODE, TV>;
+    auto fn = k_scatter<T, TP, MODE, TV, BRICK>;
     fn<<<grid_blocks((const void*)fn, sc.n_tiles, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
-        out2, out3, pap);
+        out2, out3, pap, reinterpret_cast<float4*>(coef), tile_off);
     count_launch();
     return cudaGetLastError();
 }
@@ -761,24 +966,69 @@ cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, c
 // of the diagonal / gradient (mode 2).
 cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* x, const void* p,
                            int p_dtype, const void* v, float* out, float* out2, double* pap,
-                           cudaStream_t st, float* out3) {
+                           cudaStream_t st, float* out3, float* coef, const long long* tile_off) {
     typedef __nv_bfloat16 B;
     if (dtype == 1) {
         if (mode == 1)
             return p_dtype == 1 ? launch_scatter_t<B, B, 1, float>(sc, x, p, v, out, out2, pap, st)
                                 : launch_scatter_t<B, float, 1, float>(sc, x, p, v, out, out2, pap, st);
         if (mode == 0) return launch_scatter_t<B, float, 0, float>(sc, x, p, v, out, out2, pap, st);
-        return launch_scatter_t<B, float, 2, B>(sc, x, p, v, out, out2, pap, st, out3);
+        return launch_scatter_t<B, float, 2, B>(sc, x, p, v, out, out2, pap, st, out3, coef,
+                                                tile_off);
     }
     if (mode == 1) return launch_scatter_t<float, float, 1, float>(sc, x, p, v, out, out2, pap, st);
     if (mode == 0) return launch_scatter_t<float, float, 0, float>(sc, x, p, v, out, out2, pap, st);
-    return launch_scatter_t<float, float, 2, float>(sc, x, p, v, out, out2, pap, st, out3);
+    return launch_scatter_t<float, float, 2, float>(sc, x, p, v, out, out2, pap, st, out3, coef,
+                                                    tile_off);
 }
 
 // A p from paired x / p storage (FP32 scenes).
 cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
+                              cudaStream_t st, bool brick) {
+    return brick ? launch_scatter_t<PairF32, PairF32, 1, float, true>(sc, xp, xp, nullptr, out,
+                                                                      nullptr, pap, st)
+                 : launch_scatter_t<PairF32, PairF32, 1, float>(sc, xp, xp, nullptr, out, nullptr,
+                                                                pap, st);
+}
+
+// A p into a brick-order buffer from separate x and p arrays.
+cudaError_t launch_apply_brick(const DevScene& sc, int dtype, const void* x, const void* p,
+                               int p_dtype, float* out, double* pap, cudaStream_t st) {
+    typedef __nv_bfloat16 B;
+    if (dtype == 1)
+        return p_dtype == 1 ? launch_scatter_t<B, B, 1, float, true>(sc, x, p, nullptr, out, nullptr, pap, st)
+                            : launch_scatter_t<B, float, 1, float, true>(sc, x, p, nullptr, out, nullptr, pap, st);
+    return launch_scatter_t<float, float, 1, float, true>(sc, x, p, nullptr, out, nullptr, pap, st);
+}
+
+cudaError_t launch_tile_rows(const DevScene& sc, int* rows, cudaStream_t st) {
+    if (sc.n_tiles == 0) return cudaSuccess;
+    k_tile_rows<<<grid_blocks((const void*)k_tile_rows, sc.n_tiles), kThreads, 0, st>>>(sc, rows);
+    count_launch();
+    return cudaGetLastError();
+}
+
+template <typename TP, bool BRICK>
+cudaError_t launch_apply_coef_t(const DevScene& sc, const void* p, const float* coef,
+                                const long long* tile_off, float* out, double* pap,
+                                cudaStream_t st) {
+    if (sc.n_tiles == 0) return cudaSuccess;
+    auto fn = k_apply_coef<TP, BRICK>;
+    fn<<<grid_blocks((const void*)fn, sc.n_tiles, sc.cap_per_sm), kThreads, 0, st>>>(
+        sc, static_cast<const TP*>(p), reinterpret_cast<const float4*>(coef), tile_off, out, pap);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_coef(const DevScene& sc, const void* p, int p_dtype, const float* coef,
+                              const long long* tile_off, float* out, double* pap, bool brick,
                               cudaStream_t st) {
-    return launch_scatter_t<PairF32, PairF32, 1, float>(sc, xp, xp, nullptr, out, nullptr, pap, st);
+    typedef __nv_bfloat16 B;
+    if (p_dtype == 1)
+        return brick ? launch_apply_coef_t<B, true>(sc, p, coef, tile_off, out, pap, st)
+                     : launch_apply_coef_t<B, false>(sc, p, coef, tile_off, out, pap, st);
+    return brick ? launch_apply_coef_t<float, true>(sc, p, coef, tile_off, out, pap, st)
+                 : launch_apply_coef_t<float, false>(sc, p, coef, tile_off, out, pap, st);
 }
 
 // ------------------------------------------------------ batched launchers

@@ -28,6 +28,11 @@ cudaError_t launch_block_jacobi(const float* diag, const float* cross, float* bl
                                 cudaStream_t st);
 }  // namespace perf
 
+// A p accumulation order of the PCG workspace: brick order (1) or canonical.
+#ifndef PERF_AP_BRICK
+#define PERF_AP_BRICK 1
+#endif
+
 struct perf_ctx {
     perf_scene scene;
     perf_options opts;
@@ -45,6 +50,17 @@ struct perf_ctx {
     float* p32 = nullptr;
     float* xp = nullptr;        // paired (x, p) records for A p (FP32 scenes)
     bool pair = true;           // Gauss-Newton A p reads the paired records
+    perf::ApMap am{};           // order of the PCG's A p buffer (brick order)
+    // coefficient-cached A p: per-sample (w_i, dH/dsigma_i) of the current
+    // Gauss-Newton step, stored by its diagonal march (see k_march.cu)
+    long long coef_budget = -1;        // bytes; -1 automatic, 0 off
+    long long* tile_off = nullptr;     // first row of every pixel tile (n_tiles + 1)
+    float* coef = nullptr;
+    size_t coef_bytes = 0;             // allocated
+    long long coef_rows = 0;           // rows needed by the current tiling
+    int tab_tile_w = 0, tab_max_samples = 0;
+    long long tab_epoch = -1;          // epoch of a jittered table (-1: not jittered)
+    bool coef_used = false;            // the last Gauss-Newton step used the store
     float* Ap = nullptr;
     float* x_trial = nullptr;
     __nv_bfloat16* x16 = nullptr;
@@ -115,9 +131,69 @@ perf_status ensure_pcg(perf_ctx* ctx) {
     CK(alloc(&ctx->rho, ctx->n));
     CK(alloc(&ctx->p, ctx->n));
     CK(alloc(&ctx->p32, ctx->n));
-    CK(alloc(&ctx->Ap, ctx->n));
+    if (!ctx->Ap) {
+        // brick order: the grid part is padded to 4^3 bricks; the padding is
+        // never scattered to and stays zero
+        ctx->am = perf::ap_map(ctx->ds.G, PERF_AP_BRICK != 0);
+        const long long n_ap = ctx->n + 4 * (ctx->am.n_vox_pad - ctx->am.n_vox);
+        CK(alloc(&ctx->Ap, n_ap));
+        CK(cudaMemset(ctx->Ap, 0, sizeof(float) * (size_t)n_ap));
+    }
     if (ctx->scene.dtype == PERF_BF16) CK(alloc(&ctx->p16, ctx->n));
     else CK(alloc(&ctx->xp, 2 * ctx->n));
+    return PERF_OK;
+}
+
+// Prepares the coefficient store for the context's current tiling; *use =
+// whether it fits the budget (automatic: the free device memory minus 6 GiB).
+perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
+    *use = false;
+    if (ctx->coef_budget == 0 || ctx->n_rays == 0) return PERF_OK;
+    const perf::DevScene& d = ctx->ds;
+    // with pixel jitter the rays, and so the sample counts, change with the epoch
+    const long long epoch = d.jitter ? (long long)d.epoch : -1;
+    if (!ctx->tile_off || ctx->tab_tile_w != d.tile_w || ctx->tab_max_samples != d.max_samples ||
+        ctx->tab_epoch != epoch) {
+        if (ctx->tile_off) { cudaFree(ctx->tile_off); ctx->tile_off = nullptr; }
+        int* rows = nullptr;
+        CK(cudaMalloc(&rows, sizeof(int) * (size_t)d.n_tiles));
+        cudaError_t e = perf::launch_tile_rows(d, rows, st);
+        std::vector<int> h((size_t)d.n_tiles);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h.data(), rows, sizeof(int) * (size_t)d.n_tiles, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(rows);
+        CK(e);
+        std::vector<long long> off((size_t)d.n_tiles + 1);
+        off[0] = 0;
+        for (long long t = 0; t < d.n_tiles; ++t) off[(size_t)t + 1] = off[(size_t)t] + h[(size_t)t];
+        CK(cudaMalloc(&ctx->tile_off, sizeof(long long) * off.size()));
+        CK(cudaMemcpy(ctx->tile_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice));
+        ctx->coef_rows = off.back();
+        ctx->tab_tile_w = d.tile_w;
+        ctx->tab_max_samples = d.max_samples;
+        ctx->tab_epoch = epoch;
+    }
+    const size_t need = (size_t)ctx->coef_rows * 32 * sizeof(float4);
+    size_t budget;
+    if (ctx->coef_budget > 0) {
+        budget = (size_t)ctx->coef_budget;
+    } else {
+        size_t fr = 0, tot = 0;
+        CK(cudaMemGetInfo(&fr, &tot));
+        const size_t avail = fr + ctx->coef_bytes, reserve = (size_t)6 << 30;
+        budget = avail > reserve ? avail - reserve : 0;
+    }
+    if (need > budget) {
+        if (ctx->coef) { cudaFree(ctx->coef); ctx->coef = nullptr; ctx->coef_bytes = 0; }
+        return PERF_OK;
+    }
+    if (ctx->coef_bytes < need) {
+        if (ctx->coef) { cudaFree(ctx->coef); ctx->coef = nullptr; ctx->coef_bytes = 0; }
+        CK(cudaMalloc(&ctx->coef, need > 0 ? need : 16));
+        ctx->coef_bytes = need;
+    }
+    *use = true;
     return PERF_OK;
 }
 
@@ -267,7 +343,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->p32, ctx->xp, ctx->Ap, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->p32, ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -378,7 +454,7 @@ perf_status perf_pcg_begin(perf_ctx* ctx, const float* grad, const float* diag, 
     CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p, ctx->p32,
                               ctx->p16, ctx->Ap, ctx->s, ctx->opts.pcg_iters, ctx->opts.pcg_fixed,
                               ctx->opts.pcg_eps_rel, ctx->opts.pcg_stall, B, ctx->n_block,
-                              S(stream)));
+                              S(stream), nullptr, ctx->am));
     return PERF_OK;
 }
 
@@ -388,26 +464,37 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
 
 namespace {
 
+// A p into the PCG workspace (its order) from separate x and p arrays.
+cudaError_t apply_arrays(perf_ctx* ctx, const void* x, const void* pp, double* pap, cudaStream_t st) {
+    const int pdt = ctx->scene.dtype == PERF_BF16 ? PERF_BF16 : PERF_F32;
+    return PERF_AP_BRICK ? perf::launch_apply_brick(ctx->ds, ctx->scene.dtype, x, pp, pdt, ctx->Ap, pap, st)
+                         : perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, pdt, nullptr,
+                                                ctx->Ap, nullptr, pap, st);
+}
+
 // One Algorithm 2 iteration on the context workspace with diagonal `diag`
 // and block preconditioner B (null: Jacobi).  paired: A p reads the paired
-// records ctx->xp, whose x half holds x (FP32 scenes).
+// records ctx->xp, whose x half holds x (FP32 scenes).  A p accumulates in
+// brick order (ctx->am).
 perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const float* B, cudaStream_t st,
-                     bool paired = false) {
+                     bool paired = false, bool coef = false) {
     const bool bf = ctx->scene.dtype == PERF_BF16;
     const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p32);
     t_begin(ctx, PERF_T_APPLY, st);
-    if (paired)
-        CK(perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, &ctx->s->pAp, st));
+    if (coef)
+        CK(perf::launch_apply_coef(ctx->ds, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef, ctx->tile_off,
+                                   ctx->Ap, &ctx->s->pAp, PERF_AP_BRICK != 0, st));
+    else if (paired)
+        CK(perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, &ctx->s->pAp, st, PERF_AP_BRICK != 0));
     else
-        CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, bf ? PERF_BF16 : PERF_F32,
-                                nullptr, ctx->Ap, nullptr, &ctx->s->pAp, st));
+        CK(apply_arrays(ctx, x, pp, &ctx->s->pAp, st));
     t_end(ctx, PERF_T_APPLY, st);
     t_begin(ctx, PERF_T_VECTOR, st);
     CK(perf::launch_pcg_update(ctx->n, ctx->delta, ctx->rho, ctx->p, ctx->Ap, diag, B, ctx->n_block,
-                               ctx->s, st));
+                               ctx->s, st, ctx->am));
     CK(perf::launch_pcg_finish(ctx->s, st));
     CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p32, ctx->p16,
-                            ctx->Ap, ctx->s, st, paired ? ctx->xp : nullptr));
+                            ctx->Ap, ctx->s, st, paired ? ctx->xp : nullptr, ctx->am));
     t_end(ctx, PERF_T_VECTOR, st);
     return PERF_OK;
 }
@@ -494,12 +581,18 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
             CK(alloc(&ctx->cross, 4 * nvox));
             CK(cudaMemsetAsync(ctx->cross, 0, sizeof(float) * 4 * (size_t)nvox, st));
         }
+        bool use_coef = false;
+        ps = ensure_coef(ctx, st, &use_coef);
+        if (ps != PERF_OK) return ps;
         t_begin(ctx, PERF_T_DIAG, st);
         if (ctx->n_rays > 0)
             CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, xm, nullptr, PERF_F32, ctx->r,
                                     ctx->diag, ctx->grad, nullptr, st,
-                                    need_cross ? ctx->cross : nullptr));
+                                    need_cross ? ctx->cross : nullptr,
+                                    use_coef ? ctx->coef : nullptr,
+                                    use_coef ? ctx->tile_off : nullptr));
         t_end(ctx, PERF_T_DIAG, st);
+        ctx->coef_used = use_coef;
         const float* B = nullptr;
         long long nB = 0;
         if (o.precond == PERF_PRECOND_BLOCK_JACOBI ||
@@ -521,15 +614,15 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
             nB = ctx->n_block;
         }
         int fallback = 0;
-        const bool paired = !bf && ctx->pair;
+        const bool paired = !bf && ctx->pair && !use_coef;
         if (paired) CK(perf::launch_pair_pack(ctx->n, x, nullptr, ctx->xp, st));
         for (int attempt = 0; attempt < 2; ++attempt) {
             CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
                                       ctx->p32, ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
                                       o.pcg_eps_rel, o.pcg_stall, B, nB, st,
-                                      paired ? ctx->xp : nullptr));
+                                      paired ? ctx->xp : nullptr, ctx->am));
             for (int k = 0; k < o.pcg_iters; ++k) {
-                ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired);
+                ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired, use_coef);
                 if (ps != PERF_OK) return ps;
                 if (!o.pcg_fixed) {
                     int done = 0;
@@ -647,16 +740,55 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     const void* pp = pbuf;
     if (!bf) CK(perf::launch_pair_pack(ctx->n, static_cast<const float*>(x), ctx->p32, ctx->xp, st));
     auto apply = [&](bool paired) -> cudaError_t {
-        return paired ? perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, nullptr, st)
-                      : perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp,
-                                             bf ? PERF_BF16 : PERF_F32, nullptr, ctx->Ap, nullptr,
-                                             nullptr, st);
+        return paired ? perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, nullptr, st,
+                                                PERF_AP_BRICK != 0)
+                      : apply_arrays(ctx, x, pp, nullptr, st);
     };
     const int tws[4] = {8, 4, 16, 32};
     const int caps[3] = {0, 3, 2};
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
+    // With the coefficient store, Gauss-Newton steps run the coefficient-
+    // cached A p: keep 8x4 tiles (the store is laid out per tile) and time
+    // it over the CTA caps, on coefficients stored at x.
+    set_tiling(ctx, 8);
+    bool use_coef = false;
+    perf_status pc = ensure_coef(ctx, st, &use_coef);
+    if (pc != PERF_OK) return pc;
+    if (use_coef) {
+        CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr,
+                                ctx->diag, nullptr, nullptr, st, nullptr, ctx->coef, ctx->tile_off));
+        float best = 1e30f;
+        int best_cap = 0;
+        for (int j = 0; j < 3; ++j) {
+            ctx->ds.cap_per_sm = caps[j];
+            for (int rep = 0; rep < 3; ++rep) {
+                if (rep == 1) CK(cudaEventRecord(e0, st));
+                CK(perf::launch_apply_coef(ctx->ds, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef,
+                                           ctx->tile_off, ctx->Ap, nullptr, PERF_AP_BRICK != 0, st));
+            }
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            ms *= 0.5f;
+            if (ms < (j == 0 ? 1e30f : 0.97f * best)) { best = ms; best_cap = caps[j]; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        ctx->ds.cap_per_sm = best_cap;
+        ctx->coef_used = true;
+        if (out) {
+            out->tile_w = 8;
+            out->tile_h = 4;
+            out->ctas_per_sm = best_cap;
+            out->apply_ms = best;
+            out->paired = 0;
+            out->coef = 1;
+        }
+        return PERF_OK;
+    }
     // each candidate: one warm-up launch, then the mean of two timed launches
     auto time_apply = [&](bool paired, float& ms) -> cudaError_t {
         cudaError_t e = cudaSuccess;
@@ -705,6 +837,7 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
         out->ctas_per_sm = best_cap;
         out->apply_ms = best;
         out->paired = pair ? 1 : 0;
+        out->coef = 0;
     }
     return PERF_OK;
 }
@@ -735,6 +868,25 @@ perf_status perf_diag_cross(perf_ctx* ctx, const void* x, float* diag_out, float
     if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "diag_cross: NULL x");
     CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr, diag_out,
                             nullptr, nullptr, S(stream), cross_out));
+    return PERF_OK;
+}
+
+perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bytes < -1) return fail(ctx, PERF_ERR_INVALID_ARG, "set_coef_budget: bytes must be >= -1");
+    ctx->coef_budget = bytes;
+    if (bytes >= 0 && ctx->coef && ctx->coef_bytes > (size_t)bytes) {
+        cudaFree(ctx->coef);
+        ctx->coef = nullptr;
+        ctx->coef_bytes = 0;
+    }
+    return PERF_OK;
+}
+
+perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bytes_held) *bytes_held = (int64_t)ctx->coef_bytes;
+    if (last_used) *last_used = ctx->coef_used ? 1 : 0;
     return PERF_OK;
 }
 

@@ -342,6 +342,7 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
         out->ctas_per_sm = best_cap;
         out->apply_ms = best;
         out->paired = 0;
+        out->coef = 0;
     }
     return PERF_OK;
 }

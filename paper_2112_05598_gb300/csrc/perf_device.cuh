@@ -153,6 +153,45 @@ __device__ __forceinline__ void ray_setup(const DevScene& sc, long long ray, Ray
     R.shell_hit = hit;
 }
 
+// Brick order of the A p accumulation buffer.  The grid is cut into 4x4x4
+// bricks (each axis rounded up to a multiple of 4); inside a brick the 8
+// voxels of one coordinate-parity class are consecutive, i.e. one 128-byte
+// line of float4 blocks, and the texel blocks follow the padded grid.  The
+// scatter window is parity-indexed, so the lanes of a warp flush voxels of
+// one parity class per instruction; in this order nearby voxels of a class
+// share a line, where the canonical order spreads them over several.
+// Bits of a voxel's index: 0-2 the coordinates' second bits, 3-5 their
+// parities, 6.. the brick.
+__host__ __device__ __forceinline__ int brick_part(int c, int axis, int mul) {
+    return (c >> 2) * mul + ((c & 1) << (3 + axis)) + (((c >> 1) & 1) << axis);
+}
+
+struct ApMap {
+    int G;                 // 0: canonical order
+    int Gq;                // bricks per axis
+    long long n_vox;       // grid voxels
+    long long n_vox_pad;   // 64 Gq^3
+};
+
+__host__ inline ApMap ap_map(int G, bool brick) {
+    ApMap m{0, 0, (long long)G * G * G, (long long)G * G * G};
+    if (brick) {
+        m.G = G;
+        m.Gq = (G + 3) >> 2;
+        m.n_vox_pad = 64ll * m.Gq * m.Gq * m.Gq;
+    }
+    return m;
+}
+
+// Index in the A p buffer of canonical parameter block v.
+__device__ __forceinline__ long long ap_index(const ApMap& m, long long v) {
+    if (m.G == 0) return v;
+    if (v >= m.n_vox) return v - m.n_vox + m.n_vox_pad;
+    const int vi = (int)v, G = m.G;
+    const int x = vi % G, t = vi / G, y = t % G, z = t / G;
+    return brick_part(x, 0, 64) + brick_part(y, 1, 64 * m.Gq) + brick_part(z, 2, 64 * m.Gq * m.Gq);
+}
+
 // Trilinear cell of a sample: base voxel (linear index) and fractions.
 struct Cell {
     int bx, by, bz;
@@ -182,12 +221,12 @@ __device__ __forceinline__ Cell sample_cell(const DevScene& sc, const Ray& R, lo
 // --- storage access: float4 (FP32) or 4 x bf16 (BF16) per voxel / texel
 template <typename T> struct Store;
 template <> struct Store<float> {
-    static __device__ __forceinline__ float4 ld(const float* x, long long v) {
+    static __device__ __forceinline__ float4 ld(const float* x, int v) {
         return __ldg(reinterpret_cast<const float4*>(x) + v);
     }
 };
 template <> struct Store<__nv_bfloat16> {
-    static __device__ __forceinline__ float4 ld(const __nv_bfloat16* x, long long v) {
+    static __device__ __forceinline__ float4 ld(const __nv_bfloat16* x, int v) {
         const uint2 u = __ldg(reinterpret_cast<const uint2*>(x) + v);
         float4 r;
         r.x = __uint_as_float(u.x << 16);
@@ -206,11 +245,11 @@ struct PairF32 {
     float4 x, p;
 };
 template <> struct Store<PairF32> {
-    static __device__ __forceinline__ float4 ld(const PairF32* x, long long v) {
+    static __device__ __forceinline__ float4 ld(const PairF32* x, int v) {
         return __ldg(&x[v].x);
     }
 };
-__device__ __forceinline__ void ld_pair(const PairF32* xp, long long v, float4& a, float4& q) {
+__device__ __forceinline__ void ld_pair(const PairF32* xp, int v, float4& a, float4& q) {
     asm("ld.global.nc.v8.f32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
         : "=f"(a.x), "=f"(a.y), "=f"(a.z), "=f"(a.w), "=f"(q.x), "=f"(q.y), "=f"(q.z), "=f"(q.w)
         : "l"(xp + v));
@@ -221,45 +260,82 @@ __device__ __forceinline__ float4 lerp4(float4 a, float4 b, float t) {
                        fmaf(t, b.z - a.z, a.z), fmaf(t, b.w - a.w, a.w));
 }
 
+// Trilinear interpolation as a weighted sum of the 8 corners (corner c:
+// bit a = +1 along axis a), weights w_c = prod_a (c_a ? f_a : 1 - f_a).
+#ifndef PERF_INTERP_W
+#define PERF_INTERP_W 1
+#endif
+__device__ __forceinline__ void tri_weights(const Cell& c, float (&W)[8]) {
+    const float gx[2] = {1.0f - c.fx, c.fx}, gy[2] = {1.0f - c.fy, c.fy}, gz[2] = {1.0f - c.fz, c.fz};
+#pragma unroll
+    for (int k = 0; k < 8; ++k) W[k] = (gx[k & 1] * gy[(k >> 1) & 1]) * gz[k >> 2];
+}
+
+__device__ __forceinline__ float4 wsum8(const float (&W)[8], const float4 (&a)[8]) {
+    float4 r = make_float4(W[0] * a[0].x, W[0] * a[0].y, W[0] * a[0].z, W[0] * a[0].w);
+#pragma unroll
+    for (int k = 1; k < 8; ++k) {
+        r.x = fmaf(W[k], a[k].x, r.x);
+        r.y = fmaf(W[k], a[k].y, r.y);
+        r.z = fmaf(W[k], a[k].z, r.z);
+        r.w = fmaf(W[k], a[k].w, r.w);
+    }
+    return r;
+}
+
 template <typename T>
 __device__ __forceinline__ float4 interp_grid(const T* x, const DevScene& sc, const Cell& c) {
-    const long long G = sc.G;
-    const long long i0 = ((long long)c.bz * G + c.by) * G + c.bx;
-    const long long sy = G, sz = G * G;
-    const float4 a000 = Store<T>::ld(x, i0);
-    const float4 a100 = Store<T>::ld(x, i0 + 1);
-    const float4 a010 = Store<T>::ld(x, i0 + sy);
-    const float4 a110 = Store<T>::ld(x, i0 + sy + 1);
-    const float4 a001 = Store<T>::ld(x, i0 + sz);
-    const float4 a101 = Store<T>::ld(x, i0 + sz + 1);
-    const float4 a011 = Store<T>::ld(x, i0 + sz + sy);
-    const float4 a111 = Store<T>::ld(x, i0 + sz + sy + 1);
-    const float4 b00 = lerp4(a000, a100, c.fx), b10 = lerp4(a010, a110, c.fx);
-    const float4 b01 = lerp4(a001, a101, c.fx), b11 = lerp4(a011, a111, c.fx);
+    // block indices fit in int: a scene has fewer than 2^31 parameter blocks
+    const int G = sc.G;
+    const int i0 = (c.bz * G + c.by) * G + c.bx;
+    const int sy = G, sz = G * G;
+    float4 a[8];
+    a[0] = Store<T>::ld(x, i0);
+    a[1] = Store<T>::ld(x, i0 + 1);
+    a[2] = Store<T>::ld(x, i0 + sy);
+    a[3] = Store<T>::ld(x, i0 + sy + 1);
+    a[4] = Store<T>::ld(x, i0 + sz);
+    a[5] = Store<T>::ld(x, i0 + sz + 1);
+    a[6] = Store<T>::ld(x, i0 + sz + sy);
+    a[7] = Store<T>::ld(x, i0 + sz + sy + 1);
+#if PERF_INTERP_W
+    float W[8];
+    tri_weights(c, W);
+    return wsum8(W, a);
+#else
+    const float4 b00 = lerp4(a[0], a[1], c.fx), b10 = lerp4(a[2], a[3], c.fx);
+    const float4 b01 = lerp4(a[4], a[5], c.fx), b11 = lerp4(a[6], a[7], c.fx);
     const float4 c0 = lerp4(b00, b10, c.fy), c1 = lerp4(b01, b11, c.fy);
     return lerp4(c0, c1, c.fz);
+#endif
 }
 
 // Trilinear interpolation of x (a) and p (q) from paired storage.
 __device__ __forceinline__ void interp_grid_pair(const PairF32* xp, const DevScene& sc,
                                                  const Cell& c, float4& a, float4& q) {
-    const long long G = sc.G;
-    const long long i0 = ((long long)c.bz * G + c.by) * G + c.bx;
-    const long long sy = G, sz = G * G;
-    float4 a000, a100, a010, a110, a001, a101, a011, a111;
-    float4 q000, q100, q010, q110, q001, q101, q011, q111;
-    ld_pair(xp, i0, a000, q000);
-    ld_pair(xp, i0 + 1, a100, q100);
-    ld_pair(xp, i0 + sy, a010, q010);
-    ld_pair(xp, i0 + sy + 1, a110, q110);
-    ld_pair(xp, i0 + sz, a001, q001);
-    ld_pair(xp, i0 + sz + 1, a101, q101);
-    ld_pair(xp, i0 + sz + sy, a011, q011);
-    ld_pair(xp, i0 + sz + sy + 1, a111, q111);
-    a = lerp4(lerp4(lerp4(a000, a100, c.fx), lerp4(a010, a110, c.fx), c.fy),
-              lerp4(lerp4(a001, a101, c.fx), lerp4(a011, a111, c.fx), c.fy), c.fz);
-    q = lerp4(lerp4(lerp4(q000, q100, c.fx), lerp4(q010, q110, c.fx), c.fy),
-              lerp4(lerp4(q001, q101, c.fx), lerp4(q011, q111, c.fx), c.fy), c.fz);
+    const int G = sc.G;
+    const int i0 = (c.bz * G + c.by) * G + c.bx;
+    const int sy = G, sz = G * G;
+    float4 ax[8], ap[8];
+    ld_pair(xp, i0, ax[0], ap[0]);
+    ld_pair(xp, i0 + 1, ax[1], ap[1]);
+    ld_pair(xp, i0 + sy, ax[2], ap[2]);
+    ld_pair(xp, i0 + sy + 1, ax[3], ap[3]);
+    ld_pair(xp, i0 + sz, ax[4], ap[4]);
+    ld_pair(xp, i0 + sz + 1, ax[5], ap[5]);
+    ld_pair(xp, i0 + sz + sy, ax[6], ap[6]);
+    ld_pair(xp, i0 + sz + sy + 1, ax[7], ap[7]);
+#if PERF_INTERP_W
+    float W[8];
+    tri_weights(c, W);
+    a = wsum8(W, ax);
+    q = wsum8(W, ap);
+#else
+    a = lerp4(lerp4(lerp4(ax[0], ax[1], c.fx), lerp4(ax[2], ax[3], c.fx), c.fy),
+              lerp4(lerp4(ax[4], ax[5], c.fx), lerp4(ax[6], ax[7], c.fx), c.fy), c.fz);
+    q = lerp4(lerp4(lerp4(ap[0], ap[1], c.fx), lerp4(ap[2], ap[3], c.fx), c.fy),
+              lerp4(lerp4(ap[4], ap[5], c.fx), lerp4(ap[6], ap[7], c.fx), c.fy), c.fz);
+#endif
 }
 
 // Coordinate along one axis of the voxel with parity bit `pa` in the 2x2x2
@@ -279,14 +355,14 @@ struct Corners {
 
     __device__ __forceinline__ float4 interp(const T* __restrict__ x, const DevScene& sc,
                                              const Cell& cl) {
-        const long long G = sc.G;
+        const int G = sc.G;
 #pragma unroll
         for (int p = 0; p < 8; ++p) {
             const int nx = par_coord(cl.bx, p & 1), ny = par_coord(cl.by, (p >> 1) & 1),
                       nz = par_coord(cl.bz, p >> 2);
             const bool same = nx == par_coord(b[0], p & 1) && ny == par_coord(b[1], (p >> 1) & 1) &&
                               nz == par_coord(b[2], p >> 2);
-            if (!same) v[p] = Store<T>::ld(x, ((long long)nz * G + ny) * G + nx);
+            if (!same) v[p] = Store<T>::ld(x, (nz * G + ny) * G + nx);
         }
         b[0] = cl.bx; b[1] = cl.by; b[2] = cl.bz;
         const bool sx = cl.bx & 1, sy = cl.by & 1, sz = cl.bz & 1;
@@ -308,7 +384,7 @@ struct Corners {
 
 // Bilinear texels of one shell hit: 4 parameter-block indices and weights.
 struct ShellHit {
-    long long idx[4];
+    int idx[4];
     float w[4];
 };
 
@@ -337,11 +413,11 @@ __device__ __forceinline__ bool shell_lookup(const DevScene& sc, const Ray& R, i
     i0 = fminf(i0, (float)(sc.He - 2));
     const float fv = v - i0;
     const int r0 = (int)i0;
-    const long long base = sc.n_vox + (long long)s * sc.shell_texels;
-    hs.idx[0] = base + (long long)r0 * sc.We + c0;
-    hs.idx[1] = base + (long long)r0 * sc.We + c1;
-    hs.idx[2] = base + (long long)(r0 + 1) * sc.We + c0;
-    hs.idx[3] = base + (long long)(r0 + 1) * sc.We + c1;
+    const int base = (int)(sc.n_vox + (long long)s * sc.shell_texels);
+    hs.idx[0] = base + r0 * sc.We + c0;
+    hs.idx[1] = base + r0 * sc.We + c1;
+    hs.idx[2] = base + (r0 + 1) * sc.We + c0;
+    hs.idx[3] = base + (r0 + 1) * sc.We + c1;
     hs.w[0] = (1.0f - fu) * (1.0f - fv);
     hs.w[1] = fu * (1.0f - fv);
     hs.w[2] = (1.0f - fu) * fv;

@@ -1,0 +1,116 @@
+"""Coefficient-cached A p: the per-sample derivatives stored by a Gauss-Newton
+step's diagonal march replace the recomputation in every PCG iteration.  The
+step must equal the recomputing path up to rounding (both are checked
+against the oracle in test_gpu_parity.py), under jitter, with a re-tiled
+context, in BF16 storage, and when the store does not fit its budget."""
+import numpy as np
+import pytest
+
+from conftest import rel_l2
+from gpu_common import TOL_FP32, cuda_tensor, host, mid_state, pair_from_scene
+
+pytestmark = pytest.mark.gpu
+
+
+def _scene():
+    from scenegen import make_scene
+    return make_scene("small32")
+
+
+def _step(sc, target, x, budget, pcg_iters=3, tune=None, **kw):
+    import torch
+    from paper_2112_05598_gb300 import PERF_BF16, Context
+    ctx = Context.from_scene(sc, pcg_iters=pcg_iters, pcg_fixed=1, **kw)
+    tdt = torch.bfloat16 if kw.get("dtype") == PERF_BF16 else None
+    ctx.set_coef_budget(budget)
+    xd = cuda_tensor(x)
+    if tune is not None:
+        ctx.set_coef_budget(0)
+        ctx.autotune(xd)
+        ctx.set_coef_budget(budget)
+    st = ctx.gn_solve(xd, cuda_tensor(target, tdt), 2)
+    return st, host(xd), ctx.coef_info()
+
+
+@pytest.fixture(scope="module")
+def prob():
+    sc = _scene()
+    ctx, orc = pair_from_scene(sc)
+    target = orc.render(sc.x_gt)[0].astype(np.float32).ravel()
+    x = mid_state(np.random.default_rng(5), sc)
+    return sc, target, x
+
+
+@pytest.mark.parametrize("kw", [{}, {"jitter": 1, "seed": 9, "epoch": 3}])
+def test_coef_step_equals_recompute(prob, kw):
+    sc, target, x = prob
+    st_c, x_c, info_c = _step(sc, target, x, -1, **kw)
+    st_r, x_r, info_r = _step(sc, target, x, 0, **kw)
+    assert info_c["used"] and info_c["bytes"] > 0
+    assert not info_r["used"] and info_r["bytes"] == 0
+    for a, b in zip(st_c, st_r):
+        assert abs(a["F_before"] - b["F_before"]) <= TOL_FP32 * b["F_before"]
+        assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
+        assert a["accepted"] == b["accepted"]
+    assert rel_l2(x_c, x_r) < TOL_FP32
+
+
+def test_coef_store_size(prob):
+    """16 bytes per (tile row, lane): rows = the tile's largest sample count
+    plus one per shell, summed over the 8x4 tiles."""
+    from paper_2112_05598_gb300 import Context
+    sc, target, x = prob
+    ctx = Context.from_scene(sc, pcg_iters=1, pcg_fixed=1)
+    ctx.gn_solve(cuda_tensor(x), cuda_tensor(target), 1)
+    info = ctx.coef_info()
+    assert info["used"]
+    from oracle import Oracle
+    orc = Oracle(sc.G, sc.radii, sc.env_h, sc.env_w, sc.c2w, sc.focal, sc.width, sc.height,
+                 max_samples=sc.cfg.max_samples)
+    n_rays = len(sc.c2w) * sc.height * sc.width
+    K = np.array([orc.ray_info(r)["K"] for r in range(n_rays)]).reshape(len(sc.c2w), sc.height,
+                                                                        sc.width)
+    rows = 0
+    for c in range(K.shape[0]):
+        for ty in range(0, sc.height, 4):
+            for tx in range(0, sc.width, 8):
+                rows += int(K[c, ty:ty + 4, tx:tx + 8].max()) + len(sc.radii)
+    assert info["bytes"] == rows * 32 * 16
+
+
+def test_coef_retiled_context(prob):
+    """Tiles chosen by the autotuner without the store, then the store laid
+    out for that tiling."""
+    sc, target, x = prob
+    st_c, x_c, info_c = _step(sc, target, x, -1, tune=True)
+    st_r, x_r, _ = _step(sc, target, x, 0)
+    assert info_c["used"]
+    assert rel_l2(x_c, x_r) < TOL_FP32
+
+
+def test_coef_over_budget_recomputes(prob):
+    sc, target, x = prob
+    st_s, x_s, info_s = _step(sc, target, x, 1024)
+    st_r, x_r, _ = _step(sc, target, x, 0)
+    assert not info_s["used"] and info_s["bytes"] == 0
+    assert rel_l2(x_s, x_r) < TOL_FP32
+
+
+def test_coef_bf16(prob):
+    from paper_2112_05598_gb300 import PERF_BF16
+    sc, target, x = prob
+    st_c, x_c, info_c = _step(sc, target, x, -1, dtype=PERF_BF16)
+    st_r, x_r, _ = _step(sc, target, x, 0, dtype=PERF_BF16)
+    assert info_c["used"]
+    for a, b in zip(st_c, st_r):
+        assert abs(a["F_after"] - b["F_after"]) <= 1e-4 * b["F_after"]
+    assert rel_l2(x_c, x_r) < 1e-4
+
+
+def test_coef_autotune_reports_coef(prob):
+    from paper_2112_05598_gb300 import Context
+    sc, target, x = prob
+    ctx = Context.from_scene(sc, pcg_iters=2, pcg_fixed=1)
+    t = ctx.autotune(cuda_tensor(x))
+    assert t["coef"] == 1 and (t["tile_w"], t["tile_h"]) == (8, 4) and t["apply_ms"] > 0
+    assert ctx.coef_info()["used"]

@@ -171,12 +171,19 @@ def _gn_trajectory(small, pcg_iters, steps):
     return out
 
 
-def test_gn_steps_parameter_parity(small):
+@pytest.mark.parametrize("coef", [True, False])
+def test_gn_steps_parameter_parity(small, coef):
     """Five GPU Gauss-Newton steps (PCG with the paper's typical 3 iterations,
     Algorithm 3 line search, projection), each against one oracle step from
-    the same x: parameters within 1e-4 relative L2."""
+    the same x: parameters within 1e-4 relative L2.  Both A p forms: from the
+    per-sample coefficients stored by the step's diagonal march (coef) and
+    recomputed by every march."""
+    small["ctx"].set_coef_budget(-1 if coef else 0)
     checked = 0
-    for step, (st, ref, xg, tie) in enumerate(_gn_trajectory(small, 3, small["sc"].cfg.gn_steps)):
+    traj = _gn_trajectory(small, 3, small["sc"].cfg.gn_steps)
+    assert small["ctx"].coef_info()["used"] == coef
+    small["ctx"].set_coef_budget(-1)
+    for step, (st, ref, xg, tie) in enumerate(traj):
         assert st["accepted"] == ref.accepted
         assert abs(st["F_before"] - ref.F_before) <= TOL_FP32 * ref.F_before
         if abs(st["gamma"] - ref.gamma) > 1e-9:
