@@ -58,7 +58,7 @@ FLOP_PER_SAMPLE_COEF = 207
 
 # DRAM traffic of one A p launch, from the ncu capture summarised in this
 # file; it applies only while the kernel sources hash to the recorded value.
-TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "apply_traffic_scale128.md")
+TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "apply_coef_traffic_scale128.md")
 KERNEL_SOURCES = ("paper_2112_05598_gb300/csrc/k_march.cu",
                   "paper_2112_05598_gb300/csrc/perf_device.cuh")
 
@@ -615,6 +615,7 @@ def run_ours(args, rank, world, local):
         "config": {"workload": _workload_desc(sc) + (" (BF16 storage form)" if bf else ""),
                    "n_params": sc.n_params, "n_rays": sc.n_rays,
                    "samples_per_march": samples, "tuning": tuning,
+                   "coef_store_bytes": ctx.coef_info()["bytes"],
                    "l2": "inputs larger than L2: targets and residuals 768 MB each per step"},
         "gpu_launches": int(launches),
         "rays_per_s": 2.0 * sc.n_rays * pcg_total / (ms / 1000.0),

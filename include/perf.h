@@ -249,9 +249,9 @@ perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_use
  * then, for FP32 scenes, times A p from separate x and p arrays against the
  * paired records that perf_gn_solve uses by default and keeps the separate
  * arrays only when 3% faster.  When the coefficient store fits its budget it
- * instead stores the coefficients at x and times the coefficient-cached A p
- * over the CTA caps with 8x4 tiles.  Reports the choice in *out (HOST, may be
- * NULL).  Uses the PCG workspace; synchronises. */
+ * instead lays the store out for every tile shape, fills it at x and times
+ * the coefficient-cached A p over the CTA caps (same 3% rule).  Reports the
+ * choice in *out (HOST, may be NULL).  Uses the PCG workspace; synchronises. */
 perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
                           void* stream);
 perf_status perf_set_lpc(perf_ctx* ctx, perf_lpc* lpc);
@@ -344,8 +344,14 @@ perf_status perf_batch_residual(perf_batch* b, const float* x, const float* targ
                                 float* r_out, double* F_out, void* stream);
 /* Times the A p launch at x over tile shapes 8x4, 4x8, 16x2, 32x1 and CTA caps
  * {all, 3, 2}, keeps the fastest (used by every later launch) and reports it
- * in *out (HOST, may be NULL).  Synchronises. */
+ * in *out (HOST, may be NULL); with the coefficient store (when it fits) the
+ * coefficient-cached A p is timed, its store filled at x.  Synchronises. */
 perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out, void* stream);
+/* The coefficient store of perf_set_coef_budget for a batch (rows over the
+ * batch's global pixel-tile list; perf_batch_gn_solve's diagonal march fills
+ * it and the captured PCG loop reads it). */
+perf_status perf_batch_set_coef_budget(perf_batch* b, int64_t bytes);
+perf_status perf_batch_coef_info(perf_batch* b, int64_t* bytes_held, int32_t* last_used);
 /* n_steps Gauss-Newton steps for every scene (Algorithm 2 per scene: with
  * opts.pcg_fixed exactly opts.pcg_iters iterations, else at most that many
  * with the exit tests of perf_options, a scene's device exit flag making

@@ -120,6 +120,8 @@ _SIGS = {
     "perf_batch_render": [_VP, _VP, _VP, _VP],
     "perf_batch_residual": [_VP, _VP, _VP, _VP, _VP, _VP],
     "perf_batch_autotune": [_VP, _VP, ctypes.POINTER(Tuning), _VP],
+    "perf_batch_set_coef_budget": [_VP, ctypes.c_int64],
+    "perf_batch_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
     "perf_batch_gn_solve": [_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(GNStats), _VP],
 }
 _OPTIONAL_SIGS = {
@@ -457,7 +459,19 @@ class Batch:
         t = Tuning()
         self._check(self.lib.perf_batch_autotune(self.h, _ptr(x), ctypes.byref(t), _stream(stream)),
                     "batch autotune")
-        return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms)
+        return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms,
+                    coef=t.coef)
+
+    def set_coef_budget(self, nbytes):
+        """Budget of the coefficient store: -1 automatic, 0 off, > 0 bytes."""
+        self._check(self.lib.perf_batch_set_coef_budget(self.h, int(nbytes)), "batch set_coef_budget")
+
+    def coef_info(self):
+        b = ctypes.c_int64(0)
+        u = ctypes.c_int32(0)
+        self._check(self.lib.perf_batch_coef_info(self.h, ctypes.byref(b), ctypes.byref(u)),
+                    "batch coef_info")
+        return dict(bytes=int(b.value), used=bool(u.value))
 
     def gn_solve(self, x, target, n_steps, stream=None):
         stats = (GNStats * max(int(n_steps) * self.n, 1))()

@@ -31,7 +31,6 @@
 // warp-uniform, so the lanes of a warp (an 8x4 pixel tile) that evict the
 // same voxel do it in the same 16-byte vector atomic, which the load/store
 // unit merges before it reaches L2.
-#include <type_traits>
 #include "perf_device.cuh"
 #include "perf_kernels.h"
 
@@ -251,31 +250,12 @@ struct Window {
 };
 
 
-// Index of a voxel / texel block in a scatter target: canonical order, or
-// the brick order of the A p accumulation buffer (see ApMap).
-// A key is the sum of one term per axis (axis(a, c)).
+// Index of a voxel / texel block in a scatter target.
 struct CanonKey {
     int G;
-    __device__ __forceinline__ int axis(int a, int c) const {
-        return a == 0 ? c : a == 1 ? c * G : c * G * G;
-    }
     __device__ __forceinline__ int key(int x, int y, int z) const { return (z * G + y) * G + x; }
     __device__ __forceinline__ int shell(int idx) const { return idx; }
 };
-struct BrickKey {
-    int my, mz, shell_off;
-    __device__ __forceinline__ int axis(int a, int c) const {
-        return brick_part(c, a, a == 0 ? 64 : a == 1 ? my : mz);
-    }
-    __device__ __forceinline__ int key(int x, int y, int z) const {
-        return brick_part(x, 0, 64) + brick_part(y, 1, my) + brick_part(z, 2, mz);
-    }
-    __device__ __forceinline__ int shell(int idx) const { return idx + shell_off; }
-};
-__device__ __forceinline__ BrickKey brick_key(const DevScene& sc) {
-    const int Gq = (sc.G + 3) >> 2;
-    return BrickKey{64 * Gq, 64 * Gq * Gq, (int)(64ll * Gq * Gq * Gq - sc.n_vox)};
-}
 
 // VJP sink: slot = (a, s) with a = sum W w_i and s = sum W v.dH/dsigma_i;
 // the parameter block receives (a v_0, a v_1, a v_2, s).
@@ -316,43 +296,8 @@ struct DiagSink {
 // Move the window (all lanes; `on` = this lane moves) to base nb, handing the
 // voxels that leave it to the sink.  A voxel never re-enters a ray's window:
 // its trilinear support meets the ray in one run of samples.
-#ifndef PERF_WIN_SKIP
-#define PERF_WIN_SKIP 1
-#endif
 template <int NV, class Sink>
 __device__ __forceinline__ void win_move(Window<NV>& w, const int (&nb)[3], bool on, int G, Sink& sk) {
-#if PERF_WIN_SKIP
-    // Along axis a the window's voxel of parity q moves iff par_coord changes;
-    // slot p leaves iff one of its three axis voxels moves.  Slots that no
-    // lane of the warp leaves are skipped as a whole (warp-uniform branch).
-    unsigned ev = 0;
-    if (on) {
-        const unsigned axis_slots[3][2] = {{0x55u, 0xAAu}, {0x33u, 0xCCu}, {0x0Fu, 0xF0u}};
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int q = 0; q < 2; ++q)
-                if (par_coord(w.b[a], q) != par_coord(nb[a], q)) ev |= axis_slots[a][q];
-    }
-    const unsigned wev = __reduce_or_sync(kFull, ev);
-    if (wev) {
-        int k[3][2];
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-#pragma unroll
-            for (int q = 0; q < 2; ++q) k[a][q] = sk.km.axis(a, par_coord(w.b[a], q));
-#pragma unroll
-        for (int p = 0; p < 8; ++p) {
-            if (!(wev & (1u << p))) continue;
-            const bool e = (ev >> p) & 1u;
-            sk.put(e, k[0][p & 1] + k[1][(p >> 1) & 1] + k[2][p >> 2], w.v[p]);
-            if (e) {
-#pragma unroll
-                for (int q = 0; q < NV; ++q) w.v[p][q] = 0.0f;
-            }
-        }
-    }
-#else
 #pragma unroll
     for (int p = 0; p < 8; ++p) {
         const int ox = par_coord(w.b[0], p & 1), oy = par_coord(w.b[1], (p >> 1) & 1),
@@ -366,7 +311,6 @@ __device__ __forceinline__ void win_move(Window<NV>& w, const int (&nb)[3], bool
             for (int q = 0; q < NV; ++q) w.v[p][q] = 0.0f;
         }
     }
-#endif
     if (on) { w.b[0] = nb[0]; w.b[1] = nb[1]; w.b[2] = nb[2]; }
 }
 
@@ -526,8 +470,7 @@ __device__ __forceinline__ void forward_tile(const DevScene& sc, const T* __rest
 }
 
 // All 32 lanes call it (the back-to-front sweep is warp-synchronous).
-// BRICK: the J^T v / A p target is in brick order (see ApMap).
-template <typename T, typename TP, int MODE, typename TV, bool BRICK = false>   // 0 vjp, 1 apply A, 2 diag (+grad)
+template <typename T, typename TP, int MODE, typename TV>   // 0 vjp, 1 apply A, 2 diag (+grad)
 __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __restrict__ x,
                                              const TP* __restrict__ p, const TV* __restrict__ v,
                                              float* __restrict__ out, float* __restrict__ out2,
@@ -563,9 +506,6 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
         DiagSink sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}};
         backward_sweep<4>(sc, x, R, ray, act, V, vr, sk,
                           coef ? coef + tile_off[tile] * 32 + lane : nullptr);
-    } else if (BRICK) {
-        VjpSink<BrickKey> sk{out, vr[0], vr[1], vr[2], brick_key(sc)};
-        backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
     } else {
         VjpSink<CanonKey> sk{out, vr[0], vr[1], vr[2], CanonKey{sc.G}};
         backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
@@ -605,7 +545,7 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
     }
 }
 
-template <typename T, typename TP, int MODE, typename TV, bool BRICK = false>
+template <typename T, typename TP, int MODE, typename TV>
 __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PERF_MIN_CTAS)
     k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
@@ -617,8 +557,8 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
                                                       const long long* __restrict__ tile_off) {
     double acc = 0.0;
     PERF_TILE_LOOP {
-        scatter_tile<T, TP, MODE, TV, BRICK>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
-                                             tile_off);
+        scatter_tile<T, TP, MODE, TV>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
+                                      tile_off);
     }
     if (MODE == 1 && pap) block_add_f64<kWarps>(acc, pap);
 }
@@ -654,7 +594,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) 
     }
 }
 
-template <typename TP, bool BRICK>
+template <typename TP>
 __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __restrict__ p,
                                                 const float4* __restrict__ coef,
                                                 const long long* __restrict__ tile_off,
@@ -674,9 +614,9 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
     float J[3] = {0.0f, 0.0f, 0.0f};
     if (act) {
         for (int k = 0; k < R.K; ++k) {
+            const float4 c = __ldcs(crow + (long long)k * 32);
             const Cell cl = sample_cell(sc, R, ray, k);
             const float4 q = interp_grid(p, sc, cl);
-            const float4 c = __ldcs(crow + (long long)k * 32);
             J[0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[0]));
             J[1] = fmaf(c.x, q.y, fmaf(c.z, q.w, J[1]));
             J[2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[2]));
@@ -695,10 +635,7 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
         if (J[0] == 0.0f && J[1] == 0.0f && J[2] == 0.0f) act = false;
     }
     // J^T (J p): the scatter of Algorithm 1 with v = J p
-    typedef typename std::conditional<BRICK, BrickKey, CanonKey>::type Key;
-    Key km;
-    if constexpr (BRICK) km = brick_key(sc); else km = CanonKey{sc.G};
-    VjpSink<Key> sk{out, J[0], J[1], J[2], km};
+    VjpSink<CanonKey> sk{out, J[0], J[1], J[2], CanonKey{sc.G}};
     for (int s = sc.S - 1; s >= 0; --s) {
         ShellHit hs;
         const bool hit = act && shell_lookup(sc, R, s, hs);
@@ -720,6 +657,8 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
     w.b[0] = w.b[1] = w.b[2] = 0;
     for (int k = Kmax - 1; k >= 0; --k) {
         const bool on = k < Kl;
+        // issued first: its latency overlaps the cell and window work
+        const float4 c = on ? __ldcs(crow + (long long)k * 32) : make_float4(0.f, 0.f, 0.f, 0.f);
         Cell cl;
         cl.bx = w.b[0]; cl.by = w.b[1]; cl.bz = w.b[2];
         cl.fx = cl.fy = cl.fz = 0.0f;
@@ -730,7 +669,6 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
         const int nb[3] = {cl.bx, cl.by, cl.bz};
         win_move(w, nb, on, sc.G, sk);
         if (on) {
-            const float4 c = __ldcs(crow + (long long)k * 32);
             const float val[2] = {c.x, J[0] * c.y + J[1] * c.z + J[2] * c.w};
             win_add(w, cl, val);
         }
@@ -742,12 +680,12 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
                w.v[q]);
 }
 
-template <typename TP, bool BRICK>
+template <typename TP>
 __global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
     k_apply_coef(DevScene sc, const TP* __restrict__ p, const float4* __restrict__ coef,
                  const long long* __restrict__ tile_off, float* __restrict__ out, double* pap) {
     double acc = 0.0;
-    PERF_TILE_LOOP { coef_apply_tile<TP, BRICK>(sc, p, coef, tile_off, out, tile, lane, acc); }
+    PERF_TILE_LOOP { coef_apply_tile<TP>(sc, p, coef, tile_off, out, tile, lane, acc); }
     if (pap) block_add_f64<kWarps>(acc, pap);
 }
 
@@ -836,7 +774,9 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
                                                             float* __restrict__ out,
                                                             float* __restrict__ out2, double* pap,
                                                             int pap_stride,
-                                                            const PcgScalars* __restrict__ pcg) {
+                                                            const PcgScalars* __restrict__ pcg,
+                                                            float4* __restrict__ coef,
+                                                            const long long* __restrict__ tile_off) {
     __shared__ BatchItem s_items[kBatchSmem];
     const BatchItem* it = stage_items(items, n, s_items);
     const int lane = threadIdx.x & 31;
@@ -850,11 +790,62 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
         scatter_tile<float, float, MODE, float>(b.sc, x + b.x_off, p ? p + b.x_off : nullptr,
                                                 v ? v + 3 * b.r_off : nullptr, out + b.x_off,
                                                 out2 ? out2 + b.x_off : nullptr, nullptr, tile,
-                                                lane, acc);
+                                                lane, acc, coef,
+                                                tile_off ? tile_off + b.tile_off : nullptr);
         if (MODE == 1) {
             acc = warp_sum(acc);
             if (lane == 0 && acc != 0.0) atomicAdd(&pap[(long long)sidx * pap_stride], acc);
         }
+    }
+}
+
+// Coefficient-cached A p over a batch (tile_off: rows of the global tile list;
+// scenes whose PCG has exited are skipped).
+__global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
+    k_apply_coef_batch(const BatchItem* __restrict__ items, const long long* __restrict__ start,
+                       int n, long long total, unsigned long long* counter,
+                       const float* __restrict__ p, const float4* __restrict__ coef,
+                       const long long* __restrict__ tile_off, float* __restrict__ out, double* pap,
+                       int pap_stride, const PcgScalars* __restrict__ pcg) {
+    __shared__ BatchItem s_items[kBatchSmem];
+    const BatchItem* it = stage_items(items, n, s_items);
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        int sidx = 0;
+        const long long tile = batch_next(counter, total, start, n, lane, sidx);
+        if (tile < 0) break;
+        if (pcg && pcg[sidx].done) continue;
+        const BatchItem& b = it[sidx];
+        double acc = 0.0;
+        coef_apply_tile<float>(b.sc, p + b.x_off, coef, tile_off + b.tile_off, out + b.x_off, tile,
+                               lane, acc);
+        acc = warp_sum(acc);
+        if (lane == 0 && acc != 0.0) atomicAdd(&pap[(long long)sidx * pap_stride], acc);
+    }
+}
+
+// rows[t] for every tile t of the batch's global tile list.
+__global__ void __launch_bounds__(kThreads) k_tile_rows_batch(const BatchItem* __restrict__ items,
+                                                              const long long* __restrict__ start,
+                                                              int n, long long total, int* rows) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (long long)gridDim.x * kWarps;
+    for (long long t = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); t < total; t += nw) {
+        int lo = 0, hi = n - 1;               // last scene with start <= t
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (start[mid] <= t) lo = mid; else hi = mid - 1;
+        }
+        const DevScene& sc = items[lo].sc;
+        long long ray;
+        int K = 0;
+        if (tile_pixel(sc, t - start[lo], lane, ray)) {
+            Ray R;
+            ray_setup(sc, ray, R);
+            K = R.K;
+        }
+        K = __reduce_max_sync(kFull, K);
+        if (lane == 0) rows[t] = K + sc.S;
     }
 }
 
@@ -948,13 +939,13 @@ cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void*
     return launch_jvp_t<float, float>(sc, x, p, out, st);
 }
 
-template <typename T, typename TP, int MODE, typename TV, bool BRICK = false>
+template <typename T, typename TP, int MODE, typename TV>
 cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, const void* v,
                              float* out, float* out2, double* pap, cudaStream_t st,
                              float* out3 = nullptr, float* coef = nullptr,
                              const long long* tile_off = nullptr) {
     if (sc.n_tiles == 0) return cudaSuccess;
-    auto fn = k_scatter<T, TP, MODE, TV, BRICK>;
+    auto fn = k_scatter<T, TP, MODE, TV>;
     fn<<<grid_blocks((const void*)fn, sc.n_tiles, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
         out2, out3, pap, reinterpret_cast<float4*>(coef), tile_off);
@@ -984,21 +975,8 @@ cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* 
 
 // A p from paired x / p storage (FP32 scenes).
 cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
-                              cudaStream_t st, bool brick) {
-    return brick ? launch_scatter_t<PairF32, PairF32, 1, float, true>(sc, xp, xp, nullptr, out,
-                                                                      nullptr, pap, st)
-                 : launch_scatter_t<PairF32, PairF32, 1, float>(sc, xp, xp, nullptr, out, nullptr,
-                                                                pap, st);
-}
-
-// A p into a brick-order buffer from separate x and p arrays.
-cudaError_t launch_apply_brick(const DevScene& sc, int dtype, const void* x, const void* p,
-                               int p_dtype, float* out, double* pap, cudaStream_t st) {
-    typedef __nv_bfloat16 B;
-    if (dtype == 1)
-        return p_dtype == 1 ? launch_scatter_t<B, B, 1, float, true>(sc, x, p, nullptr, out, nullptr, pap, st)
-                            : launch_scatter_t<B, float, 1, float, true>(sc, x, p, nullptr, out, nullptr, pap, st);
-    return launch_scatter_t<float, float, 1, float, true>(sc, x, p, nullptr, out, nullptr, pap, st);
+                              cudaStream_t st) {
+    return launch_scatter_t<PairF32, PairF32, 1, float>(sc, xp, xp, nullptr, out, nullptr, pap, st);
 }
 
 cudaError_t launch_tile_rows(const DevScene& sc, int* rows, cudaStream_t st) {
@@ -1008,12 +986,12 @@ cudaError_t launch_tile_rows(const DevScene& sc, int* rows, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-template <typename TP, bool BRICK>
+template <typename TP>
 cudaError_t launch_apply_coef_t(const DevScene& sc, const void* p, const float* coef,
                                 const long long* tile_off, float* out, double* pap,
                                 cudaStream_t st) {
     if (sc.n_tiles == 0) return cudaSuccess;
-    auto fn = k_apply_coef<TP, BRICK>;
+    auto fn = k_apply_coef<TP>;
     fn<<<grid_blocks((const void*)fn, sc.n_tiles, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const TP*>(p), reinterpret_cast<const float4*>(coef), tile_off, out, pap);
     count_launch();
@@ -1021,14 +999,9 @@ cudaError_t launch_apply_coef_t(const DevScene& sc, const void* p, const float* 
 }
 
 cudaError_t launch_apply_coef(const DevScene& sc, const void* p, int p_dtype, const float* coef,
-                              const long long* tile_off, float* out, double* pap, bool brick,
-                              cudaStream_t st) {
-    typedef __nv_bfloat16 B;
-    if (p_dtype == 1)
-        return brick ? launch_apply_coef_t<B, true>(sc, p, coef, tile_off, out, pap, st)
-                     : launch_apply_coef_t<B, false>(sc, p, coef, tile_off, out, pap, st);
-    return brick ? launch_apply_coef_t<float, true>(sc, p, coef, tile_off, out, pap, st)
-                 : launch_apply_coef_t<float, false>(sc, p, coef, tile_off, out, pap, st);
+                              const long long* tile_off, float* out, double* pap, cudaStream_t st) {
+    return p_dtype == 1 ? launch_apply_coef_t<__nv_bfloat16>(sc, p, coef, tile_off, out, pap, st)
+                        : launch_apply_coef_t<float>(sc, p, coef, tile_off, out, pap, st);
 }
 
 // ------------------------------------------------------ batched launchers
@@ -1071,18 +1044,44 @@ cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start,
                                  long long total, unsigned long long* counter, const float* x,
                                  const float* p, const float* v, float* out, float* out2,
                                  double* pap, int pap_stride, int mode, int cap_per_sm,
-                                 cudaStream_t st, const PcgScalars* pcg) {
+                                 cudaStream_t st, const PcgScalars* pcg, float* coef,
+                                 const long long* tile_off) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess || total == 0) return e;
     if (mode == 1) {
         auto fn = k_scatter_batch<1>;
         fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
-            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg);
+            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg, nullptr,
+            nullptr);
     } else {
         auto fn = k_scatter_batch<2>;
         fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
-            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg);
+            items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg,
+            reinterpret_cast<float4*>(coef), tile_off);
     }
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_apply_coef_batch(const BatchItem* items, const long long* start, int n,
+                                    long long total, unsigned long long* counter, const float* p,
+                                    const float* coef, const long long* tile_off, float* out,
+                                    double* pap, int pap_stride, int cap_per_sm, cudaStream_t st,
+                                    const PcgScalars* pcg) {
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess || total == 0) return e;
+    k_apply_coef_batch<<<batch_blocks((const void*)k_apply_coef_batch, cap_per_sm), kThreads, 0, st>>>(
+        items, start, n, total, counter, p, reinterpret_cast<const float4*>(coef), tile_off, out,
+        pap, pap_stride, pcg);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_rows_batch(const BatchItem* items, const long long* start, int n,
+                                   long long total, int* rows, cudaStream_t st) {
+    if (total == 0) return cudaSuccess;
+    k_tile_rows_batch<<<batch_blocks((const void*)k_tile_rows_batch, 0), kThreads, 0, st>>>(
+        items, start, n, total, rows);
     count_launch();
     return cudaGetLastError();
 }

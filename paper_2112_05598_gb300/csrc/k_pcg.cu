@@ -119,7 +119,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const lon
                                                         const float4* __restrict__ B, long long n_block,
                                                         double* delta, double* rho, double* p,
                                                         float4* p32, __nv_bfloat16* p16, float4* Ap,
-                                                        PcgScalars* s, float4* pxp, ApMap am) {
+                                                        PcgScalars* s, float4* pxp) {
     s += blockIdx.y;
     double aR = 0.0, aRz = 0.0;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -131,7 +131,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const lon
         st4(p, v, z);
         store_p(p32, p16, pxp, v, z);
         st4(delta, v, D4{0.0, 0.0, 0.0, 0.0});
-        Ap[ap_index(am, v)] = zero;
+        Ap[v] = zero;
         aR += dot4(r, r);
         aRz += dot4(r, z);
     }
@@ -173,8 +173,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, const lo
                                                          const float4* __restrict__ Ap,
                                                          const float4* __restrict__ d4,
                                                          const float4* __restrict__ B,
-                                                         long long n_block, PcgScalars* s,
-                                                         ApMap am) {
+                                                         long long n_block, PcgScalars* s) {
     s += blockIdx.y;
     if (s->done) return;
     const double pAp = s->pAp;
@@ -183,7 +182,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, const lo
     double aR = 0.0, aRz = 0.0;
     SEG_LOOP(v) {
         const D4 pv = ld4(p, v);
-        const float4 av = Ap[ap_index(am, v)];
+        const float4 av = Ap[v];
         D4 dv = ld4(delta, v), r = ld4(rho, v);
         dv.x = fma(alpha, pv.x, dv.x); dv.y = fma(alpha, pv.y, dv.y);
         dv.z = fma(alpha, pv.z, dv.z); dv.w = fma(alpha, pv.w, dv.w);
@@ -238,8 +237,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const long 
                                                       const float4* __restrict__ d4,
                                                       const float4* __restrict__ B, long long n_block,
                                                       double* p, float4* p32, __nv_bfloat16* p16,
-                                                      float4* Ap, const PcgScalars* s, float4* pxp,
-                                                      ApMap am) {
+                                                      float4* Ap, const PcgScalars* s, float4* pxp) {
     s += blockIdx.y;
     if (s->done) return;
     const double beta = s->beta;
@@ -251,7 +249,7 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const long 
         pv.z = fma(beta, pv.z, z.z); pv.w = fma(beta, pv.w, z.w);
         st4(p, v, pv);
         store_p(p32, p16, pxp, v, pv);
-        Ap[ap_index(am, v)] = zero;
+        Ap[v] = zero;
     }
 }
 
@@ -345,14 +343,14 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, l
                                  double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                                  PcgScalars* s, int max_iter, int fixed, double eps_rel,
                                  double stall, const float* blocks, long long n_block,
-                                 cudaStream_t st, float* pxp, ApMap am) {
+                                 cudaStream_t st, float* pxp) {
     const long long nb = n / 4;
     cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars) * (size_t)(n_seg > 0 ? n_seg : 1), st);
     if (e != cudaSuccess) return e;
     if (nb > 0) {
         k_pcg_begin<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
             nb, seg, CF4(grad), CF4(diag), CF4(blocks), n_block, delta, rho, p, F4(p32), p16,
-            F4(Ap), s, F4(pxp), am);
+            F4(Ap), s, F4(pxp));
         count_launch();
     }
     const int ns = n_seg > 1 ? n_seg : 1;
@@ -364,20 +362,19 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, l
 cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
                              double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                              PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
-                             const float* blocks, long long n_block, cudaStream_t st, float* pxp,
-                             ApMap am) {
+                             const float* blocks, long long n_block, cudaStream_t st, float* pxp) {
     return launch_pcg_begin_seg(n, 1, nullptr, n / 4, grad, diag, delta, rho, p, p32, p16, Ap, s,
-                                max_iter, fixed, eps_rel, stall, blocks, n_block, st, pxp, am);
+                                max_iter, fixed, eps_rel, stall, blocks, n_block, st, pxp);
 }
 
 cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                                   double* delta, double* rho, const double* p, const float* Ap,
                                   const float* diag, const float* blocks, long long n_block,
-                                  PcgScalars* s, cudaStream_t st, ApMap am) {
+                                  PcgScalars* s, cudaStream_t st) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_pcg_update<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
-            nb, seg, delta, rho, p, CF4(Ap), CF4(diag), CF4(blocks), n_block, s, am);
+            nb, seg, delta, rho, p, CF4(Ap), CF4(diag), CF4(blocks), n_block, s);
         count_launch();
     }
     return cudaGetLastError();
@@ -385,9 +382,9 @@ cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, 
 
 cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
                               const float* Ap, const float* diag, const float* blocks,
-                              long long n_block, PcgScalars* s, cudaStream_t st, ApMap am) {
+                              long long n_block, PcgScalars* s, cudaStream_t st) {
     return launch_pcg_update_seg(n, 1, nullptr, n / 4, delta, rho, p, Ap, diag, blocks, n_block, s,
-                                 st, am);
+                                 st);
 }
 
 cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st) {
@@ -402,11 +399,11 @@ cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st) { return launch_pc
 cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                                const double* rho, const float* diag, const float* blocks,
                                long long n_block, double* p, float* p32, __nv_bfloat16* p16,
-                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp, ApMap am) {
+                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_pcg_dir<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
-            nb, seg, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s, F4(pxp), am);
+            nb, seg, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s, F4(pxp));
         count_launch();
     }
     return cudaGetLastError();
@@ -414,9 +411,9 @@ cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, lon
 
 cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
                            long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                           PcgScalars* s, cudaStream_t st, float* pxp, ApMap am) {
+                           PcgScalars* s, cudaStream_t st, float* pxp) {
     return launch_pcg_dir_seg(n, 1, nullptr, n / 4, rho, diag, blocks, n_block, p, p32, p16, Ap, s,
-                              st, pxp, am);
+                              st, pxp);
 }
 
 cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,

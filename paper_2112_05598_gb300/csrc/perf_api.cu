@@ -28,11 +28,6 @@ cudaError_t launch_block_jacobi(const float* diag, const float* cross, float* bl
                                 cudaStream_t st);
 }  // namespace perf
 
-// A p accumulation order of the PCG workspace: brick order (1) or canonical.
-#ifndef PERF_AP_BRICK
-#define PERF_AP_BRICK 1
-#endif
-
 struct perf_ctx {
     perf_scene scene;
     perf_options opts;
@@ -50,7 +45,6 @@ struct perf_ctx {
     float* p32 = nullptr;
     float* xp = nullptr;        // paired (x, p) records for A p (FP32 scenes)
     bool pair = true;           // Gauss-Newton A p reads the paired records
-    perf::ApMap am{};           // order of the PCG's A p buffer (brick order)
     // coefficient-cached A p: per-sample (w_i, dH/dsigma_i) of the current
     // Gauss-Newton step, stored by its diagonal march (see k_march.cu)
     long long coef_budget = -1;        // bytes; -1 automatic, 0 off
@@ -131,14 +125,7 @@ perf_status ensure_pcg(perf_ctx* ctx) {
     CK(alloc(&ctx->rho, ctx->n));
     CK(alloc(&ctx->p, ctx->n));
     CK(alloc(&ctx->p32, ctx->n));
-    if (!ctx->Ap) {
-        // brick order: the grid part is padded to 4^3 bricks; the padding is
-        // never scattered to and stays zero
-        ctx->am = perf::ap_map(ctx->ds.G, PERF_AP_BRICK != 0);
-        const long long n_ap = ctx->n + 4 * (ctx->am.n_vox_pad - ctx->am.n_vox);
-        CK(alloc(&ctx->Ap, n_ap));
-        CK(cudaMemset(ctx->Ap, 0, sizeof(float) * (size_t)n_ap));
-    }
+    CK(alloc(&ctx->Ap, ctx->n));
     if (ctx->scene.dtype == PERF_BF16) CK(alloc(&ctx->p16, ctx->n));
     else CK(alloc(&ctx->xp, 2 * ctx->n));
     return PERF_OK;
@@ -190,7 +177,12 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
     }
     if (ctx->coef_bytes < need) {
         if (ctx->coef) { cudaFree(ctx->coef); ctx->coef = nullptr; ctx->coef_bytes = 0; }
-        CK(cudaMalloc(&ctx->coef, need > 0 ? need : 16));
+        if (cudaMalloc(&ctx->coef, need > 0 ? need : 16) != cudaSuccess) {
+            // out of memory after all (fragmentation, another user): recompute
+            cudaGetLastError();
+            ctx->coef = nullptr;
+            return PERF_OK;
+        }
         ctx->coef_bytes = need;
     }
     *use = true;
@@ -454,7 +446,7 @@ perf_status perf_pcg_begin(perf_ctx* ctx, const float* grad, const float* diag, 
     CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p, ctx->p32,
                               ctx->p16, ctx->Ap, ctx->s, ctx->opts.pcg_iters, ctx->opts.pcg_fixed,
                               ctx->opts.pcg_eps_rel, ctx->opts.pcg_stall, B, ctx->n_block,
-                              S(stream), nullptr, ctx->am));
+                              S(stream)));
     return PERF_OK;
 }
 
@@ -464,18 +456,17 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
 
 namespace {
 
-// A p into the PCG workspace (its order) from separate x and p arrays.
+// A p into the PCG workspace from separate x and p arrays.
 cudaError_t apply_arrays(perf_ctx* ctx, const void* x, const void* pp, double* pap, cudaStream_t st) {
     const int pdt = ctx->scene.dtype == PERF_BF16 ? PERF_BF16 : PERF_F32;
-    return PERF_AP_BRICK ? perf::launch_apply_brick(ctx->ds, ctx->scene.dtype, x, pp, pdt, ctx->Ap, pap, st)
-                         : perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, pdt, nullptr,
-                                                ctx->Ap, nullptr, pap, st);
+    return perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, pdt, nullptr, ctx->Ap, nullptr,
+                                pap, st);
 }
 
 // One Algorithm 2 iteration on the context workspace with diagonal `diag`
 // and block preconditioner B (null: Jacobi).  paired: A p reads the paired
-// records ctx->xp, whose x half holds x (FP32 scenes).  A p accumulates in
-// brick order (ctx->am).
+// records ctx->xp, whose x half holds x (FP32 scenes); coef: A p from the
+// coefficient store of the current Gauss-Newton step.
 perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const float* B, cudaStream_t st,
                      bool paired = false, bool coef = false) {
     const bool bf = ctx->scene.dtype == PERF_BF16;
@@ -483,18 +474,18 @@ perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const floa
     t_begin(ctx, PERF_T_APPLY, st);
     if (coef)
         CK(perf::launch_apply_coef(ctx->ds, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef, ctx->tile_off,
-                                   ctx->Ap, &ctx->s->pAp, PERF_AP_BRICK != 0, st));
+                                   ctx->Ap, &ctx->s->pAp, st));
     else if (paired)
-        CK(perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, &ctx->s->pAp, st, PERF_AP_BRICK != 0));
+        CK(perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, &ctx->s->pAp, st));
     else
         CK(apply_arrays(ctx, x, pp, &ctx->s->pAp, st));
     t_end(ctx, PERF_T_APPLY, st);
     t_begin(ctx, PERF_T_VECTOR, st);
     CK(perf::launch_pcg_update(ctx->n, ctx->delta, ctx->rho, ctx->p, ctx->Ap, diag, B, ctx->n_block,
-                               ctx->s, st, ctx->am));
+                               ctx->s, st));
     CK(perf::launch_pcg_finish(ctx->s, st));
     CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p32, ctx->p16,
-                            ctx->Ap, ctx->s, st, paired ? ctx->xp : nullptr, ctx->am));
+                            ctx->Ap, ctx->s, st, paired ? ctx->xp : nullptr));
     t_end(ctx, PERF_T_VECTOR, st);
     return PERF_OK;
 }
@@ -620,7 +611,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
             CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
                                       ctx->p32, ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
                                       o.pcg_eps_rel, o.pcg_stall, B, nB, st,
-                                      paired ? ctx->xp : nullptr, ctx->am));
+                                      paired ? ctx->xp : nullptr));
             for (int k = 0; k < o.pcg_iters; ++k) {
                 ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired, use_coef);
                 if (ps != PERF_OK) return ps;
@@ -740,8 +731,7 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     const void* pp = pbuf;
     if (!bf) CK(perf::launch_pair_pack(ctx->n, static_cast<const float*>(x), ctx->p32, ctx->xp, st));
     auto apply = [&](bool paired) -> cudaError_t {
-        return paired ? perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, nullptr, st,
-                                                PERF_AP_BRICK != 0)
+        return paired ? perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, nullptr, st)
                       : apply_arrays(ctx, x, pp, nullptr, st);
     };
     const int tws[4] = {8, 4, 16, 32};
@@ -750,38 +740,50 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     // With the coefficient store, Gauss-Newton steps run the coefficient-
-    // cached A p: keep 8x4 tiles (the store is laid out per tile) and time
-    // it over the CTA caps, on coefficients stored at x.
+    // cached A p: for every tile shape the store is laid out anew and filled
+    // at x, and the A p from it is timed over the CTA caps; the default
+    // (8x4, no cap, timed first) is kept unless beaten by 3%.
     set_tiling(ctx, 8);
     bool use_coef = false;
     perf_status pc = ensure_coef(ctx, st, &use_coef);
     if (pc != PERF_OK) return pc;
     if (use_coef) {
-        CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr,
-                                ctx->diag, nullptr, nullptr, st, nullptr, ctx->coef, ctx->tile_off));
-        float best = 1e30f;
-        int best_cap = 0;
-        for (int j = 0; j < 3; ++j) {
-            ctx->ds.cap_per_sm = caps[j];
-            for (int rep = 0; rep < 3; ++rep) {
-                if (rep == 1) CK(cudaEventRecord(e0, st));
-                CK(perf::launch_apply_coef(ctx->ds, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef,
-                                           ctx->tile_off, ctx->Ap, nullptr, PERF_AP_BRICK != 0, st));
+        float best = 1e30f, incumbent = 1e30f;
+        int best_tw = 8, best_cap = 0;
+        for (int i = 0; i < 4; ++i) {
+            set_tiling(ctx, tws[i]);
+            bool fits = false;
+            pc = ensure_coef(ctx, st, &fits);
+            if (pc != PERF_OK) return pc;
+            if (!fits) continue;
+            CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr,
+                                    ctx->diag, nullptr, nullptr, st, nullptr, ctx->coef,
+                                    ctx->tile_off));
+            for (int j = 0; j < 3; ++j) {
+                ctx->ds.cap_per_sm = caps[j];
+                for (int rep = 0; rep < 3; ++rep) {
+                    if (rep == 1) CK(cudaEventRecord(e0, st));
+                    CK(perf::launch_apply_coef(ctx->ds, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef,
+                                               ctx->tile_off, ctx->Ap, nullptr, st));
+                }
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                ms *= 0.5f;
+                if (i == 0 && j == 0) incumbent = ms;
+                if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; }
             }
-            CK(cudaEventRecord(e1, st));
-            CK(cudaEventSynchronize(e1));
-            float ms = 0.f;
-            CK(cudaEventElapsedTime(&ms, e0, e1));
-            ms *= 0.5f;
-            if (ms < (j == 0 ? 1e30f : 0.97f * best)) { best = ms; best_cap = caps[j]; }
         }
+        if (!(best < 0.97f * incumbent)) { best = incumbent; best_tw = 8; best_cap = 0; }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
+        set_tiling(ctx, best_tw);
         ctx->ds.cap_per_sm = best_cap;
         ctx->coef_used = true;
         if (out) {
-            out->tile_w = 8;
-            out->tile_h = 4;
+            out->tile_w = best_tw;
+            out->tile_h = 32 / best_tw;
             out->ctas_per_sm = best_cap;
             out->apply_ms = best;
             out->paired = 0;

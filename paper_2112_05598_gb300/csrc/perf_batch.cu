@@ -56,6 +56,15 @@ struct perf_batch {
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t graph = nullptr;
     int graph_iters = -1;
+    const float* graph_coef = nullptr;   // store the captured loop reads (null: recompute)
+    // coefficient-cached A p (as for a single scene), rows over the global tile list
+    long long coef_budget = -1;
+    long long* tile_off = nullptr;
+    float* coef = nullptr;
+    size_t coef_bytes = 0;
+    long long coef_rows = 0;
+    int tab_tile_w = 0;
+    bool use_coef = false;               // the PCG loop reads the store
     std::string err;
 };
 
@@ -116,9 +125,69 @@ cudaError_t apply_launch(perf_batch* b, const float* x, const float* p32, cudaSt
                                       skip_done ? b->s : nullptr);
 }
 
+// Lays the coefficient store out for the current tiling; *use = it fits the
+// budget (automatic: free device memory minus 6 GiB).
+perf_status ensure_coef(perf_batch* b, cudaStream_t st, bool* use) {
+    *use = false;
+    if (b->coef_budget == 0 || b->n_rays == 0 || b->total_tiles == 0) return PERF_OK;
+    if (!b->tile_off || b->tab_tile_w != b->tile_w) {
+        if (b->tile_off) { cudaFree(b->tile_off); b->tile_off = nullptr; }
+        int* rows = nullptr;
+        BK(cudaMalloc(&rows, sizeof(int) * (size_t)b->total_tiles));
+        cudaError_t e = perf::launch_tile_rows_batch(b->d_items, b->d_start, b->n, b->total_tiles,
+                                                     rows, st);
+        std::vector<int> h((size_t)b->total_tiles);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h.data(), rows, sizeof(int) * h.size(), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(rows);
+        BK(e);
+        std::vector<long long> off(h.size() + 1, 0);
+        for (size_t t = 0; t < h.size(); ++t) off[t + 1] = off[t] + h[t];
+        BK(cudaMalloc(&b->tile_off, sizeof(long long) * off.size()));
+        BK(cudaMemcpy(b->tile_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice));
+        b->coef_rows = off.back();
+        b->tab_tile_w = b->tile_w;
+    }
+    const size_t need = (size_t)b->coef_rows * 32 * 16;
+    size_t budget;
+    if (b->coef_budget > 0) {
+        budget = (size_t)b->coef_budget;
+    } else {
+        size_t fr = 0, tot = 0;
+        BK(cudaMemGetInfo(&fr, &tot));
+        const size_t avail = fr + b->coef_bytes, reserve = (size_t)6 << 30;
+        budget = avail > reserve ? avail - reserve : 0;
+    }
+    if (need > budget) {
+        if (b->coef) { cudaFree(b->coef); b->coef = nullptr; b->coef_bytes = 0; }
+        return PERF_OK;
+    }
+    if (b->coef_bytes < need) {
+        if (b->coef) { cudaFree(b->coef); b->coef = nullptr; b->coef_bytes = 0; }
+        if (cudaMalloc(&b->coef, need > 0 ? need : 16) != cudaSuccess) {
+            cudaGetLastError();
+            b->coef = nullptr;
+            return PERF_OK;
+        }
+        b->coef_bytes = need;
+    }
+    *use = true;
+    return PERF_OK;
+}
+
+cudaError_t apply_coef_launch(perf_batch* b, const float* p32, double* pap, cudaStream_t st,
+                              bool skip_done) {
+    return perf::launch_apply_coef_batch(b->d_items, b->d_start, b->n, b->total_tiles, b->counter,
+                                         p32, b->coef, b->tile_off, b->Ap, pap,
+                                         (int)(sizeof(PcgScalars) / sizeof(double)), b->cap, st,
+                                         skip_done ? b->s : nullptr);
+}
+
 // One Algorithm 2 iteration for every scene.
 cudaError_t pcg_iter(perf_batch* b, cudaStream_t st) {
-    cudaError_t e = apply_launch(b, b->x_work, b->p32, st, true);
+    cudaError_t e = b->use_coef ? apply_coef_launch(b, b->p32, &b->s[0].pAp, st, true)
+                                : apply_launch(b, b->x_work, b->p32, st, true);
     if (e == cudaSuccess)
         e = perf::launch_pcg_update_seg(b->n_params, b->n, b->d_seg, b->max_seg, b->delta, b->rho,
                                         b->p, b->Ap, b->diag, nullptr, 0, b->s, st);
@@ -130,7 +199,8 @@ cudaError_t pcg_iter(perf_batch* b, cudaStream_t st) {
 }
 
 perf_status ensure_graph(perf_batch* b, int iters) {
-    if (b->graph && b->graph_iters == iters) return PERF_OK;
+    const float* gc = b->use_coef ? b->coef : nullptr;
+    if (b->graph && b->graph_iters == iters && b->graph_coef == gc) return PERF_OK;
     if (b->graph) {
         cudaGraphExecDestroy(b->graph);
         b->graph = nullptr;
@@ -153,6 +223,7 @@ perf_status ensure_graph(perf_batch* b, int iters) {
         return PERF_ERR_CUDA;
     }
     b->graph_iters = iters;
+    b->graph_coef = gc;
     return PERF_OK;
 }
 
@@ -272,7 +343,7 @@ perf_status perf_batch_destroy(perf_batch* b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     void* bufs[] = {b->d_items, b->d_start, b->d_seg, b->cams, b->counter, b->x_work, b->x_trial,
                     b->r, b->diag, b->grad, b->delta, b->rho, b->p, b->p32, b->Ap, b->s, b->F,
-                    b->gamma, b->mask};
+                    b->gamma, b->mask, b->tile_off, b->coef};
     for (void* q : bufs)
         if (q) cudaFree(q);
     delete b;
@@ -318,13 +389,34 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
     const int caps[3] = {0, 3, 2};
     float best = 1e30f;
     int best_tw = 8, best_cap = 0;
+    // with the coefficient store (it fits at the default tiling) the
+    // coefficient-cached A p is timed, its store laid out and filled at x
+    // for every tile shape
+    if (apply_tiling(b, 8) != PERF_OK) return PERF_ERR_CUDA;
+    bool coef = false;
+    perf_status pc = ensure_coef(b, st, &coef);
+    if (pc != PERF_OK) return pc;
     for (int i = 0; i < 4; ++i) {
         if (apply_tiling(b, tws[i]) != PERF_OK) return PERF_ERR_CUDA;
+        if (coef) {
+            bool fits = false;
+            pc = ensure_coef(b, st, &fits);
+            if (pc != PERF_OK) return pc;
+            if (!fits) continue;
+            BK(cudaMemsetAsync(b->diag, 0, sizeof(float) * (size_t)b->n_params, st));
+            BK(perf::launch_scatter_batch(b->d_items, b->d_start, b->n, b->total_tiles, b->counter,
+                                          x, nullptr, nullptr, b->diag, nullptr, nullptr, 0, 2,
+                                          b->cap, st, nullptr, b->coef, b->tile_off));
+        }
         for (int j = 0; j < 3; ++j) {
             b->cap = caps[j];
-            BK(apply_launch(b, x, b->p32, st));                       // warm-up
+            auto launch = [&]() {
+                return coef ? apply_coef_launch(b, b->p32, &b->s[0].pAp, st, false)
+                            : apply_launch(b, x, b->p32, st);
+            };
+            BK(launch());                                             // warm-up
             BK(cudaEventRecord(e0, st));
-            BK(apply_launch(b, x, b->p32, st));
+            BK(launch());
             BK(cudaEventRecord(e1, st));
             BK(cudaEventSynchronize(e1));
             float ms = 0.f;
@@ -342,8 +434,27 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
         out->ctas_per_sm = best_cap;
         out->apply_ms = best;
         out->paired = 0;
-        out->coef = 0;
+        out->coef = coef ? 1 : 0;
     }
+    return PERF_OK;
+}
+
+perf_status perf_batch_set_coef_budget(perf_batch* b, int64_t bytes) {
+    if (!b || bytes < -1) return PERF_ERR_INVALID_ARG;
+    b->coef_budget = bytes;
+    if (bytes >= 0 && b->coef && b->coef_bytes > (size_t)bytes) {
+        cudaFree(b->coef);
+        b->coef = nullptr;
+        b->coef_bytes = 0;
+        b->use_coef = false;
+    }
+    return PERF_OK;
+}
+
+perf_status perf_batch_coef_info(perf_batch* b, int64_t* bytes_held, int32_t* last_used) {
+    if (!b) return PERF_ERR_INVALID_ARG;
+    if (bytes_held) *bytes_held = (int64_t)b->coef_bytes;
+    if (last_used) *last_used = b->use_coef ? 1 : 0;
     return PERF_OK;
 }
 
@@ -353,7 +464,11 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
     cudaStream_t st = S(stream);
     const perf_options& o = b->opts;
     const int n = b->n;
-    perf_status ps = ensure_graph(b, o.pcg_iters);
+    bool use = false;
+    perf_status ps = ensure_coef(b, st, &use);
+    if (ps != PERF_OK) return ps;
+    b->use_coef = use;
+    ps = ensure_graph(b, o.pcg_iters);
     if (ps != PERF_OK) return ps;
     cudaEvent_t e0, e1;
     BK(cudaEventCreate(&e0));
@@ -371,7 +486,8 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
         BK(cudaMemsetAsync(b->grad, 0, sizeof(float) * (size_t)b->n_params, st));
         BK(perf::launch_scatter_batch(b->d_items, b->d_start, n, b->total_tiles, b->counter,
                                       b->x_work, nullptr, b->r, b->diag, b->grad, nullptr, 0, 2,
-                                      b->cap, st));
+                                      b->cap, st, nullptr, b->use_coef ? b->coef : nullptr,
+                                      b->use_coef ? b->tile_off : nullptr));
         BK(perf::launch_pcg_begin_seg(b->n_params, n, b->d_seg, b->max_seg, b->grad, b->diag,
                                       b->delta, b->rho, b->p, b->p32, nullptr, b->Ap, b->s,
                                       o.pcg_iters, o.pcg_fixed, o.pcg_eps_rel, o.pcg_stall,

@@ -153,45 +153,6 @@ __device__ __forceinline__ void ray_setup(const DevScene& sc, long long ray, Ray
     R.shell_hit = hit;
 }
 
-// Brick order of the A p accumulation buffer.  The grid is cut into 4x4x4
-// bricks (each axis rounded up to a multiple of 4); inside a brick the 8
-// voxels of one coordinate-parity class are consecutive, i.e. one 128-byte
-// line of float4 blocks, and the texel blocks follow the padded grid.  The
-// scatter window is parity-indexed, so the lanes of a warp flush voxels of
-// one parity class per instruction; in this order nearby voxels of a class
-// share a line, where the canonical order spreads them over several.
-// Bits of a voxel's index: 0-2 the coordinates' second bits, 3-5 their
-// parities, 6.. the brick.
-__host__ __device__ __forceinline__ int brick_part(int c, int axis, int mul) {
-    return (c >> 2) * mul + ((c & 1) << (3 + axis)) + (((c >> 1) & 1) << axis);
-}
-
-struct ApMap {
-    int G;                 // 0: canonical order
-    int Gq;                // bricks per axis
-    long long n_vox;       // grid voxels
-    long long n_vox_pad;   // 64 Gq^3
-};
-
-__host__ inline ApMap ap_map(int G, bool brick) {
-    ApMap m{0, 0, (long long)G * G * G, (long long)G * G * G};
-    if (brick) {
-        m.G = G;
-        m.Gq = (G + 3) >> 2;
-        m.n_vox_pad = 64ll * m.Gq * m.Gq * m.Gq;
-    }
-    return m;
-}
-
-// Index in the A p buffer of canonical parameter block v.
-__device__ __forceinline__ long long ap_index(const ApMap& m, long long v) {
-    if (m.G == 0) return v;
-    if (v >= m.n_vox) return v - m.n_vox + m.n_vox_pad;
-    const int vi = (int)v, G = m.G;
-    const int x = vi % G, t = vi / G, y = t % G, z = t / G;
-    return brick_part(x, 0, 64) + brick_part(y, 1, 64 * m.Gq) + brick_part(z, 2, 64 * m.Gq * m.Gq);
-}
-
 // Trilinear cell of a sample: base voxel (linear index) and fractions.
 struct Cell {
     int bx, by, bz;

@@ -27,11 +27,23 @@ cudaError_t launch_forward_batch(const BatchItem* items, const long long* start,
 struct PcgScalars;
 // pcg (may be null): per-scene Algorithm 2 state; scenes whose solve has
 // exited (done) are skipped.
+// coef / tile_off (mode 2, may be null): also store the per-sample
+// coefficients, tile_off indexed by the global tile list.
 cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start, int n,
                                  long long total, unsigned long long* counter, const float* x,
                                  const float* p, const float* v, float* out, float* out2,
                                  double* pap, int pap_stride, int mode, int cap_per_sm,
-                                 cudaStream_t st, const PcgScalars* pcg = nullptr);
+                                 cudaStream_t st, const PcgScalars* pcg = nullptr,
+                                 float* coef = nullptr, const long long* tile_off = nullptr);
+// Coefficient-cached A p over a batch, and the rows of every tile of the
+// global tile list (see launch_tile_rows).
+cudaError_t launch_apply_coef_batch(const BatchItem* items, const long long* start, int n,
+                                    long long total, unsigned long long* counter, const float* p,
+                                    const float* coef, const long long* tile_off, float* out,
+                                    double* pap, int pap_stride, int cap_per_sm, cudaStream_t st,
+                                    const PcgScalars* pcg);
+cudaError_t launch_tile_rows_batch(const BatchItem* items, const long long* start, int n,
+                                   long long total, int* rows, cudaStream_t st);
 
 // Device scalars of Algorithm 2 and the line search (FP64).
 struct PcgScalars {
@@ -79,39 +91,31 @@ cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* 
                            const long long* tile_off = nullptr);
 // Coefficient-cached A p (k_march.cu): rows[t] = rows of pixel tile t in the
 // coefficient store (its largest grid sample count + shells); A p (+p^T A p)
-// from p (p_dtype: 0 float, 1 bf16) and the stored coefficients, into out in
-// brick order (brick) or canonical order.
+// from p (p_dtype: 0 float, 1 bf16) and the stored coefficients.
 cudaError_t launch_tile_rows(const DevScene& sc, int* rows, cudaStream_t st);
 cudaError_t launch_apply_coef(const DevScene& sc, const void* p, int p_dtype, const float* coef,
-                              const long long* tile_off, float* out, double* pap, bool brick,
-                              cudaStream_t st);
+                              const long long* tile_off, float* out, double* pap, cudaStream_t st);
 // A p (+p^T A p) of an FP32 scene from paired records xp[v] = (x[v], p[v])
-// (2 n floats, 32-byte aligned); brick: out in brick order (see ApMap).
+// (2 n floats, 32-byte aligned).
 cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
-                              cudaStream_t st, bool brick);
-// A p (+p^T A p) from separate x and p arrays into a brick-order buffer.
-cudaError_t launch_apply_brick(const DevScene& sc, int dtype, const void* x, const void* p,
-                               int p_dtype, float* out, double* pap, cudaStream_t st);
+                              cudaStream_t st);
 
 // Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP64; p32 / p16: the
-// FP32 / BF16 copies of p that the ray march gathers; Ap: FP32 scatter target
-// in the order am (canonical by default); pxp (may be null): paired x / p
-// records whose p half also receives p.
+// FP32 / BF16 copies of p that the ray march gathers; Ap: FP32 scatter target;
+// pxp (may be null): paired x / p records whose p half also receives p.
 cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
                              double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                              PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st,
-                             float* pxp = nullptr, ApMap am = ApMap{0, 0, 0, 0});
+                             float* pxp = nullptr);
 cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
                               const float* Ap, const float* diag, const float* blocks,
-                              long long n_block, PcgScalars* s, cudaStream_t st,
-                              ApMap am = ApMap{0, 0, 0, 0});
+                              long long n_block, PcgScalars* s, cudaStream_t st);
 // One thread: the exit test of Algorithm 2 and beta (after launch_pcg_update).
 cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st);
 cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
                            long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                           PcgScalars* s, cudaStream_t st, float* pxp = nullptr,
-                           ApMap am = ApMap{0, 0, 0, 0});
+                           PcgScalars* s, cudaStream_t st, float* pxp = nullptr);
 // xp[v] = (x[v], p[v]) for the n / 4 parameter blocks (p null: x half only).
 cudaError_t launch_pair_pack(long long n, const float* x, const float* p, float* xp,
                              cudaStream_t st);
@@ -129,18 +133,16 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, l
                                  double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                                  PcgScalars* s, int max_iter, int fixed, double eps_rel,
                                  double stall, const float* blocks, long long n_block,
-                                 cudaStream_t st, float* pxp = nullptr,
-                                 ApMap am = ApMap{0, 0, 0, 0});
+                                 cudaStream_t st, float* pxp = nullptr);
 cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                                   double* delta, double* rho, const double* p, const float* Ap,
                                   const float* diag, const float* blocks, long long n_block,
-                                  PcgScalars* s, cudaStream_t st, ApMap am = ApMap{0, 0, 0, 0});
+                                  PcgScalars* s, cudaStream_t st);
 cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st);
 cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                                const double* rho, const float* diag, const float* blocks,
                                long long n_block, double* p, float* p32, __nv_bfloat16* p16,
-                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp = nullptr,
-                               ApMap am = ApMap{0, 0, 0, 0});
+                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp = nullptr);
 // Segment y: x_out = P(x + gamma[y] Delta) where mask[y] (or every segment).
 cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,
                              const float* x, const double* delta, const double* gamma,
