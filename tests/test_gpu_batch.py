@@ -112,17 +112,15 @@ def test_batch_early_exit_matches_single_scenes():
 def test_batch_coef_store_equals_recompute(tune):
     """The batch's coefficient store (rows over the global tile list, filled by
     the diagonal march, read by the graph-captured PCG loop) gives the same
-    steps as recomputing every march: F and the rendered images to the
-    Gauss-Newton tolerance.  (These random-target scenes drive some opacities
-    to the hundreds, where parameters are hypersensitive: the FP32 rounding
-    of A p, amplified by CG, moves x there by ~1e-3 without changing what is
-    rendered -- the reading used for the 20-iteration single-scene test.)"""
-    import torch
+    steps as recomputing every march.  One PCG iteration per step, so that
+    the two A p forms' FP32 rounding is not amplified by CG (these
+    random-target scenes drive opacities to the hundreds, where several CG
+    iterations magnify 1e-7 differences in A p to 1e-4 in x)."""
     from paper_2112_05598_gb300 import Batch
     scenes = _scenes(seed=13)
     out = {}
     for budget in (-1, 0):
-        b = Batch(scenes, max_samples=64, pcg_iters=3, pcg_fixed=1)
+        b = Batch(scenes, max_samples=64, pcg_iters=1, pcg_fixed=1)
         b.set_coef_budget(budget)
         x = cuda_tensor(_cat(b, scenes, "x"))
         t = cuda_tensor(_cat(b, scenes, "target"))
@@ -130,14 +128,12 @@ def test_batch_coef_store_equals_recompute(tune):
             info = b.autotune(x)
             assert info["coef"] == (1 if budget else 0)
         stats = b.gn_solve(x, t, 2)
-        img = torch.zeros(3 * b.n_rays, device="cuda")
-        b.render(x, img)
-        out[budget] = (stats, host(img), b.coef_info())
-    (sc, ic_img, ic), (sr, ir_img, ir) = out[-1], out[0]
+        out[budget] = (stats, host(x), b.coef_info())
+    (sc, xc, ic), (sr, xr, ir) = out[-1], out[0]
     assert ic["used"] and ic["bytes"] > 0 and not ir["used"]
     for k in range(2):
         for a, r in zip(sc[k], sr[k]):
             assert a["accepted"] == r["accepted"]
             assert abs(a["F_before"] - r["F_before"]) <= TOL_FP32 * r["F_before"]
-            assert abs(a["F_after"] - r["F_after"]) <= TOL_GN * r["F_after"]
-    assert rel_l2(ic_img, ir_img) < TOL_GN
+            assert abs(a["F_after"] - r["F_after"]) <= TOL_FP32 * r["F_after"]
+    assert rel_l2(xc, xr) < TOL_FP32
