@@ -456,7 +456,7 @@ def run_batch(args, rank, world, local):
     iters = sum_over_ranks(float(sum(s["pcg_iters"] for st in stats for s in st)), world)
     value = iters / (ms / 1000.0)
     # end to end with host buffers
-    x_host = torch.from_numpy(np.concatenate([s["x0"] for s in scenes])).pin_memory()
+    x_host = x.detach().cpu().pin_memory()      # continue from the timed steps' state
     t_host = target.cpu().pin_memory()
     x_dev = torch.empty_like(x)
     t_dev = torch.empty_like(target)
@@ -552,7 +552,9 @@ def run_ours(args, rank, world, local):
 
     # end to end through the public API with host buffers
     e2e_steps = args.e2e_steps or args.steps
-    x_host = torch.from_numpy(sc.x0.copy()).pin_memory()
+    # the e2e steps continue the trajectory from the timed steps' state, so
+    # that both numbers measure the same kind of Gauss-Newton step
+    x_host = x.detach().to(dtype=torch.float32).cpu().pin_memory()
     t_host = target.cpu().pin_memory()
     x_dev = torch.empty_like(x)
     t_dev = torch.empty_like(target)
