@@ -106,6 +106,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cams", type=int, default=16)
     ap.add_argument("--lpc", action="store_true", help="learned vs Jacobi preconditioner study")
+    ap.add_argument("--hier", action="store_true", help="hierarchical vs single-level study")
+    ap.add_argument("--hier-steps", type=int, default=30)
+    ap.add_argument("--hier-pcg", type=int, default=3)
     ap.add_argument("--lpc-scenes", type=int, default=100)
     ap.add_argument("--lpc-steps", type=int, default=20)
     ap.add_argument("--lpc-epochs", type=int, default=2)
@@ -415,6 +418,128 @@ def run_lpc(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_hier(args, rank, world, local):
+    """Hierarchical formulation vs a single level: the coarse-to-fine driver
+    (3 levels, 32^3 -> 64^3 -> 128^3 with maps doubling to the workload's
+    size, --hier-steps Gauss-Newton steps per level, random colours with low
+    opacity at the first level) against Gauss-Newton at the final resolution
+    from the workload's constant start, both with --hier-pcg fixed PCG
+    iterations per step; held-out-view PSNR against wall-clock time."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2112_05598_gb300 import Context
+    from paper_2112_05598_gb300.hierarchy import coarse_to_fine
+    from scenegen import make_scene, random_params
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    sc = make_scene(args.workload, n_cams=args.cams)
+    levels = 3
+    G0, He0, We0 = sc.G >> (levels - 1), sc.env_h >> (levels - 1), sc.env_w >> (levels - 1)
+    S = len(sc.radii)
+    ctx = Context.from_scene(sc)
+    x_gt = torch.from_numpy(sc.x_gt).to(dev)
+    target = torch.empty(3 * ctx.n_rays, device=dev)
+    ctx.render(x_gt, target)
+    ctx.close()
+    F = torch.zeros(1, dtype=torch.float64, device=dev)
+    holds = {}
+
+    def held_psnr(shape, x):
+        G, He, We = shape
+        if shape not in holds:
+            h = Context(G, sc.radii, He, We, sc.heldout_c2w, sc.heldout_focal, sc.width,
+                        sc.height, max_samples=int(np.ceil(np.sqrt(3.0) * G)) + 1)
+            hold_gt = Context.from_scene(sc, c2w=sc.heldout_c2w, focal=sc.heldout_focal)
+            ht = torch.empty(3 * h.n_rays, device=dev)
+            hold_gt.render(x_gt, ht)
+            hold_gt.close()
+            holds[shape] = (h, ht)
+        h, ht = holds[shape]
+        h.residual(x, ht, None, F)
+        return _psnr_from_F(float(F.item()), h.n_rays)
+
+    def thresholded_psnr(x, cut=0.7):
+        """Held-out PSNR of the final state rendered with the converged-scene
+        opacity threshold of Section "Rendering"."""
+        h, ht = holds[(sc.G, sc.env_h, sc.env_w)]
+        rgb = torch.empty(3 * h.n_rays, device=dev)
+        h.render_threshold(x, cut, rgb)
+        mse = float(torch.mean((rgb - ht) ** 2).item())
+        return 10.0 * np.log10(1.0 / mse) if mse > 0 else float("inf")
+
+    opts = dict(pcg_iters=args.hier_pcg, pcg_fixed=1)
+    # paper mode: at most --hier-pcg iterations with the relative-residual
+    # (1e-3) and stall (0.85) exits, pixel and sample jitter on
+    paper_opts = dict(pcg_iters=args.hier_pcg, pcg_fixed=0, pcg_eps_rel=1e-3, pcg_stall=0.85,
+                      jitter=1, seed=99)
+    runs = {}
+    pause = [0.0]
+    for name, o in (("hierarchical", opts), ("hierarchical_paper_mode", paper_opts)):
+        rng = np.random.default_rng(77)
+        x0 = torch.from_numpy(random_params(rng, G0, S, He0, We0, 0.0, 0.1,
+                                            shell_sigma_hi=0.1)).to(dev)
+        curve, steps = [], []
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pause[0] = 0.0
+
+        def on_step(l, k, shape, x, st):
+            torch.cuda.synchronize()
+            tp = time.perf_counter()
+            curve.append((tp - t0 - pause[0], held_psnr(shape, x), l))
+            steps.append({"level": l, "G": shape[0], "ms": st["ms"], "F_after": st["F_after"],
+                          "gamma": st["gamma"], "pcg_iters": st["pcg_iters"]})
+            pause[0] += time.perf_counter() - tp      # held-out evaluation is not solve time
+        xf = coarse_to_fine(x0, G0, sc.radii, He0, We0, sc.c2w, sc.focal, sc.width, sc.height,
+                            target, levels, args.hier_steps, on_step=on_step, **o)
+        runs[name] = {"psnr_curve": curve, "steps": steps,
+                      "levels": [[G0 << l, He0 << l, We0 << l] for l in range(levels)],
+                      "final_psnr_threshold_0.7_db": thresholded_psnr(xf)}
+        del xf
+    curve = runs["hierarchical"]["psnr_curve"]
+    # single level at the final resolution, for the same wall time or more
+    budget = curve[-1][0]
+    ctx = Context.from_scene(sc, **opts)
+    x = torch.from_numpy(sc.x0.copy()).to(dev)
+    curve2, steps2 = [], []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    pause[0] = 0.0
+    while True:
+        st = ctx.gn_solve(x, target, 1)[0]
+        torch.cuda.synchronize()
+        tp = time.perf_counter()
+        curve2.append((tp - t0 - pause[0], held_psnr((sc.G, sc.env_h, sc.env_w), x), levels - 1))
+        steps2.append({"level": levels - 1, "G": sc.G, "ms": st["ms"], "F_after": st["F_after"],
+                       "gamma": st["gamma"]})
+        pause[0] += time.perf_counter() - tp
+        if curve2[-1][0] >= budget or len(steps2) >= 4 * levels * args.hier_steps:
+            break
+    ctx.close()
+    runs["single_level"] = {"psnr_curve": curve2, "steps": steps2,
+                            "final_psnr_threshold_0.7_db": thresholded_psnr(x)}
+    best_single = max(p for _, p, _ in curve2)
+    final_h = curve[-1][1]
+
+    def time_to(cv, target_db):
+        return next((t for t, p, _ in cv if p >= target_db), None)
+    target_db = min(final_h, best_single) - 0.1
+    line = {"metric": "held-out PSNR vs wall time, hierarchical vs single level",
+            "workload": f"{args.workload}: {sc.G}^3 grid + {S} shells {sc.env_h}x{sc.env_w}, "
+                        f"{sc.n_cams} cameras {sc.width}x{sc.height}; levels "
+                        f"{[G0 << l for l in range(levels)]}",
+            "pcg_iters_per_step": args.hier_pcg, "gn_steps_per_level": args.hier_steps,
+            "final_psnr_db": {k: v["psnr_curve"][-1][1] for k, v in runs.items()},
+            "target_psnr_db": target_db,
+            "time_to_psnr_s": {k: time_to(v["psnr_curve"], target_db) for k, v in runs.items()},
+            "runs": runs}
+    for h, _ in holds.values():
+        h.close()
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, rank, world, local):
     """The many-scenes form: 64 uneven scenes (grids 32^3-96^3, 8-40 cameras at
     128x128, 1-3 shells), every ray march one persistent launch, the PCG loop
@@ -643,6 +768,8 @@ def main():
         run_reference(args, rank, world)
     elif args.lpc:
         run_lpc(args, rank, world, local)
+    elif args.hier:
+        run_hier(args, rank, world, local)
     elif args.workload == "batch64":
         run_batch(args, rank, world, local)
     else:

@@ -361,6 +361,29 @@ perf_status perf_batch_coef_info(perf_batch* b, int64_t* bytes_held, int32_t* la
 perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, int32_t n_steps,
                                 perf_gn_stats* stats, void* stream);
 
+/* perf_render with the rendering threshold of Section "Rendering" for a
+ * converged scene: a ray whose total opacity within the volume, 1 - T at
+ * grid exit, is below min_opacity (the paper uses 0.7) sees the volume as
+ * fully transparent and renders the shells only.  T_out (may be NULL)
+ * receives T at grid exit before the threshold.  min_opacity in [0, 1]
+ * (0: plain perf_render). */
+perf_status perf_render_threshold(perf_ctx* ctx, const void* x, float min_opacity,
+                                  float* rgb_out, float* T_out, void* stream);
+
+/* Level change of the hierarchical formulation (Section "Hierarchical
+ * formulation"): fills the parameters of the next level -- grid 2G x 2G x 2G,
+ * environment maps 2 env_h x 2 env_w -- from level (G, env_h x env_w) by
+ * linear interpolation at the new cell centres (fine cell i' at coarse index
+ * coordinate i'/2 - 1/4): trilinear on the grid with the ray march's edge
+ * clamp, bilinear on the maps with the longitude wrapped and the latitude
+ * clamped.  Grid opacity is per voxel side and is halved (the optical depth
+ * of every path is kept); shell opacity is kept.  x: 4 (G^3 + S env_h env_w)
+ * floats, x_out: 4 (8 G^3 + 4 S env_h env_w) floats, both DEVICE, not
+ * overlapping (else PERF_ERR_INVALID_ARG).  2 <= G <= 512.  No context; the
+ * work is queued on stream (cudaStream_t). */
+perf_status perf_upsample(const float* x, int32_t G, int32_t n_shells, int32_t env_h,
+                          int32_t env_w, float* x_out, void* stream);
+
 /* Residual and objective without a context and without any device
  * allocation -- the paper has no counterpart; this serves callers that cannot
  * allocate device memory when they need a residual (a device-memory budget

@@ -121,6 +121,21 @@ class Oracle:
                          ctypes.c_int64(N), _dptr(rgb), _dptr(te), _dptr(tf))
         return rgb, te, tf
 
+    def render_threshold(self, x, min_opacity):
+        """Section "Rendering": for a converged scene, a ray whose total
+        opacity within the volume (1 - T at grid exit) is below min_opacity
+        sees the volume as fully transparent.  Written as its definition:
+        such rays take the render of the same scene with every grid opacity
+        set to zero (the shells alone); the others the plain render."""
+        x = self._x(x)
+        rgb, te, _ = self.render(x)
+        clear = x.copy()
+        clear[:4 * self.G ** 3].reshape(-1, 4)[:, 3] = 0.0
+        rgb0 = self.render(clear)[0]
+        cut = (1.0 - te) < min_opacity
+        rgb[cut] = rgb0[cut]
+        return rgb, te
+
     def residual(self, x, target, ids=None):
         """r = H^ - C per ray and channel, F = 1/2 sum r^2 (Eq. 5-6)."""
         x = self._x(x)

@@ -99,6 +99,8 @@ _SIGS = {
     "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
     "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_set_coef_budget": [_VP, ctypes.c_int64],
+    "perf_upsample": [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP],
+    "perf_render_threshold": [_VP, _VP, ctypes.c_float, _VP, _VP, _VP],
     "perf_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
     "perf_set_lpc": [_VP, _VP],
     "perf_diag_cross": [_VP, _VP, _VP, _VP, _VP],
@@ -170,6 +172,16 @@ def load_library(path: Optional[str] = None):
     if path is None:
         _lib = lib
     return lib
+
+
+def upsample(x, G, n_shells, env_h, env_w, x_out, stream=None):
+    """perf_upsample: the next hierarchical level's parameters (grid 2G, maps
+    2 env_h x 2 env_w) from level (G, env_h x env_w), into x_out."""
+    lib = load_library()
+    st = lib.perf_upsample(_ptr(x), int(G), int(n_shells), int(env_h), int(env_w), _ptr(x_out),
+                           _stream(stream))
+    if st != 0:
+        raise PerfError(st, "upsample")
 
 
 def residual_noalloc(G, radii, env_h, env_w, c2w, focal, width, height, x, target, r_out,
@@ -294,6 +306,13 @@ class Context:
         self._check(self.lib.perf_set_options(self.h, ctypes.byref(self.options)), "set_options")
 
     # --- per-call entry points (device tensors)
+    def render_threshold(self, x, min_opacity, rgb_out, T_out=None, stream=None):
+        """Rendering with the converged-scene opacity threshold (rays whose
+        volume opacity 1 - T is below min_opacity see only the shells)."""
+        self._check(self.lib.perf_render_threshold(self.h, _ptr(x), float(min_opacity),
+                                                   _ptr(rgb_out), _ptr(T_out), _stream(stream)),
+                    "render_threshold")
+
     def render(self, x, rgb_out, T_out=None, stream=None):
         self._check(self.lib.perf_render(self.h, _ptr(x), _ptr(rgb_out), _ptr(T_out),
                                          _stream(stream)), "render")

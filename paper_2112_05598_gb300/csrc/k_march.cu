@@ -121,10 +121,14 @@ __device__ __forceinline__ void comp_step(Comp& s, const float4 a, float dbar) {
     s.T = __fmul_rn(s.T, e);
 }
 
-// Eq. 3-4 over the grid samples and then the shells.
+// Eq. 3-4 over the grid samples and then the shells.  cut > 0: the
+// rendering threshold of Section "Rendering" -- a ray whose total opacity
+// within the volume, 1 - T_exit, is below cut sees the volume as fully
+// transparent (only the shells).
 template <typename T>
 __device__ __forceinline__ void composite(const DevScene& sc, const T* __restrict__ x,
-                                          const Ray& R, long long ray, Comp& s, float& T_exit) {
+                                          const Ray& R, long long ray, Comp& s, float& T_exit,
+                                          float cut = 0.0f) {
     s.T = 1.0f;
     s.H[0] = s.H[1] = s.H[2] = 0.0f;
     const float dbar = R.delta * sc.halfG;
@@ -135,6 +139,10 @@ __device__ __forceinline__ void composite(const DevScene& sc, const T* __restric
         comp_step(s, cx.at(x, sc, cl), dbar);
     }
     T_exit = s.T;
+    if (cut > 0.0f && 1.0f - s.T < cut) {
+        s.T = 1.0f;
+        s.H[0] = s.H[1] = s.H[2] = 0.0f;
+    }
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
         if (shell_lookup(sc, R, q, hs)) comp_step(s, interp_shell(x, hs), 1.0f);
@@ -446,14 +454,15 @@ template <typename T, int MODE>   // 0 render, 1 residual (+F), 2 F only
 __device__ __forceinline__ void forward_tile(const DevScene& sc, const T* __restrict__ x,
                                              const T* __restrict__ target, float* __restrict__ img,
                                              T* __restrict__ res, float* __restrict__ T_out,
-                                             long long tile, int lane, double& facc) {
+                                             long long tile, int lane, double& facc,
+                                             float cut = 0.0f) {
     long long ray;
     if (!tile_pixel(sc, tile, lane, ray)) return;
     Ray R;
     ray_setup(sc, ray, R);
     Comp s;
     float Te;
-    composite(sc, x, R, ray, s, Te);
+    composite(sc, x, R, ray, s, Te, MODE == 0 ? cut : 0.0f);
     if (MODE == 0) {
         img[3 * ray + 0] = s.H[0];
         img[3 * ray + 1] = s.H[1];
@@ -523,9 +532,10 @@ __global__ void __launch_bounds__(kThreads) k_forward(DevScene sc, const T* __re
                                                       const T* __restrict__ target,
                                                       float* __restrict__ img,
                                                       T* __restrict__ res,
-                                                      float* __restrict__ T_out, double* F) {
+                                                      float* __restrict__ T_out, double* F,
+                                                      float cut) {
     double facc = 0.0;
-    PERF_TILE_LOOP { forward_tile<T, MODE>(sc, x, target, img, res, T_out, tile, lane, facc); }
+    PERF_TILE_LOOP { forward_tile<T, MODE>(sc, x, target, img, res, T_out, tile, lane, facc, cut); }
     if (MODE != 0) block_add_f64<kWarps>(facc, F);
 }
 
@@ -893,31 +903,32 @@ cudaError_t launch_count_samples(const DevScene& sc, unsigned long long* out, cu
 
 template <typename T>
 cudaError_t launch_forward_t(const DevScene& sc, const void* x, const void* target, void* out,
-                             float* T_out, double* F, int mode, cudaStream_t st) {
+                             float* T_out, double* F, int mode, cudaStream_t st, float cut) {
     const T* xx = static_cast<const T*>(x);
     const T* tt = static_cast<const T*>(target);
     if (sc.n_tiles == 0) return cudaSuccess;
     if (mode == 0) {
         auto fn = k_forward<T, 0>;
         fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
-            sc, xx, tt, static_cast<float*>(out), nullptr, T_out, F);
+            sc, xx, tt, static_cast<float*>(out), nullptr, T_out, F, cut);
     } else if (mode == 1) {
         auto fn = k_forward<T, 1>;
         fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
-            sc, xx, tt, nullptr, static_cast<T*>(out), T_out, F);
+            sc, xx, tt, nullptr, static_cast<T*>(out), T_out, F, 0.0f);
     } else {
         auto fn = k_forward<T, 2>;
         fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(sc, xx, tt, nullptr,
-                                                                           nullptr, T_out, F);
+                                                                           nullptr, T_out, F, 0.0f);
     }
     count_launch();
     return cudaGetLastError();
 }
 
 cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const void* target,
-                           void* out, float* T_out, double* F, int mode, cudaStream_t st) {
-    return dtype == 1 ? launch_forward_t<__nv_bfloat16>(sc, x, target, out, T_out, F, mode, st)
-                      : launch_forward_t<float>(sc, x, target, out, T_out, F, mode, st);
+                           void* out, float* T_out, double* F, int mode, cudaStream_t st,
+                           float cut) {
+    return dtype == 1 ? launch_forward_t<__nv_bfloat16>(sc, x, target, out, T_out, F, mode, st, cut)
+                      : launch_forward_t<float>(sc, x, target, out, T_out, F, mode, st, cut);
 }
 
 template <typename T, typename TP>

@@ -894,6 +894,35 @@ perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_use
 
 uint64_t perf_launch_count(void) { return (uint64_t)__atomic_load_n(&perf::g_launches, __ATOMIC_RELAXED); }
 
+perf_status perf_render_threshold(perf_ctx* ctx, const void* x, float min_opacity,
+                                  float* rgb_out, float* T_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (!(min_opacity >= 0.0f && min_opacity <= 1.0f))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "render_threshold: min_opacity outside [0, 1]");
+    if (ctx->n_rays == 0) return PERF_OK;
+    if (bad_ptr(x) || bad_ptr(rgb_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "render_threshold: NULL x or rgb_out");
+    CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, x, nullptr, rgb_out, T_out, nullptr, 0,
+                            S(stream), min_opacity));
+    return PERF_OK;
+}
+
+perf_status perf_upsample(const float* x, int32_t G, int32_t n_shells, int32_t env_h,
+                          int32_t env_w, float* x_out, void* stream) {
+    if (!x || !x_out || G < 2 || G > 512 || n_shells < 0 || n_shells > PERF_MAX_SHELLS ||
+        (n_shells > 0 && (env_h < 2 || env_w < 2 || env_h > (1 << 14) || env_w > (1 << 14))))
+        return PERF_ERR_INVALID_ARG;
+    const long long G2 = 2ll * G;
+    const long long blocks = G2 * G2 * G2 + (long long)n_shells * 4 * env_h * env_w;
+    if (blocks >= (1ll << 31)) return PERF_ERR_INVALID_ARG;
+    const long long n_in = 4 * ((long long)G * G * G + (long long)n_shells * env_h * env_w);
+    const char* a = reinterpret_cast<const char*>(x);
+    const char* b = reinterpret_cast<const char*>(x_out);
+    if (a < b + 16 * blocks && b < a + 4 * n_in) return PERF_ERR_INVALID_ARG;   // overlap
+    cudaError_t e = perf::launch_upsample(x, G, n_shells, n_shells ? env_h : 0,
+                                          n_shells ? env_w : 0, x_out, S(stream));
+    return e == cudaSuccess ? PERF_OK : PERF_ERR_CUDA;
+}
+
 perf_status perf_sample_count(perf_ctx* ctx, uint64_t* out, void* stream) {
     if (!ctx || !out) return PERF_ERR_INVALID_ARG;
     *out = 0;

@@ -75,8 +75,10 @@ cudaError_t launch_count_samples(const DevScene& sc, unsigned long long* out, cu
 
 // mode: 0 render (out = float rgb, T_out), 1 residual (out = r, F), 2 F only.
 // target and the residual are in the scene's storage type (float / bf16).
+// cut (mode 0): the rendering opacity threshold (see composite in k_march.cu).
 cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const void* target,
-                           void* out, float* T_out, double* F, int mode, cudaStream_t st);
+                           void* out, float* T_out, double* F, int mode, cudaStream_t st,
+                           float cut = 0.0f);
 cudaError_t launch_jvp(const DevScene& sc, int dtype, const void* x, const void* p, int p_dtype,
                        float* out, cudaStream_t st);
 // mode: 0 J^T v (v float32), 1 A p (+p^T A p), 2 diag(J^T J) (+ J^T r when v = r,
@@ -148,5 +150,10 @@ cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long 
                              const float* x, const double* delta, const double* gamma,
                              const int* mask, int project, float* x_out, cudaStream_t st);
 cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t st);
+
+// Level change of the hierarchical formulation (k_hier.cu): y (level 2G,
+// maps 2He x 2We) from x (level G, maps He x We).
+cudaError_t launch_upsample(const float* x, int G, int S, int He, int We, float* y,
+                            cudaStream_t st);
 
 }  // namespace perf

@@ -308,3 +308,27 @@ def test_autotuned_tiling_keeps_results(small):
     rgb = empty(3 * ctx.n_rays)
     ctx.render(cuda_tensor(x), rgb)
     assert rel_l2(host(rgb), orc.render(x.astype(np.float64))[0]) < TOL_FP32
+
+
+@pytest.mark.parametrize("thr", [0.0, 0.3, 0.7])
+def test_render_threshold_parity(thr):
+    """Rendering threshold of a converged scene (Section "Rendering") against
+    the oracle's definition; random opacities put rays on both sides."""
+    rng = np.random.default_rng(41)
+    prob = tiny_problem(rng, G=8, n_cams=3, res=15, radii=(2.5, 5.0), sigma=(0.0, 0.6))
+    ctx, orc = make_pair(prob["G"], prob["radii"], prob["env_h"], prob["env_w"], prob["c2w"],
+                         prob["focal"], 15, 15)
+    x = prob["x"]
+    rgb = empty(3 * ctx.n_rays)
+    T = empty(ctx.n_rays)
+    ctx.render_threshold(cuda_tensor(x), thr, rgb, T)
+    ref, te = orc.render_threshold(x.astype(np.float64), thr)
+    # the cut is a decision on a float: rays within FP32 reach of the
+    # threshold may fall either way and are left out of the comparison
+    keep = np.abs((1 - te) - thr) > 1e-5
+    assert keep.sum() >= len(keep) - 2
+    assert rel_l2(host(rgb).reshape(-1, 3)[keep], ref[keep]) < TOL_FP32
+    assert rel_l2(host(T), te) < TOL_FP32
+    if thr > 0:
+        cut = (1 - te) < thr
+        assert 0 < cut.sum() < len(cut)

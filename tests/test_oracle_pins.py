@@ -544,3 +544,39 @@ def test_upsample_shell_wrap_by_hand():
     assert np.isclose(f[0, 0, 1], 0.0) and np.isclose(f[3, 0, 1], 1.0)
     assert np.isclose(f[1, 0, 1], 0.25) and np.isclose(f[2, 0, 1], 0.75)
     assert np.allclose(f[..., 3], 2.5)
+
+
+def test_render_threshold_closed_form():
+    """Section "Rendering": uniform medium (colour c, opacity sigma) inside a
+    constant shell (colour s, opacity sigma_s).  A ray with chord L has
+    volume opacity a = 1 - e^{-sigma L/h}; at or above the threshold it
+    renders c a + (1 - a) s (1 - e^{-sigma_s}), below it the shell alone,
+    s (1 - e^{-sigma_s}); a threshold of 0 is the plain render."""
+    from scenegen import make_cameras
+    rng = np.random.default_rng(23)
+    c2w, focal = make_cameras(rng, 3, 11, 3.0, "sphere", 40.0)
+    G = 5
+    orc = Oracle(G, [2.5], 2, 4, c2w, focal, 11, 11, max_samples=64)
+    c = np.array([0.9, 0.2, 0.4]); s_rgb = np.array([0.1, 0.7, 0.3]); sig, sig_s = 0.12, 0.8
+    x = np.zeros(orc.n_params).reshape(-1, 4)
+    x[:G ** 3, 0:3] = c; x[:G ** 3, 3] = sig
+    x[G ** 3:, 0:3] = s_rgb; x[G ** 3:, 3] = sig_s
+    x = x.reshape(-1)
+    h = 2.0 / G
+    shell = s_rgb * (1 - math.exp(-sig_s))
+    assert np.array_equal(orc.render_threshold(x, 0.0)[0], orc.render(x)[0])
+    thr = 0.5
+    rgb, te = orc.render_threshold(x, thr)
+    n_cut = n_kept = 0
+    for ray in range(orc.n_rays):
+        info = orc.ray_info(ray)
+        L = float(info["delta"]) * info["K"]
+        a = 1 - math.exp(-sig * L / h)
+        assert np.isclose(1 - te[ray], a, rtol=1e-12, atol=1e-15)
+        if a < thr:
+            assert np.allclose(rgb[ray], shell, rtol=1e-12)
+            n_cut += info["K"] > 0
+        else:
+            assert np.allclose(rgb[ray], c * a + (1 - a) * shell, rtol=1e-12)
+            n_kept += 1
+    assert n_cut > 10 and n_kept > 10
