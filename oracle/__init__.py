@@ -51,6 +51,7 @@ class _Problem(ctypes.Structure):
         ("max_samples", ctypes.c_int), ("jitter", ctypes.c_int),
         ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32),
         ("n_threads", ctypes.c_int),
+        ("aux", ctypes.c_int), ("aux_lambda", ctypes.c_double),
     ]
 
 
@@ -62,7 +63,8 @@ class Oracle:
     """One scene (grid size, shells, cameras) for the FP64 oracle."""
 
     def __init__(self, G, radii, env_h, env_w, c2w, focal, width, height,
-                 max_samples=512, jitter=False, seed=0, epoch=0, n_threads=0):
+                 max_samples=512, jitter=False, seed=0, epoch=0, n_threads=0, aux=False,
+                 aux_lambda=0.1):
         radii = [float(r) for r in radii]
         if len(radii) > 8:
             raise ValueError("at most 8 shells")
@@ -85,6 +87,11 @@ class Oracle:
         self.p.seed = int(seed)
         self.p.epoch = int(epoch)
         self.p.n_threads = int(n_threads)
+        # Section "Auxiliary terms": a 4th residual per ray penalising
+        # grid-exit transmittance away from 0 and 1
+        self.p.aux = int(bool(aux))
+        self.p.aux_lambda = float(aux_lambda)
+        self.n_res = 4 if aux else 3
         self.n_params = 4 * (self.G ** 3 + self.S * self.env_h * self.env_w)
         self.n_rays = self.n_cams * self.width * self.height
 
@@ -137,13 +144,14 @@ class Oracle:
         return rgb, te
 
     def residual(self, x, target, ids=None):
-        """r = H^ - C per ray and channel, F = 1/2 sum r^2 (Eq. 5-6)."""
+        """r = H^ - C per ray and channel, F = 1/2 sum r^2 (Eq. 5-6); with the
+        auxiliary term, 4 residuals per ray (the 4th L, its target 0)."""
         x = self._x(x)
         ids, N = self._ids(ids)
         target = np.ascontiguousarray(target, dtype=np.float64).reshape(-1)
         if target.shape[0] != 3 * N:
             raise ValueError("target size")
-        r = np.zeros(3 * N)
+        r = np.zeros(self.n_res * N)
         F = ctypes.c_double(0.0)
         _lib().oc_residual(ctypes.byref(self.p), _dptr(x), _dptr(target),
                            _dptr(ids) if ids is not None else None,
@@ -158,7 +166,7 @@ class Oracle:
         x = self._x(x)
         p = self._x(p)
         ids, N = self._ids(ids)
-        out = np.zeros(3 * N)
+        out = np.zeros(self.n_res * N)
         _lib().oc_jvp(ctypes.byref(self.p), _dptr(x), _dptr(p),
                       _dptr(ids) if ids is not None else None,
                       ctypes.c_int64(N), _dptr(out))
@@ -167,7 +175,7 @@ class Oracle:
     def vjp(self, x, v):
         x = self._x(x)
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
-        if v.shape[0] != 3 * self.n_rays:
+        if v.shape[0] != self.n_res * self.n_rays:
             raise ValueError("v size")
         out = np.zeros(self.n_params)
         _lib().oc_vjp(ctypes.byref(self.p), _dptr(x), _dptr(v), _dptr(out), 0)

@@ -60,6 +60,8 @@ typedef struct {
     uint64_t seed;
     uint32_t epoch;
     int n_threads;      /* <= 0: OpenMP default */
+    int aux;            /* 1: one auxiliary opacity residual per ray */
+    double aux_lambda;  /* its factor (the paper's 0.1) */
 } oc_problem;
 
 /* ---------------------------------------------------------------- jitter */
@@ -322,6 +324,22 @@ static int64_t oc_n_params(const oc_problem* P) {
 
 static int oc_cap(const oc_problem* P) { return P->max_samples + P->S + 1; }
 
+/* Residuals per ray: the three colour channels, plus the auxiliary one. */
+static int oc_nres(const oc_problem* P) { return P->aux ? 4 : 3; }
+
+/* Section "Auxiliary terms": L = lambda (1 - 4 (T^ - 1/2)^2), T^ the
+ * transmittance at grid exit (Eq. 4 over the grid samples).  With
+ * dT^/dsigma_i = -dbar_i T^ for a grid sample, dL/dsigma_i =
+ * 8 lambda (T^ - 1/2) T^ dbar_i; *dfac gets 8 lambda (T^ - 1/2) T^. */
+static void oc_aux(const oc_problem* P, const oc_sample* s, int n_grid, double* L,
+                   double* dfac) {
+    double V = 0.0;
+    for (int i = 0; i < n_grid; ++i) V += s[i].sigma * s[i].dbar;
+    const double T = exp(-V);
+    *L = P->aux_lambda * (1.0 - 4.0 * (T - 0.5) * (T - 0.5));
+    *dfac = 8.0 * P->aux_lambda * (T - 0.5) * T;
+}
+
 /* ---------------------------------------------------------- public API */
 
 int oc_param_count(const oc_problem* P, int64_t* n) { *n = oc_n_params(P); return 0; }
@@ -351,7 +369,8 @@ int oc_render(const oc_problem* P, const double* x, const int64_t* ids, int64_t 
     return 0;
 }
 
-/* Residuals r = H^ - C (Eq. 5, C8 sign) and F = 1/2 sum r^2 (Eq. 6). */
+/* Residuals r = H^ - C (Eq. 5, C8 sign) and F = 1/2 sum r^2 (Eq. 6); with
+ * aux, r has 4 entries per ray, the 4th the auxiliary term L. */
 int oc_residual(const oc_problem* P, const double* x, const double* target,
                 const int64_t* ids, int64_t n_ids, double* r, double* F) {
     const int64_t N = ids ? n_ids : oc_n_rays(P);
@@ -367,10 +386,17 @@ int oc_residual(const oc_problem* P, const double* x, const double* target,
             const int n = oc_collect(P, x, ray, buf, &ng);
             double H[3], Te, Tf;
             oc_composite(buf, n, ng, H, &Te, &Tf);
+            const int R = oc_nres(P);
             for (int k = 0; k < 3; ++k) {
                 const double rk = H[k] - target[3 * j + k];
-                if (r) r[3 * j + k] = rk;
+                if (r) r[R * j + k] = rk;
                 acc += 0.5 * rk * rk;
+            }
+            if (P->aux) {
+                double L, dfac;
+                oc_aux(P, buf, ng, &L, &dfac);
+                if (r) r[R * j + 3] = L;
+                acc += 0.5 * L * L;
             }
         }
         free(buf);
@@ -396,15 +422,19 @@ int oc_jvp(const oc_problem* P, const double* x, const double* p, const int64_t*
             int ng;
             const int n = oc_collect(P, x, ray, buf, &ng);
             oc_partials(buf, n, dc, ds);
-            double acc[3] = {0, 0, 0};
+            double acc[4] = {0, 0, 0, 0};
+            double L = 0.0, dfac = 0.0;
+            if (P->aux) oc_aux(P, buf, ng, &L, &dfac);
             for (int i = 0; i < n; ++i)
                 for (int c = 0; c < buf[i].nc; ++c) {
                     const int64_t q = 4 * buf[i].idx[c];
                     const double w = buf[i].w[c];
                     for (int k = 0; k < 3; ++k)
                         acc[k] += w * (dc[i] * p[q + k] + ds[3 * i + k] * p[q + 3]);
+                    if (i < ng) acc[3] += w * dfac * buf[i].dbar * p[q + 3];
                 }
-            out[3 * j] = acc[0]; out[3 * j + 1] = acc[1]; out[3 * j + 2] = acc[2];
+            const int R = oc_nres(P);
+            for (int k = 0; k < R; ++k) out[R * j + k] = acc[k];
         }
         free(buf); free(dc); free(ds);
     }
@@ -420,7 +450,8 @@ static void oc_reduce(double** parts, int nt, int64_t n, double* out, int accumu
     }
 }
 
-/* out = J^T v (all rays): out_j = sum_rays sum_k v_k dr_k/dx_j. */
+/* out = J^T v (all rays): out_j = sum_rays sum_k v_k dr_k/dx_j (v has 3,
+ * or with aux 4, entries per ray). */
 int oc_vjp(const oc_problem* P, const double* x, const double* v, double* out,
            int accumulate) {
     const int64_t N = oc_n_rays(P);
@@ -441,14 +472,17 @@ int oc_vjp(const oc_problem* P, const double* x, const double* v, double* out,
         double* ds = (double*)malloc(sizeof(double) * 3 * cap);
 #pragma omp for schedule(dynamic, 256)
         for (int64_t ray = 0; ray < N; ++ray) {
-            const double* vr = v + 3 * ray;
-            if (vr[0] == 0.0 && vr[1] == 0.0 && vr[2] == 0.0) continue;
+            const double* vr = v + oc_nres(P) * ray;
+            const double va = P->aux ? vr[3] : 0.0;
+            if (vr[0] == 0.0 && vr[1] == 0.0 && vr[2] == 0.0 && va == 0.0) continue;
             int ng;
             const int n = oc_collect(P, x, ray, buf, &ng);
             oc_partials(buf, n, dc, ds);
+            double L = 0.0, dfac = 0.0;
+            if (P->aux) oc_aux(P, buf, ng, &L, &dfac);
             for (int i = 0; i < n; ++i) {
-                const double gs = vr[0] * ds[3 * i] + vr[1] * ds[3 * i + 1] +
-                                  vr[2] * ds[3 * i + 2];
+                double gs = vr[0] * ds[3 * i] + vr[1] * ds[3 * i + 1] + vr[2] * ds[3 * i + 2];
+                if (i < ng) gs += va * dfac * buf[i].dbar;
                 for (int c = 0; c < buf[i].nc; ++c) {
                     const int64_t q = 4 * buf[i].idx[c];
                     const double w = buf[i].w[c];
@@ -519,12 +553,15 @@ static int oc_diag_impl(const oc_problem* P, const double* x, const double* r, d
         oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
         double* dc = (double*)malloc(sizeof(double) * cap);
         double* ds = (double*)malloc(sizeof(double) * 3 * cap);
-        oc_entry* ent = (oc_entry*)malloc(sizeof(oc_entry) * (size_t)cap * 8 * 6);
+        oc_entry* ent = (oc_entry*)malloc(sizeof(oc_entry) * (size_t)cap * 8 * 7);
 #pragma omp for schedule(dynamic, 64)
         for (int64_t ray = 0; ray < N; ++ray) {
             int ng;
             const int n = oc_collect(P, x, ray, buf, &ng);
             oc_partials(buf, n, dc, ds);
+            double L = 0.0, dfac = 0.0;
+            if (P->aux) oc_aux(P, buf, ng, &L, &dfac);
+            const int R = oc_nres(P);
             int64_t ne = 0;
             for (int i = 0; i < n; ++i)
                 for (int c = 0; c < buf[i].nc; ++c) {
@@ -534,6 +571,9 @@ static int oc_diag_impl(const oc_problem* P, const double* x, const double* r, d
                         ent[ne].q = q + k; ent[ne].k = k; ent[ne].val = w * dc[i]; ++ne;
                         ent[ne].q = q + 3; ent[ne].k = k; ent[ne].val = w * ds[3 * i + k]; ++ne;
                     }
+                    if (P->aux && i < ng) {   /* the auxiliary row: sigma only */
+                        ent[ne].q = q + 3; ent[ne].k = 3; ent[ne].val = w * dfac * buf[i].dbar; ++ne;
+                    }
                 }
             qsort(ent, (size_t)ne, sizeof(oc_entry), oc_entry_cmp);
             int64_t a = 0;
@@ -542,11 +582,14 @@ static int oc_diag_impl(const oc_problem* P, const double* x, const double* r, d
             memset(gv, 0, sizeof(gv));
             while (a < ne) {
                 int64_t b = a;
-                double g[3] = {0, 0, 0};
+                double g[4] = {0, 0, 0, 0};
                 while (b < ne && ent[b].q == ent[a].q) { g[ent[b].k] += ent[b].val; ++b; }
                 const int64_t q = ent[a].q;
-                ad[q] += g[0] * g[0] + g[1] * g[1] + g[2] * g[2];
-                if (r) ag[q] += g[0] * r[3 * ray] + g[1] * r[3 * ray + 1] + g[2] * r[3 * ray + 2];
+                ad[q] += g[0] * g[0] + g[1] * g[1] + g[2] * g[2] + g[3] * g[3];
+                if (r) {
+                    ag[q] += g[0] * r[R * ray] + g[1] * r[R * ray + 1] + g[2] * r[R * ray + 2];
+                    if (P->aux) ag[q] += g[3] * r[R * ray + 3];
+                }
                 if (ac && q / 4 < nvox) {
                     if (q / 4 != cur_vox) {
                         if (cur_vox >= 0)

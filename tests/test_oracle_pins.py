@@ -580,3 +580,80 @@ def test_render_threshold_closed_form():
             assert np.allclose(rgb[ray], c * a + (1 - a) * shell, rtol=1e-12)
             n_kept += 1
     assert n_cut > 10 and n_kept > 10
+
+
+# ------------------------------------------------------ auxiliary residual
+
+AUX_LAMBDA = 0.1
+
+
+def _aux_residual_fd_model(orc, x):
+    """The residual vector with the auxiliary term built from the forward
+    model alone: per ray (H^_0, H^_1, H^_2, L), L = lambda (1 - 4 (T^ - 1/2)^2)
+    with T^ the render's grid-exit transmittance (Section "Auxiliary terms")."""
+    rgb, te, _ = orc.render(x)
+    L = AUX_LAMBDA * (1.0 - 4.0 * (te - 0.5) ** 2)
+    return np.concatenate([rgb, L[:, None]], axis=1).ravel()
+
+
+@pytest.fixture(scope="module")
+def tiny_aux():
+    rng = np.random.default_rng(7)
+    prob = tiny_problem(rng)
+    orc = _orc(prob, aux=True, aux_lambda=AUX_LAMBDA)
+    x = prob["x"].astype(np.float64)
+    n, eps = x.shape[0], 1e-6
+    J = np.zeros((4 * orc.n_rays, n))
+    for j in range(n):
+        xp = x.copy(); xp[j] += eps
+        xm = x.copy(); xm[j] -= eps
+        J[:, j] = (_aux_residual_fd_model(orc, xp) - _aux_residual_fd_model(orc, xm)) / (2 * eps)
+    return orc, x, J
+
+
+def test_aux_derivatives_match_finite_differences(tiny_aux):
+    """J p, J^T v, diag(J^T J) and J^T r with the auxiliary row, against the
+    dense FD Jacobian of the forward model (the aux row has sigma entries
+    only; colours and shells do not move the grid-exit transmittance)."""
+    orc, x, J = tiny_aux
+    n, m = x.shape[0], J.shape[0]
+    assert np.abs(J[3::4]).max() > 1e-3
+    Jalg = np.stack([orc.jvp(x, np.eye(n)[j]) for j in range(n)], axis=1)
+    assert np.abs(Jalg - J).max() <= 1e-7 * np.abs(J).max() + 1e-9
+    for i in range(3, m, 4):
+        assert np.abs(orc.vjp(x, np.eye(m)[i]) - J[i]).max() <= 1e-7 * np.abs(J).max() + 1e-9
+    d, _ = orc.diag_grad(x)
+    assert rel_l2(d, np.sum(J * J, axis=0)) < 1e-7
+    rng = np.random.default_rng(4)
+    target = rng.uniform(0, 1, size=3 * orc.n_rays)
+    r, F = orc.residual(x, target)
+    rgb, te, _ = orc.render(x)
+    assert np.allclose(r.reshape(-1, 4)[:, :3], rgb - target.reshape(-1, 3), atol=1e-14)
+    assert np.allclose(r.reshape(-1, 4)[:, 3], AUX_LAMBDA * (1 - 4 * (te - 0.5) ** 2), atol=1e-14)
+    assert abs(F - 0.5 * float(r @ r)) < 1e-12
+    _, g = orc.diag_grad(x, r)
+    assert rel_l2(g, J.T @ r) < 1e-7
+    p = rng.normal(size=n)
+    v = rng.normal(size=m)
+    assert abs(float(orc.jvp(x, p) @ v) - float(p @ orc.vjp(x, v))) <= 1e-12 * max(abs(float(orc.jvp(x, p) @ v)), 1.0)
+
+
+def test_aux_closed_form_uniform_medium():
+    """Uniform medium (opacity sigma, no shells): T^ = e^{-sigma L/h} for a
+    chord L, so the auxiliary residual is lambda (1 - 4 (e^{-sigma L/h} - 1/2)^2):
+    0 for empty and opaque rays, lambda at T^ = 1/2."""
+    from scenegen import make_cameras
+    rng = np.random.default_rng(24)
+    c2w, focal = make_cameras(rng, 2, 9, 3.0, "sphere", 40.0)
+    G = 5
+    orc = Oracle(G, [], 2, 2, c2w, focal, 9, 9, max_samples=64, aux=True, aux_lambda=AUX_LAMBDA)
+    sig = 0.3
+    x = np.zeros(orc.n_params).reshape(-1, 4)
+    x[:, 0:3] = 0.5; x[:, 3] = sig
+    r, _ = orc.residual(x.reshape(-1), np.zeros(3 * orc.n_rays))
+    h = 2.0 / G
+    for ray in range(orc.n_rays):
+        info = orc.ray_info(ray)
+        T = math.exp(-sig * float(info["delta"]) * info["K"] / h)
+        assert math.isclose(r[4 * ray + 3], AUX_LAMBDA * (1 - 4 * (T - 0.5) ** 2), rel_tol=1e-12,
+                            abs_tol=1e-15)
