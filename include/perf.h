@@ -18,10 +18,13 @@
  *           an opacity per voxel side.  Storage is float32, or bfloat16 when
  *           the scene's dtype is PERF_BF16 (per-call entry points only).
  *   rays    N_r = n_cams * height * width, ray = (cam * height + row) * width
- *           + col; a residual / image / J p vector has 3 N_r values indexed
- *           ray * 3 + channel.  Images and J p are float32; targets and
- *           residuals (the per-ray intermediates of a step) are float32, or
- *           bfloat16 when the scene's dtype is PERF_BF16.
+ *           + col; an image or target has 3 N_r values indexed
+ *           ray * 3 + channel; a residual, J p or J^T-input vector has
+ *           R N_r values indexed ray * R + k, R = 3 (R = 4 with the
+ *           auxiliary residual, perf_options.aux: k = 3 is that term).
+ *           Images and J p are float32; targets and residuals (the per-ray
+ *           intermediates of a step) are float32, or bfloat16 when the
+ *           scene's dtype is PERF_BF16.
  * Pointers are DEVICE pointers unless a comment says HOST.  The caller owns
  * every buffer it passes in; the context owns only its workspace (PCG
  * vectors, residual buffer, FP64 scalars) and frees it in perf_destroy.
@@ -97,6 +100,13 @@ typedef struct {
     int32_t ls_max;       /* at most ls_max decimations (the printed loop has no cap) */
     int32_t project;      /* 1: trial points are projected to sigma >= 0, 0 <= c <= 1 */
     int32_t precond;      /* PERF_PRECOND_*; texels always use Jacobi */
+    int32_t aux;          /* 1: the auxiliary opacity residual of Section "Auxiliary
+                             terms", L = aux_lambda (1 - 4 (T^ - 1/2)^2) with T^ the
+                             transmittance at grid exit: every per-ray residual
+                             vector (r, J p, the v of J^T v) then has 4 entries per
+                             ray, [r_0, r_1, r_2, L] (targets stay 3 per ray).
+                             Single-scene contexts only. */
+    double aux_lambda;    /* its factor (the paper's 0.1), >= 0 */
 } perf_options;
 
 typedef struct {
@@ -145,7 +155,8 @@ typedef struct {
 } perf_tuning;
 
 /* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
- * eps 1e-3, stall 0.85, ls_alpha 0.7, ls_max 20, projection on, Jacobi. */
+ * eps 1e-3, stall 0.85, ls_alpha 0.7, ls_max 20, projection on, Jacobi, no
+ * auxiliary residual (aux_lambda 0.1). */
 perf_status perf_default_options(perf_options* out);
 
 /* Creates a context for one scene and camera set.  Validates everything
@@ -167,24 +178,24 @@ const char* perf_last_error(const perf_ctx* ctx);
 perf_status perf_render(perf_ctx* ctx, const void* x, float* rgb_out,
                         float* T_out, void* stream);
 
-/* Eq. 5-6: r_out[3 N_r] = H^ - C (may be NULL), *F_out (device double,
+/* Eq. 5-6: r_out[R N_r] = H^ - C (may be NULL), *F_out (device double,
  * overwritten) = 1/2 sum r^2 accumulated in FP64. */
 perf_status perf_residual(perf_ctx* ctx, const void* x, const void* target,
                           void* r_out, double* F_out, void* stream);
 
-/* jp_out[3 N_r] = J p: the directional derivative of every ray along p, the
+/* jp_out[R N_r] = J p: the directional derivative of every ray along p, the
  * per-sample partials of Algorithm 1 chained through the interpolation. */
 perf_status perf_jvp(perf_ctx* ctx, const void* x, const float* p,
                      float* jp_out, void* stream);
 
-/* out[n] (+)= J^T v for v[3 N_r] (Section "Update step", the scatter of
+/* out[n] (+)= J^T v for v[R N_r] (Section "Update step", the scatter of
  * grad r_i (grad r_i^T p)); accumulate = 0 overwrites out. */
 perf_status perf_vjp(perf_ctx* ctx, const void* x, const float* v, float* out,
                      int32_t accumulate, void* stream);
 
 /* Section "Preconditioner": diag_out[n] = diag(J^T J) (each row's entry for a
  * parameter is summed over all samples of that ray before squaring);
- * grad_out[n] = J^T r when r[3 N_r] and grad_out are given (both or neither). */
+ * grad_out[n] = J^T r when r[R N_r] and grad_out are given (both or neither). */
 perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const void* r,
                           float* diag_out, float* grad_out, void* stream);
 
@@ -400,7 +411,9 @@ perf_status perf_upsample(const float* x, int32_t G, int32_t n_shells, int32_t e
  * or events).  The first call on a device looks up that array's device
  * address (cudaGetSymbolAddress) with the device current; make that first
  * call before any stream capture.  Not thread-safe: one host thread at a time.
- * Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
+ * Allocates nothing: no cudaMalloc, cudaFree or allocating library call.
+ * The auxiliary residual (opts->aux) is not supported here
+ * (PERF_ERR_UNSUPPORTED). */
 #define PERF_NOALLOC_MAX_CAMS 4096
 perf_status perf_residual_noalloc(const perf_scene* scene, const perf_cameras* cams,
                                   const perf_options* opts, const void* x,

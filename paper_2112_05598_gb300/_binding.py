@@ -48,7 +48,8 @@ class Options(ctypes.Structure):
                 ("pcg_iters", ctypes.c_int32), ("pcg_fixed", ctypes.c_int32),
                 ("pcg_eps_rel", ctypes.c_double), ("pcg_stall", ctypes.c_double),
                 ("ls_alpha", ctypes.c_double), ("ls_max", ctypes.c_int32),
-                ("project", ctypes.c_int32), ("precond", ctypes.c_int32)]
+                ("project", ctypes.c_int32), ("precond", ctypes.c_int32),
+                ("aux", ctypes.c_int32), ("aux_lambda", ctypes.c_double)]
 
 
 class PcgInfo(ctypes.Structure):
@@ -275,6 +276,11 @@ class Context:
         self.width, self.height, self.n_cams = int(width), int(height), cams.n_cams
         self.n_params = int(self.lib.perf_param_count(h))
         self.n_rays = int(self.lib.perf_ray_count(h))
+
+    @property
+    def n_res(self):
+        """Residuals per ray: 3, or 4 with the auxiliary opacity term."""
+        return 4 if self.options.aux else 3
 
     @classmethod
     def from_scene(cls, scene, dtype=PERF_F32, c2w=None, focal=None, **opt_kw):

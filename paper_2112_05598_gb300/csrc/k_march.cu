@@ -149,10 +149,11 @@ __device__ __forceinline__ void composite(const DevScene& sc, const T* __restric
     }
 }
 
-// Total optical depth of a ray (grid samples, then shell hits), compensated.
+// Total optical depth of a ray (grid samples, then shell hits), compensated;
+// *Vg (may be null) gets the grid part.
 template <typename T>
 __device__ __forceinline__ CSum optical_depth(const DevScene& sc, const T* __restrict__ x,
-                                              const Ray& R, long long ray) {
+                                              const Ray& R, long long ray, CSum* Vg = nullptr) {
     CSum V = {0.0f, 0.0f};
     const float dbar = R.delta * sc.halfG;
     Interp<T, PERF_CACHE_X != 0> cx;
@@ -161,6 +162,7 @@ __device__ __forceinline__ CSum optical_depth(const DevScene& sc, const T* __res
         const Cell cl = sample_cell(sc, R, ray, k);
         csum_add(V, __fmul_rn(cx.at(x, sc, cl).w, dbar));
     }
+    if (Vg) *Vg = V;
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
         if (shell_lookup(sc, R, q, hs)) csum_add(V, interp_shell(x, hs).w);
@@ -172,6 +174,7 @@ __device__ __forceinline__ CSum optical_depth(const DevScene& sc, const T* __res
 struct Tang {
     float T, Td, H[3], J[3];
     CSum V;
+    float Te, Tde;   // T and its tangent at grid exit (auxiliary residual)
 };
 
 __device__ __forceinline__ void tang_step(Tang& s, const float4 a, const float4 q, float dbar) {
@@ -209,6 +212,8 @@ __device__ __forceinline__ void tangent(const DevScene& sc, const T* __restrict_
         const Cell cl = sample_cell(sc, R, ray, k);
         tang_step(s, cx.at(x, sc, cl), cp.at(p, sc, cl), dbar);
     }
+    s.Te = s.T;
+    s.Tde = s.Td;
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
         if (shell_lookup(sc, R, q, hs)) tang_step(s, interp_shell(x, hs), interp_shell(p, hs), 1.0f);
@@ -230,6 +235,8 @@ __device__ __forceinline__ void tangent(const DevScene& sc, const PairF32* __res
         interp_grid_pair(xp, sc, cl, a, q);
         tang_step(s, a, q, dbar);
     }
+    s.Te = s.T;
+    s.Tde = s.Td;
     for (int k = 0; k < sc.S; ++k) {
         ShellHit hs;
         if (shell_lookup(sc, R, k, hs)) {
@@ -278,27 +285,33 @@ struct VjpSink {
     }
 };
 
-// Diagonal sink: slot = (a, s_0, s_1, s_2), the ray's row entries for the
-// voxel (colour: a for each channel's residual; opacity: s_k for residual k),
-// squared into diag and multiplied by r into the gradient.
+// Diagonal sink: slot = (a, s_0, s_1, s_2[, s_3]), the ray's row entries for
+// the voxel (colour: a for each channel's residual; opacity: s_k for residual
+// k; s_3 for the auxiliary residual when NV = 5), squared into diag and
+// multiplied by r into the gradient.
 // With `cross`, also the off-diagonal entries of the voxel's 4x4 block of
-// J^T J: (colour k, opacity) = sum_rays a s_k (colour-colour entries vanish).
+// J^T J: (colour k, opacity) = sum_rays a s_k (colour-colour entries vanish,
+// and colour does not enter the auxiliary residual).
+template <int NV>
 struct DiagSink {
     float* diag;
     float* grad;
     float* cross;
     float r0, r1, r2;
-    __device__ __forceinline__ void put(bool ev, int key, const float (&a)[4]) {
-        if (!(ev && (a[0] != 0.0f || a[1] != 0.0f || a[2] != 0.0f || a[3] != 0.0f))) return;
-        const float aa = a[0] * a[0];
-        red_add4(diag, key, make_float4(aa, aa, aa, a[1] * a[1] + a[2] * a[2] + a[3] * a[3]));
-        if (grad)
-            red_add4(grad, key, make_float4(a[0] * r0, a[0] * r1, a[0] * r2,
-                                            a[1] * r0 + a[2] * r1 + a[3] * r2));
-        if (cross && key < n_vox) red_add4(cross, key, make_float4(a[0] * a[1], a[0] * a[2], a[0] * a[3], 0.0f));
-    }
     long long n_vox;
     CanonKey km;
+    float r3;
+    __device__ __forceinline__ void put(bool ev, int key, const float (&a)[NV]) {
+        const float s3 = NV == 5 ? a[(NV - 1) % NV] : 0.0f;
+        if (!(ev && (a[0] != 0.0f || a[1] != 0.0f || a[2] != 0.0f || a[3] != 0.0f || s3 != 0.0f)))
+            return;
+        const float aa = a[0] * a[0];
+        red_add4(diag, key, make_float4(aa, aa, aa, a[1] * a[1] + a[2] * a[2] + a[3] * a[3] + s3 * s3));
+        if (grad)
+            red_add4(grad, key, make_float4(a[0] * r0, a[0] * r1, a[0] * r2,
+                                            a[1] * r0 + a[2] * r1 + a[3] * r2 + s3 * r3));
+        if (cross && key < n_vox) red_add4(cross, key, make_float4(a[0] * a[1], a[0] * a[2], a[0] * a[3], 0.0f));
+    }
 };
 
 // Move the window (all lanes; `on` = this lane moves) to base nb, handing the
@@ -341,17 +354,24 @@ __device__ __forceinline__ void win_add(Window<NV>& w, const Cell& cl, const flo
 // Back-to-front sweep of Algorithm 1 for the 32 rays of a warp (all lanes
 // call it; `act` marks lanes with a ray to scatter).  V = total optical depth
 // from the first sweep; vv = the ray's weights on its three residuals (VJP:
-// v; diagonal: r).  NV = 2 (VJP) or 4 (diagonal).  The loop over samples is
-// warp-uniform (sample k of every lane in the same iteration), so coherent
-// rays evict a shared voxel in the same instruction.
+// v; diagonal: r).  NV = 2 (VJP), 4 (diagonal) or 5 (diagonal with the
+// auxiliary row).  aux_v: the auxiliary residual's opacity derivative per
+// unit interpolation weight, the same for every grid sample of the ray
+// (8 lambda (T^ - 1/2) T^ dbar), times v_aux for the VJP.  The loop over
+// samples is warp-uniform (sample k of every lane in the same iteration), so
+// coherent rays evict a shared voxel in the same instruction.
 template <int NV, typename T, class Sink>
 __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __restrict__ x,
                                                const Ray& R, long long ray, bool act, CSum V,
                                                const float (&vv)[3], Sink& sk,
-                                               float4* __restrict__ crow = nullptr) {
+                                               float4* __restrict__ crow = nullptr,
+                                               float aux_v = 0.0f) {
     float G[3] = {0.0f, 0.0f, 0.0f};
     const int Kl = act ? R.K : 0;
     const int Kmax = __reduce_max_sync(kFull, Kl);
+    // the auxiliary row's per-ray factor goes to the store's last row
+    if (NV == 5 && crow && act) __stcs(crow + (long long)(Kmax + sc.S) * 32,
+                                       make_float4(aux_v, 0.0f, 0.0f, 0.0f));
     // shells, outermost first
     for (int q = sc.S - 1; q >= 0; --q) {
         ShellHit hs;
@@ -384,6 +404,7 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
                 val[1 % NV] = W * ds[0];
                 val[2 % NV] = W * ds[1];
                 val[3 % NV] = W * ds[2];
+                if (NV == 5) val[(NV - 1) % NV] = 0.0f;
             }
             sk.put(hit, hit ? sk.km.shell(hs.idx[c]) : 0, val);
         }
@@ -427,11 +448,12 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
             float val[NV];
             val[0] = wi;
             if (NV == 2) {
-                val[1 % NV] = vv[0] * ds0 + vv[1] * ds1 + vv[2] * ds2;
+                val[1 % NV] = vv[0] * ds0 + vv[1] * ds1 + vv[2] * ds2 + aux_v;
             } else {
                 val[1 % NV] = ds0;
                 val[2 % NV] = ds1;
                 val[3 % NV] = ds2;
+                if (NV == 5) val[(NV - 1) % NV] = aux_v;
             }
             win_add(w, cl, val);
         }
@@ -469,11 +491,18 @@ __device__ __forceinline__ void forward_tile(const DevScene& sc, const T* __rest
         img[3 * ray + 2] = s.H[2];
         if (T_out) T_out[ray] = Te;
     } else {
+        const long long R3 = 3 + sc.aux;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const float r = s.H[k] - ldv(target, 3 * ray + k);
-            if (MODE == 1 && res) stv(res, 3 * ray + k, r);
+            if (MODE == 1 && res) stv(res, R3 * ray + k, r);
             facc += 0.5 * (double)r * (double)r;
+        }
+        if (sc.aux) {   // Section "Auxiliary terms": L = lambda (1 - 4 (T^ - 1/2)^2)
+            const float d = Te - 0.5f;
+            const float L = sc.aux_lambda * (1.0f - 4.0f * d * d);
+            if (MODE == 1 && res) stv(res, R3 * ray + 3, L);
+            facc += 0.5 * (double)L * (double)L;
         }
     }
 }
@@ -493,31 +522,52 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
     R.shell_hit = 0u;
     R.delta = 0.0f;
     float vr[3] = {0.0f, 0.0f, 0.0f};
+    float va = 0.0f, kap = 0.0f;   // auxiliary residual: its weight, and its d/dsigma per unit W
     CSum V = {0.0f, 0.0f};
     if (act) {
         ray_setup(sc, ray, R);
+        const float dbar = R.delta * sc.halfG;
         if (MODE == 1) {
             Tang s;
             tangent(sc, x, p, R, ray, s);
             vr[0] = s.J[0]; vr[1] = s.J[1]; vr[2] = s.J[2];
-            acc += (double)vr[0] * vr[0] + (double)vr[1] * vr[1] + (double)vr[2] * vr[2];
+            if (sc.aux) {   // L = lambda (1 - 4 (T^ - 1/2)^2): dL = -8 lambda (T^ - 1/2) dT^
+                const float d = s.Te - 0.5f;
+                va = -8.0f * sc.aux_lambda * d * s.Tde;
+                kap = 8.0f * sc.aux_lambda * d * s.Te * dbar;
+            }
+            acc += (double)vr[0] * vr[0] + (double)vr[1] * vr[1] + (double)vr[2] * vr[2] +
+                   (double)va * va;
             V = s.V;
         } else {
+            const int R3 = 3 + sc.aux;
             if (MODE == 0 || v != nullptr) {
-                vr[0] = ldv(v, 3 * ray); vr[1] = ldv(v, 3 * ray + 1); vr[2] = ldv(v, 3 * ray + 2);
+                vr[0] = ldv(v, (long long)R3 * ray);
+                vr[1] = ldv(v, (long long)R3 * ray + 1);
+                vr[2] = ldv(v, (long long)R3 * ray + 2);
+                if (sc.aux) va = ldv(v, (long long)R3 * ray + 3);
             }
-            if (MODE == 2 || vr[0] != 0.0f || vr[1] != 0.0f || vr[2] != 0.0f)
-                V = optical_depth(sc, x, R, ray);
+            if (MODE == 2 || vr[0] != 0.0f || vr[1] != 0.0f || vr[2] != 0.0f || va != 0.0f) {
+                CSum Vg = {0.0f, 0.0f};
+                V = optical_depth(sc, x, R, ray, &Vg);
+                if (sc.aux) {
+                    const float Te = expf(-fmaxf(Vg.hi + Vg.lo, 0.0f));
+                    kap = 8.0f * sc.aux_lambda * (Te - 0.5f) * Te * dbar;
+                }
+            }
         }
-        if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f) act = false;
+        if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f && va == 0.0f) act = false;
     }
-    if (MODE == 2) {
-        DiagSink sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}};
-        backward_sweep<4>(sc, x, R, ray, act, V, vr, sk,
-                          coef ? coef + tile_off[tile] * 32 + lane : nullptr);
+    float4* crow = (MODE == 2 && coef) ? coef + tile_off[tile] * 32 + lane : nullptr;
+    if (MODE == 2 && sc.aux) {
+        DiagSink<5> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}, va};
+        backward_sweep<5>(sc, x, R, ray, act, V, vr, sk, crow, kap);
+    } else if (MODE == 2) {
+        DiagSink<4> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}, 0.0f};
+        backward_sweep<4>(sc, x, R, ray, act, V, vr, sk, crow);
     } else {
         VjpSink<CanonKey> sk{out, vr[0], vr[1], vr[2], CanonKey{sc.G}};
-        backward_sweep<2>(sc, x, R, ray, act, V, vr, sk);
+        backward_sweep<2>(sc, x, R, ray, act, V, vr, sk, nullptr, va * kap);
     }
 }
 
@@ -549,9 +599,11 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
         ray_setup(sc, ray, R);
         Tang s;
         tangent(sc, x, p, R, ray, s);
-        out[3 * ray + 0] = s.J[0];
-        out[3 * ray + 1] = s.J[1];
-        out[3 * ray + 2] = s.J[2];
+        const long long R3 = 3 + sc.aux;
+        out[R3 * ray + 0] = s.J[0];
+        out[R3 * ray + 1] = s.J[1];
+        out[R3 * ray + 2] = s.J[2];
+        if (sc.aux) out[R3 * ray + 3] = -8.0f * sc.aux_lambda * (s.Te - 0.5f) * s.Tde;
     }
 }
 
@@ -589,7 +641,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
 // of Kmax + S over tiles).  Entries of samples a lane does not have (k >= K,
 // a shell it misses) are never read.
 
-// rows[t] = Kmax of tile t + S.
+// rows[t] = Kmax of tile t + S (+ 1: the auxiliary residual's per-ray factor).
 __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) {
     PERF_TILE_LOOP {
         long long ray;
@@ -600,7 +652,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) 
             K = R.K;
         }
         K = __reduce_max_sync(kFull, K);
-        if (lane == 0) rows[tile] = K + sc.S;
+        if (lane == 0) rows[tile] = K + sc.S + sc.aux;
     }
 }
 
@@ -618,11 +670,13 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
     R.delta = 0.0f;
     if (act) ray_setup(sc, ray, R);
     const long long r0 = tile_off[tile];
-    const int kmax_rows = (int)(tile_off[tile + 1] - r0) - sc.S;
+    const int kmax_rows = (int)(tile_off[tile + 1] - r0) - sc.S - sc.aux;
     const float4* crow = coef + r0 * 32 + lane;
-    // J p
+    // J p (with the auxiliary residual: kap sum of p~sigma over the grid samples)
     float J[3] = {0.0f, 0.0f, 0.0f};
+    float kap = 0.0f, Ja = 0.0f, psum = 0.0f;
     if (act) {
+        if (sc.aux) kap = __ldcs(crow + (long long)(kmax_rows + sc.S) * 32).x;
         for (int k = 0; k < R.K; ++k) {
             const float4 c = __ldcs(crow + (long long)k * 32);
             const Cell cl = sample_cell(sc, R, ray, k);
@@ -630,7 +684,9 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
             J[0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[0]));
             J[1] = fmaf(c.x, q.y, fmaf(c.z, q.w, J[1]));
             J[2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[2]));
+            psum += q.w;
         }
+        Ja = kap * psum;
         for (int s = 0; s < sc.S; ++s) {
             ShellHit hs;
             if (shell_lookup(sc, R, s, hs)) {
@@ -641,9 +697,10 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
                 J[2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[2]));
             }
         }
-        acc += (double)J[0] * J[0] + (double)J[1] * J[1] + (double)J[2] * J[2];
-        if (J[0] == 0.0f && J[1] == 0.0f && J[2] == 0.0f) act = false;
+        acc += (double)J[0] * J[0] + (double)J[1] * J[1] + (double)J[2] * J[2] + (double)Ja * Ja;
+        if (J[0] == 0.0f && J[1] == 0.0f && J[2] == 0.0f && Ja == 0.0f) act = false;
     }
+    const float aux_v = Ja * kap;   // v_aux dL/dsigma per unit interpolation weight
     // J^T (J p): the scatter of Algorithm 1 with v = J p
     VjpSink<CanonKey> sk{out, J[0], J[1], J[2], CanonKey{sc.G}};
     for (int s = sc.S - 1; s >= 0; --s) {
@@ -679,7 +736,7 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
         const int nb[3] = {cl.bx, cl.by, cl.bz};
         win_move(w, nb, on, sc.G, sk);
         if (on) {
-            const float val[2] = {c.x, J[0] * c.y + J[1] * c.z + J[2] * c.w};
+            const float val[2] = {c.x, J[0] * c.y + J[1] * c.z + J[2] * c.w + aux_v};
             win_add(w, cl, val);
         }
     }
@@ -855,7 +912,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows_batch(const BatchItem* _
             K = R.K;
         }
         K = __reduce_max_sync(kFull, K);
-        if (lane == 0) rows[t] = K + sc.S;
+        if (lane == 0) rows[t] = K + sc.S + sc.aux;
     }
 }
 

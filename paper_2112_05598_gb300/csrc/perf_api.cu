@@ -109,6 +109,10 @@ perf_status check_options(const perf_options* o, std::string& why) {
     if (o->precond != PERF_PRECOND_JACOBI && o->precond != PERF_PRECOND_BLOCK4 &&
         o->precond != PERF_PRECOND_BLOCK_JACOBI) { why = "unknown preconditioner"; return PERF_ERR_INVALID_ARG; }
     if (!(o->pcg_eps_rel >= 0.0) || !(o->pcg_stall > 0.0)) { why = "pcg_eps_rel / pcg_stall invalid"; return PERF_ERR_INVALID_ARG; }
+    if ((o->aux != 0 && o->aux != 1) || !(o->aux_lambda >= 0.0) || !std::isfinite(o->aux_lambda)) {
+        why = "aux must be 0 or 1 and aux_lambda finite and >= 0";
+        return PERF_ERR_INVALID_ARG;
+    }
     return PERF_OK;
 }
 
@@ -241,6 +245,8 @@ perf_status perf_default_options(perf_options* o) {
     o->ls_max = 20;
     o->project = 1;
     o->precond = PERF_PRECOND_JACOBI;
+    o->aux = 0;
+    o->aux_lambda = 0.1;
     return PERF_OK;
 }
 
@@ -303,6 +309,8 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
     if (ctx->n_rays == 0) d.n_tiles = 0;
     d.max_samples = opts->max_samples;
     d.jitter = opts->jitter;
+    d.aux = opts->aux;
+    d.aux_lambda = (float)opts->aux_lambda;
     d.seed = opts->seed;
     d.epoch = opts->epoch;
 
@@ -358,6 +366,12 @@ perf_status perf_set_options(perf_ctx* ctx, const perf_options* opts) {
     ctx->ds.jitter = opts->jitter;
     ctx->ds.seed = opts->seed;
     ctx->ds.epoch = opts->epoch;
+    if (ctx->ds.aux != opts->aux && ctx->r) {   // the residual buffer changes size
+        cudaFree(ctx->r);
+        ctx->r = nullptr;
+    }
+    ctx->ds.aux = opts->aux;
+    ctx->ds.aux_lambda = (float)opts->aux_lambda;
     return PERF_OK;
 }
 
@@ -537,8 +551,8 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
     const bool bf = ctx->scene.dtype == PERF_BF16;
     perf_status ps = ensure_pcg(ctx);
     if (ps != PERF_OK) return ps;
-    if (!ctx->r)
-        CK(cudaMalloc(&ctx->r, (bf ? 2 : 4) * (size_t)(3 * ctx->n_rays > 0 ? 3 * ctx->n_rays : 1)));
+    const long long m = (3 + ctx->ds.aux) * ctx->n_rays;   // residuals per GN step
+    if (!ctx->r) CK(cudaMalloc(&ctx->r, (bf ? 2 : 4) * (size_t)(m > 0 ? m : 1)));
     CK(alloc(&ctx->x_trial, ctx->n));
     if (bf) {
         CK(alloc(&ctx->x16, ctx->n));

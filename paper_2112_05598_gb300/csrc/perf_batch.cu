@@ -236,6 +236,7 @@ perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_sce
     if (!out) return PERF_ERR_INVALID_ARG;
     *out = nullptr;
     if (n_scenes < 1 || n_scenes > 4096 || !scenes || !cams || !opts) return PERF_ERR_INVALID_ARG;
+    if (opts->aux) return PERF_ERR_UNSUPPORTED;   // the auxiliary residual: single scenes
     if (opts->max_samples < 1 || opts->max_samples > (1 << 20) || opts->pcg_iters < 0 ||
         !(opts->ls_alpha > 0.0 && opts->ls_alpha < 1.0) || opts->ls_max < 0 || opts->ls_max > 200)
         return PERF_ERR_INVALID_ARG;

@@ -44,6 +44,8 @@ struct DevScene {
     int jitter;
     unsigned long long seed;
     unsigned epoch;
+    int aux;                 // 1: the auxiliary opacity residual (4 residuals per ray)
+    float aux_lambda;
 };
 
 struct Ray {

@@ -58,6 +58,7 @@ extern "C" perf_status perf_residual_noalloc(const perf_scene* sc, const perf_ca
         if (s > 0 && !(sc->shell_radii[s] > sc->shell_radii[s - 1])) return PERF_ERR_INVALID_ARG;
     }
     if (opts->max_samples < 1 || opts->max_samples > (1 << 20)) return PERF_ERR_INVALID_ARG;
+    if (opts->aux) return PERF_ERR_UNSUPPORTED;   // the 3-channel residual only
     if (cams->n_cams < 0 || cams->width < 0 || cams->height < 0) return PERF_ERR_INVALID_ARG;
     // the static camera table holds at most PERF_NOALLOC_MAX_CAMS cameras
     if (cams->n_cams > PERF_NOALLOC_MAX_CAMS) return PERF_ERR_INVALID_ARG;
