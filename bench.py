@@ -137,24 +137,32 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(v, world):
+def _reduce(v, world, op):
     if world == 1:
         return v
     import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def max_over_ranks(v, world):
+    import torch.distributed as dist
+    return _reduce(v, world, dist.ReduceOp.MAX if world > 1 else None)
 
 
 def sum_over_ranks(v, world):
-    if world == 1:
-        return v
-    import torch
     import torch.distributed as dist
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return _reduce(v, world, dist.ReduceOp.SUM if world > 1 else None)
+
+
+def replica_value(units, ms, world):
+    """Whole-job throughput of independent replicas: all ranks' units over
+    the slowest rank's time (each rank brackets its timed region with a
+    barrier and a synchronize)."""
+    return sum_over_ranks(float(units), world) / (max_over_ranks(ms, world) / 1000.0)
 
 
 class Clocks:
