@@ -121,3 +121,30 @@ def test_coef_autotune_reports_coef(prob):
     st_r, x_r, _ = _step(sc, target, x, 0, pcg_iters=2)
     assert ctx.coef_info()["used"]
     assert abs(st[0]["F_after"] - st_r[0]["F_after"]) <= TOL_FP32 * st_r[0]["F_after"]
+
+
+@pytest.mark.parametrize("aux", [0, 1])
+def test_coef_ragged_tiles_and_missing_rays(aux):
+    """Odd image sizes (partial 8x4 tiles at the right and bottom edges),
+    cameras far enough out that some rays miss the grid (K = 0) and hit only
+    shells: the store's rows and the lanes without pixels are handled, with
+    and without the auxiliary row."""
+    from conftest import tiny_problem
+    from paper_2112_05598_gb300 import Context
+    rng = np.random.default_rng(31)
+    prob = tiny_problem(rng, G=12, n_cams=3, res=13, radii=(2.5, 5.0), cam_radius=4.5,
+                        sigma=(0.0, 0.5))
+    target = rng.uniform(0, 1, size=3 * 3 * 13 * 13).astype(np.float32)
+    out = {}
+    for budget in (-1, 0):
+        ctx = Context(prob["G"], prob["radii"], prob["env_h"], prob["env_w"], prob["c2w"],
+                      prob["focal"], 13, 13, max_samples=64, pcg_iters=1, pcg_fixed=1, aux=aux)
+        ctx.set_coef_budget(budget)
+        xd = cuda_tensor(prob["x"])
+        st = ctx.gn_solve(xd, cuda_tensor(target), 1)
+        out[budget] = (st[0], host(xd), ctx.coef_info()["used"])
+        ctx.close()
+    (a, xa, ua), (b, xb, ub) = out[-1], out[0]
+    assert ua and not ub
+    assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
+    assert rel_l2(xa, xb) < TOL_FP32
