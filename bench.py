@@ -64,11 +64,17 @@ KERNEL_SOURCES = ("paper_2112_05598_gb300/csrc/k_march.cu",
 
 
 def kernel_source_hash():
+    """SHA-256 of the kernel sources with comments and whitespace removed
+    (a comment edit does not change the kernels)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, f)) as fh:
+            src = fh.read()
+        src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", " ", src)
+        h.update(" ".join(src.split()).encode())
     return h.hexdigest()
 
 

@@ -222,9 +222,11 @@ perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out,
 /* n_steps Gauss-Newton steps (Eq. 7) on x_inout[n] (float32 master copy, in
  * place; the scene dtype decides the storage the ray marches read): residual
  * and F, gradient and Jacobi diagonal, PCG, Algorithm 3 line search on
- * F(P(x + gamma Delta)), accept only if F falls.  stats (HOST, may be NULL)
- * receives n_steps records.  Synchronises (the line search reads one FP64
- * scalar per trial step). */
+ * F(P(x + gamma Delta)), accept only if F falls.  The step's diagonal march
+ * also fills the coefficient store when it fits its budget (see
+ * perf_set_coef_budget), and the PCG iterations' A p then read it.  stats
+ * (HOST, may be NULL) receives n_steps records.  Synchronises (the line
+ * search reads one FP64 scalar per trial step). */
 perf_status perf_gn_solve(perf_ctx* ctx, float* x_inout, const void* target,
                           int32_t n_steps, perf_gn_stats* stats, void* stream);
 

@@ -1,8 +1,11 @@
 // k_march.cu -- ray-march kernels of the PERF Gauss-Newton step (sm_103a).
 //
-//   k_forward   Eq. 3-4 composite: image, residual r = H^ - C, F (Eq. 5-6)
-//   k_jvp       J p by a forward tangent sweep of Eq. 3
-//   k_scatter   J^T v, the fused A p = J^T (J p), and diag(J^T J) with J^T r
+//   k_forward     Eq. 3-4 composite: image, residual r = H^ - C, F (Eq. 5-6)
+//   k_jvp         J p by a forward tangent sweep of Eq. 3
+//   k_scatter     J^T v, the fused A p = J^T (J p), and diag(J^T J) with J^T r
+//                 (the latter also fills the per-sample coefficient store)
+//   k_apply_coef  A p from the coefficient store of the Gauss-Newton step
+//   *_batch       the same over many scenes from a work queue
 //
 // Derivatives (Algorithm 1, Section "Computation of partial derivatives"):
 // for sample i with optical thickness s_i = sigma_i dbar_i, transmittance
@@ -26,11 +29,13 @@
 // touch it are consecutive and each voxel is flushed exactly once per ray --
 // which also makes the window compute the EXACT diag(J^T J): a row's entry for
 // a voxel is complete before it is squared (Section "Preconditioner").
-// Neighbouring rays cross the same voxels at the same time.  Window slots are
-// indexed by the parity of the voxel's coordinates, and the sample loop is
-// warp-uniform, so the lanes of a warp (an 8x4 pixel tile) that evict the
-// same voxel do it in the same 16-byte vector atomic, which the load/store
-// unit merges before it reaches L2.
+// Window slots are indexed by the parity of the voxel's coordinates, and the
+// sample loop is warp-uniform, so lanes of a warp (an 8x4 pixel tile) that
+// evict the same voxel in the same iteration do it in the same 16-byte
+// vector atomic, which the load/store unit merges.  (Measured: neighbouring
+// rays reach a shared voxel at different sample indices often enough that
+// the vector atomics still cost about one L1 wavefront per lane and voxel;
+// they are the limiter of the A p kernels.)
 #include "perf_device.cuh"
 #include "perf_kernels.h"
 
