@@ -75,20 +75,23 @@ __device__ __forceinline__ D4 precond(const D4& r, long long v, const float4* __
               d.z > kJacobiFloor ? r.z / d.z : 0.0, d.w > kJacobiFloor ? r.w / d.w : 0.0};
 }
 
-// Segments: blockIdx.y selects one independent system (a scene of a batch)
-// whose parameter blocks are [seg[y], seg[y+1]) and whose scalars are s[y];
-// seg == nullptr means a single segment [0, nb).
-__device__ __forceinline__ void seg_range(const long long* seg, long long nb, long long& lo,
-                                          long long& hi) {
-    if (seg) { lo = seg[blockIdx.y]; hi = seg[blockIdx.y + 1]; }
-    else { lo = 0; hi = nb; }
-}
+// Segments: a batch of independent systems (the scenes of a batch).  With
+// chunks (one int4 per CTA, built by the host: x = system, [y, z) = its
+// parameter blocks for this CTA) every CTA works inside one system, and big
+// systems get proportionally many CTAs; chunks == nullptr means a single
+// system [0, nb) over a grid-stride loop.
+__device__ __forceinline__ int seg_id(const int4* chunks) { return chunks ? chunks[blockIdx.x].x : 0; }
 
 #define SEG_LOOP(v)                                                                      \
-    long long lo_, hi_;                                                                   \
-    seg_range(seg, nb, lo_, hi_);                                                         \
-    for (long long v = lo_ + (long long)blockIdx.x * blockDim.x + threadIdx.x; v < hi_;   \
-         v += (long long)gridDim.x * blockDim.x)
+    long long lo_, hi_, step_;                                                            \
+    if (chunks) {                                                                         \
+        const int4 c_ = chunks[blockIdx.x];                                               \
+        lo_ = (long long)c_.y + threadIdx.x; hi_ = c_.z; step_ = blockDim.x;              \
+    } else {                                                                              \
+        lo_ = (long long)blockIdx.x * blockDim.x + threadIdx.x; hi_ = nb;                 \
+        step_ = (long long)gridDim.x * blockDim.x;                                        \
+    }                                                                                     \
+    for (long long v = lo_; v < hi_; v += step_)
 
 __device__ __forceinline__ double dot4(const D4& a, const D4& b) {
     return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
@@ -113,14 +116,14 @@ __device__ __forceinline__ void store_p(float4* p32, __nv_bfloat16* p16, float4*
     if (pxp) pxp[2 * v + 1] = f;
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const long long* seg,
+__global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const int4* chunks,
                                                         const float4* __restrict__ g,
                                                         const float4* __restrict__ d4,
                                                         const float4* __restrict__ B, long long n_block,
                                                         double* delta, double* rho, double* p,
                                                         float4* p32, __nv_bfloat16* p16, float4* Ap,
                                                         PcgScalars* s, float4* pxp) {
-    s += blockIdx.y;
+    s += seg_id(chunks);
     double aR = 0.0, aRz = 0.0;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     SEG_LOOP(v) {
@@ -167,14 +170,14 @@ __global__ void k_pcg_begin_fin(PcgScalars* s, int n_seg, int max_iter, int fixe
     }
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, const long long* seg,
+__global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, const int4* chunks,
                                                          double* delta, double* rho,
                                                          const double* __restrict__ p,
                                                          const float4* __restrict__ Ap,
                                                          const float4* __restrict__ d4,
                                                          const float4* __restrict__ B,
                                                          long long n_block, PcgScalars* s) {
-    s += blockIdx.y;
+    s += seg_id(chunks);
     if (s->done) return;
     const double pAp = s->pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) return;
@@ -232,13 +235,13 @@ __global__ void k_pcg_finish(PcgScalars* s, int n_seg) {
     s->pAp = 0.0;
 }
 
-__global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const long long* seg,
+__global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const int4* chunks,
                                                       const double* __restrict__ rho,
                                                       const float4* __restrict__ d4,
                                                       const float4* __restrict__ B, long long n_block,
                                                       double* p, float4* p32, __nv_bfloat16* p16,
                                                       float4* Ap, const PcgScalars* s, float4* pxp) {
-    s += blockIdx.y;
+    s += seg_id(chunks);
     if (s->done) return;
     const double beta = s->beta;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -288,14 +291,15 @@ __global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4*
 
 // Batched trial: segment y gets x_out = P(x + gamma[y] Delta) where mask[y]
 // is set (mask == nullptr: every segment); other segments are left alone.
-__global__ void __launch_bounds__(kVThreads) k_trial_seg(long long nb, const long long* seg,
+__global__ void __launch_bounds__(kVThreads) k_trial_seg(long long nb, const int4* chunks,
                                                         const float4* x,
                                                         const double* __restrict__ delta,
                                                         const double* __restrict__ gamma,
                                                         const int* __restrict__ mask, int project,
                                                         float4* x_out) {
-    if (mask && !mask[blockIdx.y]) return;
-    const double g = gamma[blockIdx.y];
+    const int sg = seg_id(chunks);
+    if (mask && !mask[sg]) return;
+    const double g = gamma[sg];
     SEG_LOOP(v) {
         const float4 a = x[v];
         const D4 d = ld4(delta, v);
@@ -330,15 +334,11 @@ __global__ void __launch_bounds__(kVThreads) k_to_f32(long long n, const double*
 #define F4(p) reinterpret_cast<float4*>(p)
 #define CF4(p) reinterpret_cast<const float4*>(p)
 
-static dim3 seg_grid(long long nb, int n_seg, long long max_seg) {
-    if (n_seg <= 1) return dim3(vec_blocks(nb), 1, 1);
-    int per = vec_blocks(max_seg);
-    const int cap = (vec_blocks(1ll << 40) + n_seg - 1) / n_seg;   // total ~ SMs * 8
-    if (per > cap) per = cap;
-    return dim3(per > 0 ? per : 1, n_seg, 1);
+static dim3 seg_grid(long long nb, long long n_chunks, const int4* chunks) {
+    return chunks ? dim3((unsigned)n_chunks, 1, 1) : dim3(vec_blocks(nb), 1, 1);
 }
 
-cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                                  const float* grad, const float* diag, double* delta, double* rho,
                                  double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                                  PcgScalars* s, int max_iter, int fixed, double eps_rel,
@@ -348,8 +348,8 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, l
     cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars) * (size_t)(n_seg > 0 ? n_seg : 1), st);
     if (e != cudaSuccess) return e;
     if (nb > 0) {
-        k_pcg_begin<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
-            nb, seg, CF4(grad), CF4(diag), CF4(blocks), n_block, delta, rho, p, F4(p32), p16,
+        k_pcg_begin<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
+            nb, chunks, CF4(grad), CF4(diag), CF4(blocks), n_block, delta, rho, p, F4(p32), p16,
             F4(Ap), s, F4(pxp));
         count_launch();
     }
@@ -363,18 +363,18 @@ cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, 
                              double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                              PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st, float* pxp) {
-    return launch_pcg_begin_seg(n, 1, nullptr, n / 4, grad, diag, delta, rho, p, p32, p16, Ap, s,
+    return launch_pcg_begin_seg(n, 1, nullptr, 0, grad, diag, delta, rho, p, p32, p16, Ap, s,
                                 max_iter, fixed, eps_rel, stall, blocks, n_block, st, pxp);
 }
 
-cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+cudaError_t launch_pcg_update_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                                   double* delta, double* rho, const double* p, const float* Ap,
                                   const float* diag, const float* blocks, long long n_block,
                                   PcgScalars* s, cudaStream_t st) {
     const long long nb = n / 4;
     if (nb > 0) {
-        k_pcg_update<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
-            nb, seg, delta, rho, p, CF4(Ap), CF4(diag), CF4(blocks), n_block, s);
+        k_pcg_update<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
+            nb, chunks, delta, rho, p, CF4(Ap), CF4(diag), CF4(blocks), n_block, s);
         count_launch();
     }
     return cudaGetLastError();
@@ -383,7 +383,7 @@ cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, 
 cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
                               const float* Ap, const float* diag, const float* blocks,
                               long long n_block, PcgScalars* s, cudaStream_t st) {
-    return launch_pcg_update_seg(n, 1, nullptr, n / 4, delta, rho, p, Ap, diag, blocks, n_block, s,
+    return launch_pcg_update_seg(n, 1, nullptr, 0, delta, rho, p, Ap, diag, blocks, n_block, s,
                                  st);
 }
 
@@ -396,14 +396,14 @@ cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st) {
 
 cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st) { return launch_pcg_finish_seg(s, 1, st); }
 
-cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                                const double* rho, const float* diag, const float* blocks,
                                long long n_block, double* p, float* p32, __nv_bfloat16* p16,
                                float* Ap, PcgScalars* s, cudaStream_t st, float* pxp) {
     const long long nb = n / 4;
     if (nb > 0) {
-        k_pcg_dir<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
-            nb, seg, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s, F4(pxp));
+        k_pcg_dir<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
+            nb, chunks, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s, F4(pxp));
         count_launch();
     }
     return cudaGetLastError();
@@ -412,17 +412,17 @@ cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, lon
 cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
                            long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                            PcgScalars* s, cudaStream_t st, float* pxp) {
-    return launch_pcg_dir_seg(n, 1, nullptr, n / 4, rho, diag, blocks, n_block, p, p32, p16, Ap, s,
+    return launch_pcg_dir_seg(n, 1, nullptr, 0, rho, diag, blocks, n_block, p, p32, p16, Ap, s,
                               st, pxp);
 }
 
-cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+cudaError_t launch_trial_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                              const float* x, const double* delta, const double* gamma,
                              const int* mask, int project, float* x_out, cudaStream_t st) {
     const long long nb = n / 4;
     if (nb > 0) {
-        k_trial_seg<<<seg_grid(nb, n_seg, max_seg), kVThreads, 0, st>>>(
-            nb, seg, CF4(x), delta, gamma, mask, project, F4(x_out));
+        k_trial_seg<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
+            nb, chunks, CF4(x), delta, gamma, mask, project, F4(x_out));
         count_launch();
     }
     return cudaGetLastError();

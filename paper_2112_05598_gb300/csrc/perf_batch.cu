@@ -8,6 +8,7 @@
 // as a CUDA graph and replayed every Gauss-Newton step.  An autotuner times
 // the A p launch over ray-tile shapes (4x8, 8x4, 16x2, 32x1 pixels per warp)
 // and resident-CTA caps and keeps the fastest.
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -29,6 +30,8 @@ struct perf_batch {
     std::vector<BatchItem> items;      // host copy
     std::vector<long long> seg_h;      // parameter-block offsets (n + 1)
     long long n_params = 0, n_rays = 0, total_tiles = 0, max_seg = 0;
+    int4* d_chunks = nullptr;          // per CTA of the vector kernels: (scene, first, end block)
+    long long n_chunks = 0;
     std::vector<long long> ray_off;    // n + 1
     BatchItem* d_items = nullptr;
     long long* d_start = nullptr;      // tile offsets (n + 1)
@@ -189,11 +192,11 @@ cudaError_t pcg_iter(perf_batch* b, cudaStream_t st) {
     cudaError_t e = b->use_coef ? apply_coef_launch(b, b->p32, &b->s[0].pAp, st, true)
                                 : apply_launch(b, b->x_work, b->p32, st, true);
     if (e == cudaSuccess)
-        e = perf::launch_pcg_update_seg(b->n_params, b->n, b->d_seg, b->max_seg, b->delta, b->rho,
+        e = perf::launch_pcg_update_seg(b->n_params, b->n, b->d_chunks, b->n_chunks, b->delta, b->rho,
                                         b->p, b->Ap, b->diag, nullptr, 0, b->s, st);
     if (e == cudaSuccess) e = perf::launch_pcg_finish_seg(b->s, b->n, st);
     if (e == cudaSuccess)
-        e = perf::launch_pcg_dir_seg(b->n_params, b->n, b->d_seg, b->max_seg, b->rho, b->diag,
+        e = perf::launch_pcg_dir_seg(b->n_params, b->n, b->d_chunks, b->n_chunks, b->rho, b->diag,
                                      nullptr, 0, b->p, b->p32, nullptr, b->Ap, b->s, st);
     return e;
 }
@@ -314,6 +317,19 @@ perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_sce
     if (e == cudaSuccess) e = dalloc(&b->d_seg, n_scenes + 1);
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_seg, b->seg_h.data(), sizeof(long long) * (n_scenes + 1), cudaMemcpyHostToDevice);
+    // the vector kernels' work split: chunks of at most 4096 parameter blocks,
+    // each inside one scene, so every scene gets CTAs in proportion to its size
+    if (e == cudaSuccess) {
+        const long long kChunk = 4096;
+        std::vector<int4> ch;
+        for (int i = 0; i < n_scenes; ++i)
+            for (long long lo = b->seg_h[i]; lo < b->seg_h[i + 1]; lo += kChunk)
+                ch.push_back(make_int4(i, (int)lo, (int)std::min(lo + kChunk, b->seg_h[i + 1]), 0));
+        b->n_chunks = (long long)ch.size();
+        e = dalloc(&b->d_chunks, b->n_chunks);
+        if (e == cudaSuccess && !ch.empty())
+            e = cudaMemcpy(b->d_chunks, ch.data(), sizeof(int4) * ch.size(), cudaMemcpyHostToDevice);
+    }
     if (e == cudaSuccess) e = dalloc(&b->counter, 1);
     if (e == cudaSuccess) e = dalloc(&b->x_work, n);
     if (e == cudaSuccess) e = dalloc(&b->x_trial, n);
@@ -342,7 +358,7 @@ perf_status perf_batch_destroy(perf_batch* b) {
     if (!b) return PERF_ERR_INVALID_ARG;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    void* bufs[] = {b->d_items, b->d_start, b->d_seg, b->cams, b->counter, b->x_work, b->x_trial,
+    void* bufs[] = {b->d_items, b->d_start, b->d_seg, b->d_chunks, b->cams, b->counter, b->x_work, b->x_trial,
                     b->r, b->diag, b->grad, b->delta, b->rho, b->p, b->p32, b->Ap, b->s, b->F,
                     b->gamma, b->mask, b->tile_off, b->coef};
     for (void* q : bufs)
@@ -489,7 +505,7 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
                                       b->x_work, nullptr, b->r, b->diag, b->grad, nullptr, 0, 2,
                                       b->cap, st, nullptr, b->use_coef ? b->coef : nullptr,
                                       b->use_coef ? b->tile_off : nullptr));
-        BK(perf::launch_pcg_begin_seg(b->n_params, n, b->d_seg, b->max_seg, b->grad, b->diag,
+        BK(perf::launch_pcg_begin_seg(b->n_params, n, b->d_chunks, b->n_chunks, b->grad, b->diag,
                                       b->delta, b->rho, b->p, b->p32, nullptr, b->Ap, b->s,
                                       o.pcg_iters, o.pcg_fixed, o.pcg_eps_rel, o.pcg_stall,
                                       nullptr, 0, st));
@@ -511,7 +527,7 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
             if (!any) break;
             BK(cudaMemcpyAsync(b->gamma, gam.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
             BK(cudaMemcpyAsync(b->mask, live.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-            BK(perf::launch_trial_seg(b->n_params, n, b->d_seg, b->max_seg, b->x_work, b->delta,
+            BK(perf::launch_trial_seg(b->n_params, n, b->d_chunks, b->n_chunks, b->x_work, b->delta,
                                       b->gamma, b->mask, o.project, b->x_trial, st));
             BK(cudaMemsetAsync(b->F, 0, sizeof(double) * n, st));
             BK(perf::launch_forward_batch(b->d_items, b->d_start, n, b->total_tiles, b->counter,
@@ -540,7 +556,7 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
         for (int i = 0; i < n; ++i) acc[i] = std::isfinite(mu_star[i]) && mu_star[i] < F0[i];
         BK(cudaMemcpyAsync(b->gamma, g_star.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
         BK(cudaMemcpyAsync(b->mask, acc.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
-        BK(perf::launch_trial_seg(b->n_params, n, b->d_seg, b->max_seg, b->x_work, b->delta,
+        BK(perf::launch_trial_seg(b->n_params, n, b->d_chunks, b->n_chunks, b->x_work, b->delta,
                                   b->gamma, b->mask, o.project, b->x_work, st));
         BK(cudaEventRecord(e1, st));
         BK(cudaMemcpyAsync(hs.data(), b->s, sizeof(PcgScalars) * n, cudaMemcpyDeviceToHost, st));

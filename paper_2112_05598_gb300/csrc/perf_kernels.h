@@ -127,26 +127,26 @@ cudaError_t launch_trial(long long n, const float* x, const double* delta, doubl
                          int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
 cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaStream_t st);
 
-// Segmented forms (a batch of independent systems): segment y owns parameter
-// blocks [seg[y], seg[y+1]) (seg: device array of n_seg + 1), scalars s[y];
-// max_seg = the largest segment (blocks) for grid sizing.
-cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+// Segmented forms (a batch of independent systems, scalars s[y] for system
+// y < n_seg): chunks (device, n_chunks int4) assigns CTA b the parameter
+// blocks [chunks[b].y, chunks[b].z) of system chunks[b].x; null = one system.
+cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                                  const float* grad, const float* diag, double* delta, double* rho,
                                  double* p, float* p32, __nv_bfloat16* p16, float* Ap,
                                  PcgScalars* s, int max_iter, int fixed, double eps_rel,
                                  double stall, const float* blocks, long long n_block,
                                  cudaStream_t st, float* pxp = nullptr);
-cudaError_t launch_pcg_update_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+cudaError_t launch_pcg_update_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                                   double* delta, double* rho, const double* p, const float* Ap,
                                   const float* diag, const float* blocks, long long n_block,
                                   PcgScalars* s, cudaStream_t st);
 cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st);
-cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                                const double* rho, const float* diag, const float* blocks,
                                long long n_block, double* p, float* p32, __nv_bfloat16* p16,
                                float* Ap, PcgScalars* s, cudaStream_t st, float* pxp = nullptr);
 // Segment y: x_out = P(x + gamma[y] Delta) where mask[y] (or every segment).
-cudaError_t launch_trial_seg(long long n, int n_seg, const long long* seg, long long max_seg,
+cudaError_t launch_trial_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                              const float* x, const double* delta, const double* gamma,
                              const int* mask, int project, float* x_out, cudaStream_t st);
 cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t st);
