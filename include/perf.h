@@ -246,15 +246,18 @@ perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_bl
  * diagonal march stores them (w_i and dH/dsigma_i, 16 bytes per sample and
  * shell hit, one row of 32 per pixel tile up to the tile's largest sample
  * count) and every PCG iteration's A p then gathers only p and reads the
- * stored values -- the same A p up to rounding.  The store is used when it
- * fits the budget: bytes = -1 (default) the free device memory minus 6 GiB
- * at the time of the step, 0 never (marches recompute everything; frees the
- * store), > 0 at most that many bytes.  The per-call entry points
- * (perf_apply_normal, perf_pcg_step) always recompute.
- * perf_coef_info: bytes held by the store, and whether the last
- * Gauss-Newton step (or perf_autotune) used it (HOST pointers, may be NULL). */
+ * stored values -- the same A p up to rounding.  The store holds the
+ * longest prefix of pixel tiles that fits the budget (bytes = -1, default:
+ * the free device memory minus 6 GiB at the time of the step; 0: never --
+ * marches recompute everything, the store is freed; > 0: at most that many
+ * bytes); the A p of the remaining tiles is recomputed.  The per-call entry
+ * points (perf_apply_normal, perf_pcg_step) always recompute.
+ * perf_coef_info: bytes held by the store, whether the last Gauss-Newton
+ * step (or perf_autotune) used it, and the fraction of tiles it covered
+ * (HOST pointers, may be NULL). */
 perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes);
-perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used);
+perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
+                           double* coverage);
 /* Times the A p launch at x along p (both in the scene storage type; p NULL:
  * p = x) over tile shapes 8x4, 4x8, 16x2, 32x1 and resident-CTA caps
  * {all, 3, 2} (two timed launches each), keeps the fastest for every later

@@ -102,7 +102,8 @@ _SIGS = {
     "perf_set_coef_budget": [_VP, ctypes.c_int64],
     "perf_upsample": [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP],
     "perf_render_threshold": [_VP, _VP, ctypes.c_float, _VP, _VP, _VP],
-    "perf_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
+    "perf_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
+                       ctypes.POINTER(ctypes.c_double)],
     "perf_set_lpc": [_VP, _VP],
     "perf_diag_cross": [_VP, _VP, _VP, _VP, _VP],
     "perf_lpc_create": [ctypes.POINTER(_VP), ctypes.c_uint64],
@@ -376,8 +377,10 @@ class Context:
     def coef_info(self):
         b = ctypes.c_int64(0)
         u = ctypes.c_int32(0)
-        self._check(self.lib.perf_coef_info(self.h, ctypes.byref(b), ctypes.byref(u)), "coef_info")
-        return dict(bytes=int(b.value), used=bool(u.value))
+        c = ctypes.c_double(0.0)
+        self._check(self.lib.perf_coef_info(self.h, ctypes.byref(b), ctypes.byref(u), ctypes.byref(c)),
+                    "coef_info")
+        return dict(bytes=int(b.value), used=bool(u.value), coverage=float(c.value))
 
     def set_lpc(self, lpc):
         self._lpc = lpc

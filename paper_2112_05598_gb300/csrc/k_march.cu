@@ -519,7 +519,8 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
                                              float* __restrict__ out, float* __restrict__ out2,
                                              float* __restrict__ out3, long long tile, int lane,
                                              double& acc, float4* __restrict__ coef = nullptr,
-                                             const long long* __restrict__ tile_off = nullptr) {
+                                             const long long* __restrict__ tile_off = nullptr,
+                                             long long coef_tiles = 0) {
     long long ray = 0;
     bool act = tile_pixel(sc, tile, lane, ray);
     Ray R;
@@ -563,7 +564,7 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
         }
         if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f && va == 0.0f) act = false;
     }
-    float4* crow = (MODE == 2 && coef) ? coef + tile_off[tile] * 32 + lane : nullptr;
+    float4* crow = (MODE == 2 && coef && tile < coef_tiles) ? coef + tile_off[tile] * 32 + lane : nullptr;
     if (MODE == 2 && sc.aux) {
         DiagSink<5> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}, va};
         backward_sweep<5>(sc, x, R, ray, act, V, vr, sk, crow, kap);
@@ -579,7 +580,7 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
 #define PERF_TILE_LOOP                                                              \
     const int lane = threadIdx.x & 31;                                              \
     const long long nw = (long long)gridDim.x * kWarps;                             \
-    for (long long tile = (long long)blockIdx.x * kWarps + (threadIdx.x >> 5);      \
+    for (long long tile = sc.tile_lo + (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); \
          tile < sc.n_tiles; tile += nw)
 
 template <typename T, int MODE>
@@ -625,7 +626,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
     double acc = 0.0;
     PERF_TILE_LOOP {
         scatter_tile<T, TP, MODE, TV>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
-                                      tile_off);
+                                      tile_off, sc.coef_tiles);
     }
     if (MODE == 1 && pap) block_add_f64<kWarps>(acc, pap);
 }
@@ -863,7 +864,8 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
                                                 v ? v + 3 * b.r_off : nullptr, out + b.x_off,
                                                 out2 ? out2 + b.x_off : nullptr, nullptr, tile,
                                                 lane, acc, coef,
-                                                tile_off ? tile_off + b.tile_off : nullptr);
+                                                tile_off ? tile_off + b.tile_off : nullptr,
+                                                b.sc.n_tiles);
         if (MODE == 1) {
             acc = warp_sum(acc);
             if (lane == 0 && acc != 0.0) atomicAdd(&pap[(long long)sidx * pap_stride], acc);
@@ -957,8 +959,8 @@ static int grid_blocks(const void* fn, long long n_tiles, int cap_per_sm = 0) {
 
 cudaError_t launch_count_samples(const DevScene& sc, unsigned long long* out, cudaStream_t st) {
     cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
-    if (e != cudaSuccess || sc.n_tiles == 0) return e;
-    k_count<<<grid_blocks((const void*)k_count, sc.n_tiles), kThreads, 0, st>>>(sc, out);
+    if (e != cudaSuccess || sc.n_tiles <= sc.tile_lo) return e;
+    k_count<<<grid_blocks((const void*)k_count, sc.n_tiles - sc.tile_lo), kThreads, 0, st>>>(sc, out);
     count_launch();
     return cudaGetLastError();
 }
@@ -968,18 +970,18 @@ cudaError_t launch_forward_t(const DevScene& sc, const void* x, const void* targ
                              float* T_out, double* F, int mode, cudaStream_t st, float cut) {
     const T* xx = static_cast<const T*>(x);
     const T* tt = static_cast<const T*>(target);
-    if (sc.n_tiles == 0) return cudaSuccess;
+    if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
     if (mode == 0) {
         auto fn = k_forward<T, 0>;
-        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
+        fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo), kThreads, 0, st>>>(
             sc, xx, tt, static_cast<float*>(out), nullptr, T_out, F, cut);
     } else if (mode == 1) {
         auto fn = k_forward<T, 1>;
-        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
+        fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo), kThreads, 0, st>>>(
             sc, xx, tt, nullptr, static_cast<T*>(out), T_out, F, 0.0f);
     } else {
         auto fn = k_forward<T, 2>;
-        fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(sc, xx, tt, nullptr,
+        fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo), kThreads, 0, st>>>(sc, xx, tt, nullptr,
                                                                            nullptr, T_out, F, 0.0f);
     }
     count_launch();
@@ -996,9 +998,9 @@ cudaError_t launch_forward(const DevScene& sc, int dtype, const void* x, const v
 template <typename T, typename TP>
 cudaError_t launch_jvp_t(const DevScene& sc, const void* x, const void* p, float* out,
                          cudaStream_t st) {
-    if (sc.n_tiles == 0) return cudaSuccess;
+    if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
     auto fn = k_jvp<T, TP>;
-    fn<<<grid_blocks((const void*)fn, sc.n_tiles), kThreads, 0, st>>>(
+    fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), out);
     count_launch();
     return cudaGetLastError();
@@ -1017,9 +1019,9 @@ cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, c
                              float* out, float* out2, double* pap, cudaStream_t st,
                              float* out3 = nullptr, float* coef = nullptr,
                              const long long* tile_off = nullptr) {
-    if (sc.n_tiles == 0) return cudaSuccess;
+    if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
     auto fn = k_scatter<T, TP, MODE, TV>;
-    fn<<<grid_blocks((const void*)fn, sc.n_tiles, sc.cap_per_sm), kThreads, 0, st>>>(
+    fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
         out2, out3, pap, reinterpret_cast<float4*>(coef), tile_off);
     count_launch();
@@ -1053,8 +1055,8 @@ cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, d
 }
 
 cudaError_t launch_tile_rows(const DevScene& sc, int* rows, cudaStream_t st) {
-    if (sc.n_tiles == 0) return cudaSuccess;
-    k_tile_rows<<<grid_blocks((const void*)k_tile_rows, sc.n_tiles), kThreads, 0, st>>>(sc, rows);
+    if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
+    k_tile_rows<<<grid_blocks((const void*)k_tile_rows, sc.n_tiles - sc.tile_lo), kThreads, 0, st>>>(sc, rows);
     count_launch();
     return cudaGetLastError();
 }
@@ -1063,9 +1065,9 @@ template <typename TP>
 cudaError_t launch_apply_coef_t(const DevScene& sc, const void* p, const float* coef,
                                 const long long* tile_off, float* out, double* pap,
                                 cudaStream_t st) {
-    if (sc.n_tiles == 0) return cudaSuccess;
+    if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
     auto fn = k_apply_coef<TP>;
-    fn<<<grid_blocks((const void*)fn, sc.n_tiles, sc.cap_per_sm), kThreads, 0, st>>>(
+    fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const TP*>(p), reinterpret_cast<const float4*>(coef), tile_off, out, pap);
     count_launch();
     return cudaGetLastError();

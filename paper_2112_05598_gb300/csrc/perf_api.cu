@@ -4,6 +4,7 @@
 // gradient with the Jacobi diagonal, Algorithm 2 on the context's workspace,
 // and Algorithm 3 evaluating F(P(x + gamma Delta)) on the device with one
 // FP64 scalar read back per trial step length.
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -52,6 +53,8 @@ struct perf_ctx {
     float* coef = nullptr;
     size_t coef_bytes = 0;             // allocated
     long long coef_rows = 0;           // rows needed by the current tiling
+    std::vector<long long> tile_off_h; // host copy of tile_off
+    long long coef_tiles = 0;          // tiles [0, coef_tiles) are in the store
     int tab_tile_w = 0, tab_max_samples = 0;
     long long tab_epoch = -1;          // epoch of a jittered table (-1: not jittered)
     bool coef_used = false;            // the last Gauss-Newton step used the store
@@ -161,11 +164,12 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
         CK(cudaMalloc(&ctx->tile_off, sizeof(long long) * off.size()));
         CK(cudaMemcpy(ctx->tile_off, off.data(), sizeof(long long) * off.size(), cudaMemcpyHostToDevice));
         ctx->coef_rows = off.back();
+        ctx->tile_off_h.swap(off);
         ctx->tab_tile_w = d.tile_w;
         ctx->tab_max_samples = d.max_samples;
         ctx->tab_epoch = epoch;
     }
-    const size_t need = (size_t)ctx->coef_rows * 32 * sizeof(float4);
+    const size_t row_bytes = 32 * sizeof(float4);
     size_t budget;
     if (ctx->coef_budget > 0) {
         budget = (size_t)ctx->coef_budget;
@@ -175,8 +179,18 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
         const size_t avail = fr + ctx->coef_bytes, reserve = (size_t)6 << 30;
         budget = avail > reserve ? avail - reserve : 0;
     }
-    if (need > budget) {
+    // the longest prefix of tiles whose rows fit: those tiles' A p reads the
+    // store, the rest recompute
+    const std::vector<long long>& off = ctx->tile_off_h;
+    long long T1 = d.n_tiles;
+    if ((size_t)off.back() * row_bytes > budget) {
+        const long long max_rows = (long long)(budget / row_bytes);
+        T1 = (long long)(std::upper_bound(off.begin(), off.end(), max_rows) - off.begin()) - 1;
+    }
+    const size_t need = (size_t)(T1 > 0 ? off[(size_t)T1] : 0) * row_bytes;
+    if (T1 <= 0 || need == 0) {
         if (ctx->coef) { cudaFree(ctx->coef); ctx->coef = nullptr; ctx->coef_bytes = 0; }
+        ctx->coef_tiles = 0;
         return PERF_OK;
     }
     if (ctx->coef_bytes < need) {
@@ -189,6 +203,7 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
         }
         ctx->coef_bytes = need;
     }
+    ctx->coef_tiles = T1;
     *use = true;
     return PERF_OK;
 }
@@ -470,11 +485,12 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
 
 namespace {
 
-// A p into the PCG workspace from separate x and p arrays.
-cudaError_t apply_arrays(perf_ctx* ctx, const void* x, const void* pp, double* pap, cudaStream_t st) {
+// A p into the PCG workspace from separate x and p arrays (tiles of d).
+cudaError_t apply_arrays(perf_ctx* ctx, const perf::DevScene& d, const void* x, const void* pp,
+                         double* pap, cudaStream_t st) {
     const int pdt = ctx->scene.dtype == PERF_BF16 ? PERF_BF16 : PERF_F32;
-    return perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, pp, pdt, nullptr, ctx->Ap, nullptr,
-                                pap, st);
+    return perf::launch_scatter(d, ctx->scene.dtype, 1, x, pp, pdt, nullptr, ctx->Ap, nullptr, pap,
+                                st);
 }
 
 // One Algorithm 2 iteration on the context workspace with diagonal `diag`
@@ -486,13 +502,21 @@ perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const floa
     const bool bf = ctx->scene.dtype == PERF_BF16;
     const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p32);
     t_begin(ctx, PERF_T_APPLY, st);
-    if (coef)
-        CK(perf::launch_apply_coef(ctx->ds, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef, ctx->tile_off,
+    // the store's tiles from the coefficients, any remaining tiles recomputed
+    perf::DevScene rest = ctx->ds;
+    if (coef) {
+        perf::DevScene head = ctx->ds;
+        head.n_tiles = ctx->coef_tiles;
+        CK(perf::launch_apply_coef(head, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef, ctx->tile_off,
                                    ctx->Ap, &ctx->s->pAp, st));
-    else if (paired)
-        CK(perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, &ctx->s->pAp, st));
-    else
-        CK(apply_arrays(ctx, x, pp, &ctx->s->pAp, st));
+        rest.tile_lo = ctx->coef_tiles;
+    }
+    if (rest.tile_lo < rest.n_tiles) {
+        if (paired)
+            CK(perf::launch_apply_pair(rest, ctx->xp, ctx->Ap, &ctx->s->pAp, st));
+        else
+            CK(apply_arrays(ctx, rest, x, pp, &ctx->s->pAp, st));
+    }
     t_end(ctx, PERF_T_APPLY, st);
     t_begin(ctx, PERF_T_VECTOR, st);
     CK(perf::launch_pcg_update(ctx->n, ctx->delta, ctx->rho, ctx->p, ctx->Ap, diag, B, ctx->n_block,
@@ -589,6 +613,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         bool use_coef = false;
         ps = ensure_coef(ctx, st, &use_coef);
         if (ps != PERF_OK) return ps;
+        ctx->ds.coef_tiles = use_coef ? ctx->coef_tiles : 0;
         t_begin(ctx, PERF_T_DIAG, st);
         if (ctx->n_rays > 0)
             CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, xm, nullptr, PERF_F32, ctx->r,
@@ -619,7 +644,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
             nB = ctx->n_block;
         }
         int fallback = 0;
-        const bool paired = !bf && ctx->pair && !use_coef;
+        const bool paired = !bf && ctx->pair && (!use_coef || ctx->coef_tiles < ctx->ds.n_tiles);
         if (paired) CK(perf::launch_pair_pack(ctx->n, x, nullptr, ctx->xp, st));
         for (int attempt = 0; attempt < 2; ++attempt) {
             CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
@@ -746,7 +771,7 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     if (!bf) CK(perf::launch_pair_pack(ctx->n, static_cast<const float*>(x), ctx->p32, ctx->xp, st));
     auto apply = [&](bool paired) -> cudaError_t {
         return paired ? perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, nullptr, st)
-                      : apply_arrays(ctx, x, pp, nullptr, st);
+                      : apply_arrays(ctx, ctx->ds, x, pp, nullptr, st);
     };
     const int tws[4] = {8, 4, 16, 32};
     const int caps[3] = {0, 3, 2};
@@ -761,7 +786,7 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     bool use_coef = false;
     perf_status pc = ensure_coef(ctx, st, &use_coef);
     if (pc != PERF_OK) return pc;
-    if (use_coef) {
+    if (use_coef && ctx->coef_tiles == ctx->ds.n_tiles) {
         float best = 1e30f, incumbent = 1e30f;
         int best_tw = 8, best_cap = 0;
         for (int i = 0; i < 4; ++i) {
@@ -769,7 +794,8 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
             bool fits = false;
             pc = ensure_coef(ctx, st, &fits);
             if (pc != PERF_OK) return pc;
-            if (!fits) continue;
+            if (!fits || ctx->coef_tiles < ctx->ds.n_tiles) continue;
+            ctx->ds.coef_tiles = ctx->coef_tiles;
             CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr,
                                     ctx->diag, nullptr, nullptr, st, nullptr, ctx->coef,
                                     ctx->tile_off));
@@ -899,10 +925,14 @@ perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes) {
     return PERF_OK;
 }
 
-perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used) {
+perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
+                           double* coverage) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (bytes_held) *bytes_held = (int64_t)ctx->coef_bytes;
     if (last_used) *last_used = ctx->coef_used ? 1 : 0;
+    if (coverage)
+        *coverage = ctx->coef_used && ctx->ds.n_tiles > 0
+                        ? (double)ctx->coef_tiles / (double)ctx->ds.n_tiles : 0.0;
     return PERF_OK;
 }
 

@@ -46,6 +46,8 @@ struct DevScene {
     unsigned epoch;
     int aux;                 // 1: the auxiliary opacity residual (4 residuals per ray)
     float aux_lambda;
+    long long tile_lo;       // a launch processes tiles [tile_lo, n_tiles)
+    long long coef_tiles;    // tiles [0, coef_tiles) have rows in the coefficient store
 };
 
 struct Ray {

@@ -148,3 +148,19 @@ def test_coef_ragged_tiles_and_missing_rays(aux):
     assert ua and not ub
     assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
     assert rel_l2(xa, xb) < TOL_FP32
+
+
+def test_coef_partial_store(prob):
+    """A budget of about half the store: the longest tile prefix that fits
+    reads the store, the other tiles recompute (paired records), in the same
+    A p; the step equals the recomputing path."""
+    sc, target, x = prob
+    _, _, full = _step(sc, target, x, -1)
+    assert full["coverage"] == 1.0
+    st_p, x_p, part = _step(sc, target, x, full["bytes"] // 2)
+    st_r, x_r, _ = _step(sc, target, x, 0)
+    assert part["used"] and 0.2 < part["coverage"] < 0.8
+    assert 0 < part["bytes"] <= full["bytes"] // 2
+    for a, b in zip(st_p, st_r):
+        assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
+    assert rel_l2(x_p, x_r) < TOL_FP32
