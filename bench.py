@@ -411,7 +411,7 @@ def run_lpc(args, rank, world, local):
             steps.append({"rel_residual": float(np.sqrt(st["R"] / st["R0"])) if st["R0"] > 0 else None,
                           "ms": st["ms"], "F_after": st["F_after"], "gamma": st["gamma"],
                           "fallback": st["precond_fallback"]})
-        results[name] = {"steps": steps, "psnr_curve": curve}
+        results[name] = {"steps": steps, "psnr_curve": curve, "coef_store": ctx.coef_info()}
     target_psnr = results["jacobi"]["psnr_curve"][-1][1] - 0.1
 
     def time_to(curve):
