@@ -34,15 +34,17 @@ import numpy as np
 WORKLOAD = "scale128"
 METRIC = "PCG iters/s"
 
-# Algorithmic work of one A p launch (fused J p and J^T (J p)), per ray-march
-# sample: tangent sweep = two 4-channel trilinear interpolations (x and p,
-# 7 lerps x 4 channels x 2 FLOP each = 112) + 28 FLOP of the transmittance /
-# tangent recurrence; adjoint sweep = one interpolation of x (56) + 12 FLOP of
-# corner weights + 27 FLOP of Algorithm 1 partials + 32 FLOP accumulating the
-# (w_i, v.dH/dsigma_i) pair into the 8 corners + 4 FLOP scaling the flushed
-# colour entries by v.  Total 271 FLOP per sample (two exp per sample are
-# counted as special-function work, not FLOP).
-FLOP_PER_SAMPLE_APPLY = 271
+# Algorithmic work of one recomputing A p launch (fused J p and J^T (J p)),
+# per ray-march sample, with one 4-channel trilinear interpolation counted as
+# 7 lerps x 4 channels x 2 FLOP = 56: optical-depth sweep = one interpolation
+# of x + 7 FLOP of compensated summation (63); J p sweep (Algorithm 1's
+# recurrence) = interpolations of x and p (112) + 27 FLOP of Algorithm 1
+# partials + 12 FLOP of the J p update (151); adjoint sweep = one
+# interpolation of x (56) + 12 FLOP of corner weights + 27 FLOP of partials +
+# 32 FLOP accumulating the (w_i, v.dH/dsigma_i) pair into the 8 corners +
+# 4 FLOP scaling the flushed colour entries by v (131).  Total 345 FLOP per
+# sample (exponentials are special-function work, not FLOP).
+FLOP_PER_SAMPLE_APPLY = 345
 
 # The coefficient-cached A p streams the per-sample coefficients (16 bytes,
 # stored by the step's diagonal march) twice per launch -- the J p sweep and

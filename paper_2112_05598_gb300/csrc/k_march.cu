@@ -1,7 +1,7 @@
 // k_march.cu -- ray-march kernels of the PERF Gauss-Newton step (sm_103a).
 //
 //   k_forward     Eq. 3-4 composite: image, residual r = H^ - C, F (Eq. 5-6)
-//   k_jvp         J p by a forward tangent sweep of Eq. 3
+//   k_jvp         J p by the back-to-front recurrence of Algorithm 1
 //   k_scatter     J^T v, the fused A p = J^T (J p), and diag(J^T J) with J^T r
 //                 (the latter also fills the per-sample coefficient store)
 //   k_apply_coef  A p from the coefficient store of the Gauss-Newton step
@@ -36,6 +36,7 @@
 // rays reach a shared voxel at different sample indices often enough that
 // the vector atomics still cost about one L1 wavefront per lane and voxel;
 // they are the limiter of the A p kernels.)
+#include <type_traits>
 #include "perf_device.cuh"
 #include "perf_kernels.h"
 
@@ -175,80 +176,75 @@ __device__ __forceinline__ CSum optical_depth(const DevScene& sc, const T* __res
     return V;
 }
 
-// Tangent sweep: H^, (J p) and the optical depth V of one ray.
-struct Tang {
-    float T, Td, H[3], J[3];
-    CSum V;
-    float Te, Tde;   // T and its tangent at grid exit (auxiliary residual)
-};
-
-__device__ __forceinline__ void tang_step(Tang& s, const float4 a, const float4 q, float dbar) {
-    const float sd = __fmul_rn(a.w, dbar);
-    const float e = expf(-sd);
-    const float alpha = one_minus_exp_neg(sd, e);
-    const float w = __fmul_rn(s.T, alpha);
-    const float tsd = s.T * dbar * q.w;               // T dbar sigma_dot
-    const float coef = fmaf(s.Td, alpha, tsd * e);     // T_dot alpha + T e dbar sigma_dot
-    s.J[0] = fmaf(coef, a.x, fmaf(w, q.x, s.J[0]));
-    s.J[1] = fmaf(coef, a.y, fmaf(w, q.y, s.J[1]));
-    s.J[2] = fmaf(coef, a.z, fmaf(w, q.z, s.J[2]));
-    s.H[0] = fmaf(w, a.x, s.H[0]);
-    s.H[1] = fmaf(w, a.y, s.H[1]);
-    s.H[2] = fmaf(w, a.z, s.H[2]);
-    s.Td = e * (s.Td - tsd);
-    s.T = __fmul_rn(s.T, e);
-    csum_add(s.V, sd);
-}
-
+// J p of one ray (V: the total optical depth from the first sweep; with
+// paired storage x holds both operands and p is not read) by
+// Algorithm 1's back-to-front recurrence: the same w_i and dH/dsigma_i as
+// the scatter sweep (backward_sweep), with the same operations in the same
+// order, so that J p and J^T v apply one matrix and its transpose and the
+// fused A p = J^T (J p) is symmetric.  A forward tangent sweep of Eq. 3 gives
+// the same J p in exact arithmetic, but its binary32 rounding differs from
+// the scatter's: behind opaque media dH/dsigma_i is a small difference of
+// two nearly equal terms, so along Jacobi-scaled directions (which blow up
+// barely observed parameters) the two roundings disagree by up to ~10% in
+// v.(J p) against p.(J^T v), and CG stalls.  psum = the sum of p~sigma over
+// the grid samples (the auxiliary row's J p is proportional to it).
 template <typename T, typename TP>
-__device__ __forceinline__ void tangent(const DevScene& sc, const T* __restrict__ x,
-                                        const TP* __restrict__ p, const Ray& R, long long ray,
-                                        Tang& s) {
-    s.T = 1.0f; s.Td = 0.0f;
-    s.H[0] = s.H[1] = s.H[2] = 0.0f;
-    s.J[0] = s.J[1] = s.J[2] = 0.0f;
-    s.V.hi = 0.0f; s.V.lo = 0.0f;
-    const float dbar = R.delta * sc.halfG;
-    Interp<T, PERF_CACHE_X != 0> cx;
-    Interp<TP, PERF_CACHE_P != 0> cp;
-    cx.reset();
-    cp.reset();
-    for (int k = 0; k < R.K; ++k) {
-        const Cell cl = sample_cell(sc, R, ray, k);
-        tang_step(s, cx.at(x, sc, cl), cp.at(p, sc, cl), dbar);
-    }
-    s.Te = s.T;
-    s.Tde = s.Td;
-    for (int q = 0; q < sc.S; ++q) {
+__device__ __forceinline__ void jvp_backward(const DevScene& sc, const T* __restrict__ x,
+                                             const TP* __restrict__ p, const Ray& R, long long ray,
+                                             CSum V, float (&J)[3], float& psum) {
+    float G[3] = {0.0f, 0.0f, 0.0f};
+    J[0] = J[1] = J[2] = 0.0f;
+    psum = 0.0f;
+    for (int q = sc.S - 1; q >= 0; --q) {
         ShellHit hs;
-        if (shell_lookup(sc, R, q, hs)) tang_step(s, interp_shell(x, hs), interp_shell(p, hs), 1.0f);
-    }
-}
-
-// The same sweep from paired x / p storage (one 256-bit load per corner).
-__device__ __forceinline__ void tangent(const DevScene& sc, const PairF32* __restrict__ xp,
-                                        const PairF32* __restrict__, const Ray& R, long long ray,
-                                        Tang& s) {
-    s.T = 1.0f; s.Td = 0.0f;
-    s.H[0] = s.H[1] = s.H[2] = 0.0f;
-    s.J[0] = s.J[1] = s.J[2] = 0.0f;
-    s.V.hi = 0.0f; s.V.lo = 0.0f;
-    const float dbar = R.delta * sc.halfG;
-    for (int k = 0; k < R.K; ++k) {
-        const Cell cl = sample_cell(sc, R, ray, k);
-        float4 a, q;
-        interp_grid_pair(xp, sc, cl, a, q);
-        tang_step(s, a, q, dbar);
-    }
-    s.Te = s.T;
-    s.Tde = s.Td;
-    for (int k = 0; k < sc.S; ++k) {
-        ShellHit hs;
-        if (shell_lookup(sc, R, k, hs)) {
-            float4 a, q;
-            interp_shell_pair(xp, hs, a, q);
-            tang_step(s, a, q, 1.0f);
+        if (!shell_lookup(sc, R, q, hs)) continue;
+        float4 a, pv;
+        if constexpr (std::is_same<T, PairF32>::value) {
+            interp_shell_pair(x, hs, a, pv);
+        } else {
+            a = interp_shell(x, hs);
+            pv = interp_shell(p, hs);
         }
+        const float sd = a.w;
+        csum_add(V, -sd);
+        const float Ti = expf(-fmaxf(V.hi + V.lo, 0.0f));
+        const float e = expf(-sd);
+        const float wi = Ti * one_minus_exp_neg(sd, e);
+        const float te = Ti * e;
+        const float ds0 = te * a.x - G[0], ds1 = te * a.y - G[1], ds2 = te * a.z - G[2];
+        G[0] = fmaf(wi, a.x, G[0]);
+        G[1] = fmaf(wi, a.y, G[1]);
+        G[2] = fmaf(wi, a.z, G[2]);
+        J[0] = fmaf(wi, pv.x, fmaf(ds0, pv.w, J[0]));
+        J[1] = fmaf(wi, pv.y, fmaf(ds1, pv.w, J[1]));
+        J[2] = fmaf(wi, pv.z, fmaf(ds2, pv.w, J[2]));
+    }
+    const float dbar = R.delta * sc.halfG;
+    for (int k = R.K - 1; k >= 0; --k) {
+        const Cell cl = sample_cell(sc, R, ray, k);
+        float4 a, pv;
+        if constexpr (std::is_same<T, PairF32>::value) {
+            interp_grid_pair(x, sc, cl, a, pv);
+        } else {
+            a = interp_grid(x, sc, cl);
+            pv = interp_grid(p, sc, cl);
+        }
+        const float sd = __fmul_rn(a.w, dbar);
+        csum_add(V, -sd);
+        const float Ti = expf(-fmaxf(V.hi + V.lo, 0.0f));
+        const float e = expf(-sd);
+        const float wi = Ti * one_minus_exp_neg(sd, e);
+        const float te = Ti * e;
+        const float ds0 = dbar * (te * a.x - G[0]);
+        const float ds1 = dbar * (te * a.y - G[1]);
+        const float ds2 = dbar * (te * a.z - G[2]);
+        G[0] = fmaf(wi, a.x, G[0]);
+        G[1] = fmaf(wi, a.y, G[1]);
+        G[2] = fmaf(wi, a.z, G[2]);
+        J[0] = fmaf(wi, pv.x, fmaf(ds0, pv.w, J[0]));
+        J[1] = fmaf(wi, pv.y, fmaf(ds1, pv.w, J[1]));
+        J[2] = fmaf(wi, pv.z, fmaf(ds2, pv.w, J[2]));
+        psum += pv.w;
     }
 }
 
@@ -534,17 +530,19 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
         ray_setup(sc, ray, R);
         const float dbar = R.delta * sc.halfG;
         if (MODE == 1) {
-            Tang s;
-            tangent(sc, x, p, R, ray, s);
-            vr[0] = s.J[0]; vr[1] = s.J[1]; vr[2] = s.J[2];
-            if (sc.aux) {   // L = lambda (1 - 4 (T^ - 1/2)^2): dL = -8 lambda (T^ - 1/2) dT^
-                const float d = s.Te - 0.5f;
-                va = -8.0f * sc.aux_lambda * d * s.Tde;
-                kap = 8.0f * sc.aux_lambda * d * s.Te * dbar;
+            // A p: first sweep V, second J p by Algorithm 1 (see jvp_backward),
+            // third the scatter below
+            CSum Vg = {0.0f, 0.0f};
+            V = optical_depth(sc, x, R, ray, &Vg);
+            float psum;
+            jvp_backward(sc, x, p, R, ray, V, vr, psum);
+            if (sc.aux) {   // L = lambda (1 - 4 (T^ - 1/2)^2): dL/dsigma_i = kap per unit weight
+                const float Te = expf(-fmaxf(Vg.hi + Vg.lo, 0.0f));
+                kap = 8.0f * sc.aux_lambda * (Te - 0.5f) * Te * dbar;
+                va = kap * psum;
             }
             acc += (double)vr[0] * vr[0] + (double)vr[1] * vr[1] + (double)vr[2] * vr[2] +
                    (double)va * va;
-            V = s.V;
         } else {
             const int R3 = 3 + sc.aux;
             if (MODE == 0 || v != nullptr) {
@@ -603,13 +601,18 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
         if (!tile_pixel(sc, tile, lane, ray)) continue;
         Ray R;
         ray_setup(sc, ray, R);
-        Tang s;
-        tangent(sc, x, p, R, ray, s);
+        CSum Vg = {0.0f, 0.0f};
+        const CSum V = optical_depth(sc, x, R, ray, &Vg);
+        float J[3], psum;
+        jvp_backward(sc, x, p, R, ray, V, J, psum);
         const long long R3 = 3 + sc.aux;
-        out[R3 * ray + 0] = s.J[0];
-        out[R3 * ray + 1] = s.J[1];
-        out[R3 * ray + 2] = s.J[2];
-        if (sc.aux) out[R3 * ray + 3] = -8.0f * sc.aux_lambda * (s.Te - 0.5f) * s.Tde;
+        out[R3 * ray + 0] = J[0];
+        out[R3 * ray + 1] = J[1];
+        out[R3 * ray + 2] = J[2];
+        if (sc.aux) {   // dL = -8 lambda (T^ - 1/2) dT^, dT^ = -T^ dbar sum_i p~sigma_i
+            const float Te = expf(-fmaxf(Vg.hi + Vg.lo, 0.0f));
+            out[R3 * ray + 3] = 8.0f * sc.aux_lambda * (Te - 0.5f) * Te * R.delta * sc.halfG * psum;
+        }
     }
 }
 

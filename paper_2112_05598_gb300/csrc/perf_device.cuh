@@ -203,7 +203,7 @@ template <> struct Store<__nv_bfloat16> {
 };
 
 // Paired FP32 storage: record v holds parameter block v of x (first 16 bytes)
-// and of the PCG direction p (last 16 bytes), so the tangent sweep of A p
+// and of the PCG direction p (last 16 bytes), so the J p sweep of A p
 // fetches both with one 256-bit load per corner.  Read through Store it
 // yields the x half.  Records are 32-byte aligned (device allocations are).
 struct PairF32 {
