@@ -123,6 +123,8 @@ def parse():
     ap.add_argument("--lpc-gn", type=int, default=6)
     ap.add_argument("--lpc-pcg", type=int, default=5)
     ap.add_argument("--lpc-traj", type=int, default=60)
+    ap.add_argument("--conv", type=int, default=0,
+                    help="time the learned preconditioner's 4-layer network on a G^3 grid")
     return ap.parse_args()
 
 
@@ -285,6 +287,57 @@ BATCH_PCG = 20
 def _psnr_from_F(F, n_rays):
     mse = 2.0 * F / (3.0 * n_rays)
     return float("inf") if mse <= 0 else 10.0 * np.log10(1.0 / mse)
+
+
+def run_conv(args, rank, world, local):
+    """The learned preconditioner's network (4 layers of 3x3x3 convolution,
+    16 channels, bf16 activations) on a --conv G grid of random features:
+    the tcgen05 convolution's throughput against the measured bf16 tensor
+    peak, and its activation traffic (32 bytes read + 32 written per voxel and
+    layer) against the measured HBM bandwidth."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2112_05598_gb300 import LPC
+    from paper_2112_05598_gb300._binding import launch_count
+    torch.cuda.set_device(local)
+    G = args.conv
+    net = LPC(seed=1)
+    gen = torch.Generator(device="cuda").manual_seed(0)
+    feat = torch.randn(16 * G ** 3, device="cuda", generator=gen).to(torch.bfloat16)
+    out = torch.empty(16 * G ** 3, dtype=torch.bfloat16, device="cuda")
+    for _ in range(max(args.warmup, 3)):
+        net.head_outputs(G, feat, out)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    l0 = launch_count()
+    e0.record(stream)
+    for _ in range(args.steps):
+        net.head_outputs(G, feat, out)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = launch_count() - l0
+    ms = e0.elapsed_time(e1) / args.steps
+    layers = 4
+    flop = layers * G ** 3 * 27 * 16 * 16 * 2
+    byts = layers * G ** 3 * 64
+    peaks, src = measured_peaks()
+    tf = flop / (ms * 1e-3) / 1e12
+    line = {"metric": "conv TFLOP/s", "value": tf, "unit": "TFLOP/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "dtype": "bf16", "data": "synthetic (random features)",
+            "config": {"workload": f"learned-preconditioner network, {G}^3 grid, 4 layers, "
+                                   f"16 channels, 3x3x3 taps"},
+            "gpu_launches": launches,
+            "roofline": {"bound": "tensor", "achieved": tf, "peak": peaks["bf16_tflops"],
+                         "unit": "TFLOP/s", "frac": tf / peaks["bf16_tflops"],
+                         "peak_source": f"bf16_tflops ({src})",
+                         "hbm_frac": byts / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "kernel": "k_conv_fwd_tc (tcgen05, TMA halo staging)"}}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def run_lpc(args, rank, world, local):
@@ -782,6 +835,8 @@ def main():
     rank, world, local = dist_setup(args.gpus)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.conv:
+        run_conv(args, rank, world, local)
     elif args.lpc:
         run_lpc(args, rank, world, local)
     elif args.hier:

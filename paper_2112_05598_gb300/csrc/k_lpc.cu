@@ -8,11 +8,12 @@
 // "Preconditioner".  The net: 4 layers of 3x3x3 convolution, 16 channels
 // (inputs and the 10 head outputs padded to 16), ReLU between layers,
 // activations channels-last [voxel][16] in bfloat16, FP32 accumulation.
-// Convolutions are implicit GEMMs on the tensor cores (mma.sync m16n8k16,
-// bf16 inputs, fp32 accumulators): one warp computes 16 voxels x 16 output
-// channels, K = 27 taps x 16 input channels.  The backward pass reuses the
-// forward kernel with flipped, transposed weights for the data gradient; the
-// weight gradient is a per-tap GEMM over voxels.  Training minimises, over
+// The forward convolution (k_conv_tc.cu) runs on the tcgen05 tensor cores
+// with TMA-staged halos; the backward pass reuses it with flipped,
+// transposed weights for the data gradient.  The weight gradient (here) is a
+// per-tap GEMM over voxels with M = N = 16 -- below the smallest tcgen05 tile
+// -- on warp-level mma.sync (bf16 inputs, fp32 accumulators), reduced across
+// warps with atomics.  Training minimises, over
 // logged probe pairs (xi, a_hat = D^{-1/2} A D^{-1/2} xi), the relative error
 // sum_v |Q_v a_hat_v - xi_v|^2 / sum |xi|^2 with Adam.
 #include <cuda_bf16.h>
@@ -25,10 +26,6 @@ namespace perf {
 constexpr int kC = 16;        // channels (padded)
 constexpr int kTaps = 27;
 constexpr int kLThreads = 128;
-
-__device__ __forceinline__ uint32_t ld_b32(const __nv_bfloat16* p) {
-    return *reinterpret_cast<const uint32_t*>(p);
-}
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2,
                                          uint32_t a3, uint32_t b0, uint32_t b1) {
@@ -48,64 +45,19 @@ __device__ __forceinline__ uint32_t pack_raw(__nv_bfloat16 lo, __nv_bfloat16 hi)
     return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
 }
 
-// Linear voxel index of v's neighbour at tap (dz, dy, dx) in {-1,0,1}^3, or -1.
+// Linear voxel index of v's neighbour at tap (dz, dy, dx) in {-1,0,1}^3, or
+// -1 (32-bit index arithmetic: a grid has fewer than 2^31 voxels).
 __device__ __forceinline__ long long nbr(long long v, int G, int tap) {
     if (v < 0) return -1;
     const int dx = tap % 3 - 1, dy = (tap / 3) % 3 - 1, dz = tap / 9 - 1;
-    const long long GG = (long long)G * G;
-    const int z = (int)(v / GG);
-    const int y = (int)((v / G) % G);
-    const int x = (int)(v % G);
-    const int xx = x + dx, yy = y + dy, zz = z + dz;
+    const unsigned uv = (unsigned)v, ug = (unsigned)G;
+    const unsigned q = uv / ug;
+    const int x = (int)(uv - q * ug);
+    const unsigned z = q / ug;
+    const int y = (int)(q - z * ug);
+    const int xx = x + dx, yy = y + dy, zz = (int)z + dz;
     if (xx < 0 || yy < 0 || zz < 0 || xx >= G || yy >= G || zz >= G) return -1;
     return ((long long)zz * G + yy) * G + xx;
-}
-
-// out[v][co] = act(bias[co] + sum_tap sum_ci in[nbr(v,tap)][ci] W[tap][co][ci])
-// W layout [tap][co][ci] (ci fastest, bf16); act = ReLU if relu.
-__global__ void __launch_bounds__(kLThreads) k_conv_fwd(const __nv_bfloat16* __restrict__ in,
-                                                       const __nv_bfloat16* __restrict__ W,
-                                                       const float* __restrict__ bias,
-                                                       __nv_bfloat16* __restrict__ out, int G,
-                                                       int relu) {
-    __shared__ __align__(16) __nv_bfloat16 sW[kTaps * kC * kC];
-    for (int i = threadIdx.x; i < kTaps * kC * kC / 2; i += blockDim.x)
-        reinterpret_cast<uint32_t*>(sW)[i] = reinterpret_cast<const uint32_t*>(W)[i];
-    __syncthreads();
-    const long long V = (long long)G * G * G;
-    const long long n_tiles = (V + 15) / 16;
-    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-    const long long nwarps = (long long)gridDim.x * (blockDim.x >> 5);
-    for (long long tile = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-         tile < n_tiles; tile += nwarps) {
-        const long long r0 = tile * 16 + g, r1 = r0 + 8;
-        const long long v0 = r0 < V ? r0 : -1, v1 = r1 < V ? r1 : -1;
-        float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
-        for (int tap = 0; tap < kTaps; ++tap) {
-            const long long n0 = nbr(v0, G, tap), n1 = nbr(v1, G, tap);
-            const uint32_t a0 = n0 >= 0 ? ld_b32(in + n0 * kC + 2 * t) : 0u;
-            const uint32_t a1 = n1 >= 0 ? ld_b32(in + n1 * kC + 2 * t) : 0u;
-            const uint32_t a2 = n0 >= 0 ? ld_b32(in + n0 * kC + 2 * t + 8) : 0u;
-            const uint32_t a3 = n1 >= 0 ? ld_b32(in + n1 * kC + 2 * t + 8) : 0u;
-#pragma unroll
-            for (int nt = 0; nt < 2; ++nt) {
-                const __nv_bfloat16* w = sW + (tap * kC + nt * 8 + g) * kC;
-                mma_bf16(acc[nt], a0, a1, a2, a3, ld_b32(w + 2 * t), ld_b32(w + 2 * t + 8));
-            }
-        }
-#pragma unroll
-        for (int nt = 0; nt < 2; ++nt) {
-            const int co = nt * 8 + 2 * t;
-            float o0 = acc[nt][0] + bias[co], o1 = acc[nt][1] + bias[co + 1];
-            float o2 = acc[nt][2] + bias[co], o3 = acc[nt][3] + bias[co + 1];
-            if (relu) {
-                o0 = fmaxf(o0, 0.f); o1 = fmaxf(o1, 0.f);
-                o2 = fmaxf(o2, 0.f); o3 = fmaxf(o3, 0.f);
-            }
-            if (v0 >= 0) *reinterpret_cast<uint32_t*>(out + v0 * kC + co) = pack_bf16(o0, o1);
-            if (v1 >= 0) *reinterpret_cast<uint32_t*>(out + v1 * kC + co) = pack_bf16(o2, o3);
-        }
-    }
 }
 
 // dW[tap][co][ci] += sum_v gpre[v][co] in[nbr(v,tap)][ci]   (FP32 accumulate)
@@ -460,15 +412,6 @@ static int lpc_blocks(long long work, int threads) {
     long long cap = (long long)sms * 16;
     long long b = want < cap ? want : cap;
     return (int)(b > 0 ? b : 1);
-}
-
-cudaError_t lpc_conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* W, const float* bias,
-                         __nv_bfloat16* out, int G, int relu, cudaStream_t st) {
-    const long long V = (long long)G * G * G;
-    const long long tiles = (V + 15) / 16;
-    k_conv_fwd<<<lpc_blocks(tiles * 32, kLThreads), kLThreads, 0, st>>>(in, W, bias, out, G, relu);
-    count_launch();
-    return cudaGetLastError();
 }
 
 cudaError_t lpc_conv_bwd_w(const __nv_bfloat16* in, const __nv_bfloat16* gpre, float* dW,

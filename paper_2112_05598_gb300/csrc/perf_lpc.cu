@@ -25,6 +25,7 @@ cudaError_t lpc_conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* W, const 
 cudaError_t lpc_conv_bwd_w(const __nv_bfloat16* in, const __nv_bfloat16* gpre, float* dW,
                            float* dB, int G, cudaStream_t st);
 cudaError_t lpc_conv_flip(const __nv_bfloat16* W, __nv_bfloat16* Wt, cudaStream_t st);
+int lpc_conv_error();
 cudaError_t lpc_relu_bwd(__nv_bfloat16* g, const __nv_bfloat16* act, long long n, cudaStream_t st);
 cudaError_t lpc_head_train(const __nv_bfloat16* o, const float* ahat, const float* xi,
                            const unsigned char* mask, __nv_bfloat16* gout, long long V, float scale,
@@ -247,6 +248,8 @@ perf_status perf_lpc_loss_grad(perf_lpc* L, int32_t G, const void* feat, const f
     if (loss_out) {
         LK(cudaMemcpyAsync(loss_out, L->dloss, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
         LK(cudaStreamSynchronize(S(stream)));
+        // a convolution whose bounded waits ran out has left its outputs incomplete
+        if (perf::lpc_conv_error() != 0) return PERF_ERR_CUDA;
     }
     return PERF_OK;
 }

@@ -49,11 +49,11 @@ def _feat(rng, G):
     return t, t.float().cpu().numpy().astype(np.float64).reshape(G, G, G, 16)
 
 
-def test_forward_loss_and_gradient_match_fp64_oracle():
+@pytest.mark.parametrize("G", [6, 13])
+def test_forward_loss_and_gradient_match_fp64_oracle(G):
     import torch
     from oracle import lpc as OL
     rng = np.random.default_rng(5)
-    G = 6
     net, w = _net()
     feat_t, feat = _feat(rng, G)
     out = torch.empty(16 * G ** 3, dtype=torch.bfloat16, device="cuda")
@@ -77,6 +77,39 @@ def test_forward_loss_and_gradient_match_fp64_oracle():
         s = slice(l * OL.LAYER, (l + 1) * OL.LAYER)
         a, b = host(gw)[s], gref[s]
         assert float(a @ b) > 0.95 * np.linalg.norm(a) * np.linalg.norm(b), l
+
+
+@pytest.mark.parametrize("G", [5, 13, 21, 40])
+def test_single_convolution_on_ragged_grids(G):
+    """The tensor-core convolution against the FP64 oracle on grids that are
+    not multiples of its 8 x 16 output tile (and smaller than its halo box):
+    layer 1 random, layers 2-4 the identity (centre tap, zero bias), so the
+    head outputs are layer 1's outputs, rounded to bf16 once."""
+    import torch
+    from oracle import lpc as OL
+    from paper_2112_05598_gb300 import LPC
+    rng = np.random.default_rng(G)
+    net = LPC(seed=4)
+    w = np.zeros(net.n_weights)
+    w[:OL.W_PER] = rng.normal(size=OL.W_PER) * 0.2
+    w[OL.W_PER:OL.LAYER] = rng.normal(size=OL.C) * 0.1
+    ident = np.zeros((OL.TAPS, OL.C, OL.C))
+    ident[13] = np.eye(OL.C)
+    for l in range(1, OL.LAYERS):
+        w[l * OL.LAYER:l * OL.LAYER + OL.W_PER] = ident.ravel()
+    net.set_weights(w.astype(np.float32))
+    f = rng.normal(size=(G ** 3, 16)).astype(np.float32)
+    feat_t = torch.from_numpy(f).to(torch.bfloat16).cuda()
+    feat = feat_t.float().cpu().numpy().astype(np.float64).reshape(G, G, G, 16)
+    out = torch.empty(16 * G ** 3, dtype=torch.bfloat16, device="cuda")
+    net.head_outputs(G, feat_t, out)
+    ref = OL.forward(_oracle_weights(w), feat)[-1]
+    got = out.float().cpu().numpy().reshape(G, G, G, 16)
+    # one bf16 rounding of the output (2^-9 relative) plus FP32 accumulation
+    tol = 4e-3 * np.abs(ref) + 1e-4 * np.abs(ref).max()
+    bad = np.abs(got - ref) > tol
+    assert not bad.any(), (int(bad.sum()), np.argwhere(bad)[:5])
+    assert np.abs(ref).max() > 0.5
 
 
 def test_block_couplings_and_block_jacobi_match_oracle():
