@@ -10,24 +10,26 @@
 // input channels, issued as 27 MMAs of K = 16 (kind::f16, bf16 operands,
 // FP32 accumulator in tensor memory).
 //
-// Operand staging: one TMA load per 8-channel half brings the tile's halo
-// (10 x 18 x 3 voxels, zero-filled outside the grid) into shared memory as
+// Operand staging: a CTA walks a column of output tiles in z (work item = 8
+// x 16 voxels x up to 16 slices) and keeps a ring of 4 halo planes (10 x 18
+// voxels each, z-1 .. z+2) in shared memory; each tile loads only the next
+// plane, one TMA load per 8-channel half (zero-filled outside the grid), as
 // rows of 16 bytes, x fastest.  In the no-swizzle K-major layout a core
 // matrix is 8 rows of 16 bytes, so the A operand of tap (dx, dy, dz) is the
-// halo itself seen from row (dz, dy, dx): eight consecutive x of one y-row
+// plane of z + dz seen from row (dy, dx): eight consecutive x of one y-row
 // form a core matrix, the next y-row is 10 rows (160 bytes) further (the
-// stride-dimension offset) and the second 8-channel half is the other plane
-// (the leading-dimension offset).  All 27 taps read the same 17 KB; no
-// operand is copied per tap.  Weights sit in shared memory in the same
-// layout (per tap: 2 planes x 16 rows x 16 bytes).
+// stride-dimension offset) and the second 8-channel half is the other
+// half-plane (the leading-dimension offset).  No operand is copied per tap.
+// Weights sit in shared memory in the same layout (per tap: 2 halves x 16
+// rows x 16 bytes).
 //
-// Pipeline (persistent CTAs, 4 warps): thread 0 issues the TMA loads of the
-// next tile into the other stage, waits for the current stage, issues the 27
-// MMAs and commits them to an mbarrier; all four warps then read their 32
-// accumulator lanes (one voxel per thread, 16 columns), add the bias, apply
-// the activation and store 32 bytes per voxel.  Every wait is bounded: on
-// timeout the kernel raises a device error flag, waits (bounded) for its
-// copies in flight, frees its tensor memory and returns.
+// Pipeline (persistent CTAs, 4 warps, 5 CTAs per SM): thread 0 issues the
+// TMA load of the plane the next tile needs, waits for the current tile's
+// planes, issues its 27 MMAs and commits them to an mbarrier; all four warps
+// then read their 32 accumulator lanes (one voxel per thread, 16 columns),
+// add the bias, apply the activation and store 32 bytes per voxel.  Every
+// wait is bounded: on timeout the kernel raises a device error flag, waits
+// (bounded) for its copies in flight, frees its tensor memory and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -42,17 +44,20 @@ namespace {
 constexpr int kCh = 16;
 constexpr int kNTaps = 27;
 constexpr int kTX = 8, kTY = 16;                   // output tile, one z-slice: M = 128
-constexpr int kHX = kTX + 2, kHY = kTY + 2, kHZ = 3;
-constexpr int kHalo = kHX * kHY * kHZ;              // 540 voxels
-constexpr int kHaloBytes = kHalo * 16;              // one 8-channel half: 8640 bytes
-constexpr int kPlane = (kHaloBytes + 127) / 128 * 128;   // 8704: 128-byte aligned planes
-constexpr int kStage = 2 * kPlane;                  // 17408 (17 x 1024)
+constexpr int kHX = kTX + 2, kHY = kTY + 2;         // its halo in x and y
+constexpr int kPlaneRows = kHX * kHY;               // 180 rows of 16 bytes per half-plane
+constexpr int kHalfBytes = kPlaneRows * 16;         // 2880
+constexpr int kHalf = (kHalfBytes + 127) / 128 * 128;   // 2944: 128-byte aligned halves
+constexpr int kPlaneBytes = 2 * kHalf;              // 5888: one z-plane of the halo
+constexpr int kRing = 4;                            // planes z-1, z, z+1 and the next
+constexpr int kZChunk = 16;                         // z-slices per work item
 constexpr int kWBytes = kNTaps * 512;               // 13824
-constexpr int kOffW = 2 * kStage;                   // 34816
-constexpr int kOffBar = kOffW + kWBytes;            // 48640
-constexpr int kSmemUsed = kOffBar + 64;
+constexpr int kOffW = kRing * kPlaneBytes;          // 23552
+constexpr int kOffBar = kOffW + kWBytes;            // 37376
+constexpr int kSmemUsed = kOffBar + 64;             // full[4], mma, tmem address, abort flag
 constexpr int kSmemDyn = kSmemUsed + 1024;          // room to align the base to 1024
 constexpr int kTCThreads = 128;
+constexpr int kCtasPerSm = 5;                       // 5 x 38.5 KB of shared memory
 constexpr int kTmemCols = 32;                       // smallest allocation; 16 used
 constexpr uint32_t kSpinLimit = 1u << 20;           // try_wait rounds before giving up
 
@@ -153,27 +158,23 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     return *reinterpret_cast<uint32_t*>(&h);
 }
 
-struct TileXYZ {
-    int x0, y0, z;
+struct Column {
+    int x0, y0, z_lo, z_hi;
 };
 
-__device__ __forceinline__ TileXYZ tile_coords(long long t, int nx, int ny) {
-    TileXYZ c;
+__device__ __forceinline__ Column item_coords(long long t, int nx, int ny, int G) {
+    Column c;
     const long long pl = (long long)nx * ny;
-    c.z = (int)(t / pl);
-    const int r = (int)(t - (long long)c.z * pl);
+    const int zc = (int)(t / pl);
+    const int r = (int)(t - (long long)zc * pl);
     c.y0 = (r / nx) * kTY;
     c.x0 = (r % nx) * kTX;
+    c.z_lo = zc * kZChunk;
+    c.z_hi = min(c.z_lo + kZChunk, G);
     return c;
 }
 
-// Both 8-channel halves of a tile's halo into one stage.
-__device__ __forceinline__ void load_tile(const CUtensorMap* map, uint32_t stage, uint32_t bar,
-                                          const TileXYZ& c) {
-    mbar_expect_tx(bar, 2u * kHaloBytes);
-    tma_load_5d(stage, map, bar, 0, 0, c.x0 - 1, c.y0 - 1, c.z - 1);
-    tma_load_5d(stage + kPlane, map, bar, 0, 1, c.x0 - 1, c.y0 - 1, c.z - 1);
-}
+__device__ __forceinline__ int ring_slot(int q) { return (q + kRing) & (kRing - 1); }   // q >= -1
 
 __global__ void __launch_bounds__(kTCThreads) k_conv_fwd_tc(const __grid_constant__ CUtensorMap in_map,
                                                             const __nv_bfloat16* __restrict__ W,
@@ -185,15 +186,14 @@ __global__ void __launch_bounds__(kTCThreads) k_conv_fwd_tc(const __grid_constan
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
     unsigned char* sm = smem_raw + pad;
     const uint32_t base = raw + pad;
-    const uint32_t bar_full[2] = {base + kOffBar, base + kOffBar + 8};
-    const uint32_t bar_mma = base + kOffBar + 16;
-    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 24);
-    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 28);
+    const uint32_t bar_full = base + kOffBar;   // + 8 slot
+    const uint32_t bar_mma = base + kOffBar + 8 * kRing;
+    uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(sm + kOffBar + 8 * kRing + 8);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(sm + kOffBar + 8 * kRing + 12);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
-        mbar_init(bar_full[0], 1);
-        mbar_init(bar_full[1], 1);
+        for (int q = 0; q < kRing; ++q) mbar_init(bar_full + 8 * q, 1);
         mbar_init(bar_mma, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -229,89 +229,110 @@ __global__ void __launch_bounds__(kTCThreads) k_conv_fwd_tc(const __grid_constan
     const uint32_t tmem = *tmem_slot;
 
     const int nx = (G + kTX - 1) / kTX, ny = (G + kTY - 1) / kTY;
-    const long long n_tiles = (long long)nx * ny * G;
+    const int nzc = (G + kZChunk - 1) / kZChunk;
+    const long long n_items = (long long)nx * ny * nzc;
     float bs[kCh];
 #pragma unroll
     for (int c = 0; c < kCh; ++c) bs[c] = bias ? bias[c] : 0.0f;
 
-    // thread 0's view of the two stages: a load in flight, and the parity of
-    // the stage barrier's next phase
-    bool inflight[2] = {false, false};
-    uint32_t phase[2] = {0u, 0u};
-    long long tile = blockIdx.x;
-    if (threadIdx.x == 0 && tile < n_tiles) {
-        load_tile(&in_map, base, bar_full[0], tile_coords(tile, nx, ny));
-        inflight[0] = true;
-    }
-    for (int it = 0; tile < n_tiles; tile += gridDim.x, ++it) {
-        const int s = it & 1;
-        const TileXYZ c = tile_coords(tile, nx, ny);
-        bool ok = true;
+    // thread 0: loads issued into / waits completed on each ring slot
+    int loaded[kRing], waited[kRing];
+#pragma unroll
+    for (int q = 0; q < kRing; ++q) loaded[q] = waited[q] = 0;
+    // both 8-channel halves of halo plane q (z = q) of the column into its slot
+    auto load_plane = [&](const Column& c, int q) {
+        const int sl = ring_slot(q);
+        const uint32_t dst = base + (uint32_t)(sl * kPlaneBytes);
+        mbar_expect_tx(bar_full + 8 * sl, 2u * kHalfBytes);
+        tma_load_5d(dst, &in_map, bar_full + 8 * sl, 0, 0, c.x0 - 1, c.y0 - 1, q);
+        tma_load_5d(dst + kHalf, &in_map, bar_full + 8 * sl, 0, 1, c.x0 - 1, c.y0 - 1, q);
+        ++loaded[sl];
+    };
+    auto wait_plane = [&](int q) -> bool {
+        const int sl = ring_slot(q);
+        const bool ok = mbar_wait(bar_full + 8 * sl, (uint32_t)waited[sl] & 1u);
+        if (ok) ++waited[sl];
+        return ok;
+    };
+
+    int it = 0;   // tiles processed by this CTA (phase of the MMA barrier)
+    for (long long item = blockIdx.x; item < n_items && !*abort_flag; item += gridDim.x) {
+        const Column c = item_coords(item, nx, ny, G);
         if (threadIdx.x == 0) {
-            // the other stage was last read by the previous tile's MMAs, which
-            // have completed: prefetch the next tile into it
-            const long long nxt = tile + gridDim.x;
-            if (nxt < n_tiles) {
-                load_tile(&in_map, base + (uint32_t)((s ^ 1) * kStage), bar_full[s ^ 1],
-                          tile_coords(nxt, nx, ny));
-                inflight[s ^ 1] = true;
-            }
-            ok = mbar_wait(bar_full[s], phase[s]);
-            if (ok) {
-                inflight[s] = false;
-                phase[s] ^= 1u;
-                tc_fence_after();
-                const uint32_t st = base + (uint32_t)(s * kStage);
-#pragma unroll 1
-                for (int tap = 0; tap < kNTaps; ++tap) {
-                    const int hx = tap % 3, hy = (tap / 3) % 3, hz = tap / 9;
-                    const uint64_t a = smem_desc(st + (uint32_t)((hz * kHY + hy) * kHX + hx) * 16u,
-                                                 kPlane, kHX * 16);
-                    const uint64_t b = smem_desc(base + kOffW + (uint32_t)tap * 512u, 256, 128);
-                    mma_f16(tmem, a, b, tap > 0 ? 1u : 0u);
+            load_plane(c, c.z_lo - 1);
+            load_plane(c, c.z_lo);
+            load_plane(c, c.z_lo + 1);
+        }
+        for (int z = c.z_lo; z < c.z_hi; ++z, ++it) {
+            bool ok = true;
+            if (threadIdx.x == 0) {
+                // plane z+2 serves the next tile; its slot held plane z-2,
+                // last read by the previous tile's MMAs, which have completed
+                if (z + 2 <= c.z_hi) load_plane(c, z + 2);
+                if (z == c.z_lo) ok = wait_plane(z - 1) && wait_plane(z);
+                ok = ok && wait_plane(z + 1);
+                if (ok) {
+                    tc_fence_after();
+                    // descriptors: constant high words; per tap only the start address moves
+                    const uint64_t a_hi = smem_desc(0u, kHalf, kHX * 16);
+                    const uint64_t b0 = smem_desc(base + kOffW, 256, 128);
+                    uint32_t pl[3];
+#pragma unroll
+                    for (int hz = 0; hz < 3; ++hz)
+                        pl[hz] = base + (uint32_t)(ring_slot(z - 1 + hz) * kPlaneBytes);
+#pragma unroll
+                    for (int tap = 0; tap < kNTaps; ++tap) {
+                        const int hx = tap % 3, hy = (tap / 3) % 3, hz = tap / 9;
+                        const uint64_t a = a_hi | (uint64_t)(((pl[hz] + (uint32_t)((hy * kHX + hx) * 16)) &
+                                                              0x3FFFFu) >> 4);
+                        mma_f16(tmem, a, b0 + (uint64_t)(tap * 32), tap > 0 ? 1u : 0u);
+                    }
+                    mma_commit(bar_mma);
+                } else {
+                    atomicExch(&g_conv_tc_error, 1);
+                    *abort_flag = 1;
                 }
-                mma_commit(bar_mma);
-            } else {
+            }
+            __syncwarp();
+            if (threadIdx.x != 0 || ok) ok = mbar_wait(bar_mma, (uint32_t)it & 1u);
+            if (!ok) {
                 atomicExch(&g_conv_tc_error, 1);
                 *abort_flag = 1;
             }
-        }
-        __syncwarp();
-        if (threadIdx.x != 0 || ok) ok = mbar_wait(bar_mma, (uint32_t)it & 1u);
-        if (!ok) {
-            atomicExch(&g_conv_tc_error, 1);
-            *abort_flag = 1;
-        }
-        // tcgen05.ld is warp-collective: the whole warp reads or none of it
-        ok = __all_sync(0xffffffffu, ok);
-        if (ok) {
-            tc_fence_after();
-            uint32_t r[16];
-            tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), r);
-            const int m = warp * 32 + lane;
-            const int x = c.x0 + (m & (kTX - 1)), y = c.y0 + (m >> 3);
-            if (x < G && y < G) {
-                float o[kCh];
+            // tcgen05.ld is warp-collective: the whole warp reads or none of it
+            ok = __all_sync(0xffffffffu, ok);
+            if (ok) {
+                tc_fence_after();
+                uint32_t r[16];
+                tmem_ld16(tmem + ((uint32_t)(warp * 32) << 16), r);
+                const int m = warp * 32 + lane;
+                const int x = c.x0 + (m & (kTX - 1)), y = c.y0 + (m >> 3);
+                if (x < G && y < G) {
+                    float o[kCh];
 #pragma unroll
-                for (int q = 0; q < kCh; ++q) {
-                    o[q] = __uint_as_float(r[q]) + bs[q];
-                    if (relu) o[q] = fmaxf(o[q], 0.0f);
+                    for (int q = 0; q < kCh; ++q) {
+                        o[q] = __uint_as_float(r[q]) + bs[q];
+                        if (relu) o[q] = fmaxf(o[q], 0.0f);
+                    }
+                    uint4* dst = reinterpret_cast<uint4*>(out + (((long long)z * G + y) * G + x) * kCh);
+                    dst[0] = make_uint4(pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
+                                        pack2(o[6], o[7]));
+                    dst[1] = make_uint4(pack2(o[8], o[9]), pack2(o[10], o[11]), pack2(o[12], o[13]),
+                                        pack2(o[14], o[15]));
                 }
-                uint4* dst = reinterpret_cast<uint4*>(out + (((long long)c.z * G + y) * G + x) * kCh);
-                dst[0] = make_uint4(pack2(o[0], o[1]), pack2(o[2], o[3]), pack2(o[4], o[5]),
-                                    pack2(o[6], o[7]));
-                dst[1] = make_uint4(pack2(o[8], o[9]), pack2(o[10], o[11]), pack2(o[12], o[13]),
-                                    pack2(o[14], o[15]));
             }
+            tc_fence_before();
+            __syncthreads();
+            if (*abort_flag) break;
         }
-        tc_fence_before();
-        __syncthreads();
-        if (*abort_flag) break;
     }
-    // error path: let loads still in flight land before the CTA exits
+    // error path: loads still in flight land before the CTA exits
     if (threadIdx.x == 0) {
-        for (int q = 0; q < 2; ++q)
-            if (inflight[q]) mbar_wait(bar_full[q], phase[q]);
+        for (int q = 0; q < kRing; ++q)
+            while (waited[q] < loaded[q]) {
+                if (!mbar_wait(bar_full + 8 * q, (uint32_t)waited[q] & 1u)) break;
+                ++waited[q];
+            }
     }
     tc_fence_before();
     __syncthreads();
@@ -352,7 +373,7 @@ cudaError_t lpc_conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* W, const 
     // in as (8 channels, 2 halves, x, y, z): byte strides of dims 1..4
     const cuuint64_t dims[5] = {8, 2, (cuuint64_t)G, (cuuint64_t)G, (cuuint64_t)G};
     const cuuint64_t strides[4] = {16, 32, 32ull * G, 32ull * G * G};
-    const cuuint32_t box[5] = {8, 1, kHX, kHY, kHZ};
+    const cuuint32_t box[5] = {8, 1, kHX, kHY, 1};   // one z-plane of a column's halo
     const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
     CUtensorMap map;
     const CUresult r = enc(&map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(in),
@@ -373,9 +394,9 @@ cudaError_t lpc_conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* W, const 
         attr = true;
     }
     const long long nx = (G + kTX - 1) / kTX, ny = (G + kTY - 1) / kTY;
-    const long long tiles = nx * ny * G;
-    const long long cap = (long long)sms * 4;
-    const int grid = (int)(tiles < cap ? tiles : cap);
+    const long long items = nx * ny * ((G + kZChunk - 1) / kZChunk);
+    const long long cap = (long long)sms * kCtasPerSm;
+    const int grid = (int)(items < cap ? items : cap);
     k_conv_fwd_tc<<<grid, kTCThreads, kSmemDyn, st>>>(map, W, bias, out, G, relu);
     count_launch();
     return cudaGetLastError();
