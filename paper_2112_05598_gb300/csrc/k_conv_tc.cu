@@ -381,18 +381,15 @@ cudaError_t lpc_conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* W, const 
                            CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-    static int sms = 0;
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             kSmemDyn);
-        if (e != cudaSuccess) return e;
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-        attr = true;
-    }
+    // per call: the current device may differ between calls
+    cudaError_t e = cudaFuncSetAttribute(k_conv_fwd_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         kSmemDyn);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0;
+    e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    if (sms <= 0) sms = 1;
     const long long nx = (G + kTX - 1) / kTX, ny = (G + kTY - 1) / kTY;
     const long long items = nx * ny * ((G + kZChunk - 1) / kZChunk);
     const long long cap = (long long)sms * kCtasPerSm;
