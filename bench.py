@@ -123,6 +123,9 @@ def parse():
     ap.add_argument("--lpc-gn", type=int, default=6)
     ap.add_argument("--lpc-pcg", type=int, default=5)
     ap.add_argument("--lpc-traj", type=int, default=60)
+    ap.add_argument("--coef-budget", type=int, default=-1,
+                    help="bytes for the coefficient store (-1: free memory - 6 GiB; 0: off, every "
+                         "A p recomputes)")
     ap.add_argument("--conv", type=int, default=0,
                     help="time the learned preconditioner's 4-layer network on a G^3 grid")
     return ap.parse_args()
@@ -702,6 +705,8 @@ def run_ours(args, rank, world, local):
     sdt = torch.bfloat16 if bf else torch.float32
     ctx = Context.from_scene(sc, dtype=PERF_BF16 if bf else PERF_F32, pcg_iters=cfg.pcg_iters,
                              pcg_fixed=1)
+    if args.coef_budget != -1:
+        ctx.set_coef_budget(args.coef_budget)
     stream = torch.cuda.current_stream()
     x_gt = torch.from_numpy(sc.x_gt).to(dev).to(sdt)
     target = torch.empty(3 * ctx.n_rays, device=dev)
