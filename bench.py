@@ -12,6 +12,13 @@ larger than L2, so every step streams them from HBM.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
+The JSON line's roofline object measures the dominant kernel (A p) against
+HBM (algorithmic bytes per launch / CUDA-event time, with the DRAM traffic
+of an ncu capture while the sources match it) and, under "atomics", against
+the 16-byte vector-atomic throughput the library's microbenchmark measures
+in the same process (its lane operations counted on one extra, untimed
+Gauss-Newton step).
+
 With N > 1 (torchrun) every rank runs an independent replica of the
 workload (the single-scene step has no exchange to shard without a
 collective); value = all ranks' PCG iterations / max-over-ranks time.
@@ -773,6 +780,19 @@ def run_ours(args, rank, world, local):
     ms_e2e = max_over_ranks(e0.elapsed_time(e1), world)
     e2e_value = sum_over_ranks(float(e2e_pcg), world) / (ms_e2e / 1000.0)
 
+    # the scatter's vector-atomic lane operations per A p, counted on one
+    # extra Gauss-Newton step with 2 PCG iterations (outside every timed
+    # region), against the library's atomic microbenchmark
+    from paper_2112_05598_gb300 import measure_atomic_peak
+    red_cnt = torch.zeros(1, dtype=torch.int64, device=dev)
+    ctx.set_atomic_counter(red_cnt)
+    ctx.set_options(pcg_iters=2)
+    st = ctx.gn_solve(x.clone(), target, 1)
+    ctx.set_atomic_counter(None)
+    ctx.set_options(pcg_iters=cfg.pcg_iters)
+    red_per_apply = float(red_cnt.item()) / max(sum(s["pcg_iters"] for s in st), 1)
+    red_peak = measure_atomic_peak()
+
     peaks, peak_src = measured_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
@@ -804,6 +824,15 @@ def run_ours(args, rank, world, local):
                                f"(max SM clock, {peak_src})"}
     roof["traffic"] = recorded_traffic(apply_kernel, args.workload) if args.cams is None else None
     roof["kernel"] = apply_kernel
+    # the unit that bounds A p: 16-byte vector atomics, one lane operation per
+    # active lane of each atomic instruction
+    # per PCG iteration (a partial coefficient store splits one A p in two launches)
+    apply_s_per_iter = tm["apply"]["ms"] / 1000.0 / max(sum(s["pcg_iters"] for s in stats), 1)
+    red_rate = red_per_apply / apply_s_per_iter
+    roof["atomics"] = {"lane_ops_per_apply": red_per_apply, "achieved": red_rate,
+                       "peak": red_peak, "unit": "lane-ops/s", "frac": red_rate / red_peak,
+                       "peak_source": "perf_measure_atomic_peak (16-byte vector atomic "
+                                      "microbenchmark on this GPU, measured in this run)"}
 
     if rank != 0:
         return

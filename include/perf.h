@@ -283,6 +283,22 @@ uint64_t perf_launch_count(void);
 /* *out (HOST; synchronises) = grid samples + shell hits of one march over all
  * rays of the context (the units of work of every ray-march kernel). */
 perf_status perf_sample_count(perf_ctx* ctx, uint64_t* out, void* stream);
+/* Counting the J^T scatter's vector atomics (instrumentation, off by
+ * default).  With device_counter set (DEVICE uint64, zeroed by the caller;
+ * NULL turns counting off), every later J^T v and A p launch of this context
+ * (perf_vjp, perf_apply_normal, the PCG of perf_pcg_step / perf_gn_solve)
+ * adds to *device_counter the 16-byte vector-atomic lane operations its
+ * window flushes issue -- one per active lane of each atomic instruction,
+ * the unit of work that bounds A p (the diagonal march is not counted).
+ * While on, each flush instruction also costs a warp vote and one atomic. */
+perf_status perf_set_atomic_counter(perf_ctx* ctx, uint64_t* device_counter);
+/* *lane_ops_per_s (HOST) = the best rate of 16-byte global vector atomic
+ * adds (red.global.add.v4.f32) a plain microbenchmark reaches on the current
+ * device: 1216 CTAs x 256 threads, 200 atomics per lane, all lanes active,
+ * 1, 4 or 32 distinct addresses per warp instruction (best of the three,
+ * each timed after one warm-up run).  Allocates and frees 256 MiB of device
+ * memory; synchronises the device. */
+perf_status perf_measure_atomic_peak(double* lane_ops_per_s);
 perf_status perf_get_timing(perf_ctx* ctx, perf_timing* out, int32_t reset);
 
 /* ------------------------------------------------------------------------

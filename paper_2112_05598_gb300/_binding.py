@@ -97,6 +97,8 @@ _SIGS = {
     "perf_enable_timing": [_VP, ctypes.c_int32],
     "perf_get_timing": [_VP, ctypes.POINTER(Timing), ctypes.c_int32],
     "perf_sample_count": [_VP, ctypes.POINTER(ctypes.c_uint64), _VP],
+    "perf_set_atomic_counter": [_VP, _VP],
+    "perf_measure_atomic_peak": [ctypes.POINTER(ctypes.c_double)],
     "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
     "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_set_coef_budget": [_VP, ctypes.c_int64],
@@ -217,6 +219,16 @@ def residual_noalloc(G, radii, env_h, env_w, c2w, focal, width, height, x, targe
 def launch_count() -> int:
     """Kernels launched by libperf in this process so far."""
     return int(load_library().perf_launch_count())
+
+
+def measure_atomic_peak() -> float:
+    """Best rate (lane operations/s) of 16-byte global vector atomic adds on
+    the current device, from the library's microbenchmark (synchronises)."""
+    v = ctypes.c_double(0.0)
+    st = load_library().perf_measure_atomic_peak(ctypes.byref(v))
+    if st != 0:
+        raise PerfError(st, "perf_measure_atomic_peak failed")
+    return float(v.value)
 
 
 def default_options(**kw) -> Options:
@@ -389,6 +401,14 @@ class Context:
     def diag_cross(self, x, diag_out, cross_out, stream=None):
         self._check(self.lib.perf_diag_cross(self.h, _ptr(x), _ptr(diag_out), _ptr(cross_out),
                                              _stream(stream)), "diag_cross")
+
+    def set_atomic_counter(self, counter=None):
+        """Count the J^T scatter's vector-atomic lane operations into a
+        zeroed int64 device tensor of one element (None: stop counting)."""
+        if counter is not None:
+            assert counter.is_cuda and counter.numel() >= 1 and counter.element_size() == 8
+        self._check(self.lib.perf_set_atomic_counter(self.h, _ptr(counter) if counter is not None
+                                                     else None), "set_atomic_counter")
 
     def sample_count(self, stream=None):
         n = ctypes.c_uint64(0)

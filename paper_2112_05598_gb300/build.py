@@ -18,8 +18,8 @@ BUILD = os.path.join(HERE, "_build", platform.machine())
 LIB = os.path.join(HERE, "libperf.so")
 STAMP = LIB + ".arch"
 
-SOURCES = ["k_march.cu", "k_pcg.cu", "k_lpc.cu", "k_conv_tc.cu", "k_hier.cu", "perf_api.cu",
-           "perf_batch.cu", "perf_lpc.cu", "perf_noalloc.cu"]
+SOURCES = ["k_march.cu", "k_pcg.cu", "k_lpc.cu", "k_conv_tc.cu", "k_hier.cu", "k_atomic_peak.cu",
+           "perf_api.cu", "perf_batch.cu", "perf_lpc.cu", "perf_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -274,15 +274,23 @@ struct CanonKey {
 };
 
 // VJP sink: slot = (a, s) with a = sum W w_i and s = sum W v.dH/dsigma_i;
-// the parameter block receives (a v_0, a v_1, a v_2, s).
-template <class Key>
+// the parameter block receives (a v_0, a v_1, a v_2, s).  put() is called by
+// all 32 lanes of a warp together; with cnt set (instrumentation) it also
+// counts the vector-atomic lane operations it issues (COUNT: a separate
+// instantiation, so that the timed kernels carry no trace of it).
+template <class Key, bool COUNT = false>
 struct VjpSink {
     float* out;
     float v0, v1, v2;
     Key km;
+    unsigned long long* cnt;
     __device__ __forceinline__ void put(bool ev, int key, const float (&a)[2]) {
-        if (ev && (a[0] != 0.0f || a[1] != 0.0f))
-            red_add4(out, key, make_float4(a[0] * v0, a[0] * v1, a[0] * v2, a[1]));
+        const bool red = ev && (a[0] != 0.0f || a[1] != 0.0f);
+        if constexpr (COUNT) {
+            const unsigned b = __ballot_sync(kFull, red);
+            if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, (unsigned long long)__popc(b));
+        }
+        if (red) red_add4(out, key, make_float4(a[0] * v0, a[0] * v1, a[0] * v2, a[1]));
     }
 };
 
@@ -509,7 +517,8 @@ __device__ __forceinline__ void forward_tile(const DevScene& sc, const T* __rest
 }
 
 // All 32 lanes call it (the back-to-front sweep is warp-synchronous).
-template <typename T, typename TP, int MODE, typename TV>   // 0 vjp, 1 apply A, 2 diag (+grad)
+template <typename T, typename TP, int MODE, typename TV,   // 0 vjp, 1 apply A, 2 diag (+grad)
+          bool COUNT = false>
 __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __restrict__ x,
                                              const TP* __restrict__ p, const TV* __restrict__ v,
                                              float* __restrict__ out, float* __restrict__ out2,
@@ -570,7 +579,7 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
         DiagSink<4> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}, 0.0f};
         backward_sweep<4>(sc, x, R, ray, act, V, vr, sk, crow);
     } else {
-        VjpSink<CanonKey> sk{out, vr[0], vr[1], vr[2], CanonKey{sc.G}};
+        VjpSink<CanonKey, COUNT> sk{out, vr[0], vr[1], vr[2], CanonKey{sc.G}, sc.red_count};
         backward_sweep<2>(sc, x, R, ray, act, V, vr, sk, nullptr, va * kap);
     }
 }
@@ -616,7 +625,7 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
     }
 }
 
-template <typename T, typename TP, int MODE, typename TV>
+template <typename T, typename TP, int MODE, typename TV, bool COUNT = false>
 __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PERF_MIN_CTAS)
     k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
@@ -628,8 +637,8 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
                                                       const long long* __restrict__ tile_off) {
     double acc = 0.0;
     PERF_TILE_LOOP {
-        scatter_tile<T, TP, MODE, TV>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
-                                      tile_off, sc.coef_tiles);
+        scatter_tile<T, TP, MODE, TV, COUNT>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
+                                             tile_off, sc.coef_tiles);
     }
     if (MODE == 1 && pap) block_add_f64<kWarps>(acc, pap);
 }
@@ -665,7 +674,7 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) 
     }
 }
 
-template <typename TP>
+template <typename TP, bool COUNT = false>
 __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __restrict__ p,
                                                 const float4* __restrict__ coef,
                                                 const long long* __restrict__ tile_off,
@@ -711,7 +720,7 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
     }
     const float aux_v = Ja * kap;   // v_aux dL/dsigma per unit interpolation weight
     // J^T (J p): the scatter of Algorithm 1 with v = J p
-    VjpSink<CanonKey> sk{out, J[0], J[1], J[2], CanonKey{sc.G}};
+    VjpSink<CanonKey, COUNT> sk{out, J[0], J[1], J[2], CanonKey{sc.G}, sc.red_count};
     for (int s = sc.S - 1; s >= 0; --s) {
         ShellHit hs;
         const bool hit = act && shell_lookup(sc, R, s, hs);
@@ -756,12 +765,12 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
                w.v[q]);
 }
 
-template <typename TP>
+template <typename TP, bool COUNT = false>
 __global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
     k_apply_coef(DevScene sc, const TP* __restrict__ p, const float4* __restrict__ coef,
                  const long long* __restrict__ tile_off, float* __restrict__ out, double* pap) {
     double acc = 0.0;
-    PERF_TILE_LOOP { coef_apply_tile<TP>(sc, p, coef, tile_off, out, tile, lane, acc); }
+    PERF_TILE_LOOP { coef_apply_tile<TP, COUNT>(sc, p, coef, tile_off, out, tile, lane, acc); }
     if (pap) block_add_f64<kWarps>(acc, pap);
 }
 
@@ -1023,7 +1032,10 @@ cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, c
                              float* out3 = nullptr, float* coef = nullptr,
                              const long long* tile_off = nullptr) {
     if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
-    auto fn = k_scatter<T, TP, MODE, TV>;
+    auto fn = k_scatter<T, TP, MODE, TV, false>;
+    if constexpr (MODE == 1) {   // A p: the counting instantiation when instrumented
+        if (sc.red_count) fn = k_scatter<T, TP, MODE, TV, true>;
+    }
     fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
         out2, out3, pap, reinterpret_cast<float4*>(coef), tile_off);
@@ -1069,7 +1081,7 @@ cudaError_t launch_apply_coef_t(const DevScene& sc, const void* p, const float* 
                                 const long long* tile_off, float* out, double* pap,
                                 cudaStream_t st) {
     if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
-    auto fn = k_apply_coef<TP>;
+    auto fn = sc.red_count ? k_apply_coef<TP, true> : k_apply_coef<TP, false>;
     fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const TP*>(p), reinterpret_cast<const float4*>(coef), tile_off, out, pap);
     count_launch();

@@ -938,6 +938,12 @@ perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_use
 
 uint64_t perf_launch_count(void) { return (uint64_t)__atomic_load_n(&perf::g_launches, __ATOMIC_RELAXED); }
 
+perf_status perf_set_atomic_counter(perf_ctx* ctx, uint64_t* device_counter) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    ctx->ds.red_count = reinterpret_cast<unsigned long long*>(device_counter);
+    return PERF_OK;
+}
+
 perf_status perf_render_threshold(perf_ctx* ctx, const void* x, float min_opacity,
                                   float* rgb_out, float* T_out, void* stream) {
     if (!ctx) return PERF_ERR_INVALID_ARG;

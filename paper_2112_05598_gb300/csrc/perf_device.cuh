@@ -48,6 +48,7 @@ struct DevScene {
     float aux_lambda;
     long long tile_lo;       // a launch processes tiles [tile_lo, n_tiles)
     long long coef_tiles;    // tiles [0, coef_tiles) have rows in the coefficient store
+    unsigned long long* red_count;   // non-null: count the J^T scatter's vector-atomic lane operations
 };
 
 struct Ray {
