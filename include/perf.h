@@ -283,14 +283,17 @@ uint64_t perf_launch_count(void);
 /* *out (HOST; synchronises) = grid samples + shell hits of one march over all
  * rays of the context (the units of work of every ray-march kernel). */
 perf_status perf_sample_count(perf_ctx* ctx, uint64_t* out, void* stream);
-/* Counting the J^T scatter's vector atomics (instrumentation, off by
+/* Counting the A p scatter's vector atomics (instrumentation, off by
  * default).  With device_counter set (DEVICE uint64, zeroed by the caller;
- * NULL turns counting off), every later J^T v and A p launch of this context
- * (perf_vjp, perf_apply_normal, the PCG of perf_pcg_step / perf_gn_solve)
- * adds to *device_counter the 16-byte vector-atomic lane operations its
- * window flushes issue -- one per active lane of each atomic instruction,
- * the unit of work that bounds A p (the diagonal march is not counted).
- * While on, each flush instruction also costs a warp vote and one atomic. */
+ * NULL turns counting off), every later A p launch of this context
+ * (perf_apply_normal and the PCG of perf_pcg_step / perf_gn_solve, from the
+ * coefficient store or recomputed) adds to *device_counter the 16-byte
+ * vector-atomic lane operations its window flushes issue -- one per active
+ * lane of each atomic instruction, the unit of work that bounds A p.  J^T v
+ * alone, the diagonal march and the batched forms are not counted.  While
+ * on, A p runs a separate instantiation that also votes and counts once per
+ * flush instruction (several times slower); the default kernels are
+ * unchanged. */
 perf_status perf_set_atomic_counter(perf_ctx* ctx, uint64_t* device_counter);
 /* *lane_ops_per_s (HOST) = the best rate of 16-byte global vector atomic
  * adds (red.global.add.v4.f32) a plain microbenchmark reaches on the current
