@@ -15,7 +15,7 @@ from typing import List
 
 import numpy as np
 
-from ._binding import LPC, Context, dscale, PERF_PRECOND_BLOCK4, PERF_PRECOND_JACOBI
+from ._binding import LPC, Context, dscale
 
 
 @dataclasses.dataclass

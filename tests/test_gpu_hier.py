@@ -41,7 +41,6 @@ def test_coarse_to_fine_driver_against_oracle():
     The first step of every level is checked against the oracle from the
     oracle's own level change of the previous level's result (parameters
     within the Gauss-Newton tolerance), and every level lowers F."""
-    import torch
     from oracle import Oracle, gn_step
     from oracle.hierarchy import upsample as ref_upsample
     from paper_2112_05598_gb300.hierarchy import coarse_to_fine, level_shapes
