@@ -1,0 +1,55 @@
+"""Host logic of bench.py's measurement records: the kernel-source hash that
+decides whether an ncu traffic record still applies, and the record parser."""
+import os
+import shutil
+
+import bench
+
+
+def _copy_sources(tmp_path, edit=None):
+    root = tmp_path / "repo"
+    for rel in bench.KERNEL_SOURCES:
+        dst = root / rel
+        dst.parent.mkdir(parents=True, exist_ok=True)
+        shutil.copy(os.path.join(bench.ROOT, rel), dst)
+        if edit:
+            dst.write_text(edit(dst.read_text()))
+    return str(root)
+
+
+def _hash_at(monkeypatch, root):
+    monkeypatch.setattr(bench, "ROOT", root)
+    return bench.kernel_source_hash()
+
+
+def test_hash_ignores_comments_and_whitespace(tmp_path, monkeypatch):
+    base = _hash_at(monkeypatch, _copy_sources(tmp_path / "a"))
+    commented = _copy_sources(
+        tmp_path / "b", lambda s: "// a new comment\n/* and a block\n comment */\n" +
+        s.replace("\n", "\n\n", 3))
+    assert _hash_at(monkeypatch, commented) == base
+
+
+def test_hash_changes_with_the_code(tmp_path, monkeypatch):
+    base = _hash_at(monkeypatch, _copy_sources(tmp_path / "a"))
+    changed = _copy_sources(tmp_path / "b", lambda s: s + "\nstatic int changed_code = 1;\n")
+    assert _hash_at(monkeypatch, changed) != base
+
+
+def test_traffic_record_parses_and_names_its_kernel(tmp_path, monkeypatch):
+    # a record is used only for its own kernel and workload
+    assert bench.recorded_traffic("some other kernel", "scale128") is None
+    assert bench.recorded_traffic("k_apply_coef<float> (A p from stored coefficients)",
+                                  "another workload") is None
+    text = open(bench.TRAFFIC_PROFILE).read()
+    for key in ("- kernel:", "- workload:", "- source_sha256:", "- dram_bytes_per_launch:"):
+        assert key in text
+    # with the kernel sources of the record, the recorded bytes come back
+    rec = tmp_path / "rec.md"
+    rec.write_text("- kernel: `K`\n- workload: `W`\n"
+                   f"- source_sha256: `{bench.kernel_source_hash()}`\n"
+                   "- dram_bytes_per_launch: `1234`\n")
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(rec))
+    assert bench.recorded_traffic("K", "W") == 1234
+    rec.write_text(rec.read_text().replace(bench.kernel_source_hash(), "0" * 64))
+    assert bench.recorded_traffic("K", "W") is None
