@@ -757,9 +757,8 @@ static void set_tiling(perf_ctx* ctx, int tw) {
     d.n_tiles = ctx->n_rays > 0 ? (long long)d.tiles_x * d.tiles_y * d.n_cams : 0;
 }
 
-perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
-                          void* stream) {
-    if (!ctx || !x) return PERF_ERR_INVALID_ARG;
+static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
+                                 void* stream) {
     cudaStream_t st = S(stream);
     perf_status ps = ensure_pcg(ctx);
     if (ps != PERF_OK) return ps;
@@ -882,6 +881,18 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
         out->coef = 0;
     }
     return PERF_OK;
+}
+
+perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
+                          void* stream) {
+    if (!ctx || !x) return PERF_ERR_INVALID_ARG;
+    // time the kernels the solver runs: the atomic-counting instantiation is
+    // several times slower and would skew the choice
+    unsigned long long* counter = ctx->ds.red_count;
+    ctx->ds.red_count = nullptr;
+    const perf_status ps = autotune_impl(ctx, x, p, out, stream);
+    ctx->ds.red_count = counter;
+    return ps;
 }
 
 perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_block) {
