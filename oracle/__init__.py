@@ -5,7 +5,7 @@ of the benchmark use it to check the CUDA library; the library never imports,
 links or calls it.  It shares no code with the CUDA path -- only the seeded
 inputs of ``scenegen`` serve both.
 
-The per-ray work (Eq. 3-4 ray march, Algorithm 1 partial derivatives, J p,
+The per-ray work (Eq. 3-4 ray march, the partial derivatives of Eq. 3, J p,
 J^T v, exact diag(J^T J)) is plain C in ``oracle.c``; this module adds
 
 * Algorithm 2 (Jacobi-preconditioned conjugate gradients) on
@@ -161,7 +161,7 @@ class Oracle:
     def error(self, x, target):
         return self.residual(x, target)[1]
 
-    # -- derivatives (Algorithm 1)
+    # -- derivatives of Eq. 3 (Section "Computation of partial derivatives")
     def jvp(self, x, p, ids=None):
         x = self._x(x)
         p = self._x(p)
@@ -182,7 +182,7 @@ class Oracle:
         return out
 
     def apply_A(self, x, p):
-        """A p = J^T (J p): Algorithm 1 invoked twice (Section "Update step")."""
+        """A p = J^T (J p), the product the PCG of Section "Update step" needs."""
         return self.vjp(x, self.jvp(x, p))
 
     def diag_grad(self, x, r=None):

@@ -10,17 +10,15 @@
  *     by the environment-map shells intersected in order from the grid exit
  *     outwards (Section "Volume Rendering", Section "Rendering");
  *   - residuals r = H^ - C and the objective of Eq. 5-6;
- *   - the analytic partial derivatives of Eq. 3 by Algorithm 1 (backward
- *     traversal with the two auxiliaries V and G), chained through the
- *     trilinear / bilinear interpolation weights;
+ *   - the analytic partial derivatives of Eq. 3 (dH/dc_i and dH/dsigma_i,
+ *     Section "Computation of partial derivatives"), written out from their
+ *     definition with prefix transmittances and tail sums, chained through
+ *     the trilinear / bilinear interpolation weights;
  *   - J p, J^T v and the exact diag(J^T J) of Section "Preconditioner"
  *     together with the gradient J^T r.
  *
  * Readings of the paper taken here (each is listed with its reason in the
  * design notes of the repository):
- *   - V in Algorithm 1 is the optical depth sum sigma_i delta_i (the paper
- *     initialises it with an exponential but subtracts sigma_i delta_i and
- *     exponentiates it afterwards); e^{-V} is then the transmittance T_i.
  *   - delta is measured in voxel sides (delta_bar = delta / h), so sigma is an
  *     opacity per voxel side; a shell hit counts as one sample with
  *     delta_bar = 1.
@@ -286,23 +284,43 @@ static void oc_composite(const oc_sample* s, int n, int n_grid, double H[3],
     *T_final = T;
 }
 
-/* Algorithm 1: backward traversal with the optical depth V and the colour
- * accumulator G.  dHdc[i] is dH/dc_i (same for the three channels),
- * dHds[3*i + k] is dH_k/dsigma_i. */
+/* Partial derivatives of Eq. 3, written out from the definition (Section
+ * "Computation of partial derivatives" states the same quantities; this is
+ * not its recurrence).  With s_i = sigma_i dbar_i,
+ *   T_i = exp(-sum_{j<i} s_j)          (transmittance in front of sample i)
+ *   w_i = T_i (1 - e^{-s_i})           (its weight in H^)
+ *   H^  = sum_i w_i c_i.
+ * c_i enters only term i:            dH/dc_i = w_i.
+ * sigma_i enters term i through 1 - e^{-s_i} (derivative dbar_i e^{-s_i})
+ * and every later term j > i through T_j (dT_j/dsigma_i = -dbar_i T_j):
+ *   dH_k/dsigma_i = dbar_i (T_i e^{-s_i} c_ik - sum_{j>i} w_j c_jk).
+ * T_i is formed from its prefix sum of optical depth, and the tail sums
+ * sum_{j>i} w_j c_j from the array of all weights, each on its own.
+ * dHdc[i] = dH/dc_i (same for the three channels), dHds[3 i + k] =
+ * dH_k/dsigma_i. */
 static void oc_partials(const oc_sample* s, int n, double* dHdc, double* dHds) {
-    double V = 0.0;
-    for (int i = 0; i < n; ++i) V += s[i].sigma * s[i].dbar;
-    double G[3] = {0.0, 0.0, 0.0};
-    for (int i = n - 1; i >= 0; --i) {
-        const double sd = s[i].sigma * s[i].dbar;
-        V = V - sd;
-        const double eV = exp(-V);
-        const double e = exp(-sd);
-        dHdc[i] = eV * (1.0 - e);
-        for (int k = 0; k < 3; ++k)
-            dHds[3 * i + k] = eV * s[i].dbar * e * s[i].c[k] - s[i].dbar * G[k];
-        for (int k = 0; k < 3; ++k) G[k] += eV * (1.0 - e) * s[i].c[k];
+    double* T = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+    double* w = (double*)malloc(sizeof(double) * (size_t)(n + 1));
+    double* tail = (double*)malloc(sizeof(double) * 3 * (size_t)(n + 1));
+    double depth = 0.0;                      /* sum_{j<i} s_j */
+    for (int i = 0; i < n; ++i) {
+        const double si = s[i].sigma * s[i].dbar;
+        T[i] = exp(-depth);
+        w[i] = T[i] * -expm1(-si);
+        depth += si;
     }
+    /* tail[3 i + k] = sum_{j > i} w_j c_jk */
+    for (int k = 0; k < 3; ++k) tail[3 * (n > 0 ? n - 1 : 0) + k] = 0.0;
+    for (int i = n - 2; i >= 0; --i)
+        for (int k = 0; k < 3; ++k)
+            tail[3 * i + k] = tail[3 * (i + 1) + k] + w[i + 1] * s[i + 1].c[k];
+    for (int i = 0; i < n; ++i) {
+        const double si = s[i].sigma * s[i].dbar;
+        dHdc[i] = w[i];
+        for (int k = 0; k < 3; ++k)
+            dHds[3 * i + k] = s[i].dbar * (T[i] * exp(-si) * s[i].c[k] - tail[3 * i + k]);
+    }
+    free(T); free(w); free(tail);
 }
 
 static int oc_nthreads(const oc_problem* P) {
@@ -406,7 +424,7 @@ int oc_residual(const oc_problem* P, const double* x, const double* target,
 }
 
 /* (J p) for the listed rays: sum over samples and interpolation corners of
- * dH/dx_j p_j, with the partials of Algorithm 1. */
+ * dH/dx_j p_j, with the partials of Eq. 3 (oc_partials). */
 int oc_jvp(const oc_problem* P, const double* x, const double* p, const int64_t* ids,
            int64_t n_ids, double* out) {
     const int64_t N = ids ? n_ids : oc_n_rays(P);
