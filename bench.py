@@ -41,32 +41,44 @@ import numpy as np
 WORKLOAD = "scale128"
 METRIC = "PCG iters/s"
 
-# Algorithmic work of one recomputing A p launch (fused J p and J^T (J p)),
-# per ray-march sample, with one 4-channel trilinear interpolation counted as
-# 7 lerps x 4 channels x 2 FLOP = 56: optical-depth sweep = one interpolation
-# of x + 7 FLOP of compensated summation (63); J p sweep (Algorithm 1's
-# recurrence) = interpolations of x and p (112) + 27 FLOP of Algorithm 1
-# partials + 12 FLOP of the J p update (151); adjoint sweep = one
-# interpolation of x (56) + 12 FLOP of corner weights + 27 FLOP of partials +
-# 32 FLOP accumulating the (w_i, v.dH/dsigma_i) pair into the 8 corners +
-# 4 FLOP scaling the flushed colour entries by v (131).  Total 345 FLOP per
-# sample (exponentials are special-function work, not FLOP).
-FLOP_PER_SAMPLE_APPLY = 345
-
-# The coefficient-cached A p streams the per-sample coefficients (16 bytes,
-# stored by the step's diagonal march) twice per launch -- the J p sweep and
-# the J^T (J p) sweep -- and otherwise touches p (gathers) and A p (vector
-# atomics), both L2-resident: its algorithmic HBM bytes per launch are
-# 32 per sample or shell hit plus p read once and A p written once (8 bytes
-# per parameter).  Its arithmetic is 207 FLOP per sample (interpolation of p
-# with corner weights 116, J p update 12, corner weights and accumulation of
-# the scatter window 44, v.dH/dsigma 6, flushed colour entries scaled by v
-# 14 on average, shells and per-ray work not counted).
-COEF_BYTES_PER_SAMPLE = 32
+# The method's algorithmic work per ray-march sample of one A p (the fused
+# J p and J^T (J p) of a PCG iteration), as the scope of the hot path counts
+# it: trilinear interpolation of x and p (64 FMA), the compositing weights
+# and Algorithm 1's recurrence, and the 32-element scatter products -- about
+# 200 FP32 FLOP per sample (exponentials are special-function work, not
+# FLOP).  The A p roofline is this work per launch over the launch's time,
+# against the FP32 peak (SMs x 128 lanes x 2 FLOP x max SM clock).
+FLOP_PER_SAMPLE_METHOD = 200
+# What each A p implementation executes per sample (reported beside it):
+# the recomputing march runs an optical-depth sweep, the J p sweep and the
+# adjoint sweep (345 FLOP: four 4-channel interpolations at 56, compensated
+# depth, Algorithm 1 partials twice, window accumulation); the coefficient-
+# cached A p streams stored partials instead (207 FLOP: interpolation of p
+# with corner weights 116, J p update 12, window weights and accumulation 44,
+# v.dH/dsigma 6, flushed colour entries scaled by v 14 on average).
+FLOP_PER_SAMPLE_RECOMPUTE = 345
 FLOP_PER_SAMPLE_COEF = 207
+# Compulsory HBM bytes of one A p: read x and p, zero and flush A p -- four
+# n-vector passes of 4 bytes (16 bytes per parameter).
+APPLY_COMPULSORY_BYTES_PER_PARAM = 16
+# Design traffic of the coefficient-cached A p: the per-sample coefficients
+# (16 bytes, stored by the step's diagonal march) streamed twice per launch,
+# plus p read once and A p written once (8 bytes per parameter).
+COEF_BYTES_PER_SAMPLE = 32
+# PCG vector kernels per iteration: update reads p, A p, Delta, rho, d (20 B)
+# and writes Delta, rho, A p = 0 (12 B); direction reads rho, d, p (12 B) and
+# writes p (4 B): 48 bytes per parameter (+2 for the BF16 copy of p, +4 for
+# the p half of the paired records).  The scope's count for the fused vector
+# work is 11 n-vector passes of 4 bytes (44 bytes per parameter).
+VEC_BYTES_PER_PARAM = 48
+VEC_COMPULSORY_BYTES_PER_PARAM = 44
+# The residual pass streams the targets C in and the residuals r out: 12 + 12
+# bytes per ray in FP32 (6 + 6 in BF16); its ray march gathers x from L2.
+RESIDUAL_BYTES_PER_RAY_F32 = 24
 
 # DRAM traffic of one A p launch, from the ncu capture summarised in this
-# file; it applies only while the kernel sources hash to the recorded value.
+# file (a small case, scaled to a full launch by its sample count); it applies
+# only while the kernel sources hash to the recorded value.
 TRAFFIC_PROFILE = os.path.join(ROOT, "profiles", "apply_coef_traffic_scale128.md")
 KERNEL_SOURCES = ("paper_2112_05598_gb300/csrc/k_march.cu",
                   "paper_2112_05598_gb300/csrc/perf_device.cuh")
@@ -87,9 +99,11 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(kernel, workload):
-    """Bytes per launch recorded for `kernel` on `workload`, or None when the
-    record is missing or was taken on other kernel sources."""
+def recorded_traffic(kernel, workload, samples):
+    """DRAM bytes per launch of `kernel` on `workload` with `samples` ray-march
+    samples: the recorded capture's bytes scaled by samples / its samples
+    (the coefficient stream, which dominates, is proportional to samples).
+    None when the record is missing or was taken on other kernel sources."""
     try:
         with open(TRAFFIC_PROFILE) as fh:
             kv = {}
@@ -103,8 +117,30 @@ def recorded_traffic(kernel, workload):
             or kv.get("source_sha256") != kernel_source_hash()):
         return None
     try:
-        return int(kv["dram_bytes_per_launch"])
+        dram = int(kv["dram_bytes_per_launch"])
+        cap = int(kv["samples_per_launch"])
     except (KeyError, ValueError):
+        return None
+    return int(round(dram * samples / cap)) if cap > 0 else None
+
+
+def cpu_model():
+    """The host CPU's model name (x86 'model name'; Arm: lscpu's model)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        kv = dict((a.strip(), b.strip()) for a, b in
+                  (ln.split(":", 1) for ln in out.splitlines() if ":" in ln))
+        name = kv.get("Model name") or ""
+        vendor = kv.get("Vendor ID") or ""
+        return (vendor + " " + name).strip() or None
+    except Exception:
         return None
 
 
@@ -257,7 +293,8 @@ def cpu_baseline(scene, n_cams, pcg_per_gn):
     orc.apply_A(x, p)
     dt = time.perf_counter() - t0
     full = dt * scene.n_cams / n_cams
-    return {"value": 1.0 / full, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
+    return {"value": 1.0 / full, "unit": METRIC, "cores": os.cpu_count(), "cpu": cpu_model(),
+            "kind": "oracle",
             "sample": f"one A p (J p then J^T v, FP64, OpenMP over rays) on {n_cams} of "
                       f"{scene.n_cams} cameras ({orc.n_rays} rays, {dt:.1f} s), scaled by the "
                       f"ray count; PCG vector work (O(n)) not included"}
@@ -278,8 +315,8 @@ def run_reference(args, rank, world):
             "ms_per_step": 1000.0 * sc.cfg.pcg_iters / v, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": _workload_desc(sc)},
-            "cpu_baseline": {"value": v, "unit": METRIC, "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": timed[0]["sample"]},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": os.cpu_count(),
+                             "cpu": cpu_model(), "kind": "oracle", "sample": timed[0]["sample"]},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -797,42 +834,72 @@ def run_ours(args, rank, world, local):
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     fp32_peak = sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     apply_ms = tm["apply"]["ms"] / max(tm["apply"]["launches"], 1)
     per_step = {k: v["ms"] / args.steps for k, v in tm.items()}
+    iters = max(sum(s["pcg_iters"] for s in stats), 1)
     coef = bool(tuning.get("coef"))
     if coef:
         apply_kernel = ("k_apply_coef<bf16> (A p from stored coefficients)" if bf else
                         "k_apply_coef<float> (A p from stored coefficients)")
-        hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
-        algo_bytes = COEF_BYTES_PER_SAMPLE * samples + (4 if not bf else 2) * sc.n_params + 4 * sc.n_params
-        achieved = algo_bytes / (apply_ms / 1000.0) / 1e9
-        alu = FLOP_PER_SAMPLE_COEF * samples / (apply_ms / 1000.0) / 1e12
-        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                "frac": achieved / hbm_peak,
-                "algorithmic_bytes_per_launch": algo_bytes,
-                "alu_frac": alu / fp32_peak,
-                "peak_source": f"hbm_gbs ({peak_src}); alu_frac against {sm_count} SMs x 128 "
-                               f"FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz"}
     else:
         apply_kernel = ("k_scatter<bf16,bf16,1> (A p)" if bf else
                         "k_scatter<PairF32,PairF32,1> (A p, paired x/p records)"
                         if tuning.get("paired") else "k_scatter<float,float,1> (A p)")
-        achieved = FLOP_PER_SAMPLE_APPLY * samples / (apply_ms / 1000.0) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp32_peak,
-                "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
-                               f"(max SM clock, {peak_src})"}
-    roof["traffic"] = recorded_traffic(apply_kernel, args.workload) if args.cams is None else None
-    roof["kernel"] = apply_kernel
-    # the unit that bounds A p: 16-byte vector atomics, one lane operation per
-    # active lane of each atomic instruction
     # per PCG iteration (a partial coefficient store splits one A p in two launches)
-    apply_s_per_iter = tm["apply"]["ms"] / 1000.0 / max(sum(s["pcg_iters"] for s in stats), 1)
-    red_rate = red_per_apply / apply_s_per_iter
+    apply_s = tm["apply"]["ms"] / 1000.0 / iters
+    achieved = FLOP_PER_SAMPLE_METHOD * samples / apply_s / 1e12
+    impl_flop = FLOP_PER_SAMPLE_COEF if coef else FLOP_PER_SAMPLE_RECOMPUTE
+    compulsory = APPLY_COMPULSORY_BYTES_PER_PARAM * sc.n_params
+    roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+            "frac": achieved / fp32_peak,
+            "flop_per_sample": FLOP_PER_SAMPLE_METHOD, "samples_per_launch": samples,
+            "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
+                           f"(max SM clock, {peak_src})",
+            "kernel": apply_kernel,
+            "traffic": recorded_traffic(apply_kernel, args.workload, samples)
+            if args.cams is None else None,
+            "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 4-camera "
+                              "capture, scaled by samples (profiles/apply_coef_traffic_scale128.md)",
+            "impl_flop_per_sample": impl_flop,
+            "impl_alu_frac": impl_flop * samples / apply_s / 1e12 / fp32_peak,
+            "compulsory_bytes_per_launch": compulsory,
+            "hbm_frac_compulsory": compulsory / apply_s / 1e9 / hbm_peak}
+    if coef:
+        design = COEF_BYTES_PER_SAMPLE * samples + ((2 if bf else 4) + 4) * sc.n_params
+        roof["design_traffic"] = {
+            "what": "coefficient store: 16 B per sample or shell hit streamed twice per A p, "
+                    "plus p read and A p written once (an implementation choice that trades "
+                    "HBM capacity for recomputation, not the method's compulsory bytes)",
+            "bytes_per_launch": design, "ratio_to_compulsory": design / compulsory,
+            "achieved": design / apply_s / 1e9, "unit": "GB/s",
+            "hbm_frac": design / apply_s / 1e9 / hbm_peak}
+    # the scatter's 16-byte vector atomics, one lane operation per active lane
+    red_rate = red_per_apply / apply_s
     roof["atomics"] = {"lane_ops_per_apply": red_per_apply, "achieved": red_rate,
                        "peak": red_peak, "unit": "lane-ops/s", "frac": red_rate / red_peak,
                        "peak_source": "perf_measure_atomic_peak (16-byte vector atomic "
                                       "microbenchmark on this GPU, measured in this run)"}
+    vb = VEC_BYTES_PER_PARAM + (2 if bf else 0) + (4 if (not bf and not coef and tuning.get("paired")) else 0)
+    vec_s = tm["vector"]["ms"] / 1000.0 / iters
+    vector_roof = {"kernels": "k_pcg_update + k_pcg_finish + k_pcg_dir (per PCG iteration)",
+                   "bound": "hbm", "bytes_per_iter": vb * sc.n_params,
+                   "ms_per_iter": vec_s * 1000.0,
+                   "achieved": vb * sc.n_params / vec_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                   "frac": vb * sc.n_params / vec_s / 1e9 / hbm_peak,
+                   "compulsory_bytes_per_iter": VEC_COMPULSORY_BYTES_PER_PARAM * sc.n_params,
+                   "frac_compulsory": VEC_COMPULSORY_BYTES_PER_PARAM * sc.n_params / vec_s / 1e9
+                   / hbm_peak,
+                   "peak_source": f"hbm_gbs ({peak_src})"}
+    rb = (RESIDUAL_BYTES_PER_RAY_F32 // (2 if bf else 1)) * sc.n_rays
+    res_s = tm["residual"]["ms"] / 1000.0 / max(tm["residual"]["launches"], 1)
+    residual_roof = {"kernel": "k_forward<MODE 1> (residual r = H^ - C and F: one ray march)",
+                     "bound": "hbm", "bytes_per_launch": rb, "ms_per_launch": res_s * 1000.0,
+                     "achieved": rb / res_s / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": rb / res_s / 1e9 / hbm_peak,
+                     "note": "streams C in and r out, but each ray's march (interpolation of x "
+                             "from L2, exponentials) bounds the launch",
+                     "peak_source": f"hbm_gbs ({peak_src})"}
 
     if rank != 0:
         return
@@ -854,6 +921,8 @@ def run_ours(args, rank, world, local):
         "kernel_ms_per_step": per_step,
         "apply_ms_per_launch": apply_ms,
         "roofline": roof,
+        "vector_roofline": vector_roof,
+        "residual_roofline": residual_roof,
         "e2e": {"value": e2e_value, "unit": METRIC,
                 "h2d_bytes_per_step": int(4 * sc.n_params + (2 if bf else 4) * 3 * sc.n_rays),
                 "d2h_bytes_per_step": int(4 * sc.n_params)},

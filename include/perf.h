@@ -132,11 +132,12 @@ typedef struct {
 /* Device time per kernel family, from CUDA events recorded on the launching
  * stream around each launch while timing is enabled. */
 enum { PERF_T_APPLY = 0,    /* A p: the fused J p / J^T (J p) ray march */
-       PERF_T_FORWARD = 1,  /* residual and line-search objective marches */
+       PERF_T_FORWARD = 1,  /* line-search objective marches (F only) */
        PERF_T_DIAG = 2,     /* diag(J^T J) with J^T r */
        PERF_T_VECTOR = 3,   /* PCG vector kernels (update, exit test, direction) */
        PERF_T_PRECOND = 4,  /* block preconditioner construction (network or block inverse) */
-       PERF_T_COUNT = 5 };
+       PERF_T_RESIDUAL = 5, /* the Gauss-Newton step's residual march (r = H^ - C and F) */
+       PERF_T_COUNT = 6 };
 typedef struct {
     double ms[PERF_T_COUNT];
     int64_t launches[PERF_T_COUNT];
@@ -340,6 +341,22 @@ perf_status perf_lpc_head_outputs(perf_lpc* lpc, int32_t G, const void* feat, vo
 /* blocks_out (G^3 x 16 floats) = P_v for every grid voxel. */
 perf_status perf_lpc_infer(perf_lpc* lpc, int32_t G, const void* feat, const float* diag,
                            float* blocks_out, void* stream);
+/* Failure detection of the tcgen05 convolution (Section "Preconditioner" has
+ * no counterpart: this is the library's own bounded-wait protocol).  Every
+ * wait of the convolution kernel for its TMA loads or its MMAs polls a
+ * bounded number of rounds; when one runs out the kernel raises a device
+ * flag, waits (bounded) for its loads still in flight, frees its tensor
+ * memory and returns, leaving the context usable.  perf_lpc_conv_status
+ * reads and clears that flag into HOST *timed_out (1: some convolution since
+ * the last read gave up; its outputs are incomplete) and synchronises the
+ * device.  perf_lpc_loss_grad / perf_lpc_train_step return PERF_ERR_TIMEOUT
+ * when the flag is set; perf_gn_solve falls back to Jacobi for that step.
+ * perf_lpc_test_conv_wait_limit is a test hook: later launches give each
+ * CTA's first wait `rounds` polling rounds (0: it gives up at once; the
+ * default and maximum is 2^20); every other wait keeps the normal limit.
+ * Process-wide, not thread-safe. */
+perf_status perf_lpc_conv_status(int32_t* timed_out);
+perf_status perf_lpc_test_conv_wait_limit(uint32_t rounds);
 /* out_v = D_v^{-1/2} in_v on the G^3 grid voxels (4 floats each; 0 where a
  * voxel has an unobserved parameter); mask_out (may be NULL) = 1 where all
  * four parameters are observed.  Prepares probe pairs for training. */

@@ -58,10 +58,10 @@ class PcgInfo(ctypes.Structure):
 
 
 class Timing(ctypes.Structure):
-    _fields_ = [("ms", ctypes.c_double * 5), ("launches", ctypes.c_int64 * 5)]
+    _fields_ = [("ms", ctypes.c_double * 6), ("launches", ctypes.c_int64 * 6)]
 
 
-TIMING_KINDS = ("apply", "forward", "diag", "vector", "precond")
+TIMING_KINDS = ("apply", "forward", "diag", "vector", "precond", "residual")
 
 
 class Tuning(ctypes.Structure):
@@ -120,6 +120,8 @@ _SIGS = {
     "perf_lpc_head_outputs": [_VP, ctypes.c_int32, _VP, _VP, _VP],
     "perf_lpc_infer": [_VP, ctypes.c_int32, _VP, _VP, _VP, _VP],
     "perf_block_jacobi": [ctypes.c_int32, _VP, _VP, _VP, _VP],
+    "perf_lpc_conv_status": [ctypes.POINTER(ctypes.c_int32)],
+    "perf_lpc_test_conv_wait_limit": [ctypes.c_uint32],
     "perf_lpc_dscale": [ctypes.c_int32, _VP, _VP, _VP, _VP, _VP],
     "perf_batch_create": [ctypes.POINTER(_VP), ctypes.c_int32, _VP, _VP, ctypes.POINTER(Options)],
     "perf_batch_destroy": [_VP],
@@ -602,6 +604,22 @@ class LPC:
     def infer(self, G, feat, diag, blocks_out, stream=None):
         self._check(self.lib.perf_lpc_infer(self.h, int(G), _ptr(feat), _ptr(diag),
                                             _ptr(blocks_out), _stream(stream)), "infer")
+
+
+def conv_status() -> int:
+    """1 if a convolution of the preconditioner network gave up a bounded wait
+    since the last call (its outputs are incomplete), else 0; clears the flag."""
+    v = ctypes.c_int32(0)
+    st = load_library().perf_lpc_conv_status(ctypes.byref(v))
+    if st != 0:
+        raise PerfError(st, "perf_lpc_conv_status failed")
+    return int(v.value)
+
+
+def set_conv_wait_limit_for_test(rounds: int):
+    """Test hook: polling rounds of each convolution CTA's first TMA wait in
+    later launches (0 makes it give up at once; 1 << 20 is the default)."""
+    load_library().perf_lpc_test_conv_wait_limit(ctypes.c_uint32(int(rounds)))
 
 
 def dscale(G, diag, inp, out, mask_out=None, stream=None):

@@ -84,8 +84,9 @@ __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
 }
 
 // Bounded wait for the phase with the given parity; false on timeout.
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-    for (uint32_t i = 0; i < kSpinLimit; ++i) {
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity,
+                                          uint32_t limit = kSpinLimit) {
+    for (uint32_t i = 0; i < limit; ++i) {
         uint32_t done;
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(kTCThreads) k_conv_fwd_tc(const __grid_constan
                                                             const __nv_bfloat16* __restrict__ W,
                                                             const float* __restrict__ bias,
                                                             __nv_bfloat16* __restrict__ out, int G,
-                                                            int relu) {
+                                                            int relu, uint32_t first_limit) {
     extern __shared__ unsigned char smem_raw[];
     const uint32_t raw = smem_addr(smem_raw);
     const uint32_t pad = (1024u - (raw & 1023u)) & 1023u;
@@ -248,9 +249,14 @@ __global__ void __launch_bounds__(kTCThreads) k_conv_fwd_tc(const __grid_constan
         tma_load_5d(dst + kHalf, &in_map, bar_full + 8 * sl, 0, 1, c.x0 - 1, c.y0 - 1, q);
         ++loaded[sl];
     };
+    // the CTA's first wait takes first_limit rounds (kSpinLimit except when a
+    // test makes it run out); every later one kSpinLimit
+    bool first_wait = true;
     auto wait_plane = [&](int q) -> bool {
         const int sl = ring_slot(q);
-        const bool ok = mbar_wait(bar_full + 8 * sl, (uint32_t)waited[sl] & 1u);
+        const bool ok = mbar_wait(bar_full + 8 * sl, (uint32_t)waited[sl] & 1u,
+                                  first_wait ? first_limit : kSpinLimit);
+        first_wait = false;
         if (ok) ++waited[sl];
         return ok;
     };
@@ -348,6 +354,9 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                                   CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
+// Rounds of the first TMA wait of each CTA (see lpc_conv_set_first_wait_limit).
+uint32_t g_first_wait_limit = kSpinLimit;
+
 EncodeTiledFn encode_fn() {
     static EncodeTiledFn fn = nullptr;
     if (!fn) {
@@ -394,9 +403,19 @@ cudaError_t lpc_conv_fwd(const __nv_bfloat16* in, const __nv_bfloat16* W, const 
     const long long items = nx * ny * ((G + kZChunk - 1) / kZChunk);
     const long long cap = (long long)sms * kCtasPerSm;
     const int grid = (int)(items < cap ? items : cap);
-    k_conv_fwd_tc<<<grid, kTCThreads, kSmemDyn, st>>>(map, W, bias, out, G, relu);
+    k_conv_fwd_tc<<<grid, kTCThreads, kSmemDyn, st>>>(map, W, bias, out, G, relu,
+                                                      g_first_wait_limit);
     count_launch();
     return cudaGetLastError();
+}
+
+// Test hook: the number of polling rounds of each CTA's first wait for its
+// TMA loads in later launches (0 makes that wait give up at once, so the
+// timeout path -- raise the flag, drain the loads in flight with the normal
+// limit, free tensor memory, return -- runs without any fault); values above
+// the normal limit are clamped to it.
+void lpc_conv_set_first_wait_limit(uint32_t rounds) {
+    g_first_wait_limit = rounds < kSpinLimit ? rounds : kSpinLimit;
 }
 
 // Reads and clears the device flag raised by a convolution whose bounded

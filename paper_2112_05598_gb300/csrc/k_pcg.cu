@@ -3,18 +3,22 @@
 // and written as few times as the recurrence allows (Section "Update step":
 // the vector additions and inner products run in parallel on the GPU).
 //
-// The CG recurrence vectors Delta, rho and p are FP64 (the vector kernels are
-// a few hundred MB of traffic per iteration against a ray march of tens of
-// ms, and FP32 recurrences lose conjugacy within 20 iterations on these
-// ill-conditioned normal equations); A p arrives in FP32 from the ray-march
-// scatter, and p is also written as FP32 (and BF16) for the next march's
-// gathers.  One thread handles one parameter block (4 values = one voxel or
-// texel); inner products accumulate in FP64.
-//   begin : rho = b = -grad, z = M^-1 rho, p = z, Delta = 0, R0, rho^T z
-//   update: Delta += alpha p, rho -= alpha A p, z = M^-1 rho, R, rho^T z
+// The CG recurrence vectors Delta, rho and p are FP32; the inner products
+// rho^T rho and rho^T z are accumulated per thread as compensated FP32 sums
+// (TwoSum: an unevaluated hi + lo pair) and reduced across threads and CTAs
+// in FP64, and p^T A p arrives in FP64 from the ray march.  On GB300 FP64
+// arithmetic runs at about 1/64 of the FP32 rate, so FP64 vectors (and the
+// FP64 divisions of z = rho / d) made these kernels ALU-bound at a quarter of
+// the HBM bandwidth; FP32 storage halves their bytes.  p is the array the
+// next ray march gathers (and, in BF16 scenes, is also written as BF16).
+// One thread handles one parameter block (4 values = one voxel or texel).
+//   begin : rho = b = -grad, z = M^-1 rho, p = z, Delta = 0, A p = 0, R0, rho^T z
+//   update: Delta += alpha p, rho -= alpha A p, A p = 0, z = M^-1 rho, R, rho^T z
 //   finish: exit test (R < eps^2 R0 or R / R_prev > stall, or a fixed count),
 //           beta = rho'^T z' / rho^T z                               [1 thread]
-//   dir   : p = z + beta p, A p = 0 for the next scatter
+//   dir   : p = z + beta p
+// Bytes per parameter and iteration: update 20 read + 12 written, dir 12
+// read + 4 written (48; BF16 scenes write 2 more, paired records 4 more).
 // M^-1 is Jacobi (z_j = rho_j / d_j, 0 where d_j <= 1e-30) or, where 4x4 blocks
 // are given for the grid voxels, z_v = P_v rho_v per voxel.
 #include <cuda_bf16.h>
@@ -26,14 +30,14 @@ unsigned long long g_launches = 0;
 
 constexpr int kVThreads = 256;
 
+// CTAs of a grid-stride vector kernel: enough to cover nblk blocks, at most
+// 8 per SM of the current device (queried per call: the device may change).
 static int vec_blocks(long long nblk) {
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (sms <= 0) sms = 1;
-    }
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
+        sms = 1;
     long long want = (nblk + kVThreads - 1) / kVThreads;
     long long cap = (long long)sms * 8;
     long long b = want < cap ? want : cap;
@@ -46,34 +50,39 @@ static int vec_blocks(long long nblk) {
 // sees; 1e-30 keeps full binary32 precision above the cut.
 constexpr float kJacobiFloor = 1e-30f;
 
-struct D4 {
-    double x, y, z, w;
-};
-
-__device__ __forceinline__ D4 ld4(const double* a, long long v) {
-    const double2 lo = reinterpret_cast<const double2*>(a)[2 * v];
-    const double2 hi = reinterpret_cast<const double2*>(a)[2 * v + 1];
-    return D4{lo.x, lo.y, hi.x, hi.y};
-}
-
-__device__ __forceinline__ void st4(double* a, long long v, const D4& d) {
-    reinterpret_cast<double2*>(a)[2 * v] = make_double2(d.x, d.y);
-    reinterpret_cast<double2*>(a)[2 * v + 1] = make_double2(d.z, d.w);
-}
-
-__device__ __forceinline__ D4 precond(const D4& r, long long v, const float4* __restrict__ d4,
-                                      const float4* __restrict__ B, long long n_block) {
+__device__ __forceinline__ float4 precond(const float4& r, long long v, const float4* __restrict__ d4,
+                                          const float4* __restrict__ B, long long n_block) {
     if (B != nullptr && v < n_block) {
         const float4 b0 = B[4 * v], b1 = B[4 * v + 1], b2 = B[4 * v + 2], b3 = B[4 * v + 3];
-        return D4{b0.x * r.x + b0.y * r.y + b0.z * r.z + b0.w * r.w,
-                  b1.x * r.x + b1.y * r.y + b1.z * r.z + b1.w * r.w,
-                  b2.x * r.x + b2.y * r.y + b2.z * r.z + b2.w * r.w,
-                  b3.x * r.x + b3.y * r.y + b3.z * r.z + b3.w * r.w};
+        return make_float4(b0.x * r.x + b0.y * r.y + b0.z * r.z + b0.w * r.w,
+                           b1.x * r.x + b1.y * r.y + b1.z * r.z + b1.w * r.w,
+                           b2.x * r.x + b2.y * r.y + b2.z * r.z + b2.w * r.w,
+                           b3.x * r.x + b3.y * r.y + b3.z * r.z + b3.w * r.w);
     }
     const float4 d = d4[v];
-    return D4{d.x > kJacobiFloor ? r.x / d.x : 0.0, d.y > kJacobiFloor ? r.y / d.y : 0.0,
-              d.z > kJacobiFloor ? r.z / d.z : 0.0, d.w > kJacobiFloor ? r.w / d.w : 0.0};
+    return make_float4(d.x > kJacobiFloor ? r.x / d.x : 0.0f, d.y > kJacobiFloor ? r.y / d.y : 0.0f,
+                       d.z > kJacobiFloor ? r.z / d.z : 0.0f, d.w > kJacobiFloor ? r.w / d.w : 0.0f);
 }
+
+// Compensated FP32 running sum (Knuth's TwoSum, explicit round-to-nearest
+// operations so nothing is reassociated): the value is hi + lo.
+struct Acc2 {
+    float hi = 0.0f, lo = 0.0f;
+    __device__ __forceinline__ void add(float v) {
+        const float s = __fadd_rn(hi, v);
+        const float bv = __fsub_rn(s, hi);
+        const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bv)), __fsub_rn(v, bv));
+        hi = s;
+        lo = __fadd_rn(lo, e);
+    }
+    __device__ __forceinline__ void add4(const float4& a, const float4& b) {
+        add(__fmul_rn(a.x, b.x));
+        add(__fmul_rn(a.y, b.y));
+        add(__fmul_rn(a.z, b.z));
+        add(__fmul_rn(a.w, b.w));
+    }
+    __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
 
 // Segments: a batch of independent systems (the scenes of a batch).  With
 // chunks (one int4 per CTA, built by the host: x = system, [y, z) = its
@@ -93,10 +102,6 @@ __device__ __forceinline__ int seg_id(const int4* chunks) { return chunks ? chun
     }                                                                                     \
     for (long long v = lo_; v < hi_; v += step_)
 
-__device__ __forceinline__ double dot4(const D4& a, const D4& b) {
-    return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w;
-}
-
 __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* y, long long v, float4 a) {
     __nv_bfloat162 lo = __floats2bfloat162_rn(a.x, a.y);
     __nv_bfloat162 hi = __floats2bfloat162_rn(a.z, a.w);
@@ -106,12 +111,12 @@ __device__ __forceinline__ void store_bf16x4(__nv_bfloat16* y, long long v, floa
     reinterpret_cast<uint2*>(y)[v] = u;
 }
 
-// pxp (may be null): paired x / p records (two float4 each); p goes to the
-// second half of record v.
-__device__ __forceinline__ void store_p(float4* p32, __nv_bfloat16* p16, float4* pxp, long long v,
-                                        const D4& p) {
-    const float4 f = make_float4((float)p.x, (float)p.y, (float)p.z, (float)p.w);
-    p32[v] = f;
+// p and its copies for the gathers: p16 (BF16 scenes) and pxp (paired x / p
+// records, two float4 each; p goes to the second half of record v); either
+// may be null.
+__device__ __forceinline__ void store_p(float4* p, __nv_bfloat16* p16, float4* pxp, long long v,
+                                        const float4& f) {
+    p[v] = f;
     if (p16) store_bf16x4(p16, v, f);
     if (pxp) pxp[2 * v + 1] = f;
 }
@@ -120,26 +125,25 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const int
                                                         const float4* __restrict__ g,
                                                         const float4* __restrict__ d4,
                                                         const float4* __restrict__ B, long long n_block,
-                                                        double* delta, double* rho, double* p,
-                                                        float4* p32, __nv_bfloat16* p16, float4* Ap,
+                                                        float4* delta, float4* rho, float4* p,
+                                                        __nv_bfloat16* p16, float4* Ap,
                                                         PcgScalars* s, float4* pxp) {
     s += seg_id(chunks);
-    double aR = 0.0, aRz = 0.0;
+    Acc2 aR, aRz;
     const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     SEG_LOOP(v) {
         const float4 gg = g[v];
-        const D4 r{-(double)gg.x, -(double)gg.y, -(double)gg.z, -(double)gg.w};
-        const D4 z = precond(r, v, d4, B, n_block);
-        st4(rho, v, r);
-        st4(p, v, z);
-        store_p(p32, p16, pxp, v, z);
-        st4(delta, v, D4{0.0, 0.0, 0.0, 0.0});
+        const float4 r = make_float4(-gg.x, -gg.y, -gg.z, -gg.w);
+        const float4 z = precond(r, v, d4, B, n_block);
+        rho[v] = r;
+        store_p(p, p16, pxp, v, z);
+        delta[v] = zero;
         Ap[v] = zero;
-        aR += dot4(r, r);
-        aRz += dot4(r, z);
+        aR.add4(r, r);
+        aRz.add4(r, z);
     }
-    block_add_f64<kVThreads / 32>(aR, &s->acc_R);
-    block_add_f64<kVThreads / 32>(aRz, &s->acc_rz);
+    block_add_f64<kVThreads / 32>(aR.value(), &s->acc_R);
+    block_add_f64<kVThreads / 32>(aRz.value(), &s->acc_rz);
 }
 
 __global__ void k_pcg_begin_fin(PcgScalars* s, int n_seg, int max_iter, int fixed, double eps_rel,
@@ -171,9 +175,9 @@ __global__ void k_pcg_begin_fin(PcgScalars* s, int n_seg, int max_iter, int fixe
 }
 
 __global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, const int4* chunks,
-                                                         double* delta, double* rho,
-                                                         const double* __restrict__ p,
-                                                         const float4* __restrict__ Ap,
+                                                         float4* delta, float4* rho,
+                                                         const float4* __restrict__ p,
+                                                         float4* Ap,
                                                          const float4* __restrict__ d4,
                                                          const float4* __restrict__ B,
                                                          long long n_block, PcgScalars* s) {
@@ -181,24 +185,26 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_update(long long nb, const in
     if (s->done) return;
     const double pAp = s->pAp;
     if (!(pAp > 0.0) || !isfinite(pAp)) return;
-    const double alpha = s->rz / pAp;
-    double aR = 0.0, aRz = 0.0;
+    const float alpha = (float)(s->rz / pAp);
+    Acc2 aR, aRz;
+    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
     SEG_LOOP(v) {
-        const D4 pv = ld4(p, v);
+        const float4 pv = p[v];
         const float4 av = Ap[v];
-        D4 dv = ld4(delta, v), r = ld4(rho, v);
-        dv.x = fma(alpha, pv.x, dv.x); dv.y = fma(alpha, pv.y, dv.y);
-        dv.z = fma(alpha, pv.z, dv.z); dv.w = fma(alpha, pv.w, dv.w);
-        r.x = fma(-alpha, (double)av.x, r.x); r.y = fma(-alpha, (double)av.y, r.y);
-        r.z = fma(-alpha, (double)av.z, r.z); r.w = fma(-alpha, (double)av.w, r.w);
-        st4(delta, v, dv);
-        st4(rho, v, r);
-        const D4 z = precond(r, v, d4, B, n_block);
-        aR += dot4(r, r);
-        aRz += dot4(r, z);
+        float4 dv = delta[v], r = rho[v];
+        dv.x = fmaf(alpha, pv.x, dv.x); dv.y = fmaf(alpha, pv.y, dv.y);
+        dv.z = fmaf(alpha, pv.z, dv.z); dv.w = fmaf(alpha, pv.w, dv.w);
+        r.x = fmaf(-alpha, av.x, r.x); r.y = fmaf(-alpha, av.y, r.y);
+        r.z = fmaf(-alpha, av.z, r.z); r.w = fmaf(-alpha, av.w, r.w);
+        delta[v] = dv;
+        rho[v] = r;
+        Ap[v] = zero;             // the next scatter accumulates into it
+        const float4 z = precond(r, v, d4, B, n_block);
+        aR.add4(r, r);
+        aRz.add4(r, z);
     }
-    block_add_f64<kVThreads / 32>(aR, &s->acc_R);
-    block_add_f64<kVThreads / 32>(aRz, &s->acc_rz);
+    block_add_f64<kVThreads / 32>(aR.value(), &s->acc_R);
+    block_add_f64<kVThreads / 32>(aRz.value(), &s->acc_rz);
 }
 
 __global__ void k_pcg_finish(PcgScalars* s, int n_seg) {
@@ -236,23 +242,20 @@ __global__ void k_pcg_finish(PcgScalars* s, int n_seg) {
 }
 
 __global__ void __launch_bounds__(kVThreads) k_pcg_dir(long long nb, const int4* chunks,
-                                                      const double* __restrict__ rho,
+                                                      const float4* __restrict__ rho,
                                                       const float4* __restrict__ d4,
                                                       const float4* __restrict__ B, long long n_block,
-                                                      double* p, float4* p32, __nv_bfloat16* p16,
-                                                      float4* Ap, const PcgScalars* s, float4* pxp) {
+                                                      float4* p, __nv_bfloat16* p16,
+                                                      const PcgScalars* s, float4* pxp) {
     s += seg_id(chunks);
     if (s->done) return;
-    const double beta = s->beta;
-    const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+    const float beta = (float)s->beta;
     SEG_LOOP(v) {
-        const D4 z = precond(ld4(rho, v), v, d4, B, n_block);
-        D4 pv = ld4(p, v);
-        pv.x = fma(beta, pv.x, z.x); pv.y = fma(beta, pv.y, z.y);
-        pv.z = fma(beta, pv.z, z.z); pv.w = fma(beta, pv.w, z.w);
-        st4(p, v, pv);
-        store_p(p32, p16, pxp, v, pv);
-        Ap[v] = zero;
+        const float4 z = precond(rho[v], v, d4, B, n_block);
+        float4 pv = p[v];
+        pv.x = fmaf(beta, pv.x, z.x); pv.y = fmaf(beta, pv.y, z.y);
+        pv.z = fmaf(beta, pv.z, z.z); pv.w = fmaf(beta, pv.w, z.w);
+        store_p(p, p16, pxp, v, pv);
     }
 }
 
@@ -266,16 +269,16 @@ __global__ void __launch_bounds__(kVThreads) k_pair_pack(long long nb, const flo
     }
 }
 
-// x_out = P(x + gamma Delta): the trial point is formed in FP64 and rounded
-// once to the storage type(s).
+// x_out = P(x + gamma Delta): the trial point is formed in FP64 (one FMA per
+// value) and rounded once to the storage type(s).
 __global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4* x,
-                                                    const double* __restrict__ delta, double gamma,
+                                                    const float4* __restrict__ delta, double gamma,
                                                     int project, float4* x_out,
                                                     __nv_bfloat16* x16) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
          v += (long long)gridDim.x * blockDim.x) {
         const float4 a = x[v];
-        const D4 d = ld4(delta, v);
+        const float4 d = delta[v];
         float4 y = make_float4((float)fma(gamma, d.x, (double)a.x), (float)fma(gamma, d.y, (double)a.y),
                                (float)fma(gamma, d.z, (double)a.z), (float)fma(gamma, d.w, (double)a.w));
         if (project) {
@@ -293,7 +296,7 @@ __global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4*
 // is set (mask == nullptr: every segment); other segments are left alone.
 __global__ void __launch_bounds__(kVThreads) k_trial_seg(long long nb, const int4* chunks,
                                                         const float4* x,
-                                                        const double* __restrict__ delta,
+                                                        const float4* __restrict__ delta,
                                                         const double* __restrict__ gamma,
                                                         const int* __restrict__ mask, int project,
                                                         float4* x_out) {
@@ -302,7 +305,7 @@ __global__ void __launch_bounds__(kVThreads) k_trial_seg(long long nb, const int
     const double g = gamma[sg];
     SEG_LOOP(v) {
         const float4 a = x[v];
-        const D4 d = ld4(delta, v);
+        const float4 d = delta[v];
         float4 y = make_float4((float)fma(g, d.x, (double)a.x), (float)fma(g, d.y, (double)a.y),
                                (float)fma(g, d.z, (double)a.z), (float)fma(g, d.w, (double)a.w));
         if (project) {
@@ -322,13 +325,6 @@ __global__ void __launch_bounds__(kVThreads) k_to_bf16(long long nb, const float
         store_bf16x4(y, v, x[v]);
 }
 
-__global__ void __launch_bounds__(kVThreads) k_to_f32(long long n, const double* __restrict__ a,
-                                                     float* b) {
-    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-         i += (long long)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
-}
-
 // ------------------------------------------------------------- launchers
 
 #define F4(p) reinterpret_cast<float4*>(p)
@@ -339,17 +335,17 @@ static dim3 seg_grid(long long nb, long long n_chunks, const int4* chunks) {
 }
 
 cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                                 const float* grad, const float* diag, double* delta, double* rho,
-                                 double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                                 PcgScalars* s, int max_iter, int fixed, double eps_rel,
-                                 double stall, const float* blocks, long long n_block,
-                                 cudaStream_t st, float* pxp) {
+                                 const float* grad, const float* diag, float* delta, float* rho,
+                                 float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
+                                 int max_iter, int fixed, double eps_rel, double stall,
+                                 const float* blocks, long long n_block, cudaStream_t st,
+                                 float* pxp) {
     const long long nb = n / 4;
     cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars) * (size_t)(n_seg > 0 ? n_seg : 1), st);
     if (e != cudaSuccess) return e;
     if (nb > 0) {
         k_pcg_begin<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
-            nb, chunks, CF4(grad), CF4(diag), CF4(blocks), n_block, delta, rho, p, F4(p32), p16,
+            nb, chunks, CF4(grad), CF4(diag), CF4(blocks), n_block, F4(delta), F4(rho), F4(p), p16,
             F4(Ap), s, F4(pxp));
         count_launch();
     }
@@ -359,30 +355,30 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, lon
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
-                             double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                             PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
+cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, float* delta,
+                             float* rho, float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
+                             int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st, float* pxp) {
-    return launch_pcg_begin_seg(n, 1, nullptr, 0, grad, diag, delta, rho, p, p32, p16, Ap, s,
-                                max_iter, fixed, eps_rel, stall, blocks, n_block, st, pxp);
+    return launch_pcg_begin_seg(n, 1, nullptr, 0, grad, diag, delta, rho, p, p16, Ap, s, max_iter,
+                                fixed, eps_rel, stall, blocks, n_block, st, pxp);
 }
 
 cudaError_t launch_pcg_update_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                                  double* delta, double* rho, const double* p, const float* Ap,
+                                  float* delta, float* rho, const float* p, float* Ap,
                                   const float* diag, const float* blocks, long long n_block,
                                   PcgScalars* s, cudaStream_t st) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_pcg_update<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
-            nb, chunks, delta, rho, p, CF4(Ap), CF4(diag), CF4(blocks), n_block, s);
+            nb, chunks, F4(delta), F4(rho), CF4(p), F4(Ap), CF4(diag), CF4(blocks), n_block, s);
         count_launch();
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
-                              const float* Ap, const float* diag, const float* blocks,
-                              long long n_block, PcgScalars* s, cudaStream_t st) {
+cudaError_t launch_pcg_update(long long n, float* delta, float* rho, const float* p, float* Ap,
+                              const float* diag, const float* blocks, long long n_block,
+                              PcgScalars* s, cudaStream_t st) {
     return launch_pcg_update_seg(n, 1, nullptr, 0, delta, rho, p, Ap, diag, blocks, n_block, s,
                                  st);
 }
@@ -397,42 +393,41 @@ cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st) {
 cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st) { return launch_pcg_finish_seg(s, 1, st); }
 
 cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                               const double* rho, const float* diag, const float* blocks,
-                               long long n_block, double* p, float* p32, __nv_bfloat16* p16,
-                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp) {
+                               const float* rho, const float* diag, const float* blocks,
+                               long long n_block, float* p, __nv_bfloat16* p16, PcgScalars* s,
+                               cudaStream_t st, float* pxp) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_pcg_dir<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
-            nb, chunks, rho, CF4(diag), CF4(blocks), n_block, p, F4(p32), p16, F4(Ap), s, F4(pxp));
+            nb, chunks, CF4(rho), CF4(diag), CF4(blocks), n_block, F4(p), p16, s, F4(pxp));
         count_launch();
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
-                           long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                           PcgScalars* s, cudaStream_t st, float* pxp) {
-    return launch_pcg_dir_seg(n, 1, nullptr, 0, rho, diag, blocks, n_block, p, p32, p16, Ap, s,
-                              st, pxp);
+cudaError_t launch_pcg_dir(long long n, const float* rho, const float* diag, const float* blocks,
+                           long long n_block, float* p, __nv_bfloat16* p16, PcgScalars* s,
+                           cudaStream_t st, float* pxp) {
+    return launch_pcg_dir_seg(n, 1, nullptr, 0, rho, diag, blocks, n_block, p, p16, s, st, pxp);
 }
 
 cudaError_t launch_trial_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                             const float* x, const double* delta, const double* gamma,
+                             const float* x, const float* delta, const double* gamma,
                              const int* mask, int project, float* x_out, cudaStream_t st) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_trial_seg<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
-            nb, chunks, CF4(x), delta, gamma, mask, project, F4(x_out));
+            nb, chunks, CF4(x), CF4(delta), gamma, mask, project, F4(x_out));
         count_launch();
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_trial(long long n, const float* x, const double* delta, double gamma,
+cudaError_t launch_trial(long long n, const float* x, const float* delta, double gamma,
                          int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st) {
     const long long nb = n / 4;
     if (nb > 0) {
-        k_trial<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), delta, gamma, project, F4(x_out),
+        k_trial<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), CF4(delta), gamma, project, F4(x_out),
                                                       x16_out);
         count_launch();
     }
@@ -453,14 +448,6 @@ cudaError_t launch_pair_pack(long long n, const float* x, const float* p, float*
     const long long nb = n / 4;
     if (nb > 0) {
         k_pair_pack<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), CF4(p), F4(xp));
-        count_launch();
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t st) {
-    if (n > 0) {
-        k_to_f32<<<vec_blocks((n + 3) / 4), kVThreads, 0, st>>>(n, a, b);
         count_launch();
     }
     return cudaGetLastError();

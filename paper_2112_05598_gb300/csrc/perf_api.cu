@@ -27,6 +27,7 @@ cudaError_t lpc_blocks_for(perf_lpc* L, int G, const float* x, const float* grad
                            const float* cross, __nv_bfloat16* feat, float* blocks, cudaStream_t st);
 cudaError_t launch_block_jacobi(const float* diag, const float* cross, float* blocks, long long V,
                                 cudaStream_t st);
+int lpc_conv_error();
 }  // namespace perf
 
 struct perf_ctx {
@@ -40,10 +41,9 @@ struct perf_ctx {
     void* r = nullptr;          // residuals, scene storage type
     float* diag = nullptr;
     float* grad = nullptr;
-    double* delta = nullptr;
-    double* rho = nullptr;
-    double* p = nullptr;
-    float* p32 = nullptr;
+    float* delta = nullptr;     // Algorithm 2 vectors (FP32; p is also gathered by A p)
+    float* rho = nullptr;
+    float* p = nullptr;
     float* xp = nullptr;        // paired (x, p) records for A p (FP32 scenes)
     bool pair = true;           // Gauss-Newton A p reads the paired records
     // coefficient-cached A p: per-sample (w_i, dH/dsigma_i) of the current
@@ -131,7 +131,6 @@ perf_status ensure_pcg(perf_ctx* ctx) {
     CK(alloc(&ctx->delta, ctx->n));
     CK(alloc(&ctx->rho, ctx->n));
     CK(alloc(&ctx->p, ctx->n));
-    CK(alloc(&ctx->p32, ctx->n));
     CK(alloc(&ctx->Ap, ctx->n));
     if (ctx->scene.dtype == PERF_BF16) CK(alloc(&ctx->p16, ctx->n));
     else CK(alloc(&ctx->xp, 2 * ctx->n));
@@ -196,9 +195,12 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
     if (ctx->coef_bytes < need) {
         if (ctx->coef) { cudaFree(ctx->coef); ctx->coef = nullptr; ctx->coef_bytes = 0; }
         if (cudaMalloc(&ctx->coef, need > 0 ? need : 16) != cudaSuccess) {
-            // out of memory after all (fragmentation, another user): recompute
+            // out of memory after all (fragmentation, another user): recompute,
+            // and report no store (perf_coef_info)
             cudaGetLastError();
             ctx->coef = nullptr;
+            ctx->coef_bytes = 0;
+            ctx->coef_tiles = 0;
             return PERF_OK;
         }
         ctx->coef_bytes = need;
@@ -358,7 +360,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->p32, ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -472,7 +474,7 @@ perf_status perf_pcg_begin(perf_ctx* ctx, const float* grad, const float* diag, 
         CK(cudaMemcpyAsync(ctx->diag, diag, sizeof(float) * (size_t)ctx->n,
                            cudaMemcpyDeviceToDevice, S(stream)));
     const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
-    CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p, ctx->p32,
+    CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
                               ctx->p16, ctx->Ap, ctx->s, ctx->opts.pcg_iters, ctx->opts.pcg_fixed,
                               ctx->opts.pcg_eps_rel, ctx->opts.pcg_stall, B, ctx->n_block,
                               S(stream)));
@@ -500,7 +502,7 @@ cudaError_t apply_arrays(perf_ctx* ctx, const perf::DevScene& d, const void* x, 
 perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const float* B, cudaStream_t st,
                      bool paired = false, bool coef = false) {
     const bool bf = ctx->scene.dtype == PERF_BF16;
-    const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p32);
+    const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p);
     t_begin(ctx, PERF_T_APPLY, st);
     // the store's tiles from the coefficients, any remaining tiles recomputed
     perf::DevScene rest = ctx->ds;
@@ -522,8 +524,8 @@ perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const floa
     CK(perf::launch_pcg_update(ctx->n, ctx->delta, ctx->rho, ctx->p, ctx->Ap, diag, B, ctx->n_block,
                                ctx->s, st));
     CK(perf::launch_pcg_finish(ctx->s, st));
-    CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p32, ctx->p16,
-                            ctx->Ap, ctx->s, st, paired ? ctx->xp : nullptr));
+    CK(perf::launch_pcg_dir(ctx->n, ctx->rho, diag, B, ctx->n_block, ctx->p, ctx->p16, ctx->s, st,
+                            paired ? ctx->xp : nullptr));
     t_end(ctx, PERF_T_VECTOR, st);
     return PERF_OK;
 }
@@ -551,7 +553,9 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
 perf_status perf_pcg_result(perf_ctx* ctx, float* delta_out, perf_pcg_info* info, void* stream) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (!ctx->delta || !ctx->s) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_result before pcg_begin");
-    if (delta_out) CK(perf::launch_to_f32(ctx->n, ctx->delta, delta_out, S(stream)));
+    if (delta_out)
+        CK(cudaMemcpyAsync(delta_out, ctx->delta, sizeof(float) * (size_t)ctx->n,
+                           cudaMemcpyDeviceToDevice, S(stream)));
     if (info) {
         PcgScalars h;
         CK(cudaMemcpyAsync(&h, ctx->s, sizeof(h), cudaMemcpyDeviceToHost, S(stream)));
@@ -595,10 +599,10 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         }
         // residuals and F(x)
         CK(cudaMemsetAsync(ctx->dF, 0, sizeof(double), st));
-        t_begin(ctx, PERF_T_FORWARD, st);
+        t_begin(ctx, PERF_T_RESIDUAL, st);
         if (ctx->n_rays > 0)
             CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, xm, target, ctx->r, nullptr, ctx->dF, 1, st));
-        t_end(ctx, PERF_T_FORWARD, st);
+        t_end(ctx, PERF_T_RESIDUAL, st);
         // b = -J^T r and M = diag(J^T J)
         CK(cudaMemsetAsync(ctx->diag, 0, sizeof(float) * (size_t)ctx->n, st));
         CK(cudaMemsetAsync(ctx->grad, 0, sizeof(float) * (size_t)ctx->n, st));
@@ -648,7 +652,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         if (paired) CK(perf::launch_pair_pack(ctx->n, x, nullptr, ctx->xp, st));
         for (int attempt = 0; attempt < 2; ++attempt) {
             CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
-                                      ctx->p32, ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
+                                      ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
                                       o.pcg_eps_rel, o.pcg_stall, B, nB, st,
                                       paired ? ctx->xp : nullptr));
             for (int k = 0; k < o.pcg_iters; ++k) {
@@ -666,7 +670,13 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
             PcgScalars hj;
             CK(cudaMemcpyAsync(&hj, ctx->s, sizeof(hj), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
-            if (std::isfinite(hj.R) && hj.R < hj.R0 && hj.exit_reason != 3 && hj.exit_reason != 4) break;
+            // a convolution of the network whose bounded wait ran out left the
+            // blocks incomplete: that step's PCG is rerun with Jacobi
+            const bool conv_ok = !(o.precond == PERF_PRECOND_BLOCK4 && ctx->lpc) ||
+                                 perf::lpc_conv_error() == 0;
+            if (conv_ok && std::isfinite(hj.R) && hj.R < hj.R0 && hj.exit_reason != 3 &&
+                hj.exit_reason != 4)
+                break;
             B = nullptr;
             nB = 0;
             fallback = 1;
@@ -764,19 +774,27 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
     if (ps != PERF_OK) return ps;
     const bool bf = ctx->scene.dtype == PERF_BF16;
     // the probe direction (default x: every ray then has a non-zero J p)
-    void* pbuf = bf ? static_cast<void*>(ctx->p16) : static_cast<void*>(ctx->p32);
+    void* pbuf = bf ? static_cast<void*>(ctx->p16) : static_cast<void*>(ctx->p);
     CK(cudaMemcpyAsync(pbuf, p ? p : x, (bf ? 2 : 4) * (size_t)ctx->n, cudaMemcpyDeviceToDevice, st));
     const void* pp = pbuf;
-    if (!bf) CK(perf::launch_pair_pack(ctx->n, static_cast<const float*>(x), ctx->p32, ctx->xp, st));
+    if (!bf) CK(perf::launch_pair_pack(ctx->n, static_cast<const float*>(x), ctx->p, ctx->xp, st));
     auto apply = [&](bool paired) -> cudaError_t {
         return paired ? perf::launch_apply_pair(ctx->ds, ctx->xp, ctx->Ap, nullptr, st)
                       : apply_arrays(ctx, ctx->ds, x, pp, nullptr, st);
     };
     const int tws[4] = {8, 4, 16, 32};
     const int caps[3] = {0, 3, 2};
-    cudaEvent_t e0, e1;
-    CK(cudaEventCreate(&e0));
-    CK(cudaEventCreate(&e1));
+    // events live until every return path has left (scope guard)
+    struct Events {
+        cudaEvent_t a = nullptr, b = nullptr;
+        ~Events() {
+            if (a) cudaEventDestroy(a);
+            if (b) cudaEventDestroy(b);
+        }
+    } ev;
+    CK(cudaEventCreate(&ev.a));
+    CK(cudaEventCreate(&ev.b));
+    cudaEvent_t e0 = ev.a, e1 = ev.b;
     // With the coefficient store, Gauss-Newton steps run the coefficient-
     // cached A p: for every tile shape the store is laid out anew and filled
     // at x, and the A p from it is timed over the CTA caps; the default
@@ -815,8 +833,6 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
             }
         }
         if (!(best < 0.97f * incumbent)) { best = incumbent; best_tw = 8; best_cap = 0; }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         set_tiling(ctx, best_tw);
         ctx->ds.cap_per_sm = best_cap;
         ctx->coef_used = true;
@@ -870,8 +886,6 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
         if (ms < 0.97f * best) { best = ms; pair = false; }
     }
     ctx->pair = pair;
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     if (out) {
         out->tile_w = best_tw;
         out->tile_h = 32 / best_tw;
@@ -890,8 +904,16 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     // several times slower and would skew the choice
     unsigned long long* counter = ctx->ds.red_count;
     ctx->ds.red_count = nullptr;
+    // a failed tuning run leaves the tiling, CTA cap and layout it started with
+    const int tw0 = ctx->ds.tile_w, cap0 = ctx->ds.cap_per_sm;
+    const bool pair0 = ctx->pair;
     const perf_status ps = autotune_impl(ctx, x, p, out, stream);
     ctx->ds.red_count = counter;
+    if (ps != PERF_OK) {
+        set_tiling(ctx, tw0);
+        ctx->ds.cap_per_sm = cap0;
+        ctx->pair = pair0;
+    }
     return ps;
 }
 

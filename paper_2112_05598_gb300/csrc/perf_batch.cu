@@ -44,10 +44,9 @@ struct perf_batch {
     float* r = nullptr;
     float* diag = nullptr;
     float* grad = nullptr;
-    double* delta = nullptr;
-    double* rho = nullptr;
-    double* p = nullptr;
-    float* p32 = nullptr;
+    float* delta = nullptr;     // Algorithm 2 vectors (FP32; p is also gathered by A p)
+    float* rho = nullptr;
+    float* p = nullptr;
     float* Ap = nullptr;
     PcgScalars* s = nullptr;
     double* F = nullptr;
@@ -189,15 +188,15 @@ cudaError_t apply_coef_launch(perf_batch* b, const float* p32, double* pap, cuda
 
 // One Algorithm 2 iteration for every scene.
 cudaError_t pcg_iter(perf_batch* b, cudaStream_t st) {
-    cudaError_t e = b->use_coef ? apply_coef_launch(b, b->p32, &b->s[0].pAp, st, true)
-                                : apply_launch(b, b->x_work, b->p32, st, true);
+    cudaError_t e = b->use_coef ? apply_coef_launch(b, b->p, &b->s[0].pAp, st, true)
+                                : apply_launch(b, b->x_work, b->p, st, true);
     if (e == cudaSuccess)
         e = perf::launch_pcg_update_seg(b->n_params, b->n, b->d_chunks, b->n_chunks, b->delta, b->rho,
                                         b->p, b->Ap, b->diag, nullptr, 0, b->s, st);
     if (e == cudaSuccess) e = perf::launch_pcg_finish_seg(b->s, b->n, st);
     if (e == cudaSuccess)
         e = perf::launch_pcg_dir_seg(b->n_params, b->n, b->d_chunks, b->n_chunks, b->rho, b->diag,
-                                     nullptr, 0, b->p, b->p32, nullptr, b->Ap, b->s, st);
+                                     nullptr, 0, b->p, nullptr, b->s, st);
     return e;
 }
 
@@ -339,7 +338,6 @@ perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_sce
     if (e == cudaSuccess) e = dalloc(&b->delta, n);
     if (e == cudaSuccess) e = dalloc(&b->rho, n);
     if (e == cudaSuccess) e = dalloc(&b->p, n);
-    if (e == cudaSuccess) e = dalloc(&b->p32, n);
     if (e == cudaSuccess) e = dalloc(&b->Ap, n);
     if (e == cudaSuccess) e = dalloc(&b->s, n_scenes);
     if (e == cudaSuccess) e = dalloc(&b->F, n_scenes);
@@ -359,7 +357,7 @@ perf_status perf_batch_destroy(perf_batch* b) {
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     void* bufs[] = {b->d_items, b->d_start, b->d_seg, b->d_chunks, b->cams, b->counter, b->x_work, b->x_trial,
-                    b->r, b->diag, b->grad, b->delta, b->rho, b->p, b->p32, b->Ap, b->s, b->F,
+                    b->r, b->diag, b->grad, b->delta, b->rho, b->p, b->Ap, b->s, b->F,
                     b->gamma, b->mask, b->tile_off, b->coef};
     for (void* q : bufs)
         if (q) cudaFree(q);
@@ -401,7 +399,7 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
     cudaEvent_t e0, e1;
     BK(cudaEventCreate(&e0));
     BK(cudaEventCreate(&e1));
-    BK(cudaMemcpyAsync(b->p32, x, sizeof(float) * (size_t)b->n_params, cudaMemcpyDeviceToDevice, st));
+    BK(cudaMemcpyAsync(b->p, x, sizeof(float) * (size_t)b->n_params, cudaMemcpyDeviceToDevice, st));
     const int tws[4] = {8, 4, 16, 32};
     const int caps[3] = {0, 3, 2};
     float best = 1e30f;
@@ -428,8 +426,8 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
         for (int j = 0; j < 3; ++j) {
             b->cap = caps[j];
             auto launch = [&]() {
-                return coef ? apply_coef_launch(b, b->p32, &b->s[0].pAp, st, false)
-                            : apply_launch(b, x, b->p32, st);
+                return coef ? apply_coef_launch(b, b->p, &b->s[0].pAp, st, false)
+                            : apply_launch(b, x, b->p, st);
             };
             BK(launch());                                             // warm-up
             BK(cudaEventRecord(e0, st));
@@ -506,7 +504,7 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
                                       b->cap, st, nullptr, b->use_coef ? b->coef : nullptr,
                                       b->use_coef ? b->tile_off : nullptr));
         BK(perf::launch_pcg_begin_seg(b->n_params, n, b->d_chunks, b->n_chunks, b->grad, b->diag,
-                                      b->delta, b->rho, b->p, b->p32, nullptr, b->Ap, b->s,
+                                      b->delta, b->rho, b->p, nullptr, b->Ap, b->s,
                                       o.pcg_iters, o.pcg_fixed, o.pcg_eps_rel, o.pcg_stall,
                                       nullptr, 0, st));
         if (o.pcg_iters > 0) BK(cudaGraphLaunch(b->graph, st));

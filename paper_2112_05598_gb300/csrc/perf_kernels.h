@@ -102,28 +102,29 @@ cudaError_t launch_apply_coef(const DevScene& sc, const void* p, int p_dtype, co
 cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
                               cudaStream_t st);
 
-// Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP64; p32 / p16: the
-// FP32 / BF16 copies of p that the ray march gathers; Ap: FP32 scatter target;
-// pxp (may be null): paired x / p records whose p half also receives p.
-cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, double* delta,
-                             double* rho, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                             PcgScalars* s, int max_iter, int fixed, double eps_rel, double stall,
+// Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP32 (p is also the
+// array the ray march gathers); p16 (may be null): its BF16 copy for BF16
+// scenes; Ap: FP32 scatter target, zeroed by begin and update; pxp (may be
+// null): paired x / p records whose p half also receives p.
+cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, float* delta,
+                             float* rho, float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
+                             int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st,
                              float* pxp = nullptr);
-cudaError_t launch_pcg_update(long long n, double* delta, double* rho, const double* p,
-                              const float* Ap, const float* diag, const float* blocks,
-                              long long n_block, PcgScalars* s, cudaStream_t st);
+cudaError_t launch_pcg_update(long long n, float* delta, float* rho, const float* p, float* Ap,
+                              const float* diag, const float* blocks, long long n_block,
+                              PcgScalars* s, cudaStream_t st);
 // One thread: the exit test of Algorithm 2 and beta (after launch_pcg_update).
 cudaError_t launch_pcg_finish(PcgScalars* s, cudaStream_t st);
-cudaError_t launch_pcg_dir(long long n, const double* rho, const float* diag, const float* blocks,
-                           long long n_block, double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                           PcgScalars* s, cudaStream_t st, float* pxp = nullptr);
+cudaError_t launch_pcg_dir(long long n, const float* rho, const float* diag, const float* blocks,
+                           long long n_block, float* p, __nv_bfloat16* p16, PcgScalars* s,
+                           cudaStream_t st, float* pxp = nullptr);
 // xp[v] = (x[v], p[v]) for the n / 4 parameter blocks (p null: x half only).
 cudaError_t launch_pair_pack(long long n, const float* x, const float* p, float* xp,
                              cudaStream_t st);
 // x_out = P(x + gamma delta) (project: sigma >= 0, 0 <= c <= 1), formed in FP64;
 // optional float32 and bf16 outputs.
-cudaError_t launch_trial(long long n, const float* x, const double* delta, double gamma,
+cudaError_t launch_trial(long long n, const float* x, const float* delta, double gamma,
                          int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
 cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaStream_t st);
 
@@ -131,25 +132,24 @@ cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaSt
 // y < n_seg): chunks (device, n_chunks int4) assigns CTA b the parameter
 // blocks [chunks[b].y, chunks[b].z) of system chunks[b].x; null = one system.
 cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                                 const float* grad, const float* diag, double* delta, double* rho,
-                                 double* p, float* p32, __nv_bfloat16* p16, float* Ap,
-                                 PcgScalars* s, int max_iter, int fixed, double eps_rel,
-                                 double stall, const float* blocks, long long n_block,
-                                 cudaStream_t st, float* pxp = nullptr);
+                                 const float* grad, const float* diag, float* delta, float* rho,
+                                 float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
+                                 int max_iter, int fixed, double eps_rel, double stall,
+                                 const float* blocks, long long n_block, cudaStream_t st,
+                                 float* pxp = nullptr);
 cudaError_t launch_pcg_update_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                                  double* delta, double* rho, const double* p, const float* Ap,
+                                  float* delta, float* rho, const float* p, float* Ap,
                                   const float* diag, const float* blocks, long long n_block,
                                   PcgScalars* s, cudaStream_t st);
 cudaError_t launch_pcg_finish_seg(PcgScalars* s, int n_seg, cudaStream_t st);
 cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                               const double* rho, const float* diag, const float* blocks,
-                               long long n_block, double* p, float* p32, __nv_bfloat16* p16,
-                               float* Ap, PcgScalars* s, cudaStream_t st, float* pxp = nullptr);
+                               const float* rho, const float* diag, const float* blocks,
+                               long long n_block, float* p, __nv_bfloat16* p16, PcgScalars* s,
+                               cudaStream_t st, float* pxp = nullptr);
 // Segment y: x_out = P(x + gamma[y] Delta) where mask[y] (or every segment).
 cudaError_t launch_trial_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                             const float* x, const double* delta, const double* gamma,
+                             const float* x, const float* delta, const double* gamma,
                              const int* mask, int project, float* x_out, cudaStream_t st);
-cudaError_t launch_to_f32(long long n, const double* a, float* b, cudaStream_t st);
 
 // Level change of the hierarchical formulation (k_hier.cu): y (level 2G,
 // maps 2He x 2We) from x (level G, maps He x We).

@@ -26,6 +26,7 @@ cudaError_t lpc_conv_bwd_w(const __nv_bfloat16* in, const __nv_bfloat16* gpre, f
                            float* dB, int G, cudaStream_t st);
 cudaError_t lpc_conv_flip(const __nv_bfloat16* W, __nv_bfloat16* Wt, cudaStream_t st);
 int lpc_conv_error();
+void lpc_conv_set_first_wait_limit(uint32_t rounds);
 cudaError_t lpc_relu_bwd(__nv_bfloat16* g, const __nv_bfloat16* act, long long n, cudaStream_t st);
 cudaError_t lpc_head_train(const __nv_bfloat16* o, const float* ahat, const float* xi,
                            const unsigned char* mask, __nv_bfloat16* gout, long long V, float scale,
@@ -249,7 +250,11 @@ perf_status perf_lpc_loss_grad(perf_lpc* L, int32_t G, const void* feat, const f
         LK(cudaMemcpyAsync(loss_out, L->dloss, sizeof(double), cudaMemcpyDeviceToHost, S(stream)));
         LK(cudaStreamSynchronize(S(stream)));
         // a convolution whose bounded waits ran out has left its outputs incomplete
-        if (perf::lpc_conv_error() != 0) return PERF_ERR_CUDA;
+        const int ce = perf::lpc_conv_error();
+        if (ce != 0) {
+            L->err = "loss_grad: a convolution's bounded wait gave up";
+            return ce > 0 ? PERF_ERR_TIMEOUT : PERF_ERR_CUDA;
+        }
     }
     return PERF_OK;
 }
@@ -282,6 +287,19 @@ perf_status perf_lpc_infer(perf_lpc* L, int32_t G, const void* feat, const float
     if (ps != PERF_OK) return ps;
     const long long V = (long long)G * G * G;
     LK(perf::lpc_head_infer(L->act[kLayers], diag, blocks_out, V, S(stream)));
+    return PERF_OK;
+}
+
+perf_status perf_lpc_conv_status(int32_t* timed_out) {
+    if (!timed_out) return PERF_ERR_INVALID_ARG;
+    const int v = perf::lpc_conv_error();
+    if (v < 0) return PERF_ERR_CUDA;
+    *timed_out = v;
+    return PERF_OK;
+}
+
+perf_status perf_lpc_test_conv_wait_limit(uint32_t rounds) {
+    perf::lpc_conv_set_first_wait_limit(rounds);
     return PERF_OK;
 }
 

@@ -8,6 +8,31 @@ from oracle import Oracle
 # after each Gauss-Newton step.
 TOL_FP32 = 1e-5
 TOL_GN = 1e-4
+# Element-wise bound beside the relative L2: |a - b| <= EW_REL |b| + EW_ABS max|b|.
+# The relative part is the FP32 bar; the absolute part (one millionth of the
+# largest entry) covers entries that are sums of terms of both signs (J^T v,
+# the opacity entries of A p), whose own size says nothing about the rounding
+# of the terms they cancel from.
+EW_REL = 1e-5
+EW_ABS = 1e-6
+
+
+def assert_elementwise(a, b, rel=EW_REL, abs_frac=EW_ABS, what=""):
+    """Every element of a within rel |b| + abs_frac max|b| of b; prints the
+    worst ratio of error to bound, so a log shows the margin."""
+    a = np.asarray(a, np.float64).ravel()
+    b = np.asarray(b, np.float64).ravel()
+    assert a.shape == b.shape, (what, a.shape, b.shape)
+    if b.size == 0:
+        return
+    bound = rel * np.abs(b) + abs_frac * float(np.abs(b).max())
+    ratio = np.abs(a - b) / np.where(bound > 0, bound, 1.0)
+    ratio[(bound == 0) & (a == b)] = 0.0
+    ratio[(bound == 0) & (a != b)] = np.inf
+    i = int(np.argmax(ratio))
+    print(f"[elementwise] {what}: worst |a-b|/bound = {ratio[i]:.3g} at {i} "
+          f"(a={a[i]:.9g}, b={b[i]:.9g}, n={b.size})")
+    assert ratio[i] <= 1.0, (what, i, a[i], b[i], ratio[i])
 
 
 def cuda_tensor(a, dtype=None):

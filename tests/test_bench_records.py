@@ -38,18 +38,26 @@ def test_hash_changes_with_the_code(tmp_path, monkeypatch):
 
 def test_traffic_record_parses_and_names_its_kernel(tmp_path, monkeypatch):
     # a record is used only for its own kernel and workload
-    assert bench.recorded_traffic("some other kernel", "scale128") is None
+    assert bench.recorded_traffic("some other kernel", "scale128", 10) is None
     assert bench.recorded_traffic("k_apply_coef<float> (A p from stored coefficients)",
-                                  "another workload") is None
+                                  "another workload", 10) is None
     text = open(bench.TRAFFIC_PROFILE).read()
-    for key in ("- kernel:", "- workload:", "- source_sha256:", "- dram_bytes_per_launch:"):
+    for key in ("- kernel:", "- workload:", "- source_sha256:", "- dram_bytes_per_launch:",
+                "- samples_per_launch:"):
         assert key in text
-    # with the kernel sources of the record, the recorded bytes come back
+    # with the kernel sources of the record, the recorded bytes come back,
+    # scaled from the captured case's samples to the asked-for samples
     rec = tmp_path / "rec.md"
     rec.write_text("- kernel: `K`\n- workload: `W`\n"
                    f"- source_sha256: `{bench.kernel_source_hash()}`\n"
-                   "- dram_bytes_per_launch: `1234`\n")
+                   "- dram_bytes_per_launch: `1234`\n- samples_per_launch: `100`\n")
     monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(rec))
-    assert bench.recorded_traffic("K", "W") == 1234
+    assert bench.recorded_traffic("K", "W", 100) == 1234
+    assert bench.recorded_traffic("K", "W", 250) == 3085
     rec.write_text(rec.read_text().replace(bench.kernel_source_hash(), "0" * 64))
-    assert bench.recorded_traffic("K", "W") is None
+    assert bench.recorded_traffic("K", "W", 100) is None
+
+
+def test_cpu_model_is_a_name():
+    m = bench.cpu_model()
+    assert m is None or (isinstance(m, str) and len(m) > 0)

@@ -9,8 +9,8 @@ import numpy as np
 import pytest
 
 from conftest import rel_l2, tiny_problem
-from gpu_common import (TOL_FP32, TOL_GN, cuda_tensor, empty, host, make_pair,
-                        mid_state, pair_from_scene)
+from gpu_common import (TOL_FP32, TOL_GN, assert_elementwise, cuda_tensor, empty, host,
+                        make_pair, mid_state, pair_from_scene)
 
 pytestmark = pytest.mark.gpu
 
@@ -41,6 +41,8 @@ def test_render_parity(small):
     assert rel_l2(rgb, ref) < TOL_FP32
     assert rel_l2(T, Tref) < TOL_FP32
     assert np.abs(rgb - ref.ravel()).max() < 1e-4
+    assert_elementwise(rgb, ref, what="render")
+    assert_elementwise(T, Tref, what="T at grid exit")
 
 
 def test_residual_and_objective_parity(small):
@@ -51,6 +53,7 @@ def test_residual_and_objective_parity(small):
     ctx.residual(cuda_tensor(x), cuda_tensor(target), r, F)
     rref, Fref = orc.residual(x.astype(np.float64), target)
     assert rel_l2(host(r), rref) < TOL_FP32
+    assert_elementwise(host(r), rref, what="residual")
     assert abs(host(F)[0] - Fref) <= 1e-5 * Fref
     # F only (no residual buffer)
     ctx.residual(cuda_tensor(x), cuda_tensor(target), None, F)
@@ -64,6 +67,7 @@ def test_jvp_parity(small):
     ctx.jvp(cuda_tensor(x), cuda_tensor(p), out)
     ref = orc.jvp(x.astype(np.float64), p.astype(np.float64))
     assert rel_l2(host(out), ref) < TOL_FP32
+    assert_elementwise(host(out), ref, what="J p")
 
 
 def test_vjp_parity(small):
@@ -73,6 +77,7 @@ def test_vjp_parity(small):
     ctx.vjp(cuda_tensor(x), cuda_tensor(v), out)
     ref = orc.vjp(x.astype(np.float64), v.astype(np.float64))
     assert rel_l2(host(out), ref) < TOL_FP32
+    assert_elementwise(host(out), ref, what="J^T v")
     # accumulate = 1 adds onto the output
     ctx.vjp(cuda_tensor(x), cuda_tensor(v), out, accumulate=True)
     assert rel_l2(host(out), 2 * ref) < TOL_FP32
@@ -88,6 +93,8 @@ def test_diag_and_gradient_parity(small):
     dref, gref = orc.diag_grad(x.astype(np.float64), rref.astype(np.float32).astype(np.float64))
     assert rel_l2(host(d), dref) < TOL_FP32
     assert rel_l2(host(g), gref) < TOL_FP32
+    assert_elementwise(host(d), dref, what="diag")
+    assert_elementwise(host(g), gref, what="grad")
     # diagonal alone
     d2 = empty(ctx.n_params)
     ctx.diag_jtj(cuda_tensor(x), d2)
@@ -103,6 +110,7 @@ def test_apply_normal_parity(small):
     ctx.apply_normal(cuda_tensor(x), cuda_tensor(p), ap, pap)
     ref = orc.apply_A(x.astype(np.float64), p.astype(np.float64))
     assert rel_l2(host(ap), ref) < TOL_FP32
+    assert_elementwise(host(ap), ref, what="A p")
     jp = orc.jvp(x.astype(np.float64), p.astype(np.float64))
     assert abs(host(pap)[0] - float(jp @ jp)) <= 1e-5 * float(jp @ jp)
 
@@ -196,19 +204,31 @@ def test_gn_steps_parameter_parity(small, coef):
 
 
 def test_gn_steps_20_pcg_iterations(small):
-    """The configured 5 GN x 20 PCG iterations: every step is accepted on both
-    sides, F agrees, and the rendered image after each step agrees within
-    1e-2 relative L2 (20 FP32 CG iterations on this system amplify A p
-    rounding in weakly observed directions; the parameters are compared at
-    3 iterations in test_gn_steps_parameter_parity)."""
+    """The configured 5 GN x 20 PCG iterations, each GPU step against one
+    oracle step from the same x.  What 20 iterations determine is pinned on
+    the oracle itself (test_cg_sensitivity_after_the_first_step): the first
+    step (from the constant start) is held to 1e-2 on F after the step and on
+    the rendered image, every later step to the parameter bar 1e-4 and to 1e-4
+    on F and the image.  At least four of the five steps must be compared
+    (a step whose line search ends on a near-tie of mu may take a different
+    gamma on the two sides and is skipped)."""
     orc = small["orc"]
+    checked = 0
     for step, (st, ref, xg, tie) in enumerate(_gn_trajectory(small, 20, small["sc"].cfg.gn_steps)):
         assert st["accepted"] and ref.accepted
-        assert abs(st["F_before"] - ref.F_before) <= 1e-2 * ref.F_before
+        assert abs(st["F_before"] - ref.F_before) <= TOL_FP32 * ref.F_before
         if abs(st["gamma"] - ref.gamma) > 1e-9:
             continue
-        assert abs(st["F_after"] - ref.F_after) <= 1e-2 * ref.F_after
-        assert rel_l2(orc.render(xg)[0], orc.render(ref.x)[0]) < 1e-2
+        tol = 1e-2 if step == 0 else 1e-4
+        dF = abs(st["F_after"] - ref.F_after) / ref.F_after
+        dimg = rel_l2(orc.render(xg)[0], orc.render(ref.x)[0])
+        dx = rel_l2(xg, ref.x)
+        print(f"20-iteration GN step {step}: x {dx:.3e}, F_after {dF:.3e}, image {dimg:.3e}")
+        assert dF <= tol and dimg <= tol, (step, dF, dimg)
+        if step > 0:
+            assert dx < TOL_GN, (step, dx)
+        checked += 1
+    assert checked >= 4
 
 
 def test_jitter_parity():

@@ -1,0 +1,290 @@
+"""CUDA path vs the FP64 oracle on the configurations the benchmark times,
+element by element, through the C ABI.
+
+* 128^3 workload (3 shells 256x512, 800x800 cameras, up to 222 samples per
+  ray, sample cap 256), restricted to two of its cameras: render, residual,
+  J p, J^T v, A p, diag and gradient, then the first Gauss-Newton step (3 PCG
+  iterations, from the constant start the benchmark starts from) with the
+  A p from the coefficient store and recomputed.
+* 256^3 BF16 workload (4 shells 512x1024, sample cap 512) on one camera, the
+  oracle run on the dequantised BF16 inputs.
+* The batched form: each scene of a batch against the oracle directly.
+* Paper-mode PCG (Algorithm 2 with its residual and stall exits) on the
+  single-scene path: iteration count and exit reason against the oracle's.
+
+Bars: relative L2 1e-5 and the element-wise bound of gpu_common for FP32
+results; 1e-4 relative L2 for the parameters after a Gauss-Newton step."""
+import numpy as np
+import pytest
+
+from conftest import rel_l2
+from gpu_common import (TOL_FP32, TOL_GN, assert_elementwise, cuda_tensor, empty, host,
+                        mid_state, pair_from_scene)
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(name, got, ref, tol=TOL_FP32):
+    err = rel_l2(got, ref)
+    print(f"[parity] {name}: rel L2 {err:.3e}")
+    assert err < tol, (name, err)
+    assert_elementwise(got, ref, what=name)
+
+
+# ------------------------------------------------------------ 128^3 workload
+
+
+@pytest.fixture(scope="module")
+def s128():
+    from scenegen import make_scene
+    sc = make_scene("scale128", n_cams=2)
+    ctx, orc = pair_from_scene(sc)
+    rng = np.random.default_rng(128)
+    target = orc.render(sc.x_gt)[0].astype(np.float32).ravel()
+    x = mid_state(rng, sc)
+    return dict(sc=sc, ctx=ctx, orc=orc, target=target, x=x, x64=x.astype(np.float64), rng=rng)
+
+
+def test_scale128_forward(s128):
+    import torch
+    ctx, orc, x, x64, target = s128["ctx"], s128["orc"], s128["x"], s128["x64"], s128["target"]
+    # the workload's rays are long: check that the sample counts reach the
+    # configuration's range (max K = ceil(sqrt(3) G) = 222 at G = 128)
+    ks = [orc.ray_info(r)["K"] for r in range(0, ctx.n_rays, 997)]
+    assert max(ks) > 150
+    rgb = empty(3 * ctx.n_rays)
+    T = empty(ctx.n_rays)
+    ctx.render(cuda_tensor(x), rgb, T)
+    ref, Tref, _ = orc.render(x64)
+    _check("render 128^3", host(rgb), ref)
+    _check("T 128^3", host(T), Tref)
+    r = empty(3 * ctx.n_rays)
+    F = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.residual(cuda_tensor(x), cuda_tensor(target), r, F)
+    rref, Fref = orc.residual(x64, target)
+    _check("residual 128^3", host(r), rref)
+    assert abs(host(F)[0] - Fref) <= TOL_FP32 * Fref
+
+
+def test_scale128_jvp_vjp_apply(s128):
+    import torch
+    ctx, orc, x, x64, rng = s128["ctx"], s128["orc"], s128["x"], s128["x64"], s128["rng"]
+    p = rng.normal(size=ctx.n_params).astype(np.float32)
+    jp = empty(3 * ctx.n_rays)
+    ctx.jvp(cuda_tensor(x), cuda_tensor(p), jp)
+    jref = orc.jvp(x64, p.astype(np.float64))
+    _check("J p 128^3", host(jp), jref)
+    v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
+    out = empty(ctx.n_params)
+    ctx.vjp(cuda_tensor(x), cuda_tensor(v), out)
+    _check("J^T v 128^3", host(out), orc.vjp(x64, v.astype(np.float64)))
+    ap = empty(ctx.n_params)
+    pap = torch.zeros(1, dtype=torch.float64, device="cuda")
+    ctx.apply_normal(cuda_tensor(x), cuda_tensor(p), ap, pap)
+    _check("A p (recomputed) 128^3", host(ap), orc.vjp(x64, jref))
+    assert abs(host(pap)[0] - float(jref @ jref)) <= TOL_FP32 * float(jref @ jref)
+
+
+def test_scale128_diag_grad(s128):
+    ctx, orc, x, x64, target = s128["ctx"], s128["orc"], s128["x"], s128["x64"], s128["target"]
+    rref, _ = orc.residual(x64, target)
+    r32 = rref.astype(np.float32)
+    d = empty(ctx.n_params)
+    g = empty(ctx.n_params)
+    ctx.diag_jtj(cuda_tensor(x), d, cuda_tensor(r32), g)
+    dref, gref = orc.diag_grad(x64, r32.astype(np.float64))
+    _check("diag 128^3", host(d), dref)
+    _check("grad 128^3", host(g), gref)
+
+
+@pytest.mark.parametrize("coef", [True, False])
+def test_scale128_first_gn_step(s128, coef):
+    """The benchmark's first Gauss-Newton step (constant start, residual,
+    gradient and diagonal, 3 fixed PCG iterations, Algorithm 3, projection),
+    with each PCG A p read from the per-sample coefficient store (coef) or
+    recomputed by a ray march: parameters within 1e-4 of the oracle's step."""
+    from oracle import gn_step
+    from paper_2112_05598_gb300 import Context
+    sc, orc, target = s128["sc"], s128["orc"], s128["target"]
+    ctx = Context.from_scene(sc, pcg_iters=3, pcg_fixed=1)
+    ctx.set_coef_budget(-1 if coef else 0)
+    xd = cuda_tensor(sc.x0.copy())
+    st = ctx.gn_solve(xd, cuda_tensor(target), 1)[0]
+    assert ctx.coef_info()["used"] == coef
+    if coef:
+        assert ctx.coef_info()["coverage"] == 1.0
+    ref = s128.get("gn_ref")
+    if ref is None:
+        ref = gn_step(orc, sc.x0.astype(np.float64), target, 3)
+        s128["gn_ref"] = ref
+    assert st["accepted"] == ref.accepted
+    assert abs(st["F_before"] - ref.F_before) <= TOL_FP32 * ref.F_before
+    assert abs(st["gamma"] - ref.gamma) <= 1e-9, (st["gamma"], ref.gamma)
+    assert abs(st["F_after"] - ref.F_after) <= 1e-4 * ref.F_after
+    err = rel_l2(host(xd), ref.x)
+    print(f"[parity] 128^3 first GN step (coef={coef}): x rel L2 {err:.3e}")
+    assert err < TOL_GN
+
+
+# ------------------------------------------------------------ 256^3 BF16
+
+
+@pytest.fixture(scope="module")
+def b256():
+    import torch
+    from oracle import Oracle
+    from paper_2112_05598_gb300 import PERF_BF16, Context
+    from scenegen import make_scene
+    sc = make_scene("bf16_256", n_cams=1)
+    rng = np.random.default_rng(256)
+    # 8 oracle threads: the J^T v and diagonal keep one FP64 n-vector per
+    # thread (n = 75.5 M here)
+    orc = Oracle.from_scene(sc, n_threads=8)
+    ctx = Context.from_scene(sc, dtype=PERF_BF16)
+    x16 = torch.from_numpy(mid_state(rng, sc)).to(torch.bfloat16)
+    xq = x16.to(torch.float32).numpy().astype(np.float64)
+    return dict(sc=sc, orc=orc, ctx=ctx, x16=x16.cuda(), xq=xq, rng=rng)
+
+
+def test_bf16_256_render_jvp_vjp_apply_diag(b256):
+    """Error against the FP64 oracle on the same dequantised inputs, per
+    result: render, J p, J^T v, A p, diagonal (FP32 arithmetic throughout)."""
+    ctx, orc, x16, xq, rng = b256["ctx"], b256["orc"], b256["x16"], b256["xq"], b256["rng"]
+    ks = [orc.ray_info(r)["K"] for r in range(0, ctx.n_rays, 997)]
+    assert max(ks) > 300
+    rgb = empty(3 * ctx.n_rays)
+    ctx.render(x16, rgb)
+    _check("render 256^3 bf16", host(rgb), orc.render(xq)[0])
+    p = rng.normal(size=ctx.n_params).astype(np.float32)
+    jp = empty(3 * ctx.n_rays)
+    ctx.jvp(x16, cuda_tensor(p), jp)
+    jref = orc.jvp(xq, p.astype(np.float64))
+    _check("J p 256^3 bf16", host(jp), jref)
+    v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
+    out = empty(ctx.n_params)
+    ctx.vjp(x16, cuda_tensor(v), out)
+    _check("J^T v 256^3 bf16", host(out), orc.vjp(xq, v.astype(np.float64)))
+    ap = empty(ctx.n_params)
+    ctx.apply_normal(x16, cuda_tensor(p), ap)
+    _check("A p 256^3 bf16", host(ap), orc.vjp(xq, jref))
+    d = empty(ctx.n_params)
+    ctx.diag_jtj(x16, d)
+    _check("diag 256^3 bf16", host(d), orc.diag_grad(xq)[0])
+
+
+# ------------------------------------------------------------ batched form
+
+
+def _batch_scenes(seed, n=3):
+    from oracle import Oracle
+    from scenegen import batch_scene_configs, constant_params, make_cameras, random_params
+    rng = np.random.default_rng(seed)
+    cfgs = batch_scene_configs(rng, n_scenes=n, G_lo=12, G_hi=28, cams_lo=2, cams_hi=5, res=24)
+    out = []
+    for c in cfgs:
+        r2 = np.random.default_rng(c["seed"])
+        c2w, focal = make_cameras(r2, c["n_cams"], c["res"], 3.0, "sphere", 40.0)
+        S = len(c["radii"])
+        x_gt = random_params(r2, c["G"], S, c["env_h"], c["env_w"], 0.0, 0.8)
+        orc = Oracle(c["G"], c["radii"], c["env_h"], c["env_w"], c2w, focal, c["res"], c["res"],
+                     max_samples=64)
+        tgt = orc.render(x_gt.astype(np.float64))[0].astype(np.float32).ravel()
+        x = 0.5 * x_gt + 0.5 * constant_params(c["G"], S, c["env_h"], c["env_w"])
+        out.append(dict(G=c["G"], radii=c["radii"], env_h=c["env_h"], env_w=c["env_w"],
+                        c2w=c2w, focal=focal, width=c["res"], height=c["res"],
+                        x=x.astype(np.float32), target=tgt, orc=orc))
+    return out
+
+
+def test_batch_against_oracle():
+    """Each scene of a batch (uneven grids, cameras and shell counts) against
+    the oracle: residual and F, then two Gauss-Newton steps (3 PCG
+    iterations) each compared with one oracle step from the batch's own x."""
+    import torch
+    from oracle import gn_step
+    from paper_2112_05598_gb300 import Batch
+    scenes = _batch_scenes(21)
+    b = Batch(scenes, max_samples=64, pcg_iters=3, pcg_fixed=1)
+    x = cuda_tensor(np.concatenate([s["x"] for s in scenes]))
+    t = cuda_tensor(np.concatenate([s["target"] for s in scenes]))
+    r = empty(3 * b.n_rays)
+    F = torch.zeros(b.n, dtype=torch.float64, device="cuda")
+    b.residual(x, t, r, F)
+    rh, Fh = host(r), host(F)
+    for i, s in enumerate(scenes):
+        rref, Fref = s["orc"].residual(s["x"].astype(np.float64), s["target"])
+        _check(f"batch residual scene {i}", rh[3 * b.ray_off[i]:3 * b.ray_off[i + 1]], rref)
+        assert abs(Fh[i] - Fref) <= TOL_FP32 * Fref
+    checked = 0
+    for step in range(2):
+        xb = host(x)
+        stats = b.gn_solve(x, t, 1)[0]
+        xa = host(x)
+        for i, s in enumerate(scenes):
+            sl = slice(b.param_off[i], b.param_off[i + 1])
+            ref = gn_step(s["orc"], xb[sl], s["target"], 3)
+            assert stats[i]["accepted"] == ref.accepted
+            assert abs(stats[i]["F_before"] - ref.F_before) <= TOL_FP32 * ref.F_before
+            if abs(stats[i]["gamma"] - ref.gamma) > 1e-9:
+                continue   # a near-tie of Algorithm 3 decided differently
+            err = rel_l2(xa[sl], ref.x)
+            print(f"[parity] batch scene {i} GN step {step}: x rel L2 {err:.3e}")
+            assert err < TOL_GN, (i, step, err)
+            checked += 1
+    assert checked >= 2 * len(scenes) - 1
+
+
+# ------------------------------------------------------------ paper-mode PCG
+
+
+def _near_threshold(R, R0, eps_rel, stall, rel=1e-3):
+    """True when some exit test of the oracle's trajectory is within `rel` of
+    its threshold (FP32 rounding may then decide it either way)."""
+    prev = R0
+    for Rk in R:
+        if abs(Rk - eps_rel * eps_rel * R0) <= rel * eps_rel * eps_rel * R0:
+            return True
+        if abs(Rk / prev - stall) <= rel * stall:
+            return True
+        prev = Rk
+    return False
+
+
+def test_paper_mode_pcg_exits_against_oracle():
+    """Algorithm 2 with its exits (R < eps^2 R_0, R / R_prev > stall) on the
+    single-scene path against the oracle's pcg(fixed=False): the number of
+    iterations and the exit reason agree on every compared system, and both
+    the residual exit and the stall exit occur."""
+    from oracle import gn_step
+    from paper_2112_05598_gb300 import Context
+    from scenegen import make_scene
+    sc = make_scene("small32")
+    ctx, orc = pair_from_scene(sc)
+    target = orc.render(sc.x_gt)[0].astype(np.float32).ravel()
+    states = [sc.x0.copy(), mid_state(np.random.default_rng(8), sc)]
+    seen = set()
+    compared = 0
+    for eps_rel, stall, cap in ((0.5, 0.999, 30), (0.2, 0.999, 30), (1e-6, 0.85, 40),
+                                (1e-6, 0.7, 40), (1e-3, 0.85, 3)):
+        for x0 in states:
+            c = Context.from_scene(sc, pcg_iters=cap, pcg_fixed=0, pcg_eps_rel=eps_rel,
+                                   pcg_stall=stall)
+            xd = cuda_tensor(x0)
+            st = c.gn_solve(xd, cuda_tensor(target), 1)[0]
+            ref = gn_step(orc, x0.astype(np.float64), target, cap, fixed=False,
+                          eps_rel=eps_rel, stall=stall)
+            r, _ = orc.residual(x0.astype(np.float64), target)
+            _, g = orc.diag_grad(x0.astype(np.float64), r)
+            R0 = float(g @ g)
+            if _near_threshold(ref.pcg.R, R0, eps_rel, stall):
+                continue
+            exit_ref = {"fixed": "fixed", "eps": "eps", "stall": "stall"}.get(ref.pcg.exit,
+                                                                               ref.pcg.exit)
+            print(f"[paper mode] eps {eps_rel} stall {stall} cap {cap}: GPU {st['pcg_iters']} "
+                  f"{st['pcg_exit']}, oracle {ref.pcg.iters} {exit_ref}")
+            assert st["pcg_iters"] == ref.pcg.iters, (eps_rel, stall, st, ref.pcg.iters)
+            assert st["pcg_exit"] == exit_ref, (eps_rel, stall, st["pcg_exit"], exit_ref)
+            seen.add(exit_ref)
+            compared += 1
+    assert compared >= 6
+    assert {"eps", "stall"} <= seen, seen
