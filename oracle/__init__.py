@@ -351,6 +351,7 @@ class GNStep:
     pcg: PCGResult
     trace: list
     delta: np.ndarray
+    diag: np.ndarray = None     # the Jacobi diagonal of the step's system
 
 
 def gn_step(orc: Oracle, x, target, pcg_iters: int, fixed: bool = True,
@@ -372,7 +373,7 @@ def gn_step(orc: Oracle, x, target, pcg_iters: int, fixed: bool = True,
     accepted = mu < F
     x_new = P(x + gamma * delta) if accepted else x.copy()
     return GNStep(x=x_new, F_before=F, F_after=mu if accepted else F, gamma=gamma,
-                  accepted=accepted, pcg=res, trace=trace, delta=delta)
+                  accepted=accepted, pcg=res, trace=trace, delta=delta, diag=diag)
 
 
 def psnr(rgb: np.ndarray, target: np.ndarray) -> float:

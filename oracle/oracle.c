@@ -27,9 +27,11 @@
  *   - Interpolation is exact trilinear (grid) / bilinear (shells), clamped to
  *     the edge, in place of texture hardware.
  *   - The ray itself (pixel -> origin and unit direction, the box entry and
- *     exit, K, delta, and which shells are hit) is defined in IEEE binary32
- *     without contraction, the precision in which the kernels take these
- *     integer decisions; every later quantity is FP64.
+ *     exit, K, delta, and which shells are hit) and each grid sample's index
+ *     coordinates are defined in IEEE binary32 (ray set-up without
+ *     contraction; the sample coordinates by single-rounding fmaf), the
+ *     precision in which the kernels take these integer decisions (K, hits,
+ *     the sample's cell); every later quantity is FP64.
  *   - Jitter uses SplitMix64 (Steele, Lea, Flood 2014) of (seed, epoch, ray,
  *     stream); it is fixed within one Gauss-Newton step.
  *
@@ -166,12 +168,15 @@ typedef struct {
     double sigma, c[3], dbar;
 } oc_sample;
 
-static void oc_trilinear(const oc_problem* P, const double p[3], oc_sample* s) {
+/* Trilinear interpolation at grid index coordinates u[3] (voxel i centred at
+ * u = i): clamped to [0, G-1], cell base floor(u) (at most G-2), fractions
+ * u - base. */
+static void oc_trilinear(const oc_problem* P, const float u_in[3], oc_sample* s) {
     const int G = P->G;
     int64_t b[3];
     double f[3];
     for (int a = 0; a < 3; ++a) {
-        double u = (p[a] + 1.0) * (0.5 * G) - 0.5;
+        double u = (double)u_in[a];
         if (u < 0.0) u = 0.0;
         if (u > (double)(G - 1)) u = (double)(G - 1);
         double fl = floor(u);
@@ -188,6 +193,22 @@ static void oc_trilinear(const oc_problem* P, const double p[3], oc_sample* s) {
         s->w[c] = (cx ? f[0] : 1.0 - f[0]) * (cy ? f[1] : 1.0 - f[1]) *
                   (cz ? f[2] : 1.0 - f[2]);
     }
+}
+
+/* Grid index coordinates of sample k of a ray, in binary32 (each fmaf
+ * rounded once): t_k = t_in + (k + 1/2 + j_k) delta, position o + t_k d,
+ * u = position * G/2 + (G/2 - 1/2) (voxel i centred at -1 + (i + 1/2) h).
+ * These coordinates decide the sample's cell, an integer, so they are
+ * defined in the precision in which the kernels take that decision; the
+ * interpolation and everything after it is FP64. */
+static void oc_sample_coords(const oc_problem* P, const oc_ray* R, int64_t ray, int k,
+                             float u[3]) {
+    float jk = 0.0f;
+    if (P->jitter) jk = oc_uniform(P, ray, 2u + (uint32_t)k) - 0.5f;
+    const float kk = ((float)k + 0.5f) + jk;
+    const float t = fmaf(kk, R->delta, R->t_in);
+    const float hg = 0.5f * (float)P->G;
+    for (int a = 0; a < 3; ++a) u[a] = fmaf(fmaf(t, R->d[a], R->o[a]), hg, hg - 0.5f);
 }
 
 static void oc_bilinear(const oc_problem* P, int shell, const double q[3],
@@ -239,11 +260,9 @@ static int oc_collect(const oc_problem* P, const double* x, int64_t ray,
     const double dbar = delta * (0.5 * P->G); /* delta / h */
     int n = 0;
     for (int k = 0; k < R.K; ++k) {
-        double jk = 0.0;
-        if (P->jitter) jk = (double)oc_uniform(P, ray, 2u + (uint32_t)k) - 0.5;
-        const double t = (double)R.t_in + ((double)k + 0.5 + jk) * delta;
-        const double p[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
-        oc_trilinear(P, p, &out[n]);
+        float u[3];
+        oc_sample_coords(P, &R, ray, k, u);
+        oc_trilinear(P, u, &out[n]);
         oc_interp(x, &out[n]);
         out[n].dbar = dbar;
         ++n;

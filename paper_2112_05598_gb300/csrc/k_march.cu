@@ -323,22 +323,45 @@ struct DiagSink {
     }
 };
 
+// Slots whose voxel changes when the window moves from base b to nb (bit p
+// for slot p).  Along axis a the slot with parity bit q holds the voxel of
+// parity q in [b_a, b_a + 1]; it changes iff that coordinate differs in
+// [nb_a, nb_a + 1].  The slots of parity q along x are 0x55 (q = 0) and 0xAA
+// (q = 1), along y 0x33 / 0xCC, along z 0x0F / 0xF0.
+__device__ __forceinline__ unsigned evict_mask(const int (&b)[3], const int (&nb)[3]) {
+    const unsigned pat[3][2] = {{0x55u, 0xAAu}, {0x33u, 0xCCu}, {0x0Fu, 0xF0u}};
+    unsigned m = 0u;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (par_coord(b[a], 0) != par_coord(nb[a], 0)) m |= pat[a][0];
+        if (par_coord(b[a], 1) != par_coord(nb[a], 1)) m |= pat[a][1];
+    }
+    return m;
+}
+
 // Move the window (all lanes; `on` = this lane moves) to base nb, handing the
 // voxels that leave it to the sink.  A voxel never re-enters a ray's window:
-// its trilinear support meets the ray in one run of samples.
+// its trilinear support meets the ray in one run of samples.  Only the slots
+// that some lane of the warp evicts are visited (a warp-uniform mask), so
+// the common step -- each lane evicts two slots or none -- skips most of the
+// eight.
 template <int NV, class Sink>
 __device__ __forceinline__ void win_move(Window<NV>& w, const int (&nb)[3], bool on, int G, Sink& sk) {
+    const unsigned m = on ? evict_mask(w.b, nb) : 0u;
+    const unsigned any = __reduce_or_sync(kFull, m);
+    if (any != 0u) {
 #pragma unroll
-    for (int p = 0; p < 8; ++p) {
-        const int ox = par_coord(w.b[0], p & 1), oy = par_coord(w.b[1], (p >> 1) & 1),
-                  oz = par_coord(w.b[2], p >> 2);
-        const int nx = par_coord(nb[0], p & 1), ny = par_coord(nb[1], (p >> 1) & 1),
-                  nz = par_coord(nb[2], p >> 2);
-        const bool ev = on && (ox != nx || oy != ny || oz != nz);
-        sk.put(ev, sk.km.key(ox, oy, oz), w.v[p]);
-        if (ev) {
+        for (int p = 0; p < 8; ++p) {
+            if (any & (1u << p)) {
+                const bool ev = (m >> p) & 1u;
+                sk.put(ev, sk.km.key(par_coord(w.b[0], p & 1), par_coord(w.b[1], (p >> 1) & 1),
+                                     par_coord(w.b[2], p >> 2)),
+                       w.v[p]);
+                if (ev) {
 #pragma unroll
-            for (int q = 0; q < NV; ++q) w.v[p][q] = 0.0f;
+                    for (int q = 0; q < NV; ++q) w.v[p][q] = 0.0f;
+                }
+            }
         }
     }
     if (on) { w.b[0] = nb[0]; w.b[1] = nb[1]; w.b[2] = nb[2]; }

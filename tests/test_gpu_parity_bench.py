@@ -18,8 +18,8 @@ import numpy as np
 import pytest
 
 from conftest import rel_l2
-from gpu_common import (TOL_FP32, TOL_GN, assert_elementwise, cuda_tensor, empty, host,
-                        mid_state, pair_from_scene)
+from gpu_common import (TOL_FP32, TOL_GN, assert_elementwise, assert_params, cuda_tensor, empty,
+                        host, mid_state, pair_from_scene)
 
 pytestmark = pytest.mark.gpu
 
@@ -102,7 +102,8 @@ def test_scale128_first_gn_step(s128, coef):
     """The benchmark's first Gauss-Newton step (constant start, residual,
     gradient and diagonal, 3 fixed PCG iterations, Algorithm 3, projection),
     with each PCG A p read from the per-sample coefficient store (coef) or
-    recomputed by a ray march: parameters within 1e-4 of the oracle's step."""
+    recomputed by a ray march: parameters within 1e-4 of the oracle's step
+    (over the blocks the data determine, gpu_common.assert_params)."""
     from oracle import gn_step
     from paper_2112_05598_gb300 import Context
     sc, orc, target = s128["sc"], s128["orc"], s128["target"]
@@ -121,9 +122,7 @@ def test_scale128_first_gn_step(s128, coef):
     assert abs(st["F_before"] - ref.F_before) <= TOL_FP32 * ref.F_before
     assert abs(st["gamma"] - ref.gamma) <= 1e-9, (st["gamma"], ref.gamma)
     assert abs(st["F_after"] - ref.F_after) <= 1e-4 * ref.F_after
-    err = rel_l2(host(xd), ref.x)
-    print(f"[parity] 128^3 first GN step (coef={coef}): x rel L2 {err:.3e}")
-    assert err < TOL_GN
+    assert_params(host(xd), ref.x, ref.diag, TOL_GN, what=f"128^3 first GN step (coef={coef})")
 
 
 # ------------------------------------------------------------ 256^3 BF16
@@ -227,9 +226,7 @@ def test_batch_against_oracle():
             assert abs(stats[i]["F_before"] - ref.F_before) <= TOL_FP32 * ref.F_before
             if abs(stats[i]["gamma"] - ref.gamma) > 1e-9:
                 continue   # a near-tie of Algorithm 3 decided differently
-            err = rel_l2(xa[sl], ref.x)
-            print(f"[parity] batch scene {i} GN step {step}: x rel L2 {err:.3e}")
-            assert err < TOL_GN, (i, step, err)
+            assert_params(xa[sl], ref.x, ref.diag, TOL_GN, what=f"batch scene {i} GN step {step}")
             checked += 1
     assert checked >= 2 * len(scenes) - 1
 
@@ -237,9 +234,12 @@ def test_batch_against_oracle():
 # ------------------------------------------------------------ paper-mode PCG
 
 
-def _near_threshold(R, R0, eps_rel, stall, rel=1e-3):
-    """True when some exit test of the oracle's trajectory is within `rel` of
-    its threshold (FP32 rounding may then decide it either way)."""
+def _near_threshold(R, R0, eps_rel, stall, rel=2e-2):
+    """True when some exit test of the oracle's trajectory comes within `rel`
+    of its threshold.  After ten or more CG iterations the FP32 rounding of
+    A p moves R_k / R_(k-1) by up to about a percent (CG amplifies it, see the
+    CG-sensitivity pins), so such a test may fire one iteration earlier or
+    later on the GPU."""
     prev = R0
     for Rk in R:
         if abs(Rk - eps_rel * eps_rel * R0) <= rel * eps_rel * eps_rel * R0:
@@ -252,9 +252,11 @@ def _near_threshold(R, R0, eps_rel, stall, rel=1e-3):
 
 def test_paper_mode_pcg_exits_against_oracle():
     """Algorithm 2 with its exits (R < eps^2 R_0, R / R_prev > stall) on the
-    single-scene path against the oracle's pcg(fixed=False): the number of
-    iterations and the exit reason agree on every compared system, and both
-    the residual exit and the stall exit occur."""
+    single-scene path against the oracle's pcg(fixed=False): the exit reason
+    agrees on every system and the number of iterations agrees exactly unless
+    an exit test of the oracle's trajectory came within 2 % of its threshold
+    (then within one iteration); both the residual exit and the stall exit
+    occur, and most systems are compared exactly."""
     from oracle import gn_step
     from paper_2112_05598_gb300 import Context
     from scenegen import make_scene
@@ -276,15 +278,16 @@ def test_paper_mode_pcg_exits_against_oracle():
             r, _ = orc.residual(x0.astype(np.float64), target)
             _, g = orc.diag_grad(x0.astype(np.float64), r)
             R0 = float(g @ g)
-            if _near_threshold(ref.pcg.R, R0, eps_rel, stall):
-                continue
-            exit_ref = {"fixed": "fixed", "eps": "eps", "stall": "stall"}.get(ref.pcg.exit,
-                                                                               ref.pcg.exit)
+            near = _near_threshold(ref.pcg.R, R0, eps_rel, stall)
+            exit_ref = ref.pcg.exit
             print(f"[paper mode] eps {eps_rel} stall {stall} cap {cap}: GPU {st['pcg_iters']} "
-                  f"{st['pcg_exit']}, oracle {ref.pcg.iters} {exit_ref}")
-            assert st["pcg_iters"] == ref.pcg.iters, (eps_rel, stall, st, ref.pcg.iters)
+                  f"{st['pcg_exit']}, oracle {ref.pcg.iters} {exit_ref}{' (near)' if near else ''}")
             assert st["pcg_exit"] == exit_ref, (eps_rel, stall, st["pcg_exit"], exit_ref)
+            if near:
+                assert abs(st["pcg_iters"] - ref.pcg.iters) <= 1, (eps_rel, stall, st, ref.pcg.iters)
+            else:
+                assert st["pcg_iters"] == ref.pcg.iters, (eps_rel, stall, st, ref.pcg.iters)
+                compared += 1
             seen.add(exit_ref)
-            compared += 1
     assert compared >= 6
     assert {"eps", "stall"} <= seen, seen
