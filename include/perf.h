@@ -77,7 +77,21 @@ typedef struct {
     float shell_radii[PERF_MAX_SHELLS];    /* increasing, each > sqrt(3) */
     int32_t env_h, env_w;                  /* texels per shell, >= 2 if S > 0 */
     int32_t dtype;                         /* PERF_F32 or PERF_BF16 */
+    int32_t env_kind;                      /* PERF_ENV_EQUIRECT or PERF_ENV_CUBE */
 } perf_scene;
+
+/* Shell parametrisations.  Equirectangular: texel (row, col) of an env_h x
+ * env_w map, row 0 at the +z pole, u = (atan2(y, x) / 2 pi + 1/2) env_w - 1/2
+ * wrapped in azimuth, v = (polar angle / pi) env_h - 1/2 clamped.  Cube map
+ * (Section "Implementation": the paper's environment maps are cube maps):
+ * env_w = 6 env_h, F = env_h texels per face edge, face f = +x, -x, +y, -y,
+ * +z, -z in columns [f F, (f + 1) F); a hit point q lies on the face of its
+ * largest |q_a| (ties to the lower axis); with (b, c) the other axes in
+ * increasing order, column coordinate u = (q_b / |q_a|) F/2 + F/2 - 1/2 and row
+ * coordinate v = (q_c / |q_a|) F/2 + F/2 - 1/2 (texel i centred at i),
+ * bilinear, clamped to the face's edge texels.  The hit point, face and
+ * (u, v) are binary32 with every operation rounded once. */
+enum { PERF_ENV_EQUIRECT = 0, PERF_ENV_CUBE = 1 };
 
 /* Pinhole cameras: pixel (col, row) has its centre at (col+1/2, row+1/2);
  * camera-space ray ((col+1/2 - W/2)/f, -(row+1/2 - H/2)/f, -1). */

@@ -52,6 +52,7 @@ class _Problem(ctypes.Structure):
         ("seed", ctypes.c_uint64), ("epoch", ctypes.c_uint32),
         ("n_threads", ctypes.c_int),
         ("aux", ctypes.c_int), ("aux_lambda", ctypes.c_double),
+        ("env_kind", ctypes.c_int),
     ]
 
 
@@ -64,7 +65,7 @@ class Oracle:
 
     def __init__(self, G, radii, env_h, env_w, c2w, focal, width, height,
                  max_samples=512, jitter=False, seed=0, epoch=0, n_threads=0, aux=False,
-                 aux_lambda=0.1):
+                 aux_lambda=0.1, env_kind=0):
         radii = [float(r) for r in radii]
         if len(radii) > 8:
             raise ValueError("at most 8 shells")
@@ -91,6 +92,14 @@ class Oracle:
         # grid-exit transmittance away from 0 and 1
         self.p.aux = int(bool(aux))
         self.p.aux_lambda = float(aux_lambda)
+        # Section "Implementation": cube-map shells (env_w = 6 env_h, face f in
+        # columns [f env_h, (f + 1) env_h)) instead of equirectangular ones
+        if env_kind not in (0, 1):
+            raise ValueError("env_kind is 0 (equirect) or 1 (cube map)")
+        if env_kind == 1 and self.S > 0 and self.env_w != 6 * self.env_h:
+            raise ValueError("a cube-map shell is env_h x 6 env_h texels")
+        self.p.env_kind = int(env_kind)
+        self.env_kind = int(env_kind)
         self.n_res = 4 if aux else 3
         self.n_params = 4 * (self.G ** 3 + self.S * self.env_h * self.env_w)
         self.n_rays = self.n_cams * self.width * self.height
@@ -98,6 +107,7 @@ class Oracle:
     @classmethod
     def from_scene(cls, scene, **kw):
         kw.setdefault("max_samples", scene.cfg.max_samples)
+        kw.setdefault("env_kind", getattr(scene, "env_kind", 0))
         return cls(scene.G, scene.radii, scene.env_h, scene.env_w, scene.c2w,
                    scene.focal, scene.width, scene.height, **kw)
 
@@ -162,24 +172,30 @@ class Oracle:
         return self.residual(x, target)[1]
 
     # -- derivatives of Eq. 3 (Section "Computation of partial derivatives")
-    def jvp(self, x, p, ids=None):
+    def jvp(self, x, p, ids=None, mag=False):
+        """J p; with mag=True also |J| |p| (per entry, the sum of the absolute
+        values of its terms: the scale of its rounding error)."""
         x = self._x(x)
         p = self._x(p)
         ids, N = self._ids(ids)
         out = np.zeros(self.n_res * N)
-        _lib().oc_jvp(ctypes.byref(self.p), _dptr(x), _dptr(p),
-                      _dptr(ids) if ids is not None else None,
-                      ctypes.c_int64(N), _dptr(out))
-        return out
+        m = np.zeros(self.n_res * N) if mag else None
+        _lib().oc_jvp_mag(ctypes.byref(self.p), _dptr(x), _dptr(p),
+                          _dptr(ids) if ids is not None else None,
+                          ctypes.c_int64(N), _dptr(out), _dptr(m) if mag else None)
+        return (out, m) if mag else out
 
-    def vjp(self, x, v):
+    def vjp(self, x, v, mag=False):
+        """J^T v; with mag=True also |J|^T |v|."""
         x = self._x(x)
         v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
         if v.shape[0] != self.n_res * self.n_rays:
             raise ValueError("v size")
         out = np.zeros(self.n_params)
-        _lib().oc_vjp(ctypes.byref(self.p), _dptr(x), _dptr(v), _dptr(out), 0)
-        return out
+        m = np.zeros(self.n_params) if mag else None
+        _lib().oc_vjp_mag(ctypes.byref(self.p), _dptr(x), _dptr(v), _dptr(out), 0,
+                          _dptr(m) if mag else None)
+        return (out, m) if mag else out
 
     def apply_A(self, x, p):
         """A p = J^T (J p), the product the PCG of Section "Update step" needs."""

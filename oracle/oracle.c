@@ -62,6 +62,7 @@ typedef struct {
     int n_threads;      /* <= 0: OpenMP default */
     int aux;            /* 1: one auxiliary opacity residual per ray */
     double aux_lambda;  /* its factor (the paper's 0.1) */
+    int env_kind;       /* 0: equirectangular shells, 1: cube-map shells */
 } oc_problem;
 
 /* ---------------------------------------------------------------- jitter */
@@ -240,6 +241,65 @@ static void oc_bilinear(const oc_problem* P, int shell, const double q[3],
     for (int c = 4; c < 8; ++c) { s->idx[c] = 0; s->w[c] = 0.0; }
 }
 
+/* Section "Implementation": environment maps as cube maps.  Shell s is an
+ * env_h x env_w image with env_w = 6 F, F = env_h: face f (0..5 = +x, -x,
+ * +y, -y, +z, -z) occupies columns [f F, (f + 1) F).  A hit point q (binary32,
+ * see oc_shell_hit_f32) lies on the face of its largest |q_a| (ties go to
+ * the lower axis); with (b, c) the other two axes in increasing order,
+ * s = q_b / |q_a| and t = q_c / |q_a| in [-1, 1], and the face's texel
+ * coordinates are u = s F/2 + (F/2 - 1/2) (column) and v = t F/2 + (F/2 - 1/2)
+ * (row), texel i centred at i.  Face, u and v are binary32 (they decide
+ * integers: the face and the texels); the bilinear weights, clamped to the
+ * face's edge texels (no filtering across faces), are FP64. */
+static void oc_cube(const oc_problem* P, int shell, const float q[3], oc_sample* s) {
+    const int F = P->env_h, We = P->env_w;
+    const float ax = fabsf(q[0]), ay = fabsf(q[1]), az = fabsf(q[2]);
+    int a = 2;
+    if (ax >= ay && ax >= az) a = 0;
+    else if (ay >= az) a = 1;
+    const int face = 2 * a + (q[a] < 0.0f ? 1 : 0);
+    const int b = a == 0 ? 1 : 0, c = a == 2 ? 1 : 2;
+    const float m = fabsf(q[a]);
+    const float hf = 0.5f * (float)F;
+    const float uf = fmaf(q[b] / m, hf, hf - 0.5f);
+    const float vf = fmaf(q[c] / m, hf, hf - 0.5f);
+    double uv[2] = {(double)uf, (double)vf};
+    int64_t base2[2];
+    double fr[2];
+    for (int i = 0; i < 2; ++i) {
+        double u = uv[i];
+        if (u < 0.0) u = 0.0;
+        if (u > (double)(F - 1)) u = (double)(F - 1);
+        double fl = floor(u);
+        if (fl > (double)(F - 2)) fl = (double)(F - 2);
+        base2[i] = (int64_t)fl;
+        fr[i] = u - fl;
+    }
+    const int64_t c0 = (int64_t)face * F + base2[0], r0 = base2[1];
+    const int64_t base = (int64_t)P->G * P->G * P->G + (int64_t)shell * P->env_h * We;
+    s->nc = 4;
+    s->is_grid = 0;
+    s->idx[0] = base + r0 * We + c0;           s->w[0] = (1.0 - fr[0]) * (1.0 - fr[1]);
+    s->idx[1] = base + r0 * We + c0 + 1;       s->w[1] = fr[0] * (1.0 - fr[1]);
+    s->idx[2] = base + (r0 + 1) * We + c0;     s->w[2] = (1.0 - fr[0]) * fr[1];
+    s->idx[3] = base + (r0 + 1) * We + c0 + 1; s->w[3] = fr[0] * fr[1];
+    for (int k = 4; k < 8; ++k) { s->idx[k] = 0; s->w[k] = 0.0; }
+}
+
+/* Far-root hit point of a ray with the sphere of radius `radius`, in binary32
+ * with every operation rounded once (the precision in which the kernels
+ * decide a cube map's face and texels). */
+static void oc_shell_hit_f32(const oc_ray* R, float radius, float q[3]) {
+    const float b = (R->o[0] * R->d[0] + R->o[1] * R->d[1]) + R->o[2] * R->d[2];
+    const float oo = (R->o[0] * R->o[0] + R->o[1] * R->o[1]) + R->o[2] * R->o[2];
+    const float c = oo - radius * radius;
+    float disc = b * b - c;
+    if (disc < 0.0f) disc = 0.0f;
+    const float sq = sqrtf(disc);
+    const float t = (b < 0.0f) ? (sq - b) : (c / (-b - sq));
+    for (int a = 0; a < 3; ++a) q[a] = fmaf(t, R->d[a], R->o[a]);
+}
+
 static void oc_interp(const double* x, oc_sample* s) {
     double acc[4] = {0, 0, 0, 0};
     for (int c = 0; c < s->nc; ++c)
@@ -278,8 +338,14 @@ static int oc_collect(const oc_problem* P, const double* x, int64_t ray,
         if (disc < 0.0) disc = 0.0;
         const double sq = sqrt(disc);
         const double t = (b < 0.0) ? (-b + sq) : (c / (-b - sq));
-        const double q[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
-        oc_bilinear(P, s, q, &out[n]);
+        if (P->env_kind == 1) {
+            float qf[3];
+            oc_shell_hit_f32(&R, P->radii[s], qf);
+            oc_cube(P, s, qf, &out[n]);
+        } else {
+            const double q[3] = {o[0] + t * d[0], o[1] + t * d[1], o[2] + t * d[2]};
+            oc_bilinear(P, s, q, &out[n]);
+        }
         oc_interp(x, &out[n]);
         out[n].dbar = 1.0;
         ++n;
@@ -444,8 +510,18 @@ int oc_residual(const oc_problem* P, const double* x, const double* target,
 
 /* (J p) for the listed rays: sum over samples and interpolation corners of
  * dH/dx_j p_j, with the partials of Eq. 3 (oc_partials). */
+int oc_jvp_mag(const oc_problem* P, const double* x, const double* p, const int64_t* ids,
+               int64_t n_ids, double* out, double* mag);
+
 int oc_jvp(const oc_problem* P, const double* x, const double* p, const int64_t* ids,
            int64_t n_ids, double* out) {
+    return oc_jvp_mag(P, x, p, ids, n_ids, out, NULL);
+}
+
+/* oc_jvp, and (mag != NULL) the sum of the absolute values of the terms of
+ * each entry, mag = |J| |p| (the scale of its floating-point rounding). */
+int oc_jvp_mag(const oc_problem* P, const double* x, const double* p, const int64_t* ids,
+               int64_t n_ids, double* out, double* mag) {
     const int64_t N = ids ? n_ids : oc_n_rays(P);
     const int cap = oc_cap(P);
 #pragma omp parallel num_threads(oc_nthreads(P))
@@ -459,19 +535,26 @@ int oc_jvp(const oc_problem* P, const double* x, const double* p, const int64_t*
             int ng;
             const int n = oc_collect(P, x, ray, buf, &ng);
             oc_partials(buf, n, dc, ds);
-            double acc[4] = {0, 0, 0, 0};
+            double acc[4] = {0, 0, 0, 0}, am[4] = {0, 0, 0, 0};
             double L = 0.0, dfac = 0.0;
             if (P->aux) oc_aux(P, buf, ng, &L, &dfac);
             for (int i = 0; i < n; ++i)
                 for (int c = 0; c < buf[i].nc; ++c) {
                     const int64_t q = 4 * buf[i].idx[c];
                     const double w = buf[i].w[c];
-                    for (int k = 0; k < 3; ++k)
+                    for (int k = 0; k < 3; ++k) {
                         acc[k] += w * (dc[i] * p[q + k] + ds[3 * i + k] * p[q + 3]);
-                    if (i < ng) acc[3] += w * dfac * buf[i].dbar * p[q + 3];
+                        am[k] += fabs(w) * (fabs(dc[i] * p[q + k]) + fabs(ds[3 * i + k] * p[q + 3]));
+                    }
+                    if (i < ng) {
+                        acc[3] += w * dfac * buf[i].dbar * p[q + 3];
+                        am[3] += fabs(w * dfac * buf[i].dbar * p[q + 3]);
+                    }
                 }
             const int R = oc_nres(P);
             for (int k = 0; k < R; ++k) out[R * j + k] = acc[k];
+            if (mag)
+                for (int k = 0; k < R; ++k) mag[R * j + k] = am[k];
         }
         free(buf); free(dc); free(ds);
     }
@@ -489,13 +572,24 @@ static void oc_reduce(double** parts, int nt, int64_t n, double* out, int accumu
 
 /* out = J^T v (all rays): out_j = sum_rays sum_k v_k dr_k/dx_j (v has 3,
  * or with aux 4, entries per ray). */
+int oc_vjp_mag(const oc_problem* P, const double* x, const double* v, double* out,
+               int accumulate, double* mag);
+
 int oc_vjp(const oc_problem* P, const double* x, const double* v, double* out,
            int accumulate) {
+    return oc_vjp_mag(P, x, v, out, accumulate, NULL);
+}
+
+/* oc_vjp, and (mag != NULL) mag = |J|^T |v|, the sum of the absolute values
+ * of the terms of each entry. */
+int oc_vjp_mag(const oc_problem* P, const double* x, const double* v, double* out,
+               int accumulate, double* mag) {
     const int64_t N = oc_n_rays(P);
     const int64_t np = oc_n_params(P);
     const int cap = oc_cap(P);
     const int nt = oc_nthreads(P);
     double** parts = (double**)calloc(nt, sizeof(double*));
+    double** mparts = (double**)calloc(nt, sizeof(double*));
 #pragma omp parallel num_threads(nt)
     {
         int tid = 0;
@@ -503,7 +597,9 @@ int oc_vjp(const oc_problem* P, const double* x, const double* v, double* out,
         tid = omp_get_thread_num();
 #endif
         double* acc = (double*)calloc(np, sizeof(double));
+        double* am = mag ? (double*)calloc(np, sizeof(double)) : NULL;
         parts[tid] = acc;
+        mparts[tid] = am;
         oc_sample* buf = (oc_sample*)malloc(sizeof(oc_sample) * cap);
         double* dc = (double*)malloc(sizeof(double) * cap);
         double* ds = (double*)malloc(sizeof(double) * 3 * cap);
@@ -519,12 +615,21 @@ int oc_vjp(const oc_problem* P, const double* x, const double* v, double* out,
             if (P->aux) oc_aux(P, buf, ng, &L, &dfac);
             for (int i = 0; i < n; ++i) {
                 double gs = vr[0] * ds[3 * i] + vr[1] * ds[3 * i + 1] + vr[2] * ds[3 * i + 2];
-                if (i < ng) gs += va * dfac * buf[i].dbar;
+                double gm = fabs(vr[0] * ds[3 * i]) + fabs(vr[1] * ds[3 * i + 1]) +
+                            fabs(vr[2] * ds[3 * i + 2]);
+                if (i < ng) {
+                    gs += va * dfac * buf[i].dbar;
+                    gm += fabs(va * dfac * buf[i].dbar);
+                }
                 for (int c = 0; c < buf[i].nc; ++c) {
                     const int64_t q = 4 * buf[i].idx[c];
                     const double w = buf[i].w[c];
                     for (int k = 0; k < 3; ++k) acc[q + k] += w * dc[i] * vr[k];
                     acc[q + 3] += w * gs;
+                    if (am) {
+                        for (int k = 0; k < 3; ++k) am[q + k] += fabs(w * dc[i] * vr[k]);
+                        am[q + 3] += fabs(w) * gm;
+                    }
                 }
             }
         }
@@ -533,8 +638,10 @@ int oc_vjp(const oc_problem* P, const double* x, const double* v, double* out,
     int used = 0;
     for (int t = 0; t < nt; ++t) if (parts[t]) used = t + 1;
     oc_reduce(parts, used, np, out, accumulate);
-    for (int t = 0; t < nt; ++t) free(parts[t]);
+    if (mag) oc_reduce(mparts, used, np, mag, 0);
+    for (int t = 0; t < nt; ++t) { free(parts[t]); if (mparts[t]) free(mparts[t]); }
     free(parts);
+    free(mparts);
     return 0;
 }
 

@@ -17,6 +17,7 @@ LIB_PATH = os.environ.get("PERF_LIB_PATH") or os.path.join(HERE, "libperf.so")
 
 PERF_F32, PERF_BF16 = 0, 1
 PERF_PRECOND_JACOBI, PERF_PRECOND_BLOCK4, PERF_PRECOND_BLOCK_JACOBI = 0, 1, 2
+PERF_ENV_EQUIRECT, PERF_ENV_CUBE = 0, 1
 STATUS = {0: "PERF_OK", 1: "PERF_ERR_INVALID_ARG", 2: "PERF_ERR_CUDA",
           3: "PERF_ERR_NONFINITE", 4: "PERF_ERR_TIMEOUT", 5: "PERF_ERR_NOT_SPD",
           6: "PERF_ERR_UNSUPPORTED"}
@@ -33,7 +34,7 @@ class Scene(ctypes.Structure):
     _fields_ = [("grid_res", ctypes.c_int32), ("n_shells", ctypes.c_int32),
                 ("shell_radii", ctypes.c_float * 8),
                 ("env_h", ctypes.c_int32), ("env_w", ctypes.c_int32),
-                ("dtype", ctypes.c_int32)]
+                ("dtype", ctypes.c_int32), ("env_kind", ctypes.c_int32)]
 
 
 class Cameras(ctypes.Structure):
@@ -260,7 +261,7 @@ class Context:
     tensors and run on the current torch stream unless one is given."""
 
     def __init__(self, G, radii, env_h, env_w, c2w, focal, width, height,
-                 dtype=PERF_F32, options: Optional[Options] = None, **opt_kw):
+                 dtype=PERF_F32, options: Optional[Options] = None, env_kind=0, **opt_kw):
         self.lib = load_library()
         sc = Scene()
         sc.grid_res = int(G)
@@ -270,6 +271,8 @@ class Context:
             sc.shell_radii[i] = r
         sc.env_h, sc.env_w = int(env_h), int(env_w)
         sc.dtype = int(dtype)
+        sc.env_kind = int(env_kind)
+        self.env_kind = int(env_kind)
         self._c2w = np.ascontiguousarray(c2w, dtype=np.float32).reshape(-1, 12)
         self._focal = np.ascontiguousarray(focal, dtype=np.float32).reshape(-1)
         cams = Cameras()
@@ -300,6 +303,7 @@ class Context:
     @classmethod
     def from_scene(cls, scene, dtype=PERF_F32, c2w=None, focal=None, **opt_kw):
         opt_kw.setdefault("max_samples", scene.cfg.max_samples)
+        opt_kw.setdefault("env_kind", getattr(scene, "env_kind", 0))
         return cls(scene.G, scene.radii, scene.env_h, scene.env_w,
                    scene.c2w if c2w is None else c2w,
                    scene.focal if focal is None else focal,
@@ -458,6 +462,7 @@ class Batch:
                 sc_arr[i].shell_radii[j] = r
             sc_arr[i].env_h, sc_arr[i].env_w = int(d["env_h"]), int(d["env_w"])
             sc_arr[i].dtype = PERF_F32
+            sc_arr[i].env_kind = int(d.get("env_kind", 0))
             c2w = np.ascontiguousarray(d["c2w"], dtype=np.float32).reshape(-1, 12)
             focal = np.ascontiguousarray(d["focal"], dtype=np.float32).reshape(-1)
             self._keep += [c2w, focal]

@@ -113,9 +113,20 @@ __device__ __forceinline__ void csum_add(CSum& s, float a) {
     s.lo = __fadd_rn(s.lo, err);
 }
 
-struct Comp {   // running composite of one ray
+// Running composite of one ray.  The transmittance is e^{-V} with V the
+// optical depth so far, kept as a compensated sum, rather than a running
+// product: a product of several hundred rounded factors drifts by up to
+// ~1e-4 relative on the longest rays, e^{-V} stays within a few ulps.
+struct Comp {
     float T, H[3];
+    CSum V;
 };
+
+__device__ __forceinline__ void comp_reset(Comp& s) {
+    s.T = 1.0f;
+    s.H[0] = s.H[1] = s.H[2] = 0.0f;
+    s.V.hi = s.V.lo = 0.0f;
+}
 
 __device__ __forceinline__ void comp_step(Comp& s, const float4 a, float dbar) {
     const float sd = __fmul_rn(a.w, dbar);
@@ -124,7 +135,8 @@ __device__ __forceinline__ void comp_step(Comp& s, const float4 a, float dbar) {
     s.H[0] = fmaf(w, a.x, s.H[0]);
     s.H[1] = fmaf(w, a.y, s.H[1]);
     s.H[2] = fmaf(w, a.z, s.H[2]);
-    s.T = __fmul_rn(s.T, e);
+    csum_add(s.V, sd);
+    s.T = expf(-fmaxf(s.V.hi + s.V.lo, 0.0f));
 }
 
 // Eq. 3-4 over the grid samples and then the shells.  cut > 0: the
@@ -135,8 +147,7 @@ template <typename T>
 __device__ __forceinline__ void composite(const DevScene& sc, const T* __restrict__ x,
                                           const Ray& R, long long ray, Comp& s, float& T_exit,
                                           float cut = 0.0f) {
-    s.T = 1.0f;
-    s.H[0] = s.H[1] = s.H[2] = 0.0f;
+    comp_reset(s);
     const float dbar = R.delta * sc.halfG;
     Interp<T, PERF_CACHE_X != 0> cx;
     cx.reset();
@@ -145,13 +156,10 @@ __device__ __forceinline__ void composite(const DevScene& sc, const T* __restric
         comp_step(s, cx.at(x, sc, cl), dbar);
     }
     T_exit = s.T;
-    if (cut > 0.0f && 1.0f - s.T < cut) {
-        s.T = 1.0f;
-        s.H[0] = s.H[1] = s.H[2] = 0.0f;
-    }
+    if (cut > 0.0f && 1.0f - s.T < cut) comp_reset(s);
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
-        if (shell_lookup(sc, R, q, hs)) comp_step(s, interp_shell(x, hs), 1.0f);
+        if (shell_lookup(sc, R, ray, q, hs)) comp_step(s, interp_shell(x, hs), 1.0f);
     }
 }
 
@@ -171,7 +179,7 @@ __device__ __forceinline__ CSum optical_depth(const DevScene& sc, const T* __res
     if (Vg) *Vg = V;
     for (int q = 0; q < sc.S; ++q) {
         ShellHit hs;
-        if (shell_lookup(sc, R, q, hs)) csum_add(V, interp_shell(x, hs).w);
+        if (shell_lookup(sc, R, ray, q, hs)) csum_add(V, interp_shell(x, hs).w);
     }
     return V;
 }
@@ -197,7 +205,7 @@ __device__ __forceinline__ void jvp_backward(const DevScene& sc, const T* __rest
     psum = 0.0f;
     for (int q = sc.S - 1; q >= 0; --q) {
         ShellHit hs;
-        if (!shell_lookup(sc, R, q, hs)) continue;
+        if (!shell_lookup(sc, R, ray, q, hs)) continue;
         float4 a, pv;
         if constexpr (std::is_same<T, PairF32>::value) {
             interp_shell_pair(x, hs, a, pv);
@@ -407,7 +415,7 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
     // shells, outermost first
     for (int q = sc.S - 1; q >= 0; --q) {
         ShellHit hs;
-        const bool hit = act && shell_lookup(sc, R, q, hs);
+        const bool hit = act && shell_lookup(sc, R, ray, q, hs);
         float wi = 0.0f, ds[3] = {0.0f, 0.0f, 0.0f};
         if (hit) {
             const float4 a = interp_shell(x, hs);
@@ -683,6 +691,20 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
 // a shell it misses) are never read.
 
 // rows[t] = Kmax of tile t + S (+ 1: the auxiliary residual's per-ray factor).
+// Shell-hit table: entry (ray, s) for every ray of [ray_lo, ray_lo + n) and
+// shell s it hits (others are left untouched and never read).
+__global__ void __launch_bounds__(kThreads) k_shell_table(DevScene sc, long long ray_lo,
+                                                          long long n, float4* tab) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long ray = ray_lo + i;
+        Ray R;
+        ray_setup(sc, ray, R);
+        for (int s = 0; s < sc.S; ++s)
+            if (R.shell_hit & (1u << s)) tab[ray * sc.S + s] = shell_entry(sc, R, s);
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) {
     PERF_TILE_LOOP {
         long long ray;
@@ -730,7 +752,7 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
         Ja = kap * psum;
         for (int s = 0; s < sc.S; ++s) {
             ShellHit hs;
-            if (shell_lookup(sc, R, s, hs)) {
+            if (shell_lookup(sc, R, ray, s, hs)) {
                 const float4 q = interp_shell(p, hs);
                 const float4 c = __ldcs(crow + (long long)(kmax_rows + s) * 32);
                 J[0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[0]));
@@ -746,7 +768,7 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
     VjpSink<CanonKey, COUNT> sk{out, J[0], J[1], J[2], CanonKey{sc.G}, sc.red_count};
     for (int s = sc.S - 1; s >= 0; --s) {
         ShellHit hs;
-        const bool hit = act && shell_lookup(sc, R, s, hs);
+        const bool hit = act && shell_lookup(sc, R, ray, s, hs);
         float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
         if (hit) c = __ldcs(crow + (long long)(kmax_rows + s) * 32);
         const float sv = J[0] * c.y + J[1] * c.z + J[2] * c.w;
@@ -1090,6 +1112,15 @@ cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* 
 cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
                               cudaStream_t st) {
     return launch_scatter_t<PairF32, PairF32, 1, float>(sc, xp, xp, nullptr, out, nullptr, pap, st);
+}
+
+cudaError_t launch_shell_table(const DevScene& sc, float4* tab, cudaStream_t st) {
+    if (sc.S == 0 || sc.n_rays == 0) return cudaSuccess;
+    const long long blocks = (sc.n_rays + kThreads - 1) / kThreads;
+    const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
+    k_shell_table<<<grid, kThreads, 0, st>>>(sc, 0, sc.n_rays, tab);
+    count_launch();
+    return cudaGetLastError();
 }
 
 cudaError_t launch_tile_rows(const DevScene& sc, int* rows, cudaStream_t st) {

@@ -59,6 +59,10 @@ struct perf_ctx {
     long long tab_epoch = -1;          // epoch of a jittered table (-1: not jittered)
     bool coef_used = false;            // the last Gauss-Newton step used the store
     float* Ap = nullptr;
+    // shell hits of every ray (n_rays x S entries, FP64 texel coordinates),
+    // valid for jitter epoch shell_tab_epoch (-1: no jitter); see ensure_shells
+    float4* shell_tab = nullptr;
+    long long shell_tab_epoch = -2;
     float* x_trial = nullptr;
     __nv_bfloat16* x16 = nullptr;
     __nv_bfloat16* p16 = nullptr;
@@ -212,6 +216,41 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
 
 bool bad_ptr(const void* p) { return p == nullptr; }
 
+// The shell-hit table of the context's rays at the current jitter epoch:
+// built on first use and whenever the rays move (pixel jitter of a new
+// epoch, new options); if it cannot be allocated the marches compute the hits
+// themselves in FP32.
+perf_status ensure_shells(perf_ctx* ctx, cudaStream_t st) {
+    perf::DevScene& d = ctx->ds;
+    if (d.S == 0 || ctx->n_rays == 0) {
+        d.shell_tab = nullptr;
+        return PERF_OK;
+    }
+    const long long epoch = d.jitter ? (long long)d.epoch : -1;
+    if (ctx->shell_tab && ctx->shell_tab_epoch == epoch) {
+        d.shell_tab = ctx->shell_tab;
+        return PERF_OK;
+    }
+    if (!ctx->shell_tab &&
+        cudaMalloc(&ctx->shell_tab, sizeof(float4) * (size_t)ctx->n_rays * (size_t)d.S) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->shell_tab = nullptr;
+        d.shell_tab = nullptr;
+        return PERF_OK;
+    }
+    d.shell_tab = nullptr;
+    CK(perf::launch_shell_table(d, ctx->shell_tab, st));
+    ctx->shell_tab_epoch = epoch;
+    d.shell_tab = ctx->shell_tab;
+    return PERF_OK;
+}
+
+#define SHELLS(ctx, st)                                 \
+    do {                                                \
+        const perf_status ps_ = ensure_shells(ctx, st); \
+        if (ps_ != PERF_OK) return ps_;                 \
+    } while (0)
+
 void t_begin(perf_ctx* c, int k, cudaStream_t st) {
     if (!c->timing) return;
     auto& t = c->kt[k];
@@ -278,6 +317,9 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
     if (sc->n_shells < 0 || sc->n_shells > PERF_MAX_SHELLS) return PERF_ERR_INVALID_ARG;
     if (sc->dtype != PERF_F32 && sc->dtype != PERF_BF16) return PERF_ERR_INVALID_ARG;
     if (sc->n_shells > 0 && (sc->env_h < 2 || sc->env_w < 2)) return PERF_ERR_INVALID_ARG;
+    if (sc->env_kind != PERF_ENV_EQUIRECT && sc->env_kind != PERF_ENV_CUBE) return PERF_ERR_INVALID_ARG;
+    if (sc->env_kind == PERF_ENV_CUBE && sc->n_shells > 0 && sc->env_w != 6 * sc->env_h)
+        return PERF_ERR_INVALID_ARG;
     for (int s = 0; s < sc->n_shells; ++s) {
         if (!(sc->shell_radii[s] > 1.7320508f)) return PERF_ERR_INVALID_ARG;
         if (s > 0 && !(sc->shell_radii[s] > sc->shell_radii[s - 1])) return PERF_ERR_INVALID_ARG;
@@ -312,6 +354,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
     for (int s = 0; s < sc->n_shells; ++s) d.R[s] = sc->shell_radii[s];
     d.He = ctx->scene.env_h;
     d.We = ctx->scene.env_w;
+    d.env_kind = ctx->scene.env_kind;
     d.n_vox = G * G * G;
     d.shell_texels = texels;
     d.W = cams->width;
@@ -360,7 +403,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->shell_tab, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -381,6 +424,7 @@ perf_status perf_set_options(perf_ctx* ctx, const perf_options* opts) {
     ctx->opts = *opts;
     ctx->ds.max_samples = opts->max_samples;
     ctx->ds.jitter = opts->jitter;
+    ctx->shell_tab_epoch = -2;                 // rays may move: rebuild the shell hits
     ctx->ds.seed = opts->seed;
     ctx->ds.epoch = opts->epoch;
     if (ctx->ds.aux != opts->aux && ctx->r) {   // the residual buffer changes size
@@ -400,6 +444,7 @@ perf_status perf_render(perf_ctx* ctx, const void* x, float* rgb_out, float* T_o
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x) || bad_ptr(rgb_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "render: NULL x or rgb_out");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, x, nullptr, rgb_out, T_out, nullptr, 0, S(stream)));
     return PERF_OK;
 }
@@ -411,6 +456,7 @@ perf_status perf_residual(perf_ctx* ctx, const void* x, const void* target, void
     CK(cudaMemsetAsync(F_out, 0, sizeof(double), S(stream)));
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x) || bad_ptr(target)) return fail(ctx, PERF_ERR_INVALID_ARG, "residual: NULL x or target");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, x, target, r_out, nullptr, F_out,
                             r_out ? 1 : 2, S(stream)));
     return PERF_OK;
@@ -420,6 +466,7 @@ perf_status perf_jvp(perf_ctx* ctx, const void* x, const float* p, float* jp_out
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x) || bad_ptr(p) || bad_ptr(jp_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "jvp: NULL pointer");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_jvp(ctx->ds, ctx->scene.dtype, x, p, PERF_F32, jp_out, S(stream)));
     return PERF_OK;
 }
@@ -431,6 +478,7 @@ perf_status perf_vjp(perf_ctx* ctx, const void* x, const float* v, float* out, i
     if (!accumulate) CK(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)ctx->n, S(stream)));
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x) || bad_ptr(v)) return fail(ctx, PERF_ERR_INVALID_ARG, "vjp: NULL x or v");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 0, x, nullptr, PERF_F32, v, out, nullptr,
                             nullptr, S(stream)));
     return PERF_OK;
@@ -446,6 +494,7 @@ perf_status perf_diag_jtj(perf_ctx* ctx, const void* x, const void* r, float* di
     if (grad_out) CK(cudaMemsetAsync(grad_out, 0, sizeof(float) * (size_t)ctx->n, S(stream)));
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "diag_jtj: NULL x");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, r, diag_out,
                             grad_out, nullptr, S(stream)));
     return PERF_OK;
@@ -459,6 +508,7 @@ perf_status perf_apply_normal(perf_ctx* ctx, const void* x, const float* p, floa
     if (pap_out) CK(cudaMemsetAsync(pap_out, 0, sizeof(double), S(stream)));
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x) || bad_ptr(p)) return fail(ctx, PERF_ERR_INVALID_ARG, "apply_normal: NULL x or p");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 1, x, p, PERF_F32, nullptr, ap_out, nullptr,
                             pap_out, S(stream)));
     return PERF_OK;
@@ -539,6 +589,7 @@ perf_status perf_pcg_step(perf_ctx* ctx, const void* x, int32_t* done_out, void*
     if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_step: NULL x");
     if (!ctx->delta || !ctx->s) return fail(ctx, PERF_ERR_INVALID_ARG, "pcg_step before pcg_begin");
     const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
+    SHELLS(ctx, S(stream));
     perf_status st = pcg_iter(ctx, x, ctx->diag, B, S(stream));
     if (st != PERF_OK) return st;
     if (done_out) {
@@ -591,6 +642,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
     perf_status result = PERF_OK;
     for (int step = 0; step < n_steps; ++step) {
         ctx->ds.epoch = epoch0 + (uint32_t)step;
+        SHELLS(ctx, st);
         CK(cudaEventRecord(ctx->ev0, st));
         const void* xm = x;
         if (bf) {
@@ -772,6 +824,7 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
     cudaStream_t st = S(stream);
     perf_status ps = ensure_pcg(ctx);
     if (ps != PERF_OK) return ps;
+    SHELLS(ctx, st);
     const bool bf = ctx->scene.dtype == PERF_BF16;
     // the probe direction (default x: every ray then has a non-zero J p)
     void* pbuf = bf ? static_cast<void*>(ctx->p16) : static_cast<void*>(ctx->p);
@@ -941,6 +994,7 @@ perf_status perf_diag_cross(perf_ctx* ctx, const void* x, float* diag_out, float
     CK(cudaMemsetAsync(cross_out, 0, sizeof(float) * 4 * (size_t)ctx->ds.n_vox, S(stream)));
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x)) return fail(ctx, PERF_ERR_INVALID_ARG, "diag_cross: NULL x");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr, diag_out,
                             nullptr, nullptr, S(stream), cross_out));
     return PERF_OK;
@@ -984,6 +1038,7 @@ perf_status perf_render_threshold(perf_ctx* ctx, const void* x, float min_opacit
         return fail(ctx, PERF_ERR_INVALID_ARG, "render_threshold: min_opacity outside [0, 1]");
     if (ctx->n_rays == 0) return PERF_OK;
     if (bad_ptr(x) || bad_ptr(rgb_out)) return fail(ctx, PERF_ERR_INVALID_ARG, "render_threshold: NULL x or rgb_out");
+    SHELLS(ctx, S(stream));
     CK(perf::launch_forward(ctx->ds, ctx->scene.dtype, x, nullptr, rgb_out, T_out, nullptr, 0,
                             S(stream), min_opacity));
     return PERF_OK;

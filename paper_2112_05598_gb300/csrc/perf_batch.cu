@@ -34,6 +34,7 @@ struct perf_batch {
     long long n_chunks = 0;
     std::vector<long long> ray_off;    // n + 1
     BatchItem* d_items = nullptr;
+    float4* shell_tab = nullptr;       // shell hits of every scene's rays (FP64 texel coordinates)
     long long* d_start = nullptr;      // tile offsets (n + 1)
     long long* d_seg = nullptr;        // block offsets (n + 1)
     float* cams = nullptr;
@@ -256,6 +257,8 @@ perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_sce
         bool ok = sc.grid_res >= 2 && sc.grid_res <= 1024 && sc.n_shells >= 0 &&
                   sc.n_shells <= PERF_MAX_SHELLS && sc.dtype == PERF_F32 &&
                   (sc.n_shells == 0 || (sc.env_h >= 2 && sc.env_w >= 2)) && c.n_cams >= 0 &&
+                  (sc.env_kind == PERF_ENV_EQUIRECT ||
+                   (sc.env_kind == PERF_ENV_CUBE && (sc.n_shells == 0 || sc.env_w == 6 * sc.env_h))) &&
                   c.width >= 0 && c.height >= 0 && (c.n_cams == 0 || (c.c2w && c.focal));
         for (int q = 0; ok && q < sc.n_shells; ++q)
             ok = sc.shell_radii[q] > 1.7320508f && (q == 0 || sc.shell_radii[q] > sc.shell_radii[q - 1]);
@@ -292,6 +295,7 @@ perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_sce
         for (int q = 0; q < sc.n_shells; ++q) d.R[q] = sc.shell_radii[q];
         d.He = sc.n_shells > 0 ? sc.env_h : 0;
         d.We = sc.n_shells > 0 ? sc.env_w : 0;
+        d.env_kind = sc.env_kind;
         d.n_vox = G * G * G;
         d.shell_texels = (long long)d.He * d.We;
         d.W = c.width;
@@ -310,6 +314,27 @@ perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_sce
     }
     if (e == cudaSuccess)
         e = cudaMemcpy(b->cams, camh.data(), sizeof(float) * camh.size(), cudaMemcpyHostToDevice);
+    // shell-hit tables (the batch keeps one jitter epoch): one launch per
+    // scene; without room the marches compute the hits themselves in FP32
+    if (e == cudaSuccess) {
+        long long entries = 0;
+        for (int i = 0; i < n_scenes; ++i) entries += b->items[i].sc.n_rays * b->items[i].sc.S;
+        if (entries > 0 && cudaMalloc(&b->shell_tab, sizeof(float4) * (size_t)entries) == cudaSuccess) {
+            long long off = 0;
+            for (int i = 0; i < n_scenes && e == cudaSuccess; ++i) {
+                DevScene& d = b->items[i].sc;
+                if (d.n_rays * d.S == 0) continue;
+                d.shell_tab = nullptr;
+                e = perf::launch_shell_table(d, b->shell_tab + off, nullptr);
+                d.shell_tab = b->shell_tab + off;
+                off += d.n_rays * d.S;
+            }
+            if (e == cudaSuccess) e = cudaDeviceSynchronize();
+        } else {
+            cudaGetLastError();
+            b->shell_tab = nullptr;
+        }
+    }
     const long long n = b->n_params, m = 3 * b->n_rays;
     if (e == cudaSuccess) e = dalloc(&b->d_items, n_scenes);
     if (e == cudaSuccess) e = dalloc(&b->d_start, n_scenes + 1);
@@ -356,7 +381,7 @@ perf_status perf_batch_destroy(perf_batch* b) {
     if (!b) return PERF_ERR_INVALID_ARG;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    void* bufs[] = {b->d_items, b->d_start, b->d_seg, b->d_chunks, b->cams, b->counter, b->x_work, b->x_trial,
+    void* bufs[] = {b->shell_tab, b->d_items, b->d_start, b->d_seg, b->d_chunks, b->cams, b->counter, b->x_work, b->x_trial,
                     b->r, b->diag, b->grad, b->delta, b->rho, b->p, b->Ap, b->s, b->F,
                     b->gamma, b->mask, b->tile_off, b->coef};
     for (void* q : bufs)

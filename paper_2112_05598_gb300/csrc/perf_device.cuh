@@ -31,6 +31,7 @@ struct DevScene {
     int S;
     float R[kMaxShells];
     int He, We;
+    int env_kind;            // 0 equirectangular shells, 1 cube maps (We = 6 He)
     long long n_vox;         // G^3
     long long shell_texels;  // He*We
     int W, H, n_cams;
@@ -49,6 +50,9 @@ struct DevScene {
     long long tile_lo;       // a launch processes tiles [tile_lo, n_tiles)
     long long coef_tiles;    // tiles [0, coef_tiles) have rows in the coefficient store
     unsigned long long* red_count;   // non-null: count the J^T scatter's vector-atomic lane operations
+    // Shell hits per ray (n_rays x S entries, see shell_entry); null: each
+    // march computes them itself in FP32.
+    const float4* shell_tab;
 };
 
 struct Ray {
@@ -354,8 +358,107 @@ struct ShellHit {
     float w[4];
 };
 
-__device__ __forceinline__ bool shell_lookup(const DevScene& sc, const Ray& R, int s, ShellHit& hs) {
+// Cube-map shell-hit entry (perf.h, PERF_ENV_CUBE): the far-root hit point,
+// the face of its largest coordinate and the face's texel coordinates in
+// binary32 with every operation rounded once (no contraction), so the face
+// and texel decisions are a fixed function of the ray.  Entry layout as in
+// shell_decode: (first texel index, fu, fv, column step 1).
+__device__ __forceinline__ float4 cube_entry(const DevScene& sc, const Ray& R, int s) {
+    const float b = __fadd_rn(__fadd_rn(__fmul_rn(R.o[0], R.d[0]), __fmul_rn(R.o[1], R.d[1])),
+                              __fmul_rn(R.o[2], R.d[2]));
+    const float oo = __fadd_rn(__fadd_rn(__fmul_rn(R.o[0], R.o[0]), __fmul_rn(R.o[1], R.o[1])),
+                               __fmul_rn(R.o[2], R.o[2]));
+    const float c = __fsub_rn(oo, __fmul_rn(sc.R[s], sc.R[s]));
+    const float disc = fmaxf(__fsub_rn(__fmul_rn(b, b), c), 0.0f);
+    const float sq = __fsqrt_rn(disc);
+    const float t = (b < 0.0f) ? __fsub_rn(sq, b) : __fdiv_rn(c, __fsub_rn(-b, sq));
+    const float q[3] = {__fmaf_rn(t, R.d[0], R.o[0]), __fmaf_rn(t, R.d[1], R.o[1]),
+                        __fmaf_rn(t, R.d[2], R.o[2])};
+    const float ax = fabsf(q[0]), ay = fabsf(q[1]), az = fabsf(q[2]);
+    int a = 2;
+    if (ax >= ay && ax >= az) a = 0;
+    else if (ay >= az) a = 1;
+    const float qa = a == 0 ? q[0] : (a == 1 ? q[1] : q[2]);
+    const float qb = a == 0 ? q[1] : q[0];
+    const float qc = a == 2 ? q[1] : q[2];
+    const int face = 2 * a + (qa < 0.0f ? 1 : 0);
+    const int F = sc.He;
+    const float m = fabsf(qa);
+    const float hf = 0.5f * (float)F;
+    float u = __fmaf_rn(__fdiv_rn(qb, m), hf, hf - 0.5f);
+    float v = __fmaf_rn(__fdiv_rn(qc, m), hf, hf - 0.5f);
+    u = fminf(fmaxf(u, 0.0f), (float)(F - 1));
+    v = fminf(fmaxf(v, 0.0f), (float)(F - 1));
+    const float j0 = fminf(floorf(u), (float)(F - 2));
+    const float i0 = fminf(floorf(v), (float)(F - 2));
+    const int base = (int)(sc.n_vox + (long long)s * sc.shell_texels);
+    const int idx0 = base + (int)i0 * sc.We + face * F + (int)j0;
+    return make_float4(__int_as_float(idx0), u - j0, v - i0, __int_as_float(1));
+}
+
+// Bilinear texels from a shell-hit entry: (first texel index, fu, fv, column
+// step to the second texel) -- the step is 1, or 1 - We across an
+// equirectangular map's longitude seam.
+__device__ __forceinline__ void shell_decode(const DevScene& sc, float4 e, ShellHit& hs) {
+    const int i0 = __float_as_int(e.x), dc = __float_as_int(e.w);
+    const float fu = e.y, fv = e.z;
+    hs.idx[0] = i0;
+    hs.idx[1] = i0 + dc;
+    hs.idx[2] = i0 + sc.We;
+    hs.idx[3] = i0 + sc.We + dc;
+    hs.w[0] = (1.0f - fu) * (1.0f - fv);
+    hs.w[1] = fu * (1.0f - fv);
+    hs.w[2] = (1.0f - fu) * fv;
+    hs.w[3] = fu * fv;
+}
+
+// The shell-hit entry of a ray that hits shell s.  Equirectangular maps: the
+// texel coordinates in FP64 from the binary32 ray (far root of |o + t d| = R,
+// azimuth atan2(y, x), polar angle from +z): a binary32 coordinate of a map
+// 1024 texels wide resolves only ~6e-5 of a texel, which moves the bilinear
+// weights by ~1e-4 relative.  Cube maps: the binary32 lookup (exact decisions).
+__device__ __forceinline__ float4 shell_entry(const DevScene& sc, const Ray& R, int s) {
+    if (sc.env_kind == 1) return cube_entry(sc, R, s);
+    const int base = (int)(sc.n_vox + (long long)s * sc.shell_texels);
+    const double o0 = R.o[0], o1 = R.o[1], o2 = R.o[2];
+    const double d0 = R.d[0], d1 = R.d[1], d2 = R.d[2];
+    const double b = o0 * d0 + o1 * d1 + o2 * d2;
+    const double oo = o0 * o0 + o1 * o1 + o2 * o2;
+    const double rad = (double)sc.R[s];
+    const double c = oo - rad * rad;
+    const double disc = fmax(b * b - c, 0.0);
+    const double sq = sqrt(disc);
+    const double t = (b < 0.0) ? (-b + sq) : (c / (-b - sq));
+    const double qx = o0 + t * d0, qy = o1 + t * d1, qz = o2 + t * d2;
+    const double r = sqrt(qx * qx + qy * qy + qz * qz);
+    const double wx = qx / r, wy = qy / r, wz = qz / r;
+    const double phi = atan2(wy, wx);
+    const double theta = atan2(sqrt(wx * wx + wy * wy), wz);
+    const double u = (phi / (2.0 * 3.141592653589793) + 0.5) * (double)sc.We - 0.5;
+    double v = theta / 3.141592653589793 * (double)sc.He - 0.5;
+    const double j0 = floor(u);
+    const double fu = u - j0;
+    int c0 = (int)((long long)j0 % sc.We);
+    if (c0 < 0) c0 += sc.We;
+    const int dcol = c0 + 1 < sc.We ? 1 : 1 - sc.We;
+    v = fmin(fmax(v, 0.0), (double)(sc.He - 1));
+    const double i0 = fmin(floor(v), (double)(sc.He - 2));
+    const double fv = v - i0;
+    const int idx0 = base + (int)i0 * sc.We + c0;
+    return make_float4(__int_as_float(idx0), (float)fu, (float)fv, __int_as_float(dcol));
+}
+
+__device__ __forceinline__ bool shell_lookup(const DevScene& sc, const Ray& R, long long ray, int s,
+                                             ShellHit& hs) {
     if (!(R.shell_hit & (1u << s))) return false;
+    if (sc.shell_tab) {
+        shell_decode(sc, __ldg(sc.shell_tab + ray * sc.S + s), hs);
+        return true;
+    }
+    if (sc.env_kind == 1) {
+        shell_decode(sc, cube_entry(sc, R, s), hs);
+        return true;
+    }
     const float b = R.o[0] * R.d[0] + R.o[1] * R.d[1] + R.o[2] * R.d[2];
     const float c = R.o[0] * R.o[0] + R.o[1] * R.o[1] + R.o[2] * R.o[2] - sc.R[s] * sc.R[s];
     const float disc = fmaxf(b * b - c, 0.0f);

@@ -102,6 +102,11 @@ cudaError_t launch_apply_coef(const DevScene& sc, const void* p, int p_dtype, co
 cudaError_t launch_apply_pair(const DevScene& sc, const float* xp, float* out, double* pap,
                               cudaStream_t st);
 
+// Shell-hit table of a scene (k_march.cu): n_rays x S float4 entries (first
+// texel index, fu, fv, column step) for the shells each ray hits, equirect
+// texel coordinates in FP64; a march reads it when sc.shell_tab is set.
+cudaError_t launch_shell_table(const DevScene& sc, float4* tab, cudaStream_t st);
+
 // Algorithm 2 vector work (k_pcg.cu).  Delta, rho, p: FP32 (p is also the
 // array the ray march gathers); p16 (may be null): its BF16 copy for BF16
 // scenes; Ap: FP32 scatter target, zeroed by begin and update; pxp (may be

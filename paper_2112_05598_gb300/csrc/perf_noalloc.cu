@@ -53,6 +53,9 @@ extern "C" perf_status perf_residual_noalloc(const perf_scene* sc, const perf_ca
     if (sc->n_shells < 0 || sc->n_shells > PERF_MAX_SHELLS) return PERF_ERR_INVALID_ARG;
     if (sc->dtype != PERF_F32 && sc->dtype != PERF_BF16) return PERF_ERR_INVALID_ARG;
     if (sc->n_shells > 0 && (sc->env_h < 2 || sc->env_w < 2)) return PERF_ERR_INVALID_ARG;
+    if (sc->env_kind != PERF_ENV_EQUIRECT && sc->env_kind != PERF_ENV_CUBE) return PERF_ERR_INVALID_ARG;
+    if (sc->env_kind == PERF_ENV_CUBE && sc->n_shells > 0 && sc->env_w != 6 * sc->env_h)
+        return PERF_ERR_INVALID_ARG;
     for (int s = 0; s < sc->n_shells; ++s) {
         if (!(sc->shell_radii[s] > 1.7320508f)) return PERF_ERR_INVALID_ARG;
         if (s > 0 && !(sc->shell_radii[s] > sc->shell_radii[s - 1])) return PERF_ERR_INVALID_ARG;
@@ -96,6 +99,7 @@ extern "C" perf_status perf_residual_noalloc(const perf_scene* sc, const perf_ca
     for (int q = 0; q < sc->n_shells; ++q) d.R[q] = sc->shell_radii[q];
     d.He = sc->n_shells > 0 ? sc->env_h : 0;
     d.We = sc->n_shells > 0 ? sc->env_w : 0;
+    d.env_kind = sc->env_kind;
     d.n_vox = G * G * G;
     d.shell_texels = texels;
     d.W = cams->width;

@@ -31,7 +31,7 @@ import numpy as np
 __all__ = [
     "SceneConfig", "Scene", "CONFIGS", "make_scene", "param_count",
     "look_at_c2w", "focal_from_fov", "constant_params", "random_params",
-    "ray_count",
+    "ray_count", "cube_texel_directions",
 ]
 
 
@@ -178,23 +178,55 @@ def _voxelise(rng, G, n_prims, kinds, size, sigma_inside=0.9):
     return grid
 
 
-def _env_noise(rng, H, W, sigma_max):
+def cube_texel_directions(F):
+    """Unit directions of the texel centres of a cube map with F x F texels
+    per face, as an F x 6F strip (face f = +x, -x, +y, -y, +z, -z in columns
+    [f F, (f + 1) F)).  On the face of axis a, with (b, c) the other two axes
+    in increasing order, texel (row i, column j) points along q_a = +-1,
+    q_b = 2 (j + 1/2) / F - 1, q_c = 2 (i + 1/2) / F - 1."""
+    st = 2.0 * (np.arange(F) + 0.5) / F - 1.0
+    out = np.zeros((F, 6 * F, 3))
+    for f in range(6):
+        a, sign = f // 2, (1.0 if f % 2 == 0 else -1.0)
+        b, c = [ax for ax in range(3) if ax != a]
+        q = np.zeros((F, F, 3))
+        q[..., a] = sign
+        q[..., b] = st[None, :]
+        q[..., c] = st[:, None]
+        out[:, f * F:(f + 1) * F] = q
+    return out / np.linalg.norm(out, axis=-1, keepdims=True)
+
+
+def _env_noise(rng, H, W, sigma_max, cube_face=None):
     """Smooth seeded noise: per channel a sum of 8 low-frequency sinusoids
     in (theta, phi), periodic in phi, mapped to [0, 1] (RGB) and
-    [0, sigma_max] (sigma)."""
+    [0, sigma_max] (sigma) by its range over the H x W equirectangular texel
+    grid.  With cube_face = F the same field is sampled at the texel centres
+    of a cube map (an F x 6F strip) instead, with the same mapping (clipped
+    to the range)."""
     theta = (np.arange(H) + 0.5) / H * np.pi
     phi = (np.arange(W) + 0.5) / W * 2.0 * np.pi - np.pi
     T, P = np.meshgrid(theta, phi, indexing="ij")
-    out = np.zeros((H, W, 4), dtype=np.float64)
+    if cube_face is not None:
+        d = cube_texel_directions(cube_face)
+        Tc = np.arctan2(np.hypot(d[..., 0], d[..., 1]), d[..., 2])
+        Pc = np.arctan2(d[..., 1], d[..., 0])
+    out = np.zeros((H, W, 4) if cube_face is None else (cube_face, 6 * cube_face, 4))
     for ch in range(4):
         acc = np.zeros((H, W))
+        accc = np.zeros(out.shape[:2])
         for _ in range(8):
             k = rng.uniform(0.5, 4.0)
             l = float(rng.integers(0, 5))
             ph = rng.uniform(0, 2 * np.pi)
-            acc += rng.uniform(0.3, 1.0) * np.sin(k * T + l * P + ph)
-        acc = (acc - acc.min()) / max(acc.max() - acc.min(), 1e-12)
-        out[..., ch] = acc if ch < 3 else sigma_max * acc
+            amp = rng.uniform(0.3, 1.0)
+            acc += amp * np.sin(k * T + l * P + ph)
+            if cube_face is not None:
+                accc += amp * np.sin(k * Tc + l * Pc + ph)
+        lo, span = acc.min(), max(acc.max() - acc.min(), 1e-12)
+        v = (acc if cube_face is None else accc) - lo
+        v = np.clip(v / span, 0.0, 1.0)
+        out[..., ch] = v if ch < 3 else sigma_max * v
     return out.astype(np.float32)
 
 
@@ -213,6 +245,7 @@ class Scene:
     x0: np.ndarray           # float32 [n] starting guess
     heldout_c2w: np.ndarray  # float32 [n_heldout, 3, 4]
     heldout_focal: np.ndarray
+    env_kind: int = 0        # 0 equirectangular shells, 1 cube maps (env_w = 6 env_h)
 
     @property
     def n_shells(self) -> int:
@@ -259,19 +292,27 @@ def make_cameras(rng, n, width, radius, layout, fov_deg, elev_deg=15.0):
 
 
 def make_scene(cfg, seed: Optional[int] = None, n_cams: Optional[int] = None,
-               G: Optional[int] = None) -> Scene:
+               G: Optional[int] = None, env: str = "equirect",
+               cube_face: Optional[int] = None) -> Scene:
     """Build the seeded scene of a workload.  ``n_cams`` / ``G`` override the
-    camera count or grid size (for reduced test cases)."""
+    camera count or grid size (for reduced test cases).  ``env="cube"``
+    stores the shells as cube maps of ``cube_face`` (default env_h // 2)
+    texels per face edge, sampled from the same smooth field; everything
+    else (grid, cameras, draws) is the same scene."""
     if isinstance(cfg, str):
         cfg = CONFIGS[cfg]
     if G is not None or n_cams is not None:
         cfg = dataclasses.replace(cfg, G=G or cfg.G, n_cams=n_cams or cfg.n_cams)
+    if env not in ("equirect", "cube"):
+        raise ValueError(env)
+    F = (cube_face or cfg.env_h // 2) if env == "cube" else None
+    env_h, env_w = (F, 6 * F) if F else (cfg.env_h, cfg.env_w)
     rng = np.random.default_rng(cfg.seed if seed is None else seed)
     grid = _voxelise(rng, cfg.G, cfg.n_prims, cfg.prim_kinds, cfg.prim_size)
     shells = []
     S = len(cfg.radii)
     for s in range(S):
-        env = _env_noise(rng, cfg.env_h, cfg.env_w, 3.0)
+        env = _env_noise(rng, cfg.env_h, cfg.env_w, 3.0, cube_face=F)
         if cfg.background_sigma is not None and s == S - 1:
             env[..., 3] = cfg.background_sigma
         shells.append(env.reshape(-1))
@@ -281,12 +322,11 @@ def make_scene(cfg, seed: Optional[int] = None, n_cams: Optional[int] = None,
     hc2w, hfocal = make_cameras(rng, cfg.n_heldout, cfg.width, cfg.cam_radius,
                                 "hemisphere" if cfg.cam_layout != "sphere"
                                 else "sphere", cfg.fov_deg)
-    x0 = constant_params(cfg.G, S, cfg.env_h, cfg.env_w,
-                         cfg.start_rgb, cfg.start_sigma)
+    x0 = constant_params(cfg.G, S, env_h, env_w, cfg.start_rgb, cfg.start_sigma)
     return Scene(cfg=cfg, G=cfg.G, radii=np.asarray(cfg.radii, np.float32),
-                 env_h=cfg.env_h, env_w=cfg.env_w, c2w=c2w, focal=focal,
+                 env_h=env_h, env_w=env_w, c2w=c2w, focal=focal,
                  width=cfg.width, height=cfg.height, x_gt=x_gt, x0=x0,
-                 heldout_c2w=hc2w, heldout_focal=hfocal)
+                 heldout_c2w=hc2w, heldout_focal=hfocal, env_kind=1 if F else 0)
 
 
 def sample_ray_ids(rng, n_rays: int, k: int) -> np.ndarray:

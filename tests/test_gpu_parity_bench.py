@@ -24,11 +24,11 @@ from gpu_common import (TOL_FP32, TOL_GN, assert_elementwise, assert_params, cud
 pytestmark = pytest.mark.gpu
 
 
-def _check(name, got, ref, tol=TOL_FP32):
+def _check(name, got, ref, mag=None, tol=TOL_FP32):
     err = rel_l2(got, ref)
     print(f"[parity] {name}: rel L2 {err:.3e}")
     assert err < tol, (name, err)
-    assert_elementwise(got, ref, what=name)
+    assert_elementwise(got, ref, mag, what=name)
 
 
 # ------------------------------------------------------------ 128^3 workload
@@ -62,7 +62,7 @@ def test_scale128_forward(s128):
     F = torch.zeros(1, dtype=torch.float64, device="cuda")
     ctx.residual(cuda_tensor(x), cuda_tensor(target), r, F)
     rref, Fref = orc.residual(x64, target)
-    _check("residual 128^3", host(r), rref)
+    _check("residual 128^3", host(r), rref, np.abs(rref + target) + np.abs(target))
     assert abs(host(F)[0] - Fref) <= TOL_FP32 * Fref
 
 
@@ -72,16 +72,16 @@ def test_scale128_jvp_vjp_apply(s128):
     p = rng.normal(size=ctx.n_params).astype(np.float32)
     jp = empty(3 * ctx.n_rays)
     ctx.jvp(cuda_tensor(x), cuda_tensor(p), jp)
-    jref = orc.jvp(x64, p.astype(np.float64))
-    _check("J p 128^3", host(jp), jref)
+    jref, jmag = orc.jvp(x64, p.astype(np.float64), mag=True)
+    _check("J p 128^3", host(jp), jref, jmag)
     v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
     out = empty(ctx.n_params)
     ctx.vjp(cuda_tensor(x), cuda_tensor(v), out)
-    _check("J^T v 128^3", host(out), orc.vjp(x64, v.astype(np.float64)))
+    _check("J^T v 128^3", host(out), *orc.vjp(x64, v.astype(np.float64), mag=True))
     ap = empty(ctx.n_params)
     pap = torch.zeros(1, dtype=torch.float64, device="cuda")
     ctx.apply_normal(cuda_tensor(x), cuda_tensor(p), ap, pap)
-    _check("A p (recomputed) 128^3", host(ap), orc.vjp(x64, jref))
+    _check("A p (recomputed) 128^3", host(ap), orc.vjp(x64, jref), orc.vjp(x64, jmag, mag=True)[1])
     assert abs(host(pap)[0] - float(jref @ jref)) <= TOL_FP32 * float(jref @ jref)
 
 
@@ -94,7 +94,7 @@ def test_scale128_diag_grad(s128):
     ctx.diag_jtj(cuda_tensor(x), d, cuda_tensor(r32), g)
     dref, gref = orc.diag_grad(x64, r32.astype(np.float64))
     _check("diag 128^3", host(d), dref)
-    _check("grad 128^3", host(g), gref)
+    _check("grad 128^3", host(g), gref, orc.vjp(x64, r32.astype(np.float64), mag=True)[1])
 
 
 @pytest.mark.parametrize("coef", [True, False])
@@ -157,15 +157,15 @@ def test_bf16_256_render_jvp_vjp_apply_diag(b256):
     p = rng.normal(size=ctx.n_params).astype(np.float32)
     jp = empty(3 * ctx.n_rays)
     ctx.jvp(x16, cuda_tensor(p), jp)
-    jref = orc.jvp(xq, p.astype(np.float64))
-    _check("J p 256^3 bf16", host(jp), jref)
+    jref, jmag = orc.jvp(xq, p.astype(np.float64), mag=True)
+    _check("J p 256^3 bf16", host(jp), jref, jmag)
     v = rng.normal(size=3 * ctx.n_rays).astype(np.float32)
     out = empty(ctx.n_params)
     ctx.vjp(x16, cuda_tensor(v), out)
-    _check("J^T v 256^3 bf16", host(out), orc.vjp(xq, v.astype(np.float64)))
+    _check("J^T v 256^3 bf16", host(out), *orc.vjp(xq, v.astype(np.float64), mag=True))
     ap = empty(ctx.n_params)
     ctx.apply_normal(x16, cuda_tensor(p), ap)
-    _check("A p 256^3 bf16", host(ap), orc.vjp(xq, jref))
+    _check("A p 256^3 bf16", host(ap), orc.vjp(xq, jref), orc.vjp(xq, jmag, mag=True)[1])
     d = empty(ctx.n_params)
     ctx.diag_jtj(x16, d)
     _check("diag 256^3 bf16", host(d), orc.diag_grad(xq)[0])
@@ -212,7 +212,8 @@ def test_batch_against_oracle():
     rh, Fh = host(r), host(F)
     for i, s in enumerate(scenes):
         rref, Fref = s["orc"].residual(s["x"].astype(np.float64), s["target"])
-        _check(f"batch residual scene {i}", rh[3 * b.ray_off[i]:3 * b.ray_off[i + 1]], rref)
+        _check(f"batch residual scene {i}", rh[3 * b.ray_off[i]:3 * b.ray_off[i + 1]], rref,
+               np.abs(rref + s["target"]) + np.abs(s["target"]))
         assert abs(Fh[i] - Fref) <= TOL_FP32 * Fref
     checked = 0
     for step in range(2):
@@ -234,29 +235,29 @@ def test_batch_against_oracle():
 # ------------------------------------------------------------ paper-mode PCG
 
 
-def _near_threshold(R, R0, eps_rel, stall, rel=2e-2):
-    """True when some exit test of the oracle's trajectory comes within `rel`
-    of its threshold.  After ten or more CG iterations the FP32 rounding of
-    A p moves R_k / R_(k-1) by up to about a percent (CG amplifies it, see the
-    CG-sensitivity pins), so such a test may fire one iteration earlier or
-    later on the GPU."""
-    prev = R0
-    for Rk in R:
+def _near_iterations(R, R0, eps_rel, stall, rel=2e-2):
+    """Iterations k (1-based) at which an exit test of the oracle's trajectory
+    came within `rel` of firing.  After ten or more CG iterations the FP32
+    rounding of A p moves R_k / R_(k-1) by up to about a percent (CG
+    amplifies it, see the CG-sensitivity pins), so such a test may fire on
+    the GPU where the oracle's narrowly did not, or the other way round."""
+    near, prev = set(), R0
+    for k, Rk in enumerate(R, start=1):
         if abs(Rk - eps_rel * eps_rel * R0) <= rel * eps_rel * eps_rel * R0:
-            return True
+            near.add(k)
         if abs(Rk / prev - stall) <= rel * stall:
-            return True
+            near.add(k)
         prev = Rk
-    return False
+    return near
 
 
 def test_paper_mode_pcg_exits_against_oracle():
     """Algorithm 2 with its exits (R < eps^2 R_0, R / R_prev > stall) on the
     single-scene path against the oracle's pcg(fixed=False): the exit reason
-    agrees on every system and the number of iterations agrees exactly unless
-    an exit test of the oracle's trajectory came within 2 % of its threshold
-    (then within one iteration); both the residual exit and the stall exit
-    occur, and most systems are compared exactly."""
+    agrees on every system, and the GPU stops at the oracle's iteration or at
+    an earlier one where the oracle's own exit test came within 2 % of
+    firing; both the residual exit and the stall exit occur, and most
+    systems stop at exactly the oracle's iteration."""
     from oracle import gn_step
     from paper_2112_05598_gb300 import Context
     from scenegen import make_scene
@@ -278,16 +279,15 @@ def test_paper_mode_pcg_exits_against_oracle():
             r, _ = orc.residual(x0.astype(np.float64), target)
             _, g = orc.diag_grad(x0.astype(np.float64), r)
             R0 = float(g @ g)
-            near = _near_threshold(ref.pcg.R, R0, eps_rel, stall)
+            near = _near_iterations(ref.pcg.R, R0, eps_rel, stall)
             exit_ref = ref.pcg.exit
             print(f"[paper mode] eps {eps_rel} stall {stall} cap {cap}: GPU {st['pcg_iters']} "
-                  f"{st['pcg_exit']}, oracle {ref.pcg.iters} {exit_ref}{' (near)' if near else ''}")
+                  f"{st['pcg_exit']}, oracle {ref.pcg.iters} {exit_ref} (near at {sorted(near)})")
             assert st["pcg_exit"] == exit_ref, (eps_rel, stall, st["pcg_exit"], exit_ref)
-            if near:
-                assert abs(st["pcg_iters"] - ref.pcg.iters) <= 1, (eps_rel, stall, st, ref.pcg.iters)
-            else:
-                assert st["pcg_iters"] == ref.pcg.iters, (eps_rel, stall, st, ref.pcg.iters)
-                compared += 1
+            ok = st["pcg_iters"] == ref.pcg.iters or (st["pcg_iters"] < ref.pcg.iters and
+                                                       st["pcg_iters"] in near)
+            assert ok, (eps_rel, stall, st["pcg_iters"], ref.pcg.iters, sorted(near))
+            compared += st["pcg_iters"] == ref.pcg.iters
             seen.add(exit_ref)
     assert compared >= 6
     assert {"eps", "stall"} <= seen, seen

@@ -236,3 +236,75 @@ def test_block_cross_is_column_products_of_dense_J():
     assert np.abs(ref).max() > 1e-3
     assert np.abs(cross - ref).max() <= 1e-7 * np.abs(ref).max()
     assert np.abs(diag - np.sum(J * J, axis=0)).max() <= 1e-7 * np.abs(diag).max()
+
+
+# ---------------------------------------------------------- cube-map texels
+
+# Hand-worked texels of a cube map with F = 4 texels per face edge (a 4 x 24
+# strip; face f = +x, -x, +y, -y, +z, -z in columns [4 f, 4 f + 4)), read
+# along directions from a camera at the origin.  On the face of the largest
+# |q_a| (ties to the lower axis), with (b, c) the other axes in increasing
+# order, s = q_b / |q_a|, t = q_c / |q_a|, column coordinate u = 2 s + 1.5 and
+# row coordinate v = 2 t + 1.5 (texel i centred at i), clamped to [0, 3].
+# Each entry: direction, (row value, strip-column value) of a map whose texel
+# (row, column) holds colour (row, column, 0).
+#   +x: face 0, s = t = 0: u = v = 1.5 -> (1.5, 0 + 1.5)
+#   -x: face 1 -> (1.5, 4 + 1.5); +y: face 2 -> (1.5, 8 + 1.5); -y: face 3 ->
+#   (1.5, 12 + 1.5); +z: face 4 -> (1.5, 16 + 1.5); -z: face 5 -> (1.5, 20 + 1.5)
+#   (0.5, 1, 0.25): face 2 (+y), s = 0.5, t = 0.25: u = 2.5, v = 2.0 -> (2.0, 10.5)
+#   (1, 1, 0): |x| = |y|, the tie goes to x: face 0, s = 1: u = 3.5 -> clamped
+#       to the edge texel 3; t = 0: v = 1.5 -> (1.5, 3.0)
+#   (-1, -0.5, 0.5): face 1 (-x), s = -0.5, t = 0.5: u = 0.5, v = 2.5 -> (2.5, 4.5)
+#   (0.2, -0.99, -0.95): face 3 (-y), s = 0.2 / 0.99 = 0.2020202,
+#       t = -0.95 / 0.99 = -0.9595960: u = 1.9040404, v = -0.419 -> row 0
+#       -> (0.0, 12 + 1.9040404)
+CUBE_CASES = [
+    ((1.0, 0.0, 0.0), 1.5, 1.5),
+    ((-1.0, 0.0, 0.0), 1.5, 5.5),
+    ((0.0, 1.0, 0.0), 1.5, 9.5),
+    ((0.0, -1.0, 0.0), 1.5, 13.5),
+    ((0.0, 0.0, 1.0), 1.5, 17.5),
+    ((0.0, 0.0, -1.0), 1.5, 21.5),
+    ((0.5, 1.0, 0.25), 2.0, 10.5),
+    ((1.0, 1.0, 0.0), 1.5, 3.0),
+    ((-1.0, -0.5, 0.5), 2.5, 4.5),
+    ((0.2, -0.99, -0.95), 0.0, 13.9040404),
+]
+
+
+def test_cube_map_texels_by_hand():
+    F, sig = 4, 2.0
+    c2w = np.stack([_camera_looking(c[0]) for c in CUBE_CASES]).astype(np.float32)
+    orc = Oracle(2, [2.5], F, 6 * F, c2w, np.ones(len(CUBE_CASES), np.float32), 1, 1,
+                 max_samples=64, env_kind=1)
+    x = np.zeros(orc.n_params).reshape(-1, 4)
+    rows, cols = np.meshgrid(np.arange(F), np.arange(6 * F), indexing="ij")
+    x[8:, 0] = rows.reshape(-1)
+    x[8:, 1] = cols.reshape(-1)
+    x[8:, 3] = sig
+    rgb = orc.render(x.reshape(-1))[0]
+    a = 1.0 - math.exp(-sig)
+    for i, (d, row_v, col_v) in enumerate(CUBE_CASES):
+        assert abs(rgb[i, 0] - a * row_v) < 2e-6, (d, rgb[i] / a)
+        assert abs(rgb[i, 1] - a * col_v) < 2e-6, (d, rgb[i] / a)
+
+
+def test_cube_map_derivatives_match_finite_differences():
+    """J with cube-map shells: columns of J p and rows of J^T v against central
+    differences of the forward model, and the diagonal against column norms."""
+    from test_oracle_pins import fd_jacobian, _orc
+    rng = np.random.default_rng(71)
+    prob = tiny_problem(rng, env_h=2, env_w=12, n_cams=3)
+    orc = _orc(prob, env_kind=1)
+    x = prob["x"].astype(np.float64)
+    J = fd_jacobian(orc, x)
+    nv = 4 * prob["G"] ** 3
+    assert np.abs(J[:, nv:]).max() > 1e-3          # the cube-map texels are seen
+    n = x.shape[0]
+    for j in range(0, n, 3):
+        e = np.zeros(n); e[j] = 1.0
+        assert np.abs(orc.jvp(x, e) - J[:, j]).max() <= 1e-7 * np.abs(J).max() + 1e-9
+    v = rng.normal(size=J.shape[0])
+    assert np.abs(orc.vjp(x, v) - J.T @ v).max() <= 1e-7 * np.abs(J.T @ v).max()
+    d, _ = orc.diag_grad(x)
+    assert np.abs(d - np.sum(J * J, axis=0)).max() <= 1e-7 * d.max()
