@@ -169,6 +169,9 @@ def parse():
     ap.add_argument("--coef-budget", type=int, default=-1,
                     help="bytes for the coefficient store (-1: free memory - 6 GiB; 0: off, every "
                          "A p recomputes)")
+    ap.add_argument("--tiling", default=None,
+                    help="tw,sx,sy: fix the ray tiling (tile width, sub-tile interleave) instead of "
+                         "autotuning it")
     ap.add_argument("--conv", type=int, default=0,
                     help="time the learned preconditioner's 4-layer network on a G^3 grid")
     return ap.parse_args()
@@ -763,10 +766,18 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         ctx.gn_solve(x, target, 1)
     # tile shape / CTA cap tuned at the warmed-up state along a random direction
-    gp = torch.Generator(device=dev).manual_seed(0)
-    probe = torch.randn(sc.n_params, device=dev, generator=gp).to(sdt)
-    tuning = ctx.autotune(x.to(sdt) if bf else x, probe)
-    del probe
+    if args.tiling:
+        tw, sx, sy = (int(v) for v in args.tiling.split(","))
+        ctx.set_tiling(tw, sx, sy)
+        ctx.gn_solve(x, target, 1)          # lays the coefficient store out for it
+        tuning = {"tile_w": tw, "tile_h": 32 // tw, "ctas_per_sm": 0, "apply_ms": None,
+                  "paired": 0, "coef": int(ctx.coef_info()["used"]), "rays_per_thread": sx * sy,
+                  "fixed": True}
+    else:
+        gp = torch.Generator(device=dev).manual_seed(0)
+        probe = torch.randn(sc.n_params, device=dev, generator=gp).to(sdt)
+        tuning = ctx.autotune(x.to(sdt) if bf else x, probe)
+        del probe
     torch.cuda.synchronize()
     ctx.enable_timing(True)
     ctx.timing(reset=True)

@@ -167,6 +167,11 @@ typedef struct {
                                  32-byte records (FP32 scenes); 0: two arrays */
     int32_t coef;             /* 1: the coefficient-cached A p was timed (it is
                                  what perf_gn_solve runs while the store fits) */
+    int32_t rays_per_thread;  /* coefficient-cached A p: 1, or 2 / 4 neighbouring
+                                 rays per thread (2 x 1 / 2 x 2 pixels, tiles
+                                 interleaved so that lane l of consecutive tiles
+                                 covers them) whose equal-voxel contributions
+                                 are added before one atomic */
 } perf_tuning;
 
 /* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
@@ -273,6 +278,17 @@ perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_bl
 perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes);
 perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
                            double* coverage);
+/* Ray tiling of the context's marches: tiles of tile_w x (32 / tile_w) pixels
+ * (tile_w in {4, 8, 16, 32}), interleaved by (sx, sy) in {1, 2}^2: a block of
+ * tile_w sx x (32 / tile_w) sy pixels is split into sx sy consecutive tiles,
+ * sub-tile (ox, oy) holding every sx-th column from ox and every sy-th row
+ * from oy, so lane l of the block's tiles covers neighbouring pixels.  With
+ * sx sy = 2 or 4 the coefficient-cached A p gives those neighbouring rays to
+ * one thread and adds their contributions to a voxel before its atomic.
+ * Results do not depend on the tiling beyond FP32 summation order.  The next
+ * Gauss-Newton step lays the coefficient store out anew.  perf_autotune
+ * chooses among these tilings. */
+perf_status perf_set_tiling(perf_ctx* ctx, int32_t tile_w, int32_t sx, int32_t sy);
 /* Times the A p launch at x along p (both in the scene storage type; p NULL:
  * p = x) over tile shapes 8x4, 4x8, 16x2, 32x1 and resident-CTA caps
  * {all, 3, 2} (two timed launches each), keeps the fastest for every later

@@ -42,33 +42,31 @@ def assert_elementwise(a, b, mag=None, rel=EW_REL, abs_frac=EW_ABS, what=""):
     assert ratio[i] <= 1.0, (what, i, a[i], b[i], m[i], ratio[i])
 
 
-# Parameters seen only through interpolation weights of order 1e-5 (a texel
-# at the edge of a bilinear footprint, a voxel at the corner of a trilinear
-# stencil on grazing rays) have Jacobi diagonals below ~1e-10 of the largest.
-# Their rows of J are fixed by the binary32 sample and texel coordinates only
-# to a relative accuracy of (coordinate rounding) / weight, and the Jacobi-
-# scaled step multiplies them by 1 / diagonal, to |Delta| ~ 1e5: on the 128^3
-# workload 35 of 2.2 M observed blocks carry 99.7 % of |Delta|^2.  The
-# parameter bar applies to every other block; these are checked for validity.
+# Parameters seen only through interpolation weights of order 1e-5 have
+# Jacobi diagonals below ~1e-10 of the largest, and the Jacobi-scaled step
+# gives them |Delta| ~ 1e5: on the 128^3 workload from the constant start,
+# 35 of 2.2 M observed blocks carry 99.7 % of |Delta|^2.  Their rows of J
+# must therefore agree to FP32 rounding, which is why the shells' texel
+# coordinates are FP64 (a binary32 coordinate of a 1024-texel map resolves
+# only ~6e-5 of a texel) and the grid's sample coordinates are binary32 on
+# both sides.  The bar applies to all parameters; the split by observability
+# is printed to show where the difference sits.
 WEAK_DIAG = 1e-10
 
 
-def assert_params(xg, xo, diag, tol=1e-4, what="x", weak=WEAK_DIAG, max_weak_frac=1e-4):
-    """x after a Gauss-Newton step: relative L2 below tol over the blocks
-    whose largest Jacobi diagonal entry exceeds weak x its maximum (and the
-    unobserved ones, which must stay put on both sides); the weakly observed
-    rest must be few, finite and inside the projection's bounds."""
+def assert_params(xg, xo, diag, tol=1e-4, what="x", weak=WEAK_DIAG):
+    """x after a Gauss-Newton step: relative L2 below tol over all parameters,
+    every value finite and inside the projection's bounds."""
     xg = np.asarray(xg, np.float64).reshape(-1, 4)
     xo = np.asarray(xo, np.float64).reshape(-1, 4)
     blk = np.asarray(diag, np.float64).reshape(-1, 4).max(1)
     w = (blk > 0) & (blk <= weak * blk.max())
-    err = rel_l2(xg[~w], xo[~w])
-    print(f"[params] {what}: rel L2 {err:.3e} over {int((~w).sum())} blocks "
-          f"({int(w.sum())} weakly observed blocks set aside; all blocks {rel_l2(xg, xo):.3e})")
+    err = rel_l2(xg, xo)
+    print(f"[params] {what}: rel L2 {err:.3e} (over the {int((~w).sum())} blocks with diagonal "
+          f"above {weak:g} x max: {rel_l2(xg[~w], xo[~w]):.3e}; {int(w.sum())} below)")
     assert err < tol, (what, err)
-    assert w.sum() <= max_weak_frac * len(blk), (what, int(w.sum()))
-    assert np.all(np.isfinite(xg[w]))
-    assert np.all(xg[w][:, :3] >= 0) and np.all(xg[w][:, :3] <= 1) and np.all(xg[w][:, 3] >= 0)
+    assert np.all(np.isfinite(xg))
+    assert np.all(xg[:, :3] >= 0) and np.all(xg[:, :3] <= 1) and np.all(xg[:, 3] >= 0)
 
 
 def cuda_tensor(a, dtype=None):
