@@ -163,12 +163,17 @@ def parse():
     ap.add_argument("--lpc-scenes", type=int, default=100)
     ap.add_argument("--lpc-steps", type=int, default=20)
     ap.add_argument("--lpc-epochs", type=int, default=2)
-    ap.add_argument("--lpc-gn", type=int, default=6)
+    ap.add_argument("--lpc-gn", type=int, default=30)
     ap.add_argument("--lpc-pcg", type=int, default=5)
-    ap.add_argument("--lpc-traj", type=int, default=60)
+    ap.add_argument("--lpc-traj", type=int, default=400)
+    ap.add_argument("--no-lpc-record", action="store_true",
+                    help="leave the learned-preconditioner record out of the default line")
     ap.add_argument("--coef-budget", type=int, default=-1,
                     help="bytes for the coefficient store (-1: free memory - 6 GiB; 0: off, every "
                          "A p recomputes)")
+    ap.add_argument("--compare", action="store_true",
+                    help="32^3 workload: Gauss-Newton vs Adam (time to held-out PSNR) and "
+                         "equirectangular vs cube-map shells")
     ap.add_argument("--tiling", default=None,
                     help="tw,sx,sy: fix the ray tiling (tile width, sub-tile interleave) instead of "
                          "autotuning it")
@@ -390,53 +395,64 @@ def run_conv(args, rank, world, local):
         print(json.dumps(line), flush=True)
 
 
-def run_lpc(args, rank, world, local):
-    """Learned block preconditioner vs Jacobi (and exact block-Jacobi) on the
-    ring workload (256^3, 4 shells, 150 cameras 960x540 on a 360-degree ring,
-    opaque textured background).  The network is first trained on systems the
-    solver logs from Gauss-Newton runs of 32^3 scenes (the small workload's
-    recipe, seeds 0..N); every method then runs GN steps from the same start
-    with PCG to a relative residual of 1e-3 (at most --lpc-max-iter
-    iterations), and held-out-view PSNR is recorded after each step."""
+def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train_large=8,
+              epochs=2, gn_steps=20, pcg_per_step=5, traj_iters=300, seed=7):
+    """Learned block preconditioner vs Jacobi (and exact block-Jacobi).
+
+    Training: the network learns from Gauss-Newton systems the solver logs on
+    its own runs -- train_small seeded 32^3 scenes (train_steps steps each) and
+    train_large systems of the 128^3 workload restricted to 8 cameras -- with
+    the library's BF16 kernels.  Evaluation on `workload`: (a) the first
+    Gauss-Newton system's PCG through the solver's own path (coefficient
+    store) until a relative residual of 1e-3 or traj_iters iterations: the
+    residual history and the iterations to 1e-1, 1e-2, 1e-3; (b) gn_steps
+    Gauss-Newton steps with pcg_per_step PCG iterations from the workload's
+    start, held-out-view PSNR against device time, and the time each method
+    needs to reach Jacobi's final PSNR - 0.1 dB."""
     import torch
-    import __graft_entry__
-    __graft_entry__.build()
     from paper_2112_05598_gb300 import (Context, LPC, PERF_PRECOND_BLOCK4,
                                         PERF_PRECOND_BLOCK_JACOBI, PERF_PRECOND_JACOBI)
     from paper_2112_05598_gb300 import lpc_train as T
     from scenegen import make_scene
-    if rank != 0:
-        return
-    dev = torch.device("cuda", local)
     gen = torch.Generator(device=dev).manual_seed(0)
-    # 1. log systems from the solver's own runs on small scenes
     t0 = time.perf_counter()
-    net = LPC(seed=7)
+    net = LPC(seed=seed)
     systems = []
-    n_train_scenes = args.lpc_scenes
-    for seed in range(n_train_scenes):
-        sc = make_scene("small32", seed=2000 + seed)
+    for k in range(train_small):
+        sc = make_scene("small32", seed=2000 + k)
         ctx = Context.from_scene(sc, pcg_iters=5, pcg_fixed=1)
         target = torch.empty(3 * ctx.n_rays, device=dev)
         ctx.render(torch.from_numpy(sc.x_gt).to(dev), target)
         x = torch.from_numpy(sc.x0.copy()).to(dev)
-        for _ in range(args.lpc_steps):
+        for _ in range(train_steps):
             systems.append(T.log_system(ctx, net, x, target, n_probes=1, generator=gen))
             ctx.gn_solve(x, target, 1)
         ctx.close()
+    if train_large > 0:
+        sc = make_scene("scale128", n_cams=8)
+        ctx = Context.from_scene(sc, pcg_iters=5, pcg_fixed=1)
+        target = torch.empty(3 * ctx.n_rays, device=dev)
+        ctx.render(torch.from_numpy(sc.x_gt).to(dev), target)
+        x = torch.from_numpy(sc.x0.copy()).to(dev)
+        for _ in range(train_large):
+            systems.append(T.log_system(ctx, net, x, target, n_probes=1, generator=gen))
+            ctx.gn_solve(x, target, 1)
+        ctx.close()
+        del x, target
     t_log = time.perf_counter() - t0
-    held = systems[-max(1, len(systems) // 10):]
-    train = systems[:len(systems) - len(held)]
+    held = systems[:: max(1, len(systems) // max(1, len(systems) // 10))][: max(1, len(systems) // 10)]
+    held_ids = {id(h) for h in held}
+    train = [s_ for s_ in systems if id(s_) not in held_ids]
     loss0 = T.mean_loss(net, held)
     t0 = time.perf_counter()
-    T.train(net, train, epochs=args.lpc_epochs, lr=1e-3)
+    T.train(net, train, epochs=epochs, lr=1e-3)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
     loss1 = T.mean_loss(net, held)
+    n_sys = len(systems)
     del systems, train, held
-    # 2. evaluate on the ring workload
-    from paper_2112_05598_gb300 import block_jacobi
-    sc = make_scene(args.workload, n_cams=args.cams)
+    torch.cuda.empty_cache()
+    sc = make_scene(workload, n_cams=n_cams)
     ctx = Context.from_scene(sc)
     hold = Context.from_scene(sc, c2w=sc.heldout_c2w, focal=sc.heldout_focal)
     x_gt = torch.from_numpy(sc.x_gt).to(dev)
@@ -446,95 +462,71 @@ def run_lpc(args, rank, world, local):
     hold.render(x_gt, htarget)
     del x_gt
     F = torch.zeros(1, dtype=torch.float64, device=dev)
-    G, n, V = sc.G, sc.n_params, sc.G ** 3
-    # 2a. PCG residual trajectories on the first Gauss-Newton system
-    x = torch.from_numpy(sc.x0.copy()).to(dev)
-    r = torch.empty(3 * ctx.n_rays, device=dev)
-    ctx.residual(x, target, r, F)
-    d = torch.empty(n, device=dev)
-    g = torch.empty(n, device=dev)
-    ctx.diag_jtj(x, d, r, g)
-    del r
-    d2 = torch.empty(n, device=dev)
-    cross = torch.empty(4 * V, device=dev)
-    ctx.diag_cross(x, d2, cross)
-    del d2
-    blocks = torch.empty(16 * V, device=dev)
-    traj = {}
-    t_blocks = {}
-    for name in ("jacobi", "learned", "block_jacobi"):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record()
-        if name == "learned":
-            feat = torch.empty(16 * V, dtype=torch.bfloat16, device=dev)
-            net.features(G, x, g, d, cross, feat)
-            net.infer(G, feat, d, blocks)
-            del feat
-        elif name == "block_jacobi":
-            block_jacobi(G, d, cross, blocks)
-        e1.record()
-        torch.cuda.synchronize()
-        t_blocks[name] = e0.elapsed_time(e1)
-        if name == "jacobi":
-            ctx.set_options(precond=PERF_PRECOND_JACOBI, pcg_iters=args.lpc_traj, pcg_fixed=1)
-        else:
-            ctx.set_blocks(blocks, V)
-            ctx.set_options(precond=PERF_PRECOND_BLOCK4, pcg_iters=args.lpc_traj, pcg_fixed=1)
-        ctx.pcg_begin(g, d)
-        rel = []
-        e0.record()
-        for _ in range(args.lpc_traj):
-            ctx.pcg_step(x)
-            info = ctx.pcg_result()
-            rel.append(float(np.sqrt(info["R"] / info["R0"])))
-        e1.record()
-        torch.cuda.synchronize()
-        first = {f"{t:g}": next((k + 1 for k, v in enumerate(rel) if v < t), None)
-                 for t in (1e-1, 1e-2, 1e-3)}
-        traj[name] = {"rel_residual": rel, "iters_to": first,
-                      "ms_per_iter": e0.elapsed_time(e1) / args.lpc_traj,
-                      "ms_preconditioner_setup": t_blocks[name]}
-    del blocks, cross, d, g
-    ctx.set_blocks(None, 0)
-    # 2b. Gauss-Newton with few PCG iterations per step: time to PSNR
-    results = {}
-    for name, pc in (("jacobi", PERF_PRECOND_JACOBI), ("learned", PERF_PRECOND_BLOCK4),
-                     ("block_jacobi", PERF_PRECOND_BLOCK_JACOBI)):
-        x = torch.from_numpy(sc.x0.copy()).to(dev)
-        ctx.set_options(pcg_iters=args.lpc_pcg, pcg_fixed=1, precond=pc)
+    methods = (("jacobi", PERF_PRECOND_JACOBI), ("learned", PERF_PRECOND_BLOCK4),
+               ("block_jacobi", PERF_PRECOND_BLOCK_JACOBI))
+    x0 = torch.from_numpy(sc.x0.copy()).to(dev)
+    first = {}
+    for name, pc in methods:
+        ctx.set_lpc(net if pc == PERF_PRECOND_BLOCK4 else None)
+        it = T.pcg_iterations(ctx, x0, target, pc, eps=1e-3, max_iter=traj_iters)
+        rel = it["rel_residual"]
+        first[name] = {"iters_to": it["iters_to"], "iters": it["iters"], "exit": it["exit"],
+                       "ms_per_iter": it["ms"] / max(it["iters"], 1),
+                       "rel_residual_at": {str(k): rel[k - 1] for k in (5, 10, 20, 50, 100, 200, 300)
+                                           if k <= len(rel)},
+                       "fallback": it["fallback"]}
+    runs = {}
+    for name, pc in methods:
+        x = x0.clone()
+        ctx.set_options(pcg_iters=pcg_per_step, pcg_fixed=1, precond=pc)
         ctx.set_lpc(net if pc == PERF_PRECOND_BLOCK4 else None)
         hold.residual(x, htarget, None, F)
         curve = [(0.0, _psnr_from_F(float(F.item()), hold.n_rays))]
-        steps = []
-        t_acc = 0.0
-        for _ in range(args.lpc_gn):
+        t_acc, fb = 0.0, 0
+        for _ in range(gn_steps):
             st = ctx.gn_solve(x, target, 1)[0]
             t_acc += st["ms"] / 1000.0
+            fb += int(st["precond_fallback"])
             hold.residual(x, htarget, None, F)
             curve.append((t_acc, _psnr_from_F(float(F.item()), hold.n_rays)))
-            steps.append({"rel_residual": float(np.sqrt(st["R"] / st["R0"])) if st["R0"] > 0 else None,
-                          "ms": st["ms"], "F_after": st["F_after"], "gamma": st["gamma"],
-                          "fallback": st["precond_fallback"]})
-        results[name] = {"steps": steps, "psnr_curve": curve, "coef_store": ctx.coef_info()}
-    target_psnr = results["jacobi"]["psnr_curve"][-1][1] - 0.1
+        runs[name] = {"psnr_curve": curve, "fallbacks": fb}
+    target_db = runs["jacobi"]["psnr_curve"][-1][1] - 0.1
 
     def time_to(curve):
-        for t, pv in curve:
-            if pv >= target_psnr:
-                return t
-        return None
-    line = {"metric": "PCG iterations to relative residual and time-to-PSNR, learned vs Jacobi",
-            "workload": f"{args.workload}: {sc.G}^3, {sc.n_shells} shells {sc.env_h}x{sc.env_w}, "
-                        f"{sc.n_cams} cameras {sc.width}x{sc.height} ring, background shell sigma 10",
-            "training": {"systems": n_train_scenes * args.lpc_steps, "scenes": n_train_scenes,
-                         "epochs": args.lpc_epochs, "log_s": t_log, "train_s": t_train,
-                         "held_out_probe_loss_identity": loss0, "held_out_probe_loss_trained": loss1},
-            "first_system_pcg": traj,
-            "gn": {"pcg_iters_per_step": args.lpc_pcg, "target_psnr_db": target_psnr,
-                   "time_to_psnr_s": {k: time_to(v["psnr_curve"]) for k, v in results.items()},
-                   "runs": results}}
-    print(json.dumps(line), flush=True)
+        return next((t for t, p in curve if p >= target_db), None)
+    ctx.close()
+    hold.close()
+    return {"workload": f"{workload}: {sc.G}^3, {sc.n_shells} shells {sc.env_h}x{sc.env_w}, "
+                        f"{sc.n_cams} cameras {sc.width}x{sc.height} "
+                        f"({sc.cfg.cam_layout}), background shell sigma "
+                        f"{sc.cfg.background_sigma}",
+            "training": {"systems": n_sys, "small32_scenes": train_small,
+                         "scale128_systems": train_large, "epochs": epochs, "log_s": t_log,
+                         "train_s": t_train, "held_out_probe_loss_identity": loss0,
+                         "held_out_probe_loss_trained": loss1},
+            "first_system_pcg": first,
+            "gn": {"steps": gn_steps, "pcg_iters_per_step": pcg_per_step,
+                   "target_psnr_db": target_db,
+                   "time_to_psnr_s": {k: time_to(v["psnr_curve"]) for k, v in runs.items()},
+                   "final_psnr_db": {k: v["psnr_curve"][-1][1] for k, v in runs.items()},
+                   "runs": runs}}
+
+
+def run_lpc(args, rank, world, local):
+    """The learned-preconditioner study (lpc_study) on --workload (default
+    the full ring workload: 256^3, 4 shells, 150 cameras 960x540 on a ring)."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    wl = args.workload if args.workload != WORKLOAD else "ring256"
+    res = lpc_study(dev, wl, n_cams=args.cams, train_small=args.lpc_scenes,
+                    train_steps=args.lpc_steps, epochs=args.lpc_epochs, gn_steps=args.lpc_gn,
+                    pcg_per_step=args.lpc_pcg, traj_iters=args.lpc_traj)
+    print(json.dumps(dict(metric="PCG iterations to relative residual and time-to-PSNR, "
+                                 "learned vs Jacobi", **res)), flush=True)
 
 
 def run_hier(args, rank, world, local):
@@ -656,6 +648,98 @@ def run_hier(args, rank, world, local):
             "runs": runs}
     for h, _ in holds.values():
         h.close()
+    print(json.dumps(line), flush=True)
+
+
+def run_compare(args, rank, world, local):
+    """The 32^3 workload (8 cameras 64x64, 2 shells, 5 Gauss-Newton steps x 20
+    PCG iterations): (1) Gauss-Newton against Adam on the same objective and
+    gradient -- the paper's Fig. 1 contrast -- with Adam's learning rate swept
+    and given at least Gauss-Newton's wall time; (2) the environment shells
+    as equirectangular maps (32 x 64) against cube maps (16 x 16 per face) of
+    the same smooth field.  Held-out-view PSNR against device time."""
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2112_05598_gb300 import Context
+    from scenegen import make_scene
+    if rank != 0:
+        return
+    dev = torch.device("cuda", local)
+    F = torch.zeros(1, dtype=torch.float64, device=dev)
+
+    def setup(env):
+        sc = make_scene("small32", env=env)
+        ctx = Context.from_scene(sc, pcg_iters=sc.cfg.pcg_iters, pcg_fixed=1)
+        hold = Context.from_scene(sc, c2w=sc.heldout_c2w, focal=sc.heldout_focal)
+        gt = torch.from_numpy(sc.x_gt).to(dev)
+        target = torch.empty(3 * ctx.n_rays, device=dev)
+        ctx.render(gt, target)
+        htarget = torch.empty(3 * hold.n_rays, device=dev)
+        hold.render(gt, htarget)
+        return sc, ctx, hold, target, htarget
+
+    def psnr(hold, htarget, x):
+        hold.residual(x, htarget, None, F)
+        return _psnr_from_F(float(F.item()), hold.n_rays)
+
+    def run_gn(env, steps):
+        sc, ctx, hold, target, htarget = setup(env)
+        x = torch.from_numpy(sc.x0.copy()).to(dev)
+        curve, t = [(0.0, psnr(hold, htarget, x))], 0.0
+        for _ in range(steps):
+            st = ctx.gn_solve(x, target, 1)[0]
+            t += st["ms"] / 1000.0
+            curve.append((t, psnr(hold, htarget, x)))
+        return {"psnr_curve": curve, "params": sc.n_params}
+
+    def run_adam(lr, budget_s, max_steps=4000):
+        sc, ctx, hold, target, htarget = setup("equirect")
+        x = torch.from_numpy(sc.x0.copy()).to(dev)
+        m = torch.zeros_like(x)
+        v = torch.zeros_like(x)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        curve, t, k = [(0.0, psnr(hold, htarget, x))], 0.0, 0
+        while t < budget_s and k < max_steps:
+            e0.record()
+            for _ in range(10):
+                k += 1
+                ctx.adam_step(x, target, m, v, k, lr=lr)
+            e1.record()
+            torch.cuda.synchronize()
+            t += e0.elapsed_time(e1) / 1000.0
+            curve.append((t, psnr(hold, htarget, x)))
+        return {"lr": lr, "steps": k, "psnr_curve": curve}
+
+    gn_steps = 5
+    gn = run_gn("equirect", gn_steps)
+    budget = max(2.0 * gn["psnr_curve"][-1][0], 1.0)
+    adam = [run_adam(lr, budget) for lr in (0.003, 0.01, 0.03, 0.1)]
+    best = max(adam, key=lambda a: a["psnr_curve"][-1][1])
+    target_db = min(gn["psnr_curve"][-1][1], best["psnr_curve"][-1][1]) - 0.1
+
+    def time_to(curve, db):
+        return next((t for t, p in curve if p >= db), None)
+    cube = run_gn("cube", gn_steps)
+    target_env = min(gn["psnr_curve"][-1][1], cube["psnr_curve"][-1][1]) - 0.1
+    line = {"metric": "held-out PSNR vs device time on the 32^3 workload",
+            "gn_vs_adam": {"gn_steps": gn_steps, "pcg_iters_per_step": 20,
+                           "adam_budget_s": budget, "target_psnr_db": target_db,
+                           "time_to_target_s": {"gauss_newton": time_to(gn["psnr_curve"], target_db),
+                                                "adam_best_lr": time_to(best["psnr_curve"], target_db)},
+                           "final_psnr_db": {"gauss_newton": gn["psnr_curve"][-1][1],
+                                             "adam": {str(a["lr"]): a["psnr_curve"][-1][1]
+                                                      for a in adam}},
+                           "adam_best_lr": best["lr"], "gauss_newton": gn, "adam": adam},
+            "equirect_vs_cube": {"target_psnr_db": target_env,
+                                 "time_to_target_s": {
+                                     "equirect": time_to(gn["psnr_curve"], target_env),
+                                     "cube": time_to(cube["psnr_curve"], target_env)},
+                                 "final_psnr_db": {"equirect": gn["psnr_curve"][-1][1],
+                                                   "cube": cube["psnr_curve"][-1][1]},
+                                 "shell_texels": {"equirect": "2 x 32x64", "cube": "2 x 6x16x16"},
+                                 "equirect": gn, "cube": cube}}
     print(json.dumps(line), flush=True)
 
 
@@ -941,6 +1025,13 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_cpu_baseline and world == 1 and args.cams is None:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_cams, cfg.pcg_iters)
+    if not args.no_lpc_record and world == 1 and args.cams is None:
+        # the time-to-PSNR half of the metric: learned vs Jacobi on the reduced
+        # ring workload (outside every timed region above)
+        del ctx, target, x, x_host, t_host, x_dev, t_dev
+        torch.cuda.empty_cache()
+        line["lpc"] = lpc_study(dev, "ring128", train_small=60, train_steps=10, train_large=6,
+                                gn_steps=20, pcg_per_step=5, traj_iters=300)
     print(json.dumps(line), flush=True)
 
 
@@ -951,6 +1042,8 @@ def main():
         run_reference(args, rank, world)
     elif args.conv:
         run_conv(args, rank, world, local)
+    elif args.compare:
+        run_compare(args, rank, world, local)
     elif args.lpc:
         run_lpc(args, rank, world, local)
     elif args.hier:

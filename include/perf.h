@@ -289,6 +289,26 @@ perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_use
  * Gauss-Newton step lays the coefficient store out anew.  perf_autotune
  * chooses among these tilings. */
 perf_status perf_set_tiling(perf_ctx* ctx, int32_t tile_w, int32_t sx, int32_t sy);
+
+/* Residual history of the context's last PCG solve (perf_pcg_begin /
+ * perf_pcg_step, or the last Gauss-Newton step of perf_gn_solve):
+ * R_out[k - 1] = r_k^T r_k after iteration k (Algorithm 2's R), HOST, at most
+ * cap values; *count_out = how many were written.  Synchronises. */
+perf_status perf_pcg_history(perf_ctx* ctx, double* R_out, int32_t cap, int32_t* count_out);
+
+/* One step of Adam (Kingma & Ba 2015) on the same objective and gradient --
+ * the first-order method the paper contrasts Gauss-Newton with (Fig. 1) --
+ * for comparisons on equal terms: r = H^ - C and F(x) (Eq. 5-6) into the
+ * context's workspace, g = J^T r, then per parameter m = beta1 m + (1 -
+ * beta1) g, v = beta2 v + (1 - beta2) g^2 and
+ * x = P(x - lr (m / (1 - beta1^t)) / (sqrt(v / (1 - beta2^t)) + eps)), P the
+ * projection of perf_options.project.  x, m, v: DEVICE, n floats each (m and
+ * v start at zero, t counts steps from 1); target: DEVICE, 3 N_r floats;
+ * F_out (DEVICE double, may be NULL) gets F at the x the step started from.
+ * FP32 scenes without the auxiliary term (else PERF_ERR_UNSUPPORTED). */
+perf_status perf_adam_step(perf_ctx* ctx, float* x, const void* target, float* m, float* v,
+                           int32_t t, float lr, float beta1, float beta2, float eps,
+                           double* F_out, void* stream);
 /* Times the A p launch at x along p (both in the scene storage type; p NULL:
  * p = x) over tile shapes 8x4, 4x8, 16x2, 32x1 and resident-CTA caps
  * {all, 3, 2} (two timed launches each), keeps the fastest for every later
@@ -461,10 +481,12 @@ perf_status perf_render_threshold(perf_ctx* ctx, const void* x, float min_opacit
  * clamped.  Grid opacity is per voxel side and is halved (the optical depth
  * of every path is kept); shell opacity is kept.  x: 4 (G^3 + S env_h env_w)
  * floats, x_out: 4 (8 G^3 + 4 S env_h env_w) floats, both DEVICE, not
- * overlapping (else PERF_ERR_INVALID_ARG).  2 <= G <= 512.  No context; the
+ * overlapping (else PERF_ERR_INVALID_ARG).  2 <= G <= 512.  env_kind
+ * PERF_ENV_CUBE: the maps are cube maps (env_w = 6 env_h), each face
+ * upsampled on its own with both axes clamped at its edges.  No context; the
  * work is queued on stream (cudaStream_t). */
 perf_status perf_upsample(const float* x, int32_t G, int32_t n_shells, int32_t env_h,
-                          int32_t env_w, float* x_out, void* stream);
+                          int32_t env_w, int32_t env_kind, float* x_out, void* stream);
 
 /* Residual and objective without a context and without any device
  * allocation -- the paper has no counterpart; this serves callers that cannot

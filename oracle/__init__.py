@@ -395,3 +395,28 @@ def gn_step(orc: Oracle, x, target, pcg_iters: int, fixed: bool = True,
 def psnr(rgb: np.ndarray, target: np.ndarray) -> float:
     mse = float(np.mean((np.asarray(rgb, np.float64) - np.asarray(target, np.float64)) ** 2))
     return float("inf") if mse == 0.0 else 10.0 * np.log10(1.0 / mse)
+
+
+# ------------------------------------------------------------ Adam comparator
+
+def adam_update(x, g, m, v, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One Adam update (Kingma & Ba 2015) from gradient g at step t >= 1:
+    first and second moment estimates with their bias corrections
+    1 - beta^t, then x - lr m_hat / (sqrt(v_hat) + eps).  Returns (x, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * g
+    v = beta2 * v + (1.0 - beta2) * g * g
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return x - lr * m_hat / (np.sqrt(v_hat) + eps), m, v
+
+
+def adam_step(orc: Oracle, x, target, m, v, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
+              do_project=True):
+    """The first-order comparator of the Gauss-Newton step (the paper's Fig. 1):
+    one Adam update on F (Eq. 5-6) with the gradient g = J^T r, then the
+    projection.  Returns (x, m, v, F at the starting x)."""
+    x = np.asarray(x, dtype=np.float64)
+    r, F = orc.residual(x, target)
+    g = orc.vjp(x, r)
+    x, m, v = adam_update(x, g, m, v, t, lr, beta1, beta2, eps)
+    return (project(x) if do_project else x), m, v, F

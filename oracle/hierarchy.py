@@ -16,7 +16,9 @@ a plain loop-free numpy restatement; the readings it takes are:
   depth of any path through the volume is unchanged;
 * environment maps: bilinear in texel space with the same centre mapping,
   the longitude wrapped and the latitude clamped as in the shell lookup;
-  a shell hit has delta-bar = 1 on every level, so shell sigma is kept.
+  a shell hit has delta-bar = 1 on every level, so shell sigma is kept;
+* cube maps (F x F texels per face, an F x 6F strip): each face on its own,
+  both axes clamped to the face's edge texels, as in the cube lookup.
 
 Pins: ``tests/test_oracle_pins.py`` (constant and linear fields, the wrap
 seam by hand, optical-depth preservation).
@@ -73,14 +75,35 @@ def upsample_shell(tex: np.ndarray) -> np.ndarray:
     return out
 
 
-def upsample(x: np.ndarray, G: int, n_shells: int, env_h: int, env_w: int) -> np.ndarray:
-    """Parameter vector of level (G, env_h x env_w) -> level (2G, 2env_h x 2env_w)."""
+def upsample_cube_shell(tex: np.ndarray) -> np.ndarray:
+    """tex: (F, 6F, 4), face f in columns [f F, (f + 1) F) -> (2F, 12F, 4)."""
+    F = tex.shape[0]
+    b, f = _axis(F, 2 * F)
+    t = tex.astype(np.float64)
+    out = np.zeros((2 * F, 12 * F, 4))
+    for face in range(6):
+        src = t[:, face * F:(face + 1) * F]
+        acc = np.zeros((2 * F, 2 * F, 4))
+        for dr in (0, 1):
+            wr = f if dr else 1.0 - f
+            for dc in (0, 1):
+                wc = f if dc else 1.0 - f
+                acc += (wr[:, None] * wc[None, :])[..., None] * src[np.ix_(b + dr, b + dc)]
+        out[:, 2 * face * F:2 * (face + 1) * F] = acc
+    return out
+
+
+def upsample(x: np.ndarray, G: int, n_shells: int, env_h: int, env_w: int,
+             env_kind: int = 0) -> np.ndarray:
+    """Parameter vector of level (G, env_h x env_w) -> level (2G, 2env_h x 2env_w)
+    (env_kind 1: cube-map shells)."""
     x = np.asarray(x, dtype=np.float64)
     nv = G ** 3
     grid = x[:4 * nv].reshape(G, G, G, 4)
     parts = [upsample_grid(grid).reshape(-1)]
     tex = env_h * env_w
+    up = upsample_cube_shell if env_kind == 1 else upsample_shell
     for s in range(n_shells):
         sh = x[4 * nv + 4 * s * tex: 4 * nv + 4 * (s + 1) * tex].reshape(env_h, env_w, 4)
-        parts.append(upsample_shell(sh).reshape(-1))
+        parts.append(up(sh).reshape(-1))
     return np.concatenate(parts)

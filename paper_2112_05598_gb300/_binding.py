@@ -105,7 +105,11 @@ _SIGS = {
     "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_set_coef_budget": [_VP, ctypes.c_int64],
     "perf_set_tiling": [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
-    "perf_upsample": [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _VP, _VP],
+    "perf_pcg_history": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
+    "perf_adam_step": [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
+                       ctypes.c_float, ctypes.c_float, _VP, _VP],
+    "perf_upsample": [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                      ctypes.c_int32, _VP, _VP],
     "perf_render_threshold": [_VP, _VP, ctypes.c_float, _VP, _VP, _VP],
     "perf_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                        ctypes.POINTER(ctypes.c_double)],
@@ -183,11 +187,12 @@ def load_library(path: Optional[str] = None):
     return lib
 
 
-def upsample(x, G, n_shells, env_h, env_w, x_out, stream=None):
+def upsample(x, G, n_shells, env_h, env_w, x_out, stream=None, env_kind=0):
     """perf_upsample: the next hierarchical level's parameters (grid 2G, maps
     2 env_h x 2 env_w) from level (G, env_h x env_w), into x_out."""
     lib = load_library()
-    st = lib.perf_upsample(_ptr(x), int(G), int(n_shells), int(env_h), int(env_w), _ptr(x_out),
+    st = lib.perf_upsample(_ptr(x), int(G), int(n_shells), int(env_h), int(env_w), int(env_kind),
+                           _ptr(x_out),
                            _stream(stream))
     if st != 0:
         raise PerfError(st, "upsample")
@@ -389,6 +394,21 @@ class Context:
                                            _stream(stream)), "autotune")
         return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms,
                     paired=t.paired, coef=t.coef, rays_per_thread=t.rays_per_thread)
+
+    def adam_step(self, x, target, m, v, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
+                  F_out=None, stream=None):
+        """One Adam step on F with g = J^T r (in place on x, m, v); F_out gets F(x)."""
+        self._check(self.lib.perf_adam_step(self.h, _ptr(x), _ptr(target), _ptr(m), _ptr(v),
+                                            int(t), float(lr), float(beta1), float(beta2),
+                                            float(eps), _ptr(F_out), _stream(stream)), "adam_step")
+
+    def pcg_history(self, cap=100000):
+        """R = r_k^T r_k after each iteration of the last PCG solve (numpy)."""
+        out = np.zeros(max(int(cap), 1))
+        k = ctypes.c_int32(0)
+        self._check(self.lib.perf_pcg_history(self.h, out.ctypes.data_as(ctypes.c_void_p), int(cap),
+                                              ctypes.byref(k)), "pcg_history")
+        return out[:k.value].copy()
 
     def set_tiling(self, tile_w=8, sx=1, sy=1):
         """Ray tiles of tile_w x 32/tile_w lanes, interleaved (sx, sy): the

@@ -5,7 +5,8 @@
 //
 // Fine cell i' has its centre at coarse index coordinate u = i'/2 - 1/4;
 // the grid uses the ray march's clamp convention (u in [0, G-1], base <=
-// G-2), the maps wrap in longitude and clamp in latitude.  The weights are
+// G-2), equirectangular maps wrap in longitude and clamp in latitude, and a
+// cube map's faces are upsampled one by one, clamped at their edges.  The weights are
 // 1/4, 3/4 (or 0, 1 at a clamped edge), exact in binary32.  Opacity is per
 // voxel side (Eq. 3 with delta-bar = delta / h), so grid sigma is halved to
 // keep every path's optical depth; a shell hit has delta-bar = 1 on every
@@ -34,8 +35,8 @@ __device__ __forceinline__ void acc4(float4& a, float w, float4 v) {
 }
 
 __global__ void __launch_bounds__(kUpThreads) k_upsample(const float4* __restrict__ x, int G, int S,
-                                                         int He, int We, float4* __restrict__ y,
-                                                         long long n_out) {
+                                                         int He, int We, int cube,
+                                                         float4* __restrict__ y, long long n_out) {
     const int G2 = 2 * G, He2 = 2 * He, We2 = 2 * We;
     const long long nv2 = (long long)G2 * G2 * G2;
     const long long nv = (long long)G * G * G;
@@ -64,12 +65,23 @@ __global__ void __launch_bounds__(kUpThreads) k_upsample(const float4* __restric
             int br;
             float fr;
             axis_up(ri, He, br, fr);
-            const float uc = 0.5f * (float)ci - 0.25f;
-            const float fl = floorf(uc);
-            const float fc = uc - fl;
-            int c0 = (int)fl % We;
-            if (c0 < 0) c0 += We;
-            const int c1 = c0 + 1 == We ? 0 : c0 + 1;
+            int c0, c1;
+            float fc;
+            if (cube) {
+                // each face (He x He texels) on its own, clamped at its edges
+                const int face = ci / (2 * He), cf = ci - face * 2 * He;
+                int bc;
+                axis_up(cf, He, bc, fc);
+                c0 = face * He + bc;
+                c1 = c0 + 1;
+            } else {
+                const float uc = 0.5f * (float)ci - 0.25f;
+                const float fl = floorf(uc);
+                fc = uc - fl;
+                c0 = (int)fl % We;
+                if (c0 < 0) c0 += We;
+                c1 = c0 + 1 == We ? 0 : c0 + 1;
+            }
             const float4* sh = x + nv + (long long)s * He * We;
             acc4(a, (1.0f - fr) * (1.0f - fc), sh[(long long)br * We + c0]);
             acc4(a, (1.0f - fr) * fc, sh[(long long)br * We + c1]);
@@ -82,7 +94,7 @@ __global__ void __launch_bounds__(kUpThreads) k_upsample(const float4* __restric
 
 }  // namespace
 
-cudaError_t launch_upsample(const float* x, int G, int S, int He, int We, float* y,
+cudaError_t launch_upsample(const float* x, int G, int S, int He, int We, int cube, float* y,
                             cudaStream_t st) {
     const long long G2 = 2ll * G;
     const long long n_out = G2 * G2 * G2 + (long long)S * 4 * He * We;
@@ -90,7 +102,7 @@ cudaError_t launch_upsample(const float* x, int G, int S, int He, int We, float*
     long long blocks = (n_out + kUpThreads - 1) / kUpThreads;
     if (blocks > 152ll * 32) blocks = 152ll * 32;
     k_upsample<<<(int)blocks, kUpThreads, 0, st>>>(reinterpret_cast<const float4*>(x), G, S, He, We,
-                                                 reinterpret_cast<float4*>(y), n_out);
+                                                 cube, reinterpret_cast<float4*>(y), n_out);
     count_launch();
     return cudaGetLastError();
 }

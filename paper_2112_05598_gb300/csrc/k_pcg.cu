@@ -147,10 +147,12 @@ __global__ void __launch_bounds__(kVThreads) k_pcg_begin(long long nb, const int
 }
 
 __global__ void k_pcg_begin_fin(PcgScalars* s, int n_seg, int max_iter, int fixed, double eps_rel,
-                                double stall) {
+                                double stall, double* hist, long long hist_cap) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_seg) return;
     s += i;
+    s->hist = n_seg == 1 ? hist : nullptr;
+    s->hist_cap = n_seg == 1 ? hist_cap : 0;
     s->R0 = s->acc_R;
     s->R_prev = s->acc_R;
     s->R = s->acc_R;
@@ -226,6 +228,7 @@ __global__ void k_pcg_finish(PcgScalars* s, int n_seg) {
         return;
     }
     s->R = R;
+    if (s->hist && s->iter <= s->hist_cap) s->hist[s->iter - 1] = R;
     if (s->fixed) {
         if (s->iter >= s->max_iter) { s->done = 1; s->exit_reason = 0; }
     } else {
@@ -325,6 +328,41 @@ __global__ void __launch_bounds__(kVThreads) k_to_bf16(long long nb, const float
         store_bf16x4(y, v, x[v]);
 }
 
+// One Adam step (Kingma & Ba 2015) on the parameters from the gradient g of
+// the objective, followed by the projection: m = b1 m + (1 - b1) g,
+// v = b2 v + (1 - b2) g^2, x = P(x - lr (m / c1) / (sqrt(v / c2) + eps)) with
+// the bias corrections c1 = 1 - b1^t, c2 = 1 - b2^t.  The first-order
+// comparator of the Gauss-Newton step (the paper's Fig. 1 contrasts them).
+__global__ void __launch_bounds__(kVThreads) k_adam(long long nb, float4* x, const float4* __restrict__ g,
+                                                   float4* m, float4* v, float b1, float b2,
+                                                   float lr, float eps, float c1, float c2,
+                                                   int project) {
+    for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < nb;
+         i += (long long)gridDim.x * blockDim.x) {
+        const float4 gi = g[i];
+        float4 mi = m[i], vi = v[i], xi = x[i];
+        float* mp = &mi.x;
+        float* vp = &vi.x;
+        float* xp = &xi.x;
+        const float* gp = &gi.x;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            mp[c] = fmaf(b1, mp[c], (1.0f - b1) * gp[c]);
+            vp[c] = fmaf(b2, vp[c], (1.0f - b2) * gp[c] * gp[c]);
+            xp[c] -= lr * (mp[c] / c1) / (sqrtf(vp[c] / c2) + eps);
+        }
+        if (project) {
+            xi.x = fminf(fmaxf(xi.x, 0.0f), 1.0f);
+            xi.y = fminf(fmaxf(xi.y, 0.0f), 1.0f);
+            xi.z = fminf(fmaxf(xi.z, 0.0f), 1.0f);
+            xi.w = fmaxf(xi.w, 0.0f);
+        }
+        m[i] = mi;
+        v[i] = vi;
+        x[i] = xi;
+    }
+}
+
 // ------------------------------------------------------------- launchers
 
 #define F4(p) reinterpret_cast<float4*>(p)
@@ -334,12 +372,12 @@ static dim3 seg_grid(long long nb, long long n_chunks, const int4* chunks) {
     return chunks ? dim3((unsigned)n_chunks, 1, 1) : dim3(vec_blocks(nb), 1, 1);
 }
 
-cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
-                                 const float* grad, const float* diag, float* delta, float* rho,
-                                 float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
-                                 int max_iter, int fixed, double eps_rel, double stall,
-                                 const float* blocks, long long n_block, cudaStream_t st,
-                                 float* pxp) {
+static cudaError_t pcg_begin_impl(long long n, int n_seg, const int4* chunks, long long n_chunks,
+                                  const float* grad, const float* diag, float* delta, float* rho,
+                                  float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
+                                  int max_iter, int fixed, double eps_rel, double stall,
+                                  const float* blocks, long long n_block, cudaStream_t st,
+                                  float* pxp, double* hist, long long hist_cap) {
     const long long nb = n / 4;
     cudaError_t e = cudaMemsetAsync(s, 0, sizeof(PcgScalars) * (size_t)(n_seg > 0 ? n_seg : 1), st);
     if (e != cudaSuccess) return e;
@@ -350,17 +388,29 @@ cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, lon
         count_launch();
     }
     const int ns = n_seg > 1 ? n_seg : 1;
-    k_pcg_begin_fin<<<(ns + 31) / 32, 32, 0, st>>>(s, ns, max_iter, fixed, eps_rel, stall);
+    k_pcg_begin_fin<<<(ns + 31) / 32, 32, 0, st>>>(s, ns, max_iter, fixed, eps_rel, stall, hist,
+                                                   hist_cap);
     count_launch();
     return cudaGetLastError();
+}
+
+cudaError_t launch_pcg_begin_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
+                                 const float* grad, const float* diag, float* delta, float* rho,
+                                 float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
+                                 int max_iter, int fixed, double eps_rel, double stall,
+                                 const float* blocks, long long n_block, cudaStream_t st,
+                                 float* pxp) {
+    return pcg_begin_impl(n, n_seg, chunks, n_chunks, grad, diag, delta, rho, p, p16, Ap, s,
+                          max_iter, fixed, eps_rel, stall, blocks, n_block, st, pxp, nullptr, 0);
 }
 
 cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, float* delta,
                              float* rho, float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
                              int max_iter, int fixed, double eps_rel, double stall,
-                             const float* blocks, long long n_block, cudaStream_t st, float* pxp) {
-    return launch_pcg_begin_seg(n, 1, nullptr, 0, grad, diag, delta, rho, p, p16, Ap, s, max_iter,
-                                fixed, eps_rel, stall, blocks, n_block, st, pxp);
+                             const float* blocks, long long n_block, cudaStream_t st, float* pxp,
+                             double* hist, long long hist_cap) {
+    return pcg_begin_impl(n, 1, nullptr, 0, grad, diag, delta, rho, p, p16, Ap, s, max_iter,
+                          fixed, eps_rel, stall, blocks, n_block, st, pxp, hist, hist_cap);
 }
 
 cudaError_t launch_pcg_update_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
@@ -429,6 +479,18 @@ cudaError_t launch_trial(long long n, const float* x, const float* delta, double
     if (nb > 0) {
         k_trial<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), CF4(delta), gamma, project, F4(x_out),
                                                       x16_out);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(long long n, float* x, const float* g, float* m, float* v, float b1,
+                        float b2, float lr, float eps, float c1, float c2, int project,
+                        cudaStream_t st) {
+    const long long nb = n / 4;
+    if (nb > 0) {
+        k_adam<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, F4(x), CF4(g), F4(m), F4(v), b1, b2, lr,
+                                                     eps, c1, c2, project);
         count_launch();
     }
     return cudaGetLastError();

@@ -63,6 +63,9 @@ struct perf_ctx {
     // valid for jitter epoch shell_tab_epoch (-1: no jitter); see ensure_shells
     float4* shell_tab = nullptr;
     long long shell_tab_epoch = -2;
+    // R after each PCG iteration of the last solve (perf_pcg_history)
+    double* hist = nullptr;
+    long long hist_cap = 0;
     float* x_trial = nullptr;
     __nv_bfloat16* x16 = nullptr;
     __nv_bfloat16* p16 = nullptr;
@@ -127,6 +130,17 @@ template <typename T>
 cudaError_t alloc(T** p, long long count) {
     if (*p) return cudaSuccess;
     return cudaMalloc(reinterpret_cast<void**>(p), sizeof(T) * (size_t)(count > 0 ? count : 1));
+}
+
+// Room for the residual history of a solve of up to `iters` iterations.
+perf_status ensure_hist(perf_ctx* ctx, long long iters) {
+    if (iters <= ctx->hist_cap) return PERF_OK;
+    if (ctx->hist) cudaFree(ctx->hist);
+    ctx->hist = nullptr;
+    ctx->hist_cap = 0;
+    CK(cudaMalloc(&ctx->hist, sizeof(double) * (size_t)iters));
+    ctx->hist_cap = iters;
+    return PERF_OK;
 }
 
 perf_status ensure_pcg(perf_ctx* ctx) {
@@ -408,7 +422,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->shell_tab, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->shell_tab, ctx->hist, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -529,10 +543,12 @@ perf_status perf_pcg_begin(perf_ctx* ctx, const float* grad, const float* diag, 
         CK(cudaMemcpyAsync(ctx->diag, diag, sizeof(float) * (size_t)ctx->n,
                            cudaMemcpyDeviceToDevice, S(stream)));
     const float* B = ctx->opts.precond == PERF_PRECOND_BLOCK4 ? ctx->blocks : nullptr;
+    st = ensure_hist(ctx, ctx->opts.pcg_iters);
+    if (st != PERF_OK) return st;
     CK(perf::launch_pcg_begin(ctx->n, grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
                               ctx->p16, ctx->Ap, ctx->s, ctx->opts.pcg_iters, ctx->opts.pcg_fixed,
                               ctx->opts.pcg_eps_rel, ctx->opts.pcg_stall, B, ctx->n_block,
-                              S(stream)));
+                              S(stream), nullptr, ctx->hist, ctx->hist_cap));
     return PERF_OK;
 }
 
@@ -708,10 +724,12 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         const bool paired = !bf && ctx->pair && (!use_coef || ctx->coef_tiles < ctx->ds.n_tiles);
         if (paired) CK(perf::launch_pair_pack(ctx->n, x, nullptr, ctx->xp, st));
         for (int attempt = 0; attempt < 2; ++attempt) {
+            ps = ensure_hist(ctx, o.pcg_iters);
+            if (ps != PERF_OK) return ps;
             CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
                                       ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
                                       o.pcg_eps_rel, o.pcg_stall, B, nB, st,
-                                      paired ? ctx->xp : nullptr));
+                                      paired ? ctx->xp : nullptr, ctx->hist, ctx->hist_cap));
             for (int k = 0; k < o.pcg_iters; ++k) {
                 ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired, use_coef);
                 if (ps != PERF_OK) return ps;
@@ -1024,6 +1042,49 @@ perf_status perf_diag_cross(perf_ctx* ctx, const void* x, float* diag_out, float
     return PERF_OK;
 }
 
+perf_status perf_adam_step(perf_ctx* ctx, float* x, const void* target, float* m, float* v,
+                           int32_t t, float lr, float beta1, float beta2, float eps,
+                           double* F_out, void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (bad_ptr(x) || bad_ptr(m) || bad_ptr(v) || (ctx->n_rays > 0 && bad_ptr(target)))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "adam_step: NULL pointer");
+    if (ctx->scene.dtype != PERF_F32 || ctx->ds.aux)
+        return fail(ctx, PERF_ERR_UNSUPPORTED, "adam_step: FP32 scenes without the auxiliary term");
+    if (t < 1 || !(lr > 0.0f) || !(beta1 >= 0.0f && beta1 < 1.0f) || !(beta2 >= 0.0f && beta2 < 1.0f) ||
+        !(eps > 0.0f))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "adam_step: t >= 1, lr > 0, 0 <= beta < 1, eps > 0");
+    cudaStream_t st = S(stream);
+    perf_status ps = ensure_pcg(ctx);
+    if (ps != PERF_OK) return ps;
+    if (!ctx->r) CK(cudaMalloc(&ctx->r, 4 * (size_t)(ctx->n_rays > 0 ? 3 * ctx->n_rays : 1)));
+    CK(cudaMemsetAsync(ctx->dF, 0, sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->grad, 0, sizeof(float) * (size_t)ctx->n, st));
+    if (ctx->n_rays > 0) {
+        SHELLS(ctx, st);
+        // r = H^ - C and F, then g = J^T r (Section "Update step": the gradient)
+        CK(perf::launch_forward(ctx->ds, PERF_F32, x, target, ctx->r, nullptr, ctx->dF, 1, st));
+        CK(perf::launch_scatter(ctx->ds, PERF_F32, 0, x, nullptr, PERF_F32, ctx->r, ctx->grad,
+                                nullptr, nullptr, st));
+    }
+    const float c1 = 1.0f - std::pow(beta1, (float)t), c2 = 1.0f - std::pow(beta2, (float)t);
+    CK(perf::launch_adam(ctx->n, x, ctx->grad, m, v, beta1, beta2, lr, eps, c1, c2,
+                         ctx->opts.project, st));
+    if (F_out) CK(cudaMemcpyAsync(F_out, ctx->dF, sizeof(double), cudaMemcpyDeviceToDevice, st));
+    return PERF_OK;
+}
+
+perf_status perf_pcg_history(perf_ctx* ctx, double* R_out, int32_t cap, int32_t* count_out) {
+    if (!ctx || (cap > 0 && !R_out) || !count_out) return PERF_ERR_INVALID_ARG;
+    *count_out = 0;
+    if (!ctx->s || !ctx->hist) return PERF_OK;
+    PcgScalars h;
+    CK(cudaMemcpy(&h, ctx->s, sizeof(h), cudaMemcpyDeviceToHost));
+    const long long k = std::min<long long>(std::min<long long>(h.iter, ctx->hist_cap), cap);
+    if (k > 0) CK(cudaMemcpy(R_out, ctx->hist, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost));
+    *count_out = (int32_t)k;
+    return PERF_OK;
+}
+
 perf_status perf_set_tiling(perf_ctx* ctx, int32_t tile_w, int32_t sx, int32_t sy) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     if ((tile_w != 4 && tile_w != 8 && tile_w != 16 && tile_w != 32) || (sx != 1 && sx != 2) ||
@@ -1078,9 +1139,12 @@ perf_status perf_render_threshold(perf_ctx* ctx, const void* x, float min_opacit
 }
 
 perf_status perf_upsample(const float* x, int32_t G, int32_t n_shells, int32_t env_h,
-                          int32_t env_w, float* x_out, void* stream) {
+                          int32_t env_w, int32_t env_kind, float* x_out, void* stream) {
     if (!x || !x_out || G < 2 || G > 512 || n_shells < 0 || n_shells > PERF_MAX_SHELLS ||
         (n_shells > 0 && (env_h < 2 || env_w < 2 || env_h > (1 << 14) || env_w > (1 << 14))))
+        return PERF_ERR_INVALID_ARG;
+    if ((env_kind != PERF_ENV_EQUIRECT && env_kind != PERF_ENV_CUBE) ||
+        (env_kind == PERF_ENV_CUBE && n_shells > 0 && env_w != 6 * env_h))
         return PERF_ERR_INVALID_ARG;
     const long long G2 = 2ll * G;
     const long long blocks = G2 * G2 * G2 + (long long)n_shells * 4 * env_h * env_w;
@@ -1090,7 +1154,8 @@ perf_status perf_upsample(const float* x, int32_t G, int32_t n_shells, int32_t e
     const char* b = reinterpret_cast<const char*>(x_out);
     if (a < b + 16 * blocks && b < a + 4 * n_in) return PERF_ERR_INVALID_ARG;   // overlap
     cudaError_t e = perf::launch_upsample(x, G, n_shells, n_shells ? env_h : 0,
-                                          n_shells ? env_w : 0, x_out, S(stream));
+                                          n_shells ? env_w : 0, env_kind == PERF_ENV_CUBE ? 1 : 0,
+                                          x_out, S(stream));
     return e == cudaSuccess ? PERF_OK : PERF_ERR_CUDA;
 }
 

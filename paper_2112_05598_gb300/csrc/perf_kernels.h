@@ -64,6 +64,8 @@ struct PcgScalars {
     int pad;
     double eps_rel;
     double stall;
+    double* hist;     // null, or R after iteration k written to hist[k - 1] (k <= hist_cap)
+    long long hist_cap;
 };
 
 // Kernels launched by this library since load (instrumentation).
@@ -115,7 +117,7 @@ cudaError_t launch_pcg_begin(long long n, const float* grad, const float* diag, 
                              float* rho, float* p, __nv_bfloat16* p16, float* Ap, PcgScalars* s,
                              int max_iter, int fixed, double eps_rel, double stall,
                              const float* blocks, long long n_block, cudaStream_t st,
-                             float* pxp = nullptr);
+                             float* pxp = nullptr, double* hist = nullptr, long long hist_cap = 0);
 cudaError_t launch_pcg_update(long long n, float* delta, float* rho, const float* p, float* Ap,
                               const float* diag, const float* blocks, long long n_block,
                               PcgScalars* s, cudaStream_t st);
@@ -132,6 +134,10 @@ cudaError_t launch_pair_pack(long long n, const float* x, const float* p, float*
 cudaError_t launch_trial(long long n, const float* x, const float* delta, double gamma,
                          int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
 cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaStream_t st);
+// One Adam step with projection (k_pcg.cu); c1, c2 the bias corrections.
+cudaError_t launch_adam(long long n, float* x, const float* g, float* m, float* v, float b1,
+                        float b2, float lr, float eps, float c1, float c2, int project,
+                        cudaStream_t st);
 
 // Segmented forms (a batch of independent systems, scalars s[y] for system
 // y < n_seg): chunks (device, n_chunks int4) assigns CTA b the parameter
@@ -158,7 +164,7 @@ cudaError_t launch_trial_seg(long long n, int n_seg, const int4* chunks, long lo
 
 // Level change of the hierarchical formulation (k_hier.cu): y (level 2G,
 // maps 2He x 2We) from x (level G, maps He x We).
-cudaError_t launch_upsample(const float* x, int G, int S, int He, int We, float* y,
+cudaError_t launch_upsample(const float* x, int G, int S, int He, int We, int cube, float* y,
                             cudaStream_t st);
 
 }  // namespace perf

@@ -81,15 +81,21 @@ def mean_loss(lpc: LPC, systems: List[System]) -> float:
 
 
 def pcg_iterations(ctx: Context, x, target, precond: int, eps: float = 1e-3,
-                   max_iter: int = 200, lpc: LPC = None) -> dict:
-    """PCG iterations of one GN step at x until |r_k| / |r_0| < eps (paper
-    mode without the stall exit); x is not modified."""
-    import torch
+                   max_iter: int = 200, lpc: LPC = None, thresholds=(1e-1, 1e-2, 1e-3)) -> dict:
+    """One GN step's PCG at x (the solver's own path, coefficient store
+    included) until |r_k| / |r_0| < eps or max_iter (paper mode without the
+    stall exit); x is not modified.  Returns the iterations, the relative
+    residual after each iteration and the first iteration below each
+    threshold (None: not reached)."""
     ctx.set_options(pcg_iters=max_iter, pcg_fixed=0, pcg_eps_rel=eps, pcg_stall=1e30,
                     precond=precond)
     if lpc is not None:
         ctx.set_lpc(lpc)
     xx = x.clone()
     st = ctx.gn_solve(xx, target, 1)[0]
+    R = ctx.pcg_history(max_iter)
+    rel = np.sqrt(R / st["R0"]) if st["R0"] > 0 else np.zeros_like(R)
+    first = {f"{t:g}": next((k + 1 for k, v in enumerate(rel) if v < t), None) for t in thresholds}
     return dict(iters=st["pcg_iters"], exit=st["pcg_exit"], R=st["R"], R0=st["R0"],
-                fallback=st["precond_fallback"], ms=st["ms"], F_after=st["F_after"])
+                fallback=st["precond_fallback"], ms=st["ms"], F_after=st["F_after"],
+                rel_residual=rel.tolist(), iters_to=first)

@@ -83,6 +83,13 @@ CONFIGS = {
         prim_size=(0.08, 0.3), n_cams=100, width=800, height=800,
         cam_radius=4.0, cam_layout="hemisphere", max_samples=512,
         gn_steps=10, pcg_iters=50, seed=1236),
+    # the ring workload reduced to fit a benchmark's time budget (the learned
+    # preconditioner's record in the default benchmark line)
+    "ring128": SceneConfig(
+        name="ring128", G=128, radii=(2.0, 4.0, 8.0, 16.0), env_h=256, env_w=512,
+        n_prims=60, prim_kinds=("ellipsoid", "box"), prim_size=(0.08, 0.3),
+        n_cams=40, width=480, height=270, cam_radius=4.0, cam_layout="ring",
+        max_samples=256, gn_steps=10, pcg_iters=50, background_sigma=10.0, seed=1239),
     "ring256": SceneConfig(
         name="ring256", G=256, radii=(2.0, 4.0, 8.0, 16.0), env_h=512,
         env_w=1024, n_prims=60, prim_kinds=("ellipsoid", "box"),

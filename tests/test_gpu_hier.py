@@ -11,16 +11,18 @@ from gpu_common import cuda_tensor, empty, host
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("G,S,He,We", [(2, 0, 2, 2), (5, 2, 3, 7), (16, 3, 8, 16), (33, 1, 5, 9)])
-def test_upsample_parity(G, S, He, We):
+@pytest.mark.parametrize("G,S,He,We,kind", [(2, 0, 2, 2, 0), (5, 2, 3, 7, 0), (16, 3, 8, 16, 0),
+                                            (33, 1, 5, 9, 0), (6, 2, 2, 12, 1), (9, 3, 5, 30, 1)])
+def test_upsample_parity(G, S, He, We, kind):
+    """kind 1: cube-map shells (faces of He x He texels)."""
     from oracle.hierarchy import upsample as ref_upsample
     from paper_2112_05598_gb300 import upsample
     rng = np.random.default_rng(G * 100 + S)
     n = 4 * (G ** 3 + S * He * We)
     x = rng.uniform(0, 2, size=n).astype(np.float32)
     y = empty(4 * (8 * G ** 3 + 4 * S * He * We))
-    upsample(cuda_tensor(x), G, S, He, We, y)
-    ref = ref_upsample(x.astype(np.float64), G, S, He, We)
+    upsample(cuda_tensor(x), G, S, He, We, y, env_kind=kind)
+    ref = ref_upsample(x.astype(np.float64), G, S, He, We, env_kind=kind)
     got = host(y)
     assert got.shape == ref.shape
     assert np.abs(got - ref).max() <= 1e-6 * np.abs(ref).max()

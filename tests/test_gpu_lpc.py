@@ -174,8 +174,11 @@ def test_identity_network_is_jacobi_and_blocks_are_spd():
 def test_trained_network_gain_on_held_out_systems():
     """Log systems from the solver's own Gauss-Newton runs on seeded scenes,
     train, and measure on held-out systems: the probe loss must fall below the
-    identity (Jacobi) network's, and PCG iterations to 1e-3 are reported for
-    Jacobi, the learned blocks and exact block-Jacobi."""
+    identity (Jacobi) network's, and on held-out Gauss-Newton states the
+    learned blocks must reach a relative PCG residual of 0.1 in fewer
+    iterations than Jacobi (mean over the states; the solver's own PCG with
+    the coefficient store).  Iterations to 1e-2 and 1e-3 and exact
+    block-Jacobi are reported beside it."""
     import torch
     from paper_2112_05598_gb300 import (Context, LPC, PERF_PRECOND_BLOCK4,
                                         PERF_PRECOND_BLOCK_JACOBI, PERF_PRECOND_JACOBI)
@@ -196,17 +199,26 @@ def test_trained_network_gain_on_held_out_systems():
             (test_sys if seed >= 4 else train_sys).append(s)
             if seed >= 4 and step in (1, 3):
                 test_states.append((ctx, x.clone(), target))
+            ctx.set_options(pcg_iters=5, pcg_fixed=1, precond=PERF_PRECOND_JACOBI)
             ctx.gn_solve(x, target, 1)
     before = T.mean_loss(net, test_sys)
     T.train(net, train_sys, epochs=4, lr=2e-3)
     after = T.mean_loss(net, test_sys)
+    thr = (1e-1, 3e-2, 1e-2, 1e-3)
     rows = []
     for ctx, x, target in test_states:
-        it_j = T.pcg_iterations(ctx, x, target, PERF_PRECOND_JACOBI)
-        it_l = T.pcg_iterations(ctx, x, target, PERF_PRECOND_BLOCK4, lpc=net)
-        it_b = T.pcg_iterations(ctx, x, target, PERF_PRECOND_BLOCK_JACOBI)
-        rows.append((it_j["iters"], it_l["iters"], it_b["iters"], it_l["fallback"]))
+        it_j = T.pcg_iterations(ctx, x, target, PERF_PRECOND_JACOBI, thresholds=thr)
+        it_l = T.pcg_iterations(ctx, x, target, PERF_PRECOND_BLOCK4, lpc=net, thresholds=thr)
+        it_b = T.pcg_iterations(ctx, x, target, PERF_PRECOND_BLOCK_JACOBI, thresholds=thr)
+        rows.append((it_j, it_l, it_b))
     print(f"held-out probe loss: identity (Jacobi) net {before:.4f} -> trained {after:.4f}")
-    print("PCG iterations to 1e-3 (Jacobi, learned, block-Jacobi, fallback):", rows)
+    for it_j, it_l, it_b in rows:
+        print("iterations to", list(thr), "Jacobi", it_j["iters_to"], "learned", it_l["iters_to"],
+              "block-Jacobi", it_b["iters_to"], "fallback", it_l["fallback"],
+              "rel residual at 200:", it_j["rel_residual"][-1], it_l["rel_residual"][-1])
     assert after < before
-    assert all(np.isfinite(r[1]) for r in rows)
+    assert not any(r[1]["fallback"] for r in rows)
+    jac = [r[0]["iters_to"]["0.1"] for r in rows]
+    lrn = [r[1]["iters_to"]["0.1"] for r in rows]
+    assert all(v is not None for v in jac + lrn), (jac, lrn)
+    assert np.mean(lrn) < np.mean(jac), (lrn, jac)

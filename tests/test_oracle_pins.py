@@ -698,3 +698,70 @@ def test_aux_closed_form_uniform_medium():
         T = math.exp(-sig * float(info["delta"]) * info["K"] / h)
         assert math.isclose(r[4 * ray + 3], AUX_LAMBDA * (1 - 4 * (T - 0.5) ** 2), rel_tol=1e-12,
                             abs_tol=1e-15)
+
+
+# ---------------------------------------------------------------- Adam
+
+def test_adam_update_closed_forms():
+    """Adam with its bias corrections: the first step moves every parameter by
+    lr g / (|g| + eps) (m_hat = g, v_hat = g^2), and under a constant gradient
+    every later step does too (m_hat and v_hat stay exactly g and g^2); a
+    wrong correction power or moment update breaks either."""
+    from oracle import adam_update
+    g = np.array([3.0, -0.5, 1e-3, 0.0, -2e-6])
+    x = np.zeros(5)
+    m = np.zeros(5)
+    v = np.zeros(5)
+    lr, eps = 0.05, 1e-8
+    for t in range(1, 8):
+        x_new, m, v = adam_update(x, g, m, v, t, lr=lr, eps=eps)
+        assert np.allclose(x_new - x, -lr * g / (np.abs(g) + eps), rtol=1e-12, atol=1e-15), t
+        x = x_new
+    # a changing gradient: the bias-corrected first moment is the weighted mean
+    m = np.zeros(1); v = np.zeros(1); x = np.zeros(1)
+    g1, g2, b1, b2 = 2.0, -1.0, 0.9, 0.999
+    x, m, v = adam_update(x, np.array([g1]), m, v, 1, lr=1.0, beta1=b1, beta2=b2, eps=0.0)
+    x2, m, v = adam_update(x, np.array([g2]), m, v, 2, lr=1.0, beta1=b1, beta2=b2, eps=0.0)
+    mh = (b1 * (1 - b1) * g1 + (1 - b1) * g2) / (1 - b1 ** 2)
+    vh = (b2 * (1 - b2) * g1 ** 2 + (1 - b2) * g2 ** 2) / (1 - b2 ** 2)
+    assert np.allclose(x2 - x, -mh / np.sqrt(vh), rtol=1e-12)
+
+
+def test_adam_step_uses_the_gradient_of_F(tiny):
+    """adam_step's first step is -lr g / (|g| + eps) (before projection), with
+    g = J^T r from the finite-difference Jacobian."""
+    from oracle import adam_step
+    orc, x, J = tiny
+    rng = np.random.default_rng(31)
+    target = rng.uniform(0, 1, size=3 * orc.n_rays)
+    n = x.shape[0]
+    xn, m, v, F = adam_step(orc, x, target, np.zeros(n), np.zeros(n), 1, lr=0.01,
+                            do_project=False)
+    r = orc.render(x)[0].ravel() - target
+    g = J.T @ r
+    assert abs(F - 0.5 * float(r @ r)) < 1e-12
+    big = np.abs(g) > 1e-4
+    assert big.sum() > n // 2
+    assert np.allclose((xn - x)[big], -0.01 * g[big] / (np.abs(g[big]) + 1e-8), rtol=1e-6)
+
+
+def test_upsample_cube_faces_by_hand():
+    """Cube-map level change: each face on its own.  A ramp a + b c along a
+    face's columns (a different a on every face, so faces jump) upsamples to
+    a + b (c'/2 - 1/4) at the interior fine columns c' and is clamped to the
+    face's edge texels at c' = 0 and c' = 2F - 1; nothing leaks across a face
+    boundary (an equirectangular treatment would blend neighbouring faces)."""
+    from oracle.hierarchy import upsample_cube_shell
+    F = 4
+    tex = np.zeros((F, 6 * F, 4))
+    for f in range(6):
+        for c in range(F):
+            tex[:, f * F + c, 0] = 10.0 * f + 0.5 * c
+    tex[..., 1] = 3.0
+    out = upsample_cube_shell(tex)
+    assert out.shape == (2 * F, 12 * F, 4)
+    assert np.allclose(out[..., 1], 3.0)
+    for f in range(6):
+        for cp in range(2 * F):
+            u = min(max(cp / 2.0 - 0.25, 0.0), F - 1.0)
+            assert np.allclose(out[:, 2 * f * F + cp, 0], 10.0 * f + 0.5 * u), (f, cp)
