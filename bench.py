@@ -174,9 +174,6 @@ def parse():
     ap.add_argument("--compare", action="store_true",
                     help="32^3 workload: Gauss-Newton vs Adam (time to held-out PSNR) and "
                          "equirectangular vs cube-map shells")
-    ap.add_argument("--tiling", default=None,
-                    help="tw,sx,sy: fix the ray tiling (tile width, sub-tile interleave) instead of "
-                         "autotuning it")
     ap.add_argument("--conv", type=int, default=0,
                     help="time the learned preconditioner's 4-layer network on a G^3 grid")
     return ap.parse_args()
@@ -472,7 +469,8 @@ def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train
         rel = it["rel_residual"]
         first[name] = {"iters_to": it["iters_to"], "iters": it["iters"], "exit": it["exit"],
                        "ms_per_iter": it["ms"] / max(it["iters"], 1),
-                       "rel_residual_at": {str(k): rel[k - 1] for k in (5, 10, 20, 50, 100, 200, 300)
+                       "rel_residual_at": {str(k): rel[k - 1]
+                                           for k in (5, 10, 20, 50, 100, 200, 300, 600, 1200)
                                            if k <= len(rel)},
                        "fallback": it["fallback"]}
     runs = {}
@@ -850,18 +848,10 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         ctx.gn_solve(x, target, 1)
     # tile shape / CTA cap tuned at the warmed-up state along a random direction
-    if args.tiling:
-        tw, sx, sy = (int(v) for v in args.tiling.split(","))
-        ctx.set_tiling(tw, sx, sy)
-        ctx.gn_solve(x, target, 1)          # lays the coefficient store out for it
-        tuning = {"tile_w": tw, "tile_h": 32 // tw, "ctas_per_sm": 0, "apply_ms": None,
-                  "paired": 0, "coef": int(ctx.coef_info()["used"]), "rays_per_thread": sx * sy,
-                  "fixed": True}
-    else:
-        gp = torch.Generator(device=dev).manual_seed(0)
-        probe = torch.randn(sc.n_params, device=dev, generator=gp).to(sdt)
-        tuning = ctx.autotune(x.to(sdt) if bf else x, probe)
-        del probe
+    gp = torch.Generator(device=dev).manual_seed(0)
+    probe = torch.randn(sc.n_params, device=dev, generator=gp).to(sdt)
+    tuning = ctx.autotune(x.to(sdt) if bf else x, probe)
+    del probe
     torch.cuda.synchronize()
     ctx.enable_timing(True)
     ctx.timing(reset=True)
@@ -1031,7 +1021,7 @@ def run_ours(args, rank, world, local):
         del ctx, target, x, x_host, t_host, x_dev, t_dev
         torch.cuda.empty_cache()
         line["lpc"] = lpc_study(dev, "ring128", train_small=60, train_steps=10, train_large=6,
-                                gn_steps=20, pcg_per_step=5, traj_iters=300)
+                                gn_steps=60, pcg_per_step=5, traj_iters=1200)
     print(json.dumps(line), flush=True)
 
 

@@ -167,11 +167,6 @@ typedef struct {
                                  32-byte records (FP32 scenes); 0: two arrays */
     int32_t coef;             /* 1: the coefficient-cached A p was timed (it is
                                  what perf_gn_solve runs while the store fits) */
-    int32_t rays_per_thread;  /* coefficient-cached A p: 1, or 2 / 4 neighbouring
-                                 rays per thread (2 x 1 / 2 x 2 pixels, tiles
-                                 interleaved so that lane l of consecutive tiles
-                                 covers them) whose equal-voxel contributions
-                                 are added before one atomic */
 } perf_tuning;
 
 /* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
@@ -278,18 +273,6 @@ perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_bl
 perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes);
 perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
                            double* coverage);
-/* Ray tiling of the context's marches: tiles of tile_w x (32 / tile_w) pixels
- * (tile_w in {4, 8, 16, 32}), interleaved by (sx, sy) in {1, 2}^2: a block of
- * tile_w sx x (32 / tile_w) sy pixels is split into sx sy consecutive tiles,
- * sub-tile (ox, oy) holding every sx-th column from ox and every sy-th row
- * from oy, so lane l of the block's tiles covers neighbouring pixels.  With
- * sx sy = 2 or 4 the coefficient-cached A p gives those neighbouring rays to
- * one thread and adds their contributions to a voxel before its atomic.
- * Results do not depend on the tiling beyond FP32 summation order.  The next
- * Gauss-Newton step lays the coefficient store out anew.  perf_autotune
- * chooses among these tilings. */
-perf_status perf_set_tiling(perf_ctx* ctx, int32_t tile_w, int32_t sx, int32_t sy);
-
 /* Residual history of the context's last PCG solve (perf_pcg_begin /
  * perf_pcg_step, or the last Gauss-Newton step of perf_gn_solve):
  * R_out[k - 1] = r_k^T r_k after iteration k (Algorithm 2's R), HOST, at most

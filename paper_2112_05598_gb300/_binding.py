@@ -68,8 +68,7 @@ TIMING_KINDS = ("apply", "forward", "diag", "vector", "precond", "residual")
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("apply_ms", ctypes.c_float),
-                ("paired", ctypes.c_int32), ("coef", ctypes.c_int32),
-                ("rays_per_thread", ctypes.c_int32)]
+                ("paired", ctypes.c_int32), ("coef", ctypes.c_int32)]
 
 
 class GNStats(ctypes.Structure):
@@ -104,7 +103,6 @@ _SIGS = {
     "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
     "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_set_coef_budget": [_VP, ctypes.c_int64],
-    "perf_set_tiling": [_VP, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32],
     "perf_pcg_history": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
     "perf_adam_step": [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, ctypes.c_float, _VP, _VP],
@@ -393,7 +391,7 @@ class Context:
         self._check(self.lib.perf_autotune(self.h, _ptr(x), _ptr(p), ctypes.byref(t),
                                            _stream(stream)), "autotune")
         return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms,
-                    paired=t.paired, coef=t.coef, rays_per_thread=t.rays_per_thread)
+                    paired=t.paired, coef=t.coef)
 
     def adam_step(self, x, target, m, v, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
                   F_out=None, stream=None):
@@ -409,11 +407,6 @@ class Context:
         self._check(self.lib.perf_pcg_history(self.h, out.ctypes.data_as(ctypes.c_void_p), int(cap),
                                               ctypes.byref(k)), "pcg_history")
         return out[:k.value].copy()
-
-    def set_tiling(self, tile_w=8, sx=1, sy=1):
-        """Ray tiles of tile_w x 32/tile_w lanes, interleaved (sx, sy): the
-        coefficient-cached A p then gives sx sy neighbouring rays to a thread."""
-        self._check(self.lib.perf_set_tiling(self.h, int(tile_w), int(sx), int(sy)), "set_tiling")
 
     def set_coef_budget(self, nbytes):
         """Budget of the coefficient store: -1 automatic, 0 off, > 0 bytes."""

@@ -790,236 +790,6 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
                w.v[q]);
 }
 
-// A p from the coefficient store with NR neighbouring rays per thread: the NR
-// consecutive tiles of a sub-tile interleave block (tile_pixel), lane l of
-// each.  Each ray keeps its own window; when rays of a thread evict the same
-// voxel in the same step (the common case: neighbouring pixels are a small
-// fraction of a voxel apart) their contributions are added in registers and
-// leave in one vector atomic.  The scatter's atomics are the limiter of this
-// kernel (one L1 wavefront-share per active lane), and on the 128^3 workload
-// a 2 x 1 pair merges 38 % of its flushes, a 2 x 2 quad 62 % (CPU simulation
-// of the flush sequences).
-template <int NR, bool COUNT>
-__device__ __forceinline__ void red_merged(float* out, unsigned long long* cnt, const bool (&ev)[NR],
-                                           const int (&key)[NR], const float4 (&val)[NR]) {
-    // the first evicting ray's voxel, with every ray that evicts the same one
-    int k0 = -1;
-    float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
-    bool left[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        if (ev[r] && k0 < 0) k0 = key[r];
-        const bool m = ev[r] && key[r] == k0;
-        if (m) { sum.x += val[r].x; sum.y += val[r].y; sum.z += val[r].z; sum.w += val[r].w; }
-        left[r] = ev[r] && !m;
-    }
-    if constexpr (COUNT) {
-        const unsigned b = __ballot_sync(kFull, k0 >= 0);
-        if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, (unsigned long long)__popc(b));
-    }
-    if (k0 >= 0) red_add4(out, k0, sum);
-    bool any_left = false;
-#pragma unroll
-    for (int r = 1; r < NR; ++r) any_left |= left[r];
-    if (__any_sync(kFull, any_left)) {      // rays of one thread evicting different voxels
-#pragma unroll
-        for (int r = 1; r < NR; ++r) {
-            if constexpr (COUNT) {
-                const unsigned b = __ballot_sync(kFull, left[r]);
-                if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, (unsigned long long)__popc(b));
-            }
-            if (left[r]) red_add4(out, key[r], val[r]);
-        }
-    }
-}
-
-template <typename TP, int NR, bool COUNT>
-__device__ __forceinline__ void coef_apply_group(const DevScene& sc, const TP* __restrict__ p,
-                                                 const float4* __restrict__ coef,
-                                                 const long long* __restrict__ tile_off,
-                                                 float* __restrict__ out, long long group, int lane,
-                                                 double& acc) {
-    long long ray[NR];
-    bool act[NR];
-    Ray R[NR];
-    const float4* crow[NR];
-    int kmax_rows[NR];
-    float J[NR][3], kap[NR], aux_v[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        const long long tile = group * NR + r;
-        ray[r] = 0;
-        act[r] = tile_pixel(sc, tile, lane, ray[r]);
-        R[r].K = 0;
-        R[r].shell_hit = 0u;
-        R[r].delta = 0.0f;
-        if (act[r]) ray_setup(sc, ray[r], R[r]);
-        const long long r0 = tile_off[tile];
-        kmax_rows[r] = (int)(tile_off[tile + 1] - r0) - sc.S - sc.aux;
-        crow[r] = coef + r0 * 32 + lane;
-        J[r][0] = J[r][1] = J[r][2] = 0.0f;
-        kap[r] = 0.0f;
-        aux_v[r] = 0.0f;
-    }
-    // J p of each ray (the NR rays in one loop, for independent loads in flight)
-    float psum[NR];
-    int Kl[NR];
-    int Kthr = 0;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        psum[r] = 0.0f;
-        Kl[r] = act[r] ? R[r].K : 0;
-        Kthr = max(Kthr, Kl[r]);
-        if (act[r] && sc.aux) kap[r] = __ldcs(crow[r] + (long long)(kmax_rows[r] + sc.S) * 32).x;
-    }
-    for (int k = 0; k < Kthr; ++k) {
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            if (k < Kl[r]) {
-                const float4 c = __ldcs(crow[r] + (long long)k * 32);
-                const Cell cl = sample_cell(sc, R[r], ray[r], k);
-                const float4 q = interp_grid(p, sc, cl);
-                J[r][0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[r][0]));
-                J[r][1] = fmaf(c.x, q.y, fmaf(c.z, q.w, J[r][1]));
-                J[r][2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[r][2]));
-                psum[r] += q.w;
-            }
-        }
-    }
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        if (!act[r]) continue;
-        float Ja = kap[r] * psum[r];
-        for (int s = 0; s < sc.S; ++s) {
-            ShellHit hs;
-            if (shell_lookup(sc, R[r], ray[r], s, hs)) {
-                const float4 q = interp_shell(p, hs);
-                const float4 c = __ldcs(crow[r] + (long long)(kmax_rows[r] + s) * 32);
-                J[r][0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[r][0]));
-                J[r][1] = fmaf(c.x, q.y, fmaf(c.z, q.w, J[r][1]));
-                J[r][2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[r][2]));
-            }
-        }
-        acc += (double)J[r][0] * J[r][0] + (double)J[r][1] * J[r][1] +
-               (double)J[r][2] * J[r][2] + (double)Ja * Ja;
-        if (J[r][0] == 0.0f && J[r][1] == 0.0f && J[r][2] == 0.0f && Ja == 0.0f) {
-            act[r] = false;
-            Kl[r] = 0;
-        }
-        aux_v[r] = Ja * kap[r];
-    }
-    // J^T (J p): shells first (few; one sink per ray), then the grid samples
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-        VjpSink<CanonKey, COUNT> sk{out, J[r][0], J[r][1], J[r][2], CanonKey{sc.G}, sc.red_count};
-        for (int s = sc.S - 1; s >= 0; --s) {
-            ShellHit hs;
-            const bool hit = act[r] && shell_lookup(sc, R[r], ray[r], s, hs);
-            float4 c = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (hit) c = __ldcs(crow[r] + (long long)(kmax_rows[r] + s) * 32);
-            const float sv = J[r][0] * c.y + J[r][1] * c.z + J[r][2] * c.w;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                const float W = hit ? hs.w[q] : 0.0f;
-                const float val[2] = {W * c.x, W * sv};
-                sk.put(hit, hit ? sk.km.shell(hs.idx[q]) : 0, val);
-            }
-        }
-    }
-    int Kmax = 0;
-#pragma unroll
-    for (int r = 0; r < NR; ++r) Kmax = max(Kmax, Kl[r]);
-    Kmax = __reduce_max_sync(kFull, Kmax);
-    const CanonKey km{sc.G};
-    Window<2> w[NR];
-#pragma unroll
-    for (int r = 0; r < NR; ++r) {
-#pragma unroll
-        for (int c = 0; c < 8; ++c) w[r].v[c][0] = w[r].v[c][1] = 0.0f;
-        w[r].b[0] = w[r].b[1] = w[r].b[2] = 0;
-    }
-    for (int k = Kmax - 1; k >= 0; --k) {
-        bool on[NR];
-        float4 c[NR];
-        Cell cl[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            on[r] = k < Kl[r];
-            c[r] = on[r] ? __ldcs(crow[r] + (long long)k * 32) : make_float4(0.f, 0.f, 0.f, 0.f);
-            cl[r].bx = w[r].b[0]; cl[r].by = w[r].b[1]; cl[r].bz = w[r].b[2];
-            cl[r].fx = cl[r].fy = cl[r].fz = 0.0f;
-            if (on[r]) {
-                cl[r] = sample_cell(sc, R[r], ray[r], k);
-                if (k == Kl[r] - 1) { w[r].b[0] = cl[r].bx; w[r].b[1] = cl[r].by; w[r].b[2] = cl[r].bz; }
-            }
-        }
-        // voxels leaving the windows, merged across the thread's rays
-#pragma unroll
-        for (int pp = 0; pp < 8; ++pp) {
-            bool ev[NR], evz[NR];
-            int key[NR];
-            float4 val[NR];
-#pragma unroll
-            for (int r = 0; r < NR; ++r) {
-                const int ox = par_coord(w[r].b[0], pp & 1), oy = par_coord(w[r].b[1], (pp >> 1) & 1),
-                          oz = par_coord(w[r].b[2], pp >> 2);
-                const int nx = par_coord(cl[r].bx, pp & 1), ny = par_coord(cl[r].by, (pp >> 1) & 1),
-                          nz = par_coord(cl[r].bz, pp >> 2);
-                evz[r] = on[r] && (ox != nx || oy != ny || oz != nz);
-                const float a = w[r].v[pp][0], sv = w[r].v[pp][1];
-                ev[r] = evz[r] && (a != 0.0f || sv != 0.0f);
-                key[r] = km.key(ox, oy, oz);
-                val[r] = make_float4(a * J[r][0], a * J[r][1], a * J[r][2], sv);
-            }
-            red_merged<NR, COUNT>(out, sc.red_count, ev, key, val);
-#pragma unroll
-            for (int r = 0; r < NR; ++r)
-                if (evz[r]) { w[r].v[pp][0] = 0.0f; w[r].v[pp][1] = 0.0f; }
-        }
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            if (on[r]) {
-                w[r].b[0] = cl[r].bx; w[r].b[1] = cl[r].by; w[r].b[2] = cl[r].bz;
-                const float val[2] = {c[r].x, J[r][0] * c[r].y + J[r][1] * c[r].z + J[r][2] * c[r].w +
-                                                  aux_v[r]};
-                win_add(w[r], cl[r], val);
-            }
-        }
-    }
-    // the remaining windows
-#pragma unroll
-    for (int pp = 0; pp < 8; ++pp) {
-        bool ev[NR];
-        int key[NR];
-        float4 val[NR];
-#pragma unroll
-        for (int r = 0; r < NR; ++r) {
-            const float a = w[r].v[pp][0], sv = w[r].v[pp][1];
-            ev[r] = Kl[r] > 0 && (a != 0.0f || sv != 0.0f);
-            key[r] = km.key(par_coord(w[r].b[0], pp & 1), par_coord(w[r].b[1], (pp >> 1) & 1),
-                            par_coord(w[r].b[2], pp >> 2));
-            val[r] = make_float4(a * J[r][0], a * J[r][1], a * J[r][2], sv);
-        }
-        red_merged<NR, COUNT>(out, sc.red_count, ev, key, val);
-    }
-}
-
-// Tiles of groups [tile_lo / NR, n_tiles / NR), one group per warp.
-#define PERF_GROUP_LOOP(NR)                                                         \
-    const int lane = threadIdx.x & 31;                                              \
-    const long long nw = (long long)gridDim.x * kWarps;                             \
-    for (long long group = sc.tile_lo / (NR) + (long long)blockIdx.x * kWarps + (threadIdx.x >> 5); \
-         group < sc.n_tiles / (NR); group += nw)
-
-template <typename TP, int NR, bool COUNT = false>
-__global__ void __launch_bounds__(kThreads, NR == 2 ? 3 : 1)
-    k_apply_coef_multi(DevScene sc, const TP* __restrict__ p, const float4* __restrict__ coef,
-                       const long long* __restrict__ tile_off, float* __restrict__ out, double* pap) {
-    double acc = 0.0;
-    PERF_GROUP_LOOP(NR) { coef_apply_group<TP, NR, COUNT>(sc, p, coef, tile_off, out, group, lane, acc); }
-    if (pap) block_add_f64<kWarps>(acc, pap);
-}
-
 template <typename TP, bool COUNT = false>
 __global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
     k_apply_coef(DevScene sc, const TP* __restrict__ p, const float4* __restrict__ coef,
@@ -1343,28 +1113,9 @@ cudaError_t launch_apply_coef_t(const DevScene& sc, const void* p, const float* 
                                 const long long* tile_off, float* out, double* pap,
                                 cudaStream_t st) {
     if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
-    const int nsub = (sc.tile_sx > 1 ? sc.tile_sx : 1) * (sc.tile_sy > 1 ? sc.tile_sy : 1);
-    const TP* pp = static_cast<const TP*>(p);
-    const float4* cf = reinterpret_cast<const float4*>(coef);
-    if (nsub == 2 || nsub == 4) {
-        // neighbouring rays per thread (the tiles of one interleave block); the
-        // store's prefix of tiles and the launch range are whole blocks
-        if (sc.tile_lo % nsub != 0 || sc.n_tiles % nsub != 0) return cudaErrorInvalidValue;
-        const long long groups = (sc.n_tiles - sc.tile_lo) / nsub;
-        if (nsub == 2) {
-            auto fn = sc.red_count ? k_apply_coef_multi<TP, 2, true> : k_apply_coef_multi<TP, 2, false>;
-            fn<<<grid_blocks((const void*)fn, groups, sc.cap_per_sm), kThreads, 0, st>>>(
-                sc, pp, cf, tile_off, out, pap);
-        } else {
-            auto fn = sc.red_count ? k_apply_coef_multi<TP, 4, true> : k_apply_coef_multi<TP, 4, false>;
-            fn<<<grid_blocks((const void*)fn, groups, sc.cap_per_sm), kThreads, 0, st>>>(
-                sc, pp, cf, tile_off, out, pap);
-        }
-    } else {
-        auto fn = sc.red_count ? k_apply_coef<TP, true> : k_apply_coef<TP, false>;
-        fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
-            sc, pp, cf, tile_off, out, pap);
-    }
+    auto fn = sc.red_count ? k_apply_coef<TP, true> : k_apply_coef<TP, false>;
+    fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
+        sc, static_cast<const TP*>(p), reinterpret_cast<const float4*>(coef), tile_off, out, pap);
     count_launch();
     return cudaGetLastError();
 }

@@ -55,7 +55,7 @@ struct perf_ctx {
     long long coef_rows = 0;           // rows needed by the current tiling
     std::vector<long long> tile_off_h; // host copy of tile_off
     long long coef_tiles = 0;          // tiles [0, coef_tiles) are in the store
-    int tab_tile_w = 0, tab_max_samples = 0, tab_sx = 0, tab_sy = 0;
+    int tab_tile_w = 0, tab_max_samples = 0;
     long long tab_epoch = -1;          // epoch of a jittered table (-1: not jittered)
     bool coef_used = false;            // the last Gauss-Newton step used the store
     float* Ap = nullptr;
@@ -164,7 +164,7 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
     // with pixel jitter the rays, and so the sample counts, change with the epoch
     const long long epoch = d.jitter ? (long long)d.epoch : -1;
     if (!ctx->tile_off || ctx->tab_tile_w != d.tile_w || ctx->tab_max_samples != d.max_samples ||
-        ctx->tab_epoch != epoch || ctx->tab_sx != d.tile_sx || ctx->tab_sy != d.tile_sy) {
+        ctx->tab_epoch != epoch) {
         if (ctx->tile_off) { cudaFree(ctx->tile_off); ctx->tile_off = nullptr; }
         int* rows = nullptr;
         CK(cudaMalloc(&rows, sizeof(int) * (size_t)d.n_tiles));
@@ -183,8 +183,6 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
         ctx->coef_rows = off.back();
         ctx->tile_off_h.swap(off);
         ctx->tab_tile_w = d.tile_w;
-        ctx->tab_sx = d.tile_sx;
-        ctx->tab_sy = d.tile_sy;
         ctx->tab_max_samples = d.max_samples;
         ctx->tab_epoch = epoch;
     }
@@ -205,9 +203,6 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
     if ((size_t)off.back() * row_bytes > budget) {
         const long long max_rows = (long long)(budget / row_bytes);
         T1 = (long long)(std::upper_bound(off.begin(), off.end(), max_rows) - off.begin()) - 1;
-        // whole interleave blocks (the multi-ray A p takes a block per warp)
-        const long long nsub = (long long)std::max(d.tile_sx, 1) * std::max(d.tile_sy, 1);
-        T1 -= T1 % nsub;
     }
     const size_t need = (size_t)(T1 > 0 ? off[(size_t)T1] : 0) * row_bytes;
     if (T1 <= 0 || need == 0) {
@@ -832,21 +827,14 @@ perf_status perf_enable_timing(perf_ctx* ctx, int32_t on) {
     return PERF_OK;
 }
 
-// Re-tile the context's rays for tile width tw (tile height 32 / tw) and
-// sub-tile interleave (sx, sy) (tile_pixel).
-static void set_tiling(perf_ctx* ctx, int tw, int sx = -1, int sy = -1) {
+// Re-tile the context's rays for tile width tw (tile height 32 / tw).
+static void set_tiling(perf_ctx* ctx, int tw) {
     DevScene& d = ctx->ds;
-    if (sx > 0) d.tile_sx = sx;
-    if (sy > 0) d.tile_sy = sy;
-    if (d.tile_sx < 1) d.tile_sx = 1;
-    if (d.tile_sy < 1) d.tile_sy = 1;
     d.tile_w = tw;
     d.tile_h = 32 / tw;
-    d.tiles_x = (d.W + d.tile_w * d.tile_sx - 1) / (d.tile_w * d.tile_sx);
-    d.tiles_y = (d.H + d.tile_h * d.tile_sy - 1) / (d.tile_h * d.tile_sy);
-    d.n_tiles = ctx->n_rays > 0
-                    ? (long long)d.tiles_x * d.tiles_y * d.tile_sx * d.tile_sy * d.n_cams
-                    : 0;
+    d.tiles_x = (d.W + d.tile_w - 1) / d.tile_w;
+    d.tiles_y = (d.H + d.tile_h - 1) / d.tile_h;
+    d.n_tiles = ctx->n_rays > 0 ? (long long)d.tiles_x * d.tiles_y * d.n_cams : 0;
 }
 
 static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
@@ -882,19 +870,15 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
     // cached A p: for every tile shape the store is laid out anew and filled
     // at x, and the A p from it is timed over the CTA caps; the default
     // (8x4, no cap, timed first) is kept unless beaten by 3%.
-    set_tiling(ctx, 8, 1, 1);
+    set_tiling(ctx, 8);
     bool use_coef = false;
     perf_status pc = ensure_coef(ctx, st, &use_coef);
     if (pc != PERF_OK) return pc;
     if (use_coef && ctx->coef_tiles == ctx->ds.n_tiles) {
         float best = 1e30f, incumbent = 1e30f;
-        int best_tw = 8, best_cap = 0, best_sx = 1, best_sy = 1;
-        // tile shapes without interleave, then the multi-ray A p with 2 x 1 and
-        // 2 x 2 neighbouring rays per thread
-        const int cand[8][3] = {{8, 1, 1}, {4, 1, 1}, {16, 1, 1}, {32, 1, 1},
-                                {8, 2, 1}, {4, 2, 1}, {8, 2, 2}, {4, 2, 2}};
-        for (int i = 0; i < 8; ++i) {
-            set_tiling(ctx, cand[i][0], cand[i][1], cand[i][2]);
+        int best_tw = 8, best_cap = 0;
+        for (int i = 0; i < 4; ++i) {
+            set_tiling(ctx, tws[i]);
             bool fits = false;
             pc = ensure_coef(ctx, st, &fits);
             if (pc != PERF_OK) return pc;
@@ -916,16 +900,11 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
                 CK(cudaEventElapsedTime(&ms, e0, e1));
                 ms *= 0.5f;
                 if (i == 0 && j == 0) incumbent = ms;
-                if (ms < best) {
-                    best = ms; best_tw = cand[i][0]; best_cap = caps[j];
-                    best_sx = cand[i][1]; best_sy = cand[i][2];
-                }
+                if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; }
             }
         }
-        if (!(best < 0.97f * incumbent)) {
-            best = incumbent; best_tw = 8; best_cap = 0; best_sx = 1; best_sy = 1;
-        }
-        set_tiling(ctx, best_tw, best_sx, best_sy);
+        if (!(best < 0.97f * incumbent)) { best = incumbent; best_tw = 8; best_cap = 0; }
+        set_tiling(ctx, best_tw);
         ctx->ds.cap_per_sm = best_cap;
         ctx->coef_used = true;
         if (out) {
@@ -935,7 +914,6 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
             out->apply_ms = best;
             out->paired = 0;
             out->coef = 1;
-            out->rays_per_thread = best_sx * best_sy;
         }
         return PERF_OK;
     }
@@ -958,7 +936,7 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
     float best = 1e30f, incumbent = 1e30f;
     int best_tw = 8, best_cap = 0;
     for (int i = 0; i < 4; ++i) {
-        set_tiling(ctx, tws[i], 1, 1);
+        set_tiling(ctx, tws[i]);
         for (int j = 0; j < 3; ++j) {
             ctx->ds.cap_per_sm = caps[j];
             float ms = 0.f;
@@ -986,7 +964,6 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
         out->apply_ms = best;
         out->paired = pair ? 1 : 0;
         out->coef = 0;
-        out->rays_per_thread = 1;
     }
     return PERF_OK;
 }
@@ -1000,12 +977,11 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     ctx->ds.red_count = nullptr;
     // a failed tuning run leaves the tiling, CTA cap and layout it started with
     const int tw0 = ctx->ds.tile_w, cap0 = ctx->ds.cap_per_sm;
-    const int sx0 = ctx->ds.tile_sx, sy0 = ctx->ds.tile_sy;
     const bool pair0 = ctx->pair;
     const perf_status ps = autotune_impl(ctx, x, p, out, stream);
     ctx->ds.red_count = counter;
     if (ps != PERF_OK) {
-        set_tiling(ctx, tw0, sx0, sy0);
+        set_tiling(ctx, tw0);
         ctx->ds.cap_per_sm = cap0;
         ctx->pair = pair0;
     }
@@ -1082,15 +1058,6 @@ perf_status perf_pcg_history(perf_ctx* ctx, double* R_out, int32_t cap, int32_t*
     const long long k = std::min<long long>(std::min<long long>(h.iter, ctx->hist_cap), cap);
     if (k > 0) CK(cudaMemcpy(R_out, ctx->hist, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost));
     *count_out = (int32_t)k;
-    return PERF_OK;
-}
-
-perf_status perf_set_tiling(perf_ctx* ctx, int32_t tile_w, int32_t sx, int32_t sy) {
-    if (!ctx) return PERF_ERR_INVALID_ARG;
-    if ((tile_w != 4 && tile_w != 8 && tile_w != 16 && tile_w != 32) || (sx != 1 && sx != 2) ||
-        (sy != 1 && sy != 2))
-        return fail(ctx, PERF_ERR_INVALID_ARG, "set_tiling: tile_w in {4, 8, 16, 32}, sx, sy in {1, 2}");
-    set_tiling(ctx, tile_w, sx, sy);
     return PERF_OK;
 }
 

@@ -471,7 +471,6 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
     if (out) {
         out->tile_w = best_tw;
         out->tile_h = 32 / best_tw;
-        out->rays_per_thread = 1;
         out->ctas_per_sm = best_cap;
         out->apply_ms = best;
         out->paired = 0;

@@ -39,7 +39,6 @@ struct DevScene {
     long long n_tiles;       // tile_w x tile_h pixel tiles over all cameras
     int tiles_x, tiles_y;
     int tile_w, tile_h;      // one warp per tile: tile_w * tile_h = 32
-    int tile_sx, tile_sy;    // sub-tile interleave (0 or 1: none): see tile_pixel
     int cap_per_sm;          // resident-CTA cap of the scatter kernels (0 = none)
     const float* cams;       // n_cams x 16: c2w (12), focal, pad
     int max_samples;
@@ -79,24 +78,16 @@ __device__ __forceinline__ float jitter_u(const DevScene& sc, long long ray, uns
     return (float)(h >> 40) * (1.0f / 16777216.0f);
 }
 
-// Pixel of lane `lane` in tile `tile`.  Tiles are tile_w x tile_h lanes,
-// row-major over each camera's image, cameras one after the other.  With a
-// sub-tile interleave (sx, sy) a block of tile_w sx x tile_h sy pixels is
-// split into sx sy consecutive tiles: sub-tile (ox, oy) takes the pixels
-// (tile_w-grid column * sx + ox, row * sy + oy), so lane l of the sx sy
-// tiles of one block covers neighbouring pixels (the multi-ray A p kernel
-// gives them to one thread).
+// Pixel of lane `lane` in tile `tile` (tiles are tile_w wide, tile_h high,
+// row-major over each camera's image, cameras one after the other).
 __device__ __forceinline__ bool tile_pixel(const DevScene& sc, long long tile, int lane,
                                            long long& ray) {
-    const int sx = sc.tile_sx > 1 ? sc.tile_sx : 1, sy = sc.tile_sy > 1 ? sc.tile_sy : 1;
-    const int nsub = sx * sy;
-    const long long per_cam = (long long)sc.tiles_x * sc.tiles_y * nsub;
+    const long long per_cam = (long long)sc.tiles_x * sc.tiles_y;
     const int cam = (int)(tile / per_cam);
     const int t = (int)(tile - (long long)cam * per_cam);
-    const int blk = t / nsub, sub = t - blk * nsub;
-    const int ty = blk / sc.tiles_x, tx = blk - ty * sc.tiles_x;
-    const int col = (tx * sc.tile_w + lane % sc.tile_w) * sx + sub % sx;
-    const int row = (ty * sc.tile_h + lane / sc.tile_w) * sy + sub / sx;
+    const int ty = t / sc.tiles_x, tx = t - ty * sc.tiles_x;
+    const int col = tx * sc.tile_w + lane % sc.tile_w;
+    const int row = ty * sc.tile_h + lane / sc.tile_w;
     if (col >= sc.W || row >= sc.H) return false;
     ray = ((long long)cam * sc.H + row) * sc.W + col;
     return true;

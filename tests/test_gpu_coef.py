@@ -164,53 +164,3 @@ def test_coef_partial_store(prob):
     for a, b in zip(st_p, st_r):
         assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
     assert rel_l2(x_p, x_r) < TOL_FP32
-
-
-def _step_tiled(sc, target, x, budget, sx, sy, pcg_iters=3, steps=2, **kw):
-    from paper_2112_05598_gb300 import Context
-    ctx = Context.from_scene(sc, pcg_iters=pcg_iters, pcg_fixed=1, **kw)
-    ctx.set_coef_budget(budget)
-    ctx.set_tiling(8, sx, sy)
-    xd = cuda_tensor(x)
-    st = ctx.gn_solve(xd, cuda_tensor(target), steps)
-    return st, host(xd), ctx.coef_info(), ctx
-
-
-@pytest.mark.parametrize("sx,sy", [(2, 1), (2, 2)])
-def test_multi_ray_apply_equals_single_ray(prob, sx, sy):
-    """Two or four neighbouring rays per thread (interleaved tiles), their
-    equal-voxel contributions added before one atomic: the same Gauss-Newton
-    steps as one ray per thread, with the whole store and with a store
-    holding only a prefix of the tiles (cut at whole interleave blocks; the
-    rest recomputed)."""
-    sc, target, x = prob
-    st_1, x_1, _ = _step(sc, target, x, -1)
-    st_m, x_m, info, ctx = _step_tiled(sc, target, x, -1, sx, sy)
-    assert info["used"] and info["coverage"] == 1.0
-    for a, b in zip(st_m, st_1):
-        assert a["accepted"] == b["accepted"]
-        assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
-    assert rel_l2(x_m, x_1) < TOL_FP32
-    st_p, x_p, info_p, _ = _step_tiled(sc, target, x, info["bytes"] // 3, sx, sy)
-    assert info_p["used"] and 0.0 < info_p["coverage"] < 1.0
-    assert rel_l2(x_p, x_1) < TOL_FP32
-
-
-def test_multi_ray_steps_against_oracle(prob):
-    """Three Gauss-Newton steps with the 2 x 1 multi-ray A p against the oracle."""
-    from oracle import Oracle, gn_step
-    from gpu_common import TOL_GN, assert_params
-    sc, target, x = prob
-    orc = Oracle.from_scene(sc)
-    st, _, _, ctx = _step_tiled(sc, target, x, -1, 2, 1, steps=0)
-    xd = cuda_tensor(x)
-    td = cuda_tensor(target)
-    for step in range(3):
-        xb = host(xd)
-        s = ctx.gn_solve(xd, td, 1)[0]
-        ref = gn_step(orc, xb, target, 3)
-        assert s["accepted"] == ref.accepted
-        if abs(s["gamma"] - ref.gamma) > 1e-9:
-            xd = cuda_tensor(ref.x.astype(np.float32))
-            continue
-        assert_params(host(xd), ref.x, ref.diag, TOL_GN, what=f"multi-ray GN step {step}")
