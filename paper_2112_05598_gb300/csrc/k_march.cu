@@ -13,7 +13,7 @@
 // w_i = T_i alpha_i,
 //   dH/dc_i       = w_i
 //   dH_k/dsigma_i = dbar_i (T_i e^{-s_i} c_ik - G_ik),  G_i = sum_{j>i} w_j c_j.
-// The scatter kernels run Algorithm 1 as printed: a first front-to-back sweep
+// The scatter kernels take Algorithm 1's order: a first front-to-back sweep
 // gives the total optical depth V (grid samples and shell hits), then a
 // back-to-front sweep subtracts s_i from V (so e^{-V} = T_i) and accumulates
 // G after each use.  G is a sum of non-negative terms, so every partial has

@@ -298,6 +298,20 @@ def make_cameras(rng, n, width, radius, layout, fov_deg, elev_deg=15.0):
     return c2w, focal
 
 
+def ring_heldout_cameras(n, n_train, width, radius, fov_deg, elev_deg):
+    """Held-out views of a ring capture: n cameras on the training ring, each
+    midway between two neighbouring training cameras, spread evenly around
+    the ring (novel views between the captured ones)."""
+    el = math.radians(elev_deg)
+    gaps = (np.arange(n) * n_train) // n
+    az = 2.0 * np.pi * (gaps + 0.5) / n_train
+    pos = np.stack([radius * np.cos(el) * np.cos(az), radius * np.cos(el) * np.sin(az),
+                    np.full(n, radius * np.sin(el))], axis=1)
+    c2w = np.stack([look_at_c2w(p) for p in pos]).astype(np.float32)
+    focal = np.full(n, focal_from_fov(width, fov_deg), dtype=np.float32)
+    return c2w, focal
+
+
 def make_scene(cfg, seed: Optional[int] = None, n_cams: Optional[int] = None,
                G: Optional[int] = None, env: str = "equirect",
                cube_face: Optional[int] = None) -> Scene:
@@ -326,9 +340,13 @@ def make_scene(cfg, seed: Optional[int] = None, n_cams: Optional[int] = None,
     x_gt = np.concatenate([grid.reshape(-1)] + shells).astype(np.float32)
     c2w, focal = make_cameras(rng, cfg.n_cams, cfg.width, cfg.cam_radius,
                               cfg.cam_layout, cfg.fov_deg, cfg.ring_elev_deg)
-    hc2w, hfocal = make_cameras(rng, cfg.n_heldout, cfg.width, cfg.cam_radius,
-                                "hemisphere" if cfg.cam_layout != "sphere"
-                                else "sphere", cfg.fov_deg)
+    if cfg.cam_layout == "ring":
+        hc2w, hfocal = ring_heldout_cameras(cfg.n_heldout, cfg.n_cams, cfg.width,
+                                            cfg.cam_radius, cfg.fov_deg, cfg.ring_elev_deg)
+    else:
+        hc2w, hfocal = make_cameras(rng, cfg.n_heldout, cfg.width, cfg.cam_radius,
+                                    "hemisphere" if cfg.cam_layout != "sphere"
+                                    else "sphere", cfg.fov_deg)
     x0 = constant_params(cfg.G, S, env_h, env_w, cfg.start_rgb, cfg.start_sigma)
     return Scene(cfg=cfg, G=cfg.G, radii=np.asarray(cfg.radii, np.float32),
                  env_h=env_h, env_w=env_w, c2w=c2w, focal=focal,
