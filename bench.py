@@ -168,6 +168,8 @@ def parse():
     ap.add_argument("--lpc-traj", type=int, default=400)
     ap.add_argument("--no-lpc-record", action="store_true",
                     help="leave the learned-preconditioner record out of the default line")
+    ap.add_argument("--brick", type=int, default=0,
+                    help="fix the brick edge of the PCG vectors (1, 2, 4, 8) after autotuning")
     ap.add_argument("--coef-budget", type=int, default=-1,
                     help="bytes for the coefficient store (-1: free memory - 6 GiB; 0: off, every "
                          "A p recomputes)")
@@ -773,6 +775,9 @@ def run_batch(args, rank, world, local):
     b.render(x_gt, target)
     x = torch.from_numpy(np.concatenate([s["x0"] for s in scenes])).to(dev)
     tuning = b.autotune(x)
+    if args.brick:
+        b.set_brick(args.brick)
+        tuning = dict(tuning, brick=args.brick, brick_fixed=True)
     for _ in range(args.warmup):
         b.gn_solve(x, target, 1)
     stream = torch.cuda.current_stream()
@@ -864,6 +869,9 @@ def run_ours(args, rank, world, local):
     gp = torch.Generator(device=dev).manual_seed(0)
     probe = torch.randn(sc.n_params, device=dev, generator=gp).to(sdt)
     tuning = ctx.autotune(x.to(sdt) if bf else x, probe)
+    if args.brick:
+        ctx.set_brick(args.brick)
+        tuning = dict(tuning, brick=args.brick, brick_fixed=True)
     del probe
     torch.cuda.synchronize()
     ctx.enable_timing(True)

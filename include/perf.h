@@ -139,8 +139,12 @@ typedef struct {
     int32_t ls_evals;     /* Error(gamma) evaluations */
     perf_pcg_info pcg;
     float ms;             /* device time of the step */
-    int32_t precond_fallback;  /* 1: the learned blocks failed the true-residual test and
-                                  the step's PCG was rerun with Jacobi */
+    int32_t precond_fallback;  /* 1: the step's PCG was rerun with Jacobi -- the learned
+                                  blocks failed the true-residual test (r^T r after PCG
+                                  not below r_0^T r_0, a breakdown or a non-finite
+                                  scalar), or no trial point of the line search lowered
+                                  F with the step of a block preconditioner (learned or
+                                  exact block-Jacobi) */
 } perf_gn_stats;
 
 /* Device time per kernel family, from CUDA events recorded on the launching
@@ -167,6 +171,9 @@ typedef struct {
                                  32-byte records (FP32 scenes); 0: two arrays */
     int32_t coef;             /* 1: the coefficient-cached A p was timed (it is
                                  what perf_gn_solve runs while the store fits) */
+    int32_t brick;            /* block order of a Gauss-Newton step's PCG vectors:
+                                 1 canonical, 4 or 8 bricks of that many voxels
+                                 per edge (see perf_set_brick) */
 } perf_tuning;
 
 /* Fills the defaults: max_samples 512, no jitter, 20 fixed PCG iterations,
@@ -271,6 +278,18 @@ perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_bl
  * step (or perf_autotune) used it, and the fraction of tiles it covered
  * (HOST pointers, may be NULL). */
 perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes);
+/* Block order of the vectors a Gauss-Newton step's PCG works on (p, A p, the
+ * Jacobi diagonal, the gradient, Delta, rho; an implementation choice the
+ * paper does not discuss): edge 1 = canonical [z][y][x]; edge 2, 4 or 8 =
+ * bricks of edge^3 voxels, bricks and the voxels in a brick each in
+ * [z][y][x] order (texel blocks unchanged), so that the 8 corners a sample
+ * gathers and the voxels a ray's window flushes share fewer cache lines.  G
+ * must be a multiple of edge (else PERF_ERR_INVALID_ARG).  perf_gn_solve
+ * applies it to a step only when every A p of the step runs from the
+ * coefficient store and the preconditioner works per voxel (Jacobi, exact
+ * block-Jacobi); otherwise that step is canonical.  x, the targets and every
+ * per-call entry point stay canonical.  perf_autotune sets it. */
+perf_status perf_set_brick(perf_ctx* ctx, int32_t edge);
 perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
                            double* coverage);
 /* Residual history of the context's last PCG solve (perf_pcg_begin /
@@ -436,6 +455,11 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
  * batch's global pixel-tile list; perf_batch_gn_solve's diagonal march fills
  * it and the captured PCG loop reads it). */
 perf_status perf_batch_set_coef_budget(perf_batch* b, int64_t bytes);
+/* perf_set_brick for a batch: edge 1, 2, 4 or 8; each scene whose G is a
+ * multiple of edge takes that brick order in the Gauss-Newton steps whose A p
+ * runs from the store, the others stay canonical.  perf_batch_autotune sets
+ * it. */
+perf_status perf_batch_set_brick(perf_batch* b, int32_t edge);
 perf_status perf_batch_coef_info(perf_batch* b, int64_t* bytes_held, int32_t* last_used);
 /* n_steps Gauss-Newton steps for every scene (Algorithm 2 per scene: with
  * opts.pcg_fixed exactly opts.pcg_iters iterations, else at most that many

@@ -68,7 +68,8 @@ TIMING_KINDS = ("apply", "forward", "diag", "vector", "precond", "residual")
 class Tuning(ctypes.Structure):
     _fields_ = [("tile_w", ctypes.c_int32), ("tile_h", ctypes.c_int32),
                 ("ctas_per_sm", ctypes.c_int32), ("apply_ms", ctypes.c_float),
-                ("paired", ctypes.c_int32), ("coef", ctypes.c_int32)]
+                ("paired", ctypes.c_int32), ("coef", ctypes.c_int32),
+                ("brick", ctypes.c_int32)]
 
 
 class GNStats(ctypes.Structure):
@@ -103,6 +104,7 @@ _SIGS = {
     "perf_pcg_set_blocks": [_VP, _VP, ctypes.c_int64],
     "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_set_coef_budget": [_VP, ctypes.c_int64],
+    "perf_set_brick": [_VP, ctypes.c_int32],
     "perf_pcg_history": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
     "perf_adam_step": [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, ctypes.c_float, _VP, _VP],
@@ -134,6 +136,7 @@ _SIGS = {
     "perf_batch_residual": [_VP, _VP, _VP, _VP, _VP, _VP],
     "perf_batch_autotune": [_VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_batch_set_coef_budget": [_VP, ctypes.c_int64],
+    "perf_batch_set_brick": [_VP, ctypes.c_int32],
     "perf_batch_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32)],
     "perf_batch_gn_solve": [_VP, _VP, _VP, ctypes.c_int32, ctypes.POINTER(GNStats), _VP],
 }
@@ -391,7 +394,7 @@ class Context:
         self._check(self.lib.perf_autotune(self.h, _ptr(x), _ptr(p), ctypes.byref(t),
                                            _stream(stream)), "autotune")
         return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms,
-                    paired=t.paired, coef=t.coef)
+                    paired=t.paired, coef=t.coef, brick=t.brick)
 
     def adam_step(self, x, target, m, v, t, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
                   F_out=None, stream=None):
@@ -411,6 +414,11 @@ class Context:
     def set_coef_budget(self, nbytes):
         """Budget of the coefficient store: -1 automatic, 0 off, > 0 bytes."""
         self._check(self.lib.perf_set_coef_budget(self.h, int(nbytes)), "set_coef_budget")
+
+    def set_brick(self, edge):
+        """Block order of a Gauss-Newton step's PCG vectors: 1 canonical, 2, 4
+        or 8 voxels per brick edge (perf_set_brick)."""
+        self._check(self.lib.perf_set_brick(self.h, int(edge)), "set_brick")
 
     def coef_info(self):
         b = ctypes.c_int64(0)
@@ -535,11 +543,16 @@ class Batch:
         self._check(self.lib.perf_batch_autotune(self.h, _ptr(x), ctypes.byref(t), _stream(stream)),
                     "batch autotune")
         return dict(tile_w=t.tile_w, tile_h=t.tile_h, ctas_per_sm=t.ctas_per_sm, apply_ms=t.apply_ms,
-                    coef=t.coef)
+                    coef=t.coef, brick=t.brick)
 
     def set_coef_budget(self, nbytes):
         """Budget of the coefficient store: -1 automatic, 0 off, > 0 bytes."""
         self._check(self.lib.perf_batch_set_coef_budget(self.h, int(nbytes)), "batch set_coef_budget")
+
+    def set_brick(self, edge):
+        """perf_batch_set_brick: brick edge 1, 2, 4 or 8 for the scenes whose G
+        allows it."""
+        self._check(self.lib.perf_batch_set_brick(self.h, int(edge)), "batch set_brick")
 
     def coef_info(self):
         b = ctypes.c_int64(0)

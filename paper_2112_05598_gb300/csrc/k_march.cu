@@ -309,14 +309,14 @@ struct VjpSink {
 // With `cross`, also the off-diagonal entries of the voxel's 4x4 block of
 // J^T J: (colour k, opacity) = sum_rays a s_k (colour-colour entries vanish,
 // and colour does not enter the auxiliary residual).
-template <int NV>
+template <int NV, class Key = CanonKey>
 struct DiagSink {
     float* diag;
     float* grad;
     float* cross;
     float r0, r1, r2;
     long long n_vox;
-    CanonKey km;
+    Key km;                   // the block order of diag, grad and cross
     float r3;
     __device__ __forceinline__ void put(bool ev, int key, const float (&a)[NV]) {
         const float s3 = NV == 5 ? a[(NV - 1) % NV] : 0.0f;
@@ -528,8 +528,11 @@ __device__ __forceinline__ void forward_tile(const DevScene& sc, const T* __rest
 }
 
 // All 32 lanes call it (the back-to-front sweep is warp-synchronous).
+// LAY (MODE 2): the diagonal, gradient and couplings go to the block order of
+// sc's LayoutKey (a brick order when a Gauss-Newton step's PCG vectors are
+// bricked); otherwise canonical.
 template <typename T, typename TP, int MODE, typename TV,   // 0 vjp, 1 apply A, 2 diag (+grad)
-          bool COUNT = false>
+          bool COUNT = false, bool LAY = false>
 __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __restrict__ x,
                                              const TP* __restrict__ p, const TV* __restrict__ v,
                                              float* __restrict__ out, float* __restrict__ out2,
@@ -583,11 +586,15 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
         if (MODE != 2 && vr[0] == 0.0f && vr[1] == 0.0f && vr[2] == 0.0f && va == 0.0f) act = false;
     }
     float4* crow = (MODE == 2 && coef && tile < coef_tiles) ? coef + tile_off[tile] * 32 + lane : nullptr;
+    using DKey = typename std::conditional<LAY, LayoutKey, CanonKey>::type;
+    DKey dk;
+    if constexpr (LAY) dk = layout_key(sc);
+    else dk = CanonKey{sc.G};
     if (MODE == 2 && sc.aux) {
-        DiagSink<5> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}, va};
+        DiagSink<5, DKey> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, dk, va};
         backward_sweep<5>(sc, x, R, ray, act, V, vr, sk, crow, kap);
     } else if (MODE == 2) {
-        DiagSink<4> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, CanonKey{sc.G}, 0.0f};
+        DiagSink<4, DKey> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, dk, 0.0f};
         backward_sweep<4>(sc, x, R, ray, act, V, vr, sk, crow);
     } else {
         VjpSink<CanonKey, COUNT> sk{out, vr[0], vr[1], vr[2], CanonKey{sc.G}, sc.red_count};
@@ -636,7 +643,7 @@ __global__ void __launch_bounds__(kThreads) k_jvp(DevScene sc, const T* __restri
     }
 }
 
-template <typename T, typename TP, int MODE, typename TV, bool COUNT = false>
+template <typename T, typename TP, int MODE, typename TV, bool COUNT = false, bool LAY = false>
 __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PERF_MIN_CTAS)
     k_scatter(DevScene sc, const T* __restrict__ x,
                                                       const TP* __restrict__ p,
@@ -648,7 +655,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
                                                       const long long* __restrict__ tile_off) {
     double acc = 0.0;
     PERF_TILE_LOOP {
-        scatter_tile<T, TP, MODE, TV, COUNT>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
+        scatter_tile<T, TP, MODE, TV, COUNT, LAY>(sc, x, p, v, out, out2, out3, tile, lane, acc, coef,
                                              tile_off, sc.coef_tiles);
     }
     if (MODE == 1 && pap) block_add_f64<kWarps>(acc, pap);
@@ -699,7 +706,8 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) 
     }
 }
 
-template <typename TP, bool COUNT = false>
+// BRICK: p and A p are in the block order of sc's LayoutKey (else canonical).
+template <typename TP, bool COUNT = false, bool BRICK = false>
 __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __restrict__ p,
                                                 const float4* __restrict__ coef,
                                                 const long long* __restrict__ tile_off,
@@ -723,7 +731,9 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
         for (int k = 0; k < R.K; ++k) {
             const float4 c = __ldcs(crow + (long long)k * 32);
             const Cell cl = sample_cell(sc, R, ray, k);
-            const float4 q = interp_grid(p, sc, cl);
+            float4 q;
+            if constexpr (BRICK) q = interp_grid_lay(p, layout_key(sc), cl);
+            else q = interp_grid(p, sc, cl);
             J[0] = fmaf(c.x, q.x, fmaf(c.y, q.w, J[0]));
             J[1] = fmaf(c.x, q.y, fmaf(c.z, q.w, J[1]));
             J[2] = fmaf(c.x, q.z, fmaf(c.w, q.w, J[2]));
@@ -745,7 +755,11 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
     }
     const float aux_v = Ja * kap;   // v_aux dL/dsigma per unit interpolation weight
     // J^T (J p): the scatter of Algorithm 1 with v = J p
-    VjpSink<CanonKey, COUNT> sk{out, J[0], J[1], J[2], CanonKey{sc.G}, sc.red_count};
+    using Key = typename std::conditional<BRICK, LayoutKey, CanonKey>::type;
+    Key km;
+    if constexpr (BRICK) km = layout_key(sc);
+    else km = CanonKey{sc.G};
+    VjpSink<Key, COUNT> sk{out, J[0], J[1], J[2], km, sc.red_count};
     for (int s = sc.S - 1; s >= 0; --s) {
         ShellHit hs;
         const bool hit = act && shell_lookup(sc, R, ray, s, hs);
@@ -790,12 +804,12 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
                w.v[q]);
 }
 
-template <typename TP, bool COUNT = false>
+template <typename TP, bool COUNT = false, bool BRICK = false>
 __global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
     k_apply_coef(DevScene sc, const TP* __restrict__ p, const float4* __restrict__ coef,
                  const long long* __restrict__ tile_off, float* __restrict__ out, double* pap) {
     double acc = 0.0;
-    PERF_TILE_LOOP { coef_apply_tile<TP, COUNT>(sc, p, coef, tile_off, out, tile, lane, acc); }
+    PERF_TILE_LOOP { coef_apply_tile<TP, COUNT, BRICK>(sc, p, coef, tile_off, out, tile, lane, acc); }
     if (pap) block_add_f64<kWarps>(acc, pap);
 }
 
@@ -872,7 +886,7 @@ __global__ void __launch_bounds__(kThreads) k_forward_batch(const BatchItem* __r
 // mode 2: diag (+ grad with v = residuals).  pcg (may be null): per-scene
 // Algorithm 2 state; tiles of scenes whose solve has exited are skipped (the
 // early exit of a graph-captured PCG loop).
-template <int MODE>
+template <int MODE, bool LAY = false>
 __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PERF_MIN_CTAS)
     k_scatter_batch(const BatchItem* __restrict__ items,
                                                             const long long* __restrict__ start,
@@ -897,7 +911,7 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
         if (pcg && pcg[sidx].done) continue;
         const BatchItem& b = it[sidx];
         double acc = 0.0;
-        scatter_tile<float, float, MODE, float>(b.sc, x + b.x_off, p ? p + b.x_off : nullptr,
+        scatter_tile<float, float, MODE, float, false, LAY>(b.sc, x + b.x_off, p ? p + b.x_off : nullptr,
                                                 v ? v + 3 * b.r_off : nullptr, out + b.x_off,
                                                 out2 ? out2 + b.x_off : nullptr, nullptr, tile,
                                                 lane, acc, coef,
@@ -911,7 +925,9 @@ __global__ void __launch_bounds__(kThreads, MODE == 1 ? PERF_APPLY_MIN_CTAS : PE
 }
 
 // Coefficient-cached A p over a batch (tile_off: rows of the global tile list;
-// scenes whose PCG has exited are skipped).
+// scenes whose PCG has exited are skipped).  BRICK: each scene's p and A p
+// are in the block order of its own LayoutKey (canonical for lay_s = 0).
+template <bool BRICK>
 __global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
     k_apply_coef_batch(const BatchItem* __restrict__ items, const long long* __restrict__ start,
                        int n, long long total, unsigned long long* counter,
@@ -928,8 +944,8 @@ __global__ void __launch_bounds__(kThreads, PERF_APPLY_MIN_CTAS)
         if (pcg && pcg[sidx].done) continue;
         const BatchItem& b = it[sidx];
         double acc = 0.0;
-        coef_apply_tile<float>(b.sc, p + b.x_off, coef, tile_off + b.tile_off, out + b.x_off, tile,
-                               lane, acc);
+        coef_apply_tile<float, false, BRICK>(b.sc, p + b.x_off, coef, tile_off + b.tile_off,
+                                             out + b.x_off, tile, lane, acc);
         acc = warp_sum(acc);
         if (lane == 0 && acc != 0.0) atomicAdd(&pap[(long long)sidx * pap_stride], acc);
     }
@@ -1059,6 +1075,9 @@ cudaError_t launch_scatter_t(const DevScene& sc, const void* x, const void* p, c
     if constexpr (MODE == 1) {   // A p: the counting instantiation when instrumented
         if (sc.red_count) fn = k_scatter<T, TP, MODE, TV, true>;
     }
+    if constexpr (MODE == 2) {   // the diagonal in a brick order
+        if (sc.lay_s) fn = k_scatter<T, TP, MODE, TV, false, true>;
+    }
     fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const T*>(x), static_cast<const TP*>(p), static_cast<const TV*>(v), out,
         out2, out3, pap, reinterpret_cast<float4*>(coef), tile_off);
@@ -1113,7 +1132,8 @@ cudaError_t launch_apply_coef_t(const DevScene& sc, const void* p, const float* 
                                 const long long* tile_off, float* out, double* pap,
                                 cudaStream_t st) {
     if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
-    auto fn = sc.red_count ? k_apply_coef<TP, true> : k_apply_coef<TP, false>;
+    auto fn = sc.lay_s ? (sc.red_count ? k_apply_coef<TP, true, true> : k_apply_coef<TP, false, true>)
+                       : (sc.red_count ? k_apply_coef<TP, true, false> : k_apply_coef<TP, false, false>);
     fn<<<grid_blocks((const void*)fn, sc.n_tiles - sc.tile_lo, sc.cap_per_sm), kThreads, 0, st>>>(
         sc, static_cast<const TP*>(p), reinterpret_cast<const float4*>(coef), tile_off, out, pap);
     count_launch();
@@ -1167,7 +1187,7 @@ cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start,
                                  const float* p, const float* v, float* out, float* out2,
                                  double* pap, int pap_stride, int mode, int cap_per_sm,
                                  cudaStream_t st, const PcgScalars* pcg, float* coef,
-                                 const long long* tile_off) {
+                                 const long long* tile_off, bool brick) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess || total == 0) return e;
     if (mode == 1) {
@@ -1176,7 +1196,7 @@ cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start,
             items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg, nullptr,
             nullptr);
     } else {
-        auto fn = k_scatter_batch<2>;
+        auto fn = brick ? k_scatter_batch<2, true> : k_scatter_batch<2, false>;
         fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
             items, start, n, total, counter, x, p, v, out, out2, pap, pap_stride, pcg,
             reinterpret_cast<float4*>(coef), tile_off);
@@ -1189,10 +1209,11 @@ cudaError_t launch_apply_coef_batch(const BatchItem* items, const long long* sta
                                     long long total, unsigned long long* counter, const float* p,
                                     const float* coef, const long long* tile_off, float* out,
                                     double* pap, int pap_stride, int cap_per_sm, cudaStream_t st,
-                                    const PcgScalars* pcg) {
+                                    const PcgScalars* pcg, bool brick) {
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st);
     if (e != cudaSuccess || total == 0) return e;
-    k_apply_coef_batch<<<batch_blocks((const void*)k_apply_coef_batch, cap_per_sm), kThreads, 0, st>>>(
+    auto fn = brick ? k_apply_coef_batch<true> : k_apply_coef_batch<false>;
+    fn<<<batch_blocks((const void*)fn, cap_per_sm), kThreads, 0, st>>>(
         items, start, n, total, counter, p, reinterpret_cast<const float4*>(coef), tile_off, out,
         pap, pap_stride, pcg);
     count_launch();

@@ -272,16 +272,30 @@ __global__ void __launch_bounds__(kVThreads) k_pair_pack(long long nb, const flo
     }
 }
 
+// Block of Delta that holds canonical parameter block u of a scene whose
+// PCG vectors are in the block order lay (x = G, y = s, z = ys, w = zs; see
+// LayoutKey): the grid's blocks are permuted, the texels' are not.
+__device__ __forceinline__ long long lay_block(long long u, int4 lay) {
+    const long long G = lay.x;
+    if (lay.y == 0 || u >= G * G * G) return u;
+    const int ui = (int)u, g = lay.x;
+    const int x = ui % g, yz = ui / g;
+    const int y = yz % g, z = yz / g;
+    const LayoutKey k{lay.y, (1 << lay.y) - 1, lay.z, lay.w};
+    return k.key(x, y, z);
+}
+
 // x_out = P(x + gamma Delta): the trial point is formed in FP64 (one FMA per
-// value) and rounded once to the storage type(s).
+// value) and rounded once to the storage type(s).  Delta in the block order
+// lay (x canonical).
 __global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4* x,
                                                     const float4* __restrict__ delta, double gamma,
                                                     int project, float4* x_out,
-                                                    __nv_bfloat16* x16) {
+                                                    __nv_bfloat16* x16, int4 lay) {
     for (long long v = (long long)blockIdx.x * blockDim.x + threadIdx.x; v < nb;
          v += (long long)gridDim.x * blockDim.x) {
         const float4 a = x[v];
-        const float4 d = delta[v];
+        const float4 d = delta[lay_block(v, lay)];
         float4 y = make_float4((float)fma(gamma, d.x, (double)a.x), (float)fma(gamma, d.y, (double)a.y),
                                (float)fma(gamma, d.z, (double)a.z), (float)fma(gamma, d.w, (double)a.w));
         if (project) {
@@ -297,18 +311,23 @@ __global__ void __launch_bounds__(kVThreads) k_trial(long long nb, const float4*
 
 // Batched trial: segment y gets x_out = P(x + gamma[y] Delta) where mask[y]
 // is set (mask == nullptr: every segment); other segments are left alone.
+// lay (may be null): per segment its block order and first block (lay[y],
+// base[y]) -- Delta of that segment is in that order.
 __global__ void __launch_bounds__(kVThreads) k_trial_seg(long long nb, const int4* chunks,
                                                         const float4* x,
                                                         const float4* __restrict__ delta,
                                                         const double* __restrict__ gamma,
                                                         const int* __restrict__ mask, int project,
-                                                        float4* x_out) {
+                                                        float4* x_out, const int4* __restrict__ lay,
+                                                        const long long* __restrict__ base) {
     const int sg = seg_id(chunks);
     if (mask && !mask[sg]) return;
     const double g = gamma[sg];
+    const int4 ly = lay ? lay[sg] : make_int4(0, 0, 0, 0);
+    const long long b0 = lay ? base[sg] : 0;
     SEG_LOOP(v) {
         const float4 a = x[v];
-        const float4 d = delta[v];
+        const float4 d = delta[ly.y ? b0 + lay_block(v - b0, ly) : v];
         float4 y = make_float4((float)fma(g, d.x, (double)a.x), (float)fma(g, d.y, (double)a.y),
                                (float)fma(g, d.z, (double)a.z), (float)fma(g, d.w, (double)a.w));
         if (project) {
@@ -463,22 +482,24 @@ cudaError_t launch_pcg_dir(long long n, const float* rho, const float* diag, con
 
 cudaError_t launch_trial_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                              const float* x, const float* delta, const double* gamma,
-                             const int* mask, int project, float* x_out, cudaStream_t st) {
+                             const int* mask, int project, float* x_out, cudaStream_t st,
+                             const int4* lay, const long long* base) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_trial_seg<<<seg_grid(nb, n_chunks, chunks), kVThreads, 0, st>>>(
-            nb, chunks, CF4(x), CF4(delta), gamma, mask, project, F4(x_out));
+            nb, chunks, CF4(x), CF4(delta), gamma, mask, project, F4(x_out), lay, base);
         count_launch();
     }
     return cudaGetLastError();
 }
 
 cudaError_t launch_trial(long long n, const float* x, const float* delta, double gamma,
-                         int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st) {
+                         int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st,
+                         int4 lay) {
     const long long nb = n / 4;
     if (nb > 0) {
         k_trial<<<vec_blocks(nb), kVThreads, 0, st>>>(nb, CF4(x), CF4(delta), gamma, project, F4(x_out),
-                                                      x16_out);
+                                                      x16_out, lay);
         count_launch();
     }
     return cudaGetLastError();

@@ -46,6 +46,9 @@ struct perf_ctx {
     float* p = nullptr;
     float* xp = nullptr;        // paired (x, p) records for A p (FP32 scenes)
     bool pair = true;           // Gauss-Newton A p reads the paired records
+    // brick order of a Gauss-Newton step's PCG vectors (LayoutKey shift; 0:
+    // canonical), used when the step's A p runs wholly from the store
+    int brick_s = 0;
     // coefficient-cached A p: per-sample (w_i, dH/dsigma_i) of the current
     // Gauss-Newton step, stored by its diagonal march (see k_march.cu)
     long long coef_budget = -1;        // bytes; -1 automatic, 0 off
@@ -370,6 +373,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
     d.We = ctx->scene.env_w;
     d.env_kind = ctx->scene.env_kind;
     d.n_vox = G * G * G;
+    set_layout(d, 0);
     d.shell_texels = texels;
     d.W = cams->width;
     d.H = cams->height;
@@ -565,15 +569,18 @@ cudaError_t apply_arrays(perf_ctx* ctx, const perf::DevScene& d, const void* x, 
 // and block preconditioner B (null: Jacobi).  paired: A p reads the paired
 // records ctx->xp, whose x half holds x (FP32 scenes); coef: A p from the
 // coefficient store of the current Gauss-Newton step.
+// dsp (may be null: ctx->ds): the scene descriptor of the step, whose
+// layout is the block order of the PCG vectors.
 perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const float* B, cudaStream_t st,
-                     bool paired = false, bool coef = false) {
+                     bool paired = false, bool coef = false, const perf::DevScene* dsp = nullptr) {
     const bool bf = ctx->scene.dtype == PERF_BF16;
     const void* pp = bf ? static_cast<const void*>(ctx->p16) : static_cast<const void*>(ctx->p);
+    const perf::DevScene& d0 = dsp ? *dsp : ctx->ds;
     t_begin(ctx, PERF_T_APPLY, st);
     // the store's tiles from the coefficients, any remaining tiles recomputed
-    perf::DevScene rest = ctx->ds;
+    perf::DevScene rest = d0;
     if (coef) {
-        perf::DevScene head = ctx->ds;
+        perf::DevScene head = d0;
         head.n_tiles = ctx->coef_tiles;
         CK(perf::launch_apply_coef(head, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef, ctx->tile_off,
                                    ctx->Ap, &ctx->s->pAp, st));
@@ -686,9 +693,18 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         ps = ensure_coef(ctx, st, &use_coef);
         if (ps != PERF_OK) return ps;
         ctx->ds.coef_tiles = use_coef ? ctx->coef_tiles : 0;
+        // the step's PCG vectors (and the diagonal, gradient and block
+        // couplings the diagonal march writes) take the tuned brick order when
+        // every A p of the step runs from the store and the preconditioner is
+        // per voxel; the learned network and caller-given blocks read the
+        // canonical order
+        perf::DevScene dl = ctx->ds;
+        perf::set_layout(dl, (use_coef && ctx->coef_tiles >= ctx->ds.n_tiles &&
+                              o.precond != PERF_PRECOND_BLOCK4) ? ctx->brick_s : 0);
+        const int4 lay = perf::layout_of(dl);
         t_begin(ctx, PERF_T_DIAG, st);
         if (ctx->n_rays > 0)
-            CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, xm, nullptr, PERF_F32, ctx->r,
+            CK(perf::launch_scatter(dl, ctx->scene.dtype, 2, xm, nullptr, PERF_F32, ctx->r,
                                     ctx->diag, ctx->grad, nullptr, st,
                                     need_cross ? ctx->cross : nullptr,
                                     use_coef ? ctx->coef : nullptr,
@@ -718,76 +734,88 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         int fallback = 0;
         const bool paired = !bf && ctx->pair && (!use_coef || ctx->coef_tiles < ctx->ds.n_tiles);
         if (paired) CK(perf::launch_pair_pack(ctx->n, x, nullptr, ctx->xp, st));
-        for (int attempt = 0; attempt < 2; ++attempt) {
-            ps = ensure_hist(ctx, o.pcg_iters);
-            if (ps != PERF_OK) return ps;
-            CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
-                                      ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
-                                      o.pcg_eps_rel, o.pcg_stall, B, nB, st,
-                                      paired ? ctx->xp : nullptr, ctx->hist, ctx->hist_cap));
-            for (int k = 0; k < o.pcg_iters; ++k) {
-                ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired, use_coef);
+        double F0 = 0.0;
+        CK(cudaMemcpyAsync(&F0, ctx->dF, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        double g_star = 1.0, mu_star = 0.0;
+        int evals = 0;
+        bool accept = false;
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int attempt = 0; attempt < 2; ++attempt) {
+                ps = ensure_hist(ctx, o.pcg_iters);
                 if (ps != PERF_OK) return ps;
-                if (!o.pcg_fixed) {
-                    int done = 0;
-                    CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-                    CK(cudaStreamSynchronize(st));
-                    if (done) break;
+                CK(perf::launch_pcg_begin(ctx->n, ctx->grad, ctx->diag, ctx->delta, ctx->rho, ctx->p,
+                                          ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
+                                          o.pcg_eps_rel, o.pcg_stall, B, nB, st,
+                                          paired ? ctx->xp : nullptr, ctx->hist, ctx->hist_cap));
+                for (int k = 0; k < o.pcg_iters; ++k) {
+                    ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired, use_coef, &dl);
+                    if (ps != PERF_OK) return ps;
+                    if (!o.pcg_fixed) {
+                        int done = 0;
+                        CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+                        CK(cudaStreamSynchronize(st));
+                        if (done) break;
+                    }
                 }
+                if (!(o.precond == PERF_PRECOND_BLOCK4 && blk) || B == nullptr) break;
+                // the true residual judges the learned preconditioner; Jacobi is the fallback
+                PcgScalars hj;
+                CK(cudaMemcpyAsync(&hj, ctx->s, sizeof(hj), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                // a convolution of the network whose bounded wait ran out left the
+                // blocks incomplete: that step's PCG is rerun with Jacobi
+                const bool conv_ok = !(o.precond == PERF_PRECOND_BLOCK4 && ctx->lpc) ||
+                                     perf::lpc_conv_error() == 0;
+                if (conv_ok && std::isfinite(hj.R) && hj.R < hj.R0 && hj.exit_reason != 3 &&
+                    hj.exit_reason != 4)
+                    break;
+                B = nullptr;
+                nB = 0;
+                fallback = 1;
             }
-            if (!(o.precond == PERF_PRECOND_BLOCK4 && blk) || B == nullptr) break;
-            // the true residual judges the learned preconditioner; Jacobi is the fallback
-            PcgScalars hj;
-            CK(cudaMemcpyAsync(&hj, ctx->s, sizeof(hj), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            // a convolution of the network whose bounded wait ran out left the
-            // blocks incomplete: that step's PCG is rerun with Jacobi
-            const bool conv_ok = !(o.precond == PERF_PRECOND_BLOCK4 && ctx->lpc) ||
-                                 perf::lpc_conv_error() == 0;
-            if (conv_ok && std::isfinite(hj.R) && hj.R < hj.R0 && hj.exit_reason != 3 &&
-                hj.exit_reason != 4)
-                break;
+            // Algorithm 3 on F(P(x + gamma Delta))
+            double gamma = 1.0, mu_prev = 3.4028234663852886e38;
+            g_star = 1.0;
+            mu_star = mu_prev;
+            bool found = false;
+            for (int it = 0; it <= o.ls_max; ++it) {
+                CK(perf::launch_trial(ctx->n, x, ctx->delta, gamma, o.project, ctx->x_trial,
+                                      bf ? ctx->t16 : nullptr, st, lay));
+                CK(cudaMemsetAsync(ctx->dF, 0, sizeof(double), st));
+                t_begin(ctx, PERF_T_FORWARD, st);
+                if (ctx->n_rays > 0)
+                    CK(perf::launch_forward(ctx->ds, ctx->scene.dtype,
+                                            bf ? static_cast<const void*>(ctx->t16)
+                                               : static_cast<const void*>(ctx->x_trial),
+                                            target, nullptr, nullptr, ctx->dF, 2, st));
+                t_end(ctx, PERF_T_FORWARD, st);
+                double mu = 0.0;
+                CK(cudaMemcpyAsync(&mu, ctx->dF, sizeof(double), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                ++evals;
+                if (std::isnan(mu)) mu = INFINITY;
+                if (mu > mu_prev) {
+                    g_star = gamma / o.ls_alpha;
+                    mu_star = mu_prev;
+                    found = true;
+                    break;
+                }
+                gamma *= o.ls_alpha;
+                mu_prev = mu;
+            }
+            if (!found) { g_star = gamma / o.ls_alpha; mu_star = mu_prev; }
+            accept = std::isfinite(mu_star) && mu_star < F0;
+            // a block preconditioner's step that the line search cannot use
+            // (no trial point lowers F) is redone with Jacobi PCG
+            if (accept || B == nullptr || pass == 1) break;
             B = nullptr;
             nB = 0;
             fallback = 1;
         }
-        double F0 = 0.0;
-        CK(cudaMemcpyAsync(&F0, ctx->dF, sizeof(double), cudaMemcpyDeviceToHost, st));
-        CK(cudaStreamSynchronize(st));
-        // Algorithm 3 on F(P(x + gamma Delta))
-        double gamma = 1.0, mu_prev = 3.4028234663852886e38, g_star = 1.0, mu_star = mu_prev;
-        int evals = 0;
-        bool found = false;
-        for (int it = 0; it <= o.ls_max; ++it) {
-            CK(perf::launch_trial(ctx->n, x, ctx->delta, gamma, o.project, ctx->x_trial,
-                                  bf ? ctx->t16 : nullptr, st));
-            CK(cudaMemsetAsync(ctx->dF, 0, sizeof(double), st));
-            t_begin(ctx, PERF_T_FORWARD, st);
-            if (ctx->n_rays > 0)
-                CK(perf::launch_forward(ctx->ds, ctx->scene.dtype,
-                                        bf ? static_cast<const void*>(ctx->t16)
-                                           : static_cast<const void*>(ctx->x_trial),
-                                        target, nullptr, nullptr, ctx->dF, 2, st));
-            t_end(ctx, PERF_T_FORWARD, st);
-            double mu = 0.0;
-            CK(cudaMemcpyAsync(&mu, ctx->dF, sizeof(double), cudaMemcpyDeviceToHost, st));
-            CK(cudaStreamSynchronize(st));
-            ++evals;
-            if (std::isnan(mu)) mu = INFINITY;
-            if (mu > mu_prev) {
-                g_star = gamma / o.ls_alpha;
-                mu_star = mu_prev;
-                found = true;
-                break;
-            }
-            gamma *= o.ls_alpha;
-            mu_prev = mu;
-        }
-        if (!found) { g_star = gamma / o.ls_alpha; mu_star = mu_prev; }
-        const bool accept = std::isfinite(mu_star) && mu_star < F0;
         if (accept) {
             CK(perf::launch_trial(ctx->n, x, ctx->delta, g_star, o.project, ctx->x_trial,
-                                  nullptr, st));
+                                  nullptr, st, lay));
             CK(cudaMemcpyAsync(x, ctx->x_trial, sizeof(float) * (size_t)ctx->n,
                                cudaMemcpyDeviceToDevice, st));
         }
@@ -876,7 +904,21 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
     if (pc != PERF_OK) return pc;
     if (use_coef && ctx->coef_tiles == ctx->ds.n_tiles) {
         float best = 1e30f, incumbent = 1e30f;
-        int best_tw = 8, best_cap = 0;
+        int best_tw = 8, best_cap = 0, best_s = 0;
+        auto time_coef = [&](const perf::DevScene& d, float& ms) -> cudaError_t {
+            cudaError_t e = cudaSuccess;
+            for (int rep = 0; rep < 3 && e == cudaSuccess; ++rep) {
+                if (rep == 1) e = cudaEventRecord(e0, st);
+                if (e == cudaSuccess)
+                    e = perf::launch_apply_coef(d, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef,
+                                                ctx->tile_off, ctx->Ap, nullptr, st);
+            }
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            ms *= 0.5f;
+            return e;
+        };
         for (int i = 0; i < 4; ++i) {
             set_tiling(ctx, tws[i]);
             bool fits = false;
@@ -887,25 +929,31 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
             CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr,
                                     ctx->diag, nullptr, nullptr, st, nullptr, ctx->coef,
                                     ctx->tile_off));
+            float tile_best = 1e30f;
+            int tile_cap = 0;
             for (int j = 0; j < 3; ++j) {
                 ctx->ds.cap_per_sm = caps[j];
-                for (int rep = 0; rep < 3; ++rep) {
-                    if (rep == 1) CK(cudaEventRecord(e0, st));
-                    CK(perf::launch_apply_coef(ctx->ds, pp, bf ? PERF_BF16 : PERF_F32, ctx->coef,
-                                               ctx->tile_off, ctx->Ap, nullptr, st));
-                }
-                CK(cudaEventRecord(e1, st));
-                CK(cudaEventSynchronize(e1));
                 float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                ms *= 0.5f;
+                CK(time_coef(ctx->ds, ms));
                 if (i == 0 && j == 0) incumbent = ms;
-                if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; }
+                if (ms < tile_best) { tile_best = ms; tile_cap = caps[j]; }
+                if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; best_s = 0; }
+            }
+            // the brick orders of the PCG vectors (4^3 and 8^3 voxels), at
+            // this tile shape's best CTA cap
+            for (int ls = 2; ls <= 3; ++ls) {
+                perf::DevScene dl = ctx->ds;
+                dl.cap_per_sm = tile_cap;
+                if (!perf::set_layout(dl, ls)) continue;
+                float ms = 0.f;
+                CK(time_coef(dl, ms));
+                if (ms < best) { best = ms; best_tw = tws[i]; best_cap = tile_cap; best_s = ls; }
             }
         }
-        if (!(best < 0.97f * incumbent)) { best = incumbent; best_tw = 8; best_cap = 0; }
+        if (!(best < 0.97f * incumbent)) { best = incumbent; best_tw = 8; best_cap = 0; best_s = 0; }
         set_tiling(ctx, best_tw);
         ctx->ds.cap_per_sm = best_cap;
+        ctx->brick_s = best_s;
         ctx->coef_used = true;
         if (out) {
             out->tile_w = best_tw;
@@ -914,6 +962,7 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
             out->apply_ms = best;
             out->paired = 0;
             out->coef = 1;
+            out->brick = 1 << best_s;
         }
         return PERF_OK;
     }
@@ -957,6 +1006,7 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
         if (ms < 0.97f * best) { best = ms; pair = false; }
     }
     ctx->pair = pair;
+    ctx->brick_s = 0;   // the recomputing A p runs in the canonical order
     if (out) {
         out->tile_w = best_tw;
         out->tile_h = 32 / best_tw;
@@ -964,6 +1014,7 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
         out->apply_ms = best;
         out->paired = pair ? 1 : 0;
         out->coef = 0;
+        out->brick = 1;
     }
     return PERF_OK;
 }
@@ -976,7 +1027,7 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
     unsigned long long* counter = ctx->ds.red_count;
     ctx->ds.red_count = nullptr;
     // a failed tuning run leaves the tiling, CTA cap and layout it started with
-    const int tw0 = ctx->ds.tile_w, cap0 = ctx->ds.cap_per_sm;
+    const int tw0 = ctx->ds.tile_w, cap0 = ctx->ds.cap_per_sm, s0 = ctx->brick_s;
     const bool pair0 = ctx->pair;
     const perf_status ps = autotune_impl(ctx, x, p, out, stream);
     ctx->ds.red_count = counter;
@@ -984,6 +1035,7 @@ perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuni
         set_tiling(ctx, tw0);
         ctx->ds.cap_per_sm = cap0;
         ctx->pair = pair0;
+        ctx->brick_s = s0;
     }
     return ps;
 }
@@ -1058,6 +1110,17 @@ perf_status perf_pcg_history(perf_ctx* ctx, double* R_out, int32_t cap, int32_t*
     const long long k = std::min<long long>(std::min<long long>(h.iter, ctx->hist_cap), cap);
     if (k > 0) CK(cudaMemcpy(R_out, ctx->hist, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost));
     *count_out = (int32_t)k;
+    return PERF_OK;
+}
+
+perf_status perf_set_brick(perf_ctx* ctx, int32_t edge) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    int s = 0;
+    while (s < 4 && (1 << s) < edge) ++s;
+    perf::DevScene d = ctx->ds;
+    if (edge < 1 || (1 << s) != edge || s > 3 || !perf::set_layout(d, s))
+        return fail(ctx, PERF_ERR_INVALID_ARG, "set_brick: edge 1, 2, 4 or 8 dividing G required");
+    ctx->brick_s = s;
     return PERF_OK;
 }
 

@@ -68,6 +68,12 @@ struct perf_batch {
     long long coef_rows = 0;
     int tab_tile_w = 0;
     bool use_coef = false;               // the PCG loop reads the store
+    // brick order of the PCG vectors (LayoutKey shift, per scene where G
+    // allows it), used by steps whose A p runs from the store
+    int brick_s = 0;
+    int lay_applied = 0;                 // shift the items carry now
+    bool any_brick = false;              // some scene's vectors are bricked
+    int4* d_lay = nullptr;               // per scene (G, s, ys, zs) for the trial kernel
     std::string err;
 };
 
@@ -184,7 +190,32 @@ cudaError_t apply_coef_launch(perf_batch* b, const float* p32, double* pap, cuda
     return perf::launch_apply_coef_batch(b->d_items, b->d_start, b->n, b->total_tiles, b->counter,
                                          p32, b->coef, b->tile_off, b->Ap, pap,
                                          (int)(sizeof(PcgScalars) / sizeof(double)), b->cap, st,
-                                         skip_done ? b->s : nullptr);
+                                         skip_done ? b->s : nullptr, b->any_brick);
+}
+
+// Gives every scene whose G is a multiple of 2^s the brick order s for its
+// PCG vectors (the others stay canonical) and uploads the items; a captured
+// PCG loop is dropped when the order changes.
+perf_status apply_layout(perf_batch* b, int s) {
+    if (s == b->lay_applied && b->d_lay) return PERF_OK;
+    if (!b->d_lay) BK(dalloc(&b->d_lay, b->n));
+    std::vector<int4> lay(b->n);
+    b->any_brick = false;
+    for (int i = 0; i < b->n; ++i) {
+        DevScene& d = b->items[i].sc;
+        perf::set_layout(d, s);
+        b->any_brick |= d.lay_s > 0;
+        lay[i] = perf::layout_of(d);
+    }
+    BK(cudaMemcpy(b->d_lay, lay.data(), sizeof(int4) * b->n, cudaMemcpyHostToDevice));
+    BK(cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchItem) * b->n, cudaMemcpyHostToDevice));
+    b->lay_applied = s;
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+        b->graph_iters = -1;
+    }
+    return PERF_OK;
 }
 
 // One Algorithm 2 iteration for every scene.
@@ -297,6 +328,7 @@ perf_status perf_batch_create(perf_batch** out, int32_t n_scenes, const perf_sce
         d.We = sc.n_shells > 0 ? sc.env_w : 0;
         d.env_kind = sc.env_kind;
         d.n_vox = G * G * G;
+        set_layout(d, 0);
         d.shell_texels = (long long)d.He * d.We;
         d.W = c.width;
         d.H = c.height;
@@ -383,7 +415,7 @@ perf_status perf_batch_destroy(perf_batch* b) {
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
     void* bufs[] = {b->shell_tab, b->d_items, b->d_start, b->d_seg, b->d_chunks, b->cams, b->counter, b->x_work, b->x_trial,
                     b->r, b->diag, b->grad, b->delta, b->rho, b->p, b->Ap, b->s, b->F,
-                    b->gamma, b->mask, b->tile_off, b->coef};
+                    b->gamma, b->mask, b->tile_off, b->coef, b->d_lay};
     for (void* q : bufs)
         if (q) cudaFree(q);
     delete b;
@@ -428,10 +460,11 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
     const int tws[4] = {8, 4, 16, 32};
     const int caps[3] = {0, 3, 2};
     float best = 1e30f;
-    int best_tw = 8, best_cap = 0;
+    int best_tw = 8, best_cap = 0, best_s = 0;
     // with the coefficient store (it fits at the default tiling) the
     // coefficient-cached A p is timed, its store laid out and filled at x
     // for every tile shape
+    if (apply_layout(b, 0) != PERF_OK) return PERF_ERR_CUDA;
     if (apply_tiling(b, 8) != PERF_OK) return PERF_ERR_CUDA;
     bool coef = false;
     perf_status pc = ensure_coef(b, st, &coef);
@@ -448,25 +481,46 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
                                           x, nullptr, nullptr, b->diag, nullptr, nullptr, 0, 2,
                                           b->cap, st, nullptr, b->coef, b->tile_off));
         }
-        for (int j = 0; j < 3; ++j) {
-            b->cap = caps[j];
-            auto launch = [&]() {
-                return coef ? apply_coef_launch(b, b->p, &b->s[0].pAp, st, false)
-                            : apply_launch(b, x, b->p, st);
-            };
+        auto launch = [&]() {
+            return coef ? apply_coef_launch(b, b->p, &b->s[0].pAp, st, false)
+                        : apply_launch(b, x, b->p, st);
+        };
+        auto time_one = [&](float& ms) -> perf_status {
             BK(launch());                                             // warm-up
             BK(cudaEventRecord(e0, st));
             BK(launch());
             BK(cudaEventRecord(e1, st));
             BK(cudaEventSynchronize(e1));
-            float ms = 0.f;
             BK(cudaEventElapsedTime(&ms, e0, e1));
-            if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; }
+            return PERF_OK;
+        };
+        float tile_best = 1e30f;
+        int tile_cap = 0;
+        for (int j = 0; j < 3; ++j) {
+            b->cap = caps[j];
+            float ms = 0.f;
+            pc = time_one(ms);
+            if (pc != PERF_OK) return pc;
+            if (ms < tile_best) { tile_best = ms; tile_cap = caps[j]; }
+            if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; best_s = 0; }
         }
+        // the brick orders of the PCG vectors (coefficient-cached A p only),
+        // at this tile shape's best CTA cap
+        for (int ls = 2; coef && ls <= 3; ++ls) {
+            if (apply_layout(b, ls) != PERF_OK) return PERF_ERR_CUDA;
+            if (!b->any_brick) continue;
+            b->cap = tile_cap;
+            float ms = 0.f;
+            pc = time_one(ms);
+            if (pc != PERF_OK) return pc;
+            if (ms < best) { best = ms; best_tw = tws[i]; best_cap = tile_cap; best_s = ls; }
+        }
+        if (apply_layout(b, 0) != PERF_OK) return PERF_ERR_CUDA;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     b->cap = best_cap;
+    b->brick_s = best_s;
     if (apply_tiling(b, best_tw) != PERF_OK) return PERF_ERR_CUDA;
     if (out) {
         out->tile_w = best_tw;
@@ -475,7 +529,14 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
         out->apply_ms = best;
         out->paired = 0;
         out->coef = coef ? 1 : 0;
+        out->brick = 1 << best_s;
     }
+    return PERF_OK;
+}
+
+perf_status perf_batch_set_brick(perf_batch* b, int32_t edge) {
+    if (!b || (edge != 1 && edge != 2 && edge != 4 && edge != 8)) return PERF_ERR_INVALID_ARG;
+    b->brick_s = edge == 8 ? 3 : edge == 4 ? 2 : edge == 2 ? 1 : 0;
     return PERF_OK;
 }
 
@@ -508,6 +569,8 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
     perf_status ps = ensure_coef(b, st, &use);
     if (ps != PERF_OK) return ps;
     b->use_coef = use;
+    ps = apply_layout(b, use ? b->brick_s : 0);
+    if (ps != PERF_OK) return ps;
     ps = ensure_graph(b, o.pcg_iters);
     if (ps != PERF_OK) return ps;
     cudaEvent_t e0, e1;
@@ -527,7 +590,7 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
         BK(perf::launch_scatter_batch(b->d_items, b->d_start, n, b->total_tiles, b->counter,
                                       b->x_work, nullptr, b->r, b->diag, b->grad, nullptr, 0, 2,
                                       b->cap, st, nullptr, b->use_coef ? b->coef : nullptr,
-                                      b->use_coef ? b->tile_off : nullptr));
+                                      b->use_coef ? b->tile_off : nullptr, b->any_brick));
         BK(perf::launch_pcg_begin_seg(b->n_params, n, b->d_chunks, b->n_chunks, b->grad, b->diag,
                                       b->delta, b->rho, b->p, nullptr, b->Ap, b->s,
                                       o.pcg_iters, o.pcg_fixed, o.pcg_eps_rel, o.pcg_stall,
@@ -551,7 +614,8 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
             BK(cudaMemcpyAsync(b->gamma, gam.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
             BK(cudaMemcpyAsync(b->mask, live.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
             BK(perf::launch_trial_seg(b->n_params, n, b->d_chunks, b->n_chunks, b->x_work, b->delta,
-                                      b->gamma, b->mask, o.project, b->x_trial, st));
+                                      b->gamma, b->mask, o.project, b->x_trial, st,
+                                      b->any_brick ? b->d_lay : nullptr, b->d_seg));
             BK(cudaMemsetAsync(b->F, 0, sizeof(double) * n, st));
             BK(perf::launch_forward_batch(b->d_items, b->d_start, n, b->total_tiles, b->counter,
                                           b->x_trial, target, nullptr, b->F, b->mask, 2, b->cap, st));
@@ -580,7 +644,8 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
         BK(cudaMemcpyAsync(b->gamma, g_star.data(), sizeof(double) * n, cudaMemcpyHostToDevice, st));
         BK(cudaMemcpyAsync(b->mask, acc.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
         BK(perf::launch_trial_seg(b->n_params, n, b->d_chunks, b->n_chunks, b->x_work, b->delta,
-                                  b->gamma, b->mask, o.project, b->x_work, st));
+                                  b->gamma, b->mask, o.project, b->x_work, st,
+                                  b->any_brick ? b->d_lay : nullptr, b->d_seg));
         BK(cudaEventRecord(e1, st));
         BK(cudaMemcpyAsync(hs.data(), b->s, sizeof(PcgScalars) * n, cudaMemcpyDeviceToHost, st));
         BK(cudaStreamSynchronize(st));

@@ -53,7 +53,33 @@ struct DevScene {
     // Shell hits per ray (n_rays x S entries, see shell_entry); null: each
     // march computes them itself in FP32.
     const float4* shell_tab;
+    // Block order of the grid part of the parameter-space vectors a
+    // Gauss-Newton step's PCG works on (p, A p, the diagonal, the gradient,
+    // Delta, rho): see LayoutKey.  lay_s = 0: canonical [z][y][x].
+    int lay_s, lay_ys, lay_zs;
 };
+
+// Index of voxel (x, y, z) in a parameter-space vector.  lay_s = 0: the
+// canonical order z G^2 + y G + x.  lay_s = s > 0: bricks of B^3 voxels
+// (B = 2^s, G a multiple of B), the bricks in [z][y][x] order and the voxels
+// of a brick in [z][y][x] order.  Either way the index is a sum of one term
+// per axis,
+//   f(x) = (x >> s) B^3 + (x & (B-1)),  g(y) = (y >> s) ys + (y & (B-1)) B,
+//   h(z) = (z >> s) zs + (z & (B-1)) B^2,
+// with ys = (G/B) B^3 and zs = (G/B)^2 B^3 (G and G^2 when s = 0), so the
+// index of a neighbour differs in one term only.  Texel blocks follow the
+// grid unchanged.
+struct LayoutKey {
+    int s, m, ys, zs;
+    __device__ __forceinline__ int fx(int x) const { return ((x >> s) << (3 * s)) + (x & m); }
+    __device__ __forceinline__ int gy(int y) const { return (y >> s) * ys + ((y & m) << s); }
+    __device__ __forceinline__ int hz(int z) const { return (z >> s) * zs + ((z & m) << (2 * s)); }
+    __device__ __forceinline__ int key(int x, int y, int z) const { return fx(x) + gy(y) + hz(z); }
+    __device__ __forceinline__ int shell(int idx) const { return idx; }
+};
+__device__ __forceinline__ LayoutKey layout_key(const DevScene& sc) {
+    return LayoutKey{sc.lay_s, (1 << sc.lay_s) - 1, sc.lay_ys, sc.lay_zs};
+}
 
 struct Ray {
     float o[3], d[3];
@@ -268,6 +294,33 @@ __device__ __forceinline__ float4 interp_grid(const T* x, const DevScene& sc, co
     a[5] = Store<T>::ld(x, i0 + sz + 1);
     a[6] = Store<T>::ld(x, i0 + sz + sy);
     a[7] = Store<T>::ld(x, i0 + sz + sy + 1);
+#if PERF_INTERP_W
+    float W[8];
+    tri_weights(c, W);
+    return wsum8(W, a);
+#else
+    const float4 b00 = lerp4(a[0], a[1], c.fx), b10 = lerp4(a[2], a[3], c.fx);
+    const float4 b01 = lerp4(a[4], a[5], c.fx), b11 = lerp4(a[6], a[7], c.fx);
+    const float4 c0 = lerp4(b00, b10, c.fy), c1 = lerp4(b01, b11, c.fy);
+    return lerp4(c0, c1, c.fz);
+#endif
+}
+
+// interp_grid for a vector stored in the order of a LayoutKey.
+template <typename T>
+__device__ __forceinline__ float4 interp_grid_lay(const T* x, const LayoutKey& k, const Cell& c) {
+    const int x0 = k.fx(c.bx), x1 = k.fx(c.bx + 1);
+    const int y0 = k.gy(c.by), y1 = k.gy(c.by + 1);
+    const int z0 = k.hz(c.bz), z1 = k.hz(c.bz + 1);
+    float4 a[8];
+    a[0] = Store<T>::ld(x, x0 + y0 + z0);
+    a[1] = Store<T>::ld(x, x1 + y0 + z0);
+    a[2] = Store<T>::ld(x, x0 + y1 + z0);
+    a[3] = Store<T>::ld(x, x1 + y1 + z0);
+    a[4] = Store<T>::ld(x, x0 + y0 + z1);
+    a[5] = Store<T>::ld(x, x1 + y0 + z1);
+    a[6] = Store<T>::ld(x, x0 + y1 + z1);
+    a[7] = Store<T>::ld(x, x1 + y1 + z1);
 #if PERF_INTERP_W
     float W[8];
     tri_weights(c, W);

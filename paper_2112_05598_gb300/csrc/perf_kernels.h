@@ -34,14 +34,16 @@ cudaError_t launch_scatter_batch(const BatchItem* items, const long long* start,
                                  const float* p, const float* v, float* out, float* out2,
                                  double* pap, int pap_stride, int mode, int cap_per_sm,
                                  cudaStream_t st, const PcgScalars* pcg = nullptr,
-                                 float* coef = nullptr, const long long* tile_off = nullptr);
+                                 float* coef = nullptr, const long long* tile_off = nullptr,
+                                 bool brick = false);
 // Coefficient-cached A p over a batch, and the rows of every tile of the
-// global tile list (see launch_tile_rows).
+// global tile list (see launch_tile_rows).  brick: p and A p of each scene
+// are in the block order of its items[i].sc layout (else all canonical).
 cudaError_t launch_apply_coef_batch(const BatchItem* items, const long long* start, int n,
                                     long long total, unsigned long long* counter, const float* p,
                                     const float* coef, const long long* tile_off, float* out,
                                     double* pap, int pap_stride, int cap_per_sm, cudaStream_t st,
-                                    const PcgScalars* pcg);
+                                    const PcgScalars* pcg, bool brick = false);
 cudaError_t launch_tile_rows_batch(const BatchItem* items, const long long* start, int n,
                                    long long total, int* rows, cudaStream_t st);
 
@@ -67,6 +69,24 @@ struct PcgScalars {
     double* hist;     // null, or R after iteration k written to hist[k - 1] (k <= hist_cap)
     long long hist_cap;
 };
+
+// Sets the parameter-vector block order of d (see LayoutKey): s = 0 the
+// canonical order, s > 0 bricks of 2^s voxels per edge.  Returns false (and
+// leaves d canonical) when G is not a multiple of the brick edge.
+inline bool set_layout(DevScene& d, int s) {
+    const long long G = d.G;
+    if (s <= 0 || G % (1ll << s) != 0) {
+        d.lay_s = 0;
+        d.lay_ys = (int)G;
+        d.lay_zs = (int)(G * G);
+        return s <= 0;
+    }
+    const long long B = 1ll << s, nb = G / B;
+    d.lay_s = s;
+    d.lay_ys = (int)(nb * B * B * B);
+    d.lay_zs = (int)(nb * nb * B * B * B);
+    return true;
+}
 
 // Kernels launched by this library since load (instrumentation).
 extern unsigned long long g_launches;
@@ -130,9 +150,14 @@ cudaError_t launch_pcg_dir(long long n, const float* rho, const float* diag, con
 cudaError_t launch_pair_pack(long long n, const float* x, const float* p, float* xp,
                              cudaStream_t st);
 // x_out = P(x + gamma delta) (project: sigma >= 0, 0 <= c <= 1), formed in FP64;
-// optional float32 and bf16 outputs.
+// optional float32 and bf16 outputs.  delta is in the block order lay
+// (x = G, y = brick shift s, z = ys, w = zs of the LayoutKey; y = 0:
+// canonical, the default), x and the outputs are canonical.
 cudaError_t launch_trial(long long n, const float* x, const float* delta, double gamma,
-                         int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st);
+                         int project, float* x_out, __nv_bfloat16* x16_out, cudaStream_t st,
+                         int4 lay = int4{0, 0, 0, 0});
+// The int4 block order of d for launch_trial.
+inline int4 layout_of(const DevScene& d) { return int4{d.G, d.lay_s, d.lay_ys, d.lay_zs}; }
 cudaError_t launch_to_bf16(long long n, const float* x, __nv_bfloat16* y, cudaStream_t st);
 // One Adam step with projection (k_pcg.cu); c1, c2 the bias corrections.
 cudaError_t launch_adam(long long n, float* x, const float* g, float* m, float* v, float b1,
@@ -158,9 +183,12 @@ cudaError_t launch_pcg_dir_seg(long long n, int n_seg, const int4* chunks, long 
                                long long n_block, float* p, __nv_bfloat16* p16, PcgScalars* s,
                                cudaStream_t st, float* pxp = nullptr);
 // Segment y: x_out = P(x + gamma[y] Delta) where mask[y] (or every segment).
+// lay / base (device, n_seg entries each, may be null): segment y's Delta is
+// in the block order lay[y] (see launch_trial) from its first block base[y].
 cudaError_t launch_trial_seg(long long n, int n_seg, const int4* chunks, long long n_chunks,
                              const float* x, const float* delta, const double* gamma,
-                             const int* mask, int project, float* x_out, cudaStream_t st);
+                             const int* mask, int project, float* x_out, cudaStream_t st,
+                             const int4* lay = nullptr, const long long* base = nullptr);
 
 // Level change of the hierarchical formulation (k_hier.cu): y (level 2G,
 // maps 2He x 2We) from x (level G, maps He x We).

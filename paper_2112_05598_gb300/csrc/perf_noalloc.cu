@@ -101,6 +101,7 @@ extern "C" perf_status perf_residual_noalloc(const perf_scene* sc, const perf_ca
     d.We = sc->n_shells > 0 ? sc->env_w : 0;
     d.env_kind = sc->env_kind;
     d.n_vox = G * G * G;
+    set_layout(d, 0);
     d.shell_texels = texels;
     d.W = cams->width;
     d.H = cams->height;
