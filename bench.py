@@ -472,6 +472,7 @@ def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train
         it = T.pcg_iterations(ctx, x0, target, pc, eps=1e-3, max_iter=traj_iters)
         rel = it["rel_residual"]
         first[name] = {"iters_to": it["iters_to"], "iters": it["iters"], "exit": it["exit"],
+                       "coef_coverage": ctx.coef_info()["coverage"],
                        "ms_per_iter": it["ms"] / max(it["iters"], 1),
                        "rel_residual_at": {str(k): rel[k - 1]
                                            for k in (5, 10, 20, 50, 100, 200, 300, 600, 1200)
@@ -485,9 +486,12 @@ def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train
     gn = {}
     for reg, opts in regimes.items():
         runs = {}
-        for name, pc in methods:
+        # the learned blocks under both judges of a step's PCG: the true residual
+        # (the default) and the objective (the line search)
+        gn_methods = methods + (("learned_objective_judge", PERF_PRECOND_BLOCK4),)
+        for name, pc in gn_methods:
             x = x0.clone()
-            ctx.set_options(precond=pc, **opts)
+            ctx.set_options(precond=pc, precond_judge=int(name == "learned_objective_judge"), **opts)
             ctx.set_lpc(net if pc == PERF_PRECOND_BLOCK4 else None)
             hold.residual(x, htarget, None, F)
             curve = [(0.0, _psnr_from_F(float(F.item()), hold.n_rays))]

@@ -62,6 +62,17 @@ enum { PERF_PRECOND_JACOBI = 0,        /* diag(J^T J) (Section "Preconditioner")
        PERF_PRECOND_BLOCK4 = 1,        /* 4x4 block per voxel: learned (perf_set_lpc) or
                                           caller-supplied (perf_pcg_set_blocks) */
        PERF_PRECOND_BLOCK_JACOBI = 2   /* exact inverse of each voxel's 4x4 block of J^T J */ };
+/* What decides that a Gauss-Newton step's PCG with the learned blocks is
+ * rerun with Jacobi (perf_options.precond_judge).  Either way a breakdown, a
+ * non-finite scalar or a convolution whose bounded wait ran out falls back,
+ * and a step of a block preconditioner that no trial point of the line
+ * search can use is redone with Jacobi. */
+enum { PERF_JUDGE_RESIDUAL = 0,   /* the true PCG residual: r^T r after PCG must
+                                     be below r_0^T r_0 */
+       PERF_JUDGE_OBJECTIVE = 1   /* the objective: the line search judges the
+                                     step (CG's residual norm is not monotone, and
+                                     after the 1-3 iterations a step runs it is often
+                                     above r_0 for a good direction) */ };
 enum { PERF_EXIT_FIXED = 0, PERF_EXIT_EPS = 1, PERF_EXIT_STALL = 2,
        PERF_EXIT_BREAKDOWN = 3, PERF_EXIT_NONFINITE = 4 };
 
@@ -121,6 +132,7 @@ typedef struct {
                              ray, [r_0, r_1, r_2, L] (targets stay 3 per ray).
                              Single-scene contexts only. */
     double aux_lambda;    /* its factor (the paper's 0.1), >= 0 */
+    int32_t precond_judge;  /* PERF_JUDGE_* (default PERF_JUDGE_RESIDUAL) */
 } perf_options;
 
 typedef struct {

@@ -17,6 +17,7 @@ LIB_PATH = os.environ.get("PERF_LIB_PATH") or os.path.join(HERE, "libperf.so")
 
 PERF_F32, PERF_BF16 = 0, 1
 PERF_PRECOND_JACOBI, PERF_PRECOND_BLOCK4, PERF_PRECOND_BLOCK_JACOBI = 0, 1, 2
+PERF_JUDGE_RESIDUAL, PERF_JUDGE_OBJECTIVE = 0, 1
 PERF_ENV_EQUIRECT, PERF_ENV_CUBE = 0, 1
 STATUS = {0: "PERF_OK", 1: "PERF_ERR_INVALID_ARG", 2: "PERF_ERR_CUDA",
           3: "PERF_ERR_NONFINITE", 4: "PERF_ERR_TIMEOUT", 5: "PERF_ERR_NOT_SPD",
@@ -50,7 +51,8 @@ class Options(ctypes.Structure):
                 ("pcg_eps_rel", ctypes.c_double), ("pcg_stall", ctypes.c_double),
                 ("ls_alpha", ctypes.c_double), ("ls_max", ctypes.c_int32),
                 ("project", ctypes.c_int32), ("precond", ctypes.c_int32),
-                ("aux", ctypes.c_int32), ("aux_lambda", ctypes.c_double)]
+                ("aux", ctypes.c_int32), ("aux_lambda", ctypes.c_double),
+                ("precond_judge", ctypes.c_int32)]
 
 
 class PcgInfo(ctypes.Structure):

@@ -126,6 +126,10 @@ perf_status check_options(const perf_options* o, std::string& why) {
         why = "aux must be 0 or 1 and aux_lambda finite and >= 0";
         return PERF_ERR_INVALID_ARG;
     }
+    if (o->precond_judge != PERF_JUDGE_RESIDUAL && o->precond_judge != PERF_JUDGE_OBJECTIVE) {
+        why = "unknown precond_judge";
+        return PERF_ERR_INVALID_ARG;
+    }
     return PERF_OK;
 }
 
@@ -759,7 +763,9 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
                     }
                 }
                 if (!(o.precond == PERF_PRECOND_BLOCK4 && blk) || B == nullptr) break;
-                // the true residual judges the learned preconditioner; Jacobi is the fallback
+                // the true residual (PERF_JUDGE_RESIDUAL) judges the learned
+                // preconditioner, or only its breakdowns do and the line search
+                // below judges the step (PERF_JUDGE_OBJECTIVE); Jacobi is the fallback
                 PcgScalars hj;
                 CK(cudaMemcpyAsync(&hj, ctx->s, sizeof(hj), cudaMemcpyDeviceToHost, st));
                 CK(cudaStreamSynchronize(st));
@@ -767,7 +773,8 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
                 // blocks incomplete: that step's PCG is rerun with Jacobi
                 const bool conv_ok = !(o.precond == PERF_PRECOND_BLOCK4 && ctx->lpc) ||
                                      perf::lpc_conv_error() == 0;
-                if (conv_ok && std::isfinite(hj.R) && hj.R < hj.R0 && hj.exit_reason != 3 &&
+                const bool residual_ok = o.precond_judge == PERF_JUDGE_OBJECTIVE || hj.R < hj.R0;
+                if (conv_ok && std::isfinite(hj.R) && residual_ok && hj.exit_reason != 3 &&
                     hj.exit_reason != 4)
                     break;
                 B = nullptr;

@@ -248,3 +248,34 @@ def test_trained_network_gain_on_held_out_systems():
     print(f"first systems, mean iterations: {mean}; third systems to 0.01: {later_mean}")
     assert mean[("learned", "0.1")] < mean[("jacobi", "0.1")], mean
     assert mean[("learned", "0.01")] < mean[("jacobi", "0.01")], mean
+
+
+def test_judges_of_the_learned_step():
+    """Both judges of a Gauss-Newton step's PCG with the learned blocks run
+    through perf_gn_solve: the true-residual judge (default) and the
+    objective judge (a step the line search accepts is kept; breakdowns still
+    fall back).  With the identity network the blocks are Jacobi, so both give
+    Jacobi's step; an unknown judge is rejected."""
+    from paper_2112_05598_gb300 import (PERF_JUDGE_OBJECTIVE, PERF_PRECOND_BLOCK4,
+                                        PERF_PRECOND_JACOBI, Context, LPC, PerfError)
+    from oracle import Oracle
+    from scenegen import make_scene
+    sc = make_scene("small32")
+    target = cuda_tensor(Oracle.from_scene(sc).render(sc.x_gt)[0].astype(np.float32).ravel())
+    net = LPC(seed=1)
+    out = {}
+    for name, pc, judge in (("jacobi", PERF_PRECOND_JACOBI, 0), ("residual", PERF_PRECOND_BLOCK4, 0),
+                            ("objective", PERF_PRECOND_BLOCK4, PERF_JUDGE_OBJECTIVE)):
+        ctx = Context.from_scene(sc, pcg_iters=3, pcg_fixed=1, precond=pc, precond_judge=judge)
+        if pc == PERF_PRECOND_BLOCK4:
+            ctx.set_lpc(net)
+        xd = cuda_tensor(sc.x0.copy())
+        st = ctx.gn_solve(xd, target, 2)
+        assert all(s["accepted"] for s in st)
+        out[name] = (host(xd), [s["precond_fallback"] for s in st])
+    print({k: v[1] for k, v in out.items()})
+    assert rel_l2(out["objective"][0], out["jacobi"][0]) < 5e-2
+    assert rel_l2(out["residual"][0], out["jacobi"][0]) < 5e-2
+    assert not any(out["objective"][1])
+    with pytest.raises(PerfError):
+        Context.from_scene(sc, precond_judge=2)
