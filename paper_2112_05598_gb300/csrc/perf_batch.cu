@@ -95,6 +95,15 @@ cudaError_t dalloc(T** p, long long count) {
 
 inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 
+// Two CUDA events destroyed on every return path.
+struct EventPair {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    ~EventPair() {
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+    }
+};
+
 // Re-tile every scene for tile width tw and upload items and tile offsets.
 perf_status apply_tiling(perf_batch* b, int tw) {
     b->tile_w = tw;
@@ -453,9 +462,11 @@ perf_status perf_batch_residual(perf_batch* b, const float* x, const float* targ
 perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out, void* stream) {
     if (!b || !x) return PERF_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
-    cudaEvent_t e0, e1;
-    BK(cudaEventCreate(&e0));
-    BK(cudaEventCreate(&e1));
+    // events live until every return path has left (scope guard)
+    EventPair ev;
+    BK(cudaEventCreate(&ev.e0));
+    BK(cudaEventCreate(&ev.e1));
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     BK(cudaMemcpyAsync(b->p, x, sizeof(float) * (size_t)b->n_params, cudaMemcpyDeviceToDevice, st));
     const int tws[4] = {8, 4, 16, 32};
     const int caps[3] = {0, 3, 2};
@@ -517,8 +528,6 @@ perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out,
         }
         if (apply_layout(b, 0) != PERF_OK) return PERF_ERR_CUDA;
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     b->cap = best_cap;
     b->brick_s = best_s;
     if (apply_tiling(b, best_tw) != PERF_OK) return PERF_ERR_CUDA;
@@ -573,9 +582,10 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
     if (ps != PERF_OK) return ps;
     ps = ensure_graph(b, o.pcg_iters);
     if (ps != PERF_OK) return ps;
-    cudaEvent_t e0, e1;
-    BK(cudaEventCreate(&e0));
-    BK(cudaEventCreate(&e1));
+    EventPair ev;
+    BK(cudaEventCreate(&ev.e0));
+    BK(cudaEventCreate(&ev.e1));
+    cudaEvent_t e0 = ev.e0, e1 = ev.e1;
     std::vector<double> F0(n), Fm(n), gam(n), mu_prev(n), g_star(n), mu_star(n);
     std::vector<int> live(n), acc(n), evals(n);
     std::vector<PcgScalars> hs(n);
@@ -670,8 +680,6 @@ perf_status perf_batch_gn_solve(perf_batch* b, float* x, const float* target, in
     }
     BK(cudaMemcpyAsync(x, b->x_work, sizeof(float) * (size_t)b->n_params, cudaMemcpyDeviceToDevice, st));
     BK(cudaStreamSynchronize(st));
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     return PERF_OK;
 }
 
