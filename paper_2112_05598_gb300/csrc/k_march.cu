@@ -706,6 +706,11 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) 
     }
 }
 
+// The coefficient-cached A p of one lane's ray: J p, then the scatter of
+// J^T (J p).  Splitting the two halves into two launches, with v = J p of
+// every ray stored in between, measured slower on GB300 (102-113 against
+// 95.4 ms per launch at 128^3): the scatter half needs as many registers as
+// the fused kernel, and one warp's J p no longer overlaps another's scatter.
 // BRICK: p and A p are in the block order of sc's LayoutKey (else canonical).
 template <typename TP, bool COUNT = false, bool BRICK = false>
 __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __restrict__ p,
