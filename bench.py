@@ -160,6 +160,8 @@ def parse():
     ap.add_argument("--hier", action="store_true", help="hierarchical vs single-level study")
     ap.add_argument("--hier-steps", type=int, default=30)
     ap.add_argument("--hier-pcg", type=int, default=3)
+    ap.add_argument("--hier-levels", type=int, default=3,
+                    help="levels of the coarse-to-fine study (the first at G / 2^(levels-1))")
     ap.add_argument("--lpc-scenes", type=int, default=100)
     ap.add_argument("--lpc-steps", type=int, default=20)
     ap.add_argument("--lpc-epochs", type=int, default=2)
@@ -548,8 +550,9 @@ def run_lpc(args, rank, world, local):
 
 def run_hier(args, rank, world, local):
     """Hierarchical formulation vs a single level: the coarse-to-fine driver
-    (3 levels, 32^3 -> 64^3 -> 128^3 with maps doubling to the workload's
-    size, --hier-steps Gauss-Newton steps per level, random colours with low
+    (--hier-levels levels, by default 3: 32^3 -> 64^3 -> 128^3 with maps
+    doubling to the workload's size, --hier-steps Gauss-Newton steps per
+    level, random colours with low
     opacity at the first level) against Gauss-Newton at the final resolution
     from the workload's constant start, both with --hier-pcg fixed PCG
     iterations per step; held-out-view PSNR against wall-clock time."""
@@ -563,7 +566,7 @@ def run_hier(args, rank, world, local):
         return
     dev = torch.device("cuda", local)
     sc = make_scene(args.workload, n_cams=args.cams)
-    levels = 3
+    levels = args.hier_levels
     G0, He0, We0 = sc.G >> (levels - 1), sc.env_h >> (levels - 1), sc.env_w >> (levels - 1)
     S = len(sc.radii)
     ctx = Context.from_scene(sc)
