@@ -331,8 +331,10 @@ perf_status perf_adam_step(perf_ctx* ctx, float* x, const void* target, float* m
  * paired records that perf_gn_solve uses by default and keeps the separate
  * arrays only when 3% faster.  When the coefficient store fits its budget it
  * instead lays the store out for every tile shape, fills it at x and times
- * the coefficient-cached A p over the CTA caps (same 3% rule).  Reports the
- * choice in *out (HOST, may be NULL).  Uses the PCG workspace; synchronises. */
+ * the coefficient-cached A p over the CTA caps and, at each shape's best cap,
+ * in the 4^3 and 8^3 brick orders of perf_set_brick where G allows (same 3%
+ * rule; it sets the brick order too).  Reports the choice in *out (HOST, may
+ * be NULL).  Uses the PCG workspace; synchronises. */
 perf_status perf_autotune(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
                           void* stream);
 perf_status perf_set_lpc(perf_ctx* ctx, perf_lpc* lpc);
@@ -461,7 +463,9 @@ perf_status perf_batch_residual(perf_batch* b, const float* x, const float* targ
 /* Times the A p launch at x over tile shapes 8x4, 4x8, 16x2, 32x1 and CTA caps
  * {all, 3, 2}, keeps the fastest (used by every later launch) and reports it
  * in *out (HOST, may be NULL); with the coefficient store (when it fits) the
- * coefficient-cached A p is timed, its store filled at x.  Synchronises. */
+ * coefficient-cached A p is timed, its store filled at x, and at each tile
+ * shape's best cap also in the 4^3 and 8^3 brick orders (perf_batch_set_brick;
+ * scenes whose G the edge does not divide stay canonical).  Synchronises. */
 perf_status perf_batch_autotune(perf_batch* b, const float* x, perf_tuning* out, void* stream);
 /* The coefficient store of perf_set_coef_budget for a batch (rows over the
  * batch's global pixel-tile list; perf_batch_gn_solve's diagonal march fills
