@@ -987,6 +987,17 @@ def run_ours(args, rank, world, local):
             "bytes_per_launch": design, "ratio_to_compulsory": design / compulsory,
             "achieved": design / apply_s / 1e9, "unit": "GB/s",
             "hbm_frac": design / apply_s / 1e9 / hbm_peak}
+    # the scope's labelled "effective gather bandwidth": per sample the 8
+    # corner blocks of p gathered by J p and the 8 corner contributions the
+    # J^T sweep scatters (before the window merges them), over the launch
+    # time -- served by L1 and L2, not HBM
+    pb = 8 if bf else 16
+    eff = (8 * pb + 8 * 16) * samples
+    roof["effective_gather"] = {"what": "algorithmic gather + scatter bytes (8 corners of p "
+                                        "and 8 corner contributions of A p per sample), served "
+                                        "by L1/L2: not HBM traffic",
+                                "bytes_per_launch": eff, "achieved": eff / apply_s / 1e9,
+                                "unit": "GB/s"}
     # the scatter's 16-byte vector atomics, one lane operation per active lane
     red_rate = red_per_apply / apply_s
     roof["atomics"] = {"lane_ops_per_apply": red_per_apply, "achieved": red_rate,
