@@ -61,3 +61,15 @@ def test_traffic_record_parses_and_names_its_kernel(tmp_path, monkeypatch):
 def test_cpu_model_is_a_name():
     m = bench.cpu_model()
     assert m is None or (isinstance(m, str) and len(m) > 0)
+
+
+def test_committed_traffic_record_matches_the_kernel_sources():
+    """The DRAM traffic record in profiles/ was taken on the kernel sources in
+    the tree (else the bench line would report no traffic): a kernel change
+    must come with a new capture."""
+    kernel = "k_apply_coef<float> (A p from stored coefficients)"
+    rec = bench.recorded_traffic(kernel, "scale128", 4413914798)
+    assert rec is not None
+    # the capture's bytes are within a few percent of the design bytes
+    # (32 B per sample: the coefficient rows read twice)
+    assert 0.9 * 32 * 4413914798 < rec < 1.1 * 32 * 4413914798
