@@ -270,12 +270,13 @@ def test_judges_of_the_learned_step():
         if pc == PERF_PRECOND_BLOCK4:
             ctx.set_lpc(net)
         xd = cuda_tensor(sc.x0.copy())
-        st = ctx.gn_solve(xd, target, 2)
+        st = ctx.gn_solve(xd, target, 1)
         assert all(s["accepted"] for s in st)
         out[name] = (host(xd), [s["precond_fallback"] for s in st])
-    print({k: v[1] for k, v in out.items()})
-    assert rel_l2(out["objective"][0], out["jacobi"][0]) < 5e-2
-    assert rel_l2(out["residual"][0], out["jacobi"][0]) < 5e-2
+    d_obj = rel_l2(out["objective"][0], out["jacobi"][0])
+    d_res = rel_l2(out["residual"][0], out["jacobi"][0])
+    print({k: v[1] for k, v in out.items()}, f"x vs Jacobi: {d_obj:.3e} / {d_res:.3e}")
+    assert d_obj < 5e-2 and d_res < 5e-2
     assert not any(out["objective"][1])
     with pytest.raises(PerfError):
         Context.from_scene(sc, precond_judge=2)
