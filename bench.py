@@ -1054,7 +1054,8 @@ def run_ours(args, rank, world, local):
     }
     if not args.no_cpu_baseline and world == 1 and args.cams is None:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_cams, cfg.pcg_iters)
-    if not args.no_lpc_record and world == 1 and args.cams is None:
+    if (not args.no_lpc_record and world == 1 and args.cams is None and args.workload == WORKLOAD
+            and not bf):
         # the time-to-PSNR half of the metric: learned vs Jacobi on the reduced
         # ring workload (outside every timed region above)
         del ctx, target, x, x_host, t_host, x_dev, t_dev
