@@ -528,7 +528,14 @@ def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train
                          "train_s": t_train, "held_out_probe_loss_identity": loss0,
                          "held_out_probe_loss_trained": loss1},
             "first_system_pcg": first,
-            "gn": gn}
+            "gn": gn,
+            # time to Jacobi's final PSNR - 0.1 dB, learned over Jacobi (< 1: the
+            # learned preconditioner is faster), per regime and judge
+            "summary": {reg: {name: (g["time_to_psnr_s"][name] / g["time_to_psnr_s"]["jacobi"]
+                                     if g["time_to_psnr_s"].get(name) and
+                                     g["time_to_psnr_s"].get("jacobi") else None)
+                              for name in ("learned", "learned_objective_judge", "block_jacobi")}
+                        for reg, g in gn.items()}}
 
 
 def run_lpc(args, rank, world, local):
