@@ -73,3 +73,12 @@ def test_committed_traffic_record_matches_the_kernel_sources():
     # the capture's bytes are within a few percent of the design bytes
     # (32 B per sample: the coefficient rows read twice)
     assert 0.9 * 32 * 4413914798 < rec < 1.1 * 32 * 4413914798
+
+
+def test_lpc_summary_ratios():
+    gn = {"paper": {"time_to_psnr_s": {"jacobi": 2.0, "learned": 1.0, "block_jacobi": None,
+                                       "learned_objective_judge": 0.5}},
+          "fixed2": {"time_to_psnr_s": {"jacobi": 4.0, "learned": 5.0}}}
+    s = bench.lpc_summary(gn)
+    assert s["paper"] == {"learned": 0.5, "block_jacobi": None, "learned_objective_judge": 0.25}
+    assert s["fixed2"] == {"learned": 1.25}
