@@ -1073,7 +1073,7 @@ def run_ours(args, rank, world, local):
         # ring workload (outside every timed region above)
         del ctx, target, x, x_host, t_host, x_dev, t_dev
         torch.cuda.empty_cache()
-        line["lpc"] = lpc_study(dev, "ring128", train_small=60, train_steps=10, train_large=6,
+        line["lpc"] = lpc_study(dev, "ring128", train_small=100, train_steps=20, train_large=8,
                                 gn_steps=40, pcg_per_step=2, traj_iters=1200)
     print(json.dumps(line), flush=True)
 
