@@ -179,3 +179,30 @@ def test_batch_brick_against_oracle():
             assert_params(xa[sl], ref.x, ref.diag, TOL_GN, what=f"batch brick scene {i} (G={s['G']})")
             checked += 1
     assert checked >= 2
+
+
+@pytest.mark.parametrize("G, edge", [(2, 2), (6, 2), (8, 8)])
+def test_brick_small_grids(G, edge):
+    """Small grids in brick order (a single brick, a grid of three bricks per
+    edge, one brick of 8^3) on a ragged image with rays that miss the grid:
+    one Gauss-Newton step against the oracle."""
+    from conftest import tiny_problem
+    from gpu_common import make_pair
+    from oracle import gn_step
+    rng = np.random.default_rng(40 + G)
+    # cameras at radius 6: the grid spans about 32 of the 40 degrees, so
+    # the image's edge rays miss it
+    prob = tiny_problem(rng, G=G, n_cams=3, res=13, radii=(2.5, 8.0), env_h=4, env_w=8,
+                        cam_radius=6.0)
+    ctx, orc = make_pair(prob["G"], prob["radii"], 4, 8, prob["c2w"], prob["focal"], 13, 13,
+                         pcg_iters=3, pcg_fixed=1)
+    ctx.set_brick(edge)
+    x = prob["x"].astype(np.float32)
+    target = orc.render(rng.uniform(0, 1, size=x.shape))[0].astype(np.float32).ravel()
+    xd = cuda_tensor(x.copy())
+    st = ctx.gn_solve(xd, cuda_tensor(target), 1)[0]
+    assert ctx.coef_info()["used"]
+    ref = gn_step(orc, x.astype(np.float64), target, 3)
+    assert st["accepted"] == ref.accepted
+    if abs(st["gamma"] - ref.gamma) <= 1e-9:
+        assert_params(host(xd), ref.x, ref.diag, TOL_GN, what=f"brick {edge} on {G}^3")
