@@ -302,6 +302,14 @@ perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes);
  * block-Jacobi); otherwise that step is canonical.  x, the targets and every
  * per-call entry point stay canonical.  perf_autotune sets it. */
 perf_status perf_set_brick(perf_ctx* ctx, int32_t edge);
+/* With on = 1 (the default), perf_gn_solve runs a fixed-iteration PCG
+ * (opts.pcg_fixed, pcg_iters > 1, kernel timing off) as one CUDA graph:
+ * captured on a stream of the context, replayed on the caller's stream, and
+ * captured again whenever the scene descriptor, the iteration count, the
+ * preconditioner or a workspace buffer it uses changes.  Small scenes are
+ * bound by kernel launches; the graph issues the loop at once.  on = 0
+ * launches every kernel from the host. */
+perf_status perf_set_pcg_graph(perf_ctx* ctx, int32_t on);
 perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
                            double* coverage);
 /* Residual history of the context's last PCG solve (perf_pcg_begin /

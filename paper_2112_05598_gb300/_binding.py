@@ -107,6 +107,7 @@ _SIGS = {
     "perf_autotune": [_VP, _VP, _VP, ctypes.POINTER(Tuning), _VP],
     "perf_set_coef_budget": [_VP, ctypes.c_int64],
     "perf_set_brick": [_VP, ctypes.c_int32],
+    "perf_set_pcg_graph": [_VP, ctypes.c_int32],
     "perf_pcg_history": [_VP, _VP, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)],
     "perf_adam_step": [_VP, _VP, _VP, _VP, _VP, ctypes.c_int32, ctypes.c_float, ctypes.c_float,
                        ctypes.c_float, ctypes.c_float, _VP, _VP],
@@ -421,6 +422,10 @@ class Context:
         """Block order of a Gauss-Newton step's PCG vectors: 1 canonical, 2, 4
         or 8 voxels per brick edge (perf_set_brick)."""
         self._check(self.lib.perf_set_brick(self.h, int(edge)), "set_brick")
+
+    def set_pcg_graph(self, on=True):
+        """Replay a fixed-iteration PCG loop from a CUDA graph (default on)."""
+        self._check(self.lib.perf_set_pcg_graph(self.h, int(bool(on))), "set_pcg_graph")
 
     def coef_info(self):
         b = ctypes.c_int64(0)

@@ -49,6 +49,14 @@ struct perf_ctx {
     // brick order of a Gauss-Newton step's PCG vectors (LayoutKey shift; 0:
     // canonical), used when the step's A p runs wholly from the store
     int brick_s = 0;
+    // the fixed-iteration PCG loop of perf_gn_solve as a CUDA graph, captured
+    // on an internal stream and replayed on the caller's while everything it
+    // captured (the key: pointers, scene descriptor, iteration count) holds
+    bool pcg_graph_on = true;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t pcg_graph = nullptr;
+    std::vector<unsigned char> pcg_graph_key;
+    unsigned long long pcg_graph_launches = 0;   // kernels per replay
     // coefficient-cached A p: per-sample (w_i, dH/dsigma_i) of the current
     // Gauss-Newton step, stored by its diagonal march (see k_march.cu)
     long long coef_budget = -1;        // bytes; -1 automatic, 0 off
@@ -430,6 +438,8 @@ perf_status perf_destroy(perf_ctx* ctx) {
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->pcg_graph) cudaGraphExecDestroy(ctx->pcg_graph);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (auto& t : ctx->kt)
         for (auto& pr : t.ev) {
             cudaEventDestroy(pr.first);
@@ -607,6 +617,60 @@ perf_status pcg_iter(perf_ctx* ctx, const void* x, const float* diag, const floa
     return PERF_OK;
 }
 
+template <typename T>
+void key_add(std::vector<unsigned char>& k, const T& v) {
+    const unsigned char* b = reinterpret_cast<const unsigned char*>(&v);
+    k.insert(k.end(), b, b + sizeof(T));
+}
+
+// iters fixed iterations of pcg_iter replayed from a CUDA graph on st
+// (captured on the context's own stream; recaptured when its key changes).
+perf_status pcg_graph_run(perf_ctx* ctx, const void* x, const float* B, bool paired, bool coef,
+                          const perf::DevScene& d, int iters, cudaStream_t st) {
+    std::vector<unsigned char> key;
+    key_add(key, iters);
+    key_add(key, paired);
+    key_add(key, coef);
+    key_add(key, x);
+    key_add(key, B);
+    key_add(key, ctx->n_block);
+    key_add(key, d);
+    const void* ptrs[] = {ctx->coef, ctx->tile_off, ctx->xp, ctx->p, ctx->p16, ctx->Ap,
+                          ctx->delta, ctx->rho, ctx->diag, ctx->s};
+    key_add(key, ptrs);
+    key_add(key, ctx->coef_tiles);
+    if (!ctx->pcg_graph || key != ctx->pcg_graph_key) {
+        if (ctx->pcg_graph) {
+            cudaGraphExecDestroy(ctx->pcg_graph);
+            ctx->pcg_graph = nullptr;
+        }
+        if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+        const unsigned long long n0 = perf_launch_count();
+        CK(cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal));
+        perf_status ps = PERF_OK;
+        for (int k = 0; k < iters && ps == PERF_OK; ++k)
+            ps = pcg_iter(ctx, x, ctx->diag, B, ctx->cap_stream, paired, coef, &d);
+        cudaGraph_t g = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(ctx->cap_stream, &g);
+        if (ps != PERF_OK || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return ps != PERF_OK ? ps : cuda_fail(ctx, e, "PCG graph capture");
+        }
+        const cudaError_t ei = cudaGraphInstantiate(&ctx->pcg_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            ctx->pcg_graph = nullptr;
+            return cuda_fail(ctx, ei, "PCG graph instantiate");
+        }
+        ctx->pcg_graph_key = key;
+        ctx->pcg_graph_launches = perf_launch_count() - n0;
+        perf::count_launch(0ull - ctx->pcg_graph_launches);   // counted when replayed
+    }
+    CK(cudaGraphLaunch(ctx->pcg_graph, st));
+    perf::count_launch(ctx->pcg_graph_launches);
+    return PERF_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -752,14 +816,20 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
                                           ctx->p16, ctx->Ap, ctx->s, o.pcg_iters, o.pcg_fixed,
                                           o.pcg_eps_rel, o.pcg_stall, B, nB, st,
                                           paired ? ctx->xp : nullptr, ctx->hist, ctx->hist_cap));
-                for (int k = 0; k < o.pcg_iters; ++k) {
-                    ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired, use_coef, &dl);
+                if (o.pcg_fixed && ctx->pcg_graph_on && !ctx->timing && o.pcg_iters > 1) {
+                    // launch-bound on small scenes: one graph for the whole loop
+                    ps = pcg_graph_run(ctx, xm, B, paired, use_coef, dl, o.pcg_iters, st);
                     if (ps != PERF_OK) return ps;
-                    if (!o.pcg_fixed) {
-                        int done = 0;
-                        CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
-                        CK(cudaStreamSynchronize(st));
-                        if (done) break;
+                } else {
+                    for (int k = 0; k < o.pcg_iters; ++k) {
+                        ps = pcg_iter(ctx, xm, ctx->diag, B, st, paired, use_coef, &dl);
+                        if (ps != PERF_OK) return ps;
+                        if (!o.pcg_fixed) {
+                            int done = 0;
+                            CK(cudaMemcpyAsync(&done, &ctx->s->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+                            CK(cudaStreamSynchronize(st));
+                            if (done) break;
+                        }
                     }
                 }
                 if (!(o.precond == PERF_PRECOND_BLOCK4 && blk) || B == nullptr) break;
@@ -1117,6 +1187,12 @@ perf_status perf_pcg_history(perf_ctx* ctx, double* R_out, int32_t cap, int32_t*
     const long long k = std::min<long long>(std::min<long long>(h.iter, ctx->hist_cap), cap);
     if (k > 0) CK(cudaMemcpy(R_out, ctx->hist, sizeof(double) * (size_t)k, cudaMemcpyDeviceToHost));
     *count_out = (int32_t)k;
+    return PERF_OK;
+}
+
+perf_status perf_set_pcg_graph(perf_ctx* ctx, int32_t on) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    ctx->pcg_graph_on = on != 0;
     return PERF_OK;
 }
 
