@@ -54,25 +54,25 @@ def test_graph_recaptured_when_the_step_changes(s32):
 
 
 def test_graph_equals_host_launched_loop(s32):
-    """Five steps of 20 PCG iterations (the 32^3 configuration) with the loop
-    replayed and launched from the host: the same objective after each step
-    and the same parameters (up to the order of the atomic sums), and the
-    replayed steps take less device time."""
+    """Three steps of 3 PCG iterations with the loop replayed and launched
+    from the host: the same objective after each step and the same
+    parameters, to the bars of the oracle comparisons (3 iterations determine
+    the step; at 20, CG amplifies the rounding of the atomic sums, as pinned
+    on the oracle itself).  The device time per step of the 32^3
+    configuration (20 iterations) is printed for both."""
     sc, orc, target = s32
     from paper_2112_05598_gb300 import Context
     out = {}
     for graph in (True, False):
-        ctx = Context.from_scene(sc, pcg_iters=20, pcg_fixed=1)
+        ctx = Context.from_scene(sc, pcg_iters=3, pcg_fixed=1)
         ctx.set_pcg_graph(graph)
         xd = cuda_tensor(sc.x0.copy())
-        st = ctx.gn_solve(xd, cuda_tensor(target), 5)
-        out[graph] = (host(xd), [s["F_after"] for s in st], [s["ms"] for s in st])
-    print(f"[graph] ms per step replayed {np.median(out[True][2]):.3f}, "
-          f"host-launched {np.median(out[False][2]):.3f}; x rel L2 "
-          f"{rel_l2(out[True][0], out[False][0]):.3e}")
-    # 20 CG iterations amplify the rounding of the atomic sums along weakly
-    # observed directions (pinned on the oracle itself); the objective after
-    # each step is what they determine
+        st = ctx.gn_solve(xd, cuda_tensor(target), 3)
+        out[graph] = (host(xd), [s["F_after"] for s in st])
+        ctx.set_options(pcg_iters=20)
+        x2 = cuda_tensor(sc.x0.copy())
+        ms = [s["ms"] for s in ctx.gn_solve(x2, cuda_tensor(target), 5)]
+        print(f"[graph] replayed={graph}: device ms per 20-iteration step {np.median(ms):.3f}")
     for a, b in zip(out[True][1], out[False][1]):
-        assert abs(a - b) <= 1e-3 * b
-    assert rel_l2(out[True][0], out[False][0]) < 5e-2
+        assert abs(a - b) <= TOL_FP32 * b
+    assert rel_l2(out[True][0], out[False][0]) < TOL_GN
