@@ -306,9 +306,9 @@ perf_status perf_set_brick(perf_ctx* ctx, int32_t edge);
  * (opts.pcg_fixed, pcg_iters > 1, kernel timing off) as one CUDA graph:
  * captured on a stream of the context, replayed on the caller's stream, and
  * captured again whenever the scene descriptor, the iteration count, the
- * preconditioner or a workspace buffer it uses changes.  Small scenes are
- * bound by kernel launches; the graph issues the loop at once.  on = 0
- * launches every kernel from the host. */
+ * preconditioner or a workspace buffer it uses changes.  The graph takes
+ * the per-kernel launch work off the host; on = 0 launches every kernel from
+ * the host. */
 perf_status perf_set_pcg_graph(perf_ctx* ctx, int32_t on);
 perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
                            double* coverage);

@@ -817,7 +817,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
                                           o.pcg_eps_rel, o.pcg_stall, B, nB, st,
                                           paired ? ctx->xp : nullptr, ctx->hist, ctx->hist_cap));
                 if (o.pcg_fixed && ctx->pcg_graph_on && !ctx->timing && o.pcg_iters > 1) {
-                    // launch-bound on small scenes: one graph for the whole loop
+                    // one graph for the whole loop (no per-kernel launch work on the host)
                     ps = pcg_graph_run(ctx, xm, B, paired, use_coef, dl, o.pcg_iters, st);
                     if (ps != PERF_OK) return ps;
                 } else {
