@@ -397,13 +397,13 @@ def run_conv(args, rank, world, local):
 
 
 def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train_large=8,
-              epochs=2, gn_steps=20, pcg_per_step=5, traj_iters=300, seed=7):
+              epochs=2, gn_steps=20, pcg_per_step=5, traj_iters=300, seed=7, train_pcg=5):
     """Learned block preconditioner vs Jacobi (and exact block-Jacobi).
 
     Training: the network learns from Gauss-Newton systems the solver logs on
-    its own runs -- train_small seeded 32^3 scenes (train_steps steps each) and
-    train_large systems of the 128^3 workload restricted to 8 cameras -- with
-    the library's BF16 kernels.  Evaluation on `workload`: (a) the first
+    its own runs (train_pcg fixed PCG iterations per step) -- train_small
+    seeded 32^3 scenes (train_steps steps each) and train_large systems of the
+    128^3 workload restricted to 8 cameras -- with the library's BF16 kernels.  Evaluation on `workload`: (a) the first
     Gauss-Newton system's PCG through the solver's own path (coefficient
     store) until a relative residual of 1e-3 or traj_iters iterations: the
     residual history and the iterations to 1e-1, 1e-2, 1e-3; (b) gn_steps
@@ -423,7 +423,7 @@ def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train
     systems = []
     for k in range(train_small):
         sc = make_scene("small32", seed=2000 + k)
-        ctx = Context.from_scene(sc, pcg_iters=5, pcg_fixed=1)
+        ctx = Context.from_scene(sc, pcg_iters=train_pcg, pcg_fixed=1)
         target = torch.empty(3 * ctx.n_rays, device=dev)
         ctx.render(torch.from_numpy(sc.x_gt).to(dev), target)
         x = torch.from_numpy(sc.x0.copy()).to(dev)
@@ -433,7 +433,7 @@ def lpc_study(dev, workload, n_cams=None, train_small=100, train_steps=20, train
         ctx.close()
     if train_large > 0:
         sc = make_scene("scale128", n_cams=8)
-        ctx = Context.from_scene(sc, pcg_iters=5, pcg_fixed=1)
+        ctx = Context.from_scene(sc, pcg_iters=train_pcg, pcg_fixed=1)
         target = torch.empty(3 * ctx.n_rays, device=dev)
         ctx.render(torch.from_numpy(sc.x_gt).to(dev), target)
         x = torch.from_numpy(sc.x0.copy()).to(dev)
@@ -1074,7 +1074,7 @@ def run_ours(args, rank, world, local):
         del ctx, target, x, x_host, t_host, x_dev, t_dev
         torch.cuda.empty_cache()
         line["lpc"] = lpc_study(dev, "ring128", train_small=100, train_steps=20, train_large=8,
-                                gn_steps=40, pcg_per_step=2, traj_iters=1200)
+                                gn_steps=40, pcg_per_step=2, traj_iters=1200, train_pcg=2)
     print(json.dumps(line), flush=True)
 
 
