@@ -153,6 +153,9 @@ def parse():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16"])
     ap.add_argument("--cams", type=int, default=None, help="first N cameras only (profiling)")
+    ap.add_argument("--grid", type=int, default=None,
+                    help="grid resolution G in place of the workload's (sample cap 2 G, as in the "
+                         "workloads: about the grid's diagonal in steps of 2/G)")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-cams", type=int, default=16)
@@ -313,7 +316,7 @@ def run_reference(args, rank, world):
     from scenegen import make_scene
     if rank != 0:
         return
-    sc = make_scene(args.workload)
+    sc = make_scene(_scene_config(args))
     vals = []
     for _ in range(args.warmup + args.steps):
         vals.append(cpu_baseline(sc, args.cpu_cams, sc.cfg.pcg_iters))
@@ -328,6 +331,17 @@ def run_reference(args, rank, world):
                              "cpu": cpu_model(), "kind": "oracle", "sample": timed[0]["sample"]},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def _scene_config(args):
+    """The workload's scene configuration, at --grid G if given (sample cap
+    2 G, the workloads' own ratio)."""
+    import dataclasses
+    from scenegen import CONFIGS
+    cfg = CONFIGS[args.workload]
+    if args.grid is not None:
+        cfg = dataclasses.replace(cfg, G=args.grid, max_samples=2 * args.grid)
+    return cfg
 
 
 def _workload_desc(sc):
@@ -865,7 +879,7 @@ def run_ours(args, rank, world, local):
     from scenegen import make_scene
 
     from paper_2112_05598_gb300 import PERF_BF16, PERF_F32
-    sc = make_scene(args.workload, n_cams=args.cams)
+    sc = make_scene(_scene_config(args), n_cams=args.cams)
     cfg = sc.cfg
     dev = torch.device("cuda", local)
     bf = args.dtype == "bf16"
@@ -984,7 +998,7 @@ def run_ours(args, rank, world, local):
                            f"(max SM clock, {peak_src})",
             "kernel": apply_kernel,
             "traffic": recorded_traffic(apply_kernel, args.workload, samples)
-            if args.cams is None else None,
+            if args.cams is None and args.grid is None else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 4-camera "
                               "capture, scaled by samples (profiles/apply_coef_traffic_scale128.md)",
             "impl_flop_per_sample": impl_flop,
@@ -1050,6 +1064,7 @@ def run_ours(args, rank, world, local):
                    "n_params": sc.n_params, "n_rays": sc.n_rays,
                    "samples_per_march": samples, "tuning": tuning,
                    "coef_store_bytes": ctx.coef_info()["bytes"],
+                   "coef_coverage": ctx.coef_info()["coverage"],
                    "l2": "inputs larger than L2: targets and residuals 768 MB each per step"},
         "gpu_launches": int(launches),
         "rays_per_s": 2.0 * sc.n_rays * pcg_total / (ms / 1000.0),
@@ -1068,7 +1083,7 @@ def run_ours(args, rank, world, local):
     if not args.no_cpu_baseline and world == 1 and args.cams is None:
         line["cpu_baseline"] = cpu_baseline(sc, args.cpu_cams, cfg.pcg_iters)
     if (not args.no_lpc_record and world == 1 and args.cams is None and args.workload == WORKLOAD
-            and not bf):
+            and args.grid is None and not bf):
         # the time-to-PSNR half of the metric: learned vs Jacobi on the reduced
         # ring workload (outside every timed region above)
         del ctx, target, x, x_host, t_host, x_dev, t_dev
