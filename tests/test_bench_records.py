@@ -82,3 +82,19 @@ def test_lpc_summary_ratios():
     s = bench.lpc_summary(gn)
     assert s["paper"] == {"learned": 0.5, "block_jacobi": None, "learned_objective_judge": 0.25}
     assert s["fixed2"] == {"learned": 1.25}
+
+
+def test_grid_option_scales_the_sample_cap():
+    """--grid G keeps the workload's cameras and shells and sets the sample
+    cap to 2 G, the ratio every grid workload uses (a ray crosses at most
+    sqrt(3) G steps of 2/G)."""
+    import argparse
+    from scenegen import CONFIGS
+    for name in ("scale128", "bf16_256", "small32"):
+        assert CONFIGS[name].max_samples == 2 * CONFIGS[name].G
+    base = bench._scene_config(argparse.Namespace(workload="scale128", grid=None))
+    assert base == CONFIGS["scale128"]
+    big = bench._scene_config(argparse.Namespace(workload="scale128", grid=512))
+    assert (big.G, big.max_samples) == (512, 1024)
+    assert (big.n_cams, big.width, big.radii, big.seed) == (base.n_cams, base.width, base.radii,
+                                                           base.seed)
