@@ -99,11 +99,13 @@ def kernel_source_hash():
     return h.hexdigest()
 
 
-def recorded_traffic(kernel, workload, samples):
+def recorded_traffic(kernel, workload, samples, rows_read=1.0):
     """DRAM bytes per launch of `kernel` on `workload` with `samples` ray-march
-    samples: the recorded capture's bytes scaled by samples / its samples
-    (the coefficient stream, which dominates, is proportional to samples).
-    None when the record is missing or was taken on other kernel sources."""
+    samples of which the fraction `rows_read` is streamed from the store
+    (each ray's non-zero prefix): the recorded capture's bytes scaled by the
+    rows streamed over the capture's (the coefficient stream, which
+    dominates, is proportional to them).  None when the record is missing or
+    was taken on other kernel sources."""
     try:
         with open(TRAFFIC_PROFILE) as fh:
             kv = {}
@@ -118,10 +120,10 @@ def recorded_traffic(kernel, workload, samples):
         return None
     try:
         dram = int(kv["dram_bytes_per_launch"])
-        cap = int(kv["samples_per_launch"])
+        cap = int(kv["samples_per_launch"]) * float(kv.get("rows_read_fraction", "1.0"))
     except (KeyError, ValueError):
         return None
-    return int(round(dram * samples / cap)) if cap > 0 else None
+    return int(round(dram * samples * rows_read / cap)) if cap > 0 else None
 
 
 def cpu_model():
@@ -870,6 +872,17 @@ def run_batch(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def rows_read_fraction(ctx):
+    """The share of the store's grid-sample rows the last Gauss-Newton step's
+    A p read (perf_coef_prefix); None without a filled store."""
+    from paper_2112_05598_gb300 import PerfError
+    try:
+        pre = ctx.coef_prefix()
+    except PerfError:
+        return None
+    return pre["read"] / pre["total"] if pre["total"] else None
+
+
 def count_lane_ops(ctx, x, target, pcg_iters):
     """Vector-atomic lane operations per A p of the Jacobian-transpose
     scatter, counted (perf_set_atomic_counter, the counting instantiation of
@@ -918,6 +931,7 @@ def run_ours(args, rank, world, local):
     # (before the tuner, which rebuilds the shell hits that changing the
     # options invalidates)
     red_before = count_lane_ops(ctx, x, target, cfg.pcg_iters)
+    prefix_before = rows_read_fraction(ctx)
     # tile shape / CTA cap tuned at the warmed-up state along a random direction
     gp = torch.Generator(device=dev).manual_seed(0)
     probe = torch.randn(sc.n_params, device=dev, generator=gp).to(sdt)
@@ -952,6 +966,11 @@ def run_ours(args, rank, world, local):
     tm = ctx.timing(reset=True)
     ctx.enable_timing(False)
     coef_timed = ctx.coef_info()
+    # grid-sample rows the A p reads from the store (each ray's non-zero
+    # prefix) over the store's grid samples, before and after the timed steps
+    prefix_after = rows_read_fraction(ctx)
+    rows_read = ([prefix_before, prefix_after] if prefix_before is not None
+                 and prefix_after is not None else None)
 
     # end to end through the public API with host buffers
     e2e_steps = args.e2e_steps or args.steps
@@ -1020,20 +1039,26 @@ def run_ours(args, rank, world, local):
             "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
                            f"(max SM clock, {peak_src})",
             "kernel": apply_kernel,
-            "traffic": recorded_traffic(apply_kernel, args.workload, samples)
+            "traffic": recorded_traffic(apply_kernel, args.workload, samples,
+                                        0.5 * sum(rows_read) if rows_read else 1.0)
             if args.cams is None and args.grid is None else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 4-camera "
-                              "capture, scaled by samples (profiles/apply_coef_traffic_scale128.md)",
+                              "capture, scaled by the store rows streamed: samples x the mean "
+                              "of the rows-read fractions before and after the timed steps "
+                              "(profiles/apply_coef_traffic_scale128.md)",
             "impl_flop_per_sample": impl_flop,
             "impl_alu_frac": impl_flop * samples / apply_s / 1e12 / fp32_peak,
             "compulsory_bytes_per_launch": compulsory,
             "hbm_frac_compulsory": compulsory / apply_s / 1e9 / hbm_peak}
     if coef:
-        design = COEF_BYTES_PER_SAMPLE * samples + ((2 if bf else 4) + 4) * sc.n_params
+        rf = 0.5 * sum(rows_read) if rows_read else 1.0
+        design = int(COEF_BYTES_PER_SAMPLE * samples * rf) + ((2 if bf else 4) + 4) * sc.n_params
         roof["design_traffic"] = {
-            "what": "coefficient store: 16 B per sample or shell hit streamed twice per A p, "
-                    "plus p read and A p written once (an implementation choice that trades "
-                    "HBM capacity for recomputation, not the method's compulsory bytes)",
+            "what": "coefficient store: 16 B per sample or shell hit streamed twice per A p "
+                    "(the rows each ray's non-zero prefix holds: samples x the mean rows-read "
+                    "fraction), plus p read and A p written once (an implementation choice "
+                    "that trades HBM capacity for recomputation, not the method's compulsory "
+                    "bytes)",
             "bytes_per_launch": design, "ratio_to_compulsory": design / compulsory,
             "achieved": design / apply_s / 1e9, "unit": "GB/s",
             "hbm_frac": design / apply_s / 1e9 / hbm_peak}
@@ -1095,6 +1120,7 @@ def run_ours(args, rank, world, local):
                    "samples_per_march": samples, "tuning": tuning,
                    "coef_store_bytes": coef_timed["bytes"],
                    "coef_coverage": cov,
+                   "coef_rows_read_before_after": rows_read,
                    "l2": "inputs larger than L2: targets and residuals 768 MB each per step"},
         "gpu_launches": int(launches),
         "rays_per_s": 2.0 * sc.n_rays * pcg_total / (ms / 1000.0),

@@ -284,11 +284,21 @@ perf_status perf_pcg_set_blocks(perf_ctx* ctx, const float* blocks, int64_t n_bl
  * longest prefix of pixel tiles that fits the budget (bytes = -1, default:
  * the free device memory minus 6 GiB at the time of the step; 0: never --
  * marches recompute everything, the store is freed; > 0: at most that many
- * bytes); the A p of the remaining tiles is recomputed.  The per-call entry
- * points (perf_apply_normal, perf_pcg_step) always recompute.
- * perf_coef_info: bytes held by the store, whether the last Gauss-Newton
- * step (or perf_autotune) used it, and the fraction of tiles it covered
- * (HOST pointers, may be NULL). */
+ * bytes; the store's rows and 4 bytes per ray of prefix lengths, below);
+ * the A p of the remaining tiles is recomputed.  A ray's rows past its last
+ * non-zero one (samples whose transmittance has underflowed to 0 in
+ * binary32, where w_i and dH/dsigma_i are exactly 0) are neither written
+ * nor read: the A p adds exactly the same terms.  With the auxiliary
+ * residual and a non-zero per-ray factor every row is kept.  The per-call
+ * entry points (perf_apply_normal, perf_pcg_step) always recompute.
+ * perf_coef_info: bytes held by the store's rows, whether the last
+ * Gauss-Newton step (or perf_autotune) used it, and the fraction of tiles
+ * it covered (HOST pointers, may be NULL).
+ * perf_coef_prefix: after a perf_gn_solve step that used the store, the
+ * grid-sample rows its A p reads (sum over the store's rays of the non-zero
+ * prefix) and the grid samples of those rays (HOST pointers); synchronises
+ * the stream.  PERF_ERR_INVALID_ARG when the last step did not fill the
+ * store (or the tiling changed since). */
 perf_status perf_set_coef_budget(perf_ctx* ctx, int64_t bytes);
 /* Block order of the vectors a Gauss-Newton step's PCG works on (p, A p, the
  * Jacobi diagonal, the gradient, Delta, rho; an implementation choice the
@@ -312,6 +322,8 @@ perf_status perf_set_brick(perf_ctx* ctx, int32_t edge);
 perf_status perf_set_pcg_graph(perf_ctx* ctx, int32_t on);
 perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_used,
                            double* coverage);
+perf_status perf_coef_prefix(perf_ctx* ctx, int64_t* rows_read, int64_t* rows_total,
+                             void* stream);
 /* Residual history of the context's last PCG solve (perf_pcg_begin /
  * perf_pcg_step, or the last Gauss-Newton step of perf_gn_solve):
  * R_out[k - 1] = r_k^T r_k after iteration k (Algorithm 2's R), HOST, at most

@@ -116,6 +116,7 @@ _SIGS = {
     "perf_render_threshold": [_VP, _VP, ctypes.c_float, _VP, _VP, _VP],
     "perf_coef_info": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int32),
                        ctypes.POINTER(ctypes.c_double)],
+    "perf_coef_prefix": [_VP, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64), _VP],
     "perf_set_lpc": [_VP, _VP],
     "perf_diag_cross": [_VP, _VP, _VP, _VP, _VP],
     "perf_lpc_create": [ctypes.POINTER(_VP), ctypes.c_uint64],
@@ -434,6 +435,16 @@ class Context:
         self._check(self.lib.perf_coef_info(self.h, ctypes.byref(b), ctypes.byref(u), ctypes.byref(c)),
                     "coef_info")
         return dict(bytes=int(b.value), used=bool(u.value), coverage=float(c.value))
+
+    def coef_prefix(self, stream=None):
+        """perf_coef_prefix: after a Gauss-Newton step that used the store,
+        the grid-sample rows its A p reads (each ray's non-zero prefix) and
+        the grid samples of the store's rays."""
+        r = ctypes.c_int64(0)
+        t = ctypes.c_int64(0)
+        self._check(self.lib.perf_coef_prefix(self.h, ctypes.byref(r), ctypes.byref(t),
+                                              _stream(stream)), "coef_prefix")
+        return dict(read=int(r.value), total=int(t.value))
 
     def set_lpc(self, lpc):
         self._lpc = lpc

@@ -381,14 +381,19 @@ __device__ __forceinline__ void win_add(Window<NV>& w, const Cell& cl, const flo
 // samples is warp-uniform (sample k of every lane in the same iteration), so
 // coherent rays evict a shared voxel in the same instruction.
 template <int NV, typename T, class Sink>
-__device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __restrict__ x,
-                                               const Ray& R, long long ray, bool act, CSum V,
-                                               const float (&vv)[3], Sink& sk,
-                                               float4* __restrict__ crow = nullptr,
-                                               float aux_v = 0.0f) {
+__device__ __forceinline__ int backward_sweep(const DevScene& sc, const T* __restrict__ x,
+                                              const Ray& R, long long ray, bool act, CSum V,
+                                              const float (&vv)[3], Sink& sk,
+                                              float4* __restrict__ crow = nullptr,
+                                              float aux_v = 0.0f) {
     float G[3] = {0.0f, 0.0f, 0.0f};
     const int Kl = act ? R.K : 0;
     const int Kmax = __reduce_max_sync(kFull, Kl);
+    // kf: 1 + the largest k whose coefficient row is non-zero (0: none yet;
+    // the sweep runs back to front).  With the auxiliary residual's per-sample
+    // term in play (aux_v != 0) every row counts.
+    int kf = (NV == 5 && aux_v != 0.0f) ? Kl : 0;
+    const bool skip_zero_tail = crow != nullptr && sc.keff != nullptr;
     // the auxiliary row's per-ray factor goes to the store's last row
     if (NV == 5 && crow && act) __stcs(crow + (long long)(Kmax + sc.S) * 32,
                                        make_float4(aux_v, 0.0f, 0.0f, 0.0f));
@@ -464,7 +469,9 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
             G[0] = fmaf(wi, a.x, G[0]);
             G[1] = fmaf(wi, a.y, G[1]);
             G[2] = fmaf(wi, a.z, G[2]);
-            if (crow) __stcs(crow + (long long)k * 32, make_float4(wi, ds0, ds1, ds2));
+            if (kf == 0 && (wi != 0.0f || ds0 != 0.0f || ds1 != 0.0f || ds2 != 0.0f)) kf = k + 1;
+            if (crow && (kf > 0 || !skip_zero_tail))
+                __stcs(crow + (long long)k * 32, make_float4(wi, ds0, ds1, ds2));
             float val[NV];
             val[0] = wi;
             if (NV == 2) {
@@ -484,6 +491,7 @@ __device__ __forceinline__ void backward_sweep(const DevScene& sc, const T* __re
         sk.put(Kl > 0, sk.km.key(par_coord(w.b[0], p & 1), par_coord(w.b[1], (p >> 1) & 1),
                                  par_coord(w.b[2], p >> 2)),
                w.v[p]);
+    return kf;
 }
 
 // ------------------------------------------------------------- kernels
@@ -590,12 +598,16 @@ __device__ __forceinline__ void scatter_tile(const DevScene& sc, const T* __rest
     DKey dk;
     if constexpr (LAY) dk = layout_key(sc);
     else dk = CanonKey{sc.G};
-    if (MODE == 2 && sc.aux) {
-        DiagSink<5, DKey> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, dk, va};
-        backward_sweep<5>(sc, x, R, ray, act, V, vr, sk, crow, kap);
-    } else if (MODE == 2) {
-        DiagSink<4, DKey> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, dk, 0.0f};
-        backward_sweep<4>(sc, x, R, ray, act, V, vr, sk, crow);
+    if (MODE == 2) {
+        int kf;
+        if (sc.aux) {
+            DiagSink<5, DKey> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, dk, va};
+            kf = backward_sweep<5>(sc, x, R, ray, act, V, vr, sk, crow, kap);
+        } else {
+            DiagSink<4, DKey> sk{out, out2, out3, vr[0], vr[1], vr[2], sc.n_vox, dk, 0.0f};
+            kf = backward_sweep<4>(sc, x, R, ray, act, V, vr, sk, crow);
+        }
+        if (crow && act && sc.keff) sc.keff[ray] = kf;
     } else {
         VjpSink<CanonKey, COUNT> sk{out, vr[0], vr[1], vr[2], CanonKey{sc.G}, sc.red_count};
         backward_sweep<2>(sc, x, R, ray, act, V, vr, sk, nullptr, va * kap);
@@ -706,6 +718,30 @@ __global__ void __launch_bounds__(kThreads) k_tile_rows(DevScene sc, int* rows) 
     }
 }
 
+// Store rows each ray's A p reads (its non-zero prefix) and its grid samples,
+// summed over the rays of the tiles [tile_lo, n_tiles): one 64-bit atomic per
+// warp and sum.
+__global__ void __launch_bounds__(kThreads) k_coef_prefix(DevScene sc, const int* __restrict__ keff,
+                                                          unsigned long long* sums) {
+    unsigned long long a = 0ull, b = 0ull;
+    PERF_TILE_LOOP {
+        long long ray;
+        if (!tile_pixel(sc, tile, lane, ray)) continue;
+        Ray R;
+        ray_setup(sc, ray, R);
+        a += (unsigned long long)keff[ray];
+        b += (unsigned long long)R.K;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(kFull, a, o);
+        b += __shfl_down_sync(kFull, b, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicAdd(sums, a);
+        atomicAdd(sums + 1, b);
+    }
+}
+
 // The coefficient-cached A p of one lane's ray: J p, then the scatter of
 // J^T (J p).  Splitting the two halves into two launches, with v = J p of
 // every ray stored in between, measured slower on GB300 (102-113 against
@@ -724,7 +760,11 @@ __device__ __forceinline__ void coef_apply_tile(const DevScene& sc, const TP* __
     R.K = 0;
     R.shell_hit = 0u;
     R.delta = 0.0f;
-    if (act) ray_setup(sc, ray, R);
+    if (act) {
+        ray_setup(sc, ray, R);
+        // rows past the non-zero prefix are zeros: J p and the scatter skip them
+        if (sc.keff) R.K = min(R.K, sc.keff[ray]);
+    }
     const long long r0 = tile_off[tile];
     const int kmax_rows = (int)(tile_off[tile + 1] - r0) - sc.S - sc.aux;
     const float4* crow = coef + r0 * 32 + lane;
@@ -1121,6 +1161,15 @@ cudaError_t launch_shell_table(const DevScene& sc, float4* tab, cudaStream_t st)
     const long long blocks = (sc.n_rays + kThreads - 1) / kThreads;
     const int grid = (int)(blocks < 152 * 64 ? blocks : 152 * 64);
     k_shell_table<<<grid, kThreads, 0, st>>>(sc, 0, sc.n_rays, tab);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_coef_prefix(const DevScene& sc, const int* keff, unsigned long long* sums,
+                               cudaStream_t st) {
+    if (sc.n_tiles <= sc.tile_lo) return cudaSuccess;
+    k_coef_prefix<<<grid_blocks((const void*)k_coef_prefix, sc.n_tiles - sc.tile_lo), kThreads, 0,
+                    st>>>(sc, keff, sums);
     count_launch();
     return cudaGetLastError();
 }

@@ -63,6 +63,14 @@ struct perf_ctx {
     long long* tile_off = nullptr;     // first row of every pixel tile (n_tiles + 1)
     float* coef = nullptr;
     size_t coef_bytes = 0;             // allocated
+    int* keff = nullptr;               // per ray: length of its non-zero row prefix (DevScene::keff)
+    // the last perf_gn_solve step filled keff for the rays of tiles
+    // [0, keff_tiles) at tile width keff_tile_w and jitter epoch keff_epoch
+    bool keff_valid = false;
+    long long keff_tiles = 0;
+    int keff_tile_w = 0;
+    uint32_t keff_epoch = 0;
+    unsigned long long* d_prefix = nullptr;   // perf_coef_prefix's two sums
     long long coef_rows = 0;           // rows needed by the current tiling
     std::vector<long long> tile_off_h; // host copy of tile_off
     long long coef_tiles = 0;          // tiles [0, coef_tiles) are in the store
@@ -202,15 +210,19 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
         ctx->tab_epoch = epoch;
     }
     const size_t row_bytes = 32 * sizeof(float4);
+    // the per-ray prefix lengths (4 bytes per ray) come out of the budget too
+    const size_t keff_bytes = sizeof(int) * (size_t)ctx->n_rays;
     size_t budget;
     if (ctx->coef_budget > 0) {
         budget = (size_t)ctx->coef_budget;
     } else {
         size_t fr = 0, tot = 0;
         CK(cudaMemGetInfo(&fr, &tot));
-        const size_t avail = fr + ctx->coef_bytes, reserve = (size_t)6 << 30;
+        const size_t avail = fr + ctx->coef_bytes + (ctx->keff ? keff_bytes : 0),
+                     reserve = (size_t)6 << 30;
         budget = avail > reserve ? avail - reserve : 0;
     }
+    budget = budget > keff_bytes ? budget - keff_bytes : 0;
     // the longest prefix of tiles whose rows fit: those tiles' A p reads the
     // store, the rest recompute
     const std::vector<long long>& off = ctx->tile_off_h;
@@ -237,6 +249,11 @@ perf_status ensure_coef(perf_ctx* ctx, cudaStream_t st, bool* use) {
             return PERF_OK;
         }
         ctx->coef_bytes = need;
+    }
+    if (!ctx->keff && cudaMalloc(&ctx->keff, keff_bytes) != cudaSuccess) {
+        // without the prefix lengths every row is written and read
+        cudaGetLastError();
+        ctx->keff = nullptr;
     }
     ctx->coef_tiles = T1;
     *use = true;
@@ -433,7 +450,7 @@ perf_status perf_create(perf_ctx** out, const perf_scene* sc, const perf_cameras
 perf_status perf_destroy(perf_ctx* ctx) {
     if (!ctx) return PERF_ERR_INVALID_ARG;
     void* bufs[] = {ctx->cams, ctx->r, ctx->diag, ctx->grad, ctx->delta, ctx->rho, ctx->p,
-                    ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->shell_tab, ctx->hist, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
+                    ctx->xp, ctx->Ap, ctx->tile_off, ctx->coef, ctx->keff, ctx->d_prefix, ctx->shell_tab, ctx->hist, ctx->cross, ctx->blocks_ws, ctx->feat, ctx->x_trial, ctx->x16, ctx->p16, ctx->t16, ctx->s, ctx->dF};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
@@ -769,6 +786,7 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
         perf::DevScene dl = ctx->ds;
         perf::set_layout(dl, (use_coef && ctx->coef_tiles >= ctx->ds.n_tiles &&
                               o.precond != PERF_PRECOND_BLOCK4) ? ctx->brick_s : 0);
+        dl.keff = use_coef ? ctx->keff : nullptr;
         const int4 lay = perf::layout_of(dl);
         t_begin(ctx, PERF_T_DIAG, st);
         if (ctx->n_rays > 0)
@@ -779,6 +797,10 @@ perf_status perf_gn_solve(perf_ctx* ctx, float* x, const void* target, int32_t n
                                     use_coef ? ctx->tile_off : nullptr));
         t_end(ctx, PERF_T_DIAG, st);
         ctx->coef_used = use_coef;
+        ctx->keff_valid = dl.keff != nullptr;
+        ctx->keff_tiles = ctx->coef_tiles;
+        ctx->keff_tile_w = ctx->ds.tile_w;
+        ctx->keff_epoch = ctx->ds.epoch;
         const float* B = nullptr;
         long long nB = 0;
         if (o.precond == PERF_PRECOND_BLOCK_JACOBI ||
@@ -945,6 +967,7 @@ static void set_tiling(perf_ctx* ctx, int tw) {
 static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, perf_tuning* out,
                                  void* stream) {
     cudaStream_t st = S(stream);
+    ctx->keff_valid = false;   // the tuner's store fills overwrite the prefix lengths
     perf_status ps = ensure_pcg(ctx);
     if (ps != PERF_OK) return ps;
     SHELLS(ctx, st);
@@ -1003,15 +1026,19 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
             if (pc != PERF_OK) return pc;
             if (!fits || ctx->coef_tiles < ctx->ds.n_tiles) continue;
             ctx->ds.coef_tiles = ctx->coef_tiles;
-            CK(perf::launch_scatter(ctx->ds, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr,
+            // filled and timed as a Gauss-Newton step runs it (zero row tails skipped)
+            perf::DevScene dk = ctx->ds;
+            dk.keff = ctx->keff;
+            CK(perf::launch_scatter(dk, ctx->scene.dtype, 2, x, nullptr, PERF_F32, nullptr,
                                     ctx->diag, nullptr, nullptr, st, nullptr, ctx->coef,
                                     ctx->tile_off));
             float tile_best = 1e30f;
             int tile_cap = 0;
             for (int j = 0; j < 3; ++j) {
                 ctx->ds.cap_per_sm = caps[j];
+                dk.cap_per_sm = caps[j];
                 float ms = 0.f;
-                CK(time_coef(ctx->ds, ms));
+                CK(time_coef(dk, ms));
                 if (i == 0 && j == 0) incumbent = ms;
                 if (ms < tile_best) { tile_best = ms; tile_cap = caps[j]; }
                 if (ms < best) { best = ms; best_tw = tws[i]; best_cap = caps[j]; best_s = 0; }
@@ -1019,7 +1046,7 @@ static perf_status autotune_impl(perf_ctx* ctx, const void* x, const void* p, pe
             // the brick orders of the PCG vectors (4^3 and 8^3 voxels), at
             // this tile shape's best CTA cap
             for (int ls = 2; ls <= 3; ++ls) {
-                perf::DevScene dl = ctx->ds;
+                perf::DevScene dl = dk;
                 dl.cap_per_sm = tile_cap;
                 if (!perf::set_layout(dl, ls)) continue;
                 float ms = 0.f;
@@ -1227,6 +1254,28 @@ perf_status perf_coef_info(perf_ctx* ctx, int64_t* bytes_held, int32_t* last_use
     if (coverage)
         *coverage = ctx->coef_used && ctx->ds.n_tiles > 0
                         ? (double)ctx->coef_tiles / (double)ctx->ds.n_tiles : 0.0;
+    return PERF_OK;
+}
+
+perf_status perf_coef_prefix(perf_ctx* ctx, int64_t* rows_read, int64_t* rows_total,
+                             void* stream) {
+    if (!ctx) return PERF_ERR_INVALID_ARG;
+    if (!rows_read || !rows_total) return fail(ctx, PERF_ERR_INVALID_ARG, "coef_prefix: NULL output");
+    if (!ctx->keff_valid || !ctx->keff || ctx->keff_tile_w != ctx->ds.tile_w)
+        return fail(ctx, PERF_ERR_INVALID_ARG, "coef_prefix: the last Gauss-Newton step did not fill the store");
+    if (!ctx->d_prefix) CK(cudaMalloc(&ctx->d_prefix, 2 * sizeof(unsigned long long)));
+    cudaStream_t st = S(stream);
+    perf::DevScene d = ctx->ds;
+    d.n_tiles = ctx->keff_tiles;
+    d.tile_lo = 0;
+    d.epoch = ctx->keff_epoch;
+    unsigned long long h[2] = {0ull, 0ull};
+    CK(cudaMemsetAsync(ctx->d_prefix, 0, sizeof(h), st));
+    CK(perf::launch_coef_prefix(d, ctx->keff, ctx->d_prefix, st));
+    CK(cudaMemcpyAsync(h, ctx->d_prefix, sizeof(h), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *rows_read = (int64_t)h[0];
+    *rows_total = (int64_t)h[1];
     return PERF_OK;
 }
 

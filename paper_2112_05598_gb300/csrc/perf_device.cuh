@@ -57,6 +57,12 @@ struct DevScene {
     // Gauss-Newton step's PCG works on (p, A p, the diagonal, the gradient,
     // Delta, rho): see LayoutKey.  lay_s = 0: canonical [z][y][x].
     int lay_s, lay_ys, lay_zs;
+    // Per-ray length of the coefficient store's non-zero prefix (rays of the
+    // store's tiles): grid rows k >= keff[ray] hold only zeros -- samples
+    // whose transmittance has underflowed to 0 in binary32 -- so the diagonal
+    // march does not write them and the A p neither streams nor visits them.
+    // Null: every row up to the ray's sample count is written and read.
+    int* keff;
 };
 
 // Index of voxel (x, y, z) in a parameter-space vector.  lay_s = 0: the

@@ -117,6 +117,10 @@ cudaError_t launch_scatter(const DevScene& sc, int dtype, int mode, const void* 
 // coefficient store (its largest grid sample count + shells); A p (+p^T A p)
 // from p (p_dtype: 0 float, 1 bf16) and the stored coefficients.
 cudaError_t launch_tile_rows(const DevScene& sc, int* rows, cudaStream_t st);
+// sums[0] += sum of keff[ray], sums[1] += sum of K over the rays of tiles
+// [tile_lo, n_tiles) of sc
+cudaError_t launch_coef_prefix(const DevScene& sc, const int* keff, unsigned long long* sums,
+                               cudaStream_t st);
 cudaError_t launch_apply_coef(const DevScene& sc, const void* p, int p_dtype, const float* coef,
                               const long long* tile_off, float* out, double* pap, cudaStream_t st);
 // A p (+p^T A p) of an FP32 scene from paired records xp[v] = (x[v], p[v])

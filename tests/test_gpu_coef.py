@@ -7,7 +7,8 @@ import numpy as np
 import pytest
 
 from conftest import rel_l2
-from gpu_common import TOL_FP32, cuda_tensor, host, mid_state, pair_from_scene
+from gpu_common import (TOL_FP32, TOL_GN, assert_params, cuda_tensor, host, mid_state,
+                        pair_from_scene)
 
 pytestmark = pytest.mark.gpu
 
@@ -164,3 +165,65 @@ def test_coef_partial_store(prob):
     for a, b in zip(st_p, st_r):
         assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
     assert rel_l2(x_p, x_r) < TOL_FP32
+
+
+def _opaque(sc, scale=300.0):
+    """The ground truth with its opacities scaled up: past a primitive's
+    first voxel a ray's transmittance underflows to 0 in binary32 (optical
+    depth above about 104), so its later coefficient rows are zero."""
+    x = sc.x_gt.astype(np.float64).reshape(-1, 4).copy()
+    x[:sc.G ** 3, 3] *= scale
+    return x.astype(np.float32).ravel()
+
+
+@pytest.mark.parametrize("aux", [0, 1])
+def test_zero_tail_rows_skipped_exactly(prob, aux):
+    """Rows past a ray's last non-zero one are neither written nor read:
+    on an opaque state the A p reads fewer rows than the rays have samples
+    (perf_coef_prefix), and the step still equals the recomputing path,
+    which visits every sample, and the oracle's step.  At the constant start
+    nothing underflows and every row is read."""
+    from oracle import Oracle, gn_step
+    from paper_2112_05598_gb300 import Context
+    sc, target, _ = prob
+    xo = _opaque(sc)
+    res = {}
+    for budget in (-1, 0):
+        ctx = Context.from_scene(sc, pcg_iters=3, pcg_fixed=1, aux=aux, aux_lambda=0.01)
+        ctx.set_coef_budget(budget)
+        xd = cuda_tensor(xo.copy())
+        st = ctx.gn_solve(xd, cuda_tensor(target), 1)[0]
+        res[budget] = (st, host(xd))
+        if budget == -1:
+            assert ctx.coef_info()["used"]
+            pre = ctx.coef_prefix()
+            print(f"[coef] opaque state, aux {aux}: {pre['read']} of {pre['total']} rows read")
+            assert 0 < pre["read"] < pre["total"]
+            x0 = cuda_tensor(sc.x0.copy())
+            ctx.gn_solve(x0, cuda_tensor(target), 1)
+            pre0 = ctx.coef_prefix()
+            assert pre0["read"] == pre0["total"] > 0
+        ctx.close()
+    (a, xa), (b, xb) = res[-1], res[0]
+    assert a["accepted"] == b["accepted"]
+    assert abs(a["F_after"] - b["F_after"]) <= TOL_FP32 * b["F_after"]
+    assert rel_l2(xa, xb) < TOL_FP32
+    orc = Oracle(sc.G, sc.radii, sc.env_h, sc.env_w, sc.c2w, sc.focal, sc.width, sc.height,
+                 max_samples=sc.cfg.max_samples, aux=aux, aux_lambda=0.01)
+    ref = gn_step(orc, xo.astype(np.float64), target, 3)
+    assert a["accepted"] == ref.accepted
+    assert abs(a["F_before"] - ref.F_before) <= TOL_FP32 * ref.F_before
+    if abs(a["gamma"] - ref.gamma) <= 1e-9:
+        assert_params(xa, ref.x, ref.diag, TOL_GN, what=f"opaque state, aux {aux}")
+
+
+def test_coef_prefix_needs_a_filled_store(prob):
+    from paper_2112_05598_gb300 import Context, PerfError
+    sc, target, x = prob
+    ctx = Context.from_scene(sc, pcg_iters=1, pcg_fixed=1)
+    with pytest.raises(PerfError):
+        ctx.coef_prefix()
+    ctx.set_coef_budget(0)
+    ctx.gn_solve(cuda_tensor(x), cuda_tensor(target), 1)
+    with pytest.raises(PerfError):
+        ctx.coef_prefix()
