@@ -65,6 +65,7 @@ struct perf_batch {
     long long* tile_off = nullptr;
     float* coef = nullptr;
     size_t coef_bytes = 0;
+    int* keff = nullptr;                 // per ray: its non-zero row prefix (DevScene::keff)
     long long coef_rows = 0;
     int tab_tile_w = 0;
     bool use_coef = false;               // the PCG loop reads the store
@@ -168,15 +169,19 @@ perf_status ensure_coef(perf_batch* b, cudaStream_t st, bool* use) {
         b->tab_tile_w = b->tile_w;
     }
     const size_t need = (size_t)b->coef_rows * 32 * 16;
+    // the per-ray prefix lengths (4 bytes per ray) come out of the budget too
+    const size_t keff_bytes = sizeof(int) * (size_t)b->n_rays;
     size_t budget;
     if (b->coef_budget > 0) {
         budget = (size_t)b->coef_budget;
     } else {
         size_t fr = 0, tot = 0;
         BK(cudaMemGetInfo(&fr, &tot));
-        const size_t avail = fr + b->coef_bytes, reserve = (size_t)6 << 30;
+        const size_t avail = fr + b->coef_bytes + (b->keff ? keff_bytes : 0),
+                     reserve = (size_t)6 << 30;
         budget = avail > reserve ? avail - reserve : 0;
     }
+    budget = budget > keff_bytes ? budget - keff_bytes : 0;
     if (need > budget) {
         if (b->coef) { cudaFree(b->coef); b->coef = nullptr; b->coef_bytes = 0; }
         return PERF_OK;
@@ -189,6 +194,18 @@ perf_status ensure_coef(perf_batch* b, cudaStream_t st, bool* use) {
             return PERF_OK;
         }
         b->coef_bytes = need;
+    }
+    if (!b->keff) {
+        // each scene's rays index their own slice; without the array every
+        // row is written and read
+        if (cudaMalloc(&b->keff, keff_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            b->keff = nullptr;
+        } else {
+            for (int i = 0; i < b->n; ++i) b->items[i].sc.keff = b->keff + b->ray_off[i];
+            BK(cudaMemcpy(b->d_items, b->items.data(), sizeof(BatchItem) * b->n,
+                          cudaMemcpyHostToDevice));
+        }
     }
     *use = true;
     return PERF_OK;
@@ -422,7 +439,7 @@ perf_status perf_batch_destroy(perf_batch* b) {
     if (!b) return PERF_ERR_INVALID_ARG;
     if (b->graph) cudaGraphExecDestroy(b->graph);
     if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
-    void* bufs[] = {b->shell_tab, b->d_items, b->d_start, b->d_seg, b->d_chunks, b->cams, b->counter, b->x_work, b->x_trial,
+    void* bufs[] = {b->keff, b->shell_tab, b->d_items, b->d_start, b->d_seg, b->d_chunks, b->cams, b->counter, b->x_work, b->x_trial,
                     b->r, b->diag, b->grad, b->delta, b->rho, b->p, b->Ap, b->s, b->F,
                     b->gamma, b->mask, b->tile_off, b->coef, b->d_lay};
     for (void* q : bufs)

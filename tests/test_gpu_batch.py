@@ -137,3 +137,30 @@ def test_batch_coef_store_equals_recompute(tune):
             assert abs(a["F_before"] - r["F_before"]) <= TOL_FP32 * r["F_before"]
             assert abs(a["F_after"] - r["F_after"]) <= TOL_FP32 * r["F_after"]
     assert rel_l2(xc, xr) < TOL_FP32
+
+
+def test_batch_zero_tail_rows_equal_recompute():
+    """Scenes whose opacities reach the hundreds per voxel step: past a ray's
+    first opaque voxel its transmittance underflows to 0 in binary32 and the
+    batch's store keeps only each ray's non-zero row prefix.  One step from
+    the store equals the recomputing batch, which visits every sample."""
+    from paper_2112_05598_gb300 import Batch
+    scenes = _scenes(seed=17)
+    for s in scenes:
+        x = s["x"].astype(np.float64).reshape(-1, 4)
+        x[:s["G"] ** 3, 3] *= 300.0
+        s["x"] = x.astype(np.float32).ravel()
+    out = {}
+    for budget in (-1, 0):
+        b = Batch(scenes, max_samples=64, pcg_iters=1, pcg_fixed=1)
+        b.set_coef_budget(budget)
+        x = cuda_tensor(_cat(b, scenes, "x"))
+        t = cuda_tensor(_cat(b, scenes, "target"))
+        stats = b.gn_solve(x, t, 1)
+        out[budget] = (stats, host(x), b.coef_info())
+    (sc, xc, ic), (sr, xr, ir) = out[-1], out[0]
+    assert ic["used"] and not ir["used"]
+    for a, r in zip(sc[0], sr[0]):
+        assert a["accepted"] == r["accepted"]
+        assert abs(a["F_after"] - r["F_after"]) <= TOL_FP32 * r["F_after"]
+    assert rel_l2(xc, xr) < TOL_FP32
