@@ -98,3 +98,22 @@ def test_grid_option_scales_the_sample_cap():
     assert (big.G, big.max_samples) == (512, 1024)
     assert (big.n_cams, big.width, big.radii, big.seed) == (base.n_cams, base.width, base.radii,
                                                            base.seed)
+
+
+def test_traffic_record_scales_by_rows_streamed(tmp_path, monkeypatch):
+    """A record taken on a launch that read every row, applied to a launch
+    that reads a fraction of them (zero row tails skipped): the bytes scale
+    by samples x rows-read over the capture's samples x rows-read."""
+    rec = tmp_path / "rec.md"
+    rec.write_text("- kernel: `K`\n- workload: `W`\n- source_sha256: `H`\n"
+                   "- dram_bytes_per_launch: `1000`\n- samples_per_launch: `10`\n"
+                   "- rows_read_fraction: `1.0`\n")
+    monkeypatch.setattr(bench, "TRAFFIC_PROFILE", str(rec))
+    monkeypatch.setattr(bench, "kernel_source_hash", lambda: "H")
+    assert bench.recorded_traffic("K", "W", 40) == 4000
+    assert bench.recorded_traffic("K", "W", 40, 0.5) == 2000
+    rec.write_text(rec.read_text().replace("`1.0`", "`0.5`"))
+    assert bench.recorded_traffic("K", "W", 40, 0.5) == 4000
+    # without the field the capture is taken to have read every row
+    rec.write_text(rec.read_text().replace("- rows_read_fraction: `0.5`\n", ""))
+    assert bench.recorded_traffic("K", "W", 20) == 2000
