@@ -940,6 +940,10 @@ def run_ours(args, rank, world, local):
         ctx.set_brick(args.brick)
         tuning = dict(tuning, brick=args.brick, brick_fixed=True)
     del probe
+    # the end-to-end steps below repeat the timed steps from the same state
+    # (a step's A p gets cheaper as more rays turn opaque and their zero row
+    # tails are skipped)
+    x_host = x.detach().to(dtype=torch.float32).cpu().pin_memory()
     torch.cuda.synchronize()
     ctx.enable_timing(True)
     ctx.timing(reset=True)
@@ -974,9 +978,8 @@ def run_ours(args, rank, world, local):
 
     # end to end through the public API with host buffers
     e2e_steps = args.e2e_steps or args.steps
-    # the e2e steps continue the trajectory from the timed steps' state, so
-    # that both numbers measure the same kind of Gauss-Newton step
-    x_host = x.detach().to(dtype=torch.float32).cpu().pin_memory()
+    # from the state the timed steps started in (x_host), so that both numbers
+    # measure the same Gauss-Newton steps; each step's x goes back to x_host
     t_host = target.cpu().pin_memory()
     x_dev = torch.empty_like(x)
     t_dev = torch.empty_like(target)
