@@ -117,3 +117,49 @@ def test_traffic_record_scales_by_rows_streamed(tmp_path, monkeypatch):
     # without the field the capture is taken to have read every row
     rec.write_text(rec.read_text().replace("- rows_read_fraction: `0.5`\n", ""))
     assert bench.recorded_traffic("K", "W", 20) == 2000
+
+
+class _FakeCtx:
+    """Stands in for paper_2112_05598_gb300.Context in the bench's host
+    helpers: records the calls and plays back counts."""
+
+    def __init__(self, prefix=None, lanes=0, iters=2):
+        self.prefix, self.lanes, self.iters = prefix, lanes, iters
+        self.calls = []
+        self.counter = None
+
+    def coef_prefix(self):
+        from paper_2112_05598_gb300 import PerfError
+        if self.prefix is None:
+            raise PerfError(2, "coef_prefix: the last Gauss-Newton step did not fill the store")
+        return dict(read=self.prefix[0], total=self.prefix[1])
+
+    def set_atomic_counter(self, t):
+        self.counter = t
+        self.calls.append(("counter", t is not None))
+
+    def set_options(self, **kw):
+        self.calls.append(("options", kw))
+
+    def gn_solve(self, x, target, n):
+        self.calls.append(("solve", n))
+        if self.counter is not None:
+            self.counter += self.lanes
+        return [dict(pcg_iters=self.iters)]
+
+
+def test_rows_read_fraction_of_the_last_step():
+    assert bench.rows_read_fraction(_FakeCtx(prefix=(30, 40))) == 0.75
+    assert bench.rows_read_fraction(_FakeCtx(prefix=(0, 0))) is None
+    assert bench.rows_read_fraction(_FakeCtx(prefix=None)) is None
+
+
+def test_count_lane_ops_per_apply_and_state_restored():
+    """Lane operations per A p over one 2-iteration step on a copy of x; the
+    counter is detached and the iteration count restored afterwards."""
+    import torch
+    ctx = _FakeCtx(lanes=600, iters=2)
+    x = torch.zeros(8)
+    assert bench.count_lane_ops(ctx, x, torch.zeros(3), 50) == 300.0
+    assert ctx.calls == [("counter", True), ("options", {"pcg_iters": 2}), ("solve", 1),
+                         ("counter", False), ("options", {"pcg_iters": 50})]
