@@ -1035,6 +1035,10 @@ def run_ours(args, rank, world, local):
     achieved = FLOP_PER_SAMPLE_METHOD * samples / apply_s / 1e12
     # (a partial store: weighted by the tiles each kernel runs)
     impl_flop = cov * FLOP_PER_SAMPLE_COEF + (1.0 - cov) * FLOP_PER_SAMPLE_RECOMPUTE
+    # the mean share of the store's rows its A p reads (each ray's non-zero
+    # prefix; 1 without a store): the samples the kernels actually visit
+    rf = 0.5 * sum(rows_read) if rows_read else 1.0
+    visited = samples * (cov * rf + (1.0 - cov))
     compulsory = APPLY_COMPULSORY_BYTES_PER_PARAM * sc.n_params
     roof = {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
             "frac": achieved / fp32_peak,
@@ -1042,19 +1046,18 @@ def run_ours(args, rank, world, local):
             "peak_source": f"{sm_count} SMs x 128 FP32 lanes x 2 FLOP x {sm_mhz:.0f} MHz "
                            f"(max SM clock, {peak_src})",
             "kernel": apply_kernel,
-            "traffic": recorded_traffic(apply_kernel, args.workload, samples,
-                                        0.5 * sum(rows_read) if rows_read else 1.0)
+            "traffic": recorded_traffic(apply_kernel, args.workload, samples, rf)
             if args.cams is None and args.grid is None else None,
             "traffic_source": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a 4-camera "
                               "capture, scaled by the store rows streamed: samples x the mean "
                               "of the rows-read fractions before and after the timed steps "
                               "(profiles/apply_coef_traffic_scale128.md)",
             "impl_flop_per_sample": impl_flop,
-            "impl_alu_frac": impl_flop * samples / apply_s / 1e12 / fp32_peak,
+            "samples_visited_per_launch": visited,
+            "impl_alu_frac": impl_flop * visited / apply_s / 1e12 / fp32_peak,
             "compulsory_bytes_per_launch": compulsory,
             "hbm_frac_compulsory": compulsory / apply_s / 1e9 / hbm_peak}
     if coef:
-        rf = 0.5 * sum(rows_read) if rows_read else 1.0
         design = int(COEF_BYTES_PER_SAMPLE * samples * rf) + ((2 if bf else 4) + 4) * sc.n_params
         roof["design_traffic"] = {
             "what": "coefficient store: 16 B per sample or shell hit streamed twice per A p "
